@@ -1,0 +1,152 @@
+"""Seeded synthetic inputs: triangulated dielectric bodies and excitation vectors.
+
+This module generates *inputs* only (vertex/triangle arrays, region tables,
+material tables, random coefficient vectors). It holds none of the solver's
+arithmetic and is the one module shared by the CUDA path, its tests, the bench
+and the CPU oracle.
+
+Geometry conventions (the same ones the C ABI documents for ``sie_build_mesh``):
+
+* ``verts``  float64 [nv, 3] in metres (lambda_0 = 1 m throughout).
+* ``tris``   int32   [nt, 3]; the normal (v1-v0) x (v2-v0) points into
+  ``tri_regions[t, 0]`` (the "+" region); ``tri_regions[t, 1]`` is the region
+  behind the surface.
+* ``media``  float64 [nr, 4] = (eps_r real, eps_r imag, mu_r real, mu_r imag);
+  region 0 is the unbounded host medium that contains the sources.  Lossy media
+  have eps_r imag < 0 (time convention exp(+j omega t)).
+
+The bodies stand in for the paper's examples (single and multi-layer dielectric
+spheres of Sect. "Simulation Results", Fig. 5); the paper's own meshes are not
+published, so geodesic spheres of stated frequency are used.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+C0 = 299792458.0          # speed of light [m/s]
+LAMBDA0 = 1.0             # free-space wavelength of every synthetic case [m]
+FREQ_HZ = C0 / LAMBDA0    # 299.792458 MHz
+
+
+def _icosahedron():
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = np.array([
+        [-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0],
+        [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+        [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], dtype=np.float64)
+    f = np.array([
+        [0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11],
+        [1, 5, 9], [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8],
+        [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9],
+        [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int64)
+    return v / np.linalg.norm(v, axis=1, keepdims=True), f
+
+
+def geodesic_sphere(nu: int, radius: float, center=(0.0, 0.0, 0.0)):
+    """Geodesic sphere of frequency ``nu``: 20 nu^2 triangles, 30 nu^2 edges,
+    10 nu^2 + 2 vertices, every vertex on the sphere, normals pointing outward.
+    nu = 8 gives the 1280-triangle / 1920-edge mesh of a level-3 icosphere."""
+    if nu < 1:
+        raise ValueError("nu must be >= 1")
+    iv, faces = _icosahedron()
+    # integer lattice keys make the vertex merge across faces exact
+    key_to_idx: dict = {}
+    pts = []
+    tris = []
+    # global lattice: a point is a + (b-a) i/nu + (c-a) j/nu; key it by the
+    # exact barycentric combination over icosahedron vertex ids
+    for (a, b, c) in faces:
+        local = {}
+        for i in range(nu + 1):
+            for j in range(nu + 1 - i):
+                k = nu - i - j
+                comb = {}
+                for vid, w in ((a, k), (b, i), (c, j)):
+                    if w:
+                        comb[vid] = comb.get(vid, 0) + w
+                key = tuple(sorted(comb.items()))
+                idx = key_to_idx.get(key)
+                if idx is None:
+                    p = (iv[a] * k + iv[b] * i + iv[c] * j) / nu
+                    idx = len(pts)
+                    key_to_idx[key] = idx
+                    pts.append(p)
+                local[(i, j)] = idx
+        for i in range(nu):
+            for j in range(nu - i):
+                tris.append((local[(i, j)], local[(i + 1, j)], local[(i, j + 1)]))
+                if i + j < nu - 1:
+                    tris.append((local[(i + 1, j)], local[(i + 1, j + 1)], local[(i, j + 1)]))
+    P = np.array(pts, dtype=np.float64)
+    P = P / np.linalg.norm(P, axis=1, keepdims=True) * radius + np.asarray(center, np.float64)
+    T = np.array(tris, dtype=np.int32)
+    # orient outward
+    c = P[T].mean(axis=1) - np.asarray(center)
+    n = np.cross(P[T[:, 1]] - P[T[:, 0]], P[T[:, 2]] - P[T[:, 0]])
+    flip = np.einsum("ij,ij->i", n, c) < 0
+    T[flip] = T[flip][:, [0, 2, 1]]
+    return P, T
+
+
+def homogeneous_sphere(nu=8, radius=0.5, eps_r=4.0, mu_r=1.0):
+    """Single dielectric sphere in free space (one interface, two regions)."""
+    v, t = geodesic_sphere(nu, radius)
+    regions = np.tile(np.array([[0, 1]], np.int32), (len(t), 1))
+    eps = complex(eps_r)
+    media = np.array([[1.0, 0.0, 1.0, 0.0], [eps.real, eps.imag, mu_r, 0.0]], np.float64)
+    return dict(verts=v, tris=t, tri_regions=regions, media=media)
+
+
+def coated_sphere(nu_outer=30, nu_inner=20, r_outer=1.5, r_inner=1.0, eps_shell=2.56, eps_core=4.0):
+    """Two-layer sphere: region 0 free space, region 1 shell, region 2 core."""
+    vo, to = geodesic_sphere(nu_outer, r_outer)
+    vi, ti = geodesic_sphere(nu_inner, r_inner)
+    verts = np.concatenate([vo, vi])
+    tris = np.concatenate([to, ti + len(vo)]).astype(np.int32)
+    regions = np.concatenate([np.tile([[0, 1]], (len(to), 1)), np.tile([[1, 2]], (len(ti), 1))]).astype(np.int32)
+    es, ec = complex(eps_shell), complex(eps_core)
+    media = np.array([[1, 0, 1, 0], [es.real, es.imag, 1, 0], [ec.real, ec.imag, 1, 0]], np.float64)
+    return dict(verts=verts, tris=tris, tri_regions=regions, media=media)
+
+
+def tetra_body(size=0.3, eps_r=4.0):
+    """Tiny closed body (4 triangles, 6 edges) for brute-force checks."""
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float64) * size
+    t = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]], np.int32)
+    regions = np.tile(np.array([[0, 1]], np.int32), (4, 1))
+    media = np.array([[1, 0, 1, 0], [eps_r, 0, 1, 0]], np.float64)
+    return dict(verts=v, tris=t, tri_regions=regions, media=media)
+
+
+# Named workloads (sizes follow the configurations the solver is measured on)
+def workload(name: str):
+    if name == "sphere_c1":      # radius 0.5 lambda0, eps 4, 1280 tri, 3840 unknowns
+        return homogeneous_sphere(nu=8, radius=0.5, eps_r=4.0)
+    if name == "coated_c2":      # 1.0/1.5 lambda0, eps 4/2.56, ~78k unknowns
+        return coated_sphere(30, 20)
+    if name == "coated_small":   # reduced coated sphere, ~12.5k unknowns
+        return coated_sphere(12, 8)
+    if name == "coated_tiny":    # coated sphere small enough for dense CPU checks
+        return coated_sphere(6, 4)
+    if name == "sphere_tiny":
+        return homogeneous_sphere(nu=3, radius=0.5, eps_r=4.0)
+    raise KeyError(name)
+
+
+def random_coefficients(n_unknowns: int, nrhs: int = 1, seed: int = 1234):
+    """Complex standard-normal coefficient vectors, shape [nrhs, n_unknowns]."""
+    rng = np.random.default_rng(seed)
+    x = (rng.standard_normal((nrhs, n_unknowns)) + 1j * rng.standard_normal((nrhs, n_unknowns))) / np.sqrt(2.0)
+    return x.astype(np.complex128)
+
+
+def bistatic_angles(n=361):
+    """Observation angles theta in [0, 180] deg in the phi = 0 plane, as (theta, phi) radians."""
+    th = np.linspace(0.0, np.pi, n)
+    return np.stack([th, np.zeros_like(th)], axis=1)
+
+
+def monostatic_incidences(n, seed=None):
+    """Incidence list rows (theta_i, phi_i, pol_angle, E0): theta uniform in [0, pi], phi = 0, theta-pol."""
+    th = np.linspace(0.0, np.pi, n)
+    return np.stack([th, np.zeros(n), np.zeros(n), np.ones(n)], axis=1)

@@ -1,0 +1,340 @@
+"""Pins of the CPU oracle against facts fixed by mathematics and the paper
+(closed forms, invariants, brute force) -- never against the CUDA path."""
+from math import factorial
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_1704_06862_gb300 import geometry as geo
+from oracle import fill, farfield, mie, potentials, quadrature, solvers, tree
+from oracle.rwg import Mesh, material
+
+
+# ---------------------------------------------------------------- quadrature
+def _mono(b, w, p, q):
+    return 0.5 * np.sum(w * b[:, 1] ** p * b[:, 2] ** q)
+
+
+def test_radon7_exact_to_degree5_not_6():
+    b, w = quadrature.radon7()
+    assert abs(w.sum() - 1.0) < 1e-15
+    for p in range(6):
+        for q in range(6 - p):
+            exact = factorial(p) * factorial(q) / factorial(p + q + 2)
+            assert abs(_mono(b, w, p, q) - exact) < 1e-15
+    assert abs(_mono(b, w, 6, 0) - factorial(6) / factorial(8)) > 1e-6
+
+
+def test_collapsed_gauss_degree():
+    for n in (2, 3, 4, 6):
+        b, w = quadrature.collapsed_gauss(n)
+        for p in range(2 * n - 1):
+            for q in range(2 * n - 1 - p):
+                exact = factorial(p) * factorial(q) / factorial(p + q + 2)
+                assert abs(_mono(b, w, p, q) - exact) < 1e-14
+
+
+# ---------------------------------------------------------------- potentials
+TV = np.array([[0.1, 0.05, 0.0], [1.0, 0.2, 0.1], [0.3, 0.9, -0.2]])
+
+
+def _area(tv):
+    return 0.5 * np.linalg.norm(np.cross(tv[1] - tv[0], tv[2] - tv[0]))
+
+
+@pytest.mark.parametrize("r", [[0.4, 0.4, 0.8], [2.0, -1.0, 0.3], [0.45, 0.38, 0.05], [0.5, -0.4, -0.1]])
+def test_potentials_vs_brute_force_off_plane(r):
+    r = np.array(r)
+    b, w = quadrature.collapsed_gauss(80)
+    P = b @ TV
+    A = _area(TV)
+    I1, Ir, Ig, rho = potentials.triangle_potentials(r, TV)
+    D = r - P
+    R = np.linalg.norm(D, axis=1)
+    assert abs(I1 - A * np.sum(w / R)) < 1e-9 * abs(I1)
+    assert np.allclose(Ir, A * np.sum(w[:, None] * (P - rho) / R[:, None], 0), atol=1e-9)
+    assert np.allclose(Ig, A * np.sum(-w[:, None] * D / R[:, None] ** 3, 0), rtol=1e-7, atol=1e-8)
+
+
+def test_potential_gradient_is_derivative_of_I1():
+    r = np.array([0.35, 0.3, 0.07])
+    h = 1e-6
+    _, _, Ig, _ = potentials.triangle_potentials(r, TV)
+    fd = np.array([(potentials.triangle_potentials(r + h * e, TV)[0] - potentials.triangle_potentials(r - h * e, TV)[0]) / (2 * h)
+                   for e in np.eye(3)])
+    assert np.allclose(Ig, fd, rtol=1e-6, atol=1e-7)
+
+
+def test_potential_in_plane_point_by_duffy_split():
+    """Observation point inside the triangle: split at the point into three
+    sub-triangles and integrate 1/R with a rule collapsed at the point (the
+    Duffy map cancels the singularity) -- independent of the edge formulas."""
+    bary = np.array([0.3, 0.45, 0.25])
+    r = bary @ TV
+    I1, Ir, Ig, _ = potentials.triangle_potentials(r, TV)
+    b, w = quadrature.collapsed_gauss(40)
+    tot, totr = 0.0, np.zeros(3)
+    for a, c in ((0, 1), (1, 2), (2, 0)):
+        sub = np.array([TV[a], TV[c], r])
+        # put the collapsed vertex of the map at r:
+        bb = b[:, [0, 2, 1]]          # the map collapses at barycentric coordinate 1
+        P = bb @ sub
+        A = _area(sub)
+        R = np.linalg.norm(P - r, axis=1)
+        tot += A * np.sum(w / R)
+        totr += A * np.sum(w[:, None] * (P - r) / R[:, None], 0)
+    assert abs(I1 - tot) < 1e-10 * tot
+    assert np.allclose(Ir, totr, atol=1e-10)
+    n = np.cross(TV[1] - TV[0], TV[2] - TV[0])
+    assert abs(np.dot(Ig, n)) < 1e-12 * np.linalg.norm(n)     # principal value of the normal part
+
+
+# ---------------------------------------------------------------- mesh / RWG
+def test_rwg_counts_and_charge_neutrality():
+    for nu in (1, 2, 3, 8):
+        m = Mesh(**geo.homogeneous_sphere(nu=nu))
+        assert m.nt == 20 * nu * nu and m.ne == 30 * nu * nu
+    m = Mesh(**geo.homogeneous_sphere(nu=3))
+    # divergence is +l/A+ on T+ and -l/A- on T-: total charge vanishes (Eq. 22)
+    q = m.length / m.area[m.tp] * m.area[m.tp] - m.length / m.area[m.tm] * m.area[m.tm]
+    assert np.max(np.abs(q)) < 1e-14
+    # every triangle of a closed surface carries three bases
+    assert np.all(m.tri_edge >= 0)
+
+
+def test_rwg_normal_continuity_across_edge():
+    """f_n . (edge normal in each triangle) equals 1 on the edge from both sides."""
+    m = Mesh(**geo.homogeneous_sphere(nu=2))
+    for e in range(0, m.ne, 7):
+        a, b = m.verts[m.edge_v[e]]
+        mid = 0.5 * (a + b)
+        for t, v, s in ((m.tp[e], m.vp[e], 1.0), (m.tm[e], m.vm[e], -1.0)):
+            f = s * m.length[e] / (2 * m.area[t]) * (mid - m.verts[v])
+            nhat = np.cross(b - a, m.normal[t])
+            nhat /= np.linalg.norm(nhat)
+            # outward edge normal of T+ points toward T-
+            if np.dot(nhat, mid - m.centroid[t]) < 0:
+                nhat = -nhat
+            flux = np.dot(f, nhat) * s
+            assert abs(flux - 1.0) < 1e-12
+
+
+def test_material_branch():
+    k, eta = material([6.0, -0.6, 1.0, 0.0], 2 * np.pi)
+    assert k.imag < 0 and k.real > 0 and eta.real > 0
+    assert abs(k / (2 * np.pi) - np.sqrt(6 - 0.6j)) < 1e-14
+    assert abs(eta - 1 / np.sqrt(6 - 0.6j)) < 1e-14
+
+
+# ---------------------------------------------------------------- Galerkin fill
+@pytest.fixture(scope="module")
+def small_sphere_ops():
+    m = Mesh(**geo.homogeneous_sphere(nu=3, radius=0.5, eps_r=4.0))
+    return m, [fill.region_operators(m, l) for l in range(2)]
+
+
+def _regular_edge_pairs(m):
+    """Edge pairs none of whose four triangle pairs takes the singular path."""
+    sing = fill.singular_pairs(m, np.arange(m.nt))
+    e_t = np.stack([m.tp, m.tm], 1)
+    out = np.ones((m.ne, m.ne), bool)
+    for a in range(2):
+        for b in range(2):
+            out &= ~sing[e_t[:, a][:, None], e_t[:, b][None, :]]
+    return out
+
+
+def test_galerkin_symmetry(small_sphere_ops):
+    """Reciprocity: <t_m, L b_n> and <t_m, K b_n> are symmetric.  With the
+    same Radon rule on both triangles the symmetry is exact for regular pairs;
+    the singular outer rule breaks it at quadrature-error level only."""
+    m, ops = small_sphere_ops
+    reg = _regular_edge_pairs(m)
+    assert reg.sum() > 0.5 * m.ne ** 2
+    for op in ops:
+        for nm in ("L", "K", "G"):
+            A = op[nm]
+            scale = np.max(np.abs(A))
+            assert np.max(np.abs((A - A.T)[reg])) <= 1e-12 * scale, nm
+        assert np.max(np.abs(op["L"] - op["L"].T)) <= 3e-3 * np.max(np.abs(op["L"]))
+        assert np.max(np.abs(op["K"] - op["K"].T)) <= 0.25 * np.max(np.abs(op["K"]))
+
+
+@pytest.mark.slow
+def test_singular_K_converges_to_symmetric():
+    """Refining the outer rule of singular pairs drives K toward symmetry
+    (the exact operator is symmetric), pinning the extracted inner integrals."""
+    m = Mesh(**geo.homogeneous_sphere(nu=2, radius=0.5, eps_r=4.0))
+    asym = []
+    for n in (4, 16):
+        K = fill.region_operators(m, 1, outer_n=n)["K"]
+        asym.append(np.max(np.abs(K - K.T)) / np.max(np.abs(K)))
+    assert asym[1] < 0.25 * asym[0]
+
+
+def test_gram_matches_closed_form(small_sphere_ops):
+    """Self Gram entry of an RWG: sum over both triangles of
+    l^2/(4A^2) int |r - v|^2 = l^2/(4A) * (|e1|^2+|e2|^2+|e3|^2 ... ) closed form
+    int_T |r - v0|^2 dA = A/6 (|a|^2 + |b|^2 + a.b) with a, b the sides from v0."""
+    m, ops = small_sphere_ops
+    G = ops[0]["G"]
+    for e in range(0, m.ne, 11):
+        tot = 0.0
+        for t, v in ((m.tp[e], m.vp[e]), (m.tm[e], m.vm[e])):
+            others = [x for x in m.tris[t] if x != v]
+            a = m.verts[others[0]] - m.verts[v]
+            b = m.verts[others[1]] - m.verts[v]
+            A = m.area[t]
+            tot += m.length[e] ** 2 / (4 * A * A) * A / 6 * (a @ a + b @ b + a @ b)
+        assert abs(G[e, e] - tot) < 1e-13 * tot
+
+
+def test_coplanar_K_vanishes():
+    """For coplanar triangle pairs (t.(grad G x b) with all vectors in plane
+    is normal . in-plane = 0), K and n x K vanish identically -- flat plate."""
+    v = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0.5, 0.5, 0]], float) * 0.2
+    t = np.array([[0, 1, 4], [1, 2, 4], [2, 3, 4], [3, 0, 4]], np.int32)
+    m = Mesh(v, t, np.tile([[0, 1]], (4, 1)), np.array([[1, 0, 1, 0], [4, 0, 1, 0]]))
+    op = fill.region_operators(m, 0)
+    assert np.max(np.abs(op["K"])) < 1e-15 and np.max(np.abs(op["NK"])) < 1e-15
+    assert np.max(np.abs(op["L"])) > 1e-3
+
+
+def test_null_body_scatters_nothing():
+    """eps_r = 1 body: the exact solution is the equivalent current of the
+    incident wave with zero scattered field (Eqs. 1-2, extinction).  Every
+    sign of the formulation and excitation enters this check."""
+    m = Mesh(**geo.homogeneous_sphere(nu=3, radius=0.5, eps_r=1.0))
+    Z = fill.assemble(m)
+    b = fill.rhs(m, [[0, 0, 0, 1.0]])[0]
+    x = solvers.lu_solve(Z, b)
+    obs = geo.bistatic_angles(19)
+    s = farfield.rcs(m, x, obs)[0]
+    # a real body of this size scatters ~ +5 dBsm; the null body < -35 dBsm
+    assert np.max(10 * np.log10(s + 1e-300)) < -35.0
+    # the J and M parts of the solution equal the tangential incident fields
+    # n x H and -n x E projected on RWG (Gram solve) to discretisation accuracy
+    op = fill.region_operators(m, 0)
+    G = op["G"]
+    from oracle.quadrature import radon7, points
+    bR, wR = radon7()
+    khat, e = fill.plane_wave(0, 0, 0)
+    pj = np.zeros(m.ne, complex)
+    pm = np.zeros(m.ne, complex)
+    for t in range(m.nt):
+        P = points(m.verts[m.tris[t]], bR)
+        E = np.exp(-1j * 2 * np.pi * P @ khat)[:, None] * e
+        H = np.cross(khat, E)
+        J = np.cross(m.normal[t], H)
+        M = -np.cross(m.normal[t], E)
+        for j in range(3):
+            ed = m.tri_edge[t, j]
+            f = m.tri_sign[t, j] * m.length[ed] / (2 * m.area[t]) * (P - m.verts[m.tri_free[t, j]])
+            pj[ed] += m.area[t] * np.sum(wR * np.einsum("ax,ax->a", f, J))
+            pm[ed] += m.area[t] * np.sum(wR * np.einsum("ax,ax->a", f, M))
+    cj = np.linalg.solve(G, pj)
+    cm = np.linalg.solve(G, pm)
+    assert np.linalg.norm(x[0::2] - cj) / np.linalg.norm(cj) < 0.1
+    assert np.linalg.norm(x[1::2] - cm) / np.linalg.norm(cm) < 0.1
+
+
+@pytest.mark.slow
+def test_sphere_converges_to_mie():
+    """Homogeneous sphere, eps_r = 4, radius 0.5 lambda0 (Fig. 5 type check):
+    the RCS error against Mie shrinks with mesh refinement."""
+    obs = geo.bistatic_angles(37)
+    ref = 10 * np.log10(mie.sphere_bistatic(0.5, 4.0, obs[:, 0]))
+    errs = []
+    for nu in (3, 5):
+        m = Mesh(**geo.homogeneous_sphere(nu=nu, radius=0.5, eps_r=4.0))
+        x = solvers.lu_solve(fill.assemble(m), fill.rhs(m, [[0, 0, 0, 1.0]])[0])
+        s = 10 * np.log10(farfield.rcs(m, x, obs)[0][:, 0])
+        errs.append(np.mean(np.abs(s - ref)))
+    assert errs[1] < 0.6 * errs[0]
+    assert errs[1] < 1.0
+
+
+# ---------------------------------------------------------------- Mie series
+def test_mie_rayleigh_limit():
+    x, m = 0.01, 2.0 + 0.0j
+    a, b = mie.coefficients_homogeneous(x, m)
+    S1, S2 = mie.amplitudes(a, b, np.array([0.3, 1.2, 2.5]))
+    pol = (m * m - 1) / (m * m + 2)
+    assert np.allclose(np.abs(S1), x ** 3 * abs(pol), rtol=1e-3)
+    assert np.allclose(np.abs(S2), x ** 3 * abs(pol) * np.abs(np.cos([0.3, 1.2, 2.5])), rtol=1e-3)
+
+
+def test_mie_optical_theorem_lossless():
+    for x, m in ((3.14, 2.0), (9.4, 1.6)):
+        a, b = mie.coefficients_homogeneous(x, m)
+        qe, qs = mie.efficiencies(a, b, x)
+        assert abs(qe - qs) < 1e-10 * qs
+        S1, S2 = mie.amplitudes(a, b, np.array([0.0]))
+        assert abs(qe - 4 / x ** 2 * S1[0].real) < 1e-10 * qe   # forward amplitude
+    a, b = mie.coefficients_coated(2 * np.pi, 3 * np.pi, 2.0, 1.6)
+    qe, qs = mie.efficiencies(a, b, 3 * np.pi)
+    assert abs(qe - qs) < 1e-10 * qs
+
+
+def test_coated_reduces_to_homogeneous():
+    th = np.linspace(0, np.pi, 13)
+    # shell index = core index: a sphere of the outer radius
+    s1 = mie.coated_bistatic(1.0, 1.5, 4.0, 4.0, th)
+    s2 = mie.sphere_bistatic(1.5, 4.0, th)
+    assert np.allclose(s1, s2, rtol=1e-8)
+    # shell index = host index: a sphere of the inner radius
+    s1 = mie.coated_bistatic(1.0, 1.5, 4.0, 1.0, th)
+    s2 = mie.sphere_bistatic(1.0, 4.0, th)
+    assert np.allclose(s1, s2, rtol=1e-8)
+
+
+# ---------------------------------------------------------------- solvers / ILU / tree
+def _rand_system(n=60, seed=3):
+    rng = np.random.default_rng(seed)
+    A = np.eye(n) * 4 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    return A, b
+
+
+def test_fgmres_matches_lu():
+    A, b = _rand_system()
+    x, its, hist = solvers.fgmres(lambda v: A @ v, b, restart=10, tol=1e-10)
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) < 1e-8 * np.linalg.norm(x)
+    assert hist[-1] < 1e-10 and its > 10          # restarts happened
+
+
+def test_ilu0_full_pattern_is_exact_lu():
+    A, b = _rand_system(40)
+    F = solvers.ilu0(sp.csr_matrix(A))
+    z = solvers.ilu_apply(F, b)
+    assert np.linalg.norm(z - np.linalg.solve(A, b)) < 1e-10 * np.linalg.norm(z)
+
+
+def test_ilu0_defining_property():
+    """(L U)_ij = A_ij on the pattern; fill outside the pattern is dropped."""
+    rng = np.random.default_rng(5)
+    n = 50
+    mask = rng.random((n, n)) < 0.15
+    mask |= np.eye(n, dtype=bool)
+    A = np.where(mask, rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), 0) + 6 * np.eye(n)
+    F = solvers.ilu0(sp.csr_matrix(A)).toarray()
+    L = np.tril(F, -1) + np.eye(n)
+    U = np.triu(F)
+    LU = L @ U
+    assert np.max(np.abs((LU - A)[mask])) < 1e-12
+    assert np.max(np.abs(LU[~mask] - A[~mask])) > 1e-6    # genuinely incomplete
+
+
+def test_tree_colouring_and_order():
+    m = Mesh(**geo.homogeneous_sphere(nu=4))
+    ijk = tree.box_coords(m, 4)
+    col = tree.colour(ijk)
+    near = tree.near_mask(m, 4)
+    same_box = (ijk[:, None, :] == ijk[None, :, :]).all(axis=2)
+    # touching distinct boxes never share a colour
+    assert not np.any(near & ~same_box & (col[:, None] == col[None, :]))
+    perm = tree.ordering(m, 4)
+    assert np.array_equal(np.sort(perm), np.arange(m.ne))
+    c = col[perm]
+    assert np.all(np.diff(c) >= 0)
