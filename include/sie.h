@@ -1,0 +1,186 @@
+/*
+ * sie.h -- C ABI of the GB300 MLFMM-accelerated JMCFIE surface-integral solver.
+ *
+ * The library computes, on one GPU, the operator of the Galerkin/RWG
+ * discretisation of the JMCFIE surface integral equation for piecewise
+ * homogeneous dielectric bodies (paper: "Integral Equation Formulation",
+ * Eqs. 1-16; "Discretization and Iterative Solution", Eqs. 13-26) and its
+ * preconditioned iterative solution (ILU, Sect. "Simulation Results"), the
+ * plane-wave excitation (Eq. 30, Eqs. 20-21) and the radar cross section
+ * (Eqs. 27-29).  The matrix-vector product is split into an exactly integrated
+ * near field and a multilevel fast multipole (MLFMM) far field (cited by the
+ * paper as its accelerator, Conclusion).
+ *
+ * Conventions shared by every call:
+ *   - Units: SI; lambda0 is whatever freq_hz implies.  Time convention e^{+jwt}.
+ *   - Unknowns: one RWG basis per edge shared by two triangles of the same
+ *     interface surface (Eq. 22).  RWG numbering: lexicographic order of the
+ *     (min vertex, max vertex) pair of the edge; T+ is the owning triangle of
+ *     smaller index.  Two unknowns per edge, interleaved: (eta0 * c_n, v_n) --
+ *     the electric-current coefficient scaled by the free-space impedance, then
+ *     the magnetic-current coefficient (Eqs. 13-14 of the discretisation).
+ *     Rows are (eta0 * J-row, M-row) of Eq. 14/16; every block is dimensionless.
+ *   - Vectors are complex, interleaved (re, im), layout [nrhs][n_rwg][2]:
+ *     complex128 (double2) unless a call says otherwise.  "_dev" pointers are
+ *     device pointers on the context's device; "_host" pointers are host memory.
+ *   - The caller owns every buffer it passes; the context owns everything it
+ *     allocates and frees it in sie_destroy.
+ *   - All calls are asynchronous on the context's stream, except those that
+ *     return host data (documented per call), which synchronise it.
+ *   - No call throws.  Each returns a sie_status; sie_last_error() gives the
+ *     message of the last failure of that context.  A context is not thread-safe.
+ *   - There is no CPU fallback: every numerical step runs in this library's
+ *     CUDA kernels (sm_103a).
+ */
+#ifndef SIE_H
+#define SIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sie_ctx sie_ctx;
+
+typedef enum {
+  SIE_OK = 0,
+  SIE_EINVAL = 1,      /* invalid argument (null pointer, bad size, bad mesh) */
+  SIE_ENOMEM = 2,      /* device or host allocation failed */
+  SIE_ECUDA = 3,       /* a CUDA runtime call failed */
+  SIE_ESTATE = 4,      /* call out of order (e.g. matvec before setup) */
+  SIE_ENOTCONV = 5,    /* solver hit max_iters before the tolerance */
+  SIE_EBREAKDOWN = 6,  /* Krylov breakdown or non-finite residual */
+  SIE_ETIMEOUT = 7,    /* a bounded device wait gave up */
+  SIE_EZEROPIVOT = 8   /* ILU(0) met a singular 2x2 diagonal block */
+} sie_status;
+
+typedef enum {
+  SIE_PREC_FP64 = 0,   /* plain form: every step in FP64 */
+  SIE_PREC_MIXED = 1   /* near field, translations, patterns, ILU in FP32 complex;
+                          Arnoldi, Givens, true residual in FP64 */
+} sie_prec;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (or NULL: the context creates and owns a non-blocking stream).  */
+sie_status sie_create(sie_ctx **out, int device, void *cuda_stream);
+void sie_destroy(sie_ctx *ctx);
+const char *sie_last_error(const sie_ctx *ctx);
+
+/* Mesh and media (Fig. 2-3; Eqs. 12-13).
+ *   verts       [nv][3] float64, metres.
+ *   tris        [nt][3] int32; the normal (v1-v0)x(v2-v0) points into
+ *               tri_regions[t][0] ("+" region); tri_regions[t][1] is behind.
+ *   media       [nr][4] float64 = (eps_r re, eps_r im, mu_r re, mu_r im);
+ *               region 0 is the host medium holding the incident wave.
+ *               Passive media only (Im(eps_r mu_r) <= 0).
+ *   freq_hz     frequency.
+ *   n_rwg_out   receives the number of RWG edges (unknowns = 2 * n_rwg).
+ * Errors: SIE_EINVAL for junction edges (owned by > 2 triangles), an edge
+ * shared by triangles of different surfaces or of inconsistent orientation,
+ * region indices outside [0, nr), degenerate triangles.  Host-only work
+ * (topology); synchronous.  */
+sie_status sie_build_mesh(sie_ctx *ctx, const double *verts, int64_t nv, const int32_t *tris,
+                          int64_t nt, const int32_t *tri_regions, const double *media, int32_t nr,
+                          double freq_hz, int64_t *n_rwg_out);
+
+/* MLFMM options (the paper gives none; readings in the design doc). */
+typedef struct {
+  int32_t levels;   /* octree levels including the root, in [2, 12]; 2 puts
+                       every basis pair in the near field (dense product,
+                       no MLFMM).  Leaf edge =
+                       D / 2^(levels-1) with D = 1.0009765625 * largest extent
+                       of the vertex bounding box.  */
+  double digits;    /* d0 in L = kd + 1.8 d0^(2/3) (kd)^(1/3), d = sqrt(3) * box
+                       edge, k = Re k_l.  Typical 3. */
+} sie_mlfmm_opts;
+
+/* Octree, near-field pattern, preconditioner ordering and the far-field
+ * tables of every medium: direction samples, M2L translators, exact
+ * (spherical-harmonic projection) interpolation matrices, shift phases.
+ * Requires sie_build_mesh.  Synchronous. */
+sie_status mlfmm_setup(sie_ctx *ctx, const sie_mlfmm_opts *opts);
+
+typedef struct {
+  int32_t outer_order;  /* n of the n x n collapsed-Gauss outer rule on
+                           singular / near-singular triangle pairs (4) */
+  int32_t build_ilu;    /* nonzero: factor ILU(0) of the near field */
+} sie_fill_opts;
+
+/* Near-field fill on the GPU in FP64 (Eqs. 23-26 with singularity
+ * extraction; identity terms of Eqs. 8-11), leaf radiation/receive patterns
+ * of every medium, FP32 copies, and (optionally) the 2x2-block ILU(0) of the
+ * near field in the box-colour ordering.  Requires mlfmm_setup.  Synchronous
+ * (the ILU factorisation runs on the host CPU threads). */
+sie_status sie_fill_nearfield(sie_ctx *ctx, const sie_fill_opts *opts);
+
+/* y = Z x: near-field block-sparse product plus the MLFMM far field of every
+ * medium.  x_dev, y_dev: complex128 [nrhs][n_rwg][2], user (RWG) order; they
+ * may not alias.  prec selects the arithmetic of the product (inputs and
+ * outputs stay complex128).  Requires sie_fill_nearfield. */
+sie_status mlfmm_matvec(sie_ctx *ctx, const void *x_dev, void *y_dev, int64_t nrhs, sie_prec prec);
+
+/* Parts of the product, for testing: parts bit 1 = near field, bit 2 = far
+ * field (MLFMM).  Same conventions as mlfmm_matvec. */
+sie_status sie_matvec_parts(sie_ctx *ctx, const void *x_dev, void *y_dev, int64_t nrhs, sie_prec prec,
+                            int32_t parts);
+
+/* z = (L U)^-1 r with the ILU(0) factors of the near field (Sect. "Simulation
+ * Results", ILU preconditioner).  Same vector conventions.  Requires
+ * sie_fill_nearfield with build_ilu. */
+sie_status ilu_apply(sie_ctx *ctx, const void *r_dev, void *z_dev, int64_t nrhs, sie_prec prec);
+
+/* Tested plane-wave excitation (Eqs. 20-21, Eq. 30) for nrhs incidences.
+ * inc_host [nrhs][4] float64 = (theta_i, phi_i, pol, E0): the wave arrives
+ * from direction (theta_i, phi_i), propagates along -r(theta_i, phi_i), with
+ * E = E0 (cos(pol) theta_hat + sin(pol) phi_hat) exp(-j k0 khat.r).
+ * b_dev: complex128 [nrhs][n_rwg][2], user order.  */
+sie_status sie_plane_wave_rhs(sie_ctx *ctx, const double *inc_host, int64_t nrhs, void *b_dev);
+
+typedef struct {
+  int32_t restart;     /* Krylov dimension per cycle (50) */
+  int32_t max_iters;   /* total inner iterations per right-hand side */
+  double tol;          /* relative residual ||b - A x|| / ||b|| (FP64 operator) */
+  int32_t prec;        /* sie_prec of the inner operator and preconditioner */
+  int32_t precond;     /* 0: none, 1: ILU(0) (right preconditioning) */
+} sie_solve_opts;
+
+typedef struct {
+  int32_t iters;        /* inner iterations used */
+  int32_t restarts;     /* restart cycles (true-residual recomputations) */
+  double rel_residual;  /* final true relative residual, FP64 operator */
+  int32_t converged;    /* 1 if rel_residual <= tol */
+} sie_solve_stats;
+
+/* Right-preconditioned flexible GMRES(restart) for nrhs right-hand sides in
+ * lockstep (block of independent Krylov spaces).  b_dev, x_dev complex128
+ * [nrhs][n_rwg][2] user order; x_dev holds the initial guess on entry.
+ * stats_host [nrhs] receives per-RHS results.  Synchronous.  Returns
+ * SIE_ENOTCONV if any RHS did not reach tol. */
+sie_status gmres_solve(sie_ctx *ctx, const void *b_dev, void *x_dev, int64_t nrhs,
+                       const sie_solve_opts *opts, sie_solve_stats *stats_host);
+
+/* Bistatic radar cross section (Eqs. 27-29) of solutions x_dev (complex128
+ * [nrhs][n_rwg][2], user order) at nobs directions obs_host [nobs][2] =
+ * (theta, phi) in radians.  rcs_host [nrhs][nobs][2] receives
+ * (sigma_theta, sigma_phi) in m^2 for unit E0.  Synchronous. */
+sie_status rcs_farfield(sie_ctx *ctx, const void *x_dev, int64_t nrhs, const double *obs_host,
+                        int64_t nobs, double *rcs_host);
+
+/* Export of the near-field matrix for verification.  With rows == NULL only
+ * *nnzb is written.  Otherwise rows/cols [nnzb] int32 receive RWG (user)
+ * indices and vals [nnzb][4][2] float64 the block (JJ, JM, MJ, MM) as
+ * complex128.  Synchronous. */
+sie_status sie_near_export(sie_ctx *ctx, int32_t *rows, int32_t *cols, double *vals, int64_t *nnzb);
+
+/* Integer facts about the context for tests and reports: keys
+ *   0 n_rwg, 1 near blocks, 2 levels, 3 regions, 4 leaf boxes (all media),
+ *   5 bytes of the FP64 near field, 6 bytes of FP64 leaf patterns,
+ *   7 device bytes held, 8 kernel launches so far,
+ *   100 + 16*l + j: K (directions) of medium l at level j. */
+sie_status sie_query(const sie_ctx *ctx, int32_t key, int64_t *value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIE_H */

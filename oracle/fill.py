@@ -62,12 +62,15 @@ def k0_of(freq_hz=None):
     return 2.0 * np.pi * freq_hz / c0
 
 
-def singular_pairs(mesh: Mesh, tris_l):
-    """Pairs (p, q) of triangles of region l handled by singularity extraction."""
+def singular_pairs(mesh: Mesh, tris_l, test=None):
+    """Pairs (p, q) of triangles of region l handled by singularity extraction:
+    centroid distance < hmax_p + hmax_q.  Rows restricted to ``test`` (local
+    indices into tris_l) when given."""
+    test = np.arange(len(tris_l)) if test is None else test
     c = mesh.centroid[tris_l]
     h = mesh.hmax[tris_l]
-    d = np.linalg.norm(c[:, None, :] - c[None, :, :], axis=2)
-    return d < (h[:, None] + h[None, :])
+    d = np.linalg.norm(c[test][:, None, :] - c[None, :, :], axis=2)
+    return d < (h[test][:, None] + h[None, :])
 
 
 def _inner_regular(r, tq, k):
@@ -170,13 +173,13 @@ def region_operators(mesh: Mesh, l, rows=None, chunk=24, outer_n=4, freq_hz=None
         return out
     bR, wR = radon7()
     bS, wS = collapsed_gauss(outer_n)
-    sing = singular_pairs(mesh, tris_l)
     tv_all = mesh.verts[mesh.tris[tris_l]]
     pts_all = points(tv_all, bR)                                          # [Q,7,3]
     wq_all = mesh.area[tris_l][:, None] * wR[None, :]
     tq_all = dict(pts=pts_all, wq=wq_all)
     src = _tri_data(mesh, tris_l)
     test_local = np.nonzero(need_tri[tris_l])[0]
+    sing = singular_pairs(mesh, tris_l, test_local)          # [len(test_local), Q]
 
     def scatter(pi, qi, vals):
         m = src["e"][pi][:, :, None].repeat(3, axis=2).ravel()
@@ -189,11 +192,12 @@ def region_operators(mesh: Mesh, l, rows=None, chunk=24, outer_n=4, freq_hz=None
     # regular pairs: Radon rule on both triangles
     for c0 in range(0, len(test_local), chunk):
         pl = test_local[c0:c0 + chunk]
+        srow = sing[c0:c0 + chunk]
         I_G, I_Gr, I_gG = _inner_regular(pts_all[pl], tq_all, k)          # [P,A,Q,...]
         P, A, Q = I_G.shape
         pi = np.repeat(pl, Q)
         qi = np.tile(np.arange(Q), P)
-        mask = ~sing[pl].ravel()
+        mask = ~srow.ravel()
         pi, qi = pi[mask], qi[mask]
         I_G = I_G.transpose(0, 2, 1).reshape(P * Q, A)[mask]
         I_Gr = I_Gr.transpose(0, 2, 1, 3).reshape(P * Q, A, 3)[mask]
@@ -205,8 +209,7 @@ def region_operators(mesh: Mesh, l, rows=None, chunk=24, outer_n=4, freq_hz=None
 
     # singular / near-singular pairs: collapsed-Gauss outer rule, extracted inner
     sp_, sq_ = np.nonzero(sing)
-    keep = need_tri[tris_l][sp_]
-    sp_, sq_ = sp_[keep], sq_[keep]
+    sp_ = test_local[sp_]
     for c0 in range(0, len(sp_), 4096):
         pi, qi = sp_[c0:c0 + 4096], sq_[c0:c0 + 4096]
         r = points(tv_all[pi], bS)                                        # [N,16,3]

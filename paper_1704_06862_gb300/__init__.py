@@ -1,0 +1,228 @@
+"""Thin ctypes binding of the GB300 JMCFIE/MLFMM library (``libsie.so``).
+
+The functions below carry the names of the C ABI in ``include/sie.h`` and do
+argument marshalling only: every numerical step runs in the library's CUDA
+kernels.  Device buffers are passed as torch CUDA tensors (or raw integer
+device pointers); host arrays as numpy arrays.  There is no CPU fallback: if
+the shared library is missing, importing a function raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsie.so")
+
+SIE_PREC_FP64 = 0
+SIE_PREC_MIXED = 1
+
+STATUS = {0: "SIE_OK", 1: "SIE_EINVAL", 2: "SIE_ENOMEM", 3: "SIE_ECUDA", 4: "SIE_ESTATE", 5: "SIE_ENOTCONV",
+          6: "SIE_EBREAKDOWN", 7: "SIE_ETIMEOUT", 8: "SIE_EZEROPIVOT"}
+
+EXPORTED = ["sie_create", "sie_destroy", "sie_last_error", "sie_build_mesh", "mlfmm_setup", "sie_fill_nearfield",
+            "mlfmm_matvec", "sie_matvec_parts", "ilu_apply", "sie_plane_wave_rhs", "gmres_solve", "rcs_farfield",
+            "sie_near_export", "sie_query"]
+
+
+class SieError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sie_mlfmm_opts(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("digits", ctypes.c_double)]
+
+
+class sie_fill_opts(ctypes.Structure):
+    _fields_ = [("outer_order", ctypes.c_int32), ("build_ilu", ctypes.c_int32)]
+
+
+class sie_solve_opts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("prec", ctypes.c_int32), ("precond", ctypes.c_int32)]
+
+
+class sie_solve_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("converged", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libsie.so and declare the C signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "sie_create": ([ctypes.POINTER(P), ctypes.c_int, P], I32),
+        "sie_destroy": ([P], None),
+        "sie_last_error": ([P], ctypes.c_char_p),
+        "sie_build_mesh": ([P, P, I64, P, I64, P, P, I32, D, ctypes.POINTER(I64)], I32),
+        "mlfmm_setup": ([P, ctypes.POINTER(sie_mlfmm_opts)], I32),
+        "sie_fill_nearfield": ([P, ctypes.POINTER(sie_fill_opts)], I32),
+        "mlfmm_matvec": ([P, P, P, I64, I32], I32),
+        "sie_matvec_parts": ([P, P, P, I64, I32, I32], I32),
+        "ilu_apply": ([P, P, P, I64, I32], I32),
+        "sie_plane_wave_rhs": ([P, P, I64, P], I32),
+        "gmres_solve": ([P, P, P, I64, ctypes.POINTER(sie_solve_opts), ctypes.POINTER(sie_solve_stats)], I32),
+        "rcs_farfield": ([P, P, I64, P, I64, P], I32),
+        "sie_near_export": ([P, P, P, P, ctypes.POINTER(I64)], I32),
+        "sie_query": ([P, I32, ctypes.POINTER(I64)], I32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("host array must be C-contiguous")
+        return t.ctypes.data
+    raise TypeError(f"cannot pass {type(t)} as a pointer")
+
+
+def _check(ctx, rc):
+    if rc != 0:
+        msg = load_library().sie_last_error(ctx)
+        raise SieError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ----------------------------------------------------------------- C ABI, same names
+def sie_create(device: int = 0, stream=None):
+    ctx = ctypes.c_void_p()
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    rc = load_library().sie_create(ctypes.byref(ctx), device, s)
+    if rc != 0:
+        raise SieError(rc, "sie_create failed")
+    return ctx
+
+
+def sie_destroy(ctx):
+    load_library().sie_destroy(ctx)
+
+
+def sie_last_error(ctx) -> str:
+    msg = load_library().sie_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def sie_build_mesh(ctx, verts, tris, tri_regions, media, freq_hz):
+    v = np.ascontiguousarray(verts, np.float64)
+    t = np.ascontiguousarray(tris, np.int32)
+    r = np.ascontiguousarray(tri_regions, np.int32)
+    m = np.ascontiguousarray(media, np.float64)
+    n = ctypes.c_int64()
+    _check(ctx, load_library().sie_build_mesh(ctx, _ptr(v), len(v), _ptr(t), len(t), _ptr(r), _ptr(m), len(m),
+                                              float(freq_hz), ctypes.byref(n)))
+    return n.value
+
+
+def mlfmm_setup(ctx, levels, digits=3.0):
+    o = sie_mlfmm_opts(int(levels), float(digits))
+    _check(ctx, load_library().mlfmm_setup(ctx, ctypes.byref(o)))
+
+
+def sie_fill_nearfield(ctx, outer_order=4, build_ilu=True):
+    o = sie_fill_opts(int(outer_order), 1 if build_ilu else 0)
+    _check(ctx, load_library().sie_fill_nearfield(ctx, ctypes.byref(o)))
+
+
+def mlfmm_matvec(ctx, x, y, nrhs, prec=SIE_PREC_FP64):
+    _check(ctx, load_library().mlfmm_matvec(ctx, _ptr(x), _ptr(y), int(nrhs), int(prec)))
+
+
+def sie_matvec_parts(ctx, x, y, nrhs, prec=SIE_PREC_FP64, parts=3):
+    _check(ctx, load_library().sie_matvec_parts(ctx, _ptr(x), _ptr(y), int(nrhs), int(prec), int(parts)))
+
+
+def ilu_apply(ctx, r, z, nrhs, prec=SIE_PREC_FP64):
+    _check(ctx, load_library().ilu_apply(ctx, _ptr(r), _ptr(z), int(nrhs), int(prec)))
+
+
+def sie_plane_wave_rhs(ctx, inc, b):
+    inc = np.ascontiguousarray(np.atleast_2d(inc), np.float64)
+    _check(ctx, load_library().sie_plane_wave_rhs(ctx, _ptr(inc), len(inc), _ptr(b)))
+
+
+def gmres_solve(ctx, b, x, nrhs, restart=50, max_iters=1000, tol=1e-4, prec=SIE_PREC_FP64, precond=1,
+                check=True):
+    o = sie_solve_opts(int(restart), int(max_iters), float(tol), int(prec), int(precond))
+    st = (sie_solve_stats * int(nrhs))()
+    rc = load_library().gmres_solve(ctx, _ptr(b), _ptr(x), int(nrhs), ctypes.byref(o), st)
+    stats = [dict(iters=s.iters, restarts=s.restarts, rel_residual=s.rel_residual, converged=bool(s.converged))
+             for s in st]
+    if rc not in (0, 5) or (check and rc != 0):
+        _check(ctx, rc)
+    return stats
+
+
+def rcs_farfield(ctx, x, nrhs, obs):
+    obs = np.ascontiguousarray(obs, np.float64)
+    out = np.zeros((int(nrhs), len(obs), 2), np.float64)
+    _check(ctx, load_library().rcs_farfield(ctx, _ptr(x), int(nrhs), _ptr(obs), len(obs), _ptr(out)))
+    return out
+
+
+def sie_near_export(ctx):
+    n = ctypes.c_int64()
+    L = load_library()
+    _check(ctx, L.sie_near_export(ctx, None, None, None, ctypes.byref(n)))
+    rows = np.zeros(n.value, np.int32)
+    cols = np.zeros(n.value, np.int32)
+    vals = np.zeros((n.value, 4, 2), np.float64)
+    _check(ctx, L.sie_near_export(ctx, _ptr(rows), _ptr(cols), _ptr(vals), ctypes.byref(n)))
+    return rows, cols, vals[..., 0] + 1j * vals[..., 1]
+
+
+def sie_query(ctx, key):
+    v = ctypes.c_int64()
+    _check(ctx, load_library().sie_query(ctx, int(key), ctypes.byref(v)))
+    return v.value
+
+
+# ----------------------------------------------------------------- convenience (marshalling only)
+class Solver:
+    """Owns one context: mesh -> tree -> fill, then operator calls on torch tensors."""
+
+    def __init__(self, mesh: dict, levels: int, digits: float = 3.0, freq_hz: float = 299792458.0,
+                 device: int = 0, stream=None, outer_order: int = 4, build_ilu: bool = True):
+        self.ctx = sie_create(device, stream)
+        self.ne = sie_build_mesh(self.ctx, mesh["verts"], mesh["tris"], mesh["tri_regions"], mesh["media"], freq_hz)
+        mlfmm_setup(self.ctx, levels, digits)
+        sie_fill_nearfield(self.ctx, outer_order, build_ilu)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            sie_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vec(self, nrhs=1):
+        import torch
+        return torch.zeros((nrhs, self.ne, 2), dtype=torch.complex128, device="cuda")

@@ -1,0 +1,218 @@
+// Internal declarations of the GB300 JMCFIE/MLFMM library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "sie.h"
+
+#define SIE_HD __host__ __device__ __forceinline__
+
+// ------------------------------------------------------------------ complex
+template <typename T>
+struct cx {
+  T re, im;
+  SIE_HD cx() : re(0), im(0) {}
+  SIE_HD cx(T r, T i = 0) : re(r), im(i) {}
+  template <typename U>
+  SIE_HD explicit cx(const cx<U> &o) : re((T)o.re), im((T)o.im) {}
+};
+template <typename T> SIE_HD cx<T> operator+(cx<T> a, cx<T> b) { return cx<T>(a.re + b.re, a.im + b.im); }
+template <typename T> SIE_HD cx<T> operator-(cx<T> a, cx<T> b) { return cx<T>(a.re - b.re, a.im - b.im); }
+template <typename T> SIE_HD cx<T> operator-(cx<T> a) { return cx<T>(-a.re, -a.im); }
+template <typename T> SIE_HD cx<T> operator*(cx<T> a, cx<T> b) {
+  return cx<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T> SIE_HD cx<T> operator*(T s, cx<T> a) { return cx<T>(s * a.re, s * a.im); }
+template <typename T> SIE_HD cx<T> operator*(cx<T> a, T s) { return cx<T>(s * a.re, s * a.im); }
+template <typename T> SIE_HD cx<T> &operator+=(cx<T> &a, cx<T> b) { a.re += b.re; a.im += b.im; return a; }
+template <typename T> SIE_HD cx<T> &operator-=(cx<T> &a, cx<T> b) { a.re -= b.re; a.im -= b.im; return a; }
+template <typename T> SIE_HD cx<T> conj(cx<T> a) { return cx<T>(a.re, -a.im); }
+template <typename T> SIE_HD cx<T> cfma(cx<T> a, cx<T> b, cx<T> c) {  // a*b + c
+  return cx<T>(fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im)));
+}
+typedef cx<double> zd;
+typedef cx<float> zf;
+
+// ------------------------------------------------------------------ errors
+struct SieError {
+  sie_status code;
+  std::string msg;
+};
+#define SIE_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw SieError{SIE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};         \
+  } while (0)
+#define SIE_CHECK_LAUNCH() SIE_CUDA(cudaGetLastError())
+#define SIE_REQUIRE(cond, code, msg)       \
+  do {                                     \
+    if (!(cond)) throw SieError{code, msg}; \
+  } while (0)
+
+// ------------------------------------------------------------------ device buffers
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+// ------------------------------------------------------------------ one octree level of one medium
+struct LevelHost {
+  int lev = 0;       // level number (0 = root)
+  double a = 0;      // box edge
+  int L = 0, K = 0;  // truncation and number of directions (L+1)(2L+2)
+  int nbox = 0;
+  std::vector<int> ijk;       // [nbox][3]
+  std::vector<int> parent;    // index in level lev-1
+  std::vector<int> oct;       // octant of the box in its parent (bit0 x, bit1 y, bit2 z)
+  std::vector<int> ch_ptr, ch_idx;        // children CSR (level lev+1)
+  std::vector<int> il_ptr, il_src, il_slot;  // interaction list CSR, translator slot
+  std::vector<int> slot_code;             // offset code per translator slot
+  // device tables
+  double *d_dirs = nullptr;     // [K][9]: khat, theta_hat, phi_hat
+  void *d_T64 = nullptr, *d_T32 = nullptr;       // translators [nslot][K], weights and constants folded
+  void *d_A64 = nullptr, *d_A32 = nullptr;       // interpolation to this level from lev+1: [2K][2Kc] real
+  void *d_up64 = nullptr, *d_up32 = nullptr;     // [8][K] shift, child -> this (parent) level
+  void *d_dn64 = nullptr, *d_dn32 = nullptr;     // [8][K] shift, this level -> child
+  int *d_il_ptr = nullptr, *d_il_src = nullptr, *d_il_slot = nullptr;
+  int *d_ch_ptr = nullptr, *d_ch_idx = nullptr, *d_oct = nullptr, *d_parent = nullptr;
+  // work buffers (capacity nrhs_cap): S and I [nbox][2][2][K][R]
+  void *d_S = nullptr, *d_I = nullptr;
+};
+
+struct RegionHost {
+  int id = 0;
+  std::complex<double> k, eta;  // wavenumber, relative impedance eta_l / eta_0
+  int nb = 0;                   // bases of this medium
+  std::vector<int> basis_p;     // internal edge index
+  std::vector<int> basis_sign;  // s_l
+  std::vector<int> box_start;   // leaf boxes: [nleaf+1] ranges into the basis list
+  std::vector<LevelHost> lev;   // index = level number; levels 2..leaf carry tables
+  int *d_basis_p = nullptr, *d_basis_sign = nullptr, *d_box_start = nullptr, *d_basis_box = nullptr;
+  double *d_box_centre = nullptr;  // leaf box centres [nleaf][3]
+  void *d_V64 = nullptr, *d_V32 = nullptr;    // radiation patterns [nb][2][Kleaf]
+  void *d_RN64 = nullptr, *d_RN32 = nullptr;  // receive patterns of t x n [nb][2][Kleaf]
+  int *d_pairs = nullptr;       // near triangle pairs (p, q, singular) for the fill
+  int64_t npairs = 0;
+};
+
+struct IluHost {
+  bool ready = false;
+  int nboxes = 0;
+  std::vector<int> colour_ptr;     // boxes grouped by colour: [9]
+  int *d_box_start = nullptr;      // [nbox+1] internal edge ranges
+  int *d_box_list = nullptr;       // boxes in colour order
+  int *d_lo_ptr = nullptr, *d_lo_col = nullptr, *d_up_ptr = nullptr, *d_up_col = nullptr;
+  void *d_lo64 = nullptr, *d_lo32 = nullptr, *d_up64 = nullptr, *d_up32 = nullptr;  // off-box blocks [.][4]
+  int64_t *d_dense_off = nullptr;  // per box offset (in blocks) of the dense in-box factor
+  void *d_dense64 = nullptr, *d_dense32 = nullptr;  // column-major [j][i][4] per box
+  void *d_dinv64 = nullptr, *d_dinv32 = nullptr;    // inverse of U diagonal blocks [ne][4]
+  int max_box = 0;
+};
+
+struct sie_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error;
+  int64_t launches = 0;
+  int64_t dev_bytes = 0;
+  std::vector<DBuf> bufs;
+
+  // mesh
+  bool have_mesh = false, have_tree = false, have_fill = false;
+  double freq = 0, k0 = 0;
+  int nv = 0, nt = 0, nr = 0, ne = 0;
+  std::vector<double> verts;            // [nv][3]
+  std::vector<int> tris, tri_reg;       // [nt][3], [nt][2]
+  std::vector<double> media;            // [nr][4]
+  std::vector<double> area, normal, centroid, hmax;
+  std::vector<int> edge_v, tp, tm, vp, vm;  // user edge numbering
+  std::vector<double> elen;
+  std::vector<int> tri_edge, tri_free;  // [nt][3] user edge index / free vertex
+  std::vector<double> tri_sign;         // [nt][3]
+  std::vector<std::complex<double>> kreg, etareg;
+
+  // tree and ordering
+  int levels = 0;
+  double digits = 3;
+  double origin[3] = {0, 0, 0}, D = 0, hleaf = 0;
+  std::vector<int> perm, inv;           // perm[p] = user edge; inv[user] = p
+  std::vector<int> eijk;                // [ne][3] leaf box of each user edge
+  std::vector<int> leaf_start;          // global leaf boxes (internal order): edge ranges
+  std::vector<int> leaf_ijk;
+  std::vector<int> row_ptr, col;        // near pattern (internal indices), sorted rows
+  std::vector<RegionHost> reg;
+  IluHost ilu;
+
+  // device geometry
+  double *d_tri = nullptr;       // per triangle: 3 verts (9), normal (3), area (1), free verts (9) = 22 doubles
+  int *d_tri_e = nullptr;        // per triangle: 3 internal edge ids (-1 none)
+  double *d_tri_sg = nullptr;    // per triangle: 3 signs * len/(2A)
+  int *d_tri_reg = nullptr;      // [nt][2]
+  int *d_row_ptr = nullptr, *d_col = nullptr;
+  void *d_near64 = nullptr, *d_near32 = nullptr;  // [nnzb][4] blocks
+  int *d_perm = nullptr, *d_inv = nullptr;
+  int *d_edge_tris = nullptr;    // per internal edge: T+, T-
+  int *d_edge_reg = nullptr;     // per internal edge: (r+, r-)
+  double *d_quad = nullptr;      // outer singular rule (b0,b1,b2,w) * nq
+  int nq_sing = 16;
+
+  // work buffers
+  int64_t nrhs_cap = 0;
+  void *d_xi = nullptr, *d_yi = nullptr;          // internal-order FP64 vectors [R][ne][2]
+  void *d_xf = nullptr, *d_yf = nullptr;          // FP32 copies
+  void *d_gemm = nullptr;                         // interpolation scratch
+  size_t gemm_bytes = 0;
+  void *d_stage = nullptr;                        // small host-to-device staging area
+  size_t stage_bytes = 0;
+  // Krylov storage of the last solve shape (restart m, nrhs R)
+  int gm_m = 0, gm_R = 0;
+  void *gm_V = nullptr, *gm_Z = nullptr, *gm_b = nullptr, *gm_x = nullptr, *gm_w = nullptr;
+  void *gm_h = nullptr, *gm_s = nullptr;
+};
+
+// ------------------------------------------------------------------ host helpers (host.cpp)
+void *dev_alloc(sie_ctx *c, size_t bytes);
+template <typename T>
+T *dev_upload(sie_ctx *c, const std::vector<T> &v) {
+  if (v.empty()) return nullptr;
+  T *p = (T *)dev_alloc(c, v.size() * sizeof(T));
+  SIE_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return p;
+}
+void ensure_work(sie_ctx *c, int64_t nrhs);
+void *stage(sie_ctx *c, size_t bytes);
+
+// ------------------------------------------------------------------ launchers (fill.cu)
+void launch_near_fill(sie_ctx *c, int region);
+void launch_identity(sie_ctx *c);
+void launch_patterns(sie_ctx *c, int region);
+void launch_rhs(sie_ctx *c, const double *inc_dev, int nrhs, zd *b_internal);
+void launch_farfield(sie_ctx *c, const zd *x_internal, int nrhs, const double *obs_dev, int nobs, double *out_dev);
+void launch_to_f32(sie_ctx *c, const double *src, float *dst, int64_t n);
+
+// ------------------------------------------------------------------ launchers (operator.cu)
+template <typename T>
+void op_near(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool accumulate);
+template <typename T>
+void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs);
+template <typename T>
+void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs);
+void op_permute_in(sie_ctx *c, const zd *user, zd *internal, int nrhs);    // user -> internal
+void op_permute_out(sie_ctx *c, const zd *internal, zd *user, int nrhs);   // internal -> user
+void op_d2f(sie_ctx *c, const zd *a, zf *b, int64_t n);
+void op_f2d(sie_ctx *c, const zf *a, zd *b, int64_t n);
+
+// operator on internal-order FP64 vectors, in the requested arithmetic
+void apply_matvec(sie_ctx *c, const zd *x, zd *y, int nrhs, sie_prec prec, int parts);
+void apply_ilu(sie_ctx *c, const zd *r, zd *z, int nrhs, sie_prec prec);
+
+// ------------------------------------------------------------------ solver (solve.cu)
+sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int nrhs, const sie_solve_opts *o,
+                     sie_solve_stats *st);

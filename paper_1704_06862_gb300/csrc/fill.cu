@@ -1,0 +1,541 @@
+// Setup-time kernels in FP64: near-field Galerkin fill with singularity
+// extraction (Eqs. 23-26, identity terms of Eqs. 8-11), leaf radiation and
+// receive patterns for the MLFMM, tested plane-wave excitation (Eqs. 20-21,
+// Eq. 30) and far field / RCS (Eqs. 27-29).
+#include <cmath>
+
+#include "common.h"
+
+namespace {
+
+// Radon's 7-point degree-5 rule on a triangle (barycentric, weights sum to 1).
+__constant__ double c_rb[7][3];
+__constant__ double c_rw[7];
+bool g_rule_ready = false;
+
+void upload_radon() {
+  if (g_rule_ready) return;
+  const double s = std::sqrt(15.0);
+  const double a1 = (6.0 - s) / 21.0, a2 = (6.0 + s) / 21.0;
+  const double w1 = (155.0 - s) / 1200.0, w2 = (155.0 + s) / 1200.0;
+  double b[7][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3},
+                    {1 - 2 * a1, a1, a1}, {a1, 1 - 2 * a1, a1}, {a1, a1, 1 - 2 * a1},
+                    {1 - 2 * a2, a2, a2}, {a2, 1 - 2 * a2, a2}, {a2, a2, 1 - 2 * a2}};
+  double w[7] = {9.0 / 40.0, w1, w1, w1, w2, w2, w2};
+  SIE_CUDA(cudaMemcpyToSymbol(c_rb, b, sizeof(b)));
+  SIE_CUDA(cudaMemcpyToSymbol(c_rw, w, sizeof(w)));
+  g_rule_ready = true;
+}
+
+struct V3 {
+  double x, y, z;
+};
+__device__ __forceinline__ V3 v3(double x, double y, double z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double norm(V3 a) { return sqrt(dot(a, a)); }
+
+// complex 3-vector
+struct C3 {
+  zd x, y, z;
+};
+__device__ __forceinline__ zd cdot(V3 a, const C3 &b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ C3 ccross(const C3 &a, V3 b) {  // a x b, a complex, b real
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+struct Tri {
+  V3 v[3], n, fr[3];
+  double A;
+  int e[3];
+  double c[3];  // sigma * l / (2A)
+};
+__device__ __forceinline__ void load_tri(const double *tri, const int *te, const double *tsg, int t, Tri &T) {
+  const double *o = tri + 22 * (size_t)t;
+  for (int a = 0; a < 3; ++a) T.v[a] = v3(o[3 * a], o[3 * a + 1], o[3 * a + 2]);
+  T.n = v3(o[9], o[10], o[11]);
+  T.A = o[12];
+  for (int a = 0; a < 3; ++a) {
+    T.fr[a] = v3(o[13 + 3 * a], o[14 + 3 * a], o[15 + 3 * a]);
+    T.e[a] = te[3 * t + a];
+    T.c[a] = tsg[3 * t + a];
+  }
+}
+__device__ __forceinline__ V3 bary(const Tri &T, double b0, double b1, double b2) {
+  return b0 * T.v[0] + b1 * T.v[1] + b2 * T.v[2];
+}
+
+// exp(-j k R) for complex k = kr + j ki
+__device__ __forceinline__ zd expmjkR(zd k, double R) {
+  double mag = exp(k.im * R);
+  double s, c;
+  sincos(k.re * R, &s, &c);
+  return zd(mag * c, -mag * s);
+}
+
+// Closed-form integrals of 1/R, (rho' - rho)/R and grad_r(1/R) over a flat
+// triangle (Wilton et al. 1984; Graglia 1993), written from the geometry.
+__device__ void tri_potentials(V3 r, const Tri &T, double &I1, V3 &Irho, V3 &Igr, V3 &rho) {
+  V3 n = cross(T.v[1] - T.v[0], T.v[2] - T.v[0]);
+  n = (1.0 / norm(n)) * n;
+  double w = dot(r - T.v[0], n);
+  double scale = norm(T.v[1] - T.v[0]);
+  if (fabs(w) < 1e-12 * scale) w = 0.0;
+  rho = r - w * n;
+  double aw = fabs(w);
+  I1 = 0.0;
+  Irho = v3(0, 0, 0);
+  Igr = v3(0, 0, 0);
+  double sb = 0.0;
+  for (int s = 0; s < 3; ++s) {
+    V3 a = T.v[s], b = T.v[(s + 1) % 3];
+    V3 el = b - a;
+    V3 l = (1.0 / norm(el)) * el;
+    V3 u = cross(l, n);
+    double sm = dot(a - rho, l), sp = dot(b - rho, l), t0 = dot(a - rho, u);
+    double R02 = t0 * t0 + w * w;
+    double Rp = norm(r - b), Rm = norm(r - a);
+    double f;
+    if (sp < 0 && sm < 0) {
+      f = log((Rm - sm) / (Rp - sp));
+    } else {
+      double Ap = sp >= 0 ? Rp + sp : R02 / (Rp - sp);
+      double Am = sm >= 0 ? Rm + sm : R02 / (Rm - sm);
+      f = log(Ap / Am);
+    }
+    double beta = atan2(t0 * sp, R02 + aw * Rp) - atan2(t0 * sm, R02 + aw * Rm);
+    I1 += t0 * f;
+    Irho = Irho + (0.5 * (R02 * f + sp * Rp - sm * Rm)) * u;
+    Igr = Igr - f * u;
+    sb += beta;
+  }
+  I1 -= aw * sb;
+  double sg = (w > 0) - (w < 0);
+  Igr = Igr - (sg * sb) * n;
+}
+
+// One near triangle pair of medium `l`: Galerkin values of L, K, n x L, n x K
+// for the 3x3 local bases, combined into JMCFIE blocks and added to the
+// block-sparse near matrix.
+__global__ void k_near_fill(const int *pairs, int64_t npairs, const double *tri, const int *te, const double *tsg,
+                            const int *treg, int region, zd k, zd eta, const double *quad, int nq,
+                            const int *row_ptr, const int *col, double *near) {
+  int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= npairs) return;
+  int p = pairs[3 * id], q = pairs[3 * id + 1], sing = pairs[3 * id + 2];
+  Tri P, Q;
+  load_tri(tri, te, tsg, p, P);
+  load_tri(tri, te, tsg, q, Q);
+  const zd jk = zd(-k.im, k.re);                  // j k
+  const double kk2 = k.re * k.re + k.im * k.im;
+  const zd joverk = zd(k.im / kk2, k.re / kk2);   // j / k
+  zd L[3][3], K[3][3], NL[3][3], NK[3][3], SG;
+  const int na = sing ? nq : 7;
+  const double inv4pi = 1.0 / (4.0 * M_PI);
+  for (int a = 0; a < na; ++a) {
+    double b0, b1, b2, wa;
+    if (sing) {
+      b0 = quad[4 * a]; b1 = quad[4 * a + 1]; b2 = quad[4 * a + 2]; wa = quad[4 * a + 3];
+    } else {
+      b0 = c_rb[a][0]; b1 = c_rb[a][1]; b2 = c_rb[a][2]; wa = c_rw[a];
+    }
+    V3 r = bary(P, b0, b1, b2);
+    double W = P.A * wa;
+    zd IG;
+    C3 IGr = {zd(), zd(), zd()}, IgG = {zd(), zd(), zd()};
+    if (!sing) {
+      for (int b = 0; b < 7; ++b) {
+        V3 rq = bary(Q, c_rb[b][0], c_rb[b][1], c_rb[b][2]);
+        double Wq = Q.A * c_rw[b];
+        V3 D = r - rq;
+        double R = norm(D);
+        zd e = expmjkR(k, R);
+        zd G = (Wq * inv4pi / R) * e;
+        IG += G;
+        IGr.x += rq.x * G; IGr.y += rq.y * G; IGr.z += rq.z * G;
+        zd g = (-Wq * inv4pi / (R * R * R)) * ((zd(1.0, 0.0) + R * jk) * e);
+        IgG.x += D.x * g; IgG.y += D.y * g; IgG.z += D.z * g;
+      }
+    } else {
+      double I1;
+      V3 Irho, Igr, rho;
+      tri_potentials(r, Q, I1, Irho, Igr, rho);
+      zd remS;
+      C3 remR = {zd(), zd(), zd()}, remG = {zd(), zd(), zd()};
+      for (int b = 0; b < 7; ++b) {
+        V3 rq = bary(Q, c_rb[b][0], c_rb[b][1], c_rb[b][2]);
+        double Wq = Q.A * c_rw[b];
+        V3 D = r - rq;
+        double R = norm(D);
+        zd rm, gr;
+        if (R < 1e-14) {
+          rm = zd(k.im, -k.re);  // -j k
+          gr = zd();
+        } else {
+          zd e = expmjkR(k, R);
+          rm = (1.0 / R) * (e - zd(1.0, 0.0));
+          gr = (1.0 / (R * R * R)) * (zd(1.0, 0.0) - (zd(1.0, 0.0) + R * jk) * e);
+        }
+        rm = Wq * rm;
+        gr = Wq * gr;
+        remS += rm;
+        remR.x += rq.x * rm; remR.y += rq.y * rm; remR.z += rq.z * rm;
+        remG.x += D.x * gr; remG.y += D.y * gr; remG.z += D.z * gr;
+      }
+      IG = inv4pi * (zd(I1, 0.0) + remS);
+      IGr.x = inv4pi * (zd(Irho.x + rho.x * I1, 0.0) + remR.x);
+      IGr.y = inv4pi * (zd(Irho.y + rho.y * I1, 0.0) + remR.y);
+      IGr.z = inv4pi * (zd(Irho.z + rho.z * I1, 0.0) + remR.z);
+      IgG.x = inv4pi * (zd(Igr.x, 0.0) + remG.x);
+      IgG.y = inv4pi * (zd(Igr.y, 0.0) + remG.y);
+      IgG.z = inv4pi * (zd(Igr.z, 0.0) + remG.z);
+    }
+    SG += W * IG;
+    V3 Fm[3], Fmn[3];
+    for (int i = 0; i < 3; ++i) {
+      Fm[i] = P.c[i] * (r - P.fr[i]);
+      Fmn[i] = cross(Fm[i], P.n);
+    }
+    for (int j = 0; j < 3; ++j) {
+      double cj = Q.c[j];
+      C3 Fn = {cj * (IGr.x - Q.fr[j].x * IG), cj * (IGr.y - Q.fr[j].y * IG), cj * (IGr.z - Q.fr[j].z * IG)};
+      C3 Cr = ccross(IgG, r - Q.fr[j]);
+      Cr.x = cj * Cr.x; Cr.y = cj * Cr.y; Cr.z = cj * Cr.z;
+      double dj = 2.0 * cj;
+      for (int i = 0; i < 3; ++i) {
+        L[i][j] += W * (jk * cdot(Fm[i], Fn));
+        K[i][j] += W * cdot(Fm[i], Cr);
+        NL[i][j] += W * (jk * cdot(Fmn[i], Fn) + (dj * joverk) * cdot(Fmn[i], IgG));
+        NK[i][j] += W * cdot(Fmn[i], Cr);
+      }
+    }
+  }
+  const double sm = treg[2 * p] == region ? 1.0 : -1.0;
+  const double sn = treg[2 * q] == region ? 1.0 : -1.0;
+  const double ss = sm * sn;
+  const zd ieta = zd(eta.re, -eta.im) * (1.0 / (eta.re * eta.re + eta.im * eta.im));
+  for (int i = 0; i < 3; ++i) {
+    int m = P.e[i];
+    if (m < 0) continue;
+    int lo = row_ptr[m], hi = row_ptr[m + 1];
+    for (int j = 0; j < 3; ++j) {
+      int nn = Q.e[j];
+      if (nn < 0) continue;
+      int a = lo, b = hi;  // binary search for column nn
+      while (a < b) {
+        int mid = (a + b) >> 1;
+        if (col[mid] < nn) a = mid + 1; else b = mid;
+      }
+      if (a >= hi || col[a] != nn) continue;  // far pair: carried by the MLFMM
+      zd Lij = L[i][j] - ((2.0 * P.c[i]) * (2.0 * Q.c[j])) * (joverk * SG);
+      zd jj = ss * Lij + sn * NK[i][j];
+      zd jm = (ss * K[i][j] - sn * NL[i][j]) * ieta;
+      zd mj = (ss * K[i][j] + sn * NL[i][j]) * eta;
+      zd mm = -ss * Lij + sn * NK[i][j];
+      double *o = near + 8 * (size_t)a;
+      atomicAdd(o + 0, jj.re); atomicAdd(o + 1, jj.im);
+      atomicAdd(o + 2, jm.re); atomicAdd(o + 3, jm.im);
+      atomicAdd(o + 4, mj.re); atomicAdd(o + 5, mj.im);
+      atomicAdd(o + 6, mm.re); atomicAdd(o + 7, mm.im);
+    }
+  }
+}
+
+// Identity (Gram) terms of both media of each triangle: -1/2 <t, b> per
+// side on the J and M rows, +-1/2 <t, n x b> weighted by eta~ per side.
+__global__ void k_identity(int nt, const double *tri, const int *te, const double *tsg, const int *treg,
+                           const zd *etas, const int *row_ptr, const int *col, double *near, int *err) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  Tri P;
+  load_tri(tri, te, tsg, t, P);
+  double Gm[3][3] = {}, Gx[3][3] = {};
+  for (int a = 0; a < 7; ++a) {
+    V3 r = bary(P, c_rb[a][0], c_rb[a][1], c_rb[a][2]);
+    double W = P.A * c_rw[a];
+    V3 F[3];
+    for (int i = 0; i < 3; ++i) F[i] = P.c[i] * (r - P.fr[i]);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        Gm[i][j] += W * dot(F[i], F[j]);
+        Gx[i][j] += W * dot(F[i], cross(P.n, F[j]));
+      }
+  }
+  zd ep = etas[treg[2 * t]], em = etas[treg[2 * t + 1]];
+  auto inv = [](zd z) { return zd(z.re, -z.im) * (1.0 / (z.re * z.re + z.im * z.im)); };
+  zd cjm = 0.5 * (inv(ep) - inv(em));
+  zd cmj = 0.5 * (ep - em);
+  for (int i = 0; i < 3; ++i) {
+    int m = P.e[i];
+    if (m < 0) continue;
+    for (int j = 0; j < 3; ++j) {
+      int nn = P.e[j];
+      if (nn < 0) continue;
+      int a = row_ptr[m], b = row_ptr[m + 1], hi = b;
+      while (a < b) {
+        int mid = (a + b) >> 1;
+        if (col[mid] < nn) a = mid + 1; else b = mid;
+      }
+      if (a >= hi || col[a] != nn) {
+        atomicExch(err, 1);
+        continue;
+      }
+      double *o = near + 8 * (size_t)a;
+      zd jm = Gx[i][j] * cjm, mj = Gx[i][j] * cmj;
+      atomicAdd(o + 0, -Gm[i][j]);
+      atomicAdd(o + 2, jm.re); atomicAdd(o + 3, jm.im);
+      atomicAdd(o + 4, mj.re); atomicAdd(o + 5, mj.im);
+      atomicAdd(o + 6, -Gm[i][j]);
+    }
+  }
+}
+
+// Leaf patterns of medium l at direction k:
+//   V_i(k)  = int b_i e^{+j k khat.(r - c_b)}          (radiation, theta/phi)
+//   RN_i(k) = int (t_i x n) e^{-j k khat.(r - c_b)}     (receive of n x operators)
+__global__ void k_patterns(int nb, int K, const int *basis_p, const int *basis_box, const double *centre,
+                           const int *edge_tris, const double *tri, const int *te, const double *tsg,
+                           const double *dirs, zd k, zd *V, zd *RN) {
+  int kk = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y;
+  if (kk >= K || i >= nb) return;
+  int p = basis_p[i];
+  const double *cb = centre + 3 * basis_box[i];
+  V3 c = v3(cb[0], cb[1], cb[2]);
+  const double *d = dirs + 9 * kk;
+  V3 kh = v3(d[0], d[1], d[2]), th = v3(d[3], d[4], d[5]), ph = v3(d[6], d[7], d[8]);
+  zd vt, vp, rt, rp;
+  for (int s = 0; s < 2; ++s) {
+    int t = edge_tris[2 * p + s];
+    Tri T;
+    load_tri(tri, te, tsg, t, T);
+    int li = 0;
+    for (int a = 0; a < 3; ++a)
+      if (T.e[a] == p) li = a;
+    for (int a = 0; a < 7; ++a) {
+      V3 r = bary(T, c_rb[a][0], c_rb[a][1], c_rb[a][2]);
+      double W = T.A * c_rw[a];
+      V3 f = T.c[li] * (r - T.fr[li]);
+      V3 fn = cross(f, T.n);
+      double x = dot(kh, r - c);
+      // e^{+jkx} = e^{-k_i x} (cos k_r x + j sin k_r x)
+      double s1, c1;
+      sincos(k.re * x, &s1, &c1);
+      double gp = exp(-k.im * x), gm = exp(k.im * x);
+      zd ep(gp * c1, gp * s1), em(gm * c1, -gm * s1);
+      vt += (W * dot(f, th)) * ep;
+      vp += (W * dot(f, ph)) * ep;
+      rt += (W * dot(fn, th)) * em;
+      rp += (W * dot(fn, ph)) * em;
+    }
+  }
+  V[((size_t)i * 2 + 0) * K + kk] = vt;
+  V[((size_t)i * 2 + 1) * K + kk] = vp;
+  RN[((size_t)i * 2 + 0) * K + kk] = rt;
+  RN[((size_t)i * 2 + 1) * K + kk] = rp;
+}
+
+// Tested excitation, host medium 0 only (Eqs. 20-21 with Eq. 30).
+__global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris, const int *edge_reg,
+                      const double *tri, const int *te, const double *tsg, zd k0, zd eta0, zd *b) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (p >= ne || r >= nrhs) return;
+  zd *out = b + ((size_t)r * ne + p) * 2;
+  int rp = edge_reg[2 * p], rm = edge_reg[2 * p + 1];
+  if (rp != 0 && rm != 0) {
+    out[0] = zd();
+    out[1] = zd();
+    return;
+  }
+  double s0 = rp == 0 ? 1.0 : -1.0;
+  double th = inc[4 * r], ph = inc[4 * r + 1], pol = inc[4 * r + 2], E0 = inc[4 * r + 3];
+  double st, ct, sp, cp;
+  sincos(th, &st, &ct);
+  sincos(ph, &sp, &cp);
+  V3 kh = v3(-st * cp, -st * sp, -ct);
+  V3 e = (E0 * cos(pol)) * v3(ct * cp, ct * sp, -st) + (E0 * sin(pol)) * v3(-sp, cp, 0.0);
+  V3 h = cross(kh, e);  // eta0 H times eta~_0
+  zd ie0 = zd(eta0.re, -eta0.im) * (1.0 / (eta0.re * eta0.re + eta0.im * eta0.im));
+  zd fE, fH, fnH, fnE;
+  for (int s = 0; s < 2; ++s) {
+    int t = edge_tris[2 * p + s];
+    Tri T;
+    load_tri(tri, te, tsg, t, T);
+    int li = 0;
+    for (int a = 0; a < 3; ++a)
+      if (T.e[a] == p) li = a;
+    for (int a = 0; a < 7; ++a) {
+      V3 rr = bary(T, c_rb[a][0], c_rb[a][1], c_rb[a][2]);
+      double W = T.A * c_rw[a];
+      V3 f = T.c[li] * (rr - T.fr[li]);
+      zd ph_ = expmjkR(k0, dot(kh, rr));  // exp(-j k0 khat.r)
+      zd w = W * ph_;
+      fE += dot(f, e) * w;
+      fH += (dot(f, h) * w) * ie0;
+      fnH += (dot(f, cross(T.n, h)) * w) * ie0;
+      fnE += dot(f, cross(T.n, e)) * w;
+    }
+  }
+  out[0] = (s0 * fE) * ie0 - fnH;
+  out[1] = -(s0 * (eta0 * fH)) + fnE;
+}
+
+// Far amplitudes (Eqs. 27-29): one block per (observation, rhs).
+__global__ void k_farfield(int ne, int nrhs, const zd *x, const double *obs, const int *edge_tris,
+                           const int *edge_reg, const double *tri, const int *te, const double *tsg, zd k0, zd eta0,
+                           double *out) {
+  int o = blockIdx.x, r = blockIdx.y;
+  double th = obs[2 * o], ph = obs[2 * o + 1];
+  double st, ct, sp, cp;
+  sincos(th, &st, &ct);
+  sincos(ph, &sp, &cp);
+  V3 rh = v3(st * cp, st * sp, ct), thh = v3(ct * cp, ct * sp, -st), phh = v3(-sp, cp, 0.0);
+  zd Nt, Np, Lt, Lp;
+  for (int p = threadIdx.x; p < ne; p += blockDim.x) {
+    int rp = edge_reg[2 * p], rm = edge_reg[2 * p + 1];
+    if (rp != 0 && rm != 0) continue;
+    double s0 = rp == 0 ? 1.0 : -1.0;
+    zd cJ = x[((size_t)r * ne + p) * 2], cM = x[((size_t)r * ne + p) * 2 + 1];
+    zd Pt, Pp;
+    for (int s = 0; s < 2; ++s) {
+      int t = edge_tris[2 * p + s];
+      Tri T;
+      load_tri(tri, te, tsg, t, T);
+      int li = 0;
+      for (int a = 0; a < 3; ++a)
+        if (T.e[a] == p) li = a;
+      for (int a = 0; a < 7; ++a) {
+        V3 rr = bary(T, c_rb[a][0], c_rb[a][1], c_rb[a][2]);
+        double W = T.A * c_rw[a];
+        V3 f = T.c[li] * (rr - T.fr[li]);
+        double xx = dot(rh, rr);
+        double s1, c1;
+        sincos(k0.re * xx, &s1, &c1);
+        double g = exp(-k0.im * xx);
+        zd e(g * c1, g * s1);  // exp(+j k0 rhat.r)
+        Pt += (W * dot(f, thh) * s0) * e;
+        Pp += (W * dot(f, phh) * s0) * e;
+      }
+    }
+    Nt += Pt * cJ;
+    Np += Pp * cJ;
+    Lt += Pt * cM;
+    Lp += Pp * cM;
+  }
+  __shared__ zd red[4][256];
+  red[0][threadIdx.x] = Nt;
+  red[1][threadIdx.x] = Np;
+  red[2][threadIdx.x] = Lt;
+  red[3][threadIdx.x] = Lp;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    zd pre = zd(0.0, -1.0) * k0 * (1.0 / sqrt(4.0 * M_PI));
+    zd At = pre * (eta0 * red[0][0] + red[3][0]);
+    zd Ap = pre * (eta0 * red[1][0] - red[2][0]);
+    out[((size_t)r * gridDim.x + o) * 2] = At.re * At.re + At.im * At.im;
+    out[((size_t)r * gridDim.x + o) * 2 + 1] = Ap.re * Ap.re + Ap.im * Ap.im;
+  }
+}
+
+__global__ void k_to_f32(const double *a, float *b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) b[i] = (float)a[i];
+}
+
+inline zd to_zd(std::complex<double> z) { return zd(z.real(), z.imag()); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+void launch_near_fill(sie_ctx *c, int l) {
+  upload_radon();
+  RegionHost &R = c->reg[l];
+  if (R.npairs == 0) return;
+  int bs = 128;
+  int64_t nb = (R.npairs + bs - 1) / bs;
+  k_near_fill<<<(unsigned)nb, bs, 0, c->stream>>>(R.d_pairs, R.npairs, c->d_tri, c->d_tri_e, c->d_tri_sg,
+                                                   c->d_tri_reg, l, to_zd(R.k), to_zd(R.eta), c->d_quad,
+                                                   c->nq_sing, c->d_row_ptr, c->d_col, (double *)c->d_near64);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+
+void launch_identity(sie_ctx *c) {
+  upload_radon();
+  std::vector<zd> et(c->nr);
+  for (int l = 0; l < c->nr; ++l) et[l] = to_zd(c->etareg[l]);
+  zd *d_et = dev_upload(c, et);
+  int *d_err = (int *)dev_alloc(c, sizeof(int));
+  SIE_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), c->stream));
+  k_identity<<<(c->nt + 127) / 128, 128, 0, c->stream>>>(c->nt, c->d_tri, c->d_tri_e, c->d_tri_sg, c->d_tri_reg,
+                                                        d_et, c->d_row_ptr, c->d_col, (double *)c->d_near64, d_err);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+  int err = 0;
+  SIE_CUDA(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SIE_CUDA(cudaStreamSynchronize(c->stream));
+  SIE_REQUIRE(err == 0, SIE_EINVAL, "sie_fill_nearfield: leaf boxes smaller than triangles (use fewer levels)");
+}
+
+void launch_patterns(sie_ctx *c, int l) {
+  upload_radon();
+  RegionHost &R = c->reg[l];
+  int leaf = c->levels - 1;
+  LevelHost &LL = R.lev[leaf];
+  int K = LL.K;
+  size_t n = (size_t)R.nb * 2 * K;
+  R.d_V64 = dev_alloc(c, n * sizeof(zd));
+  R.d_RN64 = dev_alloc(c, n * sizeof(zd));
+  R.d_V32 = dev_alloc(c, n * sizeof(zf));
+  R.d_RN32 = dev_alloc(c, n * sizeof(zf));
+  SIE_REQUIRE(R.nb < 65536 * 8, SIE_EINVAL, "patterns: too many bases in one medium");
+  for (int i0 = 0; i0 < R.nb; i0 += 65535) {
+    int cnt = std::min(65535, R.nb - i0);
+    dim3 grid((K + 127) / 128, cnt);
+    k_patterns<<<grid, 128, 0, c->stream>>>(cnt, K, R.d_basis_p + i0, R.d_basis_box + i0, R.d_box_centre,
+                                            c->d_edge_tris, c->d_tri, c->d_tri_e, c->d_tri_sg, LL.d_dirs,
+                                            to_zd(R.k), (zd *)R.d_V64 + (size_t)i0 * 2 * K,
+                                            (zd *)R.d_RN64 + (size_t)i0 * 2 * K);
+    SIE_CHECK_LAUNCH();
+    c->launches++;
+  }
+  launch_to_f32(c, (const double *)R.d_V64, (float *)R.d_V32, (int64_t)n * 2);
+  launch_to_f32(c, (const double *)R.d_RN64, (float *)R.d_RN32, (int64_t)n * 2);
+}
+
+void launch_rhs(sie_ctx *c, const double *inc_dev, int nrhs, zd *b) {
+  upload_radon();
+  dim3 grid((c->ne + 127) / 128, nrhs);
+  k_rhs<<<grid, 128, 0, c->stream>>>(c->ne, nrhs, inc_dev, c->d_edge_tris, c->d_edge_reg, c->d_tri, c->d_tri_e,
+                                     c->d_tri_sg, to_zd(c->kreg[0]), to_zd(c->etareg[0]), b);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+
+void launch_farfield(sie_ctx *c, const zd *x, int nrhs, const double *obs, int nobs, double *out) {
+  upload_radon();
+  dim3 grid(nobs, nrhs);
+  k_farfield<<<grid, 256, 0, c->stream>>>(c->ne, nrhs, x, obs, c->d_edge_tris, c->d_edge_reg, c->d_tri, c->d_tri_e,
+                                          c->d_tri_sg, to_zd(c->kreg[0]), to_zd(c->etareg[0]), out);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+
+void launch_to_f32(sie_ctx *c, const double *src, float *dst, int64_t n) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_to_f32<<<std::max(blocks, 1), 256, 0, c->stream>>>(src, dst, n);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}

@@ -1,0 +1,1071 @@
+// Host side of the library: mesh topology (RWG, Eq. 22), octree, near-field
+// pattern and preconditioner ordering, MLFMM tables, ILU(0) factorisation,
+// and the extern "C" entry points declared in sie.h.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <thread>
+#include <unordered_map>
+
+#include "common.h"
+
+typedef std::complex<double> cd;
+static const double PI = 3.14159265358979323846;
+
+// ------------------------------------------------------------------ allocation
+void *dev_alloc(sie_ctx *c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) throw SieError{SIE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  c->bufs.push_back({p, bytes});
+  c->dev_bytes += (int64_t)bytes;
+  return p;
+}
+
+void *stage(sie_ctx *c, size_t bytes) {
+  if (bytes > c->stage_bytes) {
+    c->d_stage = dev_alloc(c, std::max(bytes, (size_t)4096));
+    c->stage_bytes = std::max(bytes, (size_t)4096);
+  }
+  return c->d_stage;
+}
+
+void ensure_work(sie_ctx *c, int64_t nrhs) {
+  if (nrhs <= c->nrhs_cap) return;
+  size_t n = (size_t)nrhs * c->ne * 2;
+  c->d_xi = dev_alloc(c, n * sizeof(zd));
+  c->d_yi = dev_alloc(c, n * sizeof(zd));
+  c->d_xf = dev_alloc(c, n * sizeof(zf));
+  c->d_yf = dev_alloc(c, n * sizeof(zf));
+  size_t gemm = 0;
+  for (auto &R : c->reg) {
+    for (int l = 2; l < (int)R.lev.size(); ++l) {
+      LevelHost &L = R.lev[l];
+      size_t sz = (size_t)L.nbox * 4 * L.K * nrhs * sizeof(zd);
+      L.d_S = dev_alloc(c, sz);
+      L.d_I = dev_alloc(c, sz);
+      if (l >= 3) {  // scratch for interpolation into level l-1 and anterpolation from it
+        size_t g = (size_t)L.nbox * 4 * R.lev[l - 1].K * nrhs * sizeof(zd);
+        gemm = std::max(gemm, g);
+      }
+    }
+  }
+  c->d_gemm = dev_alloc(c, gemm);
+  c->gemm_bytes = gemm;
+  c->nrhs_cap = nrhs;
+}
+
+// ------------------------------------------------------------------ special functions
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1] by Newton iteration.
+static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
+      if (n == 1) { pn = z; pm = 1.0; }
+      double dp = n * (z * pn - pm) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
+    double dp = n * (z * pn - pm) / (z * z - 1.0);
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// P_0..P_L at x
+static void legendre_all(int L, double x, double *P) {
+  P[0] = 1.0;
+  if (L >= 1) P[1] = x;
+  for (int n = 1; n < L; ++n) P[n + 1] = ((2.0 * n + 1.0) * x * P[n] - n * P[n - 1]) / (n + 1.0);
+}
+
+// spherical Hankel functions of the second kind h_0..h_L at complex z (upward recurrence)
+static void hankel2_all(int L, cd z, cd *h) {
+  const cd j(0.0, 1.0);
+  cd e = std::exp(-j * z);
+  h[0] = j * e / z;
+  if (L >= 1) h[1] = e * (j / (z * z) - 1.0 / z);
+  for (int n = 1; n < L; ++n) h[n + 1] = (2.0 * n + 1.0) / z * h[n] - h[n - 1];
+}
+
+static int64_t morton3(int i, int j, int k) {
+  int64_t code = 0;
+  for (int b = 0; b < 21; ++b) {
+    code |= (int64_t)((i >> b) & 1) << (3 * b);
+    code |= (int64_t)((j >> b) & 1) << (3 * b + 1);
+    code |= (int64_t)((k >> b) & 1) << (3 * b + 2);
+  }
+  return code;
+}
+static inline int64_t ijk_key(int i, int j, int k) { return ((int64_t)i << 42) | ((int64_t)j << 21) | (int64_t)k; }
+
+// ------------------------------------------------------------------ API: context
+extern "C" sie_status sie_create(sie_ctx **out, int device, void *cuda_stream) {
+  if (!out) return SIE_EINVAL;
+  sie_ctx *c = new sie_ctx();
+  c->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete c;
+    return SIE_ECUDA;
+  }
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return SIE_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return SIE_OK;
+}
+
+extern "C" void sie_destroy(sie_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto &b : c->bufs) cudaFree(b.p);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+extern "C" const char *sie_last_error(const sie_ctx *c) { return c ? c->last_error.c_str() : "null context"; }
+
+template <typename F>
+static sie_status guard(sie_ctx *c, F &&f) {
+  if (!c) return SIE_EINVAL;
+  try {
+    cudaSetDevice(c->device);
+    f();
+    return SIE_OK;
+  } catch (const SieError &e) {
+    c->last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    c->last_error = "host allocation failed";
+    return SIE_ENOMEM;
+  } catch (const std::exception &e) {
+    c->last_error = e.what();
+    return SIE_EINVAL;
+  }
+}
+
+// ------------------------------------------------------------------ API: mesh
+static void build_mesh(sie_ctx *c, const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                       const int32_t *treg, const double *media, int32_t nr, double freq) {
+  SIE_REQUIRE(verts && tris && treg && media && nv > 0 && nt > 0 && nr > 0 && freq > 0, SIE_EINVAL,
+              "sie_build_mesh: null pointer or non-positive size");
+  SIE_REQUIRE(nt < (1 << 30) && nv < (1 << 30), SIE_EINVAL, "sie_build_mesh: mesh too large");
+  c->nv = (int)nv;
+  c->nt = (int)nt;
+  c->nr = nr;
+  c->freq = freq;
+  c->k0 = 2.0 * PI * freq / 299792458.0;
+  c->verts.assign(verts, verts + 3 * nv);
+  c->tris.assign(tris, tris + 3 * nt);
+  c->tri_reg.assign(treg, treg + 2 * nt);
+  c->media.assign(media, media + 4 * nr);
+  for (int64_t t = 0; t < nt; ++t) {
+    for (int a = 0; a < 3; ++a)
+      SIE_REQUIRE(tris[3 * t + a] >= 0 && tris[3 * t + a] < nv, SIE_EINVAL, "sie_build_mesh: vertex index out of range");
+    for (int a = 0; a < 2; ++a)
+      SIE_REQUIRE(treg[2 * t + a] >= 0 && treg[2 * t + a] < nr, SIE_EINVAL, "sie_build_mesh: region index out of range");
+    SIE_REQUIRE(treg[2 * t] != treg[2 * t + 1], SIE_EINVAL, "sie_build_mesh: triangle with the same region on both sides");
+  }
+  // media
+  c->kreg.resize(nr);
+  c->etareg.resize(nr);
+  for (int l = 0; l < nr; ++l) {
+    cd eps(media[4 * l], media[4 * l + 1]), mu(media[4 * l + 2], media[4 * l + 3]);
+    cd k = c->k0 * std::sqrt(eps * mu);
+    SIE_REQUIRE(k.imag() <= 0.0, SIE_EINVAL, "sie_build_mesh: active medium (Im eps_r mu_r > 0)");
+    cd eta = std::sqrt(mu / eps);
+    if (eta.real() < 0) eta = -eta;
+    c->kreg[l] = k;
+    c->etareg[l] = eta;
+  }
+  // triangle geometry (same arithmetic order as the definition: mean, norms)
+  c->area.resize(nt);
+  c->normal.resize(3 * nt);
+  c->centroid.resize(3 * nt);
+  c->hmax.resize(nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    const double *P[3];
+    for (int a = 0; a < 3; ++a) P[a] = &verts[3 * tris[3 * t + a]];
+    double e1[3], e2[3], cr[3];
+    for (int x = 0; x < 3; ++x) {
+      e1[x] = P[1][x] - P[0][x];
+      e2[x] = P[2][x] - P[0][x];
+    }
+    cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    double n2 = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    SIE_REQUIRE(n2 > 0, SIE_EINVAL, "sie_build_mesh: degenerate triangle");
+    c->area[t] = 0.5 * n2;
+    for (int x = 0; x < 3; ++x) {
+      c->normal[3 * t + x] = cr[x] / (2.0 * c->area[t]);
+      c->centroid[3 * t + x] = ((P[0][x] + P[1][x]) + P[2][x]) / 3.0;
+    }
+    double hm = 0;
+    for (int a = 0; a < 3; ++a) {
+      const double *A = P[a], *B = P[(a + 1) % 3];
+      double dx = A[0] - B[0], dy = A[1] - B[1], dz = A[2] - B[2];
+      hm = std::max(hm, std::sqrt((dx * dx + dy * dy) + dz * dz));
+    }
+    c->hmax[t] = hm;
+  }
+  // edges: sort (key, triangle) records
+  struct Rec {
+    int64_t key;
+    int t, free_v, u, v;
+  };
+  std::vector<Rec> recs;
+  recs.reserve(3 * nt);
+  for (int t = 0; t < (int)nt; ++t) {
+    int a = tris[3 * t], b = tris[3 * t + 1], cc = tris[3 * t + 2];
+    int U[3] = {a, b, cc}, V[3] = {b, cc, a}, W[3] = {cc, a, b};
+    for (int s = 0; s < 3; ++s) {
+      int lo = std::min(U[s], V[s]), hi = std::max(U[s], V[s]);
+      recs.push_back({((int64_t)lo << 32) | (int64_t)hi, t, W[s], U[s], V[s]});
+    }
+  }
+  std::sort(recs.begin(), recs.end(), [](const Rec &x, const Rec &y) {
+    return x.key < y.key || (x.key == y.key && x.t < y.t);
+  });
+  c->edge_v.clear();
+  c->tp.clear();
+  c->tm.clear();
+  c->vp.clear();
+  c->vm.clear();
+  c->elen.clear();
+  c->tri_edge.assign(3 * nt, -1);
+  c->tri_free.assign(3 * nt, 0);
+  c->tri_sign.assign(3 * nt, 0.0);
+  std::vector<int> fillc(nt, 0);
+  size_t i = 0;
+  while (i < recs.size()) {
+    size_t j = i;
+    while (j < recs.size() && recs[j].key == recs[i].key) ++j;
+    size_t cnt = j - i;
+    SIE_REQUIRE(cnt <= 2, SIE_EINVAL, "sie_build_mesh: junction edge (more than two triangles) is not supported");
+    if (cnt == 2) {
+      const Rec &r1 = recs[i], &r2 = recs[i + 1];
+      SIE_REQUIRE(treg[2 * r1.t] == treg[2 * r2.t] && treg[2 * r1.t + 1] == treg[2 * r2.t + 1], SIE_EINVAL,
+                  "sie_build_mesh: edge shared by triangles of different surfaces");
+      SIE_REQUIRE(r1.u == r2.v && r1.v == r2.u, SIE_EINVAL,
+                  "sie_build_mesh: inconsistent triangle orientation across an edge");
+      int e = (int)c->tp.size();
+      int lo = (int)(r1.key >> 32), hi = (int)(r1.key & 0xffffffff);
+      c->edge_v.push_back(lo);
+      c->edge_v.push_back(hi);
+      c->tp.push_back(r1.t);
+      c->tm.push_back(r2.t);
+      c->vp.push_back(r1.free_v);
+      c->vm.push_back(r2.free_v);
+      double dx = verts[3 * hi] - verts[3 * lo], dy = verts[3 * hi + 1] - verts[3 * lo + 1],
+             dz = verts[3 * hi + 2] - verts[3 * lo + 2];
+      c->elen.push_back(std::sqrt(dx * dx + dy * dy + dz * dz));
+      const Rec *rr[2] = {&r1, &r2};
+      for (int s = 0; s < 2; ++s) {
+        int t = rr[s]->t;
+        int f = fillc[t]++;
+        c->tri_edge[3 * t + f] = e;
+        c->tri_free[3 * t + f] = rr[s]->free_v;
+        c->tri_sign[3 * t + f] = s == 0 ? 1.0 : -1.0;
+      }
+    }
+    i = j;
+  }
+  c->ne = (int)c->tp.size();
+  SIE_REQUIRE(c->ne > 0, SIE_EINVAL, "sie_build_mesh: no RWG edge (open or empty mesh)");
+  c->have_mesh = true;
+  c->have_tree = c->have_fill = false;
+}
+
+extern "C" sie_status sie_build_mesh(sie_ctx *c, const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                                     const int32_t *tri_regions, const double *media, int32_t nr, double freq_hz,
+                                     int64_t *n_rwg_out) {
+  return guard(c, [&] {
+    SIE_REQUIRE(!c->have_mesh, SIE_ESTATE, "sie_build_mesh: context already holds a mesh");
+    build_mesh(c, verts, nv, tris, nt, tri_regions, media, nr, freq_hz);
+    if (n_rwg_out) *n_rwg_out = c->ne;
+  });
+}
+
+// ------------------------------------------------------------------ API: tree + MLFMM tables
+static int trunc_L(double kr, double a, double d0) {
+  double kd = kr * std::sqrt(3.0) * a;
+  double L = kd + 1.8 * std::pow(d0, 2.0 / 3.0) * std::pow(kd, 1.0 / 3.0);
+  return std::max(2, (int)std::ceil(L));
+}
+
+struct Dirs {
+  int L, K;
+  std::vector<double> d;  // [K][9]
+  std::vector<double> w;  // [K]
+};
+static Dirs make_dirs(int L) {
+  Dirs D;
+  D.L = L;
+  int nth = L + 1, nph = 2 * L + 2;
+  D.K = nth * nph;
+  std::vector<double> x, wx;
+  gauss_legendre(nth, x, wx);
+  D.d.resize(9 * D.K);
+  D.w.resize(D.K);
+  for (int it = 0; it < nth; ++it) {
+    double ct = x[it], st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+    for (int jp = 0; jp < nph; ++jp) {
+      double ph = 2.0 * PI * jp / nph, cp = std::cos(ph), sp = std::sin(ph);
+      int k = it * nph + jp;
+      double *o = &D.d[9 * k];
+      o[0] = st * cp; o[1] = st * sp; o[2] = ct;          // khat
+      o[3] = ct * cp; o[4] = ct * sp; o[5] = -st;         // theta_hat
+      o[6] = -sp;     o[7] = cp;      o[8] = 0.0;         // phi_hat
+      D.w[k] = wx[it] * 2.0 * PI / nph;
+    }
+  }
+  return D;
+}
+
+static void setup_tree(sie_ctx *c, int levels, double digits) {
+  SIE_REQUIRE(levels >= 2 && levels <= 12, SIE_EINVAL, "mlfmm_setup: levels must be in [2, 12]");
+  SIE_REQUIRE(digits > 0 && digits < 16, SIE_EINVAL, "mlfmm_setup: digits must be in (0, 16)");
+  c->levels = levels;
+  c->digits = digits;
+  const int ne = c->ne;
+  // root cube
+  double lo[3], hi[3];
+  for (int x = 0; x < 3; ++x) lo[x] = hi[x] = c->verts[x];
+  for (int v = 0; v < c->nv; ++v)
+    for (int x = 0; x < 3; ++x) {
+      lo[x] = std::min(lo[x], c->verts[3 * v + x]);
+      hi[x] = std::max(hi[x], c->verts[3 * v + x]);
+    }
+  double ext = 0, centre[3];
+  for (int x = 0; x < 3; ++x) {
+    centre[x] = (lo[x] + hi[x]) * 0.5;
+    ext = std::max(ext, hi[x] - lo[x]);
+  }
+  c->D = ext * 1.0009765625;
+  int nleaf = 1 << (levels - 1);
+  c->hleaf = c->D / nleaf;
+  for (int x = 0; x < 3; ++x) c->origin[x] = centre[x] - 0.5 * c->D;
+  c->eijk.resize(3 * ne);
+  for (int e = 0; e < ne; ++e) {
+    const double *A = &c->verts[3 * c->edge_v[2 * e]], *B = &c->verts[3 * c->edge_v[2 * e + 1]];
+    for (int x = 0; x < 3; ++x) {
+      double mid = (A[x] + B[x]) * 0.5;
+      int q = (int)std::floor((mid - c->origin[x]) / c->hleaf);
+      c->eijk[3 * e + x] = std::min(std::max(q, 0), nleaf - 1);
+    }
+  }
+  // internal order: (colour, Morton, edge)
+  std::vector<int64_t> key(ne);
+  for (int e = 0; e < ne; ++e) {
+    int i = c->eijk[3 * e], j = c->eijk[3 * e + 1], k = c->eijk[3 * e + 2];
+    int col = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+    key[e] = ((int64_t)col << 60) | morton3(i, j, k);
+  }
+  c->perm.resize(ne);
+  for (int e = 0; e < ne; ++e) c->perm[e] = e;
+  std::stable_sort(c->perm.begin(), c->perm.end(), [&](int a, int b) { return key[a] < key[b]; });
+  c->inv.resize(ne);
+  for (int p = 0; p < ne; ++p) c->inv[c->perm[p]] = p;
+  // global leaf boxes in internal order
+  c->leaf_start.clear();
+  c->leaf_ijk.clear();
+  std::vector<int> ebox(ne);  // leaf box of internal edge p
+  for (int p = 0; p < ne; ++p) {
+    int e = c->perm[p];
+    if (p == 0 || key[e] != key[c->perm[p - 1]]) {
+      c->leaf_start.push_back(p);
+      for (int x = 0; x < 3; ++x) c->leaf_ijk.push_back(c->eijk[3 * e + x]);
+    }
+    ebox[p] = (int)c->leaf_start.size() - 1;
+  }
+  int nlb = (int)c->leaf_start.size();
+  c->leaf_start.push_back(ne);
+  std::unordered_map<int64_t, int> leaf_map;
+  for (int b = 0; b < nlb; ++b) leaf_map[ijk_key(c->leaf_ijk[3 * b], c->leaf_ijk[3 * b + 1], c->leaf_ijk[3 * b + 2])] = b;
+  // near pattern: rows in internal order, columns sorted
+  std::vector<std::vector<int>> nb_of(nlb);
+  for (int b = 0; b < nlb; ++b) {
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          auto it = leaf_map.find(ijk_key(c->leaf_ijk[3 * b] + dx, c->leaf_ijk[3 * b + 1] + dy, c->leaf_ijk[3 * b + 2] + dz));
+          if (it != leaf_map.end()) nb_of[b].push_back(it->second);
+        }
+    std::sort(nb_of[b].begin(), nb_of[b].end(), [&](int x, int y) { return c->leaf_start[x] < c->leaf_start[y]; });
+  }
+  c->row_ptr.assign(ne + 1, 0);
+  for (int p = 0; p < ne; ++p) {
+    int cnt = 0;
+    for (int b : nb_of[ebox[p]]) cnt += c->leaf_start[b + 1] - c->leaf_start[b];
+    c->row_ptr[p + 1] = c->row_ptr[p] + cnt;
+  }
+  SIE_REQUIRE((int64_t)c->row_ptr[ne] < ((int64_t)1 << 31), SIE_EINVAL, "mlfmm_setup: near field too large (more levels needed)");
+  c->col.resize(c->row_ptr[ne]);
+  for (int p = 0; p < ne; ++p) {
+    int o = c->row_ptr[p];
+    for (int b : nb_of[ebox[p]])
+      for (int q = c->leaf_start[b]; q < c->leaf_start[b + 1]; ++q) c->col[o++] = q;
+  }
+
+  // ---------------- per medium
+  c->reg.assign(c->nr, RegionHost());
+  int leaf = levels - 1;
+  for (int l = 0; l < c->nr; ++l) {
+    RegionHost &R = c->reg[l];
+    R.id = l;
+    R.k = c->kreg[l];
+    R.eta = c->etareg[l];
+    std::vector<int> basis_gbox;
+    for (int p = 0; p < ne; ++p) {
+      int e = c->perm[p];
+      int t = c->tp[e];
+      int rp = c->tri_reg[2 * t], rm = c->tri_reg[2 * t + 1];
+      if (rp == l || rm == l) {
+        R.basis_p.push_back(p);
+        R.basis_sign.push_back(rp == l ? 1 : -1);
+        basis_gbox.push_back(ebox[p]);
+      }
+    }
+    R.nb = (int)R.basis_p.size();
+    R.lev.assign(levels, LevelHost());
+    for (int lv = 0; lv < levels; ++lv) {
+      R.lev[lv].lev = lv;
+      R.lev[lv].a = c->D / (double)(1 << lv);
+    }
+    if (R.nb == 0) continue;
+    // leaf level: boxes in internal order
+    LevelHost &LL = R.lev[leaf];
+    std::vector<int> basis_box(R.nb);
+    for (int i = 0; i < R.nb; ++i) {
+      if (i == 0 || basis_gbox[i] != basis_gbox[i - 1]) {
+        R.box_start.push_back(i);
+        int g = basis_gbox[i];
+        for (int x = 0; x < 3; ++x) LL.ijk.push_back(c->leaf_ijk[3 * g + x]);
+      }
+      basis_box[i] = (int)R.box_start.size() - 1;
+    }
+    LL.nbox = (int)R.box_start.size();
+    R.box_start.push_back(R.nb);
+    // coarser levels (Morton order)
+    for (int lv = leaf - 1; lv >= 1; --lv) {
+      LevelHost &C = R.lev[lv + 1], &P = R.lev[lv];
+      std::vector<std::pair<int64_t, int>> keys;  // (morton, child)
+      for (int b = 0; b < C.nbox; ++b)
+        keys.push_back({morton3(C.ijk[3 * b] >> 1, C.ijk[3 * b + 1] >> 1, C.ijk[3 * b + 2] >> 1), b});
+      std::sort(keys.begin(), keys.end());
+      C.parent.assign(C.nbox, -1);
+      C.oct.assign(C.nbox, 0);
+      P.ch_ptr.assign(1, 0);
+      for (size_t s = 0; s < keys.size(); ++s) {
+        int b = keys[s].second;
+        if (s == 0 || keys[s].first != keys[s - 1].first) {
+          for (int x = 0; x < 3; ++x) P.ijk.push_back(C.ijk[3 * b + x] >> 1);
+          P.ch_ptr.push_back(P.ch_ptr.back());
+        }
+        int pb = (int)P.ch_ptr.size() - 2;
+        C.parent[b] = pb;
+        C.oct[b] = (C.ijk[3 * b] & 1) | ((C.ijk[3 * b + 1] & 1) << 1) | ((C.ijk[3 * b + 2] & 1) << 2);
+        P.ch_idx.push_back(b);
+        P.ch_ptr.back()++;
+      }
+      P.nbox = (int)P.ch_ptr.size() - 1;
+    }
+    // interaction lists, levels 2..leaf
+    for (int lv = 2; lv <= leaf; ++lv) {
+      LevelHost &B = R.lev[lv], &P = R.lev[lv - 1];
+      std::unordered_map<int64_t, int> pmap;
+      for (int pb = 0; pb < P.nbox; ++pb) pmap[ijk_key(P.ijk[3 * pb], P.ijk[3 * pb + 1], P.ijk[3 * pb + 2])] = pb;
+      std::map<int, int> slot_of;
+      B.il_ptr.assign(1, 0);
+      for (int b = 0; b < B.nbox; ++b) {
+        int pb = B.parent[b];
+        for (int dx = -1; dx <= 1; ++dx)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+              auto it = pmap.find(ijk_key(P.ijk[3 * pb] + dx, P.ijk[3 * pb + 1] + dy, P.ijk[3 * pb + 2] + dz));
+              if (it == pmap.end()) continue;
+              int nbp = it->second;
+              for (int s = P.ch_ptr[nbp]; s < P.ch_ptr[nbp + 1]; ++s) {
+                int b2 = P.ch_idx[s];
+                int d[3];
+                int far = 0;
+                for (int x = 0; x < 3; ++x) {
+                  d[x] = B.ijk[3 * b + x] - B.ijk[3 * b2 + x];
+                  far = std::max(far, std::abs(d[x]));
+                }
+                if (far < 2) continue;
+                int code = (d[0] + 3) * 49 + (d[1] + 3) * 7 + (d[2] + 3);
+                auto si = slot_of.find(code);
+                int slot;
+                if (si == slot_of.end()) {
+                  slot = (int)B.slot_code.size();
+                  slot_of[code] = slot;
+                  B.slot_code.push_back(code);
+                } else {
+                  slot = si->second;
+                }
+                B.il_src.push_back(b2);
+                B.il_slot.push_back(slot);
+              }
+            }
+        B.il_ptr.push_back((int)B.il_src.size());
+      }
+    }
+    // directions and tables
+    double kr = R.k.real();
+    for (int lv = 2; lv <= leaf; ++lv) {
+      LevelHost &B = R.lev[lv];
+      B.L = trunc_L(kr, B.a, digits);
+    }
+    std::vector<Dirs> dirs(levels);
+    for (int lv = 2; lv <= leaf; ++lv) {
+      dirs[lv] = make_dirs(R.lev[lv].L);
+      R.lev[lv].K = dirs[lv].K;
+    }
+    cd kc = R.k;
+    cd pref = kc * kc / (16.0 * PI * PI);
+    for (int lv = 2; lv <= leaf; ++lv) {
+      LevelHost &B = R.lev[lv];
+      const Dirs &Dd = dirs[lv];
+      int K = Dd.K, L = Dd.L;
+      B.d_dirs = dev_upload(c, Dd.d);
+      // translators (weights and constants folded in)
+      int ns = (int)B.slot_code.size();
+      std::vector<cd> T((size_t)std::max(ns, 1) * K);
+      std::vector<cd> h(L + 1);
+      std::vector<double> Pl(L + 1);
+      for (int s = 0; s < ns; ++s) {
+        int code = B.slot_code[s];
+        int d[3] = {code / 49 - 3, (code / 7) % 7 - 3, code % 7 - 3};
+        double X[3] = {d[0] * B.a, d[1] * B.a, d[2] * B.a};
+        double Xn = std::sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+        hankel2_all(L, kc * Xn, h.data());
+        std::vector<cd> coef(L + 1);
+        cd mj(1.0, 0.0);
+        for (int n = 0; n <= L; ++n) {
+          coef[n] = mj * (2.0 * n + 1.0) * h[n];
+          mj *= cd(0.0, -1.0);
+        }
+        for (int k = 0; k < K; ++k) {
+          const double *kh = &Dd.d[9 * k];
+          double ct = (kh[0] * X[0] + kh[1] * X[1] + kh[2] * X[2]) / Xn;
+          legendre_all(L, ct, Pl.data());
+          cd acc = 0.0;
+          for (int n = 0; n <= L; ++n) acc += coef[n] * Pl[n];
+          T[(size_t)s * K + k] = pref * Dd.w[k] * acc;
+        }
+      }
+      B.d_T64 = dev_upload(c, T);
+      std::vector<std::complex<float>> Tf(T.size());
+      for (size_t q = 0; q < T.size(); ++q) Tf[q] = std::complex<float>((float)T[q].real(), (float)T[q].imag());
+      B.d_T32 = dev_upload(c, Tf);
+      B.d_il_ptr = dev_upload(c, B.il_ptr);
+      B.d_il_src = dev_upload(c, B.il_src);
+      B.d_il_slot = dev_upload(c, B.il_slot);
+      // shifts between this level (parent) and its children
+      if (lv < leaf) {
+        std::vector<cd> up(8 * K), dn(8 * K);
+        const cd j(0.0, 1.0);
+        for (int o = 0; o < 8; ++o) {
+          double dl[3] = {B.a * 0.25 * (2 * (o & 1) - 1), B.a * 0.25 * (2 * ((o >> 1) & 1) - 1),
+                          B.a * 0.25 * (2 * ((o >> 2) & 1) - 1)};
+          for (int k = 0; k < K; ++k) {
+            const double *kh = &Dd.d[9 * k];
+            double kd = kh[0] * dl[0] + kh[1] * dl[1] + kh[2] * dl[2];
+            up[o * K + k] = std::exp(j * kc * kd);
+            dn[o * K + k] = std::exp(-j * kc * kd);
+          }
+        }
+        B.d_up64 = dev_upload(c, up);
+        B.d_dn64 = dev_upload(c, dn);
+        std::vector<std::complex<float>> uf(8 * K), df(8 * K);
+        for (int q = 0; q < 8 * K; ++q) {
+          uf[q] = std::complex<float>((float)up[q].real(), (float)up[q].imag());
+          df[q] = std::complex<float>((float)dn[q].real(), (float)dn[q].imag());
+        }
+        B.d_up32 = dev_upload(c, uf);
+        B.d_dn32 = dev_upload(c, df);
+        // exact interpolation from level lv+1 (spherical-harmonic projection, degree L of the child)
+        const Dirs &Dc = dirs[lv + 1];
+        int Kc = Dc.K, Lc = Dc.L;
+        std::vector<double> A((size_t)2 * K * 2 * Kc);
+        std::vector<double> Pc(Lc + 1);
+        for (int p = 0; p < K; ++p) {
+          const double *dp = &Dd.d[9 * p];
+          for (int q = 0; q < Kc; ++q) {
+            const double *dq = &Dc.d[9 * q];
+            double ct = dp[0] * dq[0] + dp[1] * dq[1] + dp[2] * dq[2];
+            ct = std::max(-1.0, std::min(1.0, ct));
+            legendre_all(Lc, ct, Pc.data());
+            double s = 0;
+            for (int n = 0; n <= Lc; ++n) s += (2.0 * n + 1.0) * Pc[n];
+            s *= Dc.w[q] / (4.0 * PI);
+            for (int al = 0; al < 2; ++al)
+              for (int be = 0; be < 2; ++be) {
+                const double *ua = dp + 3 + 3 * al, *ub = dq + 3 + 3 * be;
+                double dot = ua[0] * ub[0] + ua[1] * ub[1] + ua[2] * ub[2];
+                A[(size_t)(al * K + p) * (2 * Kc) + (be * Kc + q)] = s * dot;
+              }
+          }
+        }
+        B.d_A64 = dev_upload(c, A);
+        std::vector<float> Af(A.size());
+        for (size_t q = 0; q < A.size(); ++q) Af[q] = (float)A[q];
+        B.d_A32 = dev_upload(c, Af);
+        B.d_ch_ptr = dev_upload(c, B.ch_ptr);
+        B.d_ch_idx = dev_upload(c, B.ch_idx);
+      }
+      if (lv > 2) {
+        B.d_oct = dev_upload(c, B.oct);
+        B.d_parent = dev_upload(c, B.parent);
+      }
+    }
+    // leaf tables
+    R.d_basis_p = dev_upload(c, R.basis_p);
+    R.d_basis_sign = dev_upload(c, R.basis_sign);
+    R.d_box_start = dev_upload(c, R.box_start);
+    R.d_basis_box = dev_upload(c, basis_box);
+    std::vector<double> cen(3 * LL.nbox);
+    for (int b = 0; b < LL.nbox; ++b)
+      for (int x = 0; x < 3; ++x) cen[3 * b + x] = c->origin[x] + (LL.ijk[3 * b + x] + 0.5) * c->hleaf;
+    R.d_box_centre = dev_upload(c, cen);
+  }
+  c->have_tree = true;
+}
+
+extern "C" sie_status mlfmm_setup(sie_ctx *c, const sie_mlfmm_opts *o) {
+  return guard(c, [&] {
+    SIE_REQUIRE(c->have_mesh, SIE_ESTATE, "mlfmm_setup: call sie_build_mesh first");
+    SIE_REQUIRE(!c->have_tree, SIE_ESTATE, "mlfmm_setup: already set up");
+    SIE_REQUIRE(o, SIE_EINVAL, "mlfmm_setup: null options");
+    setup_tree(c, o->levels, o->digits);
+  });
+}
+
+// ------------------------------------------------------------------ ILU(0), 2x2 blocks, box-colour order
+static inline void inv2(const cd *a, cd *o, bool &ok) {
+  cd det = a[0] * a[3] - a[1] * a[2];
+  if (std::abs(det) == 0.0 || !std::isfinite(std::abs(det))) {
+    ok = false;
+    return;
+  }
+  o[0] = a[3] / det;
+  o[1] = -a[1] / det;
+  o[2] = -a[2] / det;
+  o[3] = a[0] / det;
+}
+static inline void mul2(const cd *a, const cd *b, cd *o) {
+  cd r0 = a[0] * b[0] + a[1] * b[2], r1 = a[0] * b[1] + a[1] * b[3];
+  cd r2 = a[2] * b[0] + a[3] * b[2], r3 = a[2] * b[1] + a[3] * b[3];
+  o[0] = r0; o[1] = r1; o[2] = r2; o[3] = r3;
+}
+
+static void build_ilu(sie_ctx *c) {
+  const int ne = c->ne;
+  const int64_t nnz = c->row_ptr[ne];
+  std::vector<cd> F((size_t)nnz * 4);
+  SIE_CUDA(cudaMemcpy(F.data(), c->d_near64, (size_t)nnz * 4 * sizeof(cd), cudaMemcpyDeviceToHost));
+  std::vector<int> diag(ne, -1);
+  for (int i = 0; i < ne; ++i)
+    for (int e = c->row_ptr[i]; e < c->row_ptr[i + 1]; ++e)
+      if (c->col[e] == i) diag[i] = e;
+  int nlb = (int)c->leaf_start.size() - 1;
+  std::vector<int> bcol(nlb);
+  std::vector<int> cptr(9, 0);
+  for (int b = 0; b < nlb; ++b) {
+    bcol[b] = (c->leaf_ijk[3 * b] & 1) | ((c->leaf_ijk[3 * b + 1] & 1) << 1) | ((c->leaf_ijk[3 * b + 2] & 1) << 2);
+    cptr[bcol[b] + 1]++;
+  }
+  for (int q = 0; q < 8; ++q) cptr[q + 1] += cptr[q];
+  // boxes are already in colour order (internal order is colour-major)
+  std::vector<cd> Dinv((size_t)ne * 4);
+  std::atomic<bool> ok(true);
+  unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  for (int col = 0; col < 8; ++col) {
+    std::atomic<int> next(cptr[col]);
+    auto work = [&]() {
+      std::vector<int> where(ne, -1);
+      for (;;) {
+        int b = next.fetch_add(1);
+        if (b >= cptr[col + 1]) break;
+        for (int i = c->leaf_start[b]; i < c->leaf_start[b + 1]; ++i) {
+          int s = c->row_ptr[i], e = c->row_ptr[i + 1];
+          for (int q = s; q < e; ++q) where[c->col[q]] = q;
+          for (int q = s; q < e && c->col[q] < i; ++q) {
+            int k = c->col[q];
+            cd m[4];
+            mul2(&F[4 * (size_t)q], &Dinv[4 * (size_t)k], m);
+            for (int x = 0; x < 4; ++x) F[4 * (size_t)q + x] = m[x];
+            for (int r = diag[k] + 1; r < c->row_ptr[k + 1]; ++r) {
+              int w = where[c->col[r]];
+              if (w < 0) continue;
+              cd u[4];
+              mul2(m, &F[4 * (size_t)r], u);
+              for (int x = 0; x < 4; ++x) F[4 * (size_t)w + x] -= u[x];
+            }
+          }
+          bool good = true;
+          inv2(&F[4 * (size_t)diag[i]], &Dinv[4 * (size_t)i], good);
+          if (!good) ok = false;
+          for (int q = s; q < e; ++q) where[c->col[q]] = -1;
+        }
+      }
+    };
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nth; ++t) th.emplace_back(work);
+    for (auto &t : th) t.join();
+    SIE_REQUIRE(ok, SIE_EZEROPIVOT, "ILU(0): singular 2x2 diagonal block");
+  }
+  // apply structures
+  std::vector<int> ebox(ne);
+  for (int b = 0; b < nlb; ++b)
+    for (int p = c->leaf_start[b]; p < c->leaf_start[b + 1]; ++p) ebox[p] = b;
+  std::vector<int> lo_ptr(1, 0), up_ptr(1, 0), lo_col, up_col;
+  std::vector<cd> lo_val, up_val;
+  std::vector<int64_t> doff(nlb + 1, 0);
+  int maxb = 0;
+  for (int b = 0; b < nlb; ++b) {
+    int n = c->leaf_start[b + 1] - c->leaf_start[b];
+    maxb = std::max(maxb, n);
+    doff[b + 1] = doff[b] + (int64_t)n * n;
+  }
+  std::vector<cd> dense((size_t)doff[nlb] * 4);
+  for (int i = 0; i < ne; ++i) {
+    int bi = ebox[i], s0 = c->leaf_start[bi], n = c->leaf_start[bi + 1] - s0;
+    for (int q = c->row_ptr[i]; q < c->row_ptr[i + 1]; ++q) {
+      int k = c->col[q];
+      const cd *v = &F[4 * (size_t)q];
+      if (ebox[k] == bi) {
+        size_t o = (size_t)(doff[bi] + (int64_t)(k - s0) * n + (i - s0)) * 4;
+        for (int x = 0; x < 4; ++x) dense[o + x] = v[x];
+      } else if (k < i) {
+        lo_col.push_back(k);
+        for (int x = 0; x < 4; ++x) lo_val.push_back(v[x]);
+      } else {
+        up_col.push_back(k);
+        for (int x = 0; x < 4; ++x) up_val.push_back(v[x]);
+      }
+    }
+    lo_ptr.push_back((int)lo_col.size());
+    up_ptr.push_back((int)up_col.size());
+  }
+  IluHost &I = c->ilu;
+  I.nboxes = nlb;
+  I.colour_ptr = cptr;
+  I.max_box = maxb;
+  std::vector<int> bl(nlb);
+  for (int b = 0; b < nlb; ++b) bl[b] = b;
+  I.d_box_start = dev_upload(c, c->leaf_start);
+  I.d_box_list = dev_upload(c, bl);
+  I.d_lo_ptr = dev_upload(c, lo_ptr);
+  I.d_up_ptr = dev_upload(c, up_ptr);
+  I.d_lo_col = dev_upload(c, lo_col);
+  I.d_up_col = dev_upload(c, up_col);
+  I.d_lo64 = dev_upload(c, lo_val);
+  I.d_up64 = dev_upload(c, up_val);
+  I.d_dense_off = dev_upload(c, doff);
+  I.d_dense64 = dev_upload(c, dense);
+  I.d_dinv64 = dev_upload(c, Dinv);
+  auto f32 = [&](const std::vector<cd> &v) {
+    std::vector<std::complex<float>> o(v.size());
+    for (size_t q = 0; q < v.size(); ++q) o[q] = std::complex<float>((float)v[q].real(), (float)v[q].imag());
+    return dev_upload(c, o);
+  };
+  I.d_lo32 = f32(lo_val);
+  I.d_up32 = f32(up_val);
+  I.d_dense32 = f32(dense);
+  I.d_dinv32 = f32(Dinv);
+  I.ready = true;
+}
+
+// ------------------------------------------------------------------ API: fill
+static void fill_all(sie_ctx *c, const sie_fill_opts *o) {
+  const int ne = c->ne, nt = c->nt;
+  int on = o ? o->outer_order : 4;
+  SIE_REQUIRE(on >= 2 && on <= 12, SIE_EINVAL, "sie_fill_nearfield: outer_order must be in [2, 12]");
+  // geometry tables, internal edge ids
+  std::vector<double> tri(22 * (size_t)nt);
+  std::vector<int> tri_e(3 * (size_t)nt);
+  std::vector<double> tri_sg(3 * (size_t)nt);
+  for (int t = 0; t < nt; ++t) {
+    double *o2 = &tri[22 * (size_t)t];
+    for (int a = 0; a < 3; ++a)
+      for (int x = 0; x < 3; ++x) o2[3 * a + x] = c->verts[3 * c->tris[3 * t + a] + x];
+    for (int x = 0; x < 3; ++x) o2[9 + x] = c->normal[3 * t + x];
+    o2[12] = c->area[t];
+    for (int a = 0; a < 3; ++a) {
+      int e = c->tri_edge[3 * t + a];
+      tri_e[3 * t + a] = e >= 0 ? c->inv[e] : -1;
+      tri_sg[3 * t + a] = e >= 0 ? c->tri_sign[3 * t + a] * c->elen[e] / (2.0 * c->area[t]) : 0.0;
+      for (int x = 0; x < 3; ++x) o2[13 + 3 * a + x] = c->verts[3 * c->tri_free[3 * t + a] + x];
+    }
+  }
+  c->d_tri = dev_upload(c, tri);
+  c->d_tri_e = dev_upload(c, tri_e);
+  c->d_tri_sg = dev_upload(c, tri_sg);
+  c->d_tri_reg = dev_upload(c, c->tri_reg);
+  c->d_row_ptr = dev_upload(c, c->row_ptr);
+  c->d_col = dev_upload(c, c->col);
+  c->d_perm = dev_upload(c, c->perm);
+  c->d_inv = dev_upload(c, c->inv);
+  std::vector<int> etri(2 * (size_t)ne), ereg(2 * (size_t)ne);
+  for (int p = 0; p < ne; ++p) {
+    int e = c->perm[p];
+    etri[2 * p] = c->tp[e];
+    etri[2 * p + 1] = c->tm[e];
+    ereg[2 * p] = c->tri_reg[2 * c->tp[e]];
+    ereg[2 * p + 1] = c->tri_reg[2 * c->tp[e] + 1];
+  }
+  c->d_edge_tris = dev_upload(c, etri);
+  c->d_edge_reg = dev_upload(c, ereg);
+  // singular outer rule: n x n collapsed Gauss (barycentric b0,b1,b2,w)
+  std::vector<double> x, wx, q;
+  gauss_legendre(on, x, wx);
+  for (int i = 0; i < on; ++i)
+    for (int j = 0; j < on; ++j) {
+      double u = 0.5 * (x[i] + 1.0), wu = 0.5 * wx[i];
+      double v = 0.5 * (x[j] + 1.0), wv = 0.5 * wx[j];
+      double xi = u, eta = v * (1.0 - u);
+      q.push_back(1.0 - xi - eta);
+      q.push_back(xi);
+      q.push_back(eta);
+      q.push_back(2.0 * wu * wv * (1.0 - u));
+    }
+  c->nq_sing = on * on;
+  c->d_quad = dev_upload(c, q);
+  // near matrix
+  int64_t nnz = c->row_ptr[ne];
+  c->d_near64 = dev_alloc(c, (size_t)nnz * 4 * sizeof(zd));
+  c->d_near32 = dev_alloc(c, (size_t)nnz * 4 * sizeof(zf));
+  SIE_CUDA(cudaMemsetAsync(c->d_near64, 0, (size_t)nnz * 4 * sizeof(zd), c->stream));
+  // triangle pairs per medium: tri p (test) x tri q (source) with some near basis pair
+  std::vector<int> tri_int_edges(3 * (size_t)nt);
+  for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < 3; ++a) tri_int_edges[3 * t + a] = tri_e[3 * t + a];
+  for (int l = 0; l < c->nr; ++l) {
+    RegionHost &R = c->reg[l];
+    std::vector<int> tl;
+    for (int t = 0; t < nt; ++t)
+      if (c->tri_reg[2 * t] == l || c->tri_reg[2 * t + 1] == l) tl.push_back(t);
+    if (tl.empty()) continue;
+    unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::vector<int>> part(nth);
+    std::atomic<size_t> next(0);
+    auto work = [&](unsigned id) {
+      std::vector<int> mark(nt, -1), lst;
+      for (;;) {
+        size_t ii = next.fetch_add(1);
+        if (ii >= tl.size()) break;
+        int p = tl[ii];
+        lst.clear();
+        for (int a = 0; a < 3; ++a) {
+          int m = tri_int_edges[3 * p + a];
+          if (m < 0) continue;
+          for (int e = c->row_ptr[m]; e < c->row_ptr[m + 1]; ++e) {
+            int n = c->perm[c->col[e]];
+            int ts[2] = {c->tp[n], c->tm[n]};
+            for (int s = 0; s < 2; ++s) {
+              int qq = ts[s];
+              if (mark[qq] == p) continue;
+              if (!(c->tri_reg[2 * qq] == l || c->tri_reg[2 * qq + 1] == l)) continue;
+              mark[qq] = p;
+              lst.push_back(qq);
+            }
+          }
+        }
+        std::sort(lst.begin(), lst.end());
+        for (int qq : lst) {
+          double dx = c->centroid[3 * p] - c->centroid[3 * qq], dy = c->centroid[3 * p + 1] - c->centroid[3 * qq + 1],
+                 dz = c->centroid[3 * p + 2] - c->centroid[3 * qq + 2];
+          double d = std::sqrt((dx * dx + dy * dy) + dz * dz);
+          int sing = d < (c->hmax[p] + c->hmax[qq]) ? 1 : 0;
+          part[id].push_back(p);
+          part[id].push_back(qq);
+          part[id].push_back(sing);
+        }
+      }
+    };
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nth; ++t) th.emplace_back(work, t);
+    for (auto &t : th) t.join();
+    // singular pairs first (heavier), then regular: keeps warps uniform
+    std::vector<int> pairs;
+    for (int pass = 1; pass >= 0; --pass)
+      for (auto &pv : part)
+        for (size_t s = 0; s < pv.size(); s += 3)
+          if (pv[s + 2] == pass) pairs.insert(pairs.end(), {pv[s], pv[s + 1], pv[s + 2]});
+    R.npairs = (int64_t)pairs.size() / 3;
+    R.d_pairs = dev_upload(c, pairs);
+    launch_near_fill(c, l);
+  }
+  launch_identity(c);
+  if (c->levels >= 3)
+    for (int l = 0; l < c->nr; ++l)
+      if (c->reg[l].nb > 0) launch_patterns(c, l);
+  launch_to_f32(c, (const double *)c->d_near64, (float *)c->d_near32, nnz * 8);
+  SIE_CUDA(cudaStreamSynchronize(c->stream));
+  if (!o || o->build_ilu) build_ilu(c);
+  c->have_fill = true;
+}
+
+extern "C" sie_status sie_fill_nearfield(sie_ctx *c, const sie_fill_opts *o) {
+  return guard(c, [&] {
+    SIE_REQUIRE(c->have_tree, SIE_ESTATE, "sie_fill_nearfield: call mlfmm_setup first");
+    SIE_REQUIRE(!c->have_fill, SIE_ESTATE, "sie_fill_nearfield: already filled");
+    fill_all(c, o);
+  });
+}
+
+// ------------------------------------------------------------------ API: operator
+extern "C" sie_status sie_matvec_parts(sie_ctx *c, const void *x, void *y, int64_t nrhs, sie_prec prec,
+                                       int32_t parts) {
+  return guard(c, [&] {
+    SIE_REQUIRE(c->have_fill, SIE_ESTATE, "matvec: call sie_fill_nearfield first");
+    SIE_REQUIRE(x && y && x != y && nrhs >= 1 && nrhs <= 4096, SIE_EINVAL, "matvec: bad buffers or nrhs");
+    SIE_REQUIRE(prec == SIE_PREC_FP64 || prec == SIE_PREC_MIXED, SIE_EINVAL, "matvec: bad precision");
+    SIE_REQUIRE(parts >= 1 && parts <= 3, SIE_EINVAL, "matvec: parts must be 1, 2 or 3");
+    ensure_work(c, nrhs);
+    op_permute_in(c, (const zd *)x, (zd *)c->d_xi, (int)nrhs);
+    apply_matvec(c, (const zd *)c->d_xi, (zd *)c->d_yi, (int)nrhs, prec, parts);
+    op_permute_out(c, (const zd *)c->d_yi, (zd *)y, (int)nrhs);
+  });
+}
+
+extern "C" sie_status mlfmm_matvec(sie_ctx *c, const void *x, void *y, int64_t nrhs, sie_prec prec) {
+  return sie_matvec_parts(c, x, y, nrhs, prec, 3);
+}
+
+extern "C" sie_status ilu_apply(sie_ctx *c, const void *r, void *z, int64_t nrhs, sie_prec prec) {
+  return guard(c, [&] {
+    SIE_REQUIRE(c->have_fill && c->ilu.ready, SIE_ESTATE, "ilu_apply: no ILU factors (fill with build_ilu)");
+    SIE_REQUIRE(r && z && r != z && nrhs >= 1 && nrhs <= 4096, SIE_EINVAL, "ilu_apply: bad buffers or nrhs");
+    SIE_REQUIRE(prec == SIE_PREC_FP64 || prec == SIE_PREC_MIXED, SIE_EINVAL, "ilu_apply: bad precision");
+    ensure_work(c, nrhs);
+    op_permute_in(c, (const zd *)r, (zd *)c->d_xi, (int)nrhs);
+    apply_ilu(c, (const zd *)c->d_xi, (zd *)c->d_yi, (int)nrhs, prec);
+    op_permute_out(c, (const zd *)c->d_yi, (zd *)z, (int)nrhs);
+  });
+}
+
+extern "C" sie_status sie_plane_wave_rhs(sie_ctx *c, const double *inc, int64_t nrhs, void *b) {
+  return guard(c, [&] {
+    SIE_REQUIRE(c->have_fill, SIE_ESTATE, "sie_plane_wave_rhs: call sie_fill_nearfield first");
+    SIE_REQUIRE(inc && b && nrhs >= 1 && nrhs <= 4096, SIE_EINVAL, "sie_plane_wave_rhs: bad arguments");
+    ensure_work(c, nrhs);
+    double *d_inc = (double *)stage(c, (size_t)nrhs * 4 * sizeof(double));
+    SIE_CUDA(cudaMemcpyAsync(d_inc, inc, (size_t)nrhs * 4 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    launch_rhs(c, d_inc, (int)nrhs, (zd *)c->d_xi);
+    op_permute_out(c, (const zd *)c->d_xi, (zd *)b, (int)nrhs);
+    SIE_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+extern "C" sie_status gmres_solve(sie_ctx *c, const void *b, void *x, int64_t nrhs, const sie_solve_opts *o,
+                                  sie_solve_stats *st) {
+  sie_status rc = SIE_OK;
+  sie_status g = guard(c, [&] {
+    SIE_REQUIRE(c->have_fill, SIE_ESTATE, "gmres_solve: call sie_fill_nearfield first");
+    SIE_REQUIRE(b && x && o && st && nrhs >= 1 && nrhs <= 4096, SIE_EINVAL, "gmres_solve: bad arguments");
+    SIE_REQUIRE(o->restart >= 1 && o->restart <= 500 && o->max_iters >= 1 && o->tol > 0, SIE_EINVAL,
+                "gmres_solve: bad options");
+    SIE_REQUIRE(o->precond == 0 || c->ilu.ready, SIE_ESTATE, "gmres_solve: ILU requested but not built");
+    rc = run_gmres(c, (const zd *)b, (zd *)x, (int)nrhs, o, st);
+  });
+  return g != SIE_OK ? g : rc;
+}
+
+extern "C" sie_status rcs_farfield(sie_ctx *c, const void *x, int64_t nrhs, const double *obs, int64_t nobs,
+                                   double *rcs) {
+  return guard(c, [&] {
+    SIE_REQUIRE(c->have_fill, SIE_ESTATE, "rcs_farfield: call sie_fill_nearfield first");
+    SIE_REQUIRE(x && obs && rcs && nrhs >= 1 && nobs >= 1 && nrhs <= 4096 && nobs <= 1000000, SIE_EINVAL,
+                "rcs_farfield: bad arguments");
+    ensure_work(c, nrhs);
+    op_permute_in(c, (const zd *)x, (zd *)c->d_xi, (int)nrhs);
+    size_t ob = ((size_t)nobs * 2 * sizeof(double) + 255) / 256 * 256;
+    double *d_obs = (double *)stage(c, ob + (size_t)nrhs * nobs * 2 * sizeof(double));
+    double *d_out = (double *)((char *)d_obs + ob);
+    SIE_CUDA(cudaMemcpyAsync(d_obs, obs, (size_t)nobs * 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    launch_farfield(c, (const zd *)c->d_xi, (int)nrhs, d_obs, (int)nobs, d_out);
+    SIE_CUDA(cudaMemcpyAsync(rcs, d_out, (size_t)nrhs * nobs * 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SIE_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+extern "C" sie_status sie_near_export(sie_ctx *c, int32_t *rows, int32_t *cols, double *vals, int64_t *nnzb) {
+  return guard(c, [&] {
+    SIE_REQUIRE(c->have_fill, SIE_ESTATE, "sie_near_export: call sie_fill_nearfield first");
+    SIE_REQUIRE(nnzb, SIE_EINVAL, "sie_near_export: null nnzb");
+    int64_t nnz = c->row_ptr[c->ne];
+    *nnzb = nnz;
+    if (!rows) return;
+    SIE_REQUIRE(cols && vals, SIE_EINVAL, "sie_near_export: null cols/vals");
+    SIE_CUDA(cudaStreamSynchronize(c->stream));
+    SIE_CUDA(cudaMemcpy(vals, c->d_near64, (size_t)nnz * 8 * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int p = 0; p < c->ne; ++p)
+      for (int e = c->row_ptr[p]; e < c->row_ptr[p + 1]; ++e) {
+        rows[e] = c->perm[p];
+        cols[e] = c->perm[c->col[e]];
+      }
+  });
+}
+
+extern "C" sie_status sie_query(const sie_ctx *c, int32_t key, int64_t *v) {
+  if (!c || !v) return SIE_EINVAL;
+  switch (key) {
+    case 0: *v = c->ne; return SIE_OK;
+    case 1: *v = c->have_tree ? c->row_ptr[c->ne] : 0; return SIE_OK;
+    case 2: *v = c->levels; return SIE_OK;
+    case 3: *v = c->nr; return SIE_OK;
+    case 4: *v = c->have_tree ? (int64_t)c->leaf_start.size() - 1 : 0; return SIE_OK;
+    case 5: *v = c->have_tree ? (int64_t)c->row_ptr[c->ne] * 64 : 0; return SIE_OK;
+    case 6: {
+      int64_t s = 0;
+      for (auto &R : c->reg)
+        if (R.nb > 0 && c->levels > 0) s += (int64_t)R.nb * 4 * R.lev[c->levels - 1].K * 16;
+      *v = s;
+      return SIE_OK;
+    }
+    case 7: *v = c->dev_bytes; return SIE_OK;
+    case 8: *v = c->launches; return SIE_OK;
+    default:
+      if (key >= 100 && key < 100 + 16 * 64) {
+        int l = (key - 100) / 16, j = (key - 100) % 16;
+        if (l < (int)c->reg.size() && j < (int)c->reg[l].lev.size()) {
+          *v = c->reg[l].lev[j].K;
+          return SIE_OK;
+        }
+      }
+      return SIE_EINVAL;
+  }
+}

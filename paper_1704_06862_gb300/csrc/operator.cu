@@ -1,0 +1,572 @@
+// Hot path of the solver: y = Z x as near-field block-sparse product plus the
+// MLFMM far field of every medium, and the ILU(0) preconditioner sweeps.
+// Every kernel is templated on the real type: double (plain form) or float
+// (mixed form, FP32 complex with FP32 accumulation).
+#include <algorithm>
+
+#include "common.h"
+
+namespace {
+
+template <typename T> struct tsel;
+template <> struct tsel<double> {
+  static void *near(sie_ctx *c) { return c->d_near64; }
+  static void *V(RegionHost &R) { return R.d_V64; }
+  static void *RN(RegionHost &R) { return R.d_RN64; }
+  static void *Tr(LevelHost &L) { return L.d_T64; }
+  static void *A(LevelHost &L) { return L.d_A64; }
+  static void *up(LevelHost &L) { return L.d_up64; }
+  static void *dn(LevelHost &L) { return L.d_dn64; }
+  static void *lo(IluHost &I) { return I.d_lo64; }
+  static void *upv(IluHost &I) { return I.d_up64; }
+  static void *dense(IluHost &I) { return I.d_dense64; }
+  static void *dinv(IluHost &I) { return I.d_dinv64; }
+};
+template <> struct tsel<float> {
+  static void *near(sie_ctx *c) { return c->d_near32; }
+  static void *V(RegionHost &R) { return R.d_V32; }
+  static void *RN(RegionHost &R) { return R.d_RN32; }
+  static void *Tr(LevelHost &L) { return L.d_T32; }
+  static void *A(LevelHost &L) { return L.d_A32; }
+  static void *up(LevelHost &L) { return L.d_up32; }
+  static void *dn(LevelHost &L) { return L.d_dn32; }
+  static void *lo(IluHost &I) { return I.d_lo32; }
+  static void *upv(IluHost &I) { return I.d_up32; }
+  static void *dense(IluHost &I) { return I.d_dense32; }
+  static void *dinv(IluHost &I) { return I.d_dinv32; }
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> shfl_down(cx<T> v, int d) {
+  return cx<T>(__shfl_down_sync(0xffffffffu, v.re, d), __shfl_down_sync(0xffffffffu, v.im, d));
+}
+template <typename T>
+__device__ __forceinline__ cx<T> warp_sum(cx<T> v) {
+  for (int d = 16; d > 0; d >>= 1) v += shfl_down(v, d);
+  return v;
+}
+
+// ---------------------------------------------------------------- near field
+// y[p] (+)= sum_q B_pq x[q], 2x2 complex blocks (JJ, JM, MJ, MM); one warp per
+// block row, lanes stride over the row's blocks (coalesced 16-byte loads).
+template <typename T>
+__global__ void k_near_spmv(int ne, int nrhs, const int *__restrict__ row_ptr, const int *__restrict__ col,
+                            const cx<T> *__restrict__ B, const cx<T> *__restrict__ x, cx<T> *__restrict__ y,
+                            int accumulate) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= ne) return;
+  int s = row_ptr[warp], e = row_ptr[warp + 1];
+  for (int r = 0; r < nrhs; ++r) {
+    const cx<T> *xr = x + (size_t)r * ne * 2;
+    cx<T> a0, a1;
+    for (int q = s + lane; q < e; q += 32) {
+      int cc = col[q];
+      const cx<T> *b = B + 4 * (size_t)q;
+      cx<T> b0 = b[0], b1 = b[1], b2 = b[2], b3 = b[3];
+      cx<T> xj = xr[2 * cc], xm = xr[2 * cc + 1];
+      a0 = cfma(b0, xj, a0);
+      a0 = cfma(b1, xm, a0);
+      a1 = cfma(b2, xj, a1);
+      a1 = cfma(b3, xm, a1);
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    if (lane == 0) {
+      cx<T> *yr = y + ((size_t)r * ne + warp) * 2;
+      if (accumulate) {
+        yr[0] += a0;
+        yr[1] += a1;
+      } else {
+        yr[0] = a0;
+        yr[1] = a1;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- MLFMM
+// Leaf aggregation: S_b(k) = sum_{i in b} s_i [eta0 c, v]_p(i) (x) V_i(k),
+// S layout [box][J/M][theta/phi][k][r].
+template <typename T>
+__global__ void k_aggregate(int nbox, int K, int ne, int nrhs, const int *__restrict__ box_start,
+                            const int *__restrict__ basis_p, const int *__restrict__ sign,
+                            const cx<T> *__restrict__ V, const cx<T> *__restrict__ x, cx<T> *__restrict__ S) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  if (k >= K) return;
+  int i0 = box_start[b], i1 = box_start[b + 1];
+  for (int r = 0; r < nrhs; ++r) {
+    cx<T> a0, a1, a2, a3;
+    const cx<T> *xr = x + (size_t)r * ne * 2;
+    for (int i = i0; i < i1; ++i) {
+      int p = basis_p[i];
+      T s = (T)sign[i];
+      cx<T> xj = s * xr[2 * p], xm = s * xr[2 * p + 1];
+      cx<T> vt = V[((size_t)i * 2) * K + k], vp = V[((size_t)i * 2 + 1) * K + k];
+      a0 = cfma(xj, vt, a0);
+      a1 = cfma(xj, vp, a1);
+      a2 = cfma(xm, vt, a2);
+      a3 = cfma(xm, vp, a3);
+    }
+    cx<T> *o = S + ((size_t)b * 4 * K + k) * nrhs + r;
+    o[0] = a0;
+    o[(size_t)K * nrhs] = a1;
+    o[(size_t)2 * K * nrhs] = a2;
+    o[(size_t)3 * K * nrhs] = a3;
+  }
+}
+
+// Real-by-complex GEMM on column blocks: C(row, col) (+)= sum_kk opA(row, kk) B(kk, col)
+// with opA = A [M x Kd] row-major (trans = 0) or A^T for A [Kd x M] (trans = 1).
+// B(kk, col) lives at B[((col / R) * Kd + kk) * R + col % R]; C likewise with M rows.
+template <typename T, int TM, int TN, int TK>
+__global__ void k_gemm_rc(int M, int N, int Kd, int R, const T *__restrict__ A, int trans,
+                          const cx<T> *__restrict__ B, cx<T> *__restrict__ C, int accumulate) {
+  __shared__ T As[TK][TM + 1];
+  __shared__ cx<T> Bs[TK][TN + 1];
+  int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads
+  int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  constexpr int RM = TM / 16, RN = TN / 16;
+  cx<T> acc[RM][RN];
+  for (int kk0 = 0; kk0 < Kd; kk0 += TK) {
+    for (int t = threadIdx.x; t < TK * TM; t += 256) {
+      int mm, kk;
+      T v = 0;
+      if (trans) {
+        mm = t % TM;
+        kk = t / TM;
+        int gm = m0 + mm, gk = kk0 + kk;
+        if (gm < M && gk < Kd) v = A[(size_t)gk * M + gm];
+      } else {
+        kk = t % TK;
+        mm = t / TK;
+        int gm = m0 + mm, gk = kk0 + kk;
+        if (gm < M && gk < Kd) v = A[(size_t)gm * Kd + gk];
+      }
+      As[kk][mm] = v;
+    }
+    for (int t = threadIdx.x; t < TK * TN; t += 256) {
+      int kk = t % TK, nn = t / TK;
+      int gk = kk0 + kk, gn = n0 + nn;
+      cx<T> v;
+      if (gk < Kd && gn < N) v = B[((size_t)(gn / R) * Kd + gk) * R + gn % R];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      T a[RM];
+#pragma unroll
+      for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < RN; ++j) {
+        cx<T> b = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) {
+          acc[i][j].re = fma(a[i], b.re, acc[i][j].re);
+          acc[i][j].im = fma(a[i], b.im, acc[i][j].im);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < RM; ++i)
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm < M && gn < N) {
+        cx<T> *o = C + ((size_t)(gn / R) * M + gm) * R + gn % R;
+        if (accumulate) *o += acc[i][j];
+        else *o = acc[i][j];
+      }
+    }
+}
+
+// Parent sum of shifted, interpolated child patterns:
+// S_p[jm][row][r] = sum_{children c} up[oct(c)][k(row)] Y_c[jm][row][r]
+template <typename T>
+__global__ void k_up_gather(int nbox, int K, int nrhs, const int *__restrict__ ch_ptr, const int *__restrict__ ch_idx,
+                            const int *__restrict__ oct, const cx<T> *__restrict__ up, const cx<T> *__restrict__ Y,
+                            cx<T> *__restrict__ S) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  if (k >= K) return;
+  for (int q = 0; q < 4; ++q) {
+    int row = (q & 1) * K + k;  // theta/phi block
+    int jm = q >> 1;
+    for (int r = 0; r < nrhs; ++r) {
+      cx<T> acc;
+      for (int s = ch_ptr[b]; s < ch_ptr[b + 1]; ++s) {
+        int c = ch_idx[s];
+        acc = cfma(up[oct[c] * K + k], Y[(((size_t)c * 2 + jm) * 2 * K + row) * nrhs + r], acc);
+      }
+      S[(((size_t)b * 2 + jm) * 2 * K + row) * nrhs + r] = acc;
+    }
+  }
+}
+
+// Downward shift of the parent's incoming field into each child's column:
+// U_c[jm][row][r] = dn[oct(c)][k(row)] I_parent(c)[jm][row][r]
+template <typename T>
+__global__ void k_dn_shift(int nchild, int Kp, int nrhs, const int *__restrict__ parent, const int *__restrict__ oct,
+                           const cx<T> *__restrict__ dn, const cx<T> *__restrict__ Ip, cx<T> *__restrict__ U) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (k >= Kp) return;
+  int pb = parent[c];
+  cx<T> sh = dn[oct[c] * Kp + k];
+  for (int q = 0; q < 4; ++q) {
+    int row = (q & 1) * Kp + k;
+    int jm = q >> 1;
+    for (int r = 0; r < nrhs; ++r)
+      U[(((size_t)c * 2 + jm) * 2 * Kp + row) * nrhs + r] = sh * Ip[(((size_t)pb * 2 + jm) * 2 * Kp + row) * nrhs + r];
+  }
+}
+
+// Diagonal M2L translation: I_b(k) = sum_{b' in IL(b)} T_{b-b'}(k) S_b'(k), 4 components.
+template <typename T>
+__global__ void k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr, const int *__restrict__ il_src,
+                      const int *__restrict__ il_slot, const cx<T> *__restrict__ Tr, const cx<T> *__restrict__ S,
+                      cx<T> *__restrict__ I) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  if (k >= K) return;
+  int e0 = il_ptr[b], e1 = il_ptr[b + 1];
+  for (int r = 0; r < nrhs; ++r) {
+    cx<T> a0, a1, a2, a3;
+    for (int e = e0; e < e1; ++e) {
+      int s = il_src[e];
+      cx<T> t = Tr[(size_t)il_slot[e] * K + k];
+      const cx<T> *src = S + ((size_t)s * 4 * K + k) * nrhs + r;
+      a0 = cfma(t, src[0], a0);
+      a1 = cfma(t, src[(size_t)K * nrhs], a1);
+      a2 = cfma(t, src[(size_t)2 * K * nrhs], a2);
+      a3 = cfma(t, src[(size_t)3 * K * nrhs], a3);
+    }
+    cx<T> *o = I + ((size_t)b * 4 * K + k) * nrhs + r;
+    o[0] = a0;
+    o[(size_t)K * nrhs] = a1;
+    o[(size_t)2 * K * nrhs] = a2;
+    o[(size_t)3 * K * nrhs] = a3;
+  }
+}
+
+// Leaf receive with the JMCFIE weights of medium l (weights and constants
+// folded into the translators):
+//   J-row: s_i R^t.F1 + R^n.F2,   M-row: s_i R^t.F3 + R^n.F4
+//   F1 = I^J - khat x I^M / eta,  F2 = (F1_phi, -F1_theta)
+//   F3 = -eta khat x I^J - I^M,   F4 = (-F3_phi, F3_theta)
+// R^t_i(k) = V_i(-k) read at the antipodal sample (theta comp as is, phi negated).
+template <typename T>
+__global__ void k_disaggregate(int nb, int K, int L, int ne, int nrhs, const int *__restrict__ basis_p,
+                               const int *__restrict__ sign, const int *__restrict__ basis_box,
+                               const cx<T> *__restrict__ V, const cx<T> *__restrict__ RN, const cx<T> *__restrict__ I,
+                               cx<T> eta, cx<T> ieta, cx<T> *__restrict__ y) {
+  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= nb) return;
+  int p = basis_p[i], b = basis_box[i];
+  T s = (T)sign[i];
+  int nph = 2 * L + 2;
+  const cx<T> *Vi = V + (size_t)i * 2 * K, *Ri = RN + (size_t)i * 2 * K;
+  for (int r = 0; r < nrhs; ++r) {
+    cx<T> yj, ym;
+    const cx<T> *Ib = I + (size_t)b * 4 * K * nrhs + r;
+    for (int k = lane; k < K; k += 32) {
+      int it = k / nph, jp = k - it * nph;
+      int ka = (L - it) * nph + (jp + L + 1) % nph;
+      cx<T> rtt = Vi[ka], rtp = -Vi[K + ka];
+      cx<T> rnt = Ri[k], rnp = Ri[K + k];
+      cx<T> iJt = Ib[(size_t)k * nrhs], iJp = Ib[(size_t)(K + k) * nrhs];
+      cx<T> iMt = Ib[(size_t)(2 * K + k) * nrhs], iMp = Ib[(size_t)(3 * K + k) * nrhs];
+      // khat x (a_t, a_p) = (-a_p, a_t)
+      cx<T> f1t = iJt + iMp * ieta, f1p = iJp - iMt * ieta;
+      cx<T> f3t = eta * iJp - iMt, f3p = -(eta * iJt) - iMp;
+      yj += s * (rtt * f1t + rtp * f1p) + (rnt * f1p - rnp * f1t);
+      ym += s * (rtt * f3t + rtp * f3p) + (rnp * f3t - rnt * f3p);
+    }
+    yj = warp_sum(yj);
+    ym = warp_sum(ym);
+    if (lane == 0) {
+      cx<T> *o = y + ((size_t)r * ne + p) * 2;
+      o[0] += yj;
+      o[1] += ym;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- ILU(0) sweeps
+// Forward: z = L^-1 v.  One CTA per leaf box of the current colour; off-box
+// terms come from earlier colours (final), the in-box unit-lower solve runs
+// in warp 0 with lanes over rows.  Backward analogous with U and later colours.
+template <typename T>
+__device__ __forceinline__ void mv2(const cx<T> *B, cx<T> x0, cx<T> x1, cx<T> &y0, cx<T> &y1) {
+  y0 = B[0] * x0 + B[1] * x1;
+  y1 = B[2] * x0 + B[3] * x1;
+}
+
+template <typename T>
+__global__ void k_ilu_sweep(int ne, int nrhs, int forward, const int *__restrict__ box_list, int first,
+                            const int *__restrict__ box_start, const int *__restrict__ off_ptr,
+                            const int *__restrict__ off_col, const cx<T> *__restrict__ off_val,
+                            const int64_t *__restrict__ dense_off, const cx<T> *__restrict__ dense,
+                            const cx<T> *__restrict__ dinv, const cx<T> *__restrict__ v, cx<T> *__restrict__ z) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<T> *rr = reinterpret_cast<cx<T> *>(smem_raw);  // [n][2]
+  int b = box_list[first + blockIdx.x];
+  int s0 = box_start[b], n = box_start[b + 1] - s0;
+  const cx<T> *D = dense + 4 * dense_off[b];
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = 0; r < nrhs; ++r) {
+    const cx<T> *vr = v + (size_t)r * ne * 2;
+    cx<T> *zr = z + (size_t)r * ne * 2;
+    for (int li = warp; li < n; li += nw) {
+      int i = s0 + li;
+      cx<T> a0, a1;
+      for (int q = off_ptr[i] + lane; q < off_ptr[i + 1]; q += 32) {
+        int cc = off_col[q];
+        cx<T> t0, t1;
+        mv2(off_val + 4 * (size_t)q, zr[2 * cc], zr[2 * cc + 1], t0, t1);
+        a0 += t0;
+        a1 += t1;
+      }
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      if (lane == 0) {
+        rr[2 * li] = vr[2 * i] - a0;
+        rr[2 * li + 1] = vr[2 * i + 1] - a1;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      if (forward) {
+        for (int j = 0; j < n; ++j) {
+          __syncwarp();
+          cx<T> z0 = rr[2 * j], z1 = rr[2 * j + 1];
+          __syncwarp();
+          for (int li = j + 1 + lane; li < n; li += 32) {
+            cx<T> t0, t1;
+            mv2(D + 4 * ((size_t)j * n + li), z0, z1, t0, t1);
+            rr[2 * li] -= t0;
+            rr[2 * li + 1] -= t1;
+          }
+          if (lane == 0) {
+            zr[2 * (s0 + j)] = z0;
+            zr[2 * (s0 + j) + 1] = z1;
+          }
+        }
+      } else {
+        for (int j = n - 1; j >= 0; --j) {
+          __syncwarp();
+          cx<T> x0, x1;
+          mv2(dinv + 4 * (size_t)(s0 + j), rr[2 * j], rr[2 * j + 1], x0, x1);
+          __syncwarp();
+          for (int li = lane; li < j; li += 32) {
+            cx<T> t0, t1;
+            mv2(D + 4 * ((size_t)j * n + li), x0, x1, t0, t1);
+            rr[2 * li] -= t0;
+            rr[2 * li + 1] -= t1;
+          }
+          if (lane == 0) {
+            zr[2 * (s0 + j)] = x0;
+            zr[2 * (s0 + j) + 1] = x1;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- vectors
+__global__ void k_perm_in(int ne, int nrhs, const int *__restrict__ perm, const zd *__restrict__ u, zd *__restrict__ v) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (p >= ne) return;
+  int e = perm[p];
+  v[((size_t)r * ne + p) * 2] = u[((size_t)r * ne + e) * 2];
+  v[((size_t)r * ne + p) * 2 + 1] = u[((size_t)r * ne + e) * 2 + 1];
+}
+__global__ void k_perm_out(int ne, int nrhs, const int *__restrict__ perm, const zd *__restrict__ v, zd *__restrict__ u) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (p >= ne) return;
+  int e = perm[p];
+  u[((size_t)r * ne + e) * 2] = v[((size_t)r * ne + p) * 2];
+  u[((size_t)r * ne + e) * 2 + 1] = v[((size_t)r * ne + p) * 2 + 1];
+}
+__global__ void k_d2f(const zd *a, zf *b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = zf((float)a[i].re, (float)a[i].im);
+}
+__global__ void k_f2d(const zf *a, zd *b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = zd(a[i].re, a[i].im);
+}
+
+inline int grid1(int64_t n, int bs) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + bs - 1) / bs, 152 * 32)); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+void op_near(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool accumulate) {
+  int warps_per_block = 8;
+  int blocks = (c->ne + warps_per_block - 1) / warps_per_block;
+  k_near_spmv<T><<<blocks, 32 * warps_per_block, 0, c->stream>>>(c->ne, nrhs, c->d_row_ptr, c->d_col,
+                                                                 (const cx<T> *)tsel<T>::near(c), x, y,
+                                                                 accumulate ? 1 : 0);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+
+template <typename T>
+static void gemm(sie_ctx *c, int M, int N, int Kd, int R, const T *A, int trans, const cx<T> *B, cx<T> *C, int acc) {
+  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  k_gemm_rc<T, 64, 64, 16><<<grid, 256, 0, c->stream>>>(M, N, Kd, R, A, trans, B, C, acc);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+
+template <typename T>
+void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
+  const int leaf = c->levels - 1;
+  const int R = nrhs;
+  if (c->levels < 3) return;  // every basis pair is near: no far field
+  for (RegionHost &G : c->reg) {
+    if (G.nb == 0) continue;
+    LevelHost &LL = G.lev[leaf];
+    // aggregation at the leaf level
+    {
+      dim3 grid((LL.K + 127) / 128, LL.nbox);
+      k_aggregate<T><<<grid, 128, 0, c->stream>>>(LL.nbox, LL.K, c->ne, R, G.d_box_start, G.d_basis_p,
+                                                  G.d_basis_sign, (const cx<T> *)tsel<T>::V(G), x,
+                                                  (cx<T> *)LL.d_S);
+      SIE_CHECK_LAUNCH();
+      c->launches++;
+    }
+    // upward pass: interpolate + shift into parents
+    for (int lv = leaf; lv >= 3; --lv) {
+      LevelHost &C = G.lev[lv], &P = G.lev[lv - 1];
+      cx<T> *Y = (cx<T> *)c->d_gemm;
+      gemm<T>(c, 2 * P.K, C.nbox * 2 * R, 2 * C.K, R, (const T *)tsel<T>::A(P), 0, (const cx<T> *)C.d_S, Y, 0);
+      dim3 grid((P.K + 127) / 128, P.nbox);
+      k_up_gather<T><<<grid, 128, 0, c->stream>>>(P.nbox, P.K, R, P.d_ch_ptr, P.d_ch_idx, C.d_oct,
+                                                  (const cx<T> *)tsel<T>::up(P), Y, (cx<T> *)P.d_S);
+      SIE_CHECK_LAUNCH();
+      c->launches++;
+    }
+    // translations at every level
+    for (int lv = 2; lv <= leaf; ++lv) {
+      LevelHost &B = G.lev[lv];
+      dim3 grid((B.K + 127) / 128, B.nbox);
+      k_m2l<T><<<grid, 128, 0, c->stream>>>(B.nbox, B.K, R, B.d_il_ptr, B.d_il_src, B.d_il_slot,
+                                            (const cx<T> *)tsel<T>::Tr(B), (const cx<T> *)B.d_S, (cx<T> *)B.d_I);
+      SIE_CHECK_LAUNCH();
+      c->launches++;
+    }
+    // downward pass: shift + anterpolate (exact transpose) into children
+    for (int lv = 2; lv < leaf; ++lv) {
+      LevelHost &P = G.lev[lv], &C = G.lev[lv + 1];
+      cx<T> *U = (cx<T> *)c->d_gemm;
+      dim3 grid((P.K + 127) / 128, C.nbox);
+      k_dn_shift<T><<<grid, 128, 0, c->stream>>>(C.nbox, P.K, R, C.d_parent, C.d_oct,
+                                                 (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, U);
+      SIE_CHECK_LAUNCH();
+      c->launches++;
+      gemm<T>(c, 2 * C.K, C.nbox * 2 * R, 2 * P.K, R, (const T *)tsel<T>::A(P), 1, U, (cx<T> *)C.d_I, 1);
+    }
+    // receive at the leaves
+    {
+      int wpb = 8;
+      int blocks = (G.nb + wpb - 1) / wpb;
+      std::complex<double> ie = 1.0 / G.eta;
+      k_disaggregate<T><<<blocks, 32 * wpb, 0, c->stream>>>(
+          G.nb, LL.K, LL.L, c->ne, R, G.d_basis_p, G.d_basis_sign, G.d_basis_box, (const cx<T> *)tsel<T>::V(G),
+          (const cx<T> *)tsel<T>::RN(G), (const cx<T> *)LL.d_I, cx<T>((T)G.eta.real(), (T)G.eta.imag()),
+          cx<T>((T)ie.real(), (T)ie.imag()), y);
+      SIE_CHECK_LAUNCH();
+      c->launches++;
+    }
+  }
+}
+
+template <typename T>
+void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
+  IluHost &I = c->ilu;
+  size_t smem = (size_t)std::max(I.max_box, 1) * 2 * sizeof(cx<T>);
+  for (int pass = 0; pass < 2; ++pass) {
+    bool fwd = pass == 0;
+    for (int q = 0; q < 8; ++q) {
+      int colr = fwd ? q : 7 - q;
+      int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
+      if (cnt == 0) continue;
+      k_ilu_sweep<T><<<cnt, 128, smem, c->stream>>>(
+          c->ne, nrhs, fwd ? 1 : 0, I.d_box_list, first, I.d_box_start, fwd ? I.d_lo_ptr : I.d_up_ptr,
+          fwd ? I.d_lo_col : I.d_up_col, (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), I.d_dense_off,
+          (const cx<T> *)tsel<T>::dense(I), (const cx<T> *)tsel<T>::dinv(I), fwd ? r : z, z);
+      SIE_CHECK_LAUNCH();
+      c->launches++;
+    }
+  }
+}
+
+void op_permute_in(sie_ctx *c, const zd *u, zd *v, int nrhs) {
+  dim3 grid((c->ne + 255) / 256, nrhs);
+  k_perm_in<<<grid, 256, 0, c->stream>>>(c->ne, nrhs, c->d_perm, u, v);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+void op_permute_out(sie_ctx *c, const zd *v, zd *u, int nrhs) {
+  dim3 grid((c->ne + 255) / 256, nrhs);
+  k_perm_out<<<grid, 256, 0, c->stream>>>(c->ne, nrhs, c->d_perm, v, u);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+void op_d2f(sie_ctx *c, const zd *a, zf *b, int64_t n) {
+  k_d2f<<<grid1(n, 256), 256, 0, c->stream>>>(a, b, n);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+void op_f2d(sie_ctx *c, const zf *a, zd *b, int64_t n) {
+  k_f2d<<<grid1(n, 256), 256, 0, c->stream>>>(a, b, n);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+
+void apply_matvec(sie_ctx *c, const zd *x, zd *y, int nrhs, sie_prec prec, int parts) {
+  int64_t n = (int64_t)nrhs * c->ne * 2;
+  if (prec == SIE_PREC_FP64) {
+    if (parts & 1) op_near<double>(c, x, y, nrhs, false);
+    else SIE_CUDA(cudaMemsetAsync(y, 0, n * sizeof(zd), c->stream));
+    if (parts & 2) op_far<double>(c, x, y, nrhs);
+  } else {
+    zf *xf = (zf *)c->d_xf, *yf = (zf *)c->d_yf;
+    op_d2f(c, x, xf, n);
+    if (parts & 1) op_near<float>(c, xf, yf, nrhs, false);
+    else SIE_CUDA(cudaMemsetAsync(yf, 0, n * sizeof(zf), c->stream));
+    if (parts & 2) op_far<float>(c, xf, yf, nrhs);
+    op_f2d(c, yf, y, n);
+  }
+}
+
+void apply_ilu(sie_ctx *c, const zd *r, zd *z, int nrhs, sie_prec prec) {
+  int64_t n = (int64_t)nrhs * c->ne * 2;
+  if (prec == SIE_PREC_FP64) {
+    op_ilu<double>(c, r, z, nrhs);
+  } else {
+    zf *rf = (zf *)c->d_xf, *zf_ = (zf *)c->d_yf;
+    op_d2f(c, r, rf, n);
+    op_ilu<float>(c, rf, zf_, nrhs);
+    op_f2d(c, zf_, z, n);
+  }
+}
+
+template void op_near<double>(sie_ctx *, const zd *, zd *, int, bool);
+template void op_near<float>(sie_ctx *, const zf *, zf *, int, bool);
+template void op_far<double>(sie_ctx *, const zd *, zd *, int);
+template void op_far<float>(sie_ctx *, const zf *, zf *, int);
+template void op_ilu<double>(sie_ctx *, const zd *, zd *, int);
+template void op_ilu<float>(sie_ctx *, const zf *, zf *, int);

@@ -1,0 +1,253 @@
+// Restarted flexible GMRES with right preconditioning for a block of
+// independent right-hand sides run in lockstep.  Arnoldi vectors, classical
+// Gram-Schmidt with one re-orthogonalisation, and the true residual at every
+// restart are FP64 on the device; the Hessenberg least-squares problem (Givens
+// rotations) is solved on the host.  With SIE_PREC_MIXED the inner operator
+// and preconditioner run in FP32 while the restart residual uses the FP64
+// operator, which makes the restarts an iterative refinement.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+
+#include "common.h"
+
+namespace {
+
+typedef std::complex<double> cd;
+
+// h[i][r] = sum_n conj(V_i[r][n]) w[r][n]; block (i, r)
+__global__ void k_mdot(int n, int nrhs, const zd *__restrict__ V, size_t vstride, const zd *__restrict__ w,
+                       zd *__restrict__ h) {
+  int i = blockIdx.x, r = blockIdx.y;
+  const zd *a = V + (size_t)i * vstride + (size_t)r * n;
+  const zd *b = w + (size_t)r * n;
+  zd acc;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) acc = cfma(conj(a[t]), b[t], acc);
+  __shared__ zd red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) h[(size_t)i * nrhs + r] = red[0];
+}
+
+// w[r] -= sum_{i<=j} V_i[r] h[i][r]
+__global__ void k_orth(int n, int nrhs, int j1, const zd *__restrict__ V, size_t vstride, const zd *__restrict__ h,
+                       zd *__restrict__ w) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (t >= n) return;
+  zd acc = w[(size_t)r * n + t];
+  for (int i = 0; i < j1; ++i) acc -= V[(size_t)i * vstride + (size_t)r * n + t] * h[(size_t)i * nrhs + r];
+  w[(size_t)r * n + t] = acc;
+}
+
+// out[r] = a[r] * s[r]
+__global__ void k_scale(int n, const zd *__restrict__ a, const zd *__restrict__ s, zd *__restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (t >= n) return;
+  out[(size_t)r * n + t] = a[(size_t)r * n + t] * s[r];
+}
+
+// out = a - b
+__global__ void k_sub(int64_t n, const zd *a, const zd *b, zd *out) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = a[t] - b[t];
+}
+
+// x[r] += sum_j Z_j[r] y[j][r]
+__global__ void k_xupd(int n, int nrhs, int m, const zd *__restrict__ Z, size_t zstride, const zd *__restrict__ y,
+                       zd *__restrict__ x) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (t >= n) return;
+  zd acc = x[(size_t)r * n + t];
+  for (int j = 0; j < m; ++j) acc += Z[(size_t)j * zstride + (size_t)r * n + t] * y[(size_t)j * nrhs + r];
+  x[(size_t)r * n + t] = acc;
+}
+
+struct Gm {
+  sie_ctx *c;
+  int n, R;
+  void launch_check() {
+    SIE_CHECK_LAUNCH();
+    c->launches++;
+  }
+  void norms(const zd *w, zd *d_h, std::vector<double> &out) {
+    k_mdot<<<dim3(1, R), 256, 0, c->stream>>>(n, R, w, 0, w, d_h);
+    launch_check();
+    std::vector<zd> h(R);
+    SIE_CUDA(cudaMemcpyAsync(h.data(), d_h, R * sizeof(zd), cudaMemcpyDeviceToHost, c->stream));
+    SIE_CUDA(cudaStreamSynchronize(c->stream));
+    out.resize(R);
+    for (int r = 0; r < R; ++r) out[r] = std::sqrt(std::max(0.0, h[r].re));
+  }
+};
+
+}  // namespace
+
+sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_solve_opts *o, sie_solve_stats *st) {
+  const int m = o->restart;
+  const int n = 2 * c->ne;
+  const size_t vs = (size_t)R * n;
+  sie_prec prec = o->prec == 1 ? SIE_PREC_MIXED : SIE_PREC_FP64;
+  ensure_work(c, R);
+  // Krylov storage (allocated once per capacity and kept in the context)
+  static_assert(sizeof(zd) == 16, "complex layout");
+  if (c->gm_m != m || c->gm_R != R) {
+    c->gm_V = dev_alloc(c, (size_t)(m + 1) * vs * sizeof(zd));
+    c->gm_Z = dev_alloc(c, (size_t)m * vs * sizeof(zd));
+    c->gm_b = dev_alloc(c, vs * sizeof(zd));
+    c->gm_x = dev_alloc(c, vs * sizeof(zd));
+    c->gm_w = dev_alloc(c, vs * sizeof(zd));
+    c->gm_h = dev_alloc(c, (size_t)(m + 2) * R * sizeof(zd));
+    c->gm_s = dev_alloc(c, (size_t)(m + 2) * R * sizeof(zd));
+    c->gm_m = m;
+    c->gm_R = R;
+  }
+  zd *V = (zd *)c->gm_V, *Z = (zd *)c->gm_Z, *b = (zd *)c->gm_b, *x = (zd *)c->gm_x, *w = (zd *)c->gm_w;
+  zd *d_h = (zd *)c->gm_h, *d_s = (zd *)c->gm_s;
+  Gm g{c, n, R};
+  op_permute_in(c, b_user, b, R);
+  op_permute_in(c, x_user, x, R);
+  std::vector<double> bn, rn;
+  g.norms(b, d_h, bn);
+  std::vector<int> iters(R, 0), restarts(R, 0), active(R, 1);
+  std::vector<double> relres(R, 0.0);
+  dim3 gv((n + 255) / 256, R);
+  sie_status status = SIE_OK;
+  int total = 0;
+  std::vector<cd> H((size_t)(m + 1) * m * R), gvec((size_t)(m + 1) * R), sn((size_t)m * R);
+  std::vector<double> cs((size_t)m * R);
+  for (;;) {
+    // true residual with the FP64 operator
+    apply_matvec(c, x, w, R, SIE_PREC_FP64, 3);
+    k_sub<<<std::min(152 * 16, (int)((vs + 255) / 256)), 256, 0, c->stream>>>((int64_t)vs, b, w, w);
+    g.launch_check();
+    g.norms(w, d_h, rn);
+    bool any = false;
+    for (int r = 0; r < R; ++r) {
+      relres[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+      if (!std::isfinite(relres[r])) {
+        status = SIE_EBREAKDOWN;
+        active[r] = 0;
+        continue;
+      }
+      active[r] = relres[r] > o->tol && iters[r] < o->max_iters;
+      if (active[r]) any = true;
+    }
+    if (!any || status != SIE_OK) break;
+    // V0 = r / beta (zero for finished right-hand sides)
+    std::vector<zd> sc(R);
+    for (int r = 0; r < R; ++r) sc[r] = active[r] ? zd(1.0 / rn[r], 0.0) : zd();
+    SIE_CUDA(cudaMemcpyAsync(d_s, sc.data(), R * sizeof(zd), cudaMemcpyHostToDevice, c->stream));
+    k_scale<<<gv, 256, 0, c->stream>>>(n, w, d_s, V);
+    g.launch_check();
+    std::fill(gvec.begin(), gvec.end(), cd(0.0));
+    for (int r = 0; r < R; ++r) {
+      gvec[r] = active[r] ? rn[r] : 0.0;
+      if (active[r]) restarts[r]++;
+    }
+    int jend = 0;
+    for (int j = 0; j < m; ++j) {
+      zd *Vj = V + (size_t)j * vs, *Zj = Z + (size_t)j * vs;
+      if (o->precond == 1) apply_ilu(c, Vj, Zj, R, prec);
+      else SIE_CUDA(cudaMemcpyAsync(Zj, Vj, vs * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
+      apply_matvec(c, Zj, w, R, prec, 3);
+      // classical Gram-Schmidt, twice
+      std::vector<zd> h1((size_t)(j + 1) * R), h2((size_t)(j + 1) * R);
+      for (int pass = 0; pass < 2; ++pass) {
+        k_mdot<<<dim3(j + 1, R), 256, 0, c->stream>>>(n, R, V, vs, w, d_h);
+        g.launch_check();
+        k_orth<<<gv, 256, 0, c->stream>>>(n, R, j + 1, V, vs, d_h, w);
+        g.launch_check();
+        SIE_CUDA(cudaMemcpyAsync(pass == 0 ? h1.data() : h2.data(), d_h, (size_t)(j + 1) * R * sizeof(zd),
+                                 cudaMemcpyDeviceToHost, c->stream));
+      }
+      std::vector<double> hn;
+      g.norms(w, d_h, hn);  // synchronises
+      for (int r = 0; r < R; ++r) {
+        cd *Hc = &H[((size_t)r * (m + 1)) * m];  // column-major per RHS: H[i + j (m+1)]
+        for (int i = 0; i <= j; ++i)
+          Hc[i + (size_t)j * (m + 1)] = cd(h1[(size_t)i * R + r].re + h2[(size_t)i * R + r].re,
+                                           h1[(size_t)i * R + r].im + h2[(size_t)i * R + r].im);
+        Hc[j + 1 + (size_t)j * (m + 1)] = hn[r];
+        sc[r] = (active[r] && hn[r] > 0) ? zd(1.0 / hn[r], 0.0) : zd();
+      }
+      SIE_CUDA(cudaMemcpyAsync(d_s, sc.data(), R * sizeof(zd), cudaMemcpyHostToDevice, c->stream));
+      k_scale<<<gv, 256, 0, c->stream>>>(n, w, d_s, V + (size_t)(j + 1) * vs);
+      g.launch_check();
+      // Givens rotations per RHS
+      bool all_done = true;
+      for (int r = 0; r < R; ++r) {
+        cd *Hc = &H[((size_t)r * (m + 1)) * m];
+        double *csr = &cs[(size_t)r * m];
+        cd *snr = &sn[(size_t)r * m];
+        cd *gr = &gvec[(size_t)r * (m + 1)];
+        if (!active[r]) continue;
+        for (int i = 0; i < j; ++i) {
+          cd a = Hc[i + (size_t)j * (m + 1)], bb = Hc[i + 1 + (size_t)j * (m + 1)];
+          Hc[i + (size_t)j * (m + 1)] = csr[i] * a + snr[i] * bb;
+          Hc[i + 1 + (size_t)j * (m + 1)] = -std::conj(snr[i]) * a + csr[i] * bb;
+        }
+        cd a = Hc[j + (size_t)j * (m + 1)], bb = Hc[j + 1 + (size_t)j * (m + 1)];
+        double cc;
+        cd ss;
+        if (std::abs(bb) == 0.0) { cc = 1.0; ss = 0.0; }
+        else if (std::abs(a) == 0.0) { cc = 0.0; ss = 1.0; }
+        else {
+          double t = std::sqrt(std::norm(a) + std::norm(bb));
+          cc = std::abs(a) / t;
+          ss = (a / std::abs(a)) * std::conj(bb) / t;
+        }
+        csr[j] = cc;
+        snr[j] = ss;
+        Hc[j + (size_t)j * (m + 1)] = cc * a + ss * bb;
+        Hc[j + 1 + (size_t)j * (m + 1)] = 0.0;
+        gr[j + 1] = -std::conj(ss) * gr[j];
+        gr[j] = cc * gr[j];
+        iters[r]++;
+        double est = std::abs(gr[j + 1]) / bn[r];
+        if (!std::isfinite(est)) status = SIE_EBREAKDOWN;
+        if (est > o->tol && iters[r] < o->max_iters) all_done = false;
+      }
+      total++;
+      jend = j + 1;
+      if (all_done || status != SIE_OK) break;
+    }
+    // y = H^-1 g per RHS, x += Z y
+    std::vector<zd> y((size_t)jend * R);
+    for (int r = 0; r < R; ++r) {
+      cd *Hc = &H[((size_t)r * (m + 1)) * m];
+      cd *gr = &gvec[(size_t)r * (m + 1)];
+      std::vector<cd> yy(jend);
+      for (int i = jend - 1; i >= 0; --i) {
+        cd s = gr[i];
+        for (int k = i + 1; k < jend; ++k) s -= Hc[i + (size_t)k * (m + 1)] * yy[k];
+        yy[i] = active[r] && std::abs(Hc[i + (size_t)i * (m + 1)]) > 0 ? s / Hc[i + (size_t)i * (m + 1)] : 0.0;
+      }
+      for (int i = 0; i < jend; ++i) y[(size_t)i * R + r] = zd(yy[i].real(), yy[i].imag());
+    }
+    zd *d_y = d_s;  // reuse
+    SIE_CUDA(cudaMemcpyAsync(d_y, y.data(), y.size() * sizeof(zd), cudaMemcpyHostToDevice, c->stream));
+    k_xupd<<<gv, 256, 0, c->stream>>>(n, R, jend, Z, vs, d_y, x);
+    g.launch_check();
+    if (status != SIE_OK) break;
+  }
+  op_permute_out(c, x, x_user, R);
+  SIE_CUDA(cudaStreamSynchronize(c->stream));
+  bool conv = true;
+  for (int r = 0; r < R; ++r) {
+    st[r].iters = iters[r];
+    st[r].restarts = restarts[r];
+    st[r].rel_residual = relres[r];
+    st[r].converged = relres[r] <= o->tol ? 1 : 0;
+    if (!st[r].converged) conv = false;
+  }
+  (void)total;
+  if (status != SIE_OK) return status;
+  return conv ? SIE_OK : SIE_ENOTCONV;
+}

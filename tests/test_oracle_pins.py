@@ -136,7 +136,7 @@ def small_sphere_ops():
 
 def _regular_edge_pairs(m):
     """Edge pairs none of whose four triangle pairs takes the singular path."""
-    sing = fill.singular_pairs(m, np.arange(m.nt))
+    sing = fill.singular_pairs(m, np.arange(m.nt))   # all rows
     e_t = np.stack([m.tp, m.tm], 1)
     out = np.ones((m.ne, m.ne), bool)
     for a in range(2):
