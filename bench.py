@@ -1,0 +1,294 @@
+"""Benchmark: time-to-RCS at a 1e-4 relative residual and MLFMM matvec GB/s,
+chosen form (mixed precision, ILU(0)-preconditioned FGMRES) vs plain FP64 form.
+
+Workload: two-layer coated dielectric sphere (core radius 1.0 lambda0, eps_r 4;
+shell radius 1.5 lambda0, eps_r 2.56) in free space, geodesic meshes of
+frequency 30 (outer) and 20 (inner), 78 000 unknowns, 5-level MLFMM, one
+x-polarised plane wave along -z, bistatic RCS at 361 angles.  Synthetic
+geometry (the paper's meshes are not published).
+
+One step = plane-wave excitation + FGMRES(50) with ILU(0) to 1e-4 + bistatic
+RCS.  Under torchrun each rank solves its own incidence angle (independent
+replicas, weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-RCS at 1e-4 residual & MLFMM matvec GB/s: chosen vs plain FP64 form"
+WORKLOAD = "coated_c2"
+LEVELS = 5
+DIGITS = 3.0
+TOL = 1e-4
+RESTART = 50
+FALLBACK_HBM_GBS = 6800.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 7 for i in range(4) if "Active" in r[3 + i]
+                          and "Not" not in r[3 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- CPU oracle timing
+def oracle_sample(mesh, rng_seed=0, nrows=4):
+    """Time the oracle on a bounded sample of the workload and extrapolate its
+    time-to-RCS: dense rows of the JMCFIE matrix (all media), a dense LU of a
+    smaller complex system scaled by N^3, and a few far-field angles."""
+    from oracle import farfield, fill
+    from oracle.rwg import Mesh
+    t0 = time.perf_counter()
+    m = Mesh(**mesh)
+    t_mesh = time.perf_counter() - t0
+    rows = np.random.default_rng(rng_seed).choice(m.ne, nrows, replace=False)
+    t0 = time.perf_counter()
+    fill.assemble(m, rows=rows)
+    t_rows = time.perf_counter() - t0
+    n_lu = 2000
+    A = np.random.default_rng(1).standard_normal((n_lu, n_lu)) + 1j * np.eye(n_lu) * n_lu
+    t0 = time.perf_counter()
+    np.linalg.solve(A, np.ones(n_lu, complex))
+    t_lu = time.perf_counter() - t0
+    N = 2 * m.ne
+    x = np.zeros((1, N), complex)
+    obs = np.array([[0.3, 0.0], [1.0, 0.0]])
+    t0 = time.perf_counter()
+    farfield.rcs(m, x, obs)
+    t_ff = time.perf_counter() - t0
+    est = t_mesh + t_rows / nrows * m.ne + t_lu * (N / n_lu) ** 3 + t_ff / len(obs) * 361
+    sample = (f"oracle on host: {nrows} dense JMCFIE edge rows of {m.ne} ({t_rows:.1f} s), dense LU n={n_lu} "
+              f"({t_lu:.2f} s, scaled by N^3 to N={N}), far field at {len(obs)} of 361 angles; extrapolated")
+    return est, sample, t_mesh + t_rows + t_lu + t_ff
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_1704_06862_gb300 import geometry as geo
+    mesh = geo.workload(WORKLOAD)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        est, sample, spent = oracle_sample(mesh, rng_seed=i, nrows=2)
+        if i >= args.warmup:
+            vals.append(est)
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "unknowns": None, "levels": LEVELS},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "sample": sample, "value": v, "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as g
+    g.build()
+    import paper_1704_06862_gb300 as sie
+    from paper_1704_06862_gb300 import geometry as geo
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    mesh = geo.workload(WORKLOAD)
+    t0 = time.perf_counter()
+    s = sie.Solver(mesh, levels=LEVELS, digits=DIGITS, stream=stream)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    ne = s.ne
+    obs = geo.bistatic_angles(361)
+    # each rank its own incidence (replicas)
+    theta_i = 0.0 + 0.05 * rank
+    inc = np.array([[theta_i, 0.0, 0.0, 1.0]])
+    b_dev = s.vec(1)
+    x = s.vec(1)
+    sie.sie_plane_wave_rhs(s.ctx, inc, b_dev)
+
+    def solve(prec, e2e):
+        if e2e:                       # host incidence -> device excitation
+            sie.sie_plane_wave_rhs(s.ctx, inc, b_dev)
+        x.zero_()
+        st = sie.gmres_solve(s.ctx, b_dev, x, 1, restart=RESTART, max_iters=3000, tol=TOL, prec=prec, precond=1)
+        rcs = sie.rcs_farfield(s.ctx, x, 1, obs)  # device -> host
+        return st[0], rcs
+
+    def timed(prec, steps, e2e):
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = None
+        for _ in range(steps):
+            out = solve(prec, e2e)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, out
+
+    for _ in range(args.warmup):
+        solve(sie.SIE_PREC_MIXED, False)
+    launches0 = sie.sie_query(s.ctx, 8)
+    clk = Clocks(local)
+    clk.start()
+    ms, (st, rcs) = timed(sie.SIE_PREC_MIXED, args.steps, False)
+    clocks = clk.stop()
+    launches = (sie.sie_query(s.ctx, 8) - launches0) // args.steps
+    ms_e2e, _ = timed(sie.SIE_PREC_MIXED, 1, True)
+    plain = None
+    if not args.no_plain:
+        ms64, (st64, rcs64) = timed(sie.SIE_PREC_FP64, 1, False)
+        db = 10 * np.log10(np.maximum(rcs[:, :, 0], 1e-30)) - 10 * np.log10(np.maximum(rcs64[:, :, 0], 1e-30))
+        plain = {"ms_per_solve": ms64, "iters": st64["iters"], "rel_residual": st64["rel_residual"],
+                 "speedup_chosen_vs_plain": ms64 / ms, "rcs_max_abs_db_diff_vs_plain": float(np.max(np.abs(db)))}
+    # Mie check of the chosen form
+    mie_db = None
+    try:
+        from oracle import mie
+        ref = mie.coated_bistatic(1.0, 1.5, 4.0, 2.56, obs[:, 0]) if theta_i == 0.0 else None
+        if ref is not None:
+            d = 10 * np.log10(rcs[0, :, 0]) - 10 * np.log10(ref)
+            mie_db = {"mean_abs_db": float(np.mean(np.abs(d))), "max_abs_db": float(np.max(np.abs(d)))}
+    except Exception:
+        pass
+
+    # stage timings (CUDA events on the library stream) and the roofline of the dominant kernel
+    stages = {}
+    for name, stg in (("near_spmv", 0), ("far_mlfmm", 1), ("ilu_sweeps", 2), ("matvec", 3)):
+        stages[name] = {"fp32_ms": sie.sie_stage_timing(s.ctx, stg, 1, sie.SIE_PREC_MIXED, 20),
+                        "fp64_ms": sie.sie_stage_timing(s.ctx, stg, 1, sie.SIE_PREC_FP64, 10)}
+    nnzb = sie.sie_query(s.ctx, 1)
+    near_bytes_fp32 = nnzb * (4 * 8 + 4) + (ne + 1) * 4 + 2 * (2 * ne * 8)
+    near_bytes_fp64 = nnzb * (4 * 16 + 4) + (ne + 1) * 4 + 2 * (2 * ne * 16)
+    peak, peak_src = measured_peaks()
+    ach = near_bytes_fp32 / (stages["near_spmv"]["fp32_ms"] * 1e-3) / 1e9
+    roofline = {"kernel": "k_near_spmv<float> (near-field 2x2 block-sparse product)", "bound": "hbm",
+                "achieved": ach, "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "algorithmic_bytes_per_launch": near_bytes_fp32,
+                "fp64_achieved": near_bytes_fp64 / (stages["near_spmv"]["fp64_ms"] * 1e-3) / 1e9}
+    pat_bytes = sie.sie_query(s.ctx, 6)
+    mv_bytes32 = near_bytes_fp32 + pat_bytes // 2
+    matvec = {"fp32_ms": stages["matvec"]["fp32_ms"], "fp64_ms": stages["matvec"]["fp64_ms"],
+              "fp32_algorithmic_GBs": mv_bytes32 / (stages["matvec"]["fp32_ms"] * 1e-3) / 1e9,
+              "fp64_algorithmic_GBs": (near_bytes_fp64 + pat_bytes) / (stages["matvec"]["fp64_ms"] * 1e-3) / 1e9}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        est, sample, spent = oracle_sample(mesh)
+        cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
+               "sample_wall_s": spent}
+    line = {
+        "metric": METRIC, "value": ms / 1e3 * 1.0, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 (FP32 complex operator) + c128 Arnoldi", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "unknowns": 2 * ne, "levels": LEVELS, "digits": DIGITS, "tol": TOL,
+                   "restart": RESTART, "nrhs_per_gpu": 1, "parallelism": f"replicas{ws}",
+                   "l2": f"operator data {(near_bytes_fp32 + pat_bytes // 2) / 1e6:.0f} MB > 129 MB L2 (no flush)"},
+        "iters": st["iters"], "rel_residual": st["rel_residual"], "setup_s": t_setup,
+        "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
+                "d2h_bytes_per_step": int(rcs.nbytes)},
+        "plain_fp64": plain, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -173,6 +173,16 @@ sie_status rcs_farfield(sie_ctx *ctx, const void *x_dev, int64_t nrhs, const dou
  * complex128.  Synchronous. */
 sie_status sie_near_export(sie_ctx *ctx, int32_t *rows, int32_t *cols, double *vals, int64_t *nnzb);
 
+/* Device time of one stage of the hot path, for roofline reports: launches
+ * the stage `reps` times back to back on the context's stream on internal
+ * work vectors and returns the mean milliseconds per launch, measured with
+ * CUDA events on that stream.  stage: 0 near-field block-sparse product,
+ * 1 MLFMM far field (all media, all levels), 2 ILU(0) forward + backward
+ * sweeps, 3 whole product (near + far).  prec as for mlfmm_matvec.
+ * Synchronous.  Not a numerical operation of the method; the paper has no
+ * counterpart. */
+sie_status sie_stage_timing(sie_ctx *ctx, int32_t stage, int64_t nrhs, int32_t prec, int32_t reps, double *ms_out);
+
 /* Integer facts about the context for tests and reports: keys
  *   0 n_rwg, 1 near blocks, 2 levels, 3 regions, 4 leaf boxes (all media),
  *   5 bytes of the FP64 near field, 6 bytes of FP64 leaf patterns,

@@ -15,11 +15,15 @@ n_l = s_l n of B_l and currents J_l = s_l J, M_l = s_l M (Eqs. 12-13):
   (K is the principal value; its jump is the explicit 1/2 terms).
 
 JMCFIE (Eq. 14 for one interface, Eq. 16 for several):
-  J-row = sum_l s_l(m) [ eta_l^-1 T-EFIE_l + N-MFIE_l ]
-  M-row = sum_l s_l(m) [ eta_l    T-MFIE_l - N-EFIE_l ]
-tested with RWG t_m = b_m (Galerkin, Eqs. 13-14 of the discretisation
-section).  Unknowns and rows are scaled so that every block is dimensionless:
-unknown pair (eta_0 c_n, v_n), J-row multiplied by eta_0.  With
+  J-row = sum_l s_l(m) [ eta_l^-1 T-EFIE_l - N-MFIE_l ]
+  M-row = sum_l s_l(m) [ N-EFIE_l - eta_l T-MFIE_l ]
+The N-parts carry the (-1)^l of Eq. 14 with l = 1 the host (s_l = -(-1)^l);
+the T-parts are weighted by s_l so that the operators of the two media add
+across an interface (PMCHWT-type); with these signs every eigenvalue of the
+discrete operator lies in the right half-plane (reading of the garbled signs,
+the design doc).  Tested with RWG t_m = b_m (Galerkin, Eqs. 13-14 of the
+discretisation section).  Unknowns and rows are scaled so that every block is
+dimensionless: unknown pair (eta_0 c_n, v_n), J-row multiplied by eta_0.  With
 eta~_l = eta_l / eta_0 and the Galerkin matrices
 
   L_l[m,n]  = <t_m, L_l b_n>    (Eq. 23: jk int int [t.b - k^-2 div t div' b] G)
@@ -30,14 +34,14 @@ eta~_l = eta_l / eta_0 and the Galerkin matrices
 
 the 2x2 block of Z for (m, n) is the sum over media l containing both:
 
-  JJ += s_m s_n L_l + s_n NK_l - 1/2 s_m s_n G
-  JM += (s_m s_n K_l - s_n NL_l) / eta~_l + 1/2 s_m Gx / eta~_l
-  MJ += (s_m s_n K_l + s_n NL_l) eta~_l   + 1/2 s_m Gx eta~_l
-  MM += -s_m s_n L_l + s_n NK_l - 1/2 s_m s_n G
+  JJ += s_m s_n L_l - s_n NK_l + 1/2 s_m s_n G
+  JM += (s_m s_n K_l + s_n NL_l) / eta~_l + 1/2 s_m Gx / eta~_l
+  MJ += -(s_m s_n K_l + s_n NL_l) eta~_l - 1/2 s_m Gx eta~_l
+  MM += s_m s_n L_l - s_n NK_l + 1/2 s_m s_n G
 
 Excitation (Eqs. 20-21; only the host medium 0 holds the source):
-  b_J[m] = s_0(m)/eta~_0 <t_m, E> - <t_m, n_m x (eta_0 H)>
-  b_M[m] = -s_0(m) eta~_0 <t_m, eta_0 H> + <t_m, n_m x E>
+  b_J[m] = s_0(m)/eta~_0 <t_m, E> + <t_m, n_m x (eta_0 H)>
+  b_M[m] = s_0(m) eta~_0 <t_m, eta_0 H> - <t_m, n_m x E>
 
 Quadrature: Radon 7-point rule on both triangles for regular pairs; for
 pairs with centroid distance < hmax_p + hmax_q a 4x4 collapsed-Gauss outer
@@ -246,10 +250,10 @@ def assemble(mesh: Mesh, freq_hz=None, rows=None, chunk=24, outer_n=4):
         sn = s[None, :]
         ss = sm * sn
         eta = op["eta"]
-        Z[0::2, 0::2] += ss * op["L"] + sn * op["NK"] - 0.5 * ss * op["G"]
-        Z[0::2, 1::2] += (ss * op["K"] - sn * op["NL"]) / eta + 0.5 * sm * op["Gx"] / eta
-        Z[1::2, 0::2] += (ss * op["K"] + sn * op["NL"]) * eta + 0.5 * sm * op["Gx"] * eta
-        Z[1::2, 1::2] += -ss * op["L"] + sn * op["NK"] - 0.5 * ss * op["G"]
+        Z[0::2, 0::2] += ss * op["L"] - sn * op["NK"] + 0.5 * ss * op["G"]
+        Z[0::2, 1::2] += (ss * op["K"] + sn * op["NL"]) / eta + 0.5 * sm * op["Gx"] / eta
+        Z[1::2, 0::2] += -(ss * op["K"] + sn * op["NL"]) * eta - 0.5 * sm * op["Gx"] * eta
+        Z[1::2, 1::2] += ss * op["L"] - sn * op["NK"] + 0.5 * ss * op["G"]
     return Z
 
 
@@ -293,8 +297,8 @@ def rhs(mesh: Mesh, inc, freq_hz=None):
         m = d["e"]
         ok = m >= 0
         s = s_edge[np.maximum(m, 0)]
-        bJ = s * fE / eta0 - fnH
-        bM = -s * eta0 * fH + fnE
+        bJ = s * fE / eta0 + fnH
+        bM = s * eta0 * fH - fnE
         np.add.at(out[ri], 2 * m[ok], bJ[ok])
         np.add.at(out[ri], 2 * m[ok] + 1, bM[ok])
     return out

@@ -24,7 +24,7 @@ STATUS = {0: "SIE_OK", 1: "SIE_EINVAL", 2: "SIE_ENOMEM", 3: "SIE_ECUDA", 4: "SIE
 
 EXPORTED = ["sie_create", "sie_destroy", "sie_last_error", "sie_build_mesh", "mlfmm_setup", "sie_fill_nearfield",
             "mlfmm_matvec", "sie_matvec_parts", "ilu_apply", "sie_plane_wave_rhs", "gmres_solve", "rcs_farfield",
-            "sie_near_export", "sie_query"]
+            "sie_near_export", "sie_stage_timing", "sie_query"]
 
 
 class SieError(RuntimeError):
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         "rcs_farfield": ([P, P, I64, P, I64, P], I32),
         "sie_near_export": ([P, P, P, P, ctypes.POINTER(I64)], I32),
         "sie_query": ([P, I32, ctypes.POINTER(I64)], I32),
+        "sie_stage_timing": ([P, I32, I64, I32, I32, ctypes.POINTER(D)], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -193,6 +194,12 @@ def sie_near_export(ctx):
     vals = np.zeros((n.value, 4, 2), np.float64)
     _check(ctx, L.sie_near_export(ctx, _ptr(rows), _ptr(cols), _ptr(vals), ctypes.byref(n)))
     return rows, cols, vals[..., 0] + 1j * vals[..., 1]
+
+
+def sie_stage_timing(ctx, stage, nrhs=1, prec=SIE_PREC_FP64, reps=10):
+    ms = ctypes.c_double()
+    _check(ctx, load_library().sie_stage_timing(ctx, int(stage), int(nrhs), int(prec), int(reps), ctypes.byref(ms)))
+    return ms.value
 
 
 def sie_query(ctx, key):

@@ -233,10 +233,12 @@ __global__ void k_near_fill(const int *pairs, int64_t npairs, const double *tri,
       }
       if (a >= hi || col[a] != nn) continue;  // far pair: carried by the MLFMM
       zd Lij = L[i][j] - ((2.0 * P.c[i]) * (2.0 * Q.c[j])) * (joverk * SG);
-      zd jj = ss * Lij + sn * NK[i][j];
-      zd jm = (ss * K[i][j] - sn * NL[i][j]) * ieta;
-      zd mj = (ss * K[i][j] + sn * NL[i][j]) * eta;
-      zd mm = -ss * Lij + sn * NK[i][j];
+      // J-row = sum_l s_l [T-EFIE_l / eta_l - N-MFIE_l], M-row = sum_l s_l [N-EFIE_l - eta_l T-MFIE_l]
+      zd jj = ss * Lij - sn * NK[i][j];
+      zd kn = ss * K[i][j] + sn * NL[i][j];
+      zd jm = kn * ieta;
+      zd mj = -(kn * eta);
+      zd mm = jj;
       double *o = near + 8 * (size_t)a;
       atomicAdd(o + 0, jj.re); atomicAdd(o + 1, jj.im);
       atomicAdd(o + 2, jm.re); atomicAdd(o + 3, jm.im);
@@ -246,7 +248,7 @@ __global__ void k_near_fill(const int *pairs, int64_t npairs, const double *tri,
   }
 }
 
-// Identity (Gram) terms of both media of each triangle: -1/2 <t, b> per
+// Identity (Gram) terms of both media of each triangle: +1/2 <t, b> per
 // side on the J and M rows, +-1/2 <t, n x b> weighted by eta~ per side.
 __global__ void k_identity(int nt, const double *tri, const int *te, const double *tsg, const int *treg,
                            const zd *etas, const int *row_ptr, const int *col, double *near, int *err) {
@@ -269,7 +271,7 @@ __global__ void k_identity(int nt, const double *tri, const int *te, const doubl
   zd ep = etas[treg[2 * t]], em = etas[treg[2 * t + 1]];
   auto inv = [](zd z) { return zd(z.re, -z.im) * (1.0 / (z.re * z.re + z.im * z.im)); };
   zd cjm = 0.5 * (inv(ep) - inv(em));
-  zd cmj = 0.5 * (ep - em);
+  zd cmj = -0.5 * (ep - em);
   for (int i = 0; i < 3; ++i) {
     int m = P.e[i];
     if (m < 0) continue;
@@ -287,10 +289,10 @@ __global__ void k_identity(int nt, const double *tri, const int *te, const doubl
       }
       double *o = near + 8 * (size_t)a;
       zd jm = Gx[i][j] * cjm, mj = Gx[i][j] * cmj;
-      atomicAdd(o + 0, -Gm[i][j]);
+      atomicAdd(o + 0, Gm[i][j]);
       atomicAdd(o + 2, jm.re); atomicAdd(o + 3, jm.im);
       atomicAdd(o + 4, mj.re); atomicAdd(o + 5, mj.im);
-      atomicAdd(o + 6, -Gm[i][j]);
+      atomicAdd(o + 6, Gm[i][j]);
     }
   }
 }
@@ -382,8 +384,8 @@ __global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris,
       fnE += dot(f, cross(T.n, e)) * w;
     }
   }
-  out[0] = (s0 * fE) * ie0 - fnH;
-  out[1] = -(s0 * (eta0 * fH)) + fnE;
+  out[0] = (s0 * fE) * ie0 + fnH;
+  out[1] = s0 * (eta0 * fH) - fnE;
 }
 
 // Far amplitudes (Eqs. 27-29): one block per (observation, rhs).

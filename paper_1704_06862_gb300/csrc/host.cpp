@@ -1040,6 +1040,58 @@ extern "C" sie_status sie_near_export(sie_ctx *c, int32_t *rows, int32_t *cols, 
   });
 }
 
+extern "C" sie_status sie_stage_timing(sie_ctx *c, int32_t stage, int64_t nrhs, int32_t prec, int32_t reps,
+                                       double *ms) {
+  return guard(c, [&] {
+    SIE_REQUIRE(c->have_fill, SIE_ESTATE, "sie_stage_timing: call sie_fill_nearfield first");
+    SIE_REQUIRE(ms && stage >= 0 && stage <= 3 && nrhs >= 1 && nrhs <= 4096 && reps >= 1, SIE_EINVAL,
+                "sie_stage_timing: bad arguments");
+    SIE_REQUIRE(stage != 2 || c->ilu.ready, SIE_ESTATE, "sie_stage_timing: no ILU factors");
+    ensure_work(c, nrhs);
+    size_t n = (size_t)nrhs * c->ne * 2;
+    SIE_CUDA(cudaMemsetAsync(c->d_xi, 0, n * sizeof(zd), c->stream));
+    SIE_CUDA(cudaMemsetAsync(c->d_xf, 0, n * sizeof(zf), c->stream));
+    cudaEvent_t e0, e1;
+    SIE_CUDA(cudaEventCreate(&e0));
+    SIE_CUDA(cudaEventCreate(&e1));
+    auto run = [&]() {
+      bool f64 = prec == SIE_PREC_FP64;
+      switch (stage) {
+        case 0:
+          if (f64) op_near<double>(c, (const zd *)c->d_xi, (zd *)c->d_yi, (int)nrhs, false);
+          else op_near<float>(c, (const zf *)c->d_xf, (zf *)c->d_yf, (int)nrhs, false);
+          break;
+        case 1:
+          if (f64) op_far<double>(c, (const zd *)c->d_xi, (zd *)c->d_yi, (int)nrhs);
+          else op_far<float>(c, (const zf *)c->d_xf, (zf *)c->d_yf, (int)nrhs);
+          break;
+        case 2:
+          if (f64) op_ilu<double>(c, (const zd *)c->d_xi, (zd *)c->d_yi, (int)nrhs);
+          else op_ilu<float>(c, (const zf *)c->d_xf, (zf *)c->d_yf, (int)nrhs);
+          break;
+        default:
+          if (f64) {
+            op_near<double>(c, (const zd *)c->d_xi, (zd *)c->d_yi, (int)nrhs, false);
+            op_far<double>(c, (const zd *)c->d_xi, (zd *)c->d_yi, (int)nrhs);
+          } else {
+            op_near<float>(c, (const zf *)c->d_xf, (zf *)c->d_yf, (int)nrhs, false);
+            op_far<float>(c, (const zf *)c->d_xf, (zf *)c->d_yf, (int)nrhs);
+          }
+      }
+    };
+    run();  // warm-up
+    SIE_CUDA(cudaEventRecord(e0, c->stream));
+    for (int i = 0; i < reps; ++i) run();
+    SIE_CUDA(cudaEventRecord(e1, c->stream));
+    SIE_CUDA(cudaEventSynchronize(e1));
+    float t = 0;
+    SIE_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = (double)t / reps;
+  });
+}
+
 extern "C" sie_status sie_query(const sie_ctx *c, int32_t key, int64_t *v) {
   if (!c || !v) return SIE_EINVAL;
   switch (key) {

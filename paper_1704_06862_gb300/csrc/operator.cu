@@ -255,7 +255,7 @@ __global__ void k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr,
 
 // Leaf receive with the JMCFIE weights of medium l (weights and constants
 // folded into the translators):
-//   J-row: s_i R^t.F1 + R^n.F2,   M-row: s_i R^t.F3 + R^n.F4
+//   J-row: s_i R^t.F1 - R^n.F2,   M-row: -(s_i R^t.F3 + R^n.F4)
 //   F1 = I^J - khat x I^M / eta,  F2 = (F1_phi, -F1_theta)
 //   F3 = -eta khat x I^J - I^M,   F4 = (-F3_phi, F3_theta)
 // R^t_i(k) = V_i(-k) read at the antipodal sample (theta comp as is, phi negated).
@@ -284,8 +284,8 @@ __global__ void k_disaggregate(int nb, int K, int L, int ne, int nrhs, const int
       // khat x (a_t, a_p) = (-a_p, a_t)
       cx<T> f1t = iJt + iMp * ieta, f1p = iJp - iMt * ieta;
       cx<T> f3t = eta * iJp - iMt, f3p = -(eta * iJt) - iMp;
-      yj += s * (rtt * f1t + rtp * f1p) + (rnt * f1p - rnp * f1t);
-      ym += s * (rtt * f3t + rtp * f3p) + (rnp * f3t - rnt * f3p);
+      yj += s * (rtt * f1t + rtp * f1p) - (rnt * f1p - rnp * f1t);
+      ym -= s * (rtt * f3t + rtp * f3p) + (rnp * f3t - rnt * f3p);
     }
     yj = warp_sum(yj);
     ym = warp_sum(ym);

@@ -1,0 +1,72 @@
+"""Write the stored expected values used by the GPU parity tests.
+
+Every value here is computed by the CPU oracle (``oracle/``) alone, on seeded
+synthetic inputs from ``paper_1704_06862_gb300.geometry``; nothing comes from
+the CUDA path.  Run:  python tests/golden/make_golden.py [name ...]
+
+Cases
+  sphere_c1    eps_r = 4 sphere, radius 0.5 lambda0, geodesic nu = 8
+               (1280 triangles, 3840 unknowns); 3-level tree (leaf 0.25).
+  sphere_r1    eps_r = 4 sphere, radius 1.0 lambda0, nu = 12 (8640 unknowns);
+               4-level tree (leaf 0.25): exercises interpolation/anterpolation.
+  sphere_lossy eps_r = 6 - 0.6j sphere (complex wavenumber), radius 0.5, nu = 8.
+  coated_r075  coated sphere, core 0.5 (eps 4), shell 0.75 (eps 2.56), nu 12/8
+               (12480 unknowns, three media); 4-level tree (leaf 0.1875).
+Stored: seeded x (2 columns), y = Z x, y_near = Z_near x (touching-box
+pattern), plane-wave excitation b, dense-LU solution, bistatic RCS of that
+solution at 361 angles, and the Mie series at the same angles.
+"""
+from __future__ import annotations
+
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from paper_1704_06862_gb300 import geometry as geo  # noqa: E402
+from oracle import farfield, fill, mie, solvers, tree  # noqa: E402
+from oracle.rwg import Mesh  # noqa: E402
+
+CASES = {
+    "sphere_c1": dict(mesh=lambda: geo.homogeneous_sphere(nu=8, radius=0.5, eps_r=4.0), levels=3, radius=0.5),
+    "sphere_r1": dict(mesh=lambda: geo.homogeneous_sphere(nu=12, radius=1.0, eps_r=4.0), levels=4, radius=1.0),
+    "sphere_lossy": dict(mesh=lambda: geo.homogeneous_sphere(nu=8, radius=0.5, eps_r=6.0 - 0.6j), levels=3,
+                         radius=0.5, eps=6.0 - 0.6j),
+    "coated_r075": dict(mesh=lambda: geo.coated_sphere(12, 8, 0.75, 0.5, 2.56, 4.0), levels=4, coated=(0.5, 0.75)),
+}
+
+
+def make(name):
+    spec = CASES[name]
+    t0 = time.time()
+    m = Mesh(**spec["mesh"]())
+    Z = fill.assemble(m)
+    x = geo.random_coefficients(2 * m.ne, 2, seed=1234)
+    y = (Z @ x.T).T
+    mask = tree.near_mask(m, spec["levels"])
+    Zn = Z * np.repeat(np.repeat(mask, 2, 0), 2, 1)
+    y_near = (Zn @ x.T).T
+    inc = np.array([[0.0, 0.0, 0.0, 1.0]])
+    b = fill.rhs(m, inc)
+    xs = solvers.lu_solve(Z, b[0])
+    obs = geo.bistatic_angles(361)
+    rcs = farfield.rcs(m, xs[None], obs)[0]
+    if "coated" in spec:
+        ref = mie.coated_bistatic(spec["coated"][0], spec["coated"][1], 4.0, 2.56, obs[:, 0])
+    else:
+        ref = mie.sphere_bistatic(spec["radius"], spec.get("eps", 4.0), obs[:, 0])
+    np.savez_compressed(os.path.join(HERE, f"{name}.npz"), x=x, y=y, y_near=y_near, b=b, xs=xs, obs=obs,
+                        rcs=rcs, mie=ref, levels=spec["levels"], ne=m.ne)
+    err = np.abs(10 * np.log10(rcs[:, 0]) - 10 * np.log10(ref))
+    print(f"{name}: ne={m.ne} fill+solve {time.time() - t0:.0f}s  RCS vs Mie mean {err.mean():.3f} dB, "
+          f"max {err.max():.3f} dB")
+
+
+if __name__ == "__main__":
+    for n in (sys.argv[1:] or list(CASES)):
+        make(n)

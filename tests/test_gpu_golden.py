@@ -1,0 +1,98 @@
+"""MLFMM accuracy and solution parity on stored oracle results.
+
+The expected values in tests/golden/*.npz were written by
+tests/golden/make_golden.py, which calls only the CPU oracle (dense JMCFIE
+fill, dense product, dense LU, far field, Mie series).
+
+Tolerances:
+* near part of the product: same integrals on both sides -> 1e-12.
+* whole product, FP64 MLFMM: relative L2 1e-3 (the far-field accuracy target).
+* FP32 (mixed) product vs FP64 product: 1e-4.
+* currents solved to 1e-6 vs dense LU: 1e-3 relative L2.
+* RCS of the solved currents vs the oracle RCS of the LU currents: 0.2 dB on
+  angles within 30 dB of the peak.
+"""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1704_06862_gb300 as sie  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_spec = importlib.util.spec_from_file_location("make_golden", os.path.join(HERE, "golden", "make_golden.py"))
+make_golden = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(make_golden)
+
+NAMES = [n for n in make_golden.CASES if os.path.exists(os.path.join(HERE, "golden", f"{n}.npz"))]
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+@pytest.fixture(scope="module", params=NAMES)
+def case(request):
+    name = request.param
+    d = dict(np.load(os.path.join(HERE, "golden", f"{name}.npz")))
+    mesh = make_golden.CASES[name]["mesh"]()
+    s = sie.Solver(mesh, levels=int(d["levels"]), digits=3.0)
+    assert s.ne == int(d["ne"])
+    yield name, s, d
+    s.close()
+
+
+def _dev(a, ne):
+    return torch.from_numpy(np.ascontiguousarray(a).reshape(-1, ne, 2)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().reshape(t.shape[0], -1)
+
+
+def test_product_near_far_and_mixed(case):
+    name, s, d = case
+    x = _dev(d["x"], s.ne)
+    y = torch.zeros_like(x)
+    sie.sie_matvec_parts(s.ctx, x, y, 2, sie.SIE_PREC_FP64, parts=1)
+    assert rel(_host(y), d["y_near"]) < 1e-12
+    sie.mlfmm_matvec(s.ctx, x, y, 2, sie.SIE_PREC_FP64)
+    y64 = _host(y)
+    err = rel(y64, d["y"])
+    far_err = rel(y64 - d["y_near"], d["y"] - d["y_near"])
+    print(f"{name}: MLFMM product rel L2 {err:.2e}, far part {far_err:.2e}")
+    assert err < 1e-3
+    sie.mlfmm_matvec(s.ctx, x, y, 2, sie.SIE_PREC_MIXED)
+    assert rel(_host(y), y64) < 1e-4
+
+
+@pytest.mark.parametrize("prec", [sie.SIE_PREC_FP64, sie.SIE_PREC_MIXED])
+def test_solution_and_rcs(case, prec):
+    name, s, d = case
+    b = torch.zeros((1, s.ne, 2), dtype=torch.complex128, device="cuda")
+    sie.sie_plane_wave_rhs(s.ctx, [[0.0, 0.0, 0.0, 1.0]], b)
+    assert rel(_host(b), d["b"]) < 1e-12
+    x = torch.zeros_like(b)
+    st = sie.gmres_solve(s.ctx, b, x, 1, restart=50, max_iters=1000, tol=1e-6, prec=prec, precond=1)
+    assert st[0]["converged"]
+    xs = _host(x)[0]
+    err = rel(xs, d["xs"])
+    rcs = sie.rcs_farfield(s.ctx, x, 1, d["obs"])[0]
+    ok = d["rcs"][:, 0] > d["rcs"][:, 0].max() * 1e-3
+    db = np.abs(10 * np.log10(rcs[ok, 0]) - 10 * np.log10(d["rcs"][ok, 0]))
+    mie_db = np.abs(10 * np.log10(rcs[:, 0]) - 10 * np.log10(d["mie"]))
+    print(f"{name} prec={prec}: iters {st[0]['iters']}, currents rel err {err:.2e}, RCS vs oracle max "
+          f"{db.max():.3f} dB, vs Mie mean {mie_db.mean():.3f} dB")
+    assert err < 1e-3
+    assert db.max() < 0.2
