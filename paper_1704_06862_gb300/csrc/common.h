@@ -76,7 +76,10 @@ struct LevelHost {
   // device tables
   double *d_dirs = nullptr;     // [K][9]: khat, theta_hat, phi_hat
   void *d_T64 = nullptr, *d_T32 = nullptr;       // translators [nslot][K], weights and constants folded
-  void *d_A64 = nullptr, *d_A32 = nullptr;       // interpolation to this level from lev+1: [2K][2Kc] real
+  void *d_tp64 = nullptr, *d_tp32 = nullptr;     // [K][6]: theta_hat, phi_hat
+  // separable interpolation to this level from lev+1 (real): Phi [Np][Nc], Theta+- [L+1][Lc+1]
+  void *d_Phi64 = nullptr, *d_Phi32 = nullptr, *d_Thp64 = nullptr, *d_Thp32 = nullptr;
+  void *d_Thm64 = nullptr, *d_Thm32 = nullptr;
   void *d_up64 = nullptr, *d_up32 = nullptr;     // [8][K] shift, child -> this (parent) level
   void *d_dn64 = nullptr, *d_dn32 = nullptr;     // [8][K] shift, this level -> child
   int *d_il_ptr = nullptr, *d_il_src = nullptr, *d_il_slot = nullptr;
@@ -167,8 +170,6 @@ struct sie_ctx {
   int64_t nrhs_cap = 0;
   void *d_xi = nullptr, *d_yi = nullptr;          // internal-order FP64 vectors [R][ne][2]
   void *d_xf = nullptr, *d_yf = nullptr;          // FP32 copies
-  void *d_gemm = nullptr;                         // interpolation scratch
-  size_t gemm_bytes = 0;
   void *d_stage = nullptr;                        // small host-to-device staging area
   size_t stage_bytes = 0;
   // Krylov storage of the last solve shape (restart m, nrhs R)

@@ -40,21 +40,14 @@ void ensure_work(sie_ctx *c, int64_t nrhs) {
   c->d_yi = dev_alloc(c, n * sizeof(zd));
   c->d_xf = dev_alloc(c, n * sizeof(zf));
   c->d_yf = dev_alloc(c, n * sizeof(zf));
-  size_t gemm = 0;
   for (auto &R : c->reg) {
     for (int l = 2; l < (int)R.lev.size(); ++l) {
       LevelHost &L = R.lev[l];
       size_t sz = (size_t)L.nbox * 4 * L.K * nrhs * sizeof(zd);
       L.d_S = dev_alloc(c, sz);
       L.d_I = dev_alloc(c, sz);
-      if (l >= 3) {  // scratch for interpolation into level l-1 and anterpolation from it
-        size_t g = (size_t)L.nbox * 4 * R.lev[l - 1].K * nrhs * sizeof(zd);
-        gemm = std::max(gemm, g);
-      }
     }
   }
-  c->d_gemm = dev_alloc(c, gemm);
-  c->gemm_bytes = gemm;
   c->nrhs_cap = nrhs;
 }
 
@@ -559,6 +552,17 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
       const Dirs &Dd = dirs[lv];
       int K = Dd.K, L = Dd.L;
       B.d_dirs = dev_upload(c, Dd.d);
+      {  // theta_hat, phi_hat per direction for the Cartesian <-> (theta, phi) steps
+        std::vector<double> tp(6 * (size_t)K);
+        std::vector<float> tpf(6 * (size_t)K);
+        for (int k = 0; k < K; ++k)
+          for (int q = 0; q < 6; ++q) {
+            tp[6 * k + q] = Dd.d[9 * k + 3 + q];
+            tpf[6 * k + q] = (float)Dd.d[9 * k + 3 + q];
+          }
+        B.d_tp64 = dev_upload(c, tp);
+        B.d_tp32 = dev_upload(c, tpf);
+      }
       // translators (weights and constants folded in)
       int ns = (int)B.slot_code.size();
       std::vector<cd> T((size_t)std::max(ns, 1) * K);
@@ -615,33 +619,48 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
         }
         B.d_up32 = dev_upload(c, uf);
         B.d_dn32 = dev_upload(c, df);
-        // exact interpolation from level lv+1 (spherical-harmonic projection, degree L of the child)
+        // Exact separable interpolation from level lv+1, applied to Cartesian
+        // components (band-limited to degree Lc on the sphere):
+        //  phi:   trigonometric interpolation, Nc = 2Lc+2 uniform samples -> Np,
+        //         Phi[jp][jc] = (1 + 2 sum_{m=1..Lc} cos m(phi_p - phi_c)) / Nc;
+        //  theta: along the meridian through phi and phi+pi the function is a
+        //         trigonometric polynomial of degree Lc; its even part is a
+        //         polynomial in cos(theta) and its odd part sin(theta) times one,
+        //         both interpolated by the Lagrange basis l_i on the child's
+        //         Gauss-Legendre nodes:
+        //         h(theta_p) = sum_i l_i(x_p) [ (1+s)/2 g_i(phi) + (1-s)/2 g_i(phi+pi) ],
+        //         s = sin(theta_p) / sin(theta_i).
         const Dirs &Dc = dirs[lv + 1];
-        int Kc = Dc.K, Lc = Dc.L;
-        std::vector<double> A((size_t)2 * K * 2 * Kc);
-        std::vector<double> Pc(Lc + 1);
-        for (int p = 0; p < K; ++p) {
-          const double *dp = &Dd.d[9 * p];
-          for (int q = 0; q < Kc; ++q) {
-            const double *dq = &Dc.d[9 * q];
-            double ct = dp[0] * dq[0] + dp[1] * dq[1] + dp[2] * dq[2];
-            ct = std::max(-1.0, std::min(1.0, ct));
-            legendre_all(Lc, ct, Pc.data());
-            double s = 0;
-            for (int n = 0; n <= Lc; ++n) s += (2.0 * n + 1.0) * Pc[n];
-            s *= Dc.w[q] / (4.0 * PI);
-            for (int al = 0; al < 2; ++al)
-              for (int be = 0; be < 2; ++be) {
-                const double *ua = dp + 3 + 3 * al, *ub = dq + 3 + 3 * be;
-                double dot = ua[0] * ub[0] + ua[1] * ub[1] + ua[2] * ub[2];
-                A[(size_t)(al * K + p) * (2 * Kc) + (be * Kc + q)] = s * dot;
-              }
+        int Lc = Dc.L, Nc = 2 * Lc + 2, Np = 2 * L + 2, nthc = Lc + 1, nthp = L + 1;
+        std::vector<double> Phi((size_t)Np * Nc), Thp((size_t)nthp * nthc), Thm((size_t)nthp * nthc);
+        for (int jp = 0; jp < Np; ++jp)
+          for (int jc = 0; jc < Nc; ++jc) {
+            double dphi = 2.0 * PI * jp / Np - 2.0 * PI * jc / Nc;
+            double s = 1.0;
+            for (int m = 1; m <= Lc; ++m) s += 2.0 * std::cos(m * dphi);
+            Phi[(size_t)jp * Nc + jc] = s / Nc;
           }
-        }
-        B.d_A64 = dev_upload(c, A);
-        std::vector<float> Af(A.size());
-        for (size_t q = 0; q < A.size(); ++q) Af[q] = (float)A[q];
-        B.d_A32 = dev_upload(c, Af);
+        std::vector<double> xc(nthc), xp(nthp);
+        for (int i = 0; i < nthc; ++i) xc[i] = Dc.d[9 * (i * Nc) + 2];
+        for (int i = 0; i < nthp; ++i) xp[i] = Dd.d[9 * (i * Np) + 2];
+        for (int p = 0; p < nthp; ++p)
+          for (int i = 0; i < nthc; ++i) {
+            double li = 1.0;
+            for (int q = 0; q < nthc; ++q)
+              if (q != i) li *= (xp[p] - xc[q]) / (xc[i] - xc[q]);
+            double s = std::sqrt(1.0 - xp[p] * xp[p]) / std::sqrt(1.0 - xc[i] * xc[i]);
+            Thp[(size_t)p * nthc + i] = 0.5 * li * (1.0 + s);
+            Thm[(size_t)p * nthc + i] = 0.5 * li * (1.0 - s);
+          }
+        auto upf = [&](const std::vector<double> &v, void *&d64, void *&d32) {
+          d64 = dev_upload(c, v);
+          std::vector<float> f(v.size());
+          for (size_t q = 0; q < v.size(); ++q) f[q] = (float)v[q];
+          d32 = dev_upload(c, f);
+        };
+        upf(Phi, B.d_Phi64, B.d_Phi32);
+        upf(Thp, B.d_Thp64, B.d_Thp32);
+        upf(Thm, B.d_Thm64, B.d_Thm32);
         B.d_ch_ptr = dev_upload(c, B.ch_ptr);
         B.d_ch_idx = dev_upload(c, B.ch_idx);
       }

@@ -14,7 +14,10 @@ template <> struct tsel<double> {
   static void *V(RegionHost &R) { return R.d_V64; }
   static void *RN(RegionHost &R) { return R.d_RN64; }
   static void *Tr(LevelHost &L) { return L.d_T64; }
-  static void *A(LevelHost &L) { return L.d_A64; }
+  static void *tp(LevelHost &L) { return L.d_tp64; }
+  static void *Phi(LevelHost &L) { return L.d_Phi64; }
+  static void *Thp(LevelHost &L) { return L.d_Thp64; }
+  static void *Thm(LevelHost &L) { return L.d_Thm64; }
   static void *up(LevelHost &L) { return L.d_up64; }
   static void *dn(LevelHost &L) { return L.d_dn64; }
   static void *lo(IluHost &I) { return I.d_lo64; }
@@ -27,7 +30,10 @@ template <> struct tsel<float> {
   static void *V(RegionHost &R) { return R.d_V32; }
   static void *RN(RegionHost &R) { return R.d_RN32; }
   static void *Tr(LevelHost &L) { return L.d_T32; }
-  static void *A(LevelHost &L) { return L.d_A32; }
+  static void *tp(LevelHost &L) { return L.d_tp32; }
+  static void *Phi(LevelHost &L) { return L.d_Phi32; }
+  static void *Thp(LevelHost &L) { return L.d_Thp32; }
+  static void *Thm(LevelHost &L) { return L.d_Thm32; }
   static void *up(LevelHost &L) { return L.d_up32; }
   static void *dn(LevelHost &L) { return L.d_dn32; }
   static void *lo(IluHost &I) { return I.d_lo32; }
@@ -117,112 +123,137 @@ __global__ void k_aggregate(int nbox, int K, int ne, int nrhs, const int *__rest
   }
 }
 
-// Real-by-complex GEMM on column blocks: C(row, col) (+)= sum_kk opA(row, kk) B(kk, col)
-// with opA = A [M x Kd] row-major (trans = 0) or A^T for A [Kd x M] (trans = 1).
-// B(kk, col) lives at B[((col / R) * Kd + kk) * R + col % R]; C likewise with M rows.
-template <typename T, int TM, int TN, int TK>
-__global__ void k_gemm_rc(int M, int N, int Kd, int R, const T *__restrict__ A, int trans,
-                          const cx<T> *__restrict__ B, cx<T> *__restrict__ C, int accumulate) {
-  __shared__ T As[TK][TM + 1];
-  __shared__ cx<T> Bs[TK][TN + 1];
-  int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads
-  int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-  constexpr int RM = TM / 16, RN = TN / 16;
-  cx<T> acc[RM][RN];
-  for (int kk0 = 0; kk0 < Kd; kk0 += TK) {
-    for (int t = threadIdx.x; t < TK * TM; t += 256) {
-      int mm, kk;
-      T v = 0;
-      if (trans) {
-        mm = t % TM;
-        kk = t / TM;
-        int gm = m0 + mm, gk = kk0 + kk;
-        if (gm < M && gk < Kd) v = A[(size_t)gk * M + gm];
-      } else {
-        kk = t % TK;
-        mm = t / TK;
-        int gm = m0 + mm, gk = kk0 + kk;
-        if (gm < M && gk < Kd) v = A[(size_t)gm * Kd + gk];
-      }
-      As[kk][mm] = v;
-    }
-    for (int t = threadIdx.x; t < TK * TN; t += 256) {
-      int kk = t % TK, nn = t / TK;
-      int gk = kk0 + kk, gn = n0 + nn;
-      cx<T> v;
-      if (gk < Kd && gn < N) v = B[((size_t)(gn / R) * Kd + gk) * R + gn % R];
-      Bs[kk][nn] = v;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < TK; ++kk) {
-      T a[RM];
-#pragma unroll
-      for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < RN; ++j) {
-        cx<T> b = Bs[kk][tx + 16 * j];
-#pragma unroll
-        for (int i = 0; i < RM; ++i) {
-          acc[i][j].re = fma(a[i], b.re, acc[i][j].re);
-          acc[i][j].im = fma(a[i], b.im, acc[i][j].im);
-        }
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < RM; ++i)
-#pragma unroll
-    for (int j = 0; j < RN; ++j) {
-      int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
-      if (gm < M && gn < N) {
-        cx<T> *o = C + ((size_t)(gn / R) * M + gm) * R + gn % R;
-        if (accumulate) *o += acc[i][j];
-        else *o = acc[i][j];
-      }
-    }
-}
-
-// Parent sum of shifted, interpolated child patterns:
-// S_p[jm][row][r] = sum_{children c} up[oct(c)][k(row)] Y_c[jm][row][r]
+// Exact separable interpolation of child patterns to the parent sampling,
+// shifted to the parent centre and summed over children (upward pass).  One
+// CTA per parent box; each source (J, M) is carried as three Cartesian
+// components: (theta, phi) -> xyz at the child directions, trigonometric
+// interpolation in phi, the folded Lagrange step in theta, xyz -> (theta, phi)
+// at the parent directions, times the shift exp(j k khat.(c_child - c_parent)).
 template <typename T>
-__global__ void k_up_gather(int nbox, int K, int nrhs, const int *__restrict__ ch_ptr, const int *__restrict__ ch_idx,
-                            const int *__restrict__ oct, const cx<T> *__restrict__ up, const cx<T> *__restrict__ Y,
-                            cx<T> *__restrict__ S) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  int b = blockIdx.y;
-  if (k >= K) return;
-  for (int q = 0; q < 4; ++q) {
-    int row = (q & 1) * K + k;  // theta/phi block
-    int jm = q >> 1;
-    for (int r = 0; r < nrhs; ++r) {
-      cx<T> acc;
+__global__ void k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, const int *__restrict__ ch_ptr,
+                            const int *__restrict__ ch_idx, const int *__restrict__ oct, const T *__restrict__ tpc,
+                            const T *__restrict__ tpp, const T *__restrict__ Phi, const T *__restrict__ Thp,
+                            const T *__restrict__ Thm, const cx<T> *__restrict__ up, const cx<T> *__restrict__ Sc,
+                            cx<T> *__restrict__ Sp) {
+  extern __shared__ unsigned char smem_raw[];
+  const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1;
+  cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [3][Kc]
+  cx<T> *G = A + 3 * Kc;                            // [3][nthc][Np]
+  const int b = blockIdx.x;
+  const int nG = 3 * nthc * Np;
+  for (int r = 0; r < nrhs; ++r)
+    for (int jm = 0; jm < 2; ++jm)
       for (int s = ch_ptr[b]; s < ch_ptr[b + 1]; ++s) {
-        int c = ch_idx[s];
-        acc = cfma(up[oct[c] * K + k], Y[(((size_t)c * 2 + jm) * 2 * K + row) * nrhs + r], acc);
+        const int c = ch_idx[s], o = oct[c];
+        for (int t = threadIdx.x; t < Kc; t += blockDim.x) {
+          cx<T> ft = Sc[(((size_t)c * 4 + jm * 2) * Kc + t) * nrhs + r];
+          cx<T> fp = Sc[(((size_t)c * 4 + jm * 2 + 1) * Kc + t) * nrhs + r];
+          const T *u = tpc + 6 * (size_t)t;
+          for (int x = 0; x < 3; ++x) A[x * Kc + t] = ft * u[x] + fp * u[3 + x];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nG; idx += blockDim.x) {
+          int x = idx / (nthc * Np), rem = idx - x * nthc * Np, ic = rem / Np, jp = rem - ic * Np;
+          const cx<T> *row = A + x * Kc + ic * Nc;
+          const T *ph = Phi + (size_t)jp * Nc;
+          cx<T> acc;
+          for (int jc = 0; jc < Nc; ++jc) {
+            acc.re = fma(ph[jc], row[jc].re, acc.re);
+            acc.im = fma(ph[jc], row[jc].im, acc.im);
+          }
+          G[idx] = acc;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < Kp; t += blockDim.x) {
+          int ip = t / Np, jp = t - ip * Np, jq = (jp + Lp + 1) % Np;
+          cx<T> H[3];
+          for (int x = 0; x < 3; ++x) {
+            const cx<T> *g = G + (size_t)x * nthc * Np;
+            cx<T> acc;
+            for (int ic = 0; ic < nthc; ++ic) {
+              T a = Thp[ip * nthc + ic], bq = Thm[ip * nthc + ic];
+              cx<T> g1 = g[ic * Np + jp], g2 = g[ic * Np + jq];
+              acc.re = fma(a, g1.re, fma(bq, g2.re, acc.re));
+              acc.im = fma(a, g1.im, fma(bq, g2.im, acc.im));
+            }
+            H[x] = acc;
+          }
+          const T *u = tpp + 6 * (size_t)t;
+          cx<T> ft = H[0] * u[0] + H[1] * u[1] + H[2] * u[2];
+          cx<T> fp = H[0] * u[3] + H[1] * u[4] + H[2] * u[5];
+          cx<T> sh = up[o * Kp + t];
+          cx<T> *o0 = Sp + (((size_t)b * 4 + jm * 2) * Kp + t) * nrhs + r;
+          cx<T> *o1 = Sp + (((size_t)b * 4 + jm * 2 + 1) * Kp + t) * nrhs + r;
+          if (s == ch_ptr[b]) {
+            *o0 = sh * ft;
+            *o1 = sh * fp;
+          } else {
+            *o0 += sh * ft;
+            *o1 += sh * fp;
+          }
+        }
+        __syncthreads();
       }
-      S[(((size_t)b * 2 + jm) * 2 * K + row) * nrhs + r] = acc;
-    }
-  }
 }
 
-// Downward shift of the parent's incoming field into each child's column:
-// U_c[jm][row][r] = dn[oct(c)][k(row)] I_parent(c)[jm][row][r]
+// Exact transpose of k_interp_up (anterpolation, downward pass), with the
+// receive shift exp(-j k khat.(c_child - c_parent)): one CTA per child box,
+// I_child += Interp^T [dn (.) I_parent].  Quadrature weights are folded into
+// the translators, so the adjoint is the plain transpose.
 template <typename T>
-__global__ void k_dn_shift(int nchild, int Kp, int nrhs, const int *__restrict__ parent, const int *__restrict__ oct,
-                           const cx<T> *__restrict__ dn, const cx<T> *__restrict__ Ip, cx<T> *__restrict__ U) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  int c = blockIdx.y;
-  if (k >= Kp) return;
-  int pb = parent[c];
-  cx<T> sh = dn[oct[c] * Kp + k];
-  for (int q = 0; q < 4; ++q) {
-    int row = (q & 1) * Kp + k;
-    int jm = q >> 1;
-    for (int r = 0; r < nrhs; ++r)
-      U[(((size_t)c * 2 + jm) * 2 * Kp + row) * nrhs + r] = sh * Ip[(((size_t)pb * 2 + jm) * 2 * Kp + row) * nrhs + r];
-  }
+__global__ void k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs, const int *__restrict__ parent,
+                            const int *__restrict__ oct, const T *__restrict__ tpc, const T *__restrict__ tpp,
+                            const T *__restrict__ Phi, const T *__restrict__ Thp, const T *__restrict__ Thm,
+                            const cx<T> *__restrict__ dn, const cx<T> *__restrict__ Ip, cx<T> *__restrict__ Ic) {
+  extern __shared__ unsigned char smem_raw[];
+  const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1, nthp = Lp + 1;
+  cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [3][Kp]
+  cx<T> *G = A + 3 * Kp;                            // [3][nthc][Np]
+  const int c = blockIdx.x, pb = parent[c], o = oct[c];
+  const int nG = 3 * nthc * Np;
+  for (int r = 0; r < nrhs; ++r)
+    for (int jm = 0; jm < 2; ++jm) {
+      for (int t = threadIdx.x; t < Kp; t += blockDim.x) {
+        cx<T> sh = dn[o * Kp + t];
+        cx<T> ut = sh * Ip[(((size_t)pb * 4 + jm * 2) * Kp + t) * nrhs + r];
+        cx<T> up_ = sh * Ip[(((size_t)pb * 4 + jm * 2 + 1) * Kp + t) * nrhs + r];
+        const T *u = tpp + 6 * (size_t)t;
+        for (int x = 0; x < 3; ++x) A[x * Kp + t] = ut * u[x] + up_ * u[3 + x];
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nG; idx += blockDim.x) {
+        int x = idx / (nthc * Np), rem = idx - x * nthc * Np, ic = rem / Np, j = rem - ic * Np;
+        int jq = (j + Lp + 1) % Np;
+        const cx<T> *a = A + (size_t)x * Kp;
+        cx<T> acc;
+        for (int ip = 0; ip < nthp; ++ip) {
+          T w1 = Thp[ip * nthc + ic], w2 = Thm[ip * nthc + ic];
+          cx<T> a1 = a[ip * Np + j], a2 = a[ip * Np + jq];
+          acc.re = fma(w1, a1.re, fma(w2, a2.re, acc.re));
+          acc.im = fma(w1, a1.im, fma(w2, a2.im, acc.im));
+        }
+        G[idx] = acc;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < Kc; t += blockDim.x) {
+        int ic = t / Nc, jc = t - ic * Nc;
+        cx<T> C[3];
+        for (int x = 0; x < 3; ++x) {
+          const cx<T> *g = G + ((size_t)x * nthc + ic) * Np;
+          cx<T> acc;
+          for (int jp = 0; jp < Np; ++jp) {
+            T ph = Phi[(size_t)jp * Nc + jc];
+            acc.re = fma(ph, g[jp].re, acc.re);
+            acc.im = fma(ph, g[jp].im, acc.im);
+          }
+          C[x] = acc;
+        }
+        const T *u = tpc + 6 * (size_t)t;
+        Ic[(((size_t)c * 4 + jm * 2) * Kc + t) * nrhs + r] += C[0] * u[0] + C[1] * u[1] + C[2] * u[2];
+        Ic[(((size_t)c * 4 + jm * 2 + 1) * Kc + t) * nrhs + r] += C[0] * u[3] + C[1] * u[4] + C[2] * u[5];
+      }
+      __syncthreads();
+    }
 }
 
 // Diagonal M2L translation: I_b(k) = sum_{b' in IL(b)} T_{b-b'}(k) S_b'(k), 4 components.
@@ -406,6 +437,12 @@ __global__ void k_f2d(const zf *a, zd *b, int64_t n) {
     b[i] = zd(a[i].re, a[i].im);
 }
 
+template <typename K>
+void set_smem(K kernel, size_t bytes) {
+  SIE_REQUIRE(bytes <= 227 * 1024, SIE_EINVAL, "MLFMM interpolation tile exceeds shared memory (too many directions)");
+  if (bytes > 48 * 1024) SIE_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
 inline int grid1(int64_t n, int bs) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + bs - 1) / bs, 152 * 32)); }
 
 }  // namespace
@@ -418,14 +455,6 @@ void op_near(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool accumulate) {
   k_near_spmv<T><<<blocks, 32 * warps_per_block, 0, c->stream>>>(c->ne, nrhs, c->d_row_ptr, c->d_col,
                                                                  (const cx<T> *)tsel<T>::near(c), x, y,
                                                                  accumulate ? 1 : 0);
-  SIE_CHECK_LAUNCH();
-  c->launches++;
-}
-
-template <typename T>
-static void gemm(sie_ctx *c, int M, int N, int Kd, int R, const T *A, int trans, const cx<T> *B, cx<T> *C, int acc) {
-  dim3 grid((N + 63) / 64, (M + 63) / 64);
-  k_gemm_rc<T, 64, 64, 16><<<grid, 256, 0, c->stream>>>(M, N, Kd, R, A, trans, B, C, acc);
   SIE_CHECK_LAUNCH();
   c->launches++;
 }
@@ -450,11 +479,12 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
     // upward pass: interpolate + shift into parents
     for (int lv = leaf; lv >= 3; --lv) {
       LevelHost &C = G.lev[lv], &P = G.lev[lv - 1];
-      cx<T> *Y = (cx<T> *)c->d_gemm;
-      gemm<T>(c, 2 * P.K, C.nbox * 2 * R, 2 * C.K, R, (const T *)tsel<T>::A(P), 0, (const cx<T> *)C.d_S, Y, 0);
-      dim3 grid((P.K + 127) / 128, P.nbox);
-      k_up_gather<T><<<grid, 128, 0, c->stream>>>(P.nbox, P.K, R, P.d_ch_ptr, P.d_ch_idx, C.d_oct,
-                                                  (const cx<T> *)tsel<T>::up(P), Y, (cx<T> *)P.d_S);
+      size_t smem = (size_t)(3 * C.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>);
+      set_smem(k_interp_up<T>, smem);
+      k_interp_up<T><<<P.nbox, 256, smem, c->stream>>>(
+          C.K, C.L, P.K, P.L, R, P.d_ch_ptr, P.d_ch_idx, C.d_oct, (const T *)tsel<T>::tp(C),
+          (const T *)tsel<T>::tp(P), (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P),
+          (const T *)tsel<T>::Thm(P), (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, (cx<T> *)P.d_S);
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
@@ -470,13 +500,14 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
     // downward pass: shift + anterpolate (exact transpose) into children
     for (int lv = 2; lv < leaf; ++lv) {
       LevelHost &P = G.lev[lv], &C = G.lev[lv + 1];
-      cx<T> *U = (cx<T> *)c->d_gemm;
-      dim3 grid((P.K + 127) / 128, C.nbox);
-      k_dn_shift<T><<<grid, 128, 0, c->stream>>>(C.nbox, P.K, R, C.d_parent, C.d_oct,
-                                                 (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, U);
+      size_t smem = (size_t)(3 * P.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>);
+      set_smem(k_anterp_dn<T>, smem);
+      k_anterp_dn<T><<<C.nbox, 256, smem, c->stream>>>(
+          C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
+          (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
+          (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
       SIE_CHECK_LAUNCH();
       c->launches++;
-      gemm<T>(c, 2 * C.K, C.nbox * 2 * R, 2 * P.K, R, (const T *)tsel<T>::A(P), 1, U, (cx<T> *)C.d_I, 1);
     }
     // receive at the leaves
     {
