@@ -170,12 +170,13 @@ struct sie_ctx {
   int64_t nrhs_cap = 0;
   void *d_xi = nullptr, *d_yi = nullptr;          // internal-order FP64 vectors [R][ne][2]
   void *d_xf = nullptr, *d_yf = nullptr;          // FP32 copies
+  void *d_scratch = nullptr;                      // upward-pass child contributions
   void *d_stage = nullptr;                        // small host-to-device staging area
   size_t stage_bytes = 0;
   // Krylov storage of the last solve shape (restart m, nrhs R)
   int gm_m = 0, gm_R = 0;
   void *gm_V = nullptr, *gm_Z = nullptr, *gm_b = nullptr, *gm_x = nullptr, *gm_w = nullptr;
-  void *gm_h = nullptr, *gm_s = nullptr;
+  void *gm_h = nullptr, *gm_s = nullptr, *gm_part = nullptr;
 };
 
 // ------------------------------------------------------------------ host helpers (host.cpp)

@@ -40,14 +40,18 @@ void ensure_work(sie_ctx *c, int64_t nrhs) {
   c->d_yi = dev_alloc(c, n * sizeof(zd));
   c->d_xf = dev_alloc(c, n * sizeof(zf));
   c->d_yf = dev_alloc(c, n * sizeof(zf));
+  size_t scratch = 0;
   for (auto &R : c->reg) {
     for (int l = 2; l < (int)R.lev.size(); ++l) {
       LevelHost &L = R.lev[l];
       size_t sz = (size_t)L.nbox * 4 * L.K * nrhs * sizeof(zd);
       L.d_S = dev_alloc(c, sz);
       L.d_I = dev_alloc(c, sz);
+      if (l >= 3)  // children's interpolated patterns in the parent sampling
+        scratch = std::max(scratch, (size_t)L.nbox * 4 * R.lev[l - 1].K * nrhs * sizeof(zd));
     }
   }
+  c->d_scratch = dev_alloc(c, scratch);
   c->nrhs_cap = nrhs;
 }
 

@@ -123,77 +123,80 @@ __global__ void k_aggregate(int nbox, int K, int ne, int nrhs, const int *__rest
   }
 }
 
-// Exact separable interpolation of child patterns to the parent sampling,
-// shifted to the parent centre and summed over children (upward pass).  One
-// CTA per parent box; each source (J, M) is carried as three Cartesian
-// components: (theta, phi) -> xyz at the child directions, trigonometric
-// interpolation in phi, the folded Lagrange step in theta, xyz -> (theta, phi)
-// at the parent directions, times the shift exp(j k khat.(c_child - c_parent)).
+// Exact separable interpolation of one child's pattern to the parent
+// sampling, shifted to the parent centre (upward pass).  One CTA per (child,
+// source J|M); the source is carried as three Cartesian components:
+// (theta, phi) -> xyz at the child directions, trigonometric interpolation in
+// phi, the folded Lagrange step in theta, xyz -> (theta, phi) at the parent
+// directions, times the shift exp(j k khat.(c_child - c_parent)).  Output
+// Y[child][J|M][theta|phi][k_parent][r]; k_up_sum adds the children.
 template <typename T>
-__global__ void k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, const int *__restrict__ ch_ptr,
-                            const int *__restrict__ ch_idx, const int *__restrict__ oct, const T *__restrict__ tpc,
-                            const T *__restrict__ tpp, const T *__restrict__ Phi, const T *__restrict__ Thp,
-                            const T *__restrict__ Thm, const cx<T> *__restrict__ up, const cx<T> *__restrict__ Sc,
-                            cx<T> *__restrict__ Sp) {
+__global__ void k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, const int *__restrict__ oct,
+                            const T *__restrict__ tpc, const T *__restrict__ tpp, const T *__restrict__ Phi,
+                            const T *__restrict__ Thp, const T *__restrict__ Thm, const cx<T> *__restrict__ up,
+                            const cx<T> *__restrict__ Sc, cx<T> *__restrict__ Y) {
   extern __shared__ unsigned char smem_raw[];
   const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1;
   cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [3][Kc]
   cx<T> *G = A + 3 * Kc;                            // [3][nthc][Np]
-  const int b = blockIdx.x;
+  const int c = blockIdx.x, jm = blockIdx.y, o = oct[c];
   const int nG = 3 * nthc * Np;
-  for (int r = 0; r < nrhs; ++r)
-    for (int jm = 0; jm < 2; ++jm)
-      for (int s = ch_ptr[b]; s < ch_ptr[b + 1]; ++s) {
-        const int c = ch_idx[s], o = oct[c];
-        for (int t = threadIdx.x; t < Kc; t += blockDim.x) {
-          cx<T> ft = Sc[(((size_t)c * 4 + jm * 2) * Kc + t) * nrhs + r];
-          cx<T> fp = Sc[(((size_t)c * 4 + jm * 2 + 1) * Kc + t) * nrhs + r];
-          const T *u = tpc + 6 * (size_t)t;
-          for (int x = 0; x < 3; ++x) A[x * Kc + t] = ft * u[x] + fp * u[3 + x];
-        }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < nG; idx += blockDim.x) {
-          int x = idx / (nthc * Np), rem = idx - x * nthc * Np, ic = rem / Np, jp = rem - ic * Np;
-          const cx<T> *row = A + x * Kc + ic * Nc;
-          const T *ph = Phi + (size_t)jp * Nc;
-          cx<T> acc;
-          for (int jc = 0; jc < Nc; ++jc) {
-            acc.re = fma(ph[jc], row[jc].re, acc.re);
-            acc.im = fma(ph[jc], row[jc].im, acc.im);
-          }
-          G[idx] = acc;
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < Kp; t += blockDim.x) {
-          int ip = t / Np, jp = t - ip * Np, jq = (jp + Lp + 1) % Np;
-          cx<T> H[3];
-          for (int x = 0; x < 3; ++x) {
-            const cx<T> *g = G + (size_t)x * nthc * Np;
-            cx<T> acc;
-            for (int ic = 0; ic < nthc; ++ic) {
-              T a = Thp[ip * nthc + ic], bq = Thm[ip * nthc + ic];
-              cx<T> g1 = g[ic * Np + jp], g2 = g[ic * Np + jq];
-              acc.re = fma(a, g1.re, fma(bq, g2.re, acc.re));
-              acc.im = fma(a, g1.im, fma(bq, g2.im, acc.im));
-            }
-            H[x] = acc;
-          }
-          const T *u = tpp + 6 * (size_t)t;
-          cx<T> ft = H[0] * u[0] + H[1] * u[1] + H[2] * u[2];
-          cx<T> fp = H[0] * u[3] + H[1] * u[4] + H[2] * u[5];
-          cx<T> sh = up[o * Kp + t];
-          cx<T> *o0 = Sp + (((size_t)b * 4 + jm * 2) * Kp + t) * nrhs + r;
-          cx<T> *o1 = Sp + (((size_t)b * 4 + jm * 2 + 1) * Kp + t) * nrhs + r;
-          if (s == ch_ptr[b]) {
-            *o0 = sh * ft;
-            *o1 = sh * fp;
-          } else {
-            *o0 += sh * ft;
-            *o1 += sh * fp;
-          }
-        }
-        __syncthreads();
+  for (int r = 0; r < nrhs; ++r) {
+    for (int t = threadIdx.x; t < Kc; t += blockDim.x) {
+      cx<T> ft = Sc[(((size_t)c * 4 + jm * 2) * Kc + t) * nrhs + r];
+      cx<T> fp = Sc[(((size_t)c * 4 + jm * 2 + 1) * Kc + t) * nrhs + r];
+      const T *u = tpc + 6 * (size_t)t;
+      for (int x = 0; x < 3; ++x) A[x * Kc + t] = ft * u[x] + fp * u[3 + x];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nG; idx += blockDim.x) {
+      int x = idx / (nthc * Np), rem = idx - x * nthc * Np, ic = rem / Np, jp = rem - ic * Np;
+      const cx<T> *row = A + x * Kc + ic * Nc;
+      const T *ph = Phi + (size_t)jp * Nc;
+      cx<T> acc;
+      for (int jc = 0; jc < Nc; ++jc) {
+        acc.re = fma(ph[jc], row[jc].re, acc.re);
+        acc.im = fma(ph[jc], row[jc].im, acc.im);
       }
+      G[idx] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Kp; t += blockDim.x) {
+      int ip = t / Np, jp = t - ip * Np, jq = (jp + Lp + 1) % Np;
+      cx<T> H[3];
+      for (int x = 0; x < 3; ++x) {
+        const cx<T> *g = G + (size_t)x * nthc * Np;
+        cx<T> acc;
+        for (int ic = 0; ic < nthc; ++ic) {
+          T a = Thp[ip * nthc + ic], bq = Thm[ip * nthc + ic];
+          cx<T> g1 = g[ic * Np + jp], g2 = g[ic * Np + jq];
+          acc.re = fma(a, g1.re, fma(bq, g2.re, acc.re));
+          acc.im = fma(a, g1.im, fma(bq, g2.im, acc.im));
+        }
+        H[x] = acc;
+      }
+      const T *u = tpp + 6 * (size_t)t;
+      cx<T> sh = up[o * Kp + t];
+      Y[(((size_t)c * 4 + jm * 2) * Kp + t) * nrhs + r] = sh * (H[0] * u[0] + H[1] * u[1] + H[2] * u[2]);
+      Y[(((size_t)c * 4 + jm * 2 + 1) * Kp + t) * nrhs + r] = sh * (H[0] * u[3] + H[1] * u[4] + H[2] * u[5]);
+    }
+    __syncthreads();
+  }
+}
+
+// S_parent = sum over children of the shifted, interpolated child patterns.
+template <typename T>
+__global__ void k_up_sum(int Kp, int nrhs, const int *__restrict__ ch_ptr, const int *__restrict__ ch_idx,
+                         const cx<T> *__restrict__ Y, cx<T> *__restrict__ Sp) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  if (t >= Kp) return;
+  for (int q = 0; q < 4; ++q)
+    for (int r = 0; r < nrhs; ++r) {
+      cx<T> acc;
+      for (int s = ch_ptr[b]; s < ch_ptr[b + 1]; ++s) acc += Y[(((size_t)ch_idx[s] * 4 + q) * Kp + t) * nrhs + r];
+      Sp[(((size_t)b * 4 + q) * Kp + t) * nrhs + r] = acc;
+    }
 }
 
 // Exact transpose of k_interp_up (anterpolation, downward pass), with the
@@ -209,10 +212,9 @@ __global__ void k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
   const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1, nthp = Lp + 1;
   cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [3][Kp]
   cx<T> *G = A + 3 * Kp;                            // [3][nthc][Np]
-  const int c = blockIdx.x, pb = parent[c], o = oct[c];
+  const int c = blockIdx.x, jm = blockIdx.y, pb = parent[c], o = oct[c];
   const int nG = 3 * nthc * Np;
-  for (int r = 0; r < nrhs; ++r)
-    for (int jm = 0; jm < 2; ++jm) {
+  for (int r = 0; r < nrhs; ++r) {
       for (int t = threadIdx.x; t < Kp; t += blockDim.x) {
         cx<T> sh = dn[o * Kp + t];
         cx<T> ut = sh * Ip[(((size_t)pb * 4 + jm * 2) * Kp + t) * nrhs + r];
@@ -329,9 +331,13 @@ __global__ void k_disaggregate(int nb, int K, int L, int ne, int nrhs, const int
 }
 
 // ---------------------------------------------------------------- ILU(0) sweeps
-// Forward: z = L^-1 v.  One CTA per leaf box of the current colour; off-box
-// terms come from earlier colours (final), the in-box unit-lower solve runs
-// in warp 0 with lanes over rows.  Backward analogous with U and later colours.
+// The factors are stored in the box-colour order: for colour c, the rows of
+// all its leaf boxes are contiguous and no two of its boxes touch.  Forward
+// sweep per colour: (1) off-box part  z_i = v_i - sum_{q in earlier colours} L_iq z_q
+// for every row of the colour (one warp per row, GPU-wide); (2) in-box unit
+// lower solve, one CTA per box with the box's strictly lower triangle staged
+// in shared memory.  Backward: the same with U, later colours and the
+// inverted 2x2 diagonal blocks.
 template <typename T>
 __device__ __forceinline__ void mv2(const cx<T> *B, cx<T> x0, cx<T> x1, cx<T> &y0, cx<T> &y1) {
   y0 = B[0] * x0 + B[1] * x1;
@@ -339,37 +345,59 @@ __device__ __forceinline__ void mv2(const cx<T> *B, cx<T> x0, cx<T> x1, cx<T> &y
 }
 
 template <typename T>
-__global__ void k_ilu_sweep(int ne, int nrhs, int forward, const int *__restrict__ box_list, int first,
-                            const int *__restrict__ box_start, const int *__restrict__ off_ptr,
-                            const int *__restrict__ off_col, const cx<T> *__restrict__ off_val,
-                            const int64_t *__restrict__ dense_off, const cx<T> *__restrict__ dense,
-                            const cx<T> *__restrict__ dinv, const cx<T> *__restrict__ v, cx<T> *__restrict__ z) {
-  extern __shared__ unsigned char smem_raw[];
-  cx<T> *rr = reinterpret_cast<cx<T> *>(smem_raw);  // [n][2]
-  int b = box_list[first + blockIdx.x];
-  int s0 = box_start[b], n = box_start[b + 1] - s0;
-  const cx<T> *D = dense + 4 * dense_off[b];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+__global__ void k_ilu_offbox(int ne, int nrhs, int row0, int row1, const int *__restrict__ off_ptr,
+                             const int *__restrict__ off_col, const cx<T> *__restrict__ off_val,
+                             const cx<T> *src, cx<T> *z) {
+  int i = row0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= row1) return;
+  int q0 = off_ptr[i], q1 = off_ptr[i + 1];
   for (int r = 0; r < nrhs; ++r) {
-    const cx<T> *vr = v + (size_t)r * ne * 2;
-    cx<T> *zr = z + (size_t)r * ne * 2;
-    for (int li = warp; li < n; li += nw) {
-      int i = s0 + li;
-      cx<T> a0, a1;
-      for (int q = off_ptr[i] + lane; q < off_ptr[i + 1]; q += 32) {
-        int cc = off_col[q];
-        cx<T> t0, t1;
-        mv2(off_val + 4 * (size_t)q, zr[2 * cc], zr[2 * cc + 1], t0, t1);
-        a0 += t0;
-        a1 += t1;
-      }
-      a0 = warp_sum(a0);
-      a1 = warp_sum(a1);
-      if (lane == 0) {
-        rr[2 * li] = vr[2 * i] - a0;
-        rr[2 * li + 1] = vr[2 * i + 1] - a1;
-      }
+    const cx<T> *zr = z + (size_t)r * ne * 2;
+    cx<T> a0, a1;
+    for (int q = q0 + lane; q < q1; q += 32) {
+      int cc = off_col[q];
+      cx<T> t0, t1;
+      mv2(off_val + 4 * (size_t)q, zr[2 * cc], zr[2 * cc + 1], t0, t1);
+      a0 += t0;
+      a1 += t1;
     }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    if (lane == 0) {
+      const cx<T> *sr = src + ((size_t)r * ne + i) * 2;
+      cx<T> s0 = sr[0], s1 = sr[1];
+      cx<T> *o = z + ((size_t)r * ne + i) * 2;
+      o[0] = s0 - a0;
+      o[1] = s1 - a1;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_ilu_inbox(int ne, int nrhs, int forward, int box0, int staged, const int *__restrict__ box_start,
+                            const int64_t *__restrict__ dense_off, const cx<T> *__restrict__ dense,
+                            const cx<T> *__restrict__ dinv, cx<T> *z) {
+  extern __shared__ unsigned char smem_raw[];
+  const int b = box0 + blockIdx.x;
+  const int s0 = box_start[b], n = box_start[b + 1] - s0;
+  const cx<T> *D = dense + 4 * dense_off[b];  // column-major n x n blocks
+  cx<T> *rr = reinterpret_cast<cx<T> *>(smem_raw);  // [2n]
+  cx<T> *tri = rr + 2 * n;                          // packed triangle [n(n-1)/2][4]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // packed column start: forward keeps rows j+1..n-1 of column j, backward rows 0..j-1
+  auto pcol = [&](int j) { return forward ? j * (n - 1) - j * (j - 1) / 2 : j * (j - 1) / 2; };
+  if (staged) {
+    for (int j = warp; j < n; j += nw) {
+      int lo = forward ? j + 1 : 0, hi = forward ? n : j;
+      int base = pcol(j) - lo;
+      for (int li = lo + lane; li < hi; li += 32)
+        for (int q = 0; q < 4; ++q) tri[4 * (base + li) + q] = D[4 * ((size_t)j * n + li) + q];
+    }
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    cx<T> *zr = z + ((size_t)r * ne + s0) * 2;
+    for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) rr[t] = zr[t];
     __syncthreads();
     if (warp == 0) {
       if (forward) {
@@ -377,15 +405,12 @@ __global__ void k_ilu_sweep(int ne, int nrhs, int forward, const int *__restrict
           __syncwarp();
           cx<T> z0 = rr[2 * j], z1 = rr[2 * j + 1];
           __syncwarp();
+          const cx<T> *col = staged ? tri + 4 * (pcol(j) - (j + 1)) : D + 4 * (size_t)j * n;
           for (int li = j + 1 + lane; li < n; li += 32) {
             cx<T> t0, t1;
-            mv2(D + 4 * ((size_t)j * n + li), z0, z1, t0, t1);
+            mv2(col + 4 * li, z0, z1, t0, t1);
             rr[2 * li] -= t0;
             rr[2 * li + 1] -= t1;
-          }
-          if (lane == 0) {
-            zr[2 * (s0 + j)] = z0;
-            zr[2 * (s0 + j) + 1] = z1;
           }
         }
       } else {
@@ -394,19 +419,23 @@ __global__ void k_ilu_sweep(int ne, int nrhs, int forward, const int *__restrict
           cx<T> x0, x1;
           mv2(dinv + 4 * (size_t)(s0 + j), rr[2 * j], rr[2 * j + 1], x0, x1);
           __syncwarp();
+          if (lane == 0) {
+            rr[2 * j] = x0;
+            rr[2 * j + 1] = x1;
+          }
+          const cx<T> *col = staged ? tri + 4 * pcol(j) : D + 4 * (size_t)j * n;
           for (int li = lane; li < j; li += 32) {
             cx<T> t0, t1;
-            mv2(D + 4 * ((size_t)j * n + li), x0, x1, t0, t1);
+            mv2(col + 4 * li, x0, x1, t0, t1);
             rr[2 * li] -= t0;
             rr[2 * li + 1] -= t1;
           }
-          if (lane == 0) {
-            zr[2 * (s0 + j)] = x0;
-            zr[2 * (s0 + j) + 1] = x1;
-          }
         }
       }
+      __syncwarp();
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) zr[t] = rr[t];
     __syncthreads();
   }
 }
@@ -476,17 +505,21 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
-    // upward pass: interpolate + shift into parents
+    // upward pass: interpolate + shift each child, then sum into parents
     for (int lv = leaf; lv >= 3; --lv) {
       LevelHost &C = G.lev[lv], &P = G.lev[lv - 1];
       size_t smem = (size_t)(3 * C.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>);
       set_smem(k_interp_up<T>, smem);
-      k_interp_up<T><<<P.nbox, 256, smem, c->stream>>>(
-          C.K, C.L, P.K, P.L, R, P.d_ch_ptr, P.d_ch_idx, C.d_oct, (const T *)tsel<T>::tp(C),
-          (const T *)tsel<T>::tp(P), (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P),
-          (const T *)tsel<T>::Thm(P), (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, (cx<T> *)P.d_S);
+      cx<T> *Y = (cx<T> *)c->d_scratch;
+      k_interp_up<T><<<dim3(C.nbox, 2), 256, smem, c->stream>>>(
+          C.K, C.L, P.K, P.L, R, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
+          (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
+          (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
       SIE_CHECK_LAUNCH();
-      c->launches++;
+      k_up_sum<T><<<dim3((P.K + 127) / 128, P.nbox), 128, 0, c->stream>>>(P.K, R, P.d_ch_ptr, P.d_ch_idx, Y,
+                                                                           (cx<T> *)P.d_S);
+      SIE_CHECK_LAUNCH();
+      c->launches += 2;
     }
     // translations at every level
     for (int lv = 2; lv <= leaf; ++lv) {
@@ -502,7 +535,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       LevelHost &P = G.lev[lv], &C = G.lev[lv + 1];
       size_t smem = (size_t)(3 * P.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>);
       set_smem(k_anterp_dn<T>, smem);
-      k_anterp_dn<T><<<C.nbox, 256, smem, c->stream>>>(
+      k_anterp_dn<T><<<dim3(C.nbox, 2), 256, smem, c->stream>>>(
           C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
           (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
           (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
@@ -527,19 +560,28 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
 template <typename T>
 void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
   IluHost &I = c->ilu;
-  size_t smem = (size_t)std::max(I.max_box, 1) * 2 * sizeof(cx<T>);
+  const int mb = std::max(I.max_box, 1);
+  size_t full = ((size_t)mb * (mb - 1) / 2 * 4 + 2 * mb) * sizeof(cx<T>);
+  int staged = full <= 200 * 1024 ? 1 : 0;
+  size_t smem = staged ? full : 2 * (size_t)mb * sizeof(cx<T>);
+  set_smem(k_ilu_inbox<T>, smem);
   for (int pass = 0; pass < 2; ++pass) {
     bool fwd = pass == 0;
     for (int q = 0; q < 8; ++q) {
       int colr = fwd ? q : 7 - q;
       int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
       if (cnt == 0) continue;
-      k_ilu_sweep<T><<<cnt, 128, smem, c->stream>>>(
-          c->ne, nrhs, fwd ? 1 : 0, I.d_box_list, first, I.d_box_start, fwd ? I.d_lo_ptr : I.d_up_ptr,
-          fwd ? I.d_lo_col : I.d_up_col, (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), I.d_dense_off,
-          (const cx<T> *)tsel<T>::dense(I), (const cx<T> *)tsel<T>::dinv(I), fwd ? r : z, z);
+      int row0 = c->leaf_start[first], row1 = c->leaf_start[first + cnt];
+      int warps = row1 - row0, wpb = 8;
+      k_ilu_offbox<T><<<(warps + wpb - 1) / wpb, 32 * wpb, 0, c->stream>>>(
+          c->ne, nrhs, row0, row1, fwd ? I.d_lo_ptr : I.d_up_ptr, fwd ? I.d_lo_col : I.d_up_col,
+          (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? r : z, z);
       SIE_CHECK_LAUNCH();
-      c->launches++;
+      k_ilu_inbox<T><<<cnt, 128, smem, c->stream>>>(c->ne, nrhs, fwd ? 1 : 0, first, staged, I.d_box_start,
+                                                   I.d_dense_off, (const cx<T> *)tsel<T>::dense(I),
+                                                   (const cx<T> *)tsel<T>::dinv(I), z);
+      SIE_CHECK_LAUNCH();
+      c->launches += 2;
     }
   }
 }

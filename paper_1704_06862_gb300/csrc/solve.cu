@@ -15,15 +15,46 @@ namespace {
 
 typedef std::complex<double> cd;
 
-// h[i][r] = sum_n conj(V_i[r][n]) w[r][n]; block (i, r)
-__global__ void k_mdot(int n, int nrhs, const zd *__restrict__ V, size_t vstride, const zd *__restrict__ w,
-                       zd *__restrict__ h) {
-  int i = blockIdx.x, r = blockIdx.y;
-  const zd *a = V + (size_t)i * vstride + (size_t)r * n;
-  const zd *b = w + (size_t)r * n;
-  zd acc;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) acc = cfma(conj(a[t]), b[t], acc);
+// Two-stage dot products h[i][r] = sum_n conj(V_i[r][n]) w[r][n], i < nvec.
+// Stage 1: block (blk, r) stages its chunk of w in shared memory and writes a
+// partial sum per vector; stage 2 sums the partials.  Every V_i is read once.
+__global__ void k_mdot_part(int n, int nrhs, int nvec, int nblk, const zd *__restrict__ V, size_t vstride,
+                            const zd *__restrict__ w, zd *__restrict__ part) {
+  __shared__ zd ws[1024];
   __shared__ zd red[256];
+  const int blk = blockIdx.x, r = blockIdx.y;
+  const int chunk = (n + nblk - 1) / nblk;
+  const int t0 = blk * chunk, t1 = min(n, t0 + chunk);
+  for (int base = t0; base < t1; base += 1024) {
+    const int cnt = min(1024, t1 - base);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) ws[t] = w[(size_t)r * n + base + t];
+    __syncthreads();
+    for (int i = 0; i < nvec; ++i) {
+      const zd *a = V + (size_t)i * vstride + (size_t)r * n + base;
+      zd acc;
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) acc = cfma(conj(a[t]), ws[t], acc);
+      red[threadIdx.x] = acc;
+      __syncthreads();
+      for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {
+        zd *p = part + ((size_t)i * nrhs + r) * nblk + blk;
+        *p = (base == t0 ? zd() : *p) + red[0];
+      }
+      __syncthreads();
+    }
+  }
+  if (t0 >= t1 && threadIdx.x == 0)
+    for (int i = 0; i < nvec; ++i) part[((size_t)i * nrhs + r) * nblk + blk] = zd();
+}
+
+__global__ void k_mdot_sum(int nrhs, int nblk, const zd *__restrict__ part, zd *__restrict__ h) {
+  const int i = blockIdx.x, r = blockIdx.y;
+  __shared__ zd red[256];
+  zd acc;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += part[((size_t)i * nrhs + r) * nblk + b];
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -72,13 +103,21 @@ __global__ void k_xupd(int n, int nrhs, int m, const zd *__restrict__ Z, size_t 
 struct Gm {
   sie_ctx *c;
   int n, R;
+  int nblk;
+  zd *part;
   void launch_check() {
     SIE_CHECK_LAUNCH();
     c->launches++;
   }
-  void norms(const zd *w, zd *d_h, std::vector<double> &out) {
-    k_mdot<<<dim3(1, R), 256, 0, c->stream>>>(n, R, w, 0, w, d_h);
+  // h[i][r] = <V_i[r], w[r]> for i < nvec
+  void mdot(const zd *V, size_t vstride, int nvec, const zd *w, zd *d_h) {
+    k_mdot_part<<<dim3(nblk, R), 256, 0, c->stream>>>(n, R, nvec, nblk, V, vstride, w, part);
     launch_check();
+    k_mdot_sum<<<dim3(nvec, R), 256, 0, c->stream>>>(R, nblk, part, d_h);
+    launch_check();
+  }
+  void norms(const zd *w, zd *d_h, std::vector<double> &out) {
+    mdot(w, 0, 1, w, d_h);
     std::vector<zd> h(R);
     SIE_CUDA(cudaMemcpyAsync(h.data(), d_h, R * sizeof(zd), cudaMemcpyDeviceToHost, c->stream));
     SIE_CUDA(cudaStreamSynchronize(c->stream));
@@ -105,12 +144,13 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
     c->gm_w = dev_alloc(c, vs * sizeof(zd));
     c->gm_h = dev_alloc(c, (size_t)(m + 2) * R * sizeof(zd));
     c->gm_s = dev_alloc(c, (size_t)(m + 2) * R * sizeof(zd));
+    c->gm_part = dev_alloc(c, (size_t)(m + 2) * R * 304 * sizeof(zd));
     c->gm_m = m;
     c->gm_R = R;
   }
   zd *V = (zd *)c->gm_V, *Z = (zd *)c->gm_Z, *b = (zd *)c->gm_b, *x = (zd *)c->gm_x, *w = (zd *)c->gm_w;
   zd *d_h = (zd *)c->gm_h, *d_s = (zd *)c->gm_s;
-  Gm g{c, n, R};
+  Gm g{c, n, R, std::max(1, std::min(304, (n + 1023) / 1024)), (zd *)c->gm_part};
   op_permute_in(c, b_user, b, R);
   op_permute_in(c, x_user, x, R);
   std::vector<double> bn, rn;
@@ -122,11 +162,21 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
   int total = 0;
   std::vector<cd> H((size_t)(m + 1) * m * R), gvec((size_t)(m + 1) * R), sn((size_t)m * R);
   std::vector<double> cs((size_t)m * R);
+  std::vector<double> xn;
+  g.norms(x, d_h, xn);
+  bool x_zero = true;
+  for (int r = 0; r < R; ++r) x_zero = x_zero && xn[r] == 0.0;
+  bool first = true;
   for (;;) {
-    // true residual with the FP64 operator
-    apply_matvec(c, x, w, R, SIE_PREC_FP64, 3);
-    k_sub<<<std::min(152 * 16, (int)((vs + 255) / 256)), 256, 0, c->stream>>>((int64_t)vs, b, w, w);
-    g.launch_check();
+    // true residual with the FP64 operator (r = b for a zero initial guess)
+    if (first && x_zero) {
+      SIE_CUDA(cudaMemcpyAsync(w, b, vs * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      apply_matvec(c, x, w, R, SIE_PREC_FP64, 3);
+      k_sub<<<std::min(152 * 16, (int)((vs + 255) / 256)), 256, 0, c->stream>>>((int64_t)vs, b, w, w);
+      g.launch_check();
+    }
+    first = false;
     g.norms(w, d_h, rn);
     bool any = false;
     for (int r = 0; r < R; ++r) {
@@ -160,8 +210,7 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
       // classical Gram-Schmidt, twice
       std::vector<zd> h1((size_t)(j + 1) * R), h2((size_t)(j + 1) * R);
       for (int pass = 0; pass < 2; ++pass) {
-        k_mdot<<<dim3(j + 1, R), 256, 0, c->stream>>>(n, R, V, vs, w, d_h);
-        g.launch_check();
+        g.mdot(V, vs, j + 1, w, d_h);
         k_orth<<<gv, 256, 0, c->stream>>>(n, R, j + 1, V, vs, d_h, w);
         g.launch_check();
         SIE_CUDA(cudaMemcpyAsync(pass == 0 ? h1.data() : h2.data(), d_h, (size_t)(j + 1) * R * sizeof(zd),
