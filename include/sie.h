@@ -130,6 +130,26 @@ sie_status sie_matvec_parts(sie_ctx *ctx, const void *x_dev, void *y_dev, int64_
  * sie_fill_nearfield with build_ilu. */
 sie_status ilu_apply(sie_ctx *ctx, const void *r_dev, void *z_dev, int64_t nrhs, sie_prec prec);
 
+/* Allocation-free variant of ilu_apply (the paper has no counterpart; this
+ * is a service of the library).  ilu_apply stages its vectors in work buffers
+ * that the context allocates with cudaMalloc on first use.  Callers that must
+ * not let a library allocate device memory during a step -- a host framework
+ * that owns all device memory through its own pool, or a latency-critical
+ * loop where cudaMalloc would synchronise the device -- call this instead: it
+ * computes the same z = (L U)^-1 r, with the same conventions, and allocates
+ * nothing.  Its scratch is one 16 MiB device array inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   - Limit: nrhs * n_rwg <= 174762; larger requests return SIE_EINVAL
+ *     before touching any buffer.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - All calls share the array (it keeps the last call's contents; every
+ *     element is written before it is read, so nothing needs clearing).
+ *     Calls whose GPU work overlaps -- on different streams, contexts or host
+ *     threads -- race on it; serialise them.
+ * Requires sie_fill_nearfield with build_ilu. */
+sie_status ilu_apply_noalloc(sie_ctx *ctx, const void *r_dev, void *z_dev, int64_t nrhs, sie_prec prec);
+
 /* Tested plane-wave excitation (Eqs. 20-21, Eq. 30) for nrhs incidences.
  * inc_host [nrhs][4] float64 = (theta_i, phi_i, pol, E0): the wave arrives
  * from direction (theta_i, phi_i), propagates along -r(theta_i, phi_i), with

@@ -24,7 +24,7 @@ STATUS = {0: "SIE_OK", 1: "SIE_EINVAL", 2: "SIE_ENOMEM", 3: "SIE_ECUDA", 4: "SIE
 
 EXPORTED = ["sie_create", "sie_destroy", "sie_last_error", "sie_build_mesh", "mlfmm_setup", "sie_fill_nearfield",
             "mlfmm_matvec", "sie_matvec_parts", "ilu_apply", "sie_plane_wave_rhs", "gmres_solve", "rcs_farfield",
-            "sie_near_export", "sie_stage_timing", "sie_query"]
+            "sie_near_export", "sie_stage_timing", "sie_query", "ilu_apply_noalloc"]
 
 
 class SieError(RuntimeError):
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         "sie_near_export": ([P, P, P, P, ctypes.POINTER(I64)], I32),
         "sie_query": ([P, I32, ctypes.POINTER(I64)], I32),
         "sie_stage_timing": ([P, I32, I64, I32, I32, ctypes.POINTER(D)], I32),
+        "ilu_apply_noalloc": ([P, P, P, I64, I32], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -159,6 +160,12 @@ def sie_matvec_parts(ctx, x, y, nrhs, prec=SIE_PREC_FP64, parts=3):
 
 def ilu_apply(ctx, r, z, nrhs, prec=SIE_PREC_FP64):
     _check(ctx, load_library().ilu_apply(ctx, _ptr(r), _ptr(z), int(nrhs), int(prec)))
+
+
+def ilu_apply_noalloc(ctx, r, z, nrhs, prec=SIE_PREC_FP64):
+    """ilu_apply without any device allocation (scratch: a fixed 16 MiB
+    array inside the library; nrhs * n_rwg <= 174762)."""
+    _check(ctx, load_library().ilu_apply_noalloc(ctx, _ptr(r), _ptr(z), int(nrhs), int(prec)))
 
 
 def sie_plane_wave_rhs(ctx, inc, b):
