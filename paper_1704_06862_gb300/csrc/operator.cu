@@ -388,11 +388,18 @@ __global__ void k_ilu_inbox(int ne, int nrhs, int forward, int box0, int staged,
   // packed column start: forward keeps rows j+1..n-1 of column j, backward rows 0..j-1
   auto pcol = [&](int j) { return forward ? j * (n - 1) - j * (j - 1) / 2 : j * (j - 1) / 2; };
   if (staged) {
+    // one 2x2 block is 4 complex values: copy it as 16-byte words, many in flight
+    constexpr int W = (int)(4 * sizeof(cx<T>) / 16);
+    const int4 *Dv = reinterpret_cast<const int4 *>(D);
+    int4 *Tv = reinterpret_cast<int4 *>(tri);
     for (int j = warp; j < n; j += nw) {
       int lo = forward ? j + 1 : 0, hi = forward ? n : j;
       int base = pcol(j) - lo;
-      for (int li = lo + lane; li < hi; li += 32)
-        for (int q = 0; q < 4; ++q) tri[4 * (base + li) + q] = D[4 * ((size_t)j * n + li) + q];
+      int cnt = (hi - lo) * W;
+      const int4 *src = Dv + ((size_t)j * n + lo) * W;
+      int4 *dst = Tv + (size_t)(base + lo) * W;
+#pragma unroll 4
+      for (int q = lane; q < cnt; q += 32) dst[q] = src[q];
     }
   }
   for (int r = 0; r < nrhs; ++r) {
@@ -577,7 +584,7 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
           c->ne, nrhs, row0, row1, fwd ? I.d_lo_ptr : I.d_up_ptr, fwd ? I.d_lo_col : I.d_up_col,
           (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? r : z, z);
       SIE_CHECK_LAUNCH();
-      k_ilu_inbox<T><<<cnt, 128, smem, c->stream>>>(c->ne, nrhs, fwd ? 1 : 0, first, staged, I.d_box_start,
+      k_ilu_inbox<T><<<cnt, 256, smem, c->stream>>>(c->ne, nrhs, fwd ? 1 : 0, first, staged, I.d_box_start,
                                                    I.d_dense_off, (const cx<T> *)tsel<T>::dense(I),
                                                    (const cx<T> *)tsel<T>::dinv(I), z);
       SIE_CHECK_LAUNCH();

@@ -20,34 +20,36 @@ typedef std::complex<double> cd;
 // partial sum per vector; stage 2 sums the partials.  Every V_i is read once.
 __global__ void k_mdot_part(int n, int nrhs, int nvec, int nblk, const zd *__restrict__ V, size_t vstride,
                             const zd *__restrict__ w, zd *__restrict__ part) {
-  __shared__ zd ws[1024];
-  __shared__ zd red[256];
+  __shared__ zd red[32][8];
   const int blk = blockIdx.x, r = blockIdx.y;
   const int chunk = (n + nblk - 1) / nblk;
   const int t0 = blk * chunk, t1 = min(n, t0 + chunk);
-  for (int base = t0; base < t1; base += 1024) {
-    const int cnt = min(1024, t1 - base);
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) ws[t] = w[(size_t)r * n + base + t];
-    __syncthreads();
-    for (int i = 0; i < nvec; ++i) {
-      const zd *a = V + (size_t)i * vstride + (size_t)r * n + base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // each thread keeps its (at most 4) elements of w in registers
+  zd wv[4];
+  int nv = 0;
+  for (int t = t0 + threadIdx.x; t < t1 && nv < 4; t += blockDim.x) wv[nv++] = w[(size_t)r * n + t];
+  for (int g0 = 0; g0 < nvec; g0 += 32) {
+    const int g1 = min(nvec, g0 + 32);
+    for (int i = g0; i < g1; ++i) {
+      const zd *a = V + (size_t)i * vstride + (size_t)r * n;
       zd acc;
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) acc = cfma(conj(a[t]), ws[t], acc);
-      red[threadIdx.x] = acc;
-      __syncthreads();
-      for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
+      int q = 0;
+      for (int t = t0 + threadIdx.x; t < t1 && q < 4; t += blockDim.x, ++q) acc = cfma(conj(a[t]), wv[q], acc);
+      for (int d = 16; d > 0; d >>= 1) {
+        acc.re += __shfl_down_sync(0xffffffffu, acc.re, d);
+        acc.im += __shfl_down_sync(0xffffffffu, acc.im, d);
       }
-      if (threadIdx.x == 0) {
-        zd *p = part + ((size_t)i * nrhs + r) * nblk + blk;
-        *p = (base == t0 ? zd() : *p) + red[0];
-      }
-      __syncthreads();
+      if (lane == 0) red[i - g0][warp] = acc;
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < g1 - g0; i += blockDim.x) {
+      zd acc;
+      for (int q = 0; q < 8; ++q) acc += red[i][q];
+      part[((size_t)(g0 + i) * nrhs + r) * nblk + blk] = acc;
+    }
+    __syncthreads();
   }
-  if (t0 >= t1 && threadIdx.x == 0)
-    for (int i = 0; i < nvec; ++i) part[((size_t)i * nrhs + r) * nblk + blk] = zd();
 }
 
 __global__ void k_mdot_sum(int nrhs, int nblk, const zd *__restrict__ part, zd *__restrict__ h) {
@@ -144,13 +146,14 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
     c->gm_w = dev_alloc(c, vs * sizeof(zd));
     c->gm_h = dev_alloc(c, (size_t)(m + 2) * R * sizeof(zd));
     c->gm_s = dev_alloc(c, (size_t)(m + 2) * R * sizeof(zd));
-    c->gm_part = dev_alloc(c, (size_t)(m + 2) * R * 304 * sizeof(zd));
+    c->gm_part = dev_alloc(c, (size_t)(m + 2) * R * ((n + 1023) / 1024) * sizeof(zd));
     c->gm_m = m;
     c->gm_R = R;
   }
   zd *V = (zd *)c->gm_V, *Z = (zd *)c->gm_Z, *b = (zd *)c->gm_b, *x = (zd *)c->gm_x, *w = (zd *)c->gm_w;
   zd *d_h = (zd *)c->gm_h, *d_s = (zd *)c->gm_s;
-  Gm g{c, n, R, std::max(1, std::min(304, (n + 1023) / 1024)), (zd *)c->gm_part};
+  // 256 threads x 4 elements per block
+  Gm g{c, n, R, std::max(1, (n + 1023) / 1024), (zd *)c->gm_part};  // chunks of <= 1024 elements
   op_permute_in(c, b_user, b, R);
   op_permute_in(c, x_user, x, R);
   std::vector<double> bn, rn;
