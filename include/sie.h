@@ -162,7 +162,11 @@ typedef struct {
   int32_t max_iters;   /* total inner iterations per right-hand side */
   double tol;          /* relative residual ||b - A x|| / ||b|| (FP64 operator) */
   int32_t prec;        /* sie_prec of the inner operator and preconditioner */
-  int32_t precond;     /* 0: none, 1: ILU(0) (right preconditioning) */
+  int32_t precond;     /* 0: none, 1: ILU(0), 2: ILU(0) followed by the learned
+                          correction (needs nnprec_train or nnprec_params; the
+                          correction is dropped for the rest of a solve as soon
+                          as a restart cycle fails to reduce the true residual),
+                          all as right preconditioning */
 } sie_solve_opts;
 
 typedef struct {
@@ -179,6 +183,49 @@ typedef struct {
  * SIE_ENOTCONV if any RHS did not reach tol. */
 sie_status gmres_solve(sie_ctx *ctx, const void *b_dev, void *x_dev, int64_t nrhs,
                        const sie_solve_opts *opts, sie_solve_stats *stats_host);
+
+/* Learned right preconditioner (not in the paper; an extension of its ILU
+ * preconditioner, Sect. "Simulation Results").  One MLP 128 -> 256 -> 256 -> 128
+ * with ReLU, shared by all leaf chunks (runs of <= 32 bases of one leaf box,
+ * 64 complex unknowns = 128 reals); z_c = (ILU^-1 v)_c + |v_c| NN(v_c/|v_c|).
+ * Weights and activations BF16, FP32 accumulation, Adam with FP32 masters.
+ * Training pairs are generated by the solver itself: recording solves of
+ * FGMRES(record_restart) with ILU(0) for the training incidences store the
+ * iterate x_k and true residual r_k at every restart; after convergence
+ * e_k = x* - x_k, and the network regresses (e_k - ILU^-1 r_k)_c / |r_k,c| on
+ * r_k,c / |r_k,c| chunk by chunk (mean squared error).  Synchronous. */
+typedef struct {
+  const double *train_inc;  /* host [ntrain][4] incidences, as sie_plane_wave_rhs */
+  int32_t ntrain;
+  int32_t record_restart;   /* restart length of the recording solves (pairs per restart) */
+  int32_t max_pairs;        /* cap on recorded pairs */
+  int32_t epochs;
+  int32_t batch;            /* chunk samples per Adam step (>= 64) */
+  double lr;                /* Adam step size */
+  uint64_t seed;            /* weight initialisation and batch shuffling */
+} sie_nn_opts;
+
+typedef struct {
+  int32_t pairs;            /* recorded (residual, error) pairs */
+  int64_t samples;          /* chunk samples = pairs * chunks */
+  double loss_first;        /* mean loss of the first and last epoch */
+  double loss_last;
+  double ms;                /* device time of recording + training */
+} sie_nn_stats;
+
+sie_status nnprec_train(sie_ctx *ctx, const sie_nn_opts *opts, sie_nn_stats *stats);
+
+/* Get (set = 0) or set (set != 0) the network's FP32 master parameters,
+ * params_host [131712] = W1 [256][128], b1 [256], W2 [256][256], b2 [256],
+ * W3 [128][256], b3 [128], row-major.  Setting marks the network ready. */
+sie_status nnprec_params(sie_ctx *ctx, float *params_host, int32_t set);
+
+/* Loss and parameter gradient of the network on n given samples (for
+ * verification): X_host [n][128] inputs (rounded to BF16 on the device),
+ * T_host [n][128] targets; loss_out = sum (y - t)^2 / (2 n); grad_host
+ * [131712] FP32, same layout as nnprec_params. */
+sie_status nnprec_loss_grad(sie_ctx *ctx, const float *X_host, const float *T_host, int64_t n, double *loss_out,
+                            float *grad_host);
 
 /* Bistatic radar cross section (Eqs. 27-29) of solutions x_dev (complex128
  * [nrhs][n_rwg][2], user order) at nobs directions obs_host [nobs][2] =

@@ -24,7 +24,8 @@ STATUS = {0: "SIE_OK", 1: "SIE_EINVAL", 2: "SIE_ENOMEM", 3: "SIE_ECUDA", 4: "SIE
 
 EXPORTED = ["sie_create", "sie_destroy", "sie_last_error", "sie_build_mesh", "mlfmm_setup", "sie_fill_nearfield",
             "mlfmm_matvec", "sie_matvec_parts", "ilu_apply", "sie_plane_wave_rhs", "gmres_solve", "rcs_farfield",
-            "sie_near_export", "sie_stage_timing", "sie_query", "ilu_apply_noalloc"]
+            "sie_near_export", "sie_stage_timing", "sie_query", "ilu_apply_noalloc", "nnprec_train",
+            "nnprec_params", "nnprec_loss_grad"]
 
 
 class SieError(RuntimeError):
@@ -80,6 +81,9 @@ def load_library(path: str = LIB_PATH):
         "sie_query": ([P, I32, ctypes.POINTER(I64)], I32),
         "sie_stage_timing": ([P, I32, I64, I32, I32, ctypes.POINTER(D)], I32),
         "ilu_apply_noalloc": ([P, P, P, I64, I32], I32),
+        "nnprec_train": ([P, P, P], I32),
+        "nnprec_params": ([P, P, I32], I32),
+        "nnprec_loss_grad": ([P, P, P, I64, ctypes.POINTER(D), P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -207,6 +211,49 @@ def sie_stage_timing(ctx, stage, nrhs=1, prec=SIE_PREC_FP64, reps=10):
     ms = ctypes.c_double()
     _check(ctx, load_library().sie_stage_timing(ctx, int(stage), int(nrhs), int(prec), int(reps), ctypes.byref(ms)))
     return ms.value
+
+
+class sie_nn_opts(ctypes.Structure):
+    _fields_ = [("train_inc", ctypes.c_void_p), ("ntrain", ctypes.c_int32), ("record_restart", ctypes.c_int32),
+                ("max_pairs", ctypes.c_int32), ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("lr", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class sie_nn_stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int32), ("samples", ctypes.c_int64), ("loss_first", ctypes.c_double),
+                ("loss_last", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+NN_PARAMS = 128 * 256 + 256 + 256 * 256 + 256 + 256 * 128 + 128
+
+
+def nnprec_train(ctx, train_inc, record_restart=5, max_pairs=256, epochs=20, batch=2048, lr=1e-3, seed=2017):
+    inc = np.ascontiguousarray(np.atleast_2d(train_inc), np.float64)
+    o = sie_nn_opts(_ptr(inc), len(inc), int(record_restart), int(max_pairs), int(epochs), int(batch), float(lr),
+                    int(seed))
+    st = sie_nn_stats()
+    _check(ctx, load_library().nnprec_train(ctx, ctypes.byref(o), ctypes.byref(st)))
+    return dict(pairs=st.pairs, samples=st.samples, loss_first=st.loss_first, loss_last=st.loss_last, ms=st.ms)
+
+
+def nnprec_params(ctx, params=None):
+    """Return the FP32 master parameters, or set them when ``params`` is given."""
+    if params is None:
+        out = np.zeros(NN_PARAMS, np.float32)
+        _check(ctx, load_library().nnprec_params(ctx, _ptr(out), 0))
+        return out
+    p = np.ascontiguousarray(params, np.float32)
+    _check(ctx, load_library().nnprec_params(ctx, _ptr(p), 1))
+    return p
+
+
+def nnprec_loss_grad(ctx, X, T):
+    X = np.ascontiguousarray(X, np.float32)
+    T = np.ascontiguousarray(T, np.float32)
+    loss = ctypes.c_double()
+    g = np.zeros(NN_PARAMS, np.float32)
+    _check(ctx, load_library().nnprec_loss_grad(ctx, _ptr(X), _ptr(T), len(X), ctypes.byref(loss), _ptr(g)))
+    return loss.value, g
 
 
 def sie_query(ctx, key):

@@ -174,7 +174,8 @@ struct sie_ctx {
   void *d_stage = nullptr;                        // small host-to-device staging area
   size_t stage_bytes = 0;
   // Krylov storage of the last solve shape (restart m, nrhs R)
-  int gm_m = 0, gm_R = 0;
+  int gm_m = 0, gm_R = 0, gw_R = 0;
+  void *nn = nullptr;  // learned-preconditioner state (nn.cu)
   void *gm_V = nullptr, *gm_Z = nullptr, *gm_b = nullptr, *gm_x = nullptr, *gm_w = nullptr;
   void *gm_h = nullptr, *gm_s = nullptr, *gm_part = nullptr;
 };
@@ -218,3 +219,16 @@ void apply_ilu(sie_ctx *c, const zd *r, zd *z, int nrhs, sie_prec prec);
 // ------------------------------------------------------------------ solver (solve.cu)
 sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int nrhs, const sie_solve_opts *o,
                      sie_solve_stats *st);
+struct Recorder {  // training pairs taken at the restarts of one solve
+  zd *x, *r;       // [cap][2 ne] internal order
+  int cap;
+  int *count;
+};
+sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int max_iters, double tol,
+                              sie_prec prec, int precond, Recorder *rec, sie_solve_stats *st);
+void op_sub(sie_ctx *c, const zd *a, const zd *b, zd *out, int64_t n);
+
+// ------------------------------------------------------------------ learned preconditioner (nn.cu)
+bool nn_ready(sie_ctx *c);
+void nn_apply(sie_ctx *c, const zd *v, zd *z, int nrhs);
+void nn_free(sie_ctx *c);

@@ -144,6 +144,7 @@ extern "C" void sie_destroy(sie_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  nn_free(c);
   for (auto &b : c->bufs) cudaFree(b.p);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -1021,7 +1022,9 @@ extern "C" sie_status gmres_solve(sie_ctx *c, const void *b, void *x, int64_t nr
     SIE_REQUIRE(b && x && o && st && nrhs >= 1 && nrhs <= 4096, SIE_EINVAL, "gmres_solve: bad arguments");
     SIE_REQUIRE(o->restart >= 1 && o->restart <= 500 && o->max_iters >= 1 && o->tol > 0, SIE_EINVAL,
                 "gmres_solve: bad options");
+    SIE_REQUIRE(o->precond >= 0 && o->precond <= 2, SIE_EINVAL, "gmres_solve: precond must be 0, 1 or 2");
     SIE_REQUIRE(o->precond == 0 || c->ilu.ready, SIE_ESTATE, "gmres_solve: ILU requested but not built");
+    SIE_REQUIRE(o->precond != 2 || nn_ready(c), SIE_ESTATE, "gmres_solve: learned preconditioner not trained");
     rc = run_gmres(c, (const zd *)b, (zd *)x, (int)nrhs, o, st);
   });
   return g != SIE_OK ? g : rc;

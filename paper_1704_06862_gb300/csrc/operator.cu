@@ -3,6 +3,7 @@
 // Every kernel is templated on the real type: double (plain form) or float
 // (mixed form, FP32 complex with FP32 accumulation).
 #include <algorithm>
+#include <type_traits>
 
 #include "common.h"
 
@@ -63,18 +64,45 @@ __global__ void k_near_spmv(int ne, int nrhs, const int *__restrict__ row_ptr, c
   int lane = threadIdx.x & 31;
   if (warp >= ne) return;
   int s = row_ptr[warp], e = row_ptr[warp + 1];
+  // a 2x2 complex block is 4 (FP32) or 8 (FP64) 8-byte words: read it as 16-byte vectors
+  typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V16;
+  constexpr int NV = (int)(4 * sizeof(cx<T>) / sizeof(V16));
+  const V16 *Bv = reinterpret_cast<const V16 *>(B);
   for (int r = 0; r < nrhs; ++r) {
     const cx<T> *xr = x + (size_t)r * ne * 2;
     cx<T> a0, a1;
-    for (int q = s + lane; q < e; q += 32) {
-      int cc = col[q];
-      const cx<T> *b = B + 4 * (size_t)q;
-      cx<T> b0 = b[0], b1 = b[1], b2 = b[2], b3 = b[3];
+    int q = s + lane;
+    // two blocks in flight per lane
+    for (; q + 32 < e; q += 64) {
+      int c0 = __ldg(col + q), c1 = __ldg(col + q + 32);
+      V16 u0[NV], u1[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        u0[v] = __ldg(Bv + (size_t)q * NV + v);
+        u1[v] = __ldg(Bv + (size_t)(q + 32) * NV + v);
+      }
+      cx<T> xj0 = xr[2 * c0], xm0 = xr[2 * c0 + 1], xj1 = xr[2 * c1], xm1 = xr[2 * c1 + 1];
+      const cx<T> *b0 = reinterpret_cast<const cx<T> *>(u0), *b1 = reinterpret_cast<const cx<T> *>(u1);
+      a0 = cfma(b0[0], xj0, a0);
+      a0 = cfma(b0[1], xm0, a0);
+      a1 = cfma(b0[2], xj0, a1);
+      a1 = cfma(b0[3], xm0, a1);
+      a0 = cfma(b1[0], xj1, a0);
+      a0 = cfma(b1[1], xm1, a0);
+      a1 = cfma(b1[2], xj1, a1);
+      a1 = cfma(b1[3], xm1, a1);
+    }
+    for (; q < e; q += 32) {
+      int cc = __ldg(col + q);
+      V16 u[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) u[v] = __ldg(Bv + (size_t)q * NV + v);
+      const cx<T> *b = reinterpret_cast<const cx<T> *>(u);
       cx<T> xj = xr[2 * cc], xm = xr[2 * cc + 1];
-      a0 = cfma(b0, xj, a0);
-      a0 = cfma(b1, xm, a0);
-      a1 = cfma(b2, xj, a1);
-      a1 = cfma(b3, xm, a1);
+      a0 = cfma(b[0], xj, a0);
+      a0 = cfma(b[1], xm, a0);
+      a1 = cfma(b[2], xj, a1);
+      a1 = cfma(b[3], xm, a1);
     }
     a0 = warp_sum(a0);
     a1 = warp_sum(a1);

@@ -130,19 +130,22 @@ struct Gm {
 
 }  // namespace
 
-sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_solve_opts *o, sie_solve_stats *st) {
-  const int m = o->restart;
+// Restarted FGMRES on internal-order FP64 vectors b, x (x holds the initial
+// guess).  precond: 0 none, 1 ILU(0), 2 ILU(0) followed by the learned
+// correction; the learned part is switched off for the rest of the solve as
+// soon as a restart cycle fails to reduce the true residual.  With a recorder
+// (one right-hand side), the iterate and true residual of every restart
+// before convergence are copied out as training pairs.
+sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int max_iters, double tol,
+                              sie_prec prec, int precond, Recorder *rec, sie_solve_stats *st) {
   const int n = 2 * c->ne;
   const size_t vs = (size_t)R * n;
-  sie_prec prec = o->prec == 1 ? SIE_PREC_MIXED : SIE_PREC_FP64;
   ensure_work(c, R);
   // Krylov storage (allocated once per capacity and kept in the context)
   static_assert(sizeof(zd) == 16, "complex layout");
   if (c->gm_m != m || c->gm_R != R) {
     c->gm_V = dev_alloc(c, (size_t)(m + 1) * vs * sizeof(zd));
     c->gm_Z = dev_alloc(c, (size_t)m * vs * sizeof(zd));
-    c->gm_b = dev_alloc(c, vs * sizeof(zd));
-    c->gm_x = dev_alloc(c, vs * sizeof(zd));
     c->gm_w = dev_alloc(c, vs * sizeof(zd));
     c->gm_h = dev_alloc(c, (size_t)(m + 2) * R * sizeof(zd));
     c->gm_s = dev_alloc(c, (size_t)(m + 2) * R * sizeof(zd));
@@ -150,12 +153,12 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
     c->gm_m = m;
     c->gm_R = R;
   }
-  zd *V = (zd *)c->gm_V, *Z = (zd *)c->gm_Z, *b = (zd *)c->gm_b, *x = (zd *)c->gm_x, *w = (zd *)c->gm_w;
+  zd *V = (zd *)c->gm_V, *Z = (zd *)c->gm_Z, *w = (zd *)c->gm_w;
   zd *d_h = (zd *)c->gm_h, *d_s = (zd *)c->gm_s;
   // 256 threads x 4 elements per block
   Gm g{c, n, R, std::max(1, (n + 1023) / 1024), (zd *)c->gm_part};  // chunks of <= 1024 elements
-  op_permute_in(c, b_user, b, R);
-  op_permute_in(c, x_user, x, R);
+  bool use_nn = precond == 2 && nn_ready(c);
+  std::vector<double> prev_res(R, HUGE_VAL);
   std::vector<double> bn, rn;
   g.norms(b, d_h, bn);
   std::vector<int> iters(R, 0), restarts(R, 0), active(R, 1);
@@ -189,10 +192,17 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
         active[r] = 0;
         continue;
       }
-      active[r] = relres[r] > o->tol && iters[r] < o->max_iters;
+      active[r] = relres[r] > tol && iters[r] < max_iters;
       if (active[r]) any = true;
+      if (use_nn && rn[r] >= prev_res[r]) use_nn = false;  // fall back to plain ILU(0)
+      prev_res[r] = rn[r];
     }
     if (!any || status != SIE_OK) break;
+    if (rec && R == 1 && *rec->count < rec->cap) {
+      int k = (*rec->count)++;
+      SIE_CUDA(cudaMemcpyAsync(rec->x + (size_t)k * n, x, n * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
+      SIE_CUDA(cudaMemcpyAsync(rec->r + (size_t)k * n, w, n * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
+    }
     // V0 = r / beta (zero for finished right-hand sides)
     std::vector<zd> sc(R);
     for (int r = 0; r < R; ++r) sc[r] = active[r] ? zd(1.0 / rn[r], 0.0) : zd();
@@ -207,8 +217,9 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
     int jend = 0;
     for (int j = 0; j < m; ++j) {
       zd *Vj = V + (size_t)j * vs, *Zj = Z + (size_t)j * vs;
-      if (o->precond == 1) apply_ilu(c, Vj, Zj, R, prec);
+      if (precond >= 1) apply_ilu(c, Vj, Zj, R, prec);
       else SIE_CUDA(cudaMemcpyAsync(Zj, Vj, vs * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
+      if (use_nn) nn_apply(c, Vj, Zj, R);
       apply_matvec(c, Zj, w, R, prec, 3);
       // classical Gram-Schmidt, twice
       std::vector<zd> h1((size_t)(j + 1) * R), h2((size_t)(j + 1) * R);
@@ -264,7 +275,7 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
         iters[r]++;
         double est = std::abs(gr[j + 1]) / bn[r];
         if (!std::isfinite(est)) status = SIE_EBREAKDOWN;
-        if (est > o->tol && iters[r] < o->max_iters) all_done = false;
+        if (est > tol && iters[r] < max_iters) all_done = false;
       }
       total++;
       jend = j + 1;
@@ -289,17 +300,42 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
     g.launch_check();
     if (status != SIE_OK) break;
   }
-  op_permute_out(c, x, x_user, R);
   SIE_CUDA(cudaStreamSynchronize(c->stream));
   bool conv = true;
   for (int r = 0; r < R; ++r) {
-    st[r].iters = iters[r];
-    st[r].restarts = restarts[r];
-    st[r].rel_residual = relres[r];
-    st[r].converged = relres[r] <= o->tol ? 1 : 0;
-    if (!st[r].converged) conv = false;
+    if (st) {
+      st[r].iters = iters[r];
+      st[r].restarts = restarts[r];
+      st[r].rel_residual = relres[r];
+      st[r].converged = relres[r] <= tol ? 1 : 0;
+    }
+    if (!(relres[r] <= tol)) conv = false;
   }
   (void)total;
   if (status != SIE_OK) return status;
   return conv ? SIE_OK : SIE_ENOTCONV;
+}
+
+sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_solve_opts *o, sie_solve_stats *st) {
+  const size_t vs = (size_t)R * 2 * c->ne;
+  if (c->gw_R != R) {
+    c->gm_b = dev_alloc(c, vs * sizeof(zd));
+    c->gm_x = dev_alloc(c, vs * sizeof(zd));
+    c->gw_R = R;
+  }
+  zd *b = (zd *)c->gm_b, *x = (zd *)c->gm_x;
+  op_permute_in(c, b_user, b, R);
+  op_permute_in(c, x_user, x, R);
+  sie_prec prec = o->prec == 1 ? SIE_PREC_MIXED : SIE_PREC_FP64;
+  sie_status rc = run_gmres_internal(c, b, x, R, o->restart, o->max_iters, o->tol, prec, o->precond, nullptr, st);
+  op_permute_out(c, x, x_user, R);
+  SIE_CUDA(cudaStreamSynchronize(c->stream));
+  return rc;
+}
+
+// out = a - b
+void op_sub(sie_ctx *c, const zd *a, const zd *b, zd *out, int64_t n) {
+  k_sub<<<std::max(1, (int)std::min<int64_t>(152 * 16, (n + 255) / 256)), 256, 0, c->stream>>>(n, a, b, out);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
 }

@@ -1,0 +1,67 @@
+"""Learned preconditioner on the GPU: gradients against the oracle network,
+and training on solver-generated pairs followed by a solve whose converged
+answer must not change (only the iteration count may).
+
+Tolerances: loss 1e-4 and gradient 2e-2 relative L2 (the device stores
+activations in BF16 after FP32 accumulation; the oracle rounds the same
+activations after FP64 accumulation, so a few roundings differ)."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1704_06862_gb300 as sie  # noqa: E402
+from paper_1704_06862_gb300 import geometry as geo  # noqa: E402
+from oracle import nn  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def solver():
+    import __graft_entry__ as g
+    g.build()
+    s = sie.Solver(geo.homogeneous_sphere(nu=8, radius=0.5, eps_r=4.0), levels=3)
+    yield s
+    s.close()
+
+
+def test_gradient_matches_oracle(solver):
+    rng = np.random.default_rng(3)
+    theta = (rng.standard_normal(sie.NN_PARAMS) * 0.05).astype(np.float32)
+    sie.nnprec_params(solver.ctx, theta)
+    X = rng.standard_normal((300, 128)).astype(np.float32)
+    T = rng.standard_normal((300, 128)).astype(np.float32)
+    loss, g = sie.nnprec_loss_grad(solver.ctx, X, T)
+    lref, gref = nn.loss_grad(theta.astype(np.float64), X.astype(np.float64), T.astype(np.float64), bf16_store=True)
+    assert abs(loss - lref) <= 1e-4 * lref
+    assert np.linalg.norm(g - gref) <= 2e-2 * np.linalg.norm(gref)
+    assert np.allclose(sie.nnprec_params(solver.ctx), theta)
+
+
+def test_training_and_solve_keep_the_answer(solver):
+    s = solver
+    rng = np.random.default_rng(2017)
+    th = np.arccos(rng.uniform(-1, 1, 4))
+    ph = rng.uniform(0, 2 * np.pi, 4)
+    train = np.stack([th, ph, np.zeros(4), np.ones(4)], axis=1)
+    st = sie.nnprec_train(s.ctx, train, record_restart=5, max_pairs=64, epochs=30, batch=1024, lr=1e-3, seed=7)
+    assert st["pairs"] > 0 and st["loss_last"] < st["loss_first"]
+    d = np.load(os.path.join(HERE, "golden", "sphere_c1.npz"))
+    b = torch.zeros((1, s.ne, 2), dtype=torch.complex128, device="cuda")
+    sie.sie_plane_wave_rhs(s.ctx, [[0.0, 0.0, 0.0, 1.0]], b)
+    res = {}
+    for pc in (1, 2):
+        x = torch.zeros_like(b)
+        out = sie.gmres_solve(s.ctx, b, x, 1, restart=50, max_iters=500, tol=1e-6, prec=sie.SIE_PREC_MIXED,
+                              precond=pc)
+        torch.cuda.synchronize()
+        xs = x.cpu().numpy().reshape(-1)
+        res[pc] = (out[0]["iters"], np.linalg.norm(xs - d["xs"]) / np.linalg.norm(d["xs"]))
+        assert out[0]["converged"]
+    print(f"ILU(0) iters {res[1][0]}, ILU(0)+network iters {res[2][0]}; training {st}")
+    assert res[2][1] < 1e-3 and res[1][1] < 1e-3
+    assert res[2][0] <= 1.25 * res[1][0] + 2
