@@ -159,6 +159,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-nn", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -190,15 +191,16 @@ def main():
     x = s.vec(1)
     sie.sie_plane_wave_rhs(s.ctx, inc, b_dev)
 
-    def solve(prec, e2e):
+    def solve(prec, e2e, precond=1):
         if e2e:                       # host incidence -> device excitation
             sie.sie_plane_wave_rhs(s.ctx, inc, b_dev)
         x.zero_()
-        st = sie.gmres_solve(s.ctx, b_dev, x, 1, restart=RESTART, max_iters=3000, tol=TOL, prec=prec, precond=1)
+        st = sie.gmres_solve(s.ctx, b_dev, x, 1, restart=RESTART, max_iters=3000, tol=TOL, prec=prec,
+                             precond=precond)
         rcs = sie.rcs_farfield(s.ctx, x, 1, obs)  # device -> host
         return st[0], rcs
 
-    def timed(prec, steps, e2e):
+    def timed(prec, steps, e2e, precond=1):
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -207,7 +209,7 @@ def main():
         e0.record(stream)
         out = None
         for _ in range(steps):
-            out = solve(prec, e2e)
+            out = solve(prec, e2e, precond)
         e1.record(stream)
         torch.cuda.synchronize()
         if ws > 1:
@@ -234,6 +236,20 @@ def main():
         db = 10 * np.log10(np.maximum(rcs[:, :, 0], 1e-30)) - 10 * np.log10(np.maximum(rcs64[:, :, 0], 1e-30))
         plain = {"ms_per_solve": ms64, "iters": st64["iters"], "rel_residual": st64["rel_residual"],
                  "speedup_chosen_vs_plain": ms64 / ms, "rcs_max_abs_db_diff_vs_plain": float(np.max(np.abs(db)))}
+    # learned preconditioner: trained on solver-recorded pairs of seeded random incidences
+    learned = None
+    if not args.no_nn:
+        rng = np.random.default_rng(2017)
+        nt = 8
+        train = np.stack([np.arccos(rng.uniform(-1, 1, nt)), rng.uniform(0, 2 * np.pi, nt), np.zeros(nt),
+                          np.ones(nt)], axis=1)
+        tst = sie.nnprec_train(s.ctx, train, record_restart=5, max_pairs=96, epochs=12, batch=4096, lr=1e-3, seed=7)
+        solve(sie.SIE_PREC_MIXED, False, 2)
+        ms_nn, (st_nn, rcs_nn) = timed(sie.SIE_PREC_MIXED, args.steps, False, 2)
+        dbn = 10 * np.log10(np.maximum(rcs_nn[:, :, 0], 1e-30)) - 10 * np.log10(np.maximum(rcs[:, :, 0], 1e-30))
+        learned = {"train": tst, "ms_per_solve": ms_nn, "iters": st_nn["iters"], "rel_residual": st_nn["rel_residual"],
+                   "ilu_only_ms_per_solve": ms, "ilu_only_iters": st["iters"], "speedup_vs_ilu_only": ms / ms_nn,
+                   "rcs_max_abs_db_diff_vs_ilu_only": float(np.max(np.abs(dbn)))}
     # Mie check of the chosen form
     mie_db = None
     try:
@@ -280,7 +296,7 @@ def main():
         "iters": st["iters"], "rel_residual": st["rel_residual"], "setup_s": t_setup,
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
                 "d2h_bytes_per_step": int(rcs.nbytes)},
-        "plain_fp64": plain, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
+        "plain_fp64": plain, "learned_precond": learned, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
     }
     if rank == 0:

@@ -187,13 +187,14 @@ sie_status gmres_solve(sie_ctx *ctx, const void *b_dev, void *x_dev, int64_t nrh
 /* Learned right preconditioner (not in the paper; an extension of its ILU
  * preconditioner, Sect. "Simulation Results").  One MLP 128 -> 256 -> 256 -> 128
  * with ReLU, shared by all leaf chunks (runs of <= 32 bases of one leaf box,
- * 64 complex unknowns = 128 reals); z_c = (ILU^-1 v)_c + |v_c| NN(v_c/|v_c|).
+ * 64 complex unknowns = 128 reals); with u = ILU^-1 v,
+ * z_c = u_c + |u_c| NN(u_c/|u_c|) (a learned local correction of the ILU output).
  * Weights and activations BF16, FP32 accumulation, Adam with FP32 masters.
  * Training pairs are generated by the solver itself: recording solves of
  * FGMRES(record_restart) with ILU(0) for the training incidences store the
  * iterate x_k and true residual r_k at every restart; after convergence
- * e_k = x* - x_k, and the network regresses (e_k - ILU^-1 r_k)_c / |r_k,c| on
- * r_k,c / |r_k,c| chunk by chunk (mean squared error).  Synchronous. */
+ * e_k = x* - x_k; with u = ILU^-1 r_k the network regresses (e_k - u)_c / |u_c|
+ * on u_c / |u_c| chunk by chunk (mean squared error).  Synchronous. */
 typedef struct {
   const double *train_inc;  /* host [ntrain][4] incidences, as sie_plane_wave_rhs */
   int32_t ntrain;

@@ -175,6 +175,8 @@ struct sie_ctx {
   size_t stage_bytes = 0;
   // Krylov storage of the last solve shape (restart m, nrhs R)
   int gm_m = 0, gm_R = 0, gw_R = 0;
+  int64_t work_gen = 0;     // bumped whenever work buffers are (re)allocated
+  void *graphs = nullptr;   // captured per-step operator graphs (solve.cu)
   void *nn = nullptr;  // learned-preconditioner state (nn.cu)
   void *gm_V = nullptr, *gm_Z = nullptr, *gm_b = nullptr, *gm_x = nullptr, *gm_w = nullptr;
   void *gm_h = nullptr, *gm_s = nullptr, *gm_part = nullptr;
@@ -227,6 +229,7 @@ struct Recorder {  // training pairs taken at the restarts of one solve
 sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int max_iters, double tol,
                               sie_prec prec, int precond, Recorder *rec, sie_solve_stats *st);
 void op_sub(sie_ctx *c, const zd *a, const zd *b, zd *out, int64_t n);
+void graphs_free(sie_ctx *c);
 
 // ------------------------------------------------------------------ learned preconditioner (nn.cu)
 bool nn_ready(sie_ctx *c);

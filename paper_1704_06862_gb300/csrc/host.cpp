@@ -53,6 +53,7 @@ void ensure_work(sie_ctx *c, int64_t nrhs) {
   }
   c->d_scratch = dev_alloc(c, scratch);
   c->nrhs_cap = nrhs;
+  c->work_gen++;
 }
 
 // ------------------------------------------------------------------ special functions
@@ -145,6 +146,7 @@ extern "C" void sie_destroy(sie_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   nn_free(c);
+  graphs_free(c);
   for (auto &b : c->bufs) cudaFree(b.p);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -1,9 +1,10 @@
 // Learned right preconditioner: one MLP 128 -> 256 -> 256 -> 128 (ReLU) shared
 // by all leaf chunks (<= 32 bases of one leaf box, 64 complex unknowns).
-// Applied after ILU(0) inside flexible GMRES:
-//     z_c = (ILU^-1 v)_c + |v_c| NN(v_c / |v_c|)
+// Applied after ILU(0) inside flexible GMRES, u = ILU^-1 v:
+//     z_c = u_c + |u_c| NN(u_c / |u_c|)
 // trained on residual/error pairs (r_k, e_k = x* - x_k) that the solver
-// records at its restarts, with target e_k - ILU^-1 r_k.  Weights and
+// records at its restarts, with input u = ILU^-1 r_k and target
+// (e_k - u)_c / |u_c|: a learned local correction of the ILU output.  Weights and
 // activations are stored in BF16, products accumulate in FP32, Adam keeps FP32
 // master weights.  Every step runs in the kernels below.
 #include <cuda_bf16.h>
@@ -299,7 +300,9 @@ void nn_apply(sie_ctx *c, const zd *v, zd *z, int nrhs) {
   NnState &S = nn(c);
   const int ne2 = 2 * c->ne;
   for (int r = 0; r < nrhs; ++r) {
-    k_chunk_gather<<<S.nchunk, 128, 0, c->stream>>>(S.nchunk, S.d_cstart, S.d_clen, v + (size_t)r * ne2, S.X, S.nrm);
+    // input: the ILU(0) output already in z (u = ILU^-1 v), chunk by chunk
+    (void)v;
+    k_chunk_gather<<<S.nchunk, 128, 0, c->stream>>>(S.nchunk, S.d_cstart, S.d_clen, z + (size_t)r * ne2, S.X, S.nrm);
     SIE_CHECK_LAUNCH();
     nn_forward(c, S, S.nchunk, 0);
     k_chunk_scatter<<<S.nchunk, 64, 0, c->stream>>>(S.nchunk, S.d_cstart, S.d_clen, S.Y, S.nrm, z + (size_t)r * ne2);
@@ -352,7 +355,7 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
       }
     }
     SIE_REQUIRE(npairs > 0, SIE_EINVAL, "nnprec_train: the recording solves produced no pairs");
-    // 2. samples: per pair and chunk, input r_c / |r_c|, target (e - ILU^-1 r)_c / |r_c|
+    // 2. samples: per pair and chunk, u = ILU^-1 r, input u_c / |u_c|, target (e - u)_c / |u_c|
     const int64_t nsamp = (int64_t)npairs * S.nchunk;
     SIE_REQUIRE(nsamp < (1LL << 31) / D1, SIE_EINVAL, "nnprec_train: too many samples");
     nn_alloc(c, (int)nsamp);
@@ -360,7 +363,7 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
     for (int k = 0; k < npairs; ++k) {
       zd *rk = rec_r + (size_t)k * ne2, *ek = rec_x + (size_t)k * ne2;
       apply_ilu(c, rk, zilu, 1, SIE_PREC_FP64);
-      k_chunk_gather<<<S.nchunk, 128, 0, c->stream>>>(S.nchunk, S.d_cstart, S.d_clen, rk,
+      k_chunk_gather<<<S.nchunk, 128, 0, c->stream>>>(S.nchunk, S.d_cstart, S.d_clen, zilu,
                                                       S.X + (size_t)k * S.nchunk * D0, S.nrm + (size_t)k * S.nchunk);
       k_chunk_target<<<S.nchunk, 128, 0, c->stream>>>(S.nchunk, S.d_cstart, S.d_clen, ek, zilu,
                                                       S.nrm + (size_t)k * S.nchunk, T + (size_t)k * S.nchunk * D3);

@@ -167,6 +167,14 @@ __global__ void k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
   const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1;
   cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [3][Kc]
   cx<T> *G = A + 3 * Kc;                            // [3][nthc][Np]
+  T *Ps = reinterpret_cast<T *>(G + 3 * nthc * Np);  // Phi [Np][Nc], then Theta+ and Theta- [nthp][nthc]
+  T *Tps = Ps + Np * Nc, *Tms = Tps + (Lp + 1) * nthc;
+  for (int t = threadIdx.x; t < Np * Nc; t += blockDim.x) Ps[t] = Phi[t];
+  for (int t = threadIdx.x; t < (Lp + 1) * nthc; t += blockDim.x) {
+    Tps[t] = Thp[t];
+    Tms[t] = Thm[t];
+  }
+  __syncthreads();
   const int c = blockIdx.x, jm = blockIdx.y, o = oct[c];
   const int nG = 3 * nthc * Np;
   for (int r = 0; r < nrhs; ++r) {
@@ -180,7 +188,7 @@ __global__ void k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
     for (int idx = threadIdx.x; idx < nG; idx += blockDim.x) {
       int x = idx / (nthc * Np), rem = idx - x * nthc * Np, ic = rem / Np, jp = rem - ic * Np;
       const cx<T> *row = A + x * Kc + ic * Nc;
-      const T *ph = Phi + (size_t)jp * Nc;
+      const T *ph = Ps + jp * Nc;
       cx<T> acc;
       for (int jc = 0; jc < Nc; ++jc) {
         acc.re = fma(ph[jc], row[jc].re, acc.re);
@@ -196,7 +204,7 @@ __global__ void k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
         const cx<T> *g = G + (size_t)x * nthc * Np;
         cx<T> acc;
         for (int ic = 0; ic < nthc; ++ic) {
-          T a = Thp[ip * nthc + ic], bq = Thm[ip * nthc + ic];
+          T a = Tps[ip * nthc + ic], bq = Tms[ip * nthc + ic];
           cx<T> g1 = g[ic * Np + jp], g2 = g[ic * Np + jq];
           acc.re = fma(a, g1.re, fma(bq, g2.re, acc.re));
           acc.im = fma(a, g1.im, fma(bq, g2.im, acc.im));
@@ -240,6 +248,14 @@ __global__ void k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
   const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1, nthp = Lp + 1;
   cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [3][Kp]
   cx<T> *G = A + 3 * Kp;                            // [3][nthc][Np]
+  T *Ps = reinterpret_cast<T *>(G + 3 * nthc * Np);  // Phi [Np][Nc], then Theta+ and Theta- [nthp][nthc]
+  T *Tps = Ps + Np * Nc, *Tms = Tps + (Lp + 1) * nthc;
+  for (int t = threadIdx.x; t < Np * Nc; t += blockDim.x) Ps[t] = Phi[t];
+  for (int t = threadIdx.x; t < (Lp + 1) * nthc; t += blockDim.x) {
+    Tps[t] = Thp[t];
+    Tms[t] = Thm[t];
+  }
+  __syncthreads();
   const int c = blockIdx.x, jm = blockIdx.y, pb = parent[c], o = oct[c];
   const int nG = 3 * nthc * Np;
   for (int r = 0; r < nrhs; ++r) {
@@ -257,7 +273,7 @@ __global__ void k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
         const cx<T> *a = A + (size_t)x * Kp;
         cx<T> acc;
         for (int ip = 0; ip < nthp; ++ip) {
-          T w1 = Thp[ip * nthc + ic], w2 = Thm[ip * nthc + ic];
+          T w1 = Tps[ip * nthc + ic], w2 = Tms[ip * nthc + ic];
           cx<T> a1 = a[ip * Np + j], a2 = a[ip * Np + jq];
           acc.re = fma(w1, a1.re, fma(w2, a2.re, acc.re));
           acc.im = fma(w1, a1.im, fma(w2, a2.im, acc.im));
@@ -272,7 +288,7 @@ __global__ void k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
           const cx<T> *g = G + ((size_t)x * nthc + ic) * Np;
           cx<T> acc;
           for (int jp = 0; jp < Np; ++jp) {
-            T ph = Phi[(size_t)jp * Nc + jc];
+            T ph = Ps[jp * Nc + jc];
             acc.re = fma(ph, g[jp].re, acc.re);
             acc.im = fma(ph, g[jp].im, acc.im);
           }
@@ -295,16 +311,42 @@ __global__ void k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr,
   int b = blockIdx.y;
   if (k >= K) return;
   int e0 = il_ptr[b], e1 = il_ptr[b + 1];
+  const size_t cs = (size_t)K * nrhs;  // component stride
   for (int r = 0; r < nrhs; ++r) {
     cx<T> a0, a1, a2, a3;
-    for (int e = e0; e < e1; ++e) {
+    int e = e0;
+    // four interaction-list sources in flight per thread
+    for (; e + 4 <= e1; e += 4) {
+      int s[4], sl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        s[u] = __ldg(il_src + e + u);
+        sl[u] = __ldg(il_slot + e + u);
+      }
+      cx<T> t[4], v[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        t[u] = Tr[(size_t)sl[u] * K + k];
+        const cx<T> *src = S + ((size_t)s[u] * 4 * K + k) * nrhs + r;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[u][q] = src[q * cs];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a0 = cfma(t[u], v[u][0], a0);
+        a1 = cfma(t[u], v[u][1], a1);
+        a2 = cfma(t[u], v[u][2], a2);
+        a3 = cfma(t[u], v[u][3], a3);
+      }
+    }
+    for (; e < e1; ++e) {
       int s = il_src[e];
       cx<T> t = Tr[(size_t)il_slot[e] * K + k];
       const cx<T> *src = S + ((size_t)s * 4 * K + k) * nrhs + r;
       a0 = cfma(t, src[0], a0);
-      a1 = cfma(t, src[(size_t)K * nrhs], a1);
-      a2 = cfma(t, src[(size_t)2 * K * nrhs], a2);
-      a3 = cfma(t, src[(size_t)3 * K * nrhs], a3);
+      a1 = cfma(t, src[cs], a1);
+      a2 = cfma(t, src[2 * cs], a2);
+      a3 = cfma(t, src[3 * cs], a3);
     }
     cx<T> *o = I + ((size_t)b * 4 * K + k) * nrhs + r;
     o[0] = a0;
@@ -543,7 +585,8 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
     // upward pass: interpolate + shift each child, then sum into parents
     for (int lv = leaf; lv >= 3; --lv) {
       LevelHost &C = G.lev[lv], &P = G.lev[lv - 1];
-      size_t smem = (size_t)(3 * C.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>);
+      size_t smem = (size_t)(3 * C.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>) +
+                    (size_t)((2 * P.L + 2) * (2 * C.L + 2) + 2 * (P.L + 1) * (C.L + 1)) * sizeof(T);
       set_smem(k_interp_up<T>, smem);
       cx<T> *Y = (cx<T> *)c->d_scratch;
       k_interp_up<T><<<dim3(C.nbox, 2), 256, smem, c->stream>>>(
@@ -568,7 +611,8 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
     // downward pass: shift + anterpolate (exact transpose) into children
     for (int lv = 2; lv < leaf; ++lv) {
       LevelHost &P = G.lev[lv], &C = G.lev[lv + 1];
-      size_t smem = (size_t)(3 * P.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>);
+      size_t smem = (size_t)(3 * P.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>) +
+                    (size_t)((2 * P.L + 2) * (2 * C.L + 2) + 2 * (P.L + 1) * (C.L + 1)) * sizeof(T);
       set_smem(k_anterp_dn<T>, smem);
       k_anterp_dn<T><<<dim3(C.nbox, 2), 256, smem, c->stream>>>(
           C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),

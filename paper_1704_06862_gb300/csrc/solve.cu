@@ -128,7 +128,87 @@ struct Gm {
   }
 };
 
+// One CUDA graph per Krylov step index j holding "preconditioner, then
+// product" on that step's fixed vectors (V_j, Z_j, w), captured on first use
+// and replayed on later iterations and solves of the same shape; invalidated
+// when any work buffer is reallocated.  If capture is not possible (the
+// stream is already capturing, or capture fails) the step runs eagerly.
+struct StepGraphs {
+  int m = -1, R = -1, prec = -1, precond = -1;
+  int64_t gen = -1;
+  bool ok = true;
+  std::vector<cudaGraphExec_t> ex;
+  std::vector<int64_t> nk;  // kernels per graph (launch accounting)
+  void clear() {
+    for (auto e : ex)
+      if (e) cudaGraphExecDestroy(e);
+    ex.clear();
+    nk.clear();
+  }
+  template <typename F>
+  void run(sie_ctx *c, int j, F &&step) {
+    if (ok && !ex[j]) {
+      cudaStreamCaptureStatus cs;
+      if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
+          cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        ok = false;
+      } else {
+        int64_t l0 = c->launches;
+        bool fail = false;
+        try {
+          step();
+        } catch (...) {
+          fail = true;
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        cudaGraphExec_t x = nullptr;
+        if (!fail && e == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
+          ex[j] = x;
+          nk[j] = c->launches - l0;
+        } else {
+          ok = false;
+          cudaGetLastError();
+        }
+        if (g) cudaGraphDestroy(g);
+        c->launches = l0;
+      }
+    }
+    if (ok && ex[j]) {
+      SIE_CUDA(cudaGraphLaunch(ex[j], c->stream));
+      c->launches += nk[j];
+    } else {
+      step();
+    }
+  }
+};
+
+StepGraphs &step_graphs(sie_ctx *c, int m, int R, sie_prec prec, int precond) {
+  if (!c->graphs) c->graphs = new StepGraphs();
+  StepGraphs &G = *(StepGraphs *)c->graphs;
+  if (G.m != m || G.R != R || G.prec != (int)prec || G.precond != precond || G.gen != c->work_gen) {
+    G.clear();
+    G.m = m;
+    G.R = R;
+    G.prec = (int)prec;
+    G.precond = precond;
+    G.gen = c->work_gen;
+    G.ok = true;
+    G.ex.assign(m, nullptr);
+    G.nk.assign(m, 0);
+  }
+  return G;
+}
+
 }  // namespace
+
+void graphs_free(sie_ctx *c) {
+  if (!c->graphs) return;
+  StepGraphs *G = (StepGraphs *)c->graphs;
+  G->clear();
+  delete G;
+  c->graphs = nullptr;
+}
 
 // Restarted FGMRES on internal-order FP64 vectors b, x (x holds the initial
 // guess).  precond: 0 none, 1 ILU(0), 2 ILU(0) followed by the learned
@@ -152,8 +232,10 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
     c->gm_part = dev_alloc(c, (size_t)(m + 2) * R * ((n + 1023) / 1024) * sizeof(zd));
     c->gm_m = m;
     c->gm_R = R;
+    c->work_gen++;
   }
   zd *V = (zd *)c->gm_V, *Z = (zd *)c->gm_Z, *w = (zd *)c->gm_w;
+  StepGraphs &SG = step_graphs(c, m, R, prec, precond);
   zd *d_h = (zd *)c->gm_h, *d_s = (zd *)c->gm_s;
   // 256 threads x 4 elements per block
   Gm g{c, n, R, std::max(1, (n + 1023) / 1024), (zd *)c->gm_part};  // chunks of <= 1024 elements
@@ -217,10 +299,14 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
     int jend = 0;
     for (int j = 0; j < m; ++j) {
       zd *Vj = V + (size_t)j * vs, *Zj = Z + (size_t)j * vs;
-      if (precond >= 1) apply_ilu(c, Vj, Zj, R, prec);
-      else SIE_CUDA(cudaMemcpyAsync(Zj, Vj, vs * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
-      if (use_nn) nn_apply(c, Vj, Zj, R);
-      apply_matvec(c, Zj, w, R, prec, 3);
+      auto step = [&]() {
+        if (precond >= 1) apply_ilu(c, Vj, Zj, R, prec);
+        else SIE_CUDA(cudaMemcpyAsync(Zj, Vj, vs * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
+        if (use_nn) nn_apply(c, Vj, Zj, R);
+        apply_matvec(c, Zj, w, R, prec, 3);
+      };
+      if (use_nn) step();          // the learned part may be switched off mid-solve: run it eagerly
+      else SG.run(c, j, step);     // z_j = M^-1 v_j and w = A z_j as one captured graph per step
       // classical Gram-Schmidt, twice
       std::vector<zd> h1((size_t)(j + 1) * R), h2((size_t)(j + 1) * R);
       for (int pass = 0; pass < 2; ++pass) {

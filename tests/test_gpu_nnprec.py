@@ -48,7 +48,7 @@ def test_training_and_solve_keep_the_answer(solver):
     th = np.arccos(rng.uniform(-1, 1, 4))
     ph = rng.uniform(0, 2 * np.pi, 4)
     train = np.stack([th, ph, np.zeros(4), np.ones(4)], axis=1)
-    st = sie.nnprec_train(s.ctx, train, record_restart=5, max_pairs=64, epochs=30, batch=1024, lr=1e-3, seed=7)
+    st = sie.nnprec_train(s.ctx, train, record_restart=5, max_pairs=64, epochs=200, batch=256, lr=1e-3, seed=7)
     assert st["pairs"] > 0 and st["loss_last"] < st["loss_first"]
     d = np.load(os.path.join(HERE, "golden", "sphere_c1.npz"))
     b = torch.zeros((1, s.ne, 2), dtype=torch.complex128, device="cuda")
