@@ -221,7 +221,8 @@ class sie_nn_opts(ctypes.Structure):
 
 class sie_nn_stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int32), ("samples", ctypes.c_int64), ("loss_first", ctypes.c_double),
-                ("loss_last", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("loss_last", ctypes.c_double), ("ms", ctypes.c_double), ("val_loss_ratio", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("enabled", ctypes.c_int32)]
 
 
 NN_PARAMS = 128 * 256 + 256 + 256 * 256 + 256 + 256 * 128 + 128
@@ -233,7 +234,8 @@ def nnprec_train(ctx, train_inc, record_restart=5, max_pairs=256, epochs=20, bat
                     int(seed))
     st = sie_nn_stats()
     _check(ctx, load_library().nnprec_train(ctx, ctypes.byref(o), ctypes.byref(st)))
-    return dict(pairs=st.pairs, samples=st.samples, loss_first=st.loss_first, loss_last=st.loss_last, ms=st.ms)
+    return dict(pairs=st.pairs, samples=st.samples, loss_first=st.loss_first, loss_last=st.loss_last, ms=st.ms,
+                val_loss_ratio=st.val_loss_ratio, gamma=st.gamma, enabled=bool(st.enabled))
 
 
 def nnprec_params(ctx, params=None):

@@ -233,5 +233,6 @@ void graphs_free(sie_ctx *c);
 
 // ------------------------------------------------------------------ learned preconditioner (nn.cu)
 bool nn_ready(sie_ctx *c);
+bool nn_trained(sie_ctx *c);
 void nn_apply(sie_ctx *c, const zd *v, zd *z, int nrhs);
 void nn_free(sie_ctx *c);

@@ -1026,7 +1026,7 @@ extern "C" sie_status gmres_solve(sie_ctx *c, const void *b, void *x, int64_t nr
                 "gmres_solve: bad options");
     SIE_REQUIRE(o->precond >= 0 && o->precond <= 2, SIE_EINVAL, "gmres_solve: precond must be 0, 1 or 2");
     SIE_REQUIRE(o->precond == 0 || c->ilu.ready, SIE_ESTATE, "gmres_solve: ILU requested but not built");
-    SIE_REQUIRE(o->precond != 2 || nn_ready(c), SIE_ESTATE, "gmres_solve: learned preconditioner not trained");
+    SIE_REQUIRE(o->precond != 2 || nn_trained(c), SIE_ESTATE, "gmres_solve: learned preconditioner not trained");
     rc = run_gmres(c, (const zd *)b, (zd *)x, (int)nrhs, o, st);
   });
   return g != SIE_OK ? g : rc;

@@ -138,15 +138,17 @@ __global__ void k_relu_mask(int64_t n, const bf16 *__restrict__ H, float *__rest
     if (!(__bfloat162float(H[i]) > 0.f)) d[i] = 0.f;
 }
 
-// dY = (Y - T) / n and per-block partial losses
+// dY = w (Y - T) / n and per-block partial losses sum w (Y - T)^2 / (2n);
+// w = per-sample weight (null: 1)
 __global__ void k_mse(int64_t n_el, float inv_n, const float *__restrict__ Y, const float *__restrict__ T,
-                      float *__restrict__ dY, double *__restrict__ loss) {
+                      const float *__restrict__ wt, float *__restrict__ dY, double *__restrict__ loss) {
   __shared__ double red[256];
   double acc = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_el; i += (int64_t)gridDim.x * blockDim.x) {
     float d = Y[i] - T[i];
-    dY[i] = d * inv_n;
-    acc += 0.5 * (double)d * d;
+    float w = wt ? wt[i / D3] : 1.f;
+    dY[i] = w * d * inv_n;
+    acc += 0.5 * (double)w * d * d;
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -182,6 +184,56 @@ __global__ void k_adam(int64_t n, float lr, float b1, float b2, float eps, float
   }
 }
 
+// weighted dots[0] += <Y,T>, dots[1] += <Y,Y>, dots[2] += <T,T>
+__global__ void k_dots(int64_t n, const float *__restrict__ Y, const float *__restrict__ T,
+                       const float *__restrict__ wt, double *dots) {
+  __shared__ double red[3][256];
+  double a = 0, b = 0, cc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double y = Y[i], t = T[i], w = wt[i / D3];
+    a += w * y * t;
+    b += w * y * y;
+    cc += w * t * t;
+  }
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  red[2][threadIdx.x] = cc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) atomicAdd(dots + q, red[q][0]);
+}
+
+// sample weights of one pair: |u_c|^2 normalised to mean 1 over the pair's chunks,
+// so that the loss measures the error of the corrected z itself
+__global__ void k_pair_weights(int nchunk, const float *__restrict__ nrm, float *__restrict__ wt) {
+  __shared__ double red[256];
+  const float *a = nrm + (size_t)blockIdx.x * nchunk;
+  float *w = wt + (size_t)blockIdx.x * nchunk;
+  double acc = 0;
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) acc += (double)a[c] * a[c];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  double tot = red[0];
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x)
+    w[c] = tot > 0 ? (float)((double)a[c] * a[c] * nchunk / tot) : 0.f;
+}
+
+__global__ void k_scale_params(int64_t n, float s, float *__restrict__ w, bf16 *__restrict__ wb) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    w[i] *= s;
+    wb[i] = __float2bfloat16(w[i]);
+  }
+}
+
 __global__ void k_f2b(int64_t n, const float *__restrict__ a, bf16 *__restrict__ b) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = __float2bfloat16(a[i]);
@@ -197,14 +249,16 @@ inline int g1(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n
 
 // ------------------------------------------------------------------ network state
 struct NnState {
-  bool ready = false;
+  bool ready = false;    // correction enabled (trained and accepted by the validation gate, or set)
+  bool trained = false;
+  double *dots = nullptr;
   int nchunk = 0;
   int *d_cstart = nullptr, *d_clen = nullptr;
   float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;  // FP32 master, Adam moments, gradient
   bf16 *wb = nullptr;                                             // BF16 weights
   int cap = 0;                                                    // activation capacity (samples)
   bf16 *X = nullptr, *H1 = nullptr, *H2 = nullptr;
-  float *Y = nullptr, *dY = nullptr, *dH1 = nullptr, *dH2 = nullptr, *nrm = nullptr;
+  float *Y = nullptr, *dY = nullptr, *dH1 = nullptr, *dH2 = nullptr, *nrm = nullptr, *wts = nullptr;
   double *loss = nullptr;
 };
 
@@ -234,6 +288,7 @@ static void nn_alloc(sie_ctx *c, int cap) {
     S.g = (float *)dev_alloc(c, NPAR * 4);
     S.wb = (bf16 *)dev_alloc(c, NPAR * 2);
     S.loss = (double *)dev_alloc(c, sizeof(double));
+    S.dots = (double *)dev_alloc(c, 3 * sizeof(double));
   }
   cap = std::max(cap, S.nchunk);
   if (cap > S.cap) {
@@ -245,6 +300,7 @@ static void nn_alloc(sie_ctx *c, int cap) {
     S.dH1 = (float *)dev_alloc(c, (size_t)cap * D1 * 4);
     S.dH2 = (float *)dev_alloc(c, (size_t)cap * D2 * 4);
     S.nrm = (float *)dev_alloc(c, (size_t)cap * 4);
+    S.wts = (float *)dev_alloc(c, (size_t)cap * 4);
     S.cap = cap;
   }
 }
@@ -266,11 +322,12 @@ static void nn_forward(sie_ctx *c, NnState &S, int n, size_t off) {
   dense(c, n, D3, D2, S.H2 + off * D2, D2, 0, S.wb + OW3, D2, 1, S.w + OB3, 0, S.Y + off * D3, (bf16 *)nullptr);
 }
 
-// gradient of the MSE loss over samples [off, off+n) against targets T -> S.g; returns nothing (loss in S.loss)
-static void nn_backward(sie_ctx *c, NnState &S, int n, size_t off, const float *T) {
+// gradient of the (weighted, wt may be null) MSE loss over samples [off, off+n)
+// against targets T -> S.g; the loss is added to S.loss
+static void nn_backward(sie_ctx *c, NnState &S, int n, size_t off, const float *T, const float *wt) {
   const float inv_n = 1.f / (float)n;
   k_mse<<<g1((int64_t)n * D3), 256, 0, c->stream>>>((int64_t)n * D3, inv_n, S.Y + off * D3, T + off * D3,
-                                                    S.dY + off * D3, S.loss);
+                                                    wt ? wt + off : nullptr, S.dY + off * D3, S.loss);
   SIE_CHECK_LAUNCH();
   const float *dY = S.dY + off * D3;
   const bf16 *X = S.X + off * D0, *H1 = S.H1 + off * D1, *H2 = S.H2 + off * D2;
@@ -294,6 +351,7 @@ static void nn_backward(sie_ctx *c, NnState &S, int n, size_t off, const float *
 
 // ------------------------------------------------------------------ used by the solver
 bool nn_ready(sie_ctx *c) { return c->nn && ((NnState *)c->nn)->ready; }
+bool nn_trained(sie_ctx *c) { return c->nn && (((NnState *)c->nn)->trained || ((NnState *)c->nn)->ready); }
 
 // z (internal order, FP64) += chunk-wise network correction computed from v
 void nn_apply(sie_ctx *c, const zd *v, zd *z, int nrhs) {
@@ -370,6 +428,10 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
       SIE_CHECK_LAUNCH();
       c->launches += 2;
     }
+    // sample weights |u_c|^2 (normalised per pair): the loss is the error of z itself
+    k_pair_weights<<<npairs, 256, 0, c->stream>>>(S.nchunk, S.nrm, S.wts);
+    SIE_CHECK_LAUNCH();
+    c->launches++;
     // 3. initialise (He, seeded) and train with Adam on shuffled minibatches of whole sample blocks
     std::mt19937_64 rng(o->seed);
     std::vector<float> w(NPAR, 0.f);
@@ -385,8 +447,11 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
     SIE_CUDA(cudaMemsetAsync(S.v, 0, NPAR * 4, c->stream));
     k_f2b<<<g1(NPAR), 256, 0, c->stream>>>((int64_t)NPAR, S.w, S.wb);
     SIE_CHECK_LAUNCH();
-    const int B = std::min<int64_t>(o->batch, nsamp);
-    const int nbat = (int)((nsamp + B - 1) / B);
+    // hold out the last fifth of the pairs for the validation gate
+    const int nval = npairs >= 5 ? npairs / 5 : 0;
+    const int64_t ntr_s = (int64_t)(npairs - nval) * S.nchunk;
+    const int B = std::min<int64_t>(o->batch, ntr_s);
+    const int nbat = (int)((ntr_s + B - 1) / B);
     int step = 0;
     double loss_first = -1, loss_last = 0;
     std::vector<int> order(nbat);
@@ -396,9 +461,9 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
       SIE_CUDA(cudaMemsetAsync(S.loss, 0, sizeof(double), c->stream));
       for (int bi : order) {
         size_t off = (size_t)bi * B;
-        int n = (int)std::min<int64_t>(B, nsamp - (int64_t)off);
+        int n = (int)std::min<int64_t>(B, ntr_s - (int64_t)off);
         nn_forward(c, S, n, off);
-        nn_backward(c, S, n, off, T);
+        nn_backward(c, S, n, off, T, S.wts);
         ++step;
         float c1 = 1.f - std::pow(0.9f, (float)step), c2 = 1.f - std::pow(0.999f, (float)step);
         k_adam<<<g1(NPAR), 256, 0, c->stream>>>((int64_t)NPAR, (float)o->lr, 0.9f, 0.999f, 1e-8f, c1, c2, S.g, S.w,
@@ -419,7 +484,36 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
     SIE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    S.ready = true;
+    // validation gate: best output scale g* = <Y,T>/<Y,Y> on held-out samples;
+    // the correction is kept (scaled by min(g*, 1)) only if it lowers the
+    // held-out loss below 95 % of the loss of no correction at all
+    const int64_t v0 = nval ? ntr_s : 0, nv = nval ? nsamp - ntr_s : ntr_s;
+    SIE_CUDA(cudaMemsetAsync(S.dots, 0, 3 * sizeof(double), c->stream));
+    for (int64_t off = v0; off < v0 + nv; off += B) {
+      int n = (int)std::min<int64_t>(B, v0 + nv - off);
+      nn_forward(c, S, n, (size_t)off);
+      k_dots<<<g1((int64_t)n * D3), 256, 0, c->stream>>>((int64_t)n * D3, S.Y + (size_t)off * D3,
+                                                        T + (size_t)off * D3, S.wts + off, S.dots);
+      SIE_CHECK_LAUNCH();
+      c->launches++;
+    }
+    double dots[3];
+    SIE_CUDA(cudaMemcpyAsync(dots, S.dots, sizeof(dots), cudaMemcpyDeviceToHost, c->stream));
+    SIE_CUDA(cudaStreamSynchronize(c->stream));
+    double gam = dots[1] > 0 ? dots[0] / dots[1] : 0.0;
+    double ratio = dots[2] > 0 ? 1.0 - (dots[1] > 0 ? dots[0] * dots[0] / (dots[1] * dots[2]) : 0.0) : 1.0;
+    bool enabled = gam > 0 && ratio < 0.95;
+    if (enabled) {
+      float sc = (float)std::min(gam, 1.0);
+      k_scale_params<<<g1((int64_t)(NPAR - OW3)), 256, 0, c->stream>>>((int64_t)(NPAR - OW3), sc, S.w + OW3, S.wb + OW3);
+      SIE_CHECK_LAUNCH();
+      SIE_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    S.trained = true;
+    S.ready = enabled;
+    st->val_loss_ratio = ratio;
+    st->gamma = gam;
+    st->enabled = enabled ? 1 : 0;
     st->pairs = npairs;
     st->samples = nsamp;
     st->loss_first = loss_first;
@@ -447,6 +541,7 @@ extern "C" sie_status nnprec_params(sie_ctx *c, float *params, int32_t set) {
       k_f2b<<<g1(NPAR), 256, 0, c->stream>>>((int64_t)NPAR, S.w, S.wb);
       SIE_CHECK_LAUNCH();
       S.ready = true;
+      S.trained = true;
     } else {
       SIE_CUDA(cudaMemcpyAsync(params, S.w, NPAR * 4, cudaMemcpyDeviceToHost, c->stream));
     }
@@ -475,7 +570,7 @@ extern "C" sie_status nnprec_loss_grad(sie_ctx *c, const float *X_host, const fl
     SIE_CHECK_LAUNCH();
     SIE_CUDA(cudaMemsetAsync(S.loss, 0, sizeof(double), c->stream));
     nn_forward(c, S, (int)n, 0);
-    nn_backward(c, S, (int)n, 0, Tf);
+    nn_backward(c, S, (int)n, 0, Tf, nullptr);
     SIE_CUDA(cudaMemcpyAsync(grad_host, S.g, NPAR * 4, cudaMemcpyDeviceToHost, c->stream));
     SIE_CUDA(cudaMemcpyAsync(loss, S.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SIE_CUDA(cudaStreamSynchronize(c->stream));
