@@ -160,6 +160,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-nn", action="store_true")
+    ap.add_argument("--batch", type=int, default=16, help="right-hand sides of the batched monostatic leg")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -251,6 +252,38 @@ def main():
                    "converged": st_nn["converged"],
                    "ilu_only_ms_per_solve": ms, "ilu_only_iters": st["iters"], "speedup_vs_ilu_only": ms / ms_nn,
                    "rcs_max_abs_db_diff_vs_ilu_only": float(np.max(np.abs(dbn)))}
+    # batched monostatic sweep: nb incidence angles theta in [0, 180] deg (phi = 0, theta-pol)
+    # solved as one block of right-hand sides (block-RHS products and ILU sweeps)
+    batched = None
+    if args.batch > 1:
+        nb = args.batch
+        incb = geo.monostatic_incidences(nb)
+        bb = s.vec(nb)
+        xb = s.vec(nb)
+
+        def solve_b():
+            sie.sie_plane_wave_rhs(s.ctx, incb, bb)
+            xb.zero_()
+            stb = sie.gmres_solve(s.ctx, bb, xb, nb, restart=RESTART, max_iters=3000, tol=TOL,
+                                  prec=sie.SIE_PREC_MIXED, precond=1, check=False)
+            obs_b = np.stack([incb[:, 0], incb[:, 1]], axis=1)
+            mono = sie.rcs_farfield(s.ctx, xb, nb, obs_b)
+            return stb, mono[np.arange(nb), np.arange(nb), 0]
+
+        solve_b()
+        torch.cuda.synchronize()
+        eb0 = torch.cuda.Event(enable_timing=True)
+        eb1 = torch.cuda.Event(enable_timing=True)
+        eb0.record(stream)
+        stb, mono = solve_b()
+        eb1.record(stream)
+        torch.cuda.synchronize()
+        msb = eb0.elapsed_time(eb1)
+        batched = {"nrhs": nb, "ms_per_block": msb, "rhs_per_s": nb / (msb / 1e3),
+                   "ms_per_rhs": msb / nb, "single_rhs_ms": ms, "speedup_per_rhs_vs_single": ms / (msb / nb),
+                   "iters_max": max(t["iters"] for t in stb), "all_converged": all(t["converged"] for t in stb),
+                   "monostatic_rcs_dbsm": [round(float(10 * np.log10(v)), 3) for v in mono]}
+        del bb, xb
     # Mie check of the chosen form
     mie_db = None
     try:
@@ -297,7 +330,7 @@ def main():
         "iters": st["iters"], "rel_residual": st["rel_residual"], "setup_s": t_setup,
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
                 "d2h_bytes_per_step": int(rcs.nbytes)},
-        "plain_fp64": plain, "learned_precond": learned, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
+        "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
     }
     if rank == 0:

@@ -96,3 +96,23 @@ def test_solution_and_rcs(case, prec):
           f"{db.max():.3f} dB, vs Mie mean {mie_db.mean():.3f} dB")
     assert err < 1e-3
     assert db.max() < 0.2
+
+
+def test_batched_solve_equals_single_solves(case):
+    """A block of right-hand sides (monostatic incidences) solved together
+    gives the currents of the individual solves."""
+    name, s, d = case
+    if name != "sphere_c1":
+        pytest.skip("one case suffices")
+    inc = np.array([[0.0, 0.0, 0.0, 1.0], [0.9, 0.0, 0.0, 1.0], [2.2, 0.0, 0.0, 1.0]])
+    b = torch.zeros((3, s.ne, 2), dtype=torch.complex128, device="cuda")
+    sie.sie_plane_wave_rhs(s.ctx, inc, b)
+    xb = torch.zeros_like(b)
+    st = sie.gmres_solve(s.ctx, b, xb, 3, restart=50, max_iters=500, tol=1e-8, prec=sie.SIE_PREC_FP64, precond=1)
+    assert all(t["converged"] for t in st)
+    xb = _host(xb)
+    for r in range(3):
+        x1 = torch.zeros((1, s.ne, 2), dtype=torch.complex128, device="cuda")
+        sie.gmres_solve(s.ctx, b[r:r + 1].contiguous(), x1, 1, restart=50, max_iters=500, tol=1e-8,
+                        prec=sie.SIE_PREC_FP64, precond=1)
+        assert rel(xb[r], _host(x1)[0]) < 1e-6
