@@ -293,7 +293,7 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
     g.launch_check();
     std::fill(gvec.begin(), gvec.end(), cd(0.0));
     for (int r = 0; r < R; ++r) {
-      gvec[r] = active[r] ? rn[r] : 0.0;
+      gvec[(size_t)r * (m + 1)] = active[r] ? rn[r] : 0.0;
       if (active[r]) restarts[r]++;
     }
     int jend = 0;
