@@ -196,9 +196,11 @@ sie_status gmres_solve(sie_ctx *ctx, const void *b_dev, void *x_dev, int64_t nrh
  * e_k = x* - x_k; with u = ILU^-1 r_k the network regresses (e_k - u)_c / |u_c|
  * on u_c / |u_c| chunk by chunk (squared error weighted by |u_c|^2, normalised
  * per pair, i.e. the error of the corrected z itself).  The last fifth of the
- * pairs is held out: the output is scaled by the least-squares factor gamma
- * (at most 1) fitted there, and the correction is enabled only if it lowers
- * the held-out loss below 95 % of the loss of no correction.  Synchronous. */
+ * incidences is held out: the output is scaled by the least-squares factor
+ * gamma (at most 1) fitted on their pairs; the correction is kept only if it
+ * lowers their loss below 95 % of the loss of no correction AND the plain
+ * ILU(0) solver, acting as judge, needs more FGMRES(50) iterations than the
+ * corrected one on the last held-out incidence.  Synchronous. */
 typedef struct {
   const double *train_inc;  /* host [ntrain][4] incidences, as sie_plane_wave_rhs */
   int32_t ntrain;
@@ -218,8 +220,11 @@ typedef struct {
   double ms;                /* device time of recording + training */
   double val_loss_ratio;    /* held-out loss with the (scaled) correction / without any */
   double gamma;             /* least-squares output scale on the held-out pairs */
-  int32_t enabled;          /* 1 if the correction passed the gate (ratio < 0.95, gamma > 0);
-                               otherwise precond = 2 runs as plain ILU(0) */
+  int32_t enabled;          /* 1 if the correction passed both gates; otherwise
+                               precond = 2 runs as plain ILU(0) */
+  int32_t judge_iters_ilu;  /* FGMRES(50) iterations to 1e-4 on the last (held-out)
+                               incidence with ILU(0) alone, and with the correction */
+  int32_t judge_iters_nn;   /* (-1: not run, the loss gate already rejected it) */
 } sie_nn_stats;
 
 sie_status nnprec_train(sie_ctx *ctx, const sie_nn_opts *opts, sie_nn_stats *stats);

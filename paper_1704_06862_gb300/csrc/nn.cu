@@ -447,8 +447,13 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
     SIE_CUDA(cudaMemsetAsync(S.v, 0, NPAR * 4, c->stream));
     k_f2b<<<g1(NPAR), 256, 0, c->stream>>>((int64_t)NPAR, S.w, S.wb);
     SIE_CHECK_LAUNCH();
-    // hold out the last fifth of the pairs for the validation gate
-    const int nval = npairs >= 5 ? npairs / 5 : 0;
+    // hold out the pairs of the last fifth of the incidences (at least one when
+    // there are two or more) for the validation gate
+    const int nval_inc = o->ntrain >= 2 ? std::max(1, o->ntrain / 5) : 0;
+    int nval = 0;
+    for (int k = 0; k < npairs; ++k)
+      if (owner[k] >= o->ntrain - nval_inc) ++nval;
+    if (nval == npairs) nval = 0;
     const int64_t ntr_s = (int64_t)(npairs - nval) * S.nchunk;
     const int B = std::min<int64_t>(o->batch, ntr_s);
     const int nbat = (int)((ntr_s + B - 1) / B);
@@ -509,6 +514,26 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
       SIE_CHECK_LAUNCH();
       SIE_CUDA(cudaStreamSynchronize(c->stream));
     }
+    // the plain ILU(0) solver is the judge: solve the last (held-out) incidence
+    // with and without the correction; keep it only if it saves iterations
+    int it_ilu = -1, it_nn = -1;
+    if (enabled) {
+      SIE_CUDA(cudaMemcpyAsync(d_inc, o->train_inc + 4 * (o->ntrain - 1), 4 * sizeof(double), cudaMemcpyHostToDevice,
+                               c->stream));
+      launch_rhs(c, d_inc, 1, b);
+      sie_solve_stats sv;
+      S.ready = false;
+      SIE_CUDA(cudaMemsetAsync(xs, 0, (size_t)ne2 * sizeof(zd), c->stream));
+      run_gmres_internal(c, b, xs, 1, 50, 1000, 1e-4, SIE_PREC_MIXED, 1, nullptr, &sv);
+      it_ilu = sv.iters;
+      S.ready = true;
+      SIE_CUDA(cudaMemsetAsync(xs, 0, (size_t)ne2 * sizeof(zd), c->stream));
+      run_gmres_internal(c, b, xs, 1, 50, 1000, 1e-4, SIE_PREC_MIXED, 2, nullptr, &sv);
+      it_nn = sv.iters;
+      enabled = it_nn < it_ilu;
+    }
+    st->judge_iters_ilu = it_ilu;
+    st->judge_iters_nn = it_nn;
     S.trained = true;
     S.ready = enabled;
     st->val_loss_ratio = ratio;
