@@ -119,6 +119,58 @@ __global__ void k_near_spmv(int ne, int nrhs, const int *__restrict__ row_ptr, c
   }
 }
 
+// Block of right-hand sides: each 2x2 block is loaded once and applied to RB
+// right-hand sides at a time, so the matrix is read ceil(R/RB) times instead of R.
+template <typename T, int RB>
+__global__ void k_near_spmv_blk(int ne, int nrhs, const int *__restrict__ row_ptr, const int *__restrict__ col,
+                                const cx<T> *__restrict__ B, const cx<T> *__restrict__ x, cx<T> *__restrict__ y,
+                                int accumulate) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= ne) return;
+  int s = row_ptr[warp], e = row_ptr[warp + 1];
+  typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V16;
+  constexpr int NV = (int)(4 * sizeof(cx<T>) / sizeof(V16));
+  const V16 *Bv = reinterpret_cast<const V16 *>(B);
+  const size_t vs = (size_t)ne * 2;
+  for (int r0 = 0; r0 < nrhs; r0 += RB) {
+    const int nr = min(RB, nrhs - r0);
+    cx<T> a0[RB], a1[RB];
+    for (int q = s + lane; q < e; q += 32) {
+      int cc = __ldg(col + q);
+      V16 u[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) u[v] = __ldg(Bv + (size_t)q * NV + v);
+      const cx<T> *b = reinterpret_cast<const cx<T> *>(u);
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr)
+        if (rr < nr) {
+          const cx<T> *xr = x + (size_t)(r0 + rr) * vs;
+          cx<T> xj = xr[2 * cc], xm = xr[2 * cc + 1];
+          a0[rr] = cfma(b[0], xj, a0[rr]);
+          a0[rr] = cfma(b[1], xm, a0[rr]);
+          a1[rr] = cfma(b[2], xj, a1[rr]);
+          a1[rr] = cfma(b[3], xm, a1[rr]);
+        }
+    }
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr)
+      if (rr < nr) {
+        cx<T> s0 = warp_sum(a0[rr]), s1 = warp_sum(a1[rr]);
+        if (lane == 0) {
+          cx<T> *yr = y + (size_t)(r0 + rr) * vs + 2 * (size_t)warp;
+          if (accumulate) {
+            yr[0] += s0;
+            yr[1] += s1;
+          } else {
+            yr[0] = s0;
+            yr[1] = s1;
+          }
+        }
+      }
+  }
+}
+
 // ---------------------------------------------------------------- MLFMM
 // Leaf aggregation: S_b(k) = sum_{i in b} s_i [eta0 c, v]_p(i) (x) V_i(k),
 // S layout [box][J/M][theta/phi][k][r].
@@ -130,24 +182,34 @@ __global__ void k_aggregate(int nbox, int K, int ne, int nrhs, const int *__rest
   int b = blockIdx.y;
   if (k >= K) return;
   int i0 = box_start[b], i1 = box_start[b + 1];
-  for (int r = 0; r < nrhs; ++r) {
-    cx<T> a0, a1, a2, a3;
-    const cx<T> *xr = x + (size_t)r * ne * 2;
+  constexpr int RB = 4;  // right-hand sides per pass: each pattern value is read once per pass
+  for (int r0 = 0; r0 < nrhs; r0 += RB) {
+    const int nr = min(RB, nrhs - r0);
+    cx<T> a0[RB], a1[RB], a2[RB], a3[RB];
     for (int i = i0; i < i1; ++i) {
       int p = basis_p[i];
       T s = (T)sign[i];
-      cx<T> xj = s * xr[2 * p], xm = s * xr[2 * p + 1];
       cx<T> vt = V[((size_t)i * 2) * K + k], vp = V[((size_t)i * 2 + 1) * K + k];
-      a0 = cfma(xj, vt, a0);
-      a1 = cfma(xj, vp, a1);
-      a2 = cfma(xm, vt, a2);
-      a3 = cfma(xm, vp, a3);
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr)
+        if (rr < nr) {
+          const cx<T> *xr = x + (size_t)(r0 + rr) * ne * 2;
+          cx<T> xj = s * xr[2 * p], xm = s * xr[2 * p + 1];
+          a0[rr] = cfma(xj, vt, a0[rr]);
+          a1[rr] = cfma(xj, vp, a1[rr]);
+          a2[rr] = cfma(xm, vt, a2[rr]);
+          a3[rr] = cfma(xm, vp, a3[rr]);
+        }
     }
-    cx<T> *o = S + ((size_t)b * 4 * K + k) * nrhs + r;
-    o[0] = a0;
-    o[(size_t)K * nrhs] = a1;
-    o[(size_t)2 * K * nrhs] = a2;
-    o[(size_t)3 * K * nrhs] = a3;
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr)
+      if (rr < nr) {
+        cx<T> *o = S + ((size_t)b * 4 * K + k) * nrhs + r0 + rr;
+        o[0] = a0[rr];
+        o[(size_t)K * nrhs] = a1[rr];
+        o[(size_t)2 * K * nrhs] = a2[rr];
+        o[(size_t)3 * K * nrhs] = a3[rr];
+      }
   }
 }
 
@@ -414,6 +476,49 @@ __device__ __forceinline__ void mv2(const cx<T> *B, cx<T> x0, cx<T> x1, cx<T> &y
   y1 = B[2] * x0 + B[3] * x1;
 }
 
+constexpr int ILU_RC = 8;  // right-hand sides carried together through the in-box solve
+
+// off-box product for a block of right-hand sides: each block loaded once per RB of them
+template <typename T, int RB>
+__global__ void k_ilu_offbox_blk(int ne, int nrhs, int row0, int row1, const int *__restrict__ off_ptr,
+                                 const int *__restrict__ off_col, const cx<T> *__restrict__ off_val,
+                                 const cx<T> *src, cx<T> *z) {
+  int i = row0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= row1) return;
+  int q0 = off_ptr[i], q1 = off_ptr[i + 1];
+  const size_t vs = (size_t)ne * 2;
+  for (int r0 = 0; r0 < nrhs; r0 += RB) {
+    const int nr = min(RB, nrhs - r0);
+    cx<T> a0[RB], a1[RB];
+    for (int q = q0 + lane; q < q1; q += 32) {
+      int cc = off_col[q];
+      const cx<T> *B = off_val + 4 * (size_t)q;
+      cx<T> b0 = B[0], b1 = B[1], b2 = B[2], b3 = B[3];
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr)
+        if (rr < nr) {
+          const cx<T> *zr = z + (size_t)(r0 + rr) * vs;
+          cx<T> x0 = zr[2 * cc], x1 = zr[2 * cc + 1];
+          a0[rr] += b0 * x0 + b1 * x1;
+          a1[rr] += b2 * x0 + b3 * x1;
+        }
+    }
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr)
+      if (rr < nr) {
+        cx<T> s0 = warp_sum(a0[rr]), s1 = warp_sum(a1[rr]);
+        if (lane == 0) {
+          const cx<T> *sr = src + (size_t)(r0 + rr) * vs + 2 * (size_t)i;
+          cx<T> v0 = sr[0], v1 = sr[1];
+          cx<T> *o = z + (size_t)(r0 + rr) * vs + 2 * (size_t)i;
+          o[0] = v0 - s0;
+          o[1] = v1 - s1;
+        }
+      }
+  }
+}
+
 template <typename T>
 __global__ void k_ilu_offbox(int ne, int nrhs, int row0, int row1, const int *__restrict__ off_ptr,
                              const int *__restrict__ off_col, const cx<T> *__restrict__ off_val,
@@ -452,8 +557,8 @@ __global__ void k_ilu_inbox(int ne, int nrhs, int forward, int box0, int staged,
   const int b = box0 + blockIdx.x;
   const int s0 = box_start[b], n = box_start[b + 1] - s0;
   const cx<T> *D = dense + 4 * dense_off[b];  // column-major n x n blocks
-  cx<T> *rr = reinterpret_cast<cx<T> *>(smem_raw);  // [2n]
-  cx<T> *tri = rr + 2 * n;                          // packed triangle [n(n-1)/2][4]
+  cx<T> *rr = reinterpret_cast<cx<T> *>(smem_raw);  // [ILU_RC][2n]
+  cx<T> *tri = rr + 2 * n * min(nrhs, ILU_RC);      // packed triangle [n(n-1)/2][4]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   // packed column start: forward keeps rows j+1..n-1 of column j, backward rows 0..j-1
   auto pcol = [&](int j) { return forward ? j * (n - 1) - j * (j - 1) / 2 : j * (j - 1) / 2; };
@@ -472,47 +577,59 @@ __global__ void k_ilu_inbox(int ne, int nrhs, int forward, int box0, int staged,
       for (int q = lane; q < cnt; q += 32) dst[q] = src[q];
     }
   }
-  for (int r = 0; r < nrhs; ++r) {
-    cx<T> *zr = z + ((size_t)r * ne + s0) * 2;
-    for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) rr[t] = zr[t];
+  // right-hand sides in chunks of ILU_RC; within a step, lanes run over (row, rhs) pairs
+  for (int r0 = 0; r0 < nrhs; r0 += ILU_RC) {
+    const int nr = min(ILU_RC, nrhs - r0);
+    for (int t = threadIdx.x; t < 2 * n * nr; t += blockDim.x) {
+      int r = t / (2 * n), u = t - r * 2 * n;
+      rr[t] = z[((size_t)(r0 + r) * ne + s0) * 2 + u];
+    }
     __syncthreads();
     if (warp == 0) {
       if (forward) {
         for (int j = 0; j < n; ++j) {
           __syncwarp();
-          cx<T> z0 = rr[2 * j], z1 = rr[2 * j + 1];
-          __syncwarp();
           const cx<T> *col = staged ? tri + 4 * (pcol(j) - (j + 1)) : D + 4 * (size_t)j * n;
-          for (int li = j + 1 + lane; li < n; li += 32) {
+          const int cnt = (n - j - 1) * nr;
+          for (int idx = lane; idx < cnt; idx += 32) {
+            int li = j + 1 + idx / nr, r = idx % nr;
+            cx<T> *v = rr + (size_t)r * 2 * n;
             cx<T> t0, t1;
-            mv2(col + 4 * li, z0, z1, t0, t1);
-            rr[2 * li] -= t0;
-            rr[2 * li + 1] -= t1;
+            mv2(col + 4 * li, v[2 * j], v[2 * j + 1], t0, t1);
+            v[2 * li] -= t0;
+            v[2 * li + 1] -= t1;
           }
         }
       } else {
         for (int j = n - 1; j >= 0; --j) {
           __syncwarp();
-          cx<T> x0, x1;
-          mv2(dinv + 4 * (size_t)(s0 + j), rr[2 * j], rr[2 * j + 1], x0, x1);
-          __syncwarp();
-          if (lane == 0) {
-            rr[2 * j] = x0;
-            rr[2 * j + 1] = x1;
+          if (lane < nr) {
+            cx<T> *v = rr + (size_t)lane * 2 * n;
+            cx<T> x0, x1;
+            mv2(dinv + 4 * (size_t)(s0 + j), v[2 * j], v[2 * j + 1], x0, x1);
+            v[2 * j] = x0;
+            v[2 * j + 1] = x1;
           }
+          __syncwarp();
           const cx<T> *col = staged ? tri + 4 * pcol(j) : D + 4 * (size_t)j * n;
-          for (int li = lane; li < j; li += 32) {
+          const int cnt = j * nr;
+          for (int idx = lane; idx < cnt; idx += 32) {
+            int li = idx / nr, r = idx % nr;
+            cx<T> *v = rr + (size_t)r * 2 * n;
             cx<T> t0, t1;
-            mv2(col + 4 * li, x0, x1, t0, t1);
-            rr[2 * li] -= t0;
-            rr[2 * li + 1] -= t1;
+            mv2(col + 4 * li, v[2 * j], v[2 * j + 1], t0, t1);
+            v[2 * li] -= t0;
+            v[2 * li + 1] -= t1;
           }
         }
       }
       __syncwarp();
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) zr[t] = rr[t];
+    for (int t = threadIdx.x; t < 2 * n * nr; t += blockDim.x) {
+      int r = t / (2 * n), u = t - r * 2 * n;
+      z[((size_t)(r0 + r) * ne + s0) * 2 + u] = rr[t];
+    }
     __syncthreads();
   }
 }
@@ -558,9 +675,13 @@ template <typename T>
 void op_near(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool accumulate) {
   int warps_per_block = 8;
   int blocks = (c->ne + warps_per_block - 1) / warps_per_block;
-  k_near_spmv<T><<<blocks, 32 * warps_per_block, 0, c->stream>>>(c->ne, nrhs, c->d_row_ptr, c->d_col,
-                                                                 (const cx<T> *)tsel<T>::near(c), x, y,
-                                                                 accumulate ? 1 : 0);
+  if (nrhs == 1)
+    k_near_spmv<T><<<blocks, 32 * warps_per_block, 0, c->stream>>>(c->ne, nrhs, c->d_row_ptr, c->d_col,
+                                                                   (const cx<T> *)tsel<T>::near(c), x, y,
+                                                                   accumulate ? 1 : 0);
+  else
+    k_near_spmv_blk<T, sizeof(T) == 4 ? 8 : 4><<<blocks, 32 * warps_per_block, 0, c->stream>>>(
+        c->ne, nrhs, c->d_row_ptr, c->d_col, (const cx<T> *)tsel<T>::near(c), x, y, accumulate ? 1 : 0);
   SIE_CHECK_LAUNCH();
   c->launches++;
 }
@@ -640,10 +761,12 @@ template <typename T>
 void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
   IluHost &I = c->ilu;
   const int mb = std::max(I.max_box, 1);
-  size_t full = ((size_t)mb * (mb - 1) / 2 * 4 + 2 * mb) * sizeof(cx<T>);
+  const size_t rc = (size_t)std::min(nrhs, ILU_RC);
+  size_t full = ((size_t)mb * (mb - 1) / 2 * 4 + 2 * mb * rc) * sizeof(cx<T>);
   int staged = full <= 200 * 1024 ? 1 : 0;
-  size_t smem = staged ? full : 2 * (size_t)mb * sizeof(cx<T>);
+  size_t smem = staged ? full : 2 * (size_t)mb * rc * sizeof(cx<T>);
   set_smem(k_ilu_inbox<T>, smem);
+  constexpr int RB = sizeof(T) == 4 ? 8 : 4;
   for (int pass = 0; pass < 2; ++pass) {
     bool fwd = pass == 0;
     for (int q = 0; q < 8; ++q) {
@@ -652,9 +775,14 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
       if (cnt == 0) continue;
       int row0 = c->leaf_start[first], row1 = c->leaf_start[first + cnt];
       int warps = row1 - row0, wpb = 8;
-      k_ilu_offbox<T><<<(warps + wpb - 1) / wpb, 32 * wpb, 0, c->stream>>>(
-          c->ne, nrhs, row0, row1, fwd ? I.d_lo_ptr : I.d_up_ptr, fwd ? I.d_lo_col : I.d_up_col,
-          (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? r : z, z);
+      if (nrhs == 1)
+        k_ilu_offbox<T><<<(warps + wpb - 1) / wpb, 32 * wpb, 0, c->stream>>>(
+            c->ne, nrhs, row0, row1, fwd ? I.d_lo_ptr : I.d_up_ptr, fwd ? I.d_lo_col : I.d_up_col,
+            (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? r : z, z);
+      else
+        k_ilu_offbox_blk<T, RB><<<(warps + wpb - 1) / wpb, 32 * wpb, 0, c->stream>>>(
+            c->ne, nrhs, row0, row1, fwd ? I.d_lo_ptr : I.d_up_ptr, fwd ? I.d_lo_col : I.d_up_col,
+            (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? r : z, z);
       SIE_CHECK_LAUNCH();
       k_ilu_inbox<T><<<cnt, 256, smem, c->stream>>>(c->ne, nrhs, fwd ? 1 : 0, first, staged, I.d_box_start,
                                                    I.d_dense_off, (const cx<T> *)tsel<T>::dense(I),
