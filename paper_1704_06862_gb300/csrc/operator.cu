@@ -592,7 +592,7 @@ __global__ void k_ilu_inbox(int ne, int nrhs, int forward, int box0, int staged,
           const cx<T> *col = staged ? tri + 4 * (pcol(j) - (j + 1)) : D + 4 * (size_t)j * n;
           const int cnt = (n - j - 1) * nr;
           for (int idx = lane; idx < cnt; idx += 32) {
-            int li = j + 1 + idx / nr, r = idx % nr;
+            int li = nr == 1 ? j + 1 + idx : j + 1 + idx / nr, r = nr == 1 ? 0 : idx % nr;
             cx<T> *v = rr + (size_t)r * 2 * n;
             cx<T> t0, t1;
             mv2(col + 4 * li, v[2 * j], v[2 * j + 1], t0, t1);
@@ -614,7 +614,7 @@ __global__ void k_ilu_inbox(int ne, int nrhs, int forward, int box0, int staged,
           const cx<T> *col = staged ? tri + 4 * pcol(j) : D + 4 * (size_t)j * n;
           const int cnt = j * nr;
           for (int idx = lane; idx < cnt; idx += 32) {
-            int li = idx / nr, r = idx % nr;
+            int li = nr == 1 ? idx : idx / nr, r = nr == 1 ? 0 : idx % nr;
             cx<T> *v = rr + (size_t)r * 2 * n;
             cx<T> t0, t1;
             mv2(col + 4 * li, v[2 * j], v[2 * j + 1], t0, t1);
