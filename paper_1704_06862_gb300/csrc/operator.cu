@@ -172,8 +172,10 @@ __global__ void k_near_spmv_blk(int ne, int nrhs, const int *__restrict__ row_pt
 }
 
 // ---------------------------------------------------------------- MLFMM
-// Leaf aggregation: S_b(k) = sum_{i in b} s_i [eta0 c, v]_p(i) (x) V_i(k),
-// S layout [box][J/M][theta/phi][k][r].
+// Leaf aggregation: S_b(k) = sum_{i in b} s_i [eta0 c, v]_p(i) (x) V_i(k).
+// Every level's S and I are laid out [box][J/M][theta/phi][r][k]: for one
+// right-hand side the K samples of a component are contiguous, so a warp over
+// k reads and writes whole lines for any number of right-hand sides.
 template <typename T>
 __global__ void k_aggregate(int nbox, int K, int ne, int nrhs, const int *__restrict__ box_start,
                             const int *__restrict__ basis_p, const int *__restrict__ sign,
@@ -204,11 +206,12 @@ __global__ void k_aggregate(int nbox, int K, int ne, int nrhs, const int *__rest
 #pragma unroll
     for (int rr = 0; rr < RB; ++rr)
       if (rr < nr) {
-        cx<T> *o = S + ((size_t)b * 4 * K + k) * nrhs + r0 + rr;
+        const size_t cs = (size_t)nrhs * K;  // component stride
+        cx<T> *o = S + ((size_t)b * 4 * nrhs + r0 + rr) * K + k;
         o[0] = a0[rr];
-        o[(size_t)K * nrhs] = a1[rr];
-        o[(size_t)2 * K * nrhs] = a2[rr];
-        o[(size_t)3 * K * nrhs] = a3[rr];
+        o[cs] = a1[rr];
+        o[2 * cs] = a2[rr];
+        o[3 * cs] = a3[rr];
       }
   }
 }
@@ -218,8 +221,9 @@ __global__ void k_aggregate(int nbox, int K, int ne, int nrhs, const int *__rest
 // source J|M); the source is carried as three Cartesian components:
 // (theta, phi) -> xyz at the child directions, trigonometric interpolation in
 // phi, the folded Lagrange step in theta, xyz -> (theta, phi) at the parent
-// directions, times the shift exp(j k khat.(c_child - c_parent)).  Output
-// Y[child][J|M][theta|phi][k_parent][r]; k_up_sum adds the children.
+// directions, times the shift exp(j k khat.(c_child - c_parent)).  One CTA
+// per (child, J|M, right-hand side); output Y[child][J|M][theta|phi][r][k_parent];
+// k_up_sum adds the children.
 template <typename T>
 __global__ void k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, const int *__restrict__ oct,
                             const T *__restrict__ tpc, const T *__restrict__ tpp, const T *__restrict__ Phi,
@@ -237,12 +241,12 @@ __global__ void k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
     Tms[t] = Thm[t];
   }
   __syncthreads();
-  const int c = blockIdx.x, jm = blockIdx.y, o = oct[c];
+  const int c = blockIdx.x, jm = blockIdx.y, r = blockIdx.z, o = oct[c];
   const int nG = 3 * nthc * Np;
-  for (int r = 0; r < nrhs; ++r) {
+  {
     for (int t = threadIdx.x; t < Kc; t += blockDim.x) {
-      cx<T> ft = Sc[(((size_t)c * 4 + jm * 2) * Kc + t) * nrhs + r];
-      cx<T> fp = Sc[(((size_t)c * 4 + jm * 2 + 1) * Kc + t) * nrhs + r];
+      cx<T> ft = Sc[(((size_t)c * 4 + jm * 2) * nrhs + r) * Kc + t];
+      cx<T> fp = Sc[(((size_t)c * 4 + jm * 2 + 1) * nrhs + r) * Kc + t];
       const T *u = tpc + 6 * (size_t)t;
       for (int x = 0; x < 3; ++x) A[x * Kc + t] = ft * u[x] + fp * u[3 + x];
     }
@@ -275,10 +279,9 @@ __global__ void k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
       }
       const T *u = tpp + 6 * (size_t)t;
       cx<T> sh = up[o * Kp + t];
-      Y[(((size_t)c * 4 + jm * 2) * Kp + t) * nrhs + r] = sh * (H[0] * u[0] + H[1] * u[1] + H[2] * u[2]);
-      Y[(((size_t)c * 4 + jm * 2 + 1) * Kp + t) * nrhs + r] = sh * (H[0] * u[3] + H[1] * u[4] + H[2] * u[5]);
+      Y[(((size_t)c * 4 + jm * 2) * nrhs + r) * Kp + t] = sh * (H[0] * u[0] + H[1] * u[1] + H[2] * u[2]);
+      Y[(((size_t)c * 4 + jm * 2 + 1) * nrhs + r) * Kp + t] = sh * (H[0] * u[3] + H[1] * u[4] + H[2] * u[5]);
     }
-    __syncthreads();
   }
 }
 
@@ -289,17 +292,17 @@ __global__ void k_up_sum(int Kp, int nrhs, const int *__restrict__ ch_ptr, const
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   if (t >= Kp) return;
-  for (int q = 0; q < 4; ++q)
-    for (int r = 0; r < nrhs; ++r) {
-      cx<T> acc;
-      for (int s = ch_ptr[b]; s < ch_ptr[b + 1]; ++s) acc += Y[(((size_t)ch_idx[s] * 4 + q) * Kp + t) * nrhs + r];
-      Sp[(((size_t)b * 4 + q) * Kp + t) * nrhs + r] = acc;
-    }
+  const int s0 = ch_ptr[b], s1 = ch_ptr[b + 1];
+  for (int qr = 0; qr < 4 * nrhs; ++qr) {
+    cx<T> acc;
+    for (int s = s0; s < s1; ++s) acc += Y[((size_t)ch_idx[s] * 4 * nrhs + qr) * Kp + t];
+    Sp[((size_t)b * 4 * nrhs + qr) * Kp + t] = acc;
+  }
 }
 
 // Exact transpose of k_interp_up (anterpolation, downward pass), with the
-// receive shift exp(-j k khat.(c_child - c_parent)): one CTA per child box,
-// I_child += Interp^T [dn (.) I_parent].  Quadrature weights are folded into
+// receive shift exp(-j k khat.(c_child - c_parent)): one CTA per (child box,
+// J|M, right-hand side), I_child += Interp^T [dn (.) I_parent].  Quadrature weights are folded into
 // the translators, so the adjoint is the plain transpose.
 template <typename T>
 __global__ void k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs, const int *__restrict__ parent,
@@ -318,13 +321,13 @@ __global__ void k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
     Tms[t] = Thm[t];
   }
   __syncthreads();
-  const int c = blockIdx.x, jm = blockIdx.y, pb = parent[c], o = oct[c];
+  const int c = blockIdx.x, jm = blockIdx.y, r = blockIdx.z, pb = parent[c], o = oct[c];
   const int nG = 3 * nthc * Np;
-  for (int r = 0; r < nrhs; ++r) {
+  {
       for (int t = threadIdx.x; t < Kp; t += blockDim.x) {
         cx<T> sh = dn[o * Kp + t];
-        cx<T> ut = sh * Ip[(((size_t)pb * 4 + jm * 2) * Kp + t) * nrhs + r];
-        cx<T> up_ = sh * Ip[(((size_t)pb * 4 + jm * 2 + 1) * Kp + t) * nrhs + r];
+        cx<T> ut = sh * Ip[(((size_t)pb * 4 + jm * 2) * nrhs + r) * Kp + t];
+        cx<T> up_ = sh * Ip[(((size_t)pb * 4 + jm * 2 + 1) * nrhs + r) * Kp + t];
         const T *u = tpp + 6 * (size_t)t;
         for (int x = 0; x < 3; ++x) A[x * Kp + t] = ut * u[x] + up_ * u[3 + x];
       }
@@ -357,11 +360,10 @@ __global__ void k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs, const int 
           C[x] = acc;
         }
         const T *u = tpc + 6 * (size_t)t;
-        Ic[(((size_t)c * 4 + jm * 2) * Kc + t) * nrhs + r] += C[0] * u[0] + C[1] * u[1] + C[2] * u[2];
-        Ic[(((size_t)c * 4 + jm * 2 + 1) * Kc + t) * nrhs + r] += C[0] * u[3] + C[1] * u[4] + C[2] * u[5];
+        Ic[(((size_t)c * 4 + jm * 2) * nrhs + r) * Kc + t] += C[0] * u[0] + C[1] * u[1] + C[2] * u[2];
+        Ic[(((size_t)c * 4 + jm * 2 + 1) * nrhs + r) * Kc + t] += C[0] * u[3] + C[1] * u[4] + C[2] * u[5];
       }
-      __syncthreads();
-    }
+  }
 }
 
 // Diagonal M2L translation: I_b(k) = sum_{b' in IL(b)} T_{b-b'}(k) S_b'(k), 4 components.
@@ -373,7 +375,7 @@ __global__ void k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr,
   int b = blockIdx.y;
   if (k >= K) return;
   int e0 = il_ptr[b], e1 = il_ptr[b + 1];
-  const size_t cs = (size_t)K * nrhs;  // component stride
+  const size_t cs = (size_t)nrhs * K;  // component stride
   for (int r = 0; r < nrhs; ++r) {
     cx<T> a0, a1, a2, a3;
     int e = e0;
@@ -389,7 +391,7 @@ __global__ void k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr,
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         t[u] = Tr[(size_t)sl[u] * K + k];
-        const cx<T> *src = S + ((size_t)s[u] * 4 * K + k) * nrhs + r;
+        const cx<T> *src = S + ((size_t)s[u] * 4 * nrhs + r) * K + k;
 #pragma unroll
         for (int q = 0; q < 4; ++q) v[u][q] = src[q * cs];
       }
@@ -404,17 +406,17 @@ __global__ void k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr,
     for (; e < e1; ++e) {
       int s = il_src[e];
       cx<T> t = Tr[(size_t)il_slot[e] * K + k];
-      const cx<T> *src = S + ((size_t)s * 4 * K + k) * nrhs + r;
+      const cx<T> *src = S + ((size_t)s * 4 * nrhs + r) * K + k;
       a0 = cfma(t, src[0], a0);
       a1 = cfma(t, src[cs], a1);
       a2 = cfma(t, src[2 * cs], a2);
       a3 = cfma(t, src[3 * cs], a3);
     }
-    cx<T> *o = I + ((size_t)b * 4 * K + k) * nrhs + r;
+    cx<T> *o = I + ((size_t)b * 4 * nrhs + r) * K + k;
     o[0] = a0;
-    o[(size_t)K * nrhs] = a1;
-    o[(size_t)2 * K * nrhs] = a2;
-    o[(size_t)3 * K * nrhs] = a3;
+    o[cs] = a1;
+    o[2 * cs] = a2;
+    o[3 * cs] = a3;
   }
 }
 
@@ -438,14 +440,15 @@ __global__ void k_disaggregate(int nb, int K, int L, int ne, int nrhs, const int
   const cx<T> *Vi = V + (size_t)i * 2 * K, *Ri = RN + (size_t)i * 2 * K;
   for (int r = 0; r < nrhs; ++r) {
     cx<T> yj, ym;
-    const cx<T> *Ib = I + (size_t)b * 4 * K * nrhs + r;
+    const size_t cs = (size_t)nrhs * K;
+    const cx<T> *Ib = I + ((size_t)b * 4 * nrhs + r) * K;
     for (int k = lane; k < K; k += 32) {
       int it = k / nph, jp = k - it * nph;
       int ka = (L - it) * nph + (jp + L + 1) % nph;
       cx<T> rtt = Vi[ka], rtp = -Vi[K + ka];
       cx<T> rnt = Ri[k], rnp = Ri[K + k];
-      cx<T> iJt = Ib[(size_t)k * nrhs], iJp = Ib[(size_t)(K + k) * nrhs];
-      cx<T> iMt = Ib[(size_t)(2 * K + k) * nrhs], iMp = Ib[(size_t)(3 * K + k) * nrhs];
+      cx<T> iJt = Ib[k], iJp = Ib[cs + k];
+      cx<T> iMt = Ib[2 * cs + k], iMp = Ib[3 * cs + k];
       // khat x (a_t, a_p) = (-a_p, a_t)
       cx<T> f1t = iJt + iMp * ieta, f1p = iJp - iMt * ieta;
       cx<T> f3t = eta * iJp - iMt, f3p = -(eta * iJt) - iMp;
@@ -710,7 +713,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
                     (size_t)((2 * P.L + 2) * (2 * C.L + 2) + 2 * (P.L + 1) * (C.L + 1)) * sizeof(T);
       set_smem(k_interp_up<T>, smem);
       cx<T> *Y = (cx<T> *)c->d_scratch;
-      k_interp_up<T><<<dim3(C.nbox, 2), 256, smem, c->stream>>>(
+      k_interp_up<T><<<dim3(C.nbox, 2, R), 256, smem, c->stream>>>(
           C.K, C.L, P.K, P.L, R, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
           (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
           (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
@@ -735,7 +738,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       size_t smem = (size_t)(3 * P.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>) +
                     (size_t)((2 * P.L + 2) * (2 * C.L + 2) + 2 * (P.L + 1) * (C.L + 1)) * sizeof(T);
       set_smem(k_anterp_dn<T>, smem);
-      k_anterp_dn<T><<<dim3(C.nbox, 2), 256, smem, c->stream>>>(
+      k_anterp_dn<T><<<dim3(C.nbox, 2, R), 256, smem, c->stream>>>(
           C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
           (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
           (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
