@@ -111,10 +111,14 @@ struct IluHost {
   int *d_box_start = nullptr;      // [nbox+1] internal edge ranges
   int *d_box_list = nullptr;       // boxes in colour order
   int *d_lo_ptr = nullptr, *d_lo_col = nullptr, *d_up_ptr = nullptr, *d_up_col = nullptr;
+  // per row, [9] starts of each column colour's blocks within its off-box range (the 9th = end)
+  int *d_lo_cptr = nullptr, *d_up_cptr = nullptr;
   void *d_lo64 = nullptr, *d_lo32 = nullptr, *d_up64 = nullptr, *d_up32 = nullptr;  // off-box blocks [.][4]
-  int64_t *d_dense_off = nullptr;  // per box offset (in blocks) of the dense in-box factor
-  void *d_dense64 = nullptr, *d_dense32 = nullptr;  // column-major [j][i][4] per box
-  void *d_dinv64 = nullptr, *d_dinv32 = nullptr;    // inverse of U diagonal blocks [ne][4]
+  // in-box inverses packed by rows, per box: strictly lower part of L_bb^{-1}
+  // (its diagonal blocks are identities; row i holds blocks j < i) and the
+  // upper part, diagonal included, of U_bb^{-1} (row i holds blocks j >= i)
+  int64_t *d_tl_off = nullptr, *d_tu_off = nullptr;  // per box offsets, in blocks
+  void *d_tl64 = nullptr, *d_tl32 = nullptr, *d_tu64 = nullptr, *d_tu32 = nullptr;
   int max_box = 0;
 };
 

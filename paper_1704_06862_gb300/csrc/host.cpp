@@ -778,23 +778,15 @@ static void build_ilu(sie_ctx *c) {
     for (int p = c->leaf_start[b]; p < c->leaf_start[b + 1]; ++p) ebox[p] = b;
   std::vector<int> lo_ptr(1, 0), up_ptr(1, 0), lo_col, up_col;
   std::vector<cd> lo_val, up_val;
-  std::vector<int64_t> doff(nlb + 1, 0);
   int maxb = 0;
-  for (int b = 0; b < nlb; ++b) {
-    int n = c->leaf_start[b + 1] - c->leaf_start[b];
-    maxb = std::max(maxb, n);
-    doff[b + 1] = doff[b] + (int64_t)n * n;
-  }
-  std::vector<cd> dense((size_t)doff[nlb] * 4);
+  for (int b = 0; b < nlb; ++b) maxb = std::max(maxb, c->leaf_start[b + 1] - c->leaf_start[b]);
   for (int i = 0; i < ne; ++i) {
-    int bi = ebox[i], s0 = c->leaf_start[bi], n = c->leaf_start[bi + 1] - s0;
+    int bi = ebox[i];
     for (int q = c->row_ptr[i]; q < c->row_ptr[i + 1]; ++q) {
       int k = c->col[q];
       const cd *v = &F[4 * (size_t)q];
-      if (ebox[k] == bi) {
-        size_t o = (size_t)(doff[bi] + (int64_t)(k - s0) * n + (i - s0)) * 4;
-        for (int x = 0; x < 4; ++x) dense[o + x] = v[x];
-      } else if (k < i) {
+      if (ebox[k] == bi) continue;
+      if (k < i) {
         lo_col.push_back(k);
         for (int x = 0; x < 4; ++x) lo_val.push_back(v[x]);
       } else {
@@ -804,6 +796,72 @@ static void build_ilu(sie_ctx *c) {
     }
     lo_ptr.push_back((int)lo_col.size());
     up_ptr.push_back((int)up_col.size());
+  }
+  // in-box inverses, row-major blocks per box: X = L_bb^{-1} below the diagonal
+  // (unit lower, X_jj = I), Y = U_bb^{-1} on and above it, by block substitution
+  std::vector<int64_t> tloff(nlb + 1, 0), tuoff(nlb + 1, 0);
+  for (int b = 0; b < nlb; ++b) {
+    int64_t n = c->leaf_start[b + 1] - c->leaf_start[b];
+    tloff[b + 1] = tloff[b] + n * (n - 1) / 2;
+    tuoff[b + 1] = tuoff[b] + n * (n + 1) / 2;
+  }
+  std::vector<cd> tl((size_t)tloff[nlb] * 4), tu((size_t)tuoff[nlb] * 4);
+  {
+    std::atomic<int> next(0);
+    auto work = [&]() {
+      std::vector<cd> A, Xv;
+      for (;;) {
+        int b = next.fetch_add(1);
+        if (b >= nlb) break;
+        const int s0 = c->leaf_start[b], n = c->leaf_start[b + 1] - s0;
+        A.assign((size_t)n * n * 4, cd(0.0));
+        for (int i = s0; i < s0 + n; ++i)
+          for (int q = c->row_ptr[i]; q < c->row_ptr[i + 1]; ++q) {
+            int k = c->col[q];
+            if (k < s0 || k >= s0 + n) continue;
+            for (int x = 0; x < 4; ++x) A[((size_t)(i - s0) * n + (k - s0)) * 4 + x] = F[4 * (size_t)q + x];
+          }
+        Xv.assign((size_t)n * n * 4, cd(0.0));
+        cd *X = Xv.data();
+        auto blk = [&](cd *M, int i, int j) { return M + ((size_t)i * n + j) * 4; };
+        for (int j = 0; j < n; ++j) {
+          // column j of L^{-1}: X_ij = -sum_{j<=k<i} L_ik X_kj, X_jj = I (implicit)
+          for (int i = j + 1; i < n; ++i) {
+            cd acc[4] = {-A[((size_t)i * n + j) * 4], -A[((size_t)i * n + j) * 4 + 1],
+                         -A[((size_t)i * n + j) * 4 + 2], -A[((size_t)i * n + j) * 4 + 3]};
+            for (int k = j + 1; k < i; ++k) {
+              cd u[4];
+              mul2(blk(A.data(), i, k), blk(X, k, j), u);
+              for (int x = 0; x < 4; ++x) acc[x] -= u[x];
+            }
+            for (int x = 0; x < 4; ++x) blk(X, i, j)[x] = acc[x];
+          }
+          // column j of U^{-1}: Y_jj = D_j^{-1}, Y_ij = -D_i^{-1} sum_{i<k<=j} U_ik Y_kj
+          for (int x = 0; x < 4; ++x) blk(X, j, j)[x] = Dinv[4 * (size_t)(s0 + j) + x];
+          for (int i = j - 1; i >= 0; --i) {
+            cd acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int k = i + 1; k <= j; ++k) {
+              cd u[4];
+              mul2(blk(A.data(), i, k), blk(X, k, j), u);
+              for (int x = 0; x < 4; ++x) acc[x] -= u[x];
+            }
+            mul2(&Dinv[4 * (size_t)(s0 + i)], acc, blk(X, i, j));
+          }
+        }
+        // pack by rows
+        for (int i = 0; i < n; ++i) {
+          cd *dl = &tl[(size_t)(tloff[b] + (int64_t)i * (i - 1) / 2) * 4];
+          for (int j = 0; j < i; ++j)
+            for (int x = 0; x < 4; ++x) dl[4 * j + x] = blk(X, i, j)[x];
+          cd *du = &tu[(size_t)(tuoff[b] + (int64_t)i * n - (int64_t)i * (i - 1) / 2) * 4];
+          for (int j = i; j < n; ++j)
+            for (int x = 0; x < 4; ++x) du[4 * (j - i) + x] = blk(X, i, j)[x];
+        }
+      }
+    };
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nth; ++t) th.emplace_back(work);
+    for (auto &t : th) t.join();
   }
   IluHost &I = c->ilu;
   I.nboxes = nlb;
@@ -816,12 +874,29 @@ static void build_ilu(sie_ctx *c) {
   I.d_lo_ptr = dev_upload(c, lo_ptr);
   I.d_up_ptr = dev_upload(c, up_ptr);
   I.d_lo_col = dev_upload(c, lo_col);
+  {
+    auto colour_ptrs = [&](const std::vector<int> &ptr, const std::vector<int> &col) {
+      std::vector<int> cp((size_t)ne * 9);
+      for (int i = 0; i < ne; ++i) {
+        int q = ptr[i];
+        for (int k = 0; k < 8; ++k) {
+          while (q < ptr[i + 1] && bcol[ebox[col[q]]] < k) ++q;
+          cp[9 * (size_t)i + k] = q;
+        }
+        cp[9 * (size_t)i + 8] = ptr[i + 1];
+      }
+      return cp;
+    };
+    I.d_lo_cptr = dev_upload(c, colour_ptrs(lo_ptr, lo_col));
+    I.d_up_cptr = dev_upload(c, colour_ptrs(up_ptr, up_col));
+  }
   I.d_up_col = dev_upload(c, up_col);
   I.d_lo64 = dev_upload(c, lo_val);
   I.d_up64 = dev_upload(c, up_val);
-  I.d_dense_off = dev_upload(c, doff);
-  I.d_dense64 = dev_upload(c, dense);
-  I.d_dinv64 = dev_upload(c, Dinv);
+  I.d_tl_off = dev_upload(c, tloff);
+  I.d_tu_off = dev_upload(c, tuoff);
+  I.d_tl64 = dev_upload(c, tl);
+  I.d_tu64 = dev_upload(c, tu);
   auto f32 = [&](const std::vector<cd> &v) {
     std::vector<std::complex<float>> o(v.size());
     for (size_t q = 0; q < v.size(); ++q) o[q] = std::complex<float>((float)v[q].real(), (float)v[q].imag());
@@ -829,8 +904,8 @@ static void build_ilu(sie_ctx *c) {
   };
   I.d_lo32 = f32(lo_val);
   I.d_up32 = f32(up_val);
-  I.d_dense32 = f32(dense);
-  I.d_dinv32 = f32(Dinv);
+  I.d_tl32 = f32(tl);
+  I.d_tu32 = f32(tu);
   I.ready = true;
 }
 

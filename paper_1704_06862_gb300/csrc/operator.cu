@@ -23,8 +23,8 @@ template <> struct tsel<double> {
   static void *dn(LevelHost &L) { return L.d_dn64; }
   static void *lo(IluHost &I) { return I.d_lo64; }
   static void *upv(IluHost &I) { return I.d_up64; }
-  static void *dense(IluHost &I) { return I.d_dense64; }
-  static void *dinv(IluHost &I) { return I.d_dinv64; }
+  static void *tl(IluHost &I) { return I.d_tl64; }
+  static void *tu(IluHost &I) { return I.d_tu64; }
 };
 template <> struct tsel<float> {
   static void *near(sie_ctx *c) { return c->d_near32; }
@@ -39,13 +39,25 @@ template <> struct tsel<float> {
   static void *dn(LevelHost &L) { return L.d_dn32; }
   static void *lo(IluHost &I) { return I.d_lo32; }
   static void *upv(IluHost &I) { return I.d_up32; }
-  static void *dense(IluHost &I) { return I.d_dense32; }
-  static void *dinv(IluHost &I) { return I.d_dinv32; }
+  static void *tl(IluHost &I) { return I.d_tl32; }
+  static void *tu(IluHost &I) { return I.d_tu32; }
 };
 
 template <typename T>
 __device__ __forceinline__ cx<T> shfl_down(cx<T> v, int d) {
   return cx<T>(__shfl_down_sync(0xffffffffu, v.re, d), __shfl_down_sync(0xffffffffu, v.im, d));
+}
+// the two unknowns (J, M) of one edge through the read-only path; p is 16-byte
+// aligned (vectors start on 256-byte boundaries, an edge's pair is 2 complex)
+__device__ __forceinline__ void ldg_pair(const cx<float> *p, cx<float> &x0, cx<float> &x1) {
+  float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  x0 = cx<float>(v.x, v.y);
+  x1 = cx<float>(v.z, v.w);
+}
+__device__ __forceinline__ void ldg_pair(const cx<double> *p, cx<double> &x0, cx<double> &x1) {
+  double2 v0 = __ldg(reinterpret_cast<const double2 *>(p)), v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  x0 = cx<double>(v0.x, v0.y);
+  x1 = cx<double>(v1.x, v1.y);
 }
 template <typename T>
 __device__ __forceinline__ cx<T> warp_sum(cx<T> v) {
@@ -467,171 +479,349 @@ __global__ void k_disaggregate(int nb, int K, int L, int ne, int nrhs, const int
 
 // ---------------------------------------------------------------- ILU(0) sweeps
 // The factors are stored in the box-colour order: for colour c, the rows of
-// all its leaf boxes are contiguous and no two of its boxes touch.  Forward
-// sweep per colour: (1) off-box part  z_i = v_i - sum_{q in earlier colours} L_iq z_q
-// for every row of the colour (one warp per row, GPU-wide); (2) in-box unit
-// lower solve, one CTA per box with the box's strictly lower triangle staged
-// in shared memory.  Backward: the same with U, later colours and the
-// inverted 2x2 diagonal blocks.
+// all its leaf boxes are contiguous and no two of its boxes touch, so a box's
+// rows couple only to its own rows and to rows of other colours.  One launch
+// per colour and sweep, one CTA per box of the colour:
+//   (1) t_b = src_b - sum_q F_bq z_q over the off-box blocks of the box's rows
+//       (earlier colours in the forward sweep, later ones in the backward);
+//   (2) z_b = L_bb^{-1} t_b (forward) or U_bb^{-1} t_b (backward).
+// The in-box inverses are formed once at setup, so (2) is a dense product
+// instead of a sequential substitution; z equals the substitution result up
+// to rounding.  The inverses are packed by rows: forward, row i holds the
+// blocks j < i of L_bb^{-1} (its diagonal blocks are identities); backward,
+// row i holds the blocks j >= i of U_bb^{-1}.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T>
-__device__ __forceinline__ void mv2(const cx<T> *B, cx<T> x0, cx<T> x1, cx<T> &y0, cx<T> &y1) {
-  y0 = B[0] * x0 + B[1] * x1;
-  y1 = B[2] * x0 + B[3] * x1;
+__device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
+  return cx<T>(__shfl_up_sync(0xffffffffu, v.re, d), __shfl_up_sync(0xffffffffu, v.im, d));
 }
 
-constexpr int ILU_RC = 8;  // right-hand sides carried together through the in-box solve
-
-// off-box product for a block of right-hand sides: each block loaded once per RB of them
-template <typename T, int RB>
-__global__ void k_ilu_offbox_blk(int ne, int nrhs, int row0, int row1, const int *__restrict__ off_ptr,
-                                 const int *__restrict__ off_col, const cx<T> *__restrict__ off_val,
-                                 const cx<T> *src, cx<T> *z) {
-  int i = row0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  int lane = threadIdx.x & 31;
-  if (i >= row1) return;
-  int q0 = off_ptr[i], q1 = off_ptr[i + 1];
-  const size_t vs = (size_t)ne * 2;
-  for (int r0 = 0; r0 < nrhs; r0 += RB) {
-    const int nr = min(RB, nrhs - r0);
-    cx<T> a0[RB], a1[RB];
-    for (int q = q0 + lane; q < q1; q += 32) {
-      int cc = off_col[q];
-      const cx<T> *B = off_val + 4 * (size_t)q;
-      cx<T> b0 = B[0], b1 = B[1], b2 = B[2], b3 = B[3];
-#pragma unroll
-      for (int rr = 0; rr < RB; ++rr)
-        if (rr < nr) {
-          const cx<T> *zr = z + (size_t)(r0 + rr) * vs;
-          cx<T> x0 = zr[2 * cc], x1 = zr[2 * cc + 1];
-          a0[rr] += b0 * x0 + b1 * x1;
-          a1[rr] += b2 * x0 + b3 * x1;
-        }
+// Single right-hand side: the off-box products are pushed one source colour
+// at a time, so that each launch has the whole GPU's worth of short rows.
+// Sweep step for colour c with source colour sc (forward: c-1, backward: c+1):
+//   role A, one CTA per box B of colour c:
+//       t_B = w_B - F_{B,sc} z_sc,   z_B = L_BB^{-1} t_B   (U_BB^{-1} backward);
+//       the last forward step also applies U_BB^{-1} (colour 7 has no later colour);
+//   role B, one warp per row i of the colours still to come:
+//       w_i -= F_{i,sc} z_sc   (the first forward step copies w = src).
+// w lives in z until the row is solved.  Each row's off-box blocks are sorted
+// by column, hence grouped by colour; cptr[i][c] .. cptr[i][c+1] is colour c.
+// In role A the box's blocks from sc are spread evenly over the CTA in groups
+// of 32 (one per lane); a segmented scan over the lanes keyed by row adds each
+// row's products, every warp keeps its own row partials, and the warps'
+// partials are added in warp order, so the result is deterministic.  The
+// packed in-box inverse is copied to shared memory asynchronously meanwhile.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int colour, int nboxA, int box0, int rb0,
+                                                  int rb1, int stage_tri, const int *__restrict__ box_start,
+                                                  const int *__restrict__ cptr, const int *__restrict__ off_col,
+                                                  const cx<T> *__restrict__ off_val,
+                                                  const int64_t *__restrict__ tri_off, const cx<T> *__restrict__ tri,
+                                                  const int64_t *__restrict__ tri2_off,
+                                                  const cx<T> *__restrict__ tri2, const cx<T> *src, cx<T> *z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NW = NT / 32;
+  typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V16;
+  constexpr int NV = (int)(4 * sizeof(cx<T>) / sizeof(V16));
+  const V16 *Ov = reinterpret_cast<const V16 *>(off_val);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sc = forward ? colour - 1 : colour + 1;
+  const bool has_src = sc >= 0 && sc < 8;
+  // w of rows not yet solved: src before the first forward step has run
+  const cx<T> *w = (forward && colour == 0) ? src : z;
+  if ((int)blockIdx.x >= nboxA) {
+    // ---- role B: rows of later colours take the contribution of colour sc
+    const int i = rb0 + ((int)blockIdx.x - nboxA) * NW + warp;
+    if (i >= rb1) return;
+    if (!has_src) {
+      if (lane < 2) z[2 * (size_t)i + lane] = src[2 * (size_t)i + lane];
+      return;
     }
-#pragma unroll
-    for (int rr = 0; rr < RB; ++rr)
-      if (rr < nr) {
-        cx<T> s0 = warp_sum(a0[rr]), s1 = warp_sum(a1[rr]);
-        if (lane == 0) {
-          const cx<T> *sr = src + (size_t)(r0 + rr) * vs + 2 * (size_t)i;
-          cx<T> v0 = sr[0], v1 = sr[1];
-          cx<T> *o = z + (size_t)(r0 + rr) * vs + 2 * (size_t)i;
-          o[0] = v0 - s0;
-          o[1] = v1 - s1;
-        }
-      }
-  }
-}
-
-template <typename T>
-__global__ void k_ilu_offbox(int ne, int nrhs, int row0, int row1, const int *__restrict__ off_ptr,
-                             const int *__restrict__ off_col, const cx<T> *__restrict__ off_val,
-                             const cx<T> *src, cx<T> *z) {
-  int i = row0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  int lane = threadIdx.x & 31;
-  if (i >= row1) return;
-  int q0 = off_ptr[i], q1 = off_ptr[i + 1];
-  for (int r = 0; r < nrhs; ++r) {
-    const cx<T> *zr = z + (size_t)r * ne * 2;
+    const int q0 = cptr[9 * (size_t)i + sc], q1 = cptr[9 * (size_t)i + sc + 1];
+    if (q0 == q1) return;
     cx<T> a0, a1;
-    for (int q = q0 + lane; q < q1; q += 32) {
-      int cc = off_col[q];
-      cx<T> t0, t1;
-      mv2(off_val + 4 * (size_t)q, zr[2 * cc], zr[2 * cc + 1], t0, t1);
-      a0 += t0;
-      a1 += t1;
+    int q = q0 + lane;
+    for (; q + 32 < q1; q += 64) {
+      const int c0 = __ldg(off_col + q), c1 = __ldg(off_col + q + 32);
+      V16 u0[NV], u1[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        u0[v] = __ldg(Ov + (size_t)q * NV + v);
+        u1[v] = __ldg(Ov + (size_t)(q + 32) * NV + v);
+      }
+      cx<T> x0, x1, y0, y1;
+      ldg_pair(z + 2 * (size_t)c0, x0, x1);  // colour sc: not written by this launch
+      ldg_pair(z + 2 * (size_t)c1, y0, y1);
+      const cx<T> *b0 = reinterpret_cast<const cx<T> *>(u0), *b1 = reinterpret_cast<const cx<T> *>(u1);
+      a0 = cfma(b0[0], x0, cfma(b0[1], x1, a0));
+      a1 = cfma(b0[2], x0, cfma(b0[3], x1, a1));
+      a0 = cfma(b1[0], y0, cfma(b1[1], y1, a0));
+      a1 = cfma(b1[2], y0, cfma(b1[3], y1, a1));
+    }
+    if (q < q1) {
+      const int c0 = __ldg(off_col + q);
+      V16 u0[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) u0[v] = __ldg(Ov + (size_t)q * NV + v);
+      cx<T> x0, x1;
+      ldg_pair(z + 2 * (size_t)c0, x0, x1);
+      const cx<T> *b0 = reinterpret_cast<const cx<T> *>(u0);
+      a0 = cfma(b0[0], x0, cfma(b0[1], x1, a0));
+      a1 = cfma(b0[2], x0, cfma(b0[3], x1, a1));
     }
     a0 = warp_sum(a0);
     a1 = warp_sum(a1);
     if (lane == 0) {
-      const cx<T> *sr = src + ((size_t)r * ne + i) * 2;
-      cx<T> s0 = sr[0], s1 = sr[1];
-      cx<T> *o = z + ((size_t)r * ne + i) * 2;
-      o[0] = s0 - a0;
-      o[1] = s1 - a1;
+      z[2 * (size_t)i] -= a0;
+      z[2 * (size_t)i + 1] -= a1;
     }
+    return;
+  }
+  // ---- role A: one box of this colour
+  const int b = box0 + blockIdx.x;
+  const int s0 = box_start[b], n = box_start[b + 1] - s0;
+  const int ntri = forward ? n * (n - 1) / 2 : n * (n + 1) / 2;
+  const cx<T> *Mg = tri + 4 * tri_off[b];
+  // shared: [packed triangle (if staged)] [NW][n][2] partials, [2n] t, [2n] t2, [n+1] prefix, [n] starts
+  cx<T> *Ms = reinterpret_cast<cx<T> *>(smem_raw);
+  cx<T> *part = Ms + (stage_tri ? 4 * (size_t)ntri : 0);
+  cx<T> *t = part + (size_t)NW * 2 * n;
+  cx<T> *t2 = t + 2 * n;
+  int *pre = reinterpret_cast<int *>(t2 + 2 * n);
+  int *st = pre + n + 1;
+  if (stage_tri) {
+    const size_t bytes = (size_t)ntri * 4 * sizeof(cx<T>);
+    const char *g = reinterpret_cast<const char *>(Mg);
+    char *d = reinterpret_cast<char *>(Ms);
+    for (size_t o = (size_t)threadIdx.x * 16; o < bytes; o += (size_t)NT * 16) cp_async16(d + o, g + o);
+    cp_async_commit();
+  }
+  for (int idx = threadIdx.x; idx < NW * 2 * n; idx += NT) part[idx] = cx<T>();
+  if (warp == 0) {
+    // prefix of the rows' block counts from colour sc
+    int carry = 0;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int li = c0 + lane;
+      int len = 0;
+      if (li < n && has_src) {
+        const int a = cptr[9 * (size_t)(s0 + li) + sc];
+        len = cptr[9 * (size_t)(s0 + li) + sc + 1] - a;
+        st[li] = a;
+      }
+      int inc = len;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += u;
+      }
+      if (li < n) pre[li] = carry + inc - len;
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) pre[n] = carry;
+  }
+  __syncthreads();
+  const int total = pre[n];
+  const int ng = (total + 31) >> 5;
+  const int g0 = (int)((int64_t)warp * ng / NW), g1 = (int)((int64_t)(warp + 1) * ng / NW);
+  cx<T> *pw = part + (size_t)warp * 2 * n;
+  // virtual index v of the box's blocks -> row (last row whose prefix is <= v) and block index
+  auto locate = [&](int v, int &r, int &q) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pre[mid] <= v) lo = mid;
+      else hi = mid - 1;
+    }
+    r = lo;
+    q = st[lo] + v - pre[lo];
+  };
+  auto segsum = [&](int r, cx<T> p0, cx<T> p1) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const cx<T> u0 = shfl_up(p0, d), u1 = shfl_up(p1, d);
+      const int ru = __shfl_up_sync(0xffffffffu, r, d);
+      if (lane >= d && ru == r) {
+        p0 += u0;
+        p1 += u1;
+      }
+    }
+    const int rn = __shfl_down_sync(0xffffffffu, r, 1);
+    if (r >= 0 && (lane == 31 || rn != r)) {
+      pw[2 * r] += p0;
+      pw[2 * r + 1] += p1;
+    }
+    __syncwarp();
+  };
+  for (int g = g0; g < g1; g += 2) {
+    // two groups in flight: issue both groups' loads, then reduce
+    const int vA = g * 32 + lane, vB = vA + 32;
+    const bool hasB = g + 1 < g1;
+    int rA = -1, rB = -1, qA = 0, qB = 0, cA = 0, cB = 0;
+    V16 uA[NV], uB[NV];
+    if (vA < total) {
+      locate(vA, rA, qA);
+      cA = __ldg(off_col + qA);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) uA[v] = __ldg(Ov + (size_t)qA * NV + v);
+    }
+    if (hasB && vB < total) {
+      locate(vB, rB, qB);
+      cB = __ldg(off_col + qB);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) uB[v] = __ldg(Ov + (size_t)qB * NV + v);
+    }
+    cx<T> a0, a1, b0, b1;
+    if (rA >= 0) {
+      const cx<T> *bb = reinterpret_cast<const cx<T> *>(uA);
+      cx<T> x0, x1;
+      ldg_pair(z + 2 * (size_t)cA, x0, x1);
+      a0 = cfma(bb[0], x0, bb[1] * x1);
+      a1 = cfma(bb[2], x0, bb[3] * x1);
+    }
+    if (rB >= 0) {
+      const cx<T> *bb = reinterpret_cast<const cx<T> *>(uB);
+      cx<T> x0, x1;
+      ldg_pair(z + 2 * (size_t)cB, x0, x1);
+      b0 = cfma(bb[0], x0, bb[1] * x1);
+      b1 = cfma(bb[2], x0, bb[3] * x1);
+    }
+    segsum(rA, a0, a1);
+    if (hasB) segsum(rB, b0, b1);
+  }
+  __syncthreads();
+  for (int li = threadIdx.x; li < n; li += NT) {
+    cx<T> u0 = w[2 * (size_t)(s0 + li)], u1 = w[2 * (size_t)(s0 + li) + 1];
+    for (int ww = 0; ww < NW; ++ww) {
+      u0 -= part[(size_t)ww * 2 * n + 2 * li];
+      u1 -= part[(size_t)ww * 2 * n + 2 * li + 1];
+    }
+    t[2 * li] = u0;
+    t[2 * li + 1] = u1;
+  }
+  if (stage_tri) cp_async_wait_all();
+  __syncthreads();
+  // in-box product(s): rows one per warp, lanes over the row's packed blocks
+  for (int pass = 0; pass < (both ? 2 : 1); ++pass) {
+    const bool lower = forward && pass == 0;
+    const cx<T> *M = pass == 0 ? (stage_tri ? Ms : Mg) : tri2 + 4 * tri2_off[b];
+    const cx<T> *in = pass == 0 ? t : t2;
+    for (int li = warp; li < n; li += NW) {
+      const int j0 = lower ? 0 : li, j1 = lower ? li : n;
+      const cx<T> *row = M + 4 * (size_t)(lower ? li * (li - 1) / 2 : li * n - li * (li - 1) / 2);
+      cx<T> a0, a1;
+      for (int j = j0 + lane; j < j1; j += 32) {
+        const cx<T> *B = row + 4 * (j - j0);
+        const cx<T> x0 = in[2 * j], x1 = in[2 * j + 1];
+        a0 = cfma(B[0], x0, cfma(B[1], x1, a0));
+        a1 = cfma(B[2], x0, cfma(B[3], x1, a1));
+      }
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      if (lane == 0) {
+        if (lower) {
+          a0 += in[2 * li];
+          a1 += in[2 * li + 1];
+        }
+        if (both && pass == 0) {
+          t2[2 * li] = a0;
+          t2[2 * li + 1] = a1;
+        } else {
+          z[2 * (size_t)(s0 + li)] = a0;
+          z[2 * (size_t)(s0 + li) + 1] = a1;
+        }
+      }
+    }
+    if (both && pass == 0) __syncthreads();
   }
 }
 
-template <typename T>
-__global__ void k_ilu_inbox(int ne, int nrhs, int forward, int box0, int staged, const int *__restrict__ box_start,
-                            const int64_t *__restrict__ dense_off, const cx<T> *__restrict__ dense,
-                            const cx<T> *__restrict__ dinv, cx<T> *z) {
-  extern __shared__ unsigned char smem_raw[];
+// Block of right-hand sides: rows one per warp with lanes over the blocks of
+// the row; RB right-hand sides share every block load.
+template <typename T, int RB>
+__global__ void __launch_bounds__(512) k_ilu_colour(int ne, int nrhs, int forward, int box0,
+                                                    const int *__restrict__ box_start,
+                                                    const int *__restrict__ off_ptr,
+                                                    const int *__restrict__ off_col,
+                                                    const cx<T> *__restrict__ off_val,
+                                                    const int64_t *__restrict__ tri_off,
+                                                    const cx<T> *__restrict__ tri, const cx<T> *src, cx<T> *z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T> *t = reinterpret_cast<cx<T> *>(smem_raw);  // [RB][2n]
   const int b = box0 + blockIdx.x;
   const int s0 = box_start[b], n = box_start[b + 1] - s0;
-  const cx<T> *D = dense + 4 * dense_off[b];  // column-major n x n blocks
-  cx<T> *rr = reinterpret_cast<cx<T> *>(smem_raw);  // [ILU_RC][2n]
-  cx<T> *tri = rr + 2 * n * min(nrhs, ILU_RC);      // packed triangle [n(n-1)/2][4]
+  const cx<T> *M = tri + 4 * tri_off[b];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  // packed column start: forward keeps rows j+1..n-1 of column j, backward rows 0..j-1
-  auto pcol = [&](int j) { return forward ? j * (n - 1) - j * (j - 1) / 2 : j * (j - 1) / 2; };
-  if (staged) {
-    // one 2x2 block is 4 complex values: copy it as 16-byte words, many in flight
-    constexpr int W = (int)(4 * sizeof(cx<T>) / 16);
-    const int4 *Dv = reinterpret_cast<const int4 *>(D);
-    int4 *Tv = reinterpret_cast<int4 *>(tri);
-    for (int j = warp; j < n; j += nw) {
-      int lo = forward ? j + 1 : 0, hi = forward ? n : j;
-      int base = pcol(j) - lo;
-      int cnt = (hi - lo) * W;
-      const int4 *src = Dv + ((size_t)j * n + lo) * W;
-      int4 *dst = Tv + (size_t)(base + lo) * W;
-#pragma unroll 4
-      for (int q = lane; q < cnt; q += 32) dst[q] = src[q];
-    }
-  }
-  // right-hand sides in chunks of ILU_RC; within a step, lanes run over (row, rhs) pairs
-  for (int r0 = 0; r0 < nrhs; r0 += ILU_RC) {
-    const int nr = min(ILU_RC, nrhs - r0);
-    for (int t = threadIdx.x; t < 2 * n * nr; t += blockDim.x) {
-      int r = t / (2 * n), u = t - r * 2 * n;
-      rr[t] = z[((size_t)(r0 + r) * ne + s0) * 2 + u];
-    }
-    __syncthreads();
-    if (warp == 0) {
-      if (forward) {
-        for (int j = 0; j < n; ++j) {
-          __syncwarp();
-          const cx<T> *col = staged ? tri + 4 * (pcol(j) - (j + 1)) : D + 4 * (size_t)j * n;
-          const int cnt = (n - j - 1) * nr;
-          for (int idx = lane; idx < cnt; idx += 32) {
-            int li = nr == 1 ? j + 1 + idx : j + 1 + idx / nr, r = nr == 1 ? 0 : idx % nr;
-            cx<T> *v = rr + (size_t)r * 2 * n;
-            cx<T> t0, t1;
-            mv2(col + 4 * li, v[2 * j], v[2 * j + 1], t0, t1);
-            v[2 * li] -= t0;
-            v[2 * li + 1] -= t1;
-          }
-        }
-      } else {
-        for (int j = n - 1; j >= 0; --j) {
-          __syncwarp();
-          if (lane < nr) {
-            cx<T> *v = rr + (size_t)lane * 2 * n;
+  const size_t vs = (size_t)ne * 2;
+  typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V16;
+  constexpr int NV = (int)(4 * sizeof(cx<T>) / sizeof(V16));
+  const V16 *Ov = reinterpret_cast<const V16 *>(off_val);
+  for (int r0 = 0; r0 < nrhs; r0 += RB) {
+    const int nr = min(RB, nrhs - r0);
+    for (int li = warp; li < n; li += nw) {
+      const int i = s0 + li, q0 = off_ptr[i], q1 = off_ptr[i + 1];
+      cx<T> a0[RB], a1[RB];
+      for (int q = q0 + lane; q < q1; q += 32) {
+        const int cc = __ldg(off_col + q);
+        V16 u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = __ldg(Ov + (size_t)q * NV + v);
+        const cx<T> *bb = reinterpret_cast<const cx<T> *>(u);
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+          if (rr < nr) {
             cx<T> x0, x1;
-            mv2(dinv + 4 * (size_t)(s0 + j), v[2 * j], v[2 * j + 1], x0, x1);
-            v[2 * j] = x0;
-            v[2 * j + 1] = x1;
+            ldg_pair(z + (size_t)(r0 + rr) * vs + 2 * (size_t)cc, x0, x1);  // other colours only
+            a0[rr] = cfma(bb[0], x0, cfma(bb[1], x1, a0[rr]));
+            a1[rr] = cfma(bb[2], x0, cfma(bb[3], x1, a1[rr]));
           }
-          __syncwarp();
-          const cx<T> *col = staged ? tri + 4 * pcol(j) : D + 4 * (size_t)j * n;
-          const int cnt = j * nr;
-          for (int idx = lane; idx < cnt; idx += 32) {
-            int li = nr == 1 ? idx : idx / nr, r = nr == 1 ? 0 : idx % nr;
-            cx<T> *v = rr + (size_t)r * 2 * n;
-            cx<T> t0, t1;
-            mv2(col + 4 * li, v[2 * j], v[2 * j + 1], t0, t1);
-            v[2 * li] -= t0;
-            v[2 * li + 1] -= t1;
+      }
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr)
+        if (rr < nr) {
+          const cx<T> u0 = warp_sum(a0[rr]), u1 = warp_sum(a1[rr]);
+          if (lane == 0) {
+            const cx<T> *sr = src + (size_t)(r0 + rr) * vs + 2 * (size_t)i;
+            t[(size_t)rr * 2 * n + 2 * li] = sr[0] - u0;
+            t[(size_t)rr * 2 * n + 2 * li + 1] = sr[1] - u1;
           }
         }
-      }
-      __syncwarp();
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 2 * n * nr; t += blockDim.x) {
-      int r = t / (2 * n), u = t - r * 2 * n;
-      z[((size_t)(r0 + r) * ne + s0) * 2 + u] = rr[t];
+    for (int li = warp; li < n; li += nw) {
+      const int j0 = forward ? 0 : li, j1 = forward ? li : n;
+      const cx<T> *row = M + 4 * (size_t)(forward ? li * (li - 1) / 2 : li * n - li * (li - 1) / 2);
+      cx<T> a0[RB], a1[RB];
+      for (int j = j0 + lane; j < j1; j += 32) {
+        const cx<T> *B = row + 4 * (j - j0);
+        const cx<T> b0 = B[0], b1 = B[1], b2 = B[2], b3 = B[3];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+          if (rr < nr) {
+            const cx<T> x0 = t[(size_t)rr * 2 * n + 2 * j], x1 = t[(size_t)rr * 2 * n + 2 * j + 1];
+            a0[rr] = cfma(b0, x0, cfma(b1, x1, a0[rr]));
+            a1[rr] = cfma(b2, x0, cfma(b3, x1, a1[rr]));
+          }
+      }
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr)
+        if (rr < nr) {
+          cx<T> u0 = warp_sum(a0[rr]), u1 = warp_sum(a1[rr]);
+          if (lane == 0) {
+            if (forward) {
+              u0 += t[(size_t)rr * 2 * n + 2 * li];
+              u1 += t[(size_t)rr * 2 * n + 2 * li + 1];
+            }
+            cx<T> *o = z + (size_t)(r0 + rr) * vs + 2 * (size_t)(s0 + li);
+            o[0] = u0;
+            o[1] = u1;
+          }
+        }
     }
     __syncthreads();
   }
@@ -764,34 +954,50 @@ template <typename T>
 void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
   IluHost &I = c->ilu;
   const int mb = std::max(I.max_box, 1);
-  const size_t rc = (size_t)std::min(nrhs, ILU_RC);
-  size_t full = ((size_t)mb * (mb - 1) / 2 * 4 + 2 * mb * rc) * sizeof(cx<T>);
-  int staged = full <= 200 * 1024 ? 1 : 0;
-  size_t smem = staged ? full : 2 * (size_t)mb * rc * sizeof(cx<T>);
-  set_smem(k_ilu_inbox<T>, smem);
-  constexpr int RB = sizeof(T) == 4 ? 8 : 4;
+  if (nrhs == 1) {
+    constexpr int NT = 512, NW = NT / 32;
+    const size_t base = ((size_t)NW * 2 * mb + 4 * (size_t)mb) * sizeof(cx<T>) + (2 * (size_t)mb + 1) * sizeof(int) + 16;
+    const size_t trib = (size_t)mb * (mb + 1) / 2 * 4 * sizeof(cx<T>);
+    const int stage = base + trib <= 100 * 1024 ? 1 : 0;
+    const size_t smem = base + (stage ? trib : 0);
+    set_smem(k_ilu_sweep<T, NT>, smem);
+    auto rows_from = [&](int colr) { return c->leaf_start[I.colour_ptr[colr]]; };
+    // forward colours 0..7 (the last also applies U^{-1}), then backward 6..0
+    for (int step = 0; step < 15; ++step) {
+      const bool fwd = step < 8;
+      const int colr = fwd ? step : 14 - step;
+      const int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
+      const int rb0 = fwd ? rows_from(colr + 1) : 0, rb1 = fwd ? c->ne : rows_from(colr);
+      const int nrowB = rb1 - rb0;
+      const int grid = cnt + (nrowB + NW - 1) / NW;
+      if (grid == 0) continue;
+      k_ilu_sweep<T, NT><<<grid, NT, smem, c->stream>>>(
+          fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, cnt, first, rb0, rb1, stage, I.d_box_start,
+          fwd ? I.d_lo_cptr : I.d_up_cptr, fwd ? I.d_lo_col : I.d_up_col,
+          (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? I.d_tl_off : I.d_tu_off,
+          (const cx<T> *)(fwd ? tsel<T>::tl(I) : tsel<T>::tu(I)), I.d_tu_off, (const cx<T> *)tsel<T>::tu(I), r, z);
+      SIE_CHECK_LAUNCH();
+      c->launches++;
+    }
+    return;
+  }
   for (int pass = 0; pass < 2; ++pass) {
-    bool fwd = pass == 0;
+    const bool fwd = pass == 0;
+    const int *optr = fwd ? I.d_lo_ptr : I.d_up_ptr, *ocol = fwd ? I.d_lo_col : I.d_up_col;
+    const cx<T> *oval = (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I));
+    const int64_t *toff = fwd ? I.d_tl_off : I.d_tu_off;
+    const cx<T> *tri = (const cx<T> *)(fwd ? tsel<T>::tl(I) : tsel<T>::tu(I));
     for (int q = 0; q < 8; ++q) {
-      int colr = fwd ? q : 7 - q;
-      int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
+      const int colr = fwd ? q : 7 - q;
+      const int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
       if (cnt == 0) continue;
-      int row0 = c->leaf_start[first], row1 = c->leaf_start[first + cnt];
-      int warps = row1 - row0, wpb = 8;
-      if (nrhs == 1)
-        k_ilu_offbox<T><<<(warps + wpb - 1) / wpb, 32 * wpb, 0, c->stream>>>(
-            c->ne, nrhs, row0, row1, fwd ? I.d_lo_ptr : I.d_up_ptr, fwd ? I.d_lo_col : I.d_up_col,
-            (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? r : z, z);
-      else
-        k_ilu_offbox_blk<T, RB><<<(warps + wpb - 1) / wpb, 32 * wpb, 0, c->stream>>>(
-            c->ne, nrhs, row0, row1, fwd ? I.d_lo_ptr : I.d_up_ptr, fwd ? I.d_lo_col : I.d_up_col,
-            (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? r : z, z);
+      constexpr int RB = sizeof(T) == 4 ? 8 : 4;
+      const size_t smem = 2 * (size_t)mb * RB * sizeof(cx<T>);
+      set_smem(k_ilu_colour<T, RB>, smem);
+      k_ilu_colour<T, RB><<<cnt, 32 * std::min(16, mb), smem, c->stream>>>(
+          c->ne, nrhs, fwd ? 1 : 0, first, I.d_box_start, optr, ocol, oval, toff, tri, fwd ? r : z, z);
       SIE_CHECK_LAUNCH();
-      k_ilu_inbox<T><<<cnt, 256, smem, c->stream>>>(c->ne, nrhs, fwd ? 1 : 0, first, staged, I.d_box_start,
-                                                   I.d_dense_off, (const cx<T> *)tsel<T>::dense(I),
-                                                   (const cx<T> *)tsel<T>::dinv(I), z);
-      SIE_CHECK_LAUNCH();
-      c->launches += 2;
+      c->launches++;
     }
   }
 }
