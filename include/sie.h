@@ -248,6 +248,15 @@ sie_status nnprec_loss_grad(sie_ctx *ctx, const float *X_host, const float *T_ho
 sie_status rcs_farfield(sie_ctx *ctx, const void *x_dev, int64_t nrhs, const double *obs_host,
                         int64_t nobs, double *rcs_host);
 
+/* rcs_farfield with a precision: SIE_PREC_FP64 is rcs_farfield itself;
+ * SIE_PREC_MIXED evaluates the radiation integrals with FP32 phases and
+ * currents (positions taken relative to the octree centre, FP32 sums within
+ * a slice of the quadrature points, FP64 across slices), the precision of
+ * the far-field step in the mixed form; the RCS then differs from the FP64
+ * one by about 1e-6 relative.  Other prec values give SIE_EINVAL. */
+sie_status rcs_farfield_prec(sie_ctx *ctx, const void *x_dev, int64_t nrhs, const double *obs_host,
+                             int64_t nobs, int32_t prec, double *rcs_host);
+
 /* Export of the near-field matrix for verification.  With rows == NULL only
  * *nnzb is written.  Otherwise rows/cols [nnzb] int32 receive RWG (user)
  * indices and vals [nnzb][4][2] float64 the block (JJ, JM, MJ, MM) as

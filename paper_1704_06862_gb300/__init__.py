@@ -23,7 +23,7 @@ STATUS = {0: "SIE_OK", 1: "SIE_EINVAL", 2: "SIE_ENOMEM", 3: "SIE_ECUDA", 4: "SIE
           6: "SIE_EBREAKDOWN", 7: "SIE_ETIMEOUT", 8: "SIE_EZEROPIVOT"}
 
 EXPORTED = ["sie_create", "sie_destroy", "sie_last_error", "sie_build_mesh", "mlfmm_setup", "sie_fill_nearfield",
-            "mlfmm_matvec", "sie_matvec_parts", "ilu_apply", "sie_plane_wave_rhs", "gmres_solve", "rcs_farfield",
+            "mlfmm_matvec", "sie_matvec_parts", "ilu_apply", "sie_plane_wave_rhs", "gmres_solve", "rcs_farfield", "rcs_farfield_prec",
             "sie_near_export", "sie_stage_timing", "sie_query", "ilu_apply_noalloc", "nnprec_train",
             "nnprec_params", "nnprec_loss_grad"]
 
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
         "sie_plane_wave_rhs": ([P, P, I64, P], I32),
         "gmres_solve": ([P, P, P, I64, ctypes.POINTER(sie_solve_opts), ctypes.POINTER(sie_solve_stats)], I32),
         "rcs_farfield": ([P, P, I64, P, I64, P], I32),
+        "rcs_farfield_prec": ([P, P, I64, P, I64, I32, P], I32),
         "sie_near_export": ([P, P, P, P, ctypes.POINTER(I64)], I32),
         "sie_query": ([P, I32, ctypes.POINTER(I64)], I32),
         "sie_stage_timing": ([P, I32, I64, I32, I32, ctypes.POINTER(D)], I32),
@@ -193,6 +194,13 @@ def rcs_farfield(ctx, x, nrhs, obs):
     obs = np.ascontiguousarray(obs, np.float64)
     out = np.zeros((int(nrhs), len(obs), 2), np.float64)
     _check(ctx, load_library().rcs_farfield(ctx, _ptr(x), int(nrhs), _ptr(obs), len(obs), _ptr(out)))
+    return out
+
+
+def rcs_farfield_prec(ctx, x, nrhs, obs, prec=SIE_PREC_FP64):
+    obs = np.ascontiguousarray(obs, np.float64)
+    out = np.zeros((int(nrhs), len(obs), 2), np.float64)
+    _check(ctx, load_library().rcs_farfield_prec(ctx, _ptr(x), int(nrhs), _ptr(obs), len(obs), int(prec), _ptr(out)))
     return out
 
 

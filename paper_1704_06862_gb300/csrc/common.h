@@ -162,6 +162,10 @@ struct sie_ctx {
   int *d_tri_e = nullptr;        // per triangle: 3 internal edge ids (-1 none)
   double *d_tri_sg = nullptr;    // per triangle: 3 signs * len/(2A)
   int *d_tri_reg = nullptr;      // [nt][2]
+  int *d_tri0 = nullptr;         // triangles bounding the host medium (region 0)
+  int ntri0 = 0;
+  void *d_ff = nullptr;          // far-field work: point positions, point currents, partial sums
+  size_t ff_bytes = 0;
   int *d_row_ptr = nullptr, *d_col = nullptr;
   void *d_near64 = nullptr, *d_near32 = nullptr;  // [nnzb][4] blocks
   int *d_perm = nullptr, *d_inv = nullptr;
@@ -203,7 +207,8 @@ void launch_near_fill(sie_ctx *c, int region);
 void launch_identity(sie_ctx *c);
 void launch_patterns(sie_ctx *c, int region);
 void launch_rhs(sie_ctx *c, const double *inc_dev, int nrhs, zd *b_internal);
-void launch_farfield(sie_ctx *c, const zd *x_internal, int nrhs, const double *obs_dev, int nobs, double *out_dev);
+void launch_farfield(sie_ctx *c, const zd *x_internal, int nrhs, const double *obs_dev, int nobs, double *out_dev,
+                     sie_prec prec);
 void launch_to_f32(sie_ctx *c, const double *src, float *dst, int64_t n);
 
 // ------------------------------------------------------------------ launchers (operator.cu)

@@ -4,6 +4,8 @@
 // Eq. 30) and far field / RCS (Eqs. 27-29).
 #include <cmath>
 
+#include <algorithm>
+
 #include "common.h"
 
 namespace {
@@ -388,66 +390,184 @@ __global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris,
   out[1] = s0 * (eta0 * fH) - fnE;
 }
 
-// Far amplitudes (Eqs. 27-29): one block per (observation, rhs).
-__global__ void k_farfield(int ne, int nrhs, const zd *x, const double *obs, const int *edge_tris,
-                           const int *edge_reg, const double *tri, const int *te, const double *tsg, zd k0, zd eta0,
-                           double *out) {
-  int o = blockIdx.x, r = blockIdx.y;
-  double th = obs[2 * o], ph = obs[2 * o + 1];
-  double st, ct, sp, cp;
-  sincos(th, &st, &ct);
-  sincos(ph, &sp, &cp);
-  V3 rh = v3(st * cp, st * sp, ct), thh = v3(ct * cp, ct * sp, -st), phh = v3(-sp, cp, 0.0);
-  zd Nt, Np, Lt, Lp;
-  for (int p = threadIdx.x; p < ne; p += blockDim.x) {
-    int rp = edge_reg[2 * p], rm = edge_reg[2 * p + 1];
+// Far field (Eqs. 27-29), in two steps.  (1) Surface currents at the
+// quadrature points of every host-medium triangle, weights folded in:
+//   J_q = sum over the triangle's edges of s0 c_J W_q f_e(r_q),  M_q alike with c_M
+// (f_e the RWG function of Eq. 22, s0 = +-1 the side of the host medium).
+// (2) Radiation integrals N = sum_q exp(j k0 rhat.r_q) J_q, L alike with M_q,
+// per observation direction; the sum over points is split into NS parts
+// added in a fixed order by k_farfield_sum, which forms sigma.
+__global__ void k_quad_currents(int ntri0, int ne, int nrhs, const int *__restrict__ tri0, const zd *__restrict__ x,
+                                const int *__restrict__ edge_reg, const double *__restrict__ tri,
+                                const int *__restrict__ te, const double *__restrict__ tsg, double *qpos, zd *qcur) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // (triangle, point)
+  const int r = blockIdx.y;
+  const int npts = ntri0 * 7;
+  if (i >= npts) return;
+  const int t = tri0[i / 7], a = i % 7;
+  Tri T;
+  load_tri(tri, te, tsg, t, T);
+  const V3 rr = bary(T, c_rb[a][0], c_rb[a][1], c_rb[a][2]);
+  const double W = T.A * c_rw[a];
+  if (r == 0) {
+    qpos[4 * (size_t)i] = rr.x;
+    qpos[4 * (size_t)i + 1] = rr.y;
+    qpos[4 * (size_t)i + 2] = rr.z;
+    qpos[4 * (size_t)i + 3] = 0.0;
+  }
+  zd J[3], M[3];
+  for (int k = 0; k < 3; ++k) {
+    const int e = T.e[k];
+    if (e < 0) continue;
+    const int rp = edge_reg[2 * e], rm = edge_reg[2 * e + 1];
     if (rp != 0 && rm != 0) continue;
-    double s0 = rp == 0 ? 1.0 : -1.0;
-    zd cJ = x[((size_t)r * ne + p) * 2], cM = x[((size_t)r * ne + p) * 2 + 1];
-    zd Pt, Pp;
-    for (int s = 0; s < 2; ++s) {
-      int t = edge_tris[2 * p + s];
-      Tri T;
-      load_tri(tri, te, tsg, t, T);
-      int li = 0;
-      for (int a = 0; a < 3; ++a)
-        if (T.e[a] == p) li = a;
-      for (int a = 0; a < 7; ++a) {
-        V3 rr = bary(T, c_rb[a][0], c_rb[a][1], c_rb[a][2]);
-        double W = T.A * c_rw[a];
-        V3 f = T.c[li] * (rr - T.fr[li]);
-        double xx = dot(rh, rr);
+    const double w = (rp == 0 ? 1.0 : -1.0) * W;
+    const zd cJ = x[((size_t)r * ne + e) * 2], cM = x[((size_t)r * ne + e) * 2 + 1];
+    const V3 f = T.c[k] * (rr - T.fr[k]);
+    const double fw[3] = {w * f.x, w * f.y, w * f.z};
+    for (int d = 0; d < 3; ++d) {
+      J[d] += fw[d] * cJ;
+      M[d] += fw[d] * cM;
+    }
+  }
+  zd *o = qcur + ((size_t)r * npts + i) * 6;
+  for (int d = 0; d < 3; ++d) {
+    o[d] = J[d];
+    o[3 + d] = M[d];
+  }
+}
+
+constexpr int FF_TP = 64;  // points per shared-memory tile
+__global__ void __launch_bounds__(128) k_farfield_part(int npts, int nobs, const double *__restrict__ obs,
+                                                       const double *__restrict__ qpos, const zd *__restrict__ qcur,
+                                                       zd k0, zd *part) {
+  __shared__ double sp[FF_TP][4];
+  __shared__ zd sc[FF_TP][6];
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y, NS = gridDim.y, r = blockIdx.z;
+  V3 rh = v3(0.0, 0.0, 0.0);
+  if (o < nobs) {
+    double st, ct, sp_, cp;
+    sincos(obs[2 * o], &st, &ct);
+    sincos(obs[2 * o + 1], &sp_, &cp);
+    rh = v3(st * cp, st * sp_, ct);
+  }
+  const int p0 = (int)((int64_t)s * npts / NS), p1 = (int)((int64_t)(s + 1) * npts / NS);
+  const zd *qc = qcur + (size_t)r * npts * 6;
+  zd acc[6];
+  for (int base = p0; base < p1; base += FF_TP) {
+    const int cnt = min(FF_TP, p1 - base);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < cnt * 4; idx += blockDim.x) sp[idx / 4][idx % 4] = qpos[4 * (size_t)base + idx];
+    for (int idx = threadIdx.x; idx < cnt * 6; idx += blockDim.x) sc[idx / 6][idx % 6] = qc[6 * (size_t)base + idx];
+    __syncthreads();
+    if (o < nobs) {
+      for (int q = 0; q < cnt; ++q) {
+        const double xx = rh.x * sp[q][0] + rh.y * sp[q][1] + rh.z * sp[q][2];
         double s1, c1;
         sincos(k0.re * xx, &s1, &c1);
-        double g = exp(-k0.im * xx);
-        zd e(g * c1, g * s1);  // exp(+j k0 rhat.r)
-        Pt += (W * dot(f, thh) * s0) * e;
-        Pp += (W * dot(f, phh) * s0) * e;
+        zd e(c1, s1);  // exp(+j k0 rhat.r)
+        if (k0.im != 0.0) e = exp(-k0.im * xx) * e;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) acc[m] += e * sc[q][m];
       }
     }
-    Nt += Pt * cJ;
-    Np += Pp * cJ;
-    Lt += Pt * cM;
-    Lp += Pp * cM;
   }
-  __shared__ zd red[4][256];
-  red[0][threadIdx.x] = Nt;
-  red[1][threadIdx.x] = Np;
-  red[2][threadIdx.x] = Lt;
-  red[3][threadIdx.x] = Lp;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
+  if (o < nobs) {
+    zd *d = part + (((size_t)r * NS + s) * nobs + o) * 6;
+    for (int m = 0; m < 6; ++m) d[m] = acc[m];
+  }
+}
+
+// Mixed form (FP32 far field, the chosen precision of the excitation/RCS
+// step): positions relative to the tree centre r0 and currents in FP32, the
+// phase exp(j k0 rhat.(r - r0)) in FP32 with FP32 accumulation inside a
+// split; the splits are added in FP64 and k_farfield_sum restores the common
+// factor exp(j k0 rhat.r0).
+__global__ void __launch_bounds__(128) k_farfield_part32(int npts, int nobs, const double *__restrict__ obs,
+                                                         const double *__restrict__ qpos, const zd *__restrict__ qcur,
+                                                         double r0x, double r0y, double r0z, zd k0, zd *part) {
+  __shared__ float4 sp[FF_TP];
+  __shared__ zf sc[FF_TP][6];
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y, NS = gridDim.y, r = blockIdx.z;
+  float rx = 0.f, ry = 0.f, rz = 0.f;
+  if (o < nobs) {
+    double st, ct, sp_, cp;
+    sincos(obs[2 * o], &st, &ct);
+    sincos(obs[2 * o + 1], &sp_, &cp);
+    rx = (float)(st * cp);
+    ry = (float)(st * sp_);
+    rz = (float)ct;
+  }
+  const float kr = (float)k0.re, ki = (float)k0.im;
+  const int p0 = (int)((int64_t)s * npts / NS), p1 = (int)((int64_t)(s + 1) * npts / NS);
+  const zd *qc = qcur + (size_t)r * npts * 6;
+  zf acc[6];
+  for (int base = p0; base < p1; base += FF_TP) {
+    const int cnt = min(FF_TP, p1 - base);
     __syncthreads();
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      const double *pp = qpos + 4 * (size_t)(base + q);
+      sp[q] = make_float4((float)(pp[0] - r0x), (float)(pp[1] - r0y), (float)(pp[2] - r0z), 0.f);
+    }
+    for (int idx = threadIdx.x; idx < cnt * 6; idx += blockDim.x) {
+      const zd v = qc[6 * (size_t)base + idx];
+      sc[idx / 6][idx % 6] = zf((float)v.re, (float)v.im);
+    }
+    __syncthreads();
+    if (o < nobs) {
+      for (int q = 0; q < cnt; ++q) {
+        const float4 pq = sp[q];
+        const float xx = rx * pq.x + ry * pq.y + rz * pq.z;
+        float s1, c1;
+        sincosf(kr * xx, &s1, &c1);
+        zf e(c1, s1);
+        if (ki != 0.f) e = expf(-ki * xx) * e;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) acc[m] += e * sc[q][m];
+      }
+    }
   }
-  if (threadIdx.x == 0) {
-    zd pre = zd(0.0, -1.0) * k0 * (1.0 / sqrt(4.0 * M_PI));
-    zd At = pre * (eta0 * red[0][0] + red[3][0]);
-    zd Ap = pre * (eta0 * red[1][0] - red[2][0]);
-    out[((size_t)r * gridDim.x + o) * 2] = At.re * At.re + At.im * At.im;
-    out[((size_t)r * gridDim.x + o) * 2 + 1] = Ap.re * Ap.re + Ap.im * Ap.im;
+  if (o < nobs) {
+    zd *d = part + (((size_t)r * NS + s) * nobs + o) * 6;
+    for (int m = 0; m < 6; ++m) d[m] = zd(acc[m].re, acc[m].im);
   }
+}
+
+__global__ void k_farfield_sum(int nobs, int NS, const double *__restrict__ obs, const zd *__restrict__ part, zd k0,
+                               zd eta0, double r0x, double r0y, double r0z, double *out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (o >= nobs) return;
+  zd v[6];
+  for (int s = 0; s < NS; ++s) {
+    const zd *d = part + (((size_t)r * NS + s) * nobs + o) * 6;
+    for (int m = 0; m < 6; ++m) v[m] += d[m];
+  }
+  double st, ct, sp, cp;
+  sincos(obs[2 * o], &st, &ct);
+  sincos(obs[2 * o + 1], &sp, &cp);
+  if (r0x != 0.0 || r0y != 0.0 || r0z != 0.0) {
+    // partial sums taken relative to r0: restore exp(j k0 rhat.r0)
+    const double xx = st * cp * r0x + st * sp * r0y + ct * r0z;
+    double s1, c1;
+    sincos(k0.re * xx, &s1, &c1);
+    const zd e = exp(-k0.im * xx) * zd(c1, s1);
+    for (int m = 0; m < 6; ++m) v[m] = e * v[m];
+  }
+  const double th[3] = {ct * cp, ct * sp, -st}, ph[3] = {-sp, cp, 0.0};
+  zd Nt, Np, Lt, Lp;
+  for (int d = 0; d < 3; ++d) {
+    Nt += th[d] * v[d];
+    Np += ph[d] * v[d];
+    Lt += th[d] * v[3 + d];
+    Lp += ph[d] * v[3 + d];
+  }
+  const zd pre = zd(0.0, -1.0) * k0 * (1.0 / sqrt(4.0 * M_PI));
+  const zd At = pre * (eta0 * Nt + Lp);
+  const zd Ap = pre * (eta0 * Np - Lt);
+  out[((size_t)r * nobs + o) * 2] = At.re * At.re + At.im * At.im;
+  out[((size_t)r * nobs + o) * 2 + 1] = Ap.re * Ap.re + Ap.im * Ap.im;
 }
 
 __global__ void k_to_f32(const double *a, float *b, int64_t n) {
@@ -526,13 +646,44 @@ void launch_rhs(sie_ctx *c, const double *inc_dev, int nrhs, zd *b) {
   c->launches++;
 }
 
-void launch_farfield(sie_ctx *c, const zd *x, int nrhs, const double *obs, int nobs, double *out) {
+void launch_farfield(sie_ctx *c, const zd *x, int nrhs, const double *obs, int nobs, double *out, sie_prec prec) {
   upload_radon();
-  dim3 grid(nobs, nrhs);
-  k_farfield<<<grid, 256, 0, c->stream>>>(c->ne, nrhs, x, obs, c->d_edge_tris, c->d_edge_reg, c->d_tri, c->d_tri_e,
-                                          c->d_tri_sg, to_zd(c->kreg[0]), to_zd(c->etareg[0]), out);
+  const int npts = c->ntri0 * 7;
+  const int ob = (nobs + 127) / 128;
+  // split the point sum so that the grid fills the GPU, partials kept small
+  int NS = std::min(256, (152 * 4 + ob * nrhs - 1) / (ob * nrhs));
+  NS = std::max(1, std::min(NS, npts / 256));
+  const size_t qpos_b = ((size_t)npts * 4 * sizeof(double) + 255) / 256 * 256;
+  const size_t qcur_b = ((size_t)nrhs * npts * 6 * sizeof(zd) + 255) / 256 * 256;
+  const size_t part_b = (size_t)nrhs * NS * nobs * 6 * sizeof(zd);
+  const size_t need = qpos_b + qcur_b + part_b;
+  if (need > c->ff_bytes) {
+    c->d_ff = dev_alloc(c, need);
+    c->ff_bytes = need;
+  }
+  double *qpos = (double *)c->d_ff;
+  zd *qcur = (zd *)((char *)c->d_ff + qpos_b);
+  zd *part = (zd *)((char *)c->d_ff + qpos_b + qcur_b);
+  const zd k0 = to_zd(c->kreg[0]), eta0 = to_zd(c->etareg[0]);
+  if (npts > 0) {
+    k_quad_currents<<<dim3((npts + 127) / 128, nrhs), 128, 0, c->stream>>>(
+        c->ntri0, c->ne, nrhs, c->d_tri0, x, c->d_edge_reg, c->d_tri, c->d_tri_e, c->d_tri_sg, qpos, qcur);
+    SIE_CHECK_LAUNCH();
+    c->launches++;
+  }
+  double r0[3] = {0.0, 0.0, 0.0};
+  if (prec == SIE_PREC_FP64) {
+    k_farfield_part<<<dim3(ob, NS, nrhs), 128, 0, c->stream>>>(npts, nobs, obs, qpos, qcur, k0, part);
+  } else {
+    const double root = c->hleaf * (double)(1 << std::max(0, c->levels - 1));
+    for (int d = 0; d < 3; ++d) r0[d] = c->origin[d] + 0.5 * root;
+    k_farfield_part32<<<dim3(ob, NS, nrhs), 128, 0, c->stream>>>(npts, nobs, obs, qpos, qcur, r0[0], r0[1], r0[2],
+                                                                 k0, part);
+  }
   SIE_CHECK_LAUNCH();
-  c->launches++;
+  k_farfield_sum<<<dim3(ob, nrhs), 128, 0, c->stream>>>(nobs, NS, obs, part, k0, eta0, r0[0], r0[1], r0[2], out);
+  SIE_CHECK_LAUNCH();
+  c->launches += 2;
 }
 
 void launch_to_f32(sie_ctx *c, const double *src, float *dst, int64_t n) {

@@ -935,6 +935,13 @@ static void fill_all(sie_ctx *c, const sie_fill_opts *o) {
   c->d_tri_e = dev_upload(c, tri_e);
   c->d_tri_sg = dev_upload(c, tri_sg);
   c->d_tri_reg = dev_upload(c, c->tri_reg);
+  {
+    std::vector<int> t0;
+    for (int t = 0; t < nt; ++t)
+      if (c->tri_reg[2 * t] == 0 || c->tri_reg[2 * t + 1] == 0) t0.push_back(t);
+    c->ntri0 = (int)t0.size();
+    if (!t0.empty()) c->d_tri0 = dev_upload(c, t0);
+  }
   c->d_row_ptr = dev_upload(c, c->row_ptr);
   c->d_col = dev_upload(c, c->col);
   c->d_perm = dev_upload(c, c->perm);
@@ -1107,22 +1114,28 @@ extern "C" sie_status gmres_solve(sie_ctx *c, const void *b, void *x, int64_t nr
   return g != SIE_OK ? g : rc;
 }
 
-extern "C" sie_status rcs_farfield(sie_ctx *c, const void *x, int64_t nrhs, const double *obs, int64_t nobs,
-                                   double *rcs) {
+extern "C" sie_status rcs_farfield_prec(sie_ctx *c, const void *x, int64_t nrhs, const double *obs, int64_t nobs,
+                                        int32_t prec, double *rcs) {
   return guard(c, [&] {
     SIE_REQUIRE(c->have_fill, SIE_ESTATE, "rcs_farfield: call sie_fill_nearfield first");
     SIE_REQUIRE(x && obs && rcs && nrhs >= 1 && nobs >= 1 && nrhs <= 4096 && nobs <= 1000000, SIE_EINVAL,
                 "rcs_farfield: bad arguments");
+    SIE_REQUIRE(prec == SIE_PREC_FP64 || prec == SIE_PREC_MIXED, SIE_EINVAL, "rcs_farfield: prec must be 0 or 1");
     ensure_work(c, nrhs);
     op_permute_in(c, (const zd *)x, (zd *)c->d_xi, (int)nrhs);
     size_t ob = ((size_t)nobs * 2 * sizeof(double) + 255) / 256 * 256;
     double *d_obs = (double *)stage(c, ob + (size_t)nrhs * nobs * 2 * sizeof(double));
     double *d_out = (double *)((char *)d_obs + ob);
     SIE_CUDA(cudaMemcpyAsync(d_obs, obs, (size_t)nobs * 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    launch_farfield(c, (const zd *)c->d_xi, (int)nrhs, d_obs, (int)nobs, d_out);
+    launch_farfield(c, (const zd *)c->d_xi, (int)nrhs, d_obs, (int)nobs, d_out, (sie_prec)prec);
     SIE_CUDA(cudaMemcpyAsync(rcs, d_out, (size_t)nrhs * nobs * 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SIE_CUDA(cudaStreamSynchronize(c->stream));
   });
+}
+
+extern "C" sie_status rcs_farfield(sie_ctx *c, const void *x, int64_t nrhs, const double *obs, int64_t nobs,
+                                   double *rcs) {
+  return rcs_farfield_prec(c, x, nrhs, obs, nobs, SIE_PREC_FP64, rcs);
 }
 
 extern "C" sie_status sie_near_export(sie_ctx *c, int32_t *rows, int32_t *cols, double *vals, int64_t *nnzb) {

@@ -162,6 +162,9 @@ def test_rhs_and_rcs(sphere, coated):
         got = sie.rcs_farfield(c.s.ctx, _dev(x, c.ne), 2, obs)
         ref = farfield.rcs(c.m, x, obs)
         assert np.max(np.abs(got - ref)) < 1e-9 * np.max(ref)
+        # mixed form: FP32 phases and currents; the RCS bar of the method is 0.2 dB
+        got32 = sie.rcs_farfield_prec(c.s.ctx, _dev(x, c.ne), 2, obs, sie.SIE_PREC_MIXED)
+        assert np.max(np.abs(got32 - ref)) < 1e-5 * np.max(ref)
 
 
 def test_ilu_reduces_iterations(coated):
