@@ -95,11 +95,12 @@ struct RegionHost {
   std::vector<int> basis_p;     // internal edge index
   std::vector<int> basis_sign;  // s_l
   std::vector<int> box_start;   // leaf boxes: [nleaf+1] ranges into the basis list
+  int max_leaf = 0;             // most bases in one leaf box
   std::vector<LevelHost> lev;   // index = level number; levels 2..leaf carry tables
   int *d_basis_p = nullptr, *d_basis_sign = nullptr, *d_box_start = nullptr, *d_basis_box = nullptr;
   double *d_box_centre = nullptr;  // leaf box centres [nleaf][3]
   void *d_V64 = nullptr, *d_V32 = nullptr;    // radiation patterns [nb][2][Kleaf]
-  void *d_RN64 = nullptr, *d_RN32 = nullptr;  // receive patterns of t x n [nb][2][Kleaf]
+  void *d_P64 = nullptr, *d_P32 = nullptr;  // combined receive patterns [nb][2][Kleaf] (k_receive_fold)
   int *d_pairs = nullptr;       // near triangle pairs (p, q, singular) for the fill
   int64_t npairs = 0;
 };
@@ -165,6 +166,7 @@ struct sie_ctx {
   int *d_tri0 = nullptr;         // triangles bounding the host medium (region 0)
   int ntri0 = 0;
   void *d_ff = nullptr;          // far-field work: point positions, point currents, partial sums
+  int *d_err = nullptr;          // device error flag: 1 = a bounded wait in a kernel gave up
   size_t ff_bytes = 0;
   int *d_row_ptr = nullptr, *d_col = nullptr;
   void *d_near64 = nullptr, *d_near32 = nullptr;  // [nnzb][4] blocks
@@ -201,6 +203,7 @@ T *dev_upload(sie_ctx *c, const std::vector<T> &v) {
 }
 void ensure_work(sie_ctx *c, int64_t nrhs);
 void *stage(sie_ctx *c, size_t bytes);
+void check_device_errors(sie_ctx *c);  // after a stream synchronisation: SIE_ETIMEOUT if a kernel gave up
 
 // ------------------------------------------------------------------ launchers (fill.cu)
 void launch_near_fill(sie_ctx *c, int region);

@@ -344,6 +344,26 @@ __global__ void k_patterns(int nb, int K, const int *basis_p, const int *basis_b
   RN[((size_t)i * 2 + 1) * K + kk] = rp;
 }
 
+// Combined receive pattern of basis i in medium l, so that the leaf receive
+// reads one pattern per basis instead of two:
+//   P_t(k) = s_i V_t(-k) + RN_p(k),   P_p(k) = -s_i V_p(-k) - RN_t(k),
+// V(-k) taken at the antipodal sample (theta row L - it, phi column + pi),
+// where the theta unit vector is the same and the phi unit vector reversed.
+// Written over RN in place (each thread reads only its own RN entries).
+__global__ void k_receive_fold(int nb, int K, int L, const int *sign, const zd *V, zd *RN) {
+  const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (kk >= K || i >= nb) return;
+  const int nph = 2 * L + 2, it = kk / nph, jp = kk - it * nph;
+  const int ka = (L - it) * nph + (jp + L + 1) % nph;
+  const double s = (double)sign[i];
+  const zd *Vi = V + (size_t)i * 2 * K;
+  zd *Ri = RN + (size_t)i * 2 * K;
+  const zd rt = Ri[kk], rp = Ri[K + kk];
+  Ri[kk] = s * Vi[ka] + rp;
+  Ri[K + kk] = (-s) * Vi[K + ka] - rt;
+}
+
 // Tested excitation, host medium 0 only (Eqs. 20-21 with Eq. 30).
 __global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris, const int *edge_reg,
                       const double *tri, const int *te, const double *tsg, zd k0, zd eta0, zd *b) {
@@ -619,9 +639,9 @@ void launch_patterns(sie_ctx *c, int l) {
   int K = LL.K;
   size_t n = (size_t)R.nb * 2 * K;
   R.d_V64 = dev_alloc(c, n * sizeof(zd));
-  R.d_RN64 = dev_alloc(c, n * sizeof(zd));
+  R.d_P64 = dev_alloc(c, n * sizeof(zd));
   R.d_V32 = dev_alloc(c, n * sizeof(zf));
-  R.d_RN32 = dev_alloc(c, n * sizeof(zf));
+  R.d_P32 = dev_alloc(c, n * sizeof(zf));
   SIE_REQUIRE(R.nb < 65536 * 8, SIE_EINVAL, "patterns: too many bases in one medium");
   for (int i0 = 0; i0 < R.nb; i0 += 65535) {
     int cnt = std::min(65535, R.nb - i0);
@@ -629,12 +649,20 @@ void launch_patterns(sie_ctx *c, int l) {
     k_patterns<<<grid, 128, 0, c->stream>>>(cnt, K, R.d_basis_p + i0, R.d_basis_box + i0, R.d_box_centre,
                                             c->d_edge_tris, c->d_tri, c->d_tri_e, c->d_tri_sg, LL.d_dirs,
                                             to_zd(R.k), (zd *)R.d_V64 + (size_t)i0 * 2 * K,
-                                            (zd *)R.d_RN64 + (size_t)i0 * 2 * K);
+                                            (zd *)R.d_P64 + (size_t)i0 * 2 * K);
+    SIE_CHECK_LAUNCH();
+    c->launches++;
+  }
+  for (int i0 = 0; i0 < R.nb; i0 += 65535) {
+    int cnt = std::min(65535, R.nb - i0);
+    dim3 grid((K + 127) / 128, cnt);
+    k_receive_fold<<<grid, 128, 0, c->stream>>>(cnt, K, LL.L, R.d_basis_sign + i0, (const zd *)R.d_V64 + (size_t)i0 * 2 * K,
+                                                (zd *)R.d_P64 + (size_t)i0 * 2 * K);
     SIE_CHECK_LAUNCH();
     c->launches++;
   }
   launch_to_f32(c, (const double *)R.d_V64, (float *)R.d_V32, (int64_t)n * 2);
-  launch_to_f32(c, (const double *)R.d_RN64, (float *)R.d_RN32, (int64_t)n * 2);
+  launch_to_f32(c, (const double *)R.d_P64, (float *)R.d_P32, (int64_t)n * 2);
 }
 
 void launch_rhs(sie_ctx *c, const double *inc_dev, int nrhs, zd *b) {

@@ -25,6 +25,16 @@ void *dev_alloc(sie_ctx *c, size_t bytes) {
   return p;
 }
 
+void check_device_errors(sie_ctx *c) {
+  if (!c->d_err) return;
+  int e = 0;
+  SIE_CUDA(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    SIE_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+    SIE_REQUIRE(false, SIE_ETIMEOUT, "a bounded wait for a bulk copy in a kernel gave up");
+  }
+}
+
 void *stage(sie_ctx *c, size_t bytes) {
   if (bytes > c->stage_bytes) {
     c->d_stage = dev_alloc(c, std::max(bytes, (size_t)4096));
@@ -680,6 +690,9 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
     R.d_basis_p = dev_upload(c, R.basis_p);
     R.d_basis_sign = dev_upload(c, R.basis_sign);
     R.d_box_start = dev_upload(c, R.box_start);
+    R.max_leaf = 0;
+    for (size_t b = 0; b + 1 < R.box_start.size(); ++b)
+      R.max_leaf = std::max(R.max_leaf, R.box_start[b + 1] - R.box_start[b]);
     R.d_basis_box = dev_upload(c, basis_box);
     std::vector<double> cen(3 * LL.nbox);
     for (int b = 0; b < LL.nbox; ++b)
@@ -912,6 +925,10 @@ static void build_ilu(sie_ctx *c) {
 // ------------------------------------------------------------------ API: fill
 static void fill_all(sie_ctx *c, const sie_fill_opts *o) {
   const int ne = c->ne, nt = c->nt;
+  if (!c->d_err) {
+    c->d_err = (int *)dev_alloc(c, sizeof(int));
+    SIE_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+  }
   int on = o ? o->outer_order : 4;
   SIE_REQUIRE(on >= 2 && on <= 12, SIE_EINVAL, "sie_fill_nearfield: outer_order must be in [2, 12]");
   // geometry tables, internal edge ids
@@ -1204,6 +1221,7 @@ extern "C" sie_status sie_stage_timing(sie_ctx *c, int32_t stage, int64_t nrhs, 
     SIE_CUDA(cudaEventElapsedTime(&t, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    check_device_errors(c);
     *ms = (double)t / reps;
   });
 }

@@ -13,7 +13,7 @@ template <typename T> struct tsel;
 template <> struct tsel<double> {
   static void *near(sie_ctx *c) { return c->d_near64; }
   static void *V(RegionHost &R) { return R.d_V64; }
-  static void *RN(RegionHost &R) { return R.d_RN64; }
+  static void *P(RegionHost &R) { return R.d_P64; }
   static void *Tr(LevelHost &L) { return L.d_T64; }
   static void *tp(LevelHost &L) { return L.d_tp64; }
   static void *Phi(LevelHost &L) { return L.d_Phi64; }
@@ -29,7 +29,7 @@ template <> struct tsel<double> {
 template <> struct tsel<float> {
   static void *near(sie_ctx *c) { return c->d_near32; }
   static void *V(RegionHost &R) { return R.d_V32; }
-  static void *RN(RegionHost &R) { return R.d_RN32; }
+  static void *P(RegionHost &R) { return R.d_P32; }
   static void *Tr(LevelHost &L) { return L.d_T32; }
   static void *tp(LevelHost &L) { return L.d_tp32; }
   static void *Phi(LevelHost &L) { return L.d_Phi32; }
@@ -183,116 +183,254 @@ __global__ void k_near_spmv_blk(int ne, int nrhs, const int *__restrict__ row_pt
   }
 }
 
+// ---------------------------------------------------------------- bulk copies
+// Bulk global -> shared copies (cp.async.bulk, the non-tensor TMA form) that
+// complete on a shared-memory mbarrier.  Every wait is bounded: a wait that
+// gives up records SIE_ETIMEOUT-style code 1 in *err and returns false.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err) {
+  const unsigned a = smem_u32(bar);
+  for (int it = 0; it < (1 << 20); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
 // ---------------------------------------------------------------- MLFMM
 // Leaf aggregation: S_b(k) = sum_{i in b} s_i [eta0 c, v]_p(i) (x) V_i(k).
 // Every level's S and I are laid out [box][J/M][theta/phi][r][k]: for one
 // right-hand side the K samples of a component are contiguous, so a warp over
 // k reads and writes whole lines for any number of right-hand sides.
-template <typename T>
-__global__ void k_aggregate(int nbox, int K, int ne, int nrhs, const int *__restrict__ box_start,
-                            const int *__restrict__ basis_p, const int *__restrict__ sign,
-                            const cx<T> *__restrict__ V, const cx<T> *__restrict__ x, cx<T> *__restrict__ S) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  int b = blockIdx.y;
-  if (k >= K) return;
-  int i0 = box_start[b], i1 = box_start[b + 1];
-  constexpr int RB = 4;  // right-hand sides per pass: each pattern value is read once per pass
+// One CTA per leaf box, threads over the directions k (up to AGG_KS per
+// thread).  The box's patterns, one contiguous block, stream through shared
+// memory in chunks of cb bases by bulk copies into a two-stage ring, so the
+// whole chunk is in flight at once; the box's signed coefficients are staged
+// in shared memory and each pattern value serves RB right-hand sides.
+constexpr int AGG_KS = 2, STAGES = 2;
+template <typename T, int RB>
+__global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int cb, const int *__restrict__ box_start,
+                                                  const int *__restrict__ basis_p, const int *__restrict__ sign,
+                                                  const cx<T> *__restrict__ V, const cx<T> *__restrict__ x,
+                                                  cx<T> *__restrict__ S, int *err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ unsigned long long bar[STAGES];
+  const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
+  const size_t per = (size_t)2 * K;  // complex values per basis
+  cx<T> *ring = reinterpret_cast<cx<T> *>(smem_raw);       // [STAGES][cb][2][K]
+  cx<T> *xs = ring + (size_t)STAGES * cb * per;            // [n][RB][2]
+  const size_t cs = (size_t)nrhs * K;  // component stride
+  const int nch = (n + cb - 1) / cb;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < STAGES; ++q) mbar_init(&bar[q], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  int issued = 0, used = 0;  // chunks issued / consumed over all passes (ring position and parity)
+  auto issue = [&](int ch) {
+    const int li0 = ch * cb, m = min(cb, n - li0);
+    const int st = issued % STAGES;
+    bulk_load(ring + (size_t)st * cb * per, V + (size_t)(i0 + li0) * per, (unsigned)(m * per * sizeof(cx<T>)),
+              &bar[st]);
+    ++issued;
+  };
+  bool ok = true;
   for (int r0 = 0; r0 < nrhs; r0 += RB) {
     const int nr = min(RB, nrhs - r0);
-    cx<T> a0[RB], a1[RB], a2[RB], a3[RB];
-    for (int i = i0; i < i1; ++i) {
-      int p = basis_p[i];
-      T s = (T)sign[i];
-      cx<T> vt = V[((size_t)i * 2) * K + k], vp = V[((size_t)i * 2 + 1) * K + k];
+    if (threadIdx.x == 0)
+      for (int ch = 0; ch < min(STAGES, nch); ++ch) issue(ch);
+    for (int idx = threadIdx.x; idx < n * RB; idx += blockDim.x) {
+      const int li = idx / RB, rr = idx - li * RB;
+      cx<T> xj, xm;
+      if (rr < nr) {
+        const int p = basis_p[i0 + li];
+        const T sg = (T)sign[i0 + li];
+        const cx<T> *xr = x + (size_t)(r0 + rr) * ne * 2;
+        xj = sg * xr[2 * p];
+        xm = sg * xr[2 * p + 1];
+      }
+      xs[2 * idx] = xj;
+      xs[2 * idx + 1] = xm;
+    }
+    __syncthreads();
+    cx<T> a0[AGG_KS][RB], a1[AGG_KS][RB], a2[AGG_KS][RB], a3[AGG_KS][RB];
+    for (int ch = 0; ch < nch; ++ch) {
+      const int st = used % STAGES;
+      ok = mbar_wait(&bar[st], (unsigned)((used / STAGES) & 1), err) && ok;
+      ++used;
+      const int li0 = ch * cb, m = min(cb, n - li0);
+      const cx<T> *v = ring + (size_t)st * cb * per;
+#pragma unroll
+      for (int s = 0; s < AGG_KS; ++s) {
+        const int k = threadIdx.x + s * blockDim.x;
+        if (k >= K) break;
+        for (int li = 0; li < m; ++li) {
+          const cx<T> vt = v[(size_t)li * per + k], vp = v[(size_t)li * per + K + k];
+#pragma unroll
+          for (int rr = 0; rr < RB; ++rr)
+            if (rr < nr) {
+              const cx<T> xj = xs[2 * ((li0 + li) * RB + rr)], xm = xs[2 * ((li0 + li) * RB + rr) + 1];
+              a0[s][rr] = cfma(xj, vt, a0[s][rr]);
+              a1[s][rr] = cfma(xj, vp, a1[s][rr]);
+              a2[s][rr] = cfma(xm, vt, a2[s][rr]);
+              a3[s][rr] = cfma(xm, vp, a3[s][rr]);
+            }
+        }
+      }
+      __syncthreads();  // the stage is free again
+      if (threadIdx.x == 0 && ch + STAGES < nch) issue(ch + STAGES);
+    }
+#pragma unroll
+    for (int s = 0; s < AGG_KS; ++s) {
+      const int k = threadIdx.x + s * blockDim.x;
+      if (k >= K) break;
 #pragma unroll
       for (int rr = 0; rr < RB; ++rr)
         if (rr < nr) {
-          const cx<T> *xr = x + (size_t)(r0 + rr) * ne * 2;
-          cx<T> xj = s * xr[2 * p], xm = s * xr[2 * p + 1];
-          a0[rr] = cfma(xj, vt, a0[rr]);
-          a1[rr] = cfma(xj, vp, a1[rr]);
-          a2[rr] = cfma(xm, vt, a2[rr]);
-          a3[rr] = cfma(xm, vp, a3[rr]);
+          cx<T> *o = S + ((size_t)b * 4 * nrhs + r0 + rr) * K + k;
+          o[0] = a0[s][rr];
+          o[cs] = a1[s][rr];
+          o[2 * cs] = a2[s][rr];
+          o[3 * cs] = a3[s][rr];
         }
     }
-#pragma unroll
-    for (int rr = 0; rr < RB; ++rr)
-      if (rr < nr) {
-        const size_t cs = (size_t)nrhs * K;  // component stride
-        cx<T> *o = S + ((size_t)b * 4 * nrhs + r0 + rr) * K + k;
-        o[0] = a0[rr];
-        o[cs] = a1[rr];
-        o[2 * cs] = a2[rr];
-        o[3 * cs] = a3[rr];
-      }
+    __syncthreads();
+  }
+  if (!ok) {
+    // a wait gave up: wait once more, bounded, for every stage's last copy before leaving
+    for (int u = max(0, used - STAGES); u < used; ++u) mbar_wait(&bar[u % STAGES], (unsigned)((u / STAGES) & 1), err);
   }
 }
 
 // Exact separable interpolation of one child's pattern to the parent
 // sampling, shifted to the parent centre (upward pass).  One CTA per (child,
-// source J|M); the source is carried as three Cartesian components:
-// (theta, phi) -> xyz at the child directions, trigonometric interpolation in
-// phi, the folded Lagrange step in theta, xyz -> (theta, phi) at the parent
-// directions, times the shift exp(j k khat.(c_child - c_parent)).  One CTA
-// per (child, J|M, right-hand side); output Y[child][J|M][theta|phi][r][k_parent];
-// k_up_sum adds the children.
-template <typename T>
-__global__ void k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, const int *__restrict__ oct,
-                            const T *__restrict__ tpc, const T *__restrict__ tpp, const T *__restrict__ Phi,
-                            const T *__restrict__ Thp, const T *__restrict__ Thm, const cx<T> *__restrict__ up,
-                            const cx<T> *__restrict__ Sc, cx<T> *__restrict__ Y) {
-  extern __shared__ unsigned char smem_raw[];
-  const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1;
-  cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [3][Kc]
-  cx<T> *G = A + 3 * Kc;                            // [3][nthc][Np]
-  T *Ps = reinterpret_cast<T *>(G + 3 * nthc * Np);  // Phi [Np][Nc], then Theta+ and Theta- [nthp][nthc]
-  T *Tps = Ps + Np * Nc, *Tms = Tps + (Lp + 1) * nthc;
-  for (int t = threadIdx.x; t < Np * Nc; t += blockDim.x) Ps[t] = Phi[t];
-  for (int t = threadIdx.x; t < (Lp + 1) * nthc; t += blockDim.x) {
-    Tps[t] = Thp[t];
-    Tms[t] = Thm[t];
+// right-hand side), JM of the sources J, M per pass.  The pattern is carried
+// as three Cartesian components: (theta, phi) -> xyz at the child directions
+// (A), trigonometric interpolation in phi (G = A Phi^T), the folded Lagrange
+// step in theta (H = Th+ G + Th- G(phi + pi)), xyz -> (theta, phi) at the
+// parent directions, times the shift exp(j k khat.(c_child - c_parent)).
+// Output Y[child][J|M][theta|phi][r][k_parent]; k_up_sum adds the children.
+// Register tiles: a G task owns the columns jp and jp + Np/2 of one theta row;
+// an H task owns the pair (jp, jp + Np/2), whose phi + pi partners are each
+// other, for two parent theta rows, so every shared-memory load feeds several FMAs.
+template <typename T, int JM>
+__global__ void __launch_bounds__(256) k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs,
+                                                  const int *__restrict__ oct, const T *__restrict__ tpc,
+                                                  const T *__restrict__ tpp, const T *__restrict__ Phi,
+                                                  const T *__restrict__ Thp, const T *__restrict__ Thm,
+                                                  const cx<T> *__restrict__ up, const cx<T> *__restrict__ Sc,
+                                                  cx<T> *__restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int Q = 3 * JM, IP = 2;
+  const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1, nthp = Lp + 1, hp = Lp + 1;
+  cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [Q][Kc]
+  cx<T> *G = A + (size_t)Q * Kc;                    // [Q][nthc][Np]
+  T *PhT = reinterpret_cast<T *>(G + (size_t)Q * nthc * Np);  // [Nc][Np]
+  T *Tps = PhT + Nc * Np, *Tms = Tps + nthp * nthc;           // [nthp][nthc]
+  const int c = blockIdx.x, r = blockIdx.y, o = oct[c], tid = threadIdx.x, NT = blockDim.x;
+  for (int i = tid; i < Np * Nc; i += NT) {
+    const int jp = i / Nc, jc = i - jp * Nc;
+    PhT[jc * Np + jp] = Phi[i];
   }
-  __syncthreads();
-  const int c = blockIdx.x, jm = blockIdx.y, r = blockIdx.z, o = oct[c];
-  const int nG = 3 * nthc * Np;
-  {
-    for (int t = threadIdx.x; t < Kc; t += blockDim.x) {
-      cx<T> ft = Sc[(((size_t)c * 4 + jm * 2) * nrhs + r) * Kc + t];
-      cx<T> fp = Sc[(((size_t)c * 4 + jm * 2 + 1) * nrhs + r) * Kc + t];
+  for (int i = tid; i < nthp * nthc; i += NT) {
+    Tps[i] = Thp[i];
+    Tms[i] = Thm[i];
+  }
+  const int nib = (nthp + IP - 1) / IP;
+  for (int jm0 = 0; jm0 < 2; jm0 += JM) {
+    __syncthreads();
+    for (int i = tid; i < JM * Kc; i += NT) {
+      const int m = i / Kc, t = i - m * Kc;
+      const cx<T> *st = Sc + (((size_t)c * 4 + (jm0 + m) * 2) * nrhs + r) * Kc;
+      const cx<T> ft = st[t], fp = st[(size_t)nrhs * Kc + t];
       const T *u = tpc + 6 * (size_t)t;
-      for (int x = 0; x < 3; ++x) A[x * Kc + t] = ft * u[x] + fp * u[3 + x];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) A[(size_t)(m * 3 + x) * Kc + t] = ft * u[x] + fp * u[3 + x];
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nG; idx += blockDim.x) {
-      int x = idx / (nthc * Np), rem = idx - x * nthc * Np, ic = rem / Np, jp = rem - ic * Np;
-      const cx<T> *row = A + x * Kc + ic * Nc;
-      const T *ph = Ps + jp * Nc;
-      cx<T> acc;
+    for (int task = tid; task < nthc * hp; task += NT) {
+      const int ic = task / hp, jp = task - ic * hp;
+      cx<T> g0[Q], g1[Q];
       for (int jc = 0; jc < Nc; ++jc) {
-        acc.re = fma(ph[jc], row[jc].re, acc.re);
-        acc.im = fma(ph[jc], row[jc].im, acc.im);
+        const T f0 = PhT[jc * Np + jp], f1 = PhT[jc * Np + jp + hp];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const cx<T> a = A[(size_t)q * Kc + ic * Nc + jc];
+          g0[q].re = fma(f0, a.re, g0[q].re);
+          g0[q].im = fma(f0, a.im, g0[q].im);
+          g1[q].re = fma(f1, a.re, g1[q].re);
+          g1[q].im = fma(f1, a.im, g1[q].im);
+        }
       }
-      G[idx] = acc;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        G[((size_t)q * nthc + ic) * Np + jp] = g0[q];
+        G[((size_t)q * nthc + ic) * Np + jp + hp] = g1[q];
+      }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < Kp; t += blockDim.x) {
-      int ip = t / Np, jp = t - ip * Np, jq = (jp + Lp + 1) % Np;
-      cx<T> H[3];
-      for (int x = 0; x < 3; ++x) {
-        const cx<T> *g = G + (size_t)x * nthc * Np;
-        cx<T> acc;
-        for (int ic = 0; ic < nthc; ++ic) {
-          T a = Tps[ip * nthc + ic], bq = Tms[ip * nthc + ic];
-          cx<T> g1 = g[ic * Np + jp], g2 = g[ic * Np + jq];
-          acc.re = fma(a, g1.re, fma(bq, g2.re, acc.re));
-          acc.im = fma(a, g1.im, fma(bq, g2.im, acc.im));
+    for (int task = tid; task < nib * hp; task += NT) {
+      const int ib = task / hp, jh = task - ib * hp, ip0 = ib * IP;
+      cx<T> h0[IP][Q], h1[IP][Q];  // parent columns jh and jh + hp
+      for (int ic = 0; ic < nthc; ++ic) {
+        cx<T> ga[Q], gb[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          ga[q] = G[((size_t)q * nthc + ic) * Np + jh];
+          gb[q] = G[((size_t)q * nthc + ic) * Np + jh + hp];
         }
-        H[x] = acc;
+#pragma unroll
+        for (int k = 0; k < IP; ++k) {
+          const int ip = min(ip0 + k, nthp - 1);
+          const T a = Tps[ip * nthc + ic], bq = Tms[ip * nthc + ic];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            h0[k][q].re = fma(a, ga[q].re, fma(bq, gb[q].re, h0[k][q].re));
+            h0[k][q].im = fma(a, ga[q].im, fma(bq, gb[q].im, h0[k][q].im));
+            h1[k][q].re = fma(a, gb[q].re, fma(bq, ga[q].re, h1[k][q].re));
+            h1[k][q].im = fma(a, gb[q].im, fma(bq, ga[q].im, h1[k][q].im));
+          }
+        }
       }
-      const T *u = tpp + 6 * (size_t)t;
-      cx<T> sh = up[o * Kp + t];
-      Y[(((size_t)c * 4 + jm * 2) * nrhs + r) * Kp + t] = sh * (H[0] * u[0] + H[1] * u[1] + H[2] * u[2]);
-      Y[(((size_t)c * 4 + jm * 2 + 1) * nrhs + r) * Kp + t] = sh * (H[0] * u[3] + H[1] * u[4] + H[2] * u[5]);
+#pragma unroll
+      for (int k = 0; k < IP; ++k) {
+        const int ip = ip0 + k;
+        if (ip >= nthp) break;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int tp = ip * Np + jh + half * hp;
+          const T *u = tpp + 6 * (size_t)tp;
+          const cx<T> sh = up[(size_t)o * Kp + tp];
+#pragma unroll
+          for (int m = 0; m < JM; ++m) {
+            const cx<T> *H = half ? &h1[k][3 * m] : &h0[k][3 * m];
+            const cx<T> yt = H[0] * u[0] + H[1] * u[1] + H[2] * u[2];
+            const cx<T> yp = H[0] * u[3] + H[1] * u[4] + H[2] * u[5];
+            Y[(((size_t)c * 4 + (jm0 + m) * 2) * nrhs + r) * Kp + tp] = sh * yt;
+            Y[(((size_t)c * 4 + (jm0 + m) * 2 + 1) * nrhs + r) * Kp + tp] = sh * yp;
+          }
+        }
+      }
     }
   }
 }
@@ -314,67 +452,108 @@ __global__ void k_up_sum(int Kp, int nrhs, const int *__restrict__ ch_ptr, const
 
 // Exact transpose of k_interp_up (anterpolation, downward pass), with the
 // receive shift exp(-j k khat.(c_child - c_parent)): one CTA per (child box,
-// J|M, right-hand side), I_child += Interp^T [dn (.) I_parent].  Quadrature weights are folded into
-// the translators, so the adjoint is the plain transpose.
-template <typename T>
-__global__ void k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs, const int *__restrict__ parent,
-                            const int *__restrict__ oct, const T *__restrict__ tpc, const T *__restrict__ tpp,
-                            const T *__restrict__ Phi, const T *__restrict__ Thp, const T *__restrict__ Thm,
-                            const cx<T> *__restrict__ dn, const cx<T> *__restrict__ Ip, cx<T> *__restrict__ Ic) {
-  extern __shared__ unsigned char smem_raw[];
-  const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1, nthp = Lp + 1;
-  cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [3][Kp]
-  cx<T> *G = A + 3 * Kp;                            // [3][nthc][Np]
-  T *Ps = reinterpret_cast<T *>(G + 3 * nthc * Np);  // Phi [Np][Nc], then Theta+ and Theta- [nthp][nthc]
-  T *Tps = Ps + Np * Nc, *Tms = Tps + (Lp + 1) * nthc;
-  for (int t = threadIdx.x; t < Np * Nc; t += blockDim.x) Ps[t] = Phi[t];
-  for (int t = threadIdx.x; t < (Lp + 1) * nthc; t += blockDim.x) {
-    Tps[t] = Thp[t];
-    Tms[t] = Thm[t];
+// right-hand side), I_child += Interp^T [dn (.) I_parent].  Quadrature weights
+// are folded into the translators, so the adjoint is the plain transpose.
+// Register tiles as in k_interp_up: a theta-step task owns the column pair
+// (j, j + Np/2) for two child theta rows; a phi-step task owns the child
+// columns jc and jc + Nc/2 of one theta row.
+template <typename T, int JM>
+__global__ void __launch_bounds__(256) k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs,
+                                                  const int *__restrict__ parent, const int *__restrict__ oct,
+                                                  const T *__restrict__ tpc, const T *__restrict__ tpp,
+                                                  const T *__restrict__ Phi, const T *__restrict__ Thp,
+                                                  const T *__restrict__ Thm, const cx<T> *__restrict__ dn,
+                                                  const cx<T> *__restrict__ Ip, cx<T> *__restrict__ Ic) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int Q = 3 * JM, IC = 2;
+  const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1, nthp = Lp + 1, hp = Lp + 1, hc = Lc + 1;
+  cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [Q][Kp]
+  cx<T> *G = A + (size_t)Q * Kp;                    // [Q][nthc][Np]
+  T *Ps = reinterpret_cast<T *>(G + (size_t)Q * nthc * Np);  // Phi [Np][Nc]
+  T *Tps = Ps + Np * Nc, *Tms = Tps + nthp * nthc;           // [nthp][nthc]
+  const int c = blockIdx.x, r = blockIdx.y, pb = parent[c], o = oct[c], tid = threadIdx.x, NT = blockDim.x;
+  for (int i = tid; i < Np * Nc; i += NT) Ps[i] = Phi[i];
+  for (int i = tid; i < nthp * nthc; i += NT) {
+    Tps[i] = Thp[i];
+    Tms[i] = Thm[i];
   }
-  __syncthreads();
-  const int c = blockIdx.x, jm = blockIdx.y, r = blockIdx.z, pb = parent[c], o = oct[c];
-  const int nG = 3 * nthc * Np;
-  {
-      for (int t = threadIdx.x; t < Kp; t += blockDim.x) {
-        cx<T> sh = dn[o * Kp + t];
-        cx<T> ut = sh * Ip[(((size_t)pb * 4 + jm * 2) * nrhs + r) * Kp + t];
-        cx<T> up_ = sh * Ip[(((size_t)pb * 4 + jm * 2 + 1) * nrhs + r) * Kp + t];
-        const T *u = tpp + 6 * (size_t)t;
-        for (int x = 0; x < 3; ++x) A[x * Kp + t] = ut * u[x] + up_ * u[3 + x];
-      }
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < nG; idx += blockDim.x) {
-        int x = idx / (nthc * Np), rem = idx - x * nthc * Np, ic = rem / Np, j = rem - ic * Np;
-        int jq = (j + Lp + 1) % Np;
-        const cx<T> *a = A + (size_t)x * Kp;
-        cx<T> acc;
-        for (int ip = 0; ip < nthp; ++ip) {
-          T w1 = Tps[ip * nthc + ic], w2 = Tms[ip * nthc + ic];
-          cx<T> a1 = a[ip * Np + j], a2 = a[ip * Np + jq];
-          acc.re = fma(w1, a1.re, fma(w2, a2.re, acc.re));
-          acc.im = fma(w1, a1.im, fma(w2, a2.im, acc.im));
+  const int nicb = (nthc + IC - 1) / IC;
+  for (int jm0 = 0; jm0 < 2; jm0 += JM) {
+    __syncthreads();
+    for (int i = tid; i < JM * Kp; i += NT) {
+      const int m = i / Kp, t = i - m * Kp;
+      const cx<T> *it = Ip + (((size_t)pb * 4 + (jm0 + m) * 2) * nrhs + r) * Kp;
+      const cx<T> sh = dn[(size_t)o * Kp + t];
+      const cx<T> ut = sh * it[t], up_ = sh * it[(size_t)nrhs * Kp + t];
+      const T *u = tpp + 6 * (size_t)t;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) A[(size_t)(m * 3 + x) * Kp + t] = ut * u[x] + up_ * u[3 + x];
+    }
+    __syncthreads();
+    // transpose of the theta step: G[q][ic][j] = sum_ip Th+[ip][ic] A[q][ip][j] + Th-[ip][ic] A[q][ip][j + Np/2]
+    for (int task = tid; task < nicb * hp; task += NT) {
+      const int cb = task / hp, jh = task - cb * hp, ic0 = cb * IC;
+      cx<T> g0[IC][Q], g1[IC][Q];
+      for (int ip = 0; ip < nthp; ++ip) {
+        cx<T> aa[Q], ab[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          aa[q] = A[(size_t)q * Kp + ip * Np + jh];
+          ab[q] = A[(size_t)q * Kp + ip * Np + jh + hp];
         }
-        G[idx] = acc;
-      }
-      __syncthreads();
-      for (int t = threadIdx.x; t < Kc; t += blockDim.x) {
-        int ic = t / Nc, jc = t - ic * Nc;
-        cx<T> C[3];
-        for (int x = 0; x < 3; ++x) {
-          const cx<T> *g = G + ((size_t)x * nthc + ic) * Np;
-          cx<T> acc;
-          for (int jp = 0; jp < Np; ++jp) {
-            T ph = Ps[jp * Nc + jc];
-            acc.re = fma(ph, g[jp].re, acc.re);
-            acc.im = fma(ph, g[jp].im, acc.im);
+#pragma unroll
+        for (int k = 0; k < IC; ++k) {
+          const int ic = min(ic0 + k, nthc - 1);
+          const T w1 = Tps[ip * nthc + ic], w2 = Tms[ip * nthc + ic];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            g0[k][q].re = fma(w1, aa[q].re, fma(w2, ab[q].re, g0[k][q].re));
+            g0[k][q].im = fma(w1, aa[q].im, fma(w2, ab[q].im, g0[k][q].im));
+            g1[k][q].re = fma(w1, ab[q].re, fma(w2, aa[q].re, g1[k][q].re));
+            g1[k][q].im = fma(w1, ab[q].im, fma(w2, aa[q].im, g1[k][q].im));
           }
-          C[x] = acc;
         }
-        const T *u = tpc + 6 * (size_t)t;
-        Ic[(((size_t)c * 4 + jm * 2) * nrhs + r) * Kc + t] += C[0] * u[0] + C[1] * u[1] + C[2] * u[2];
-        Ic[(((size_t)c * 4 + jm * 2 + 1) * nrhs + r) * Kc + t] += C[0] * u[3] + C[1] * u[4] + C[2] * u[5];
       }
+#pragma unroll
+      for (int k = 0; k < IC; ++k) {
+        const int ic = ic0 + k;
+        if (ic >= nthc) break;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          G[((size_t)q * nthc + ic) * Np + jh] = g0[k][q];
+          G[((size_t)q * nthc + ic) * Np + jh + hp] = g1[k][q];
+        }
+      }
+    }
+    __syncthreads();
+    // transpose of the phi step, projection to (theta, phi) at the child directions
+    for (int task = tid; task < nthc * hc; task += NT) {
+      const int ic = task / hc, jc = task - ic * hc;
+      cx<T> c0[Q], c1[Q];
+      for (int jp = 0; jp < Np; ++jp) {
+        const T f0 = Ps[jp * Nc + jc], f1 = Ps[jp * Nc + jc + hc];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const cx<T> g = G[((size_t)q * nthc + ic) * Np + jp];
+          c0[q].re = fma(f0, g.re, c0[q].re);
+          c0[q].im = fma(f0, g.im, c0[q].im);
+          c1[q].re = fma(f1, g.re, c1[q].re);
+          c1[q].im = fma(f1, g.im, c1[q].im);
+        }
+      }
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int tc = ic * Nc + jc + half * hc;
+        const T *u = tpc + 6 * (size_t)tc;
+#pragma unroll
+        for (int m = 0; m < JM; ++m) {
+          const cx<T> *C = half ? &c1[3 * m] : &c0[3 * m];
+          cx<T> *it = Ic + (((size_t)c * 4 + (jm0 + m) * 2) * nrhs + r) * Kc;
+          it[tc] += C[0] * u[0] + C[1] * u[1] + C[2] * u[2];
+          it[(size_t)nrhs * Kc + tc] += C[0] * u[3] + C[1] * u[4] + C[2] * u[5];
+        }
+      }
+    }
   }
 }
 
@@ -433,47 +612,97 @@ __global__ void k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr,
 }
 
 // Leaf receive with the JMCFIE weights of medium l (weights and constants
-// folded into the translators):
-//   J-row: s_i R^t.F1 - R^n.F2,   M-row: -(s_i R^t.F3 + R^n.F4)
-//   F1 = I^J - khat x I^M / eta,  F2 = (F1_phi, -F1_theta)
-//   F3 = -eta khat x I^J - I^M,   F4 = (-F3_phi, F3_theta)
-// R^t_i(k) = V_i(-k) read at the antipodal sample (theta comp as is, phi negated).
-template <typename T>
-__global__ void k_disaggregate(int nb, int K, int L, int ne, int nrhs, const int *__restrict__ basis_p,
-                               const int *__restrict__ sign, const int *__restrict__ basis_box,
-                               const cx<T> *__restrict__ V, const cx<T> *__restrict__ RN, const cx<T> *__restrict__ I,
-                               cx<T> eta, cx<T> ieta, cx<T> *__restrict__ y) {
-  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (i >= nb) return;
-  int p = basis_p[i], b = basis_box[i];
-  T s = (T)sign[i];
-  int nph = 2 * L + 2;
-  const cx<T> *Vi = V + (size_t)i * 2 * K, *Ri = RN + (size_t)i * 2 * K;
-  for (int r = 0; r < nrhs; ++r) {
-    cx<T> yj, ym;
-    const size_t cs = (size_t)nrhs * K;
-    const cx<T> *Ib = I + ((size_t)b * 4 * nrhs + r) * K;
-    for (int k = lane; k < K; k += 32) {
-      int it = k / nph, jp = k - it * nph;
-      int ka = (L - it) * nph + (jp + L + 1) % nph;
-      cx<T> rtt = Vi[ka], rtp = -Vi[K + ka];
-      cx<T> rnt = Ri[k], rnp = Ri[K + k];
-      cx<T> iJt = Ib[k], iJp = Ib[cs + k];
-      cx<T> iMt = Ib[2 * cs + k], iMp = Ib[3 * cs + k];
-      // khat x (a_t, a_p) = (-a_p, a_t)
-      cx<T> f1t = iJt + iMp * ieta, f1p = iJp - iMt * ieta;
-      cx<T> f3t = eta * iJp - iMt, f3p = -(eta * iJt) - iMp;
-      yj += s * (rtt * f1t + rtp * f1p) - (rnt * f1p - rnp * f1t);
-      ym -= s * (rtt * f3t + rtp * f3p) + (rnp * f3t - rnt * f3p);
+// folded into the translators).  Per box the combined fields
+//   F1 = I^J - khat x I^M / eta,   F3 = -eta khat x I^J - I^M,
+// khat x (a_t, a_p) = (-a_p, a_t), are formed once in shared memory; then each
+// basis (one warp, lanes over k) takes
+//   y_J += sum_k P_t F1_t + P_p F1_p,   y_M -= sum_k P_t F3_t + P_p F3_p
+// with its combined receive pattern P (antipodal radiation pattern for the
+// tangential test, t x n pattern for the n x operators, signs folded in).
+// The box's P block streams through shared memory by bulk copies, as in
+// k_aggregate.
+template <typename T, int RB>
+__global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, int cb,
+                                                     const int *__restrict__ box_start,
+                                                     const int *__restrict__ basis_p, const cx<T> *__restrict__ P,
+                                                     const cx<T> *__restrict__ I, cx<T> eta, cx<T> ieta,
+                                                     cx<T> *__restrict__ y, int *err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ unsigned long long bar[STAGES];
+  const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const size_t per = (size_t)2 * K;
+  cx<T> *ring = reinterpret_cast<cx<T> *>(smem_raw);  // [STAGES][cb][2][K]
+  cx<T> *F = ring + (size_t)STAGES * cb * per;        // [RB][4][K]: F1t, F1p, F3t, F3p
+  const size_t cs = (size_t)nrhs * K;
+  const int nch = (n + cb - 1) / cb;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < STAGES; ++q) mbar_init(&bar[q], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  int issued = 0, used = 0;
+  auto issue = [&](int ch) {
+    const int li0 = ch * cb, m = min(cb, n - li0);
+    const int st = issued % STAGES;
+    bulk_load(ring + (size_t)st * cb * per, P + (size_t)(i0 + li0) * per, (unsigned)(m * per * sizeof(cx<T>)),
+              &bar[st]);
+    ++issued;
+  };
+  bool ok = true;
+  for (int r0 = 0; r0 < nrhs; r0 += RB) {
+    const int nr = min(RB, nrhs - r0);
+    if (threadIdx.x == 0)
+      for (int ch = 0; ch < min(STAGES, nch); ++ch) issue(ch);
+    for (int idx = threadIdx.x; idx < nr * K; idx += blockDim.x) {
+      const int rr = idx / K, k = idx - rr * K;
+      const cx<T> *Ib = I + ((size_t)b * 4 * nrhs + r0 + rr) * K + k;
+      const cx<T> iJt = Ib[0], iJp = Ib[cs], iMt = Ib[2 * cs], iMp = Ib[3 * cs];
+      cx<T> *f = F + (size_t)rr * 4 * K + k;
+      f[0] = iJt + iMp * ieta;
+      f[K] = iJp - iMt * ieta;
+      f[2 * K] = eta * iJp - iMt;
+      f[3 * K] = -(eta * iJt) - iMp;
     }
-    yj = warp_sum(yj);
-    ym = warp_sum(ym);
-    if (lane == 0) {
-      cx<T> *o = y + ((size_t)r * ne + p) * 2;
-      o[0] += yj;
-      o[1] += ym;
+    __syncthreads();
+    for (int ch = 0; ch < nch; ++ch) {
+      const int st = used % STAGES;
+      ok = mbar_wait(&bar[st], (unsigned)((used / STAGES) & 1), err) && ok;
+      ++used;
+      const int li0 = ch * cb, m = min(cb, n - li0);
+      const cx<T> *pc = ring + (size_t)st * cb * per;
+      for (int li = warp; li < m; li += nw) {
+        const cx<T> *Pi = pc + (size_t)li * per;
+        cx<T> yj[RB], ym[RB];
+        for (int k = lane; k < K; k += 32) {
+          const cx<T> pt = Pi[k], pp = Pi[K + k];
+#pragma unroll
+          for (int rr = 0; rr < RB; ++rr)
+            if (rr < nr) {
+              const cx<T> *f = F + (size_t)rr * 4 * K + k;
+              yj[rr] = cfma(pt, f[0], cfma(pp, f[K], yj[rr]));
+              ym[rr] = cfma(pt, f[2 * K], cfma(pp, f[3 * K], ym[rr]));
+            }
+        }
+        const int p = basis_p[i0 + li0 + li];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+          if (rr < nr) {
+            const cx<T> sj = warp_sum(yj[rr]), sm = warp_sum(ym[rr]);
+            if (lane == 0) {
+              cx<T> *o = y + ((size_t)(r0 + rr) * ne + p) * 2;
+              o[0] += sj;
+              o[1] -= sm;
+            }
+          }
+      }
+      __syncthreads();  // the stage is free again
+      if (threadIdx.x == 0 && ch + STAGES < nch) issue(ch + STAGES);
     }
+  }
+  if (!ok) {
+    // a wait gave up: wait once more, bounded, for every stage's last copy before leaving
+    for (int u = max(0, used - STAGES); u < used; ++u) mbar_wait(&bar[u % STAGES], (unsigned)((u / STAGES) & 1), err);
   }
 }
 
@@ -888,25 +1117,40 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
     if (G.nb == 0) continue;
     LevelHost &LL = G.lev[leaf];
     // aggregation at the leaf level
+    const size_t per_basis = (size_t)2 * LL.K * sizeof(cx<T>);
+    const int cb = (int)std::max<size_t>(1, std::min<size_t>(32, (32 * 1024) / per_basis));  // bases per chunk
+    SIE_REQUIRE(LL.K <= AGG_KS * 256, SIE_EINVAL, "MLFMM: too many leaf directions for the aggregation kernel");
     {
-      dim3 grid((LL.K + 127) / 128, LL.nbox);
-      k_aggregate<T><<<grid, 128, 0, c->stream>>>(LL.nbox, LL.K, c->ne, R, G.d_box_start, G.d_basis_p,
-                                                  G.d_basis_sign, (const cx<T> *)tsel<T>::V(G), x,
-                                                  (cx<T> *)LL.d_S);
+      auto agg = [&](auto kern, int rb) {
+        const size_t smem = STAGES * cb * per_basis + (size_t)G.max_leaf * rb * 2 * sizeof(cx<T>);
+        set_smem(kern, smem);
+        kern<<<LL.nbox, 256, smem, c->stream>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p, G.d_basis_sign,
+                                                (const cx<T> *)tsel<T>::V(G), x, (cx<T> *)LL.d_S, c->d_err);
+      };
+      if (R == 1) agg(k_aggregate<T, 1>, 1);
+      else agg(k_aggregate<T, 4>, 4);
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
     // upward pass: interpolate + shift each child, then sum into parents
     for (int lv = leaf; lv >= 3; --lv) {
       LevelHost &C = G.lev[lv], &P = G.lev[lv - 1];
-      size_t smem = (size_t)(3 * C.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>) +
-                    (size_t)((2 * P.L + 2) * (2 * C.L + 2) + 2 * (P.L + 1) * (C.L + 1)) * sizeof(T);
-      set_smem(k_interp_up<T>, smem);
+      const int nthc = C.L + 1, Nc = 2 * C.L + 2, Np = 2 * P.L + 2, nthp = P.L + 1;
+      const size_t tabs = ((size_t)Np * Nc + 2 * (size_t)nthp * nthc) * sizeof(T);
+      auto smem_for = [&](int jm) { return ((size_t)3 * jm * C.K + (size_t)3 * jm * nthc * Np) * sizeof(cx<T>) + tabs; };
+      const bool both = smem_for(2) <= 160 * 1024;
+      const size_t smem = smem_for(both ? 2 : 1);
       cx<T> *Y = (cx<T> *)c->d_scratch;
-      k_interp_up<T><<<dim3(C.nbox, 2, R), 256, smem, c->stream>>>(
-          C.K, C.L, P.K, P.L, R, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
-          (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
-          (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
+      dim3 grid(C.nbox, R);
+      auto args = [&](auto kern) {
+        set_smem(kern, smem);
+        kern<<<grid, 256, smem, c->stream>>>(C.K, C.L, P.K, P.L, R, C.d_oct, (const T *)tsel<T>::tp(C),
+                                             (const T *)tsel<T>::tp(P), (const T *)tsel<T>::Phi(P),
+                                             (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
+                                             (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
+      };
+      if (both) args(k_interp_up<T, 2>);
+      else args(k_interp_up<T, 1>);
       SIE_CHECK_LAUNCH();
       k_up_sum<T><<<dim3((P.K + 127) / 128, P.nbox), 128, 0, c->stream>>>(P.K, R, P.d_ch_ptr, P.d_ch_idx, Y,
                                                                            (cx<T> *)P.d_S);
@@ -925,25 +1169,37 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
     // downward pass: shift + anterpolate (exact transpose) into children
     for (int lv = 2; lv < leaf; ++lv) {
       LevelHost &P = G.lev[lv], &C = G.lev[lv + 1];
-      size_t smem = (size_t)(3 * P.K + 3 * (C.L + 1) * (2 * P.L + 2)) * sizeof(cx<T>) +
-                    (size_t)((2 * P.L + 2) * (2 * C.L + 2) + 2 * (P.L + 1) * (C.L + 1)) * sizeof(T);
-      set_smem(k_anterp_dn<T>, smem);
-      k_anterp_dn<T><<<dim3(C.nbox, 2, R), 256, smem, c->stream>>>(
-          C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
-          (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
-          (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
+      const int nthc = C.L + 1, Nc = 2 * C.L + 2, Np = 2 * P.L + 2, nthp = P.L + 1;
+      const size_t tabs = ((size_t)Np * Nc + 2 * (size_t)nthp * nthc) * sizeof(T);
+      auto smem_for = [&](int jm) { return ((size_t)3 * jm * P.K + (size_t)3 * jm * nthc * Np) * sizeof(cx<T>) + tabs; };
+      const bool both = smem_for(2) <= 160 * 1024;
+      const size_t smem = smem_for(both ? 2 : 1);
+      dim3 grid(C.nbox, R);
+      auto args = [&](auto kern) {
+        set_smem(kern, smem);
+        kern<<<grid, 256, smem, c->stream>>>(C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C),
+                                             (const T *)tsel<T>::tp(P), (const T *)tsel<T>::Phi(P),
+                                             (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
+                                             (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
+      };
+      if (both) args(k_anterp_dn<T, 2>);
+      else args(k_anterp_dn<T, 1>);
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
     // receive at the leaves
     {
-      int wpb = 8;
-      int blocks = (G.nb + wpb - 1) / wpb;
       std::complex<double> ie = 1.0 / G.eta;
-      k_disaggregate<T><<<blocks, 32 * wpb, 0, c->stream>>>(
-          G.nb, LL.K, LL.L, c->ne, R, G.d_basis_p, G.d_basis_sign, G.d_basis_box, (const cx<T> *)tsel<T>::V(G),
-          (const cx<T> *)tsel<T>::RN(G), (const cx<T> *)LL.d_I, cx<T>((T)G.eta.real(), (T)G.eta.imag()),
-          cx<T>((T)ie.real(), (T)ie.imag()), y);
+      auto rec = [&](auto kern, int rb) {
+        const size_t smem = STAGES * cb * per_basis + (size_t)rb * 4 * LL.K * sizeof(cx<T>);
+        set_smem(kern, smem);
+        kern<<<LL.nbox, 256, smem, c->stream>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p,
+                                                (const cx<T> *)tsel<T>::P(G), (const cx<T> *)LL.d_I,
+                                                cx<T>((T)G.eta.real(), (T)G.eta.imag()),
+                                                cx<T>((T)ie.real(), (T)ie.imag()), y, c->d_err);
+      };
+      if (R == 1) rec(k_disaggregate<T, 1>, 1);
+      else rec(k_disaggregate<T, 4>, 4);
       SIE_CHECK_LAUNCH();
       c->launches++;
     }

@@ -416,6 +416,7 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
   sie_status rc = run_gmres_internal(c, b, x, R, o->restart, o->max_iters, o->tol, prec, o->precond, nullptr, st);
   op_permute_out(c, x, x_user, R);
   SIE_CUDA(cudaStreamSynchronize(c->stream));
+  check_device_errors(c);
   return rc;
 }
 
