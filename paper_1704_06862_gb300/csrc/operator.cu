@@ -1138,8 +1138,8 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       const int nthc = C.L + 1, Nc = 2 * C.L + 2, Np = 2 * P.L + 2, nthp = P.L + 1;
       const size_t tabs = ((size_t)Np * Nc + 2 * (size_t)nthp * nthc) * sizeof(T);
       auto smem_for = [&](int jm) { return ((size_t)3 * jm * C.K + (size_t)3 * jm * nthc * Np) * sizeof(cx<T>) + tabs; };
-      const bool both = smem_for(2) <= 160 * 1024;
-      const size_t smem = smem_for(both ? 2 : 1);
+      // one source (J or M) per pass: fewer registers, more CTAs per SM (measured faster than both at once)
+      const size_t smem = smem_for(1);
       cx<T> *Y = (cx<T> *)c->d_scratch;
       dim3 grid(C.nbox, R);
       auto args = [&](auto kern) {
@@ -1149,8 +1149,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
                                              (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
                                              (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
       };
-      if (both) args(k_interp_up<T, 2>);
-      else args(k_interp_up<T, 1>);
+      args(k_interp_up<T, 1>);
       SIE_CHECK_LAUNCH();
       k_up_sum<T><<<dim3((P.K + 127) / 128, P.nbox), 128, 0, c->stream>>>(P.K, R, P.d_ch_ptr, P.d_ch_idx, Y,
                                                                            (cx<T> *)P.d_S);
@@ -1172,8 +1171,8 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       const int nthc = C.L + 1, Nc = 2 * C.L + 2, Np = 2 * P.L + 2, nthp = P.L + 1;
       const size_t tabs = ((size_t)Np * Nc + 2 * (size_t)nthp * nthc) * sizeof(T);
       auto smem_for = [&](int jm) { return ((size_t)3 * jm * P.K + (size_t)3 * jm * nthc * Np) * sizeof(cx<T>) + tabs; };
-      const bool both = smem_for(2) <= 160 * 1024;
-      const size_t smem = smem_for(both ? 2 : 1);
+      // one source (J or M) per pass: fewer registers, more CTAs per SM (measured faster than both at once)
+      const size_t smem = smem_for(1);
       dim3 grid(C.nbox, R);
       auto args = [&](auto kern) {
         set_smem(kern, smem);
@@ -1182,8 +1181,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
                                              (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
                                              (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
       };
-      if (both) args(k_anterp_dn<T, 2>);
-      else args(k_anterp_dn<T, 1>);
+      args(k_anterp_dn<T, 1>);
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
