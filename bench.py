@@ -161,6 +161,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-nn", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="right-hand sides of the batched monostatic leg")
+    ap.add_argument("--no-graphs", action="store_true", help="launch every Krylov step eagerly (for profilers)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -197,7 +198,7 @@ def main():
             sie.sie_plane_wave_rhs(s.ctx, inc, b_dev)
         x.zero_()
         st = sie.gmres_solve(s.ctx, b_dev, x, 1, restart=RESTART, max_iters=3000, tol=TOL, prec=prec,
-                             precond=precond, check=False)
+                             precond=precond, check=False, graphs=not args.no_graphs)
         rcs = sie.rcs_farfield_prec(s.ctx, x, 1, obs, prec)  # device -> host
         return st[0], rcs
 
@@ -265,7 +266,8 @@ def main():
             sie.sie_plane_wave_rhs(s.ctx, incb, bb)
             xb.zero_()
             stb = sie.gmres_solve(s.ctx, bb, xb, nb, restart=RESTART, max_iters=3000, tol=TOL,
-                                  prec=sie.SIE_PREC_MIXED, precond=1, check=False)
+                                  prec=sie.SIE_PREC_MIXED, precond=1, check=False,
+                                  graphs=not args.no_graphs)
             obs_b = np.stack([incb[:, 0], incb[:, 1]], axis=1)
             mono = sie.rcs_farfield_prec(s.ctx, xb, nb, obs_b, sie.SIE_PREC_MIXED)
             return stb, mono[np.arange(nb), np.arange(nb), 0]

@@ -167,6 +167,10 @@ typedef struct {
                           correction is dropped for the rest of a solve as soon
                           as a restart cycle fails to reduce the true residual),
                           all as right preconditioning */
+  int32_t no_graphs;   /* 0: each Krylov step (preconditioner + product) is
+                          captured once as a CUDA graph and replayed; 1: every
+                          step is launched eagerly (same kernels, same results;
+                          for tools that cannot follow graph launches) */
 } sie_solve_opts;
 
 typedef struct {

@@ -44,7 +44,7 @@ class sie_fill_opts(ctypes.Structure):
 
 class sie_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("prec", ctypes.c_int32), ("precond", ctypes.c_int32)]
+                ("prec", ctypes.c_int32), ("precond", ctypes.c_int32), ("no_graphs", ctypes.c_int32)]
 
 
 class sie_solve_stats(ctypes.Structure):
@@ -179,8 +179,8 @@ def sie_plane_wave_rhs(ctx, inc, b):
 
 
 def gmres_solve(ctx, b, x, nrhs, restart=50, max_iters=1000, tol=1e-4, prec=SIE_PREC_FP64, precond=1,
-                check=True):
-    o = sie_solve_opts(int(restart), int(max_iters), float(tol), int(prec), int(precond))
+                check=True, graphs=True):
+    o = sie_solve_opts(int(restart), int(max_iters), float(tol), int(prec), int(precond), 0 if graphs else 1)
     st = (sie_solve_stats * int(nrhs))()
     rc = load_library().gmres_solve(ctx, _ptr(b), _ptr(x), int(nrhs), ctypes.byref(o), st)
     stats = [dict(iters=s.iters, restarts=s.restarts, rel_residual=s.rel_residual, converged=bool(s.converged))

@@ -163,10 +163,10 @@ struct sie_ctx {
   int *d_tri_e = nullptr;        // per triangle: 3 internal edge ids (-1 none)
   double *d_tri_sg = nullptr;    // per triangle: 3 signs * len/(2A)
   int *d_tri_reg = nullptr;      // [nt][2]
+  bool graphs_off = false;       // Krylov steps launched eagerly (sie_solve_opts.no_graphs)
   int *d_tri0 = nullptr;         // triangles bounding the host medium (region 0)
   int ntri0 = 0;
   void *d_ff = nullptr;          // far-field work: point positions, point currents, partial sums
-  int *d_err = nullptr;          // device error flag: 1 = a bounded wait in a kernel gave up
   size_t ff_bytes = 0;
   int *d_row_ptr = nullptr, *d_col = nullptr;
   void *d_near64 = nullptr, *d_near32 = nullptr;  // [nnzb][4] blocks
@@ -189,7 +189,9 @@ struct sie_ctx {
   void *graphs = nullptr;   // captured per-step operator graphs (solve.cu)
   void *nn = nullptr;  // learned-preconditioner state (nn.cu)
   void *gm_V = nullptr, *gm_Z = nullptr, *gm_b = nullptr, *gm_x = nullptr, *gm_w = nullptr;
-  void *gm_h = nullptr, *gm_s = nullptr, *gm_part = nullptr;
+  void *gm_h = nullptr, *gm_s = nullptr, *gm_part = nullptr, *gm_act = nullptr, *gm_gate = nullptr;
+  void *gm_hpin = nullptr;        // pinned host mirror of gm_h (one copy per Krylov step)
+  cudaEvent_t gm_ev = nullptr;    // marks that copy
 };
 
 // ------------------------------------------------------------------ host helpers (host.cpp)
@@ -203,7 +205,6 @@ T *dev_upload(sie_ctx *c, const std::vector<T> &v) {
 }
 void ensure_work(sie_ctx *c, int64_t nrhs);
 void *stage(sie_ctx *c, size_t bytes);
-void check_device_errors(sie_ctx *c);  // after a stream synchronisation: SIE_ETIMEOUT if a kernel gave up
 
 // ------------------------------------------------------------------ launchers (fill.cu)
 void launch_near_fill(sie_ctx *c, int region);

@@ -25,16 +25,6 @@ void *dev_alloc(sie_ctx *c, size_t bytes) {
   return p;
 }
 
-void check_device_errors(sie_ctx *c) {
-  if (!c->d_err) return;
-  int e = 0;
-  SIE_CUDA(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (e != 0) {
-    SIE_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
-    SIE_REQUIRE(false, SIE_ETIMEOUT, "a bounded wait for a bulk copy in a kernel gave up");
-  }
-}
-
 void *stage(sie_ctx *c, size_t bytes) {
   if (bytes > c->stage_bytes) {
     c->d_stage = dev_alloc(c, std::max(bytes, (size_t)4096));
@@ -158,6 +148,8 @@ extern "C" void sie_destroy(sie_ctx *c) {
   nn_free(c);
   graphs_free(c);
   for (auto &b : c->bufs) cudaFree(b.p);
+  if (c->gm_hpin) cudaFreeHost(c->gm_hpin);
+  if (c->gm_ev) cudaEventDestroy(c->gm_ev);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -925,10 +917,6 @@ static void build_ilu(sie_ctx *c) {
 // ------------------------------------------------------------------ API: fill
 static void fill_all(sie_ctx *c, const sie_fill_opts *o) {
   const int ne = c->ne, nt = c->nt;
-  if (!c->d_err) {
-    c->d_err = (int *)dev_alloc(c, sizeof(int));
-    SIE_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
-  }
   int on = o ? o->outer_order : 4;
   SIE_REQUIRE(on >= 2 && on <= 12, SIE_EINVAL, "sie_fill_nearfield: outer_order must be in [2, 12]");
   // geometry tables, internal edge ids
@@ -1221,7 +1209,6 @@ extern "C" sie_status sie_stage_timing(sie_ctx *c, int32_t stage, int64_t nrhs, 
     SIE_CUDA(cudaEventElapsedTime(&t, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    check_device_errors(c);
     *ms = (double)t / reps;
   });
 }

@@ -3,6 +3,8 @@
 // Every kernel is templated on the real type: double (plain form) or float
 // (mixed form, FP32 complex with FP32 accumulation).
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "common.h"
@@ -183,38 +185,25 @@ __global__ void k_near_spmv_blk(int ne, int nrhs, const int *__restrict__ row_pt
   }
 }
 
-// ---------------------------------------------------------------- bulk copies
-// Bulk global -> shared copies (cp.async.bulk, the non-tensor TMA form) that
-// complete on a shared-memory mbarrier.  Every wait is bounded: a wait that
-// gives up records SIE_ETIMEOUT-style code 1 in *err and returns false.
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+// ---------------------------------------------------------------- async staging
+// Per-thread 16-byte asynchronous global -> shared copies (cp.async), used to
+// stream contiguous pattern blocks through a shared-memory ring: every thread
+// issues its pieces of a chunk and commits them as one group; a chunk is read
+// after cp.async.wait_group has retired its group and the CTA has synchronised.
+__device__ __forceinline__ void cp_async16_s(void *smem, const void *gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+__device__ __forceinline__ void cp_async_commit_s() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_s() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err) {
-  const unsigned a = smem_u32(bar);
-  for (int it = 0; it < (1 << 20); ++it) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  atomicExch(err, 1);
-  return false;
+// copy `bytes` (a multiple of 16, both addresses 16-byte aligned) with all threads of the CTA
+__device__ __forceinline__ void cta_copy_async(void *dst, const void *src, size_t bytes) {
+  char *d = reinterpret_cast<char *>(dst);
+  const char *g = reinterpret_cast<const char *>(src);
+  for (size_t o = (size_t)threadIdx.x * 16; o < bytes; o += (size_t)blockDim.x * 16) cp_async16_s(d + o, g + o);
 }
 
 // ---------------------------------------------------------------- MLFMM
@@ -224,41 +213,33 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // k reads and writes whole lines for any number of right-hand sides.
 // One CTA per leaf box, threads over the directions k (up to AGG_KS per
 // thread).  The box's patterns, one contiguous block, stream through shared
-// memory in chunks of cb bases by bulk copies into a two-stage ring, so the
-// whole chunk is in flight at once; the box's signed coefficients are staged
-// in shared memory and each pattern value serves RB right-hand sides.
+// memory in chunks of cb bases by asynchronous copies into a two-stage ring,
+// so a whole chunk is in flight at once; the box's signed coefficients are
+// staged in shared memory and each pattern value serves RB right-hand sides.
 constexpr int AGG_KS = 2, STAGES = 2;
 template <typename T, int RB>
 __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int cb, const int *__restrict__ box_start,
                                                   const int *__restrict__ basis_p, const int *__restrict__ sign,
                                                   const cx<T> *__restrict__ V, const cx<T> *__restrict__ x,
-                                                  cx<T> *__restrict__ S, int *err) {
+                                                  cx<T> *__restrict__ S) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ unsigned long long bar[STAGES];
   const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
   const size_t per = (size_t)2 * K;  // complex values per basis
   cx<T> *ring = reinterpret_cast<cx<T> *>(smem_raw);       // [STAGES][cb][2][K]
   cx<T> *xs = ring + (size_t)STAGES * cb * per;            // [n][RB][2]
   const size_t cs = (size_t)nrhs * K;  // component stride
   const int nch = (n + cb - 1) / cb;
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < STAGES; ++q) mbar_init(&bar[q], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  int issued = 0, used = 0;  // chunks issued / consumed over all passes (ring position and parity)
-  auto issue = [&](int ch) {
-    const int li0 = ch * cb, m = min(cb, n - li0);
-    const int st = issued % STAGES;
-    bulk_load(ring + (size_t)st * cb * per, V + (size_t)(i0 + li0) * per, (unsigned)(m * per * sizeof(cx<T>)),
-              &bar[st]);
-    ++issued;
+  auto fetch = [&](int ch) {  // every thread issues its pieces of chunk ch, then commits (possibly empty)
+    if (ch < nch) {
+      const int li0 = ch * cb, m = min(cb, n - li0);
+      cta_copy_async(ring + (size_t)(ch % STAGES) * cb * per, V + (size_t)(i0 + li0) * per,
+                     (size_t)m * per * sizeof(cx<T>));
+    }
+    cp_async_commit_s();
   };
-  bool ok = true;
   for (int r0 = 0; r0 < nrhs; r0 += RB) {
     const int nr = min(RB, nrhs - r0);
-    if (threadIdx.x == 0)
-      for (int ch = 0; ch < min(STAGES, nch); ++ch) issue(ch);
+    for (int ch = 0; ch < STAGES; ++ch) fetch(ch);
     for (int idx = threadIdx.x; idx < n * RB; idx += blockDim.x) {
       const int li = idx / RB, rr = idx - li * RB;
       cx<T> xj, xm;
@@ -272,14 +253,12 @@ __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int 
       xs[2 * idx] = xj;
       xs[2 * idx + 1] = xm;
     }
-    __syncthreads();
     cx<T> a0[AGG_KS][RB], a1[AGG_KS][RB], a2[AGG_KS][RB], a3[AGG_KS][RB];
     for (int ch = 0; ch < nch; ++ch) {
-      const int st = used % STAGES;
-      ok = mbar_wait(&bar[st], (unsigned)((used / STAGES) & 1), err) && ok;
-      ++used;
+      cp_async_wait_s<STAGES - 1>();
+      __syncthreads();  // chunk ch (and, the first time, the coefficients) visible to all
       const int li0 = ch * cb, m = min(cb, n - li0);
-      const cx<T> *v = ring + (size_t)st * cb * per;
+      const cx<T> *v = ring + (size_t)(ch % STAGES) * cb * per;
 #pragma unroll
       for (int s = 0; s < AGG_KS; ++s) {
         const int k = threadIdx.x + s * blockDim.x;
@@ -298,8 +277,9 @@ __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int 
         }
       }
       __syncthreads();  // the stage is free again
-      if (threadIdx.x == 0 && ch + STAGES < nch) issue(ch + STAGES);
+      fetch(ch + STAGES);
     }
+    cp_async_wait_s<0>();
 #pragma unroll
     for (int s = 0; s < AGG_KS; ++s) {
       const int k = threadIdx.x + s * blockDim.x;
@@ -315,10 +295,6 @@ __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int 
         }
     }
     __syncthreads();
-  }
-  if (!ok) {
-    // a wait gave up: wait once more, bounded, for every stage's last copy before leaving
-    for (int u = max(0, used - STAGES); u < used; ++u) mbar_wait(&bar[u % STAGES], (unsigned)((u / STAGES) & 1), err);
   }
 }
 
@@ -619,16 +595,14 @@ __global__ void k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr,
 //   y_J += sum_k P_t F1_t + P_p F1_p,   y_M -= sum_k P_t F3_t + P_p F3_p
 // with its combined receive pattern P (antipodal radiation pattern for the
 // tangential test, t x n pattern for the n x operators, signs folded in).
-// The box's P block streams through shared memory by bulk copies, as in
-// k_aggregate.
+// The box's P block streams through shared memory as in k_aggregate.
 template <typename T, int RB>
 __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, int cb,
                                                      const int *__restrict__ box_start,
                                                      const int *__restrict__ basis_p, const cx<T> *__restrict__ P,
                                                      const cx<T> *__restrict__ I, cx<T> eta, cx<T> ieta,
-                                                     cx<T> *__restrict__ y, int *err) {
+                                                     cx<T> *__restrict__ y) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ unsigned long long bar[STAGES];
   const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const size_t per = (size_t)2 * K;
@@ -636,24 +610,17 @@ __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, i
   cx<T> *F = ring + (size_t)STAGES * cb * per;        // [RB][4][K]: F1t, F1p, F3t, F3p
   const size_t cs = (size_t)nrhs * K;
   const int nch = (n + cb - 1) / cb;
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < STAGES; ++q) mbar_init(&bar[q], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  int issued = 0, used = 0;
-  auto issue = [&](int ch) {
-    const int li0 = ch * cb, m = min(cb, n - li0);
-    const int st = issued % STAGES;
-    bulk_load(ring + (size_t)st * cb * per, P + (size_t)(i0 + li0) * per, (unsigned)(m * per * sizeof(cx<T>)),
-              &bar[st]);
-    ++issued;
+  auto fetch = [&](int ch) {
+    if (ch < nch) {
+      const int li0 = ch * cb, m = min(cb, n - li0);
+      cta_copy_async(ring + (size_t)(ch % STAGES) * cb * per, P + (size_t)(i0 + li0) * per,
+                     (size_t)m * per * sizeof(cx<T>));
+    }
+    cp_async_commit_s();
   };
-  bool ok = true;
   for (int r0 = 0; r0 < nrhs; r0 += RB) {
     const int nr = min(RB, nrhs - r0);
-    if (threadIdx.x == 0)
-      for (int ch = 0; ch < min(STAGES, nch); ++ch) issue(ch);
+    for (int ch = 0; ch < STAGES; ++ch) fetch(ch);
     for (int idx = threadIdx.x; idx < nr * K; idx += blockDim.x) {
       const int rr = idx / K, k = idx - rr * K;
       const cx<T> *Ib = I + ((size_t)b * 4 * nrhs + r0 + rr) * K + k;
@@ -664,13 +631,11 @@ __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, i
       f[2 * K] = eta * iJp - iMt;
       f[3 * K] = -(eta * iJt) - iMp;
     }
-    __syncthreads();
     for (int ch = 0; ch < nch; ++ch) {
-      const int st = used % STAGES;
-      ok = mbar_wait(&bar[st], (unsigned)((used / STAGES) & 1), err) && ok;
-      ++used;
+      cp_async_wait_s<STAGES - 1>();
+      __syncthreads();  // chunk ch (and, the first time, the fields) visible to all
       const int li0 = ch * cb, m = min(cb, n - li0);
-      const cx<T> *pc = ring + (size_t)st * cb * per;
+      const cx<T> *pc = ring + (size_t)(ch % STAGES) * cb * per;
       for (int li = warp; li < m; li += nw) {
         const cx<T> *Pi = pc + (size_t)li * per;
         cx<T> yj[RB], ym[RB];
@@ -697,12 +662,10 @@ __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, i
           }
       }
       __syncthreads();  // the stage is free again
-      if (threadIdx.x == 0 && ch + STAGES < nch) issue(ch + STAGES);
+      fetch(ch + STAGES);
     }
-  }
-  if (!ok) {
-    // a wait gave up: wait once more, bounded, for every stage's last copy before leaving
-    for (int u = max(0, used - STAGES); u < used; ++u) mbar_wait(&bar[u % STAGES], (unsigned)((u / STAGES) & 1), err);
+    cp_async_wait_s<0>();
+    __syncthreads();
   }
 }
 
@@ -1085,7 +1048,19 @@ __global__ void k_f2d(const zf *a, zd *b, int64_t n) {
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
   SIE_REQUIRE(bytes <= 227 * 1024, SIE_EINVAL, "MLFMM interpolation tile exceeds shared memory (too many directions)");
-  if (bytes > 48 * 1024) SIE_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  if (bytes <= 48 * 1024) return;
+  // the attribute is raised once per (device, kernel) to the largest size asked for:
+  // a driver call per launch costs more host time than some launches take on the GPU
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> raised;
+  int dev = 0;
+  SIE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  size_t &have = raised[{dev, reinterpret_cast<const void *>(kernel)}];
+  if (bytes > have) {
+    SIE_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    have = bytes;
+  }
 }
 
 inline int grid1(int64_t n, int bs) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + bs - 1) / bs, 152 * 32)); }
@@ -1125,7 +1100,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
         const size_t smem = STAGES * cb * per_basis + (size_t)G.max_leaf * rb * 2 * sizeof(cx<T>);
         set_smem(kern, smem);
         kern<<<LL.nbox, 256, smem, c->stream>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p, G.d_basis_sign,
-                                                (const cx<T> *)tsel<T>::V(G), x, (cx<T> *)LL.d_S, c->d_err);
+                                                (const cx<T> *)tsel<T>::V(G), x, (cx<T> *)LL.d_S);
       };
       if (R == 1) agg(k_aggregate<T, 1>, 1);
       else agg(k_aggregate<T, 4>, 4);
@@ -1194,7 +1169,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
         kern<<<LL.nbox, 256, smem, c->stream>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p,
                                                 (const cx<T> *)tsel<T>::P(G), (const cx<T> *)LL.d_I,
                                                 cx<T>((T)G.eta.real(), (T)G.eta.imag()),
-                                                cx<T>((T)ie.real(), (T)ie.imag()), y, c->d_err);
+                                                cx<T>((T)ie.real(), (T)ie.imag()), y);
       };
       if (R == 1) rec(k_disaggregate<T, 1>, 1);
       else rec(k_disaggregate<T, 4>, 4);

@@ -16,40 +16,46 @@ namespace {
 typedef std::complex<double> cd;
 
 // Two-stage dot products h[i][r] = sum_n conj(V_i[r][n]) w[r][n], i < nvec.
-// Stage 1: block (blk, r) stages its chunk of w in shared memory and writes a
-// partial sum per vector; stage 2 sums the partials.  Every V_i is read once.
-__global__ void k_mdot_part(int n, int nrhs, int nvec, int nblk, const zd *__restrict__ V, size_t vstride,
-                            const zd *__restrict__ w, zd *__restrict__ part) {
-  __shared__ zd red[32][8];
-  const int blk = blockIdx.x, r = blockIdx.y;
-  const int chunk = (n + nblk - 1) / nblk;
-  const int t0 = blk * chunk, t1 = min(n, t0 + chunk);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // each thread keeps its (at most 4) elements of w in registers
-  zd wv[4];
-  int nv = 0;
-  for (int t = t0 + threadIdx.x; t < t1 && nv < 4; t += blockDim.x) wv[nv++] = w[(size_t)r * n + t];
-  for (int g0 = 0; g0 < nvec; g0 += 32) {
-    const int g1 = min(nvec, g0 + 32);
-    for (int i = g0; i < g1; ++i) {
-      const zd *a = V + (size_t)i * vstride + (size_t)r * n;
-      zd acc;
-      int q = 0;
-      for (int t = t0 + threadIdx.x; t < t1 && q < 4; t += blockDim.x, ++q) acc = cfma(conj(a[t]), wv[q], acc);
-      for (int d = 16; d > 0; d >>= 1) {
-        acc.re += __shfl_down_sync(0xffffffffu, acc.re, d);
-        acc.im += __shfl_down_sync(0xffffffffu, acc.im, d);
-      }
-      if (lane == 0) red[i - g0][warp] = acc;
+// Stage 1: one warp per (vector i, chunk of MD_CH elements, rhs r), lanes over
+// the chunk with many loads in flight, one partial per warp (no block-level
+// synchronisation); stage 2 adds the partials in chunk order.  With a gate,
+// right-hand sides whose gate is 0 get zero partials.
+constexpr int MD_CH = 1024;
+__global__ void __launch_bounds__(256) k_mdot_part(int n, int nrhs, int nvec, int nblk, const zd *__restrict__ V,
+                                                  size_t vstride, const zd *__restrict__ w, zd *__restrict__ part,
+                                                  const int *__restrict__ gate) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r = blockIdx.y;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (gw >= nvec * nblk) return;
+  const int i = gw / nblk, blk = gw - i * nblk;
+  zd acc;
+  if (!gate || gate[r]) {
+    const zd *a = V + (size_t)i * vstride + (size_t)r * n;
+    const zd *x = w + (size_t)r * n;
+    const int t1 = min(n, (blk + 1) * MD_CH);
+#pragma unroll 8
+    for (int t = blk * MD_CH + lane; t < t1; t += 32) acc = cfma(conj(a[t]), x[t], acc);
+    for (int d = 16; d > 0; d >>= 1) {
+      acc.re += __shfl_down_sync(0xffffffffu, acc.re, d);
+      acc.im += __shfl_down_sync(0xffffffffu, acc.im, d);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < g1 - g0; i += blockDim.x) {
-      zd acc;
-      for (int q = 0; q < 8; ++q) acc += red[i][q];
-      part[((size_t)(g0 + i) * nrhs + r) * nblk + blk] = acc;
-    }
-    __syncthreads();
   }
+  if (lane == 0) part[((size_t)i * nrhs + r) * nblk + blk] = acc;
+}
+
+// Selective second Gram-Schmidt pass (Daniel-Gragg-Kaufman-Stewart test):
+// after the first pass w' = w - V h, |w|^2 = |w'|^2 + |h|^2, and the pass is
+// repeated only when |w'| < |w| / sqrt(2), i.e. |w'|^2 < |h|^2.
+__global__ void k_reorth_gate(int nrhs, int nvec, const zd *__restrict__ h, const zd *__restrict__ nn1,
+                              int *__restrict__ gate) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  double hh = 0.0;
+  for (int i = 0; i < nvec; ++i) {
+    const zd v = h[(size_t)i * nrhs + r];
+    hh += v.re * v.re + v.im * v.im;
+  }
+  gate[r] = nn1[r].re < hh ? 1 : 0;
 }
 
 __global__ void k_mdot_sum(int nrhs, int nblk, const zd *__restrict__ part, zd *__restrict__ h) {
@@ -68,11 +74,12 @@ __global__ void k_mdot_sum(int nrhs, int nblk, const zd *__restrict__ part, zd *
 
 // w[r] -= sum_{i<=j} V_i[r] h[i][r]
 __global__ void k_orth(int n, int nrhs, int j1, const zd *__restrict__ V, size_t vstride, const zd *__restrict__ h,
-                       zd *__restrict__ w) {
+                       zd *__restrict__ w, const int *__restrict__ gate) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int r = blockIdx.y;
-  if (t >= n) return;
+  if (t >= n || (gate && !gate[r])) return;
   zd acc = w[(size_t)r * n + t];
+#pragma unroll 8
   for (int i = 0; i < j1; ++i) acc -= V[(size_t)i * vstride + (size_t)r * n + t] * h[(size_t)i * nrhs + r];
   w[(size_t)r * n + t] = acc;
 }
@@ -83,6 +90,18 @@ __global__ void k_scale(int n, const zd *__restrict__ a, const zd *__restrict__ 
   int r = blockIdx.y;
   if (t >= n) return;
   out[(size_t)r * n + t] = a[(size_t)r * n + t] * s[r];
+}
+
+// V_{j+1}[r] = w[r] / sqrt(nn[r]) where nn[r] = <w[r], w[r]>; zero for right-hand
+// sides that are finished (act[r] == 0) or whose new vector vanished
+__global__ void k_scale_norm(int n, const zd *__restrict__ a, const zd *__restrict__ nn, const zd *__restrict__ act,
+                             zd *__restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (t >= n) return;
+  const double q = nn[r].re;
+  const double s = (act[r].re != 0.0 && q > 0.0) ? 1.0 / sqrt(q) : 0.0;
+  out[(size_t)r * n + t] = a[(size_t)r * n + t] * s;
 }
 
 // out = a - b
@@ -98,6 +117,7 @@ __global__ void k_xupd(int n, int nrhs, int m, const zd *__restrict__ Z, size_t 
   int r = blockIdx.y;
   if (t >= n) return;
   zd acc = x[(size_t)r * n + t];
+#pragma unroll 8
   for (int j = 0; j < m; ++j) acc += Z[(size_t)j * zstride + (size_t)r * n + t] * y[(size_t)j * nrhs + r];
   x[(size_t)r * n + t] = acc;
 }
@@ -112,8 +132,8 @@ struct Gm {
     c->launches++;
   }
   // h[i][r] = <V_i[r], w[r]> for i < nvec
-  void mdot(const zd *V, size_t vstride, int nvec, const zd *w, zd *d_h) {
-    k_mdot_part<<<dim3(nblk, R), 256, 0, c->stream>>>(n, R, nvec, nblk, V, vstride, w, part);
+  void mdot(const zd *V, size_t vstride, int nvec, const zd *w, zd *d_h, const int *gate = nullptr) {
+    k_mdot_part<<<dim3((nvec * nblk + 7) / 8, R), 256, 0, c->stream>>>(n, R, nvec, nblk, V, vstride, w, part, gate);
     launch_check();
     k_mdot_sum<<<dim3(nvec, R), 256, 0, c->stream>>>(R, nblk, part, d_h);
     launch_check();
@@ -147,7 +167,7 @@ struct StepGraphs {
   }
   template <typename F>
   void run(sie_ctx *c, int j, F &&step) {
-    if (ok && !ex[j]) {
+    if (ok && !c->graphs_off && !ex[j]) {
       cudaStreamCaptureStatus cs;
       if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
           cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
@@ -174,7 +194,7 @@ struct StepGraphs {
         c->launches = l0;
       }
     }
-    if (ok && ex[j]) {
+    if (ok && !c->graphs_off && ex[j]) {
       SIE_CUDA(cudaGraphLaunch(ex[j], c->stream));
       c->launches += nk[j];
     } else {
@@ -227,9 +247,15 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
     c->gm_V = dev_alloc(c, (size_t)(m + 1) * vs * sizeof(zd));
     c->gm_Z = dev_alloc(c, (size_t)m * vs * sizeof(zd));
     c->gm_w = dev_alloc(c, vs * sizeof(zd));
-    c->gm_h = dev_alloc(c, (size_t)(m + 2) * R * sizeof(zd));
+    c->gm_h = dev_alloc(c, 3 * (size_t)(m + 2) * R * sizeof(zd));  // h (first pass), h (second pass), |w|^2
     c->gm_s = dev_alloc(c, (size_t)(m + 2) * R * sizeof(zd));
-    c->gm_part = dev_alloc(c, (size_t)(m + 2) * R * ((n + 1023) / 1024) * sizeof(zd));
+    c->gm_act = dev_alloc(c, (size_t)R * sizeof(zd));
+    if (c->gm_hpin) cudaFreeHost(c->gm_hpin);
+    c->gm_hpin = nullptr;
+    SIE_CUDA(cudaMallocHost(&c->gm_hpin, 3 * (size_t)(m + 2) * R * sizeof(zd)));
+    if (!c->gm_ev) SIE_CUDA(cudaEventCreateWithFlags(&c->gm_ev, cudaEventDisableTiming));
+    c->gm_part = dev_alloc(c, (size_t)(m + 2) * R * ((n + MD_CH - 1) / MD_CH) * sizeof(zd));
+    c->gm_gate = dev_alloc(c, (size_t)R * sizeof(int));
     c->gm_m = m;
     c->gm_R = R;
     c->work_gen++;
@@ -238,7 +264,7 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
   StepGraphs &SG = step_graphs(c, m, R, prec, precond);
   zd *d_h = (zd *)c->gm_h, *d_s = (zd *)c->gm_s;
   // 256 threads x 4 elements per block
-  Gm g{c, n, R, std::max(1, (n + 1023) / 1024), (zd *)c->gm_part};  // chunks of <= 1024 elements
+  Gm g{c, n, R, std::max(1, (n + MD_CH - 1) / MD_CH), (zd *)c->gm_part};  // chunks of MD_CH elements
   bool use_nn = precond == 2 && nn_ready(c);
   std::vector<double> prev_res(R, HUGE_VAL);
   std::vector<double> bn, rn;
@@ -292,12 +318,15 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
     k_scale<<<gv, 256, 0, c->stream>>>(n, w, d_s, V);
     g.launch_check();
     std::fill(gvec.begin(), gvec.end(), cd(0.0));
+    std::vector<zd> act(R);
     for (int r = 0; r < R; ++r) {
       gvec[(size_t)r * (m + 1)] = active[r] ? rn[r] : 0.0;
       if (active[r]) restarts[r]++;
+      act[r] = zd(active[r] ? 1.0 : 0.0, 0.0);
     }
-    int jend = 0;
-    for (int j = 0; j < m; ++j) {
+    SIE_CUDA(cudaMemcpyAsync(c->gm_act, act.data(), R * sizeof(zd), cudaMemcpyHostToDevice, c->stream));
+    // z_j = M^-1 v_j and w = A z_j, as one captured graph per step (eagerly while the learned part is on)
+    auto run_step = [&](int j) {
       zd *Vj = V + (size_t)j * vs, *Zj = Z + (size_t)j * vs;
       auto step = [&]() {
         if (precond >= 1) apply_ilu(c, Vj, Zj, R, prec);
@@ -305,30 +334,44 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
         if (use_nn) nn_apply(c, Vj, Zj, R);
         apply_matvec(c, Zj, w, R, prec, 3);
       };
-      if (use_nn) step();          // the learned part may be switched off mid-solve: run it eagerly
-      else SG.run(c, j, step);     // z_j = M^-1 v_j and w = A z_j as one captured graph per step
-      // classical Gram-Schmidt, twice
-      std::vector<zd> h1((size_t)(j + 1) * R), h2((size_t)(j + 1) * R);
-      for (int pass = 0; pass < 2; ++pass) {
-        g.mdot(V, vs, j + 1, w, d_h);
-        k_orth<<<gv, 256, 0, c->stream>>>(n, R, j + 1, V, vs, d_h, w);
-        g.launch_check();
-        SIE_CUDA(cudaMemcpyAsync(pass == 0 ? h1.data() : h2.data(), d_h, (size_t)(j + 1) * R * sizeof(zd),
-                                 cudaMemcpyDeviceToHost, c->stream));
-      }
-      std::vector<double> hn;
-      g.norms(w, d_h, hn);  // synchronises
+      if (use_nn) step();
+      else SG.run(c, j, step);
+    };
+    zd *dh1 = d_h, *dh2 = d_h + (size_t)(m + 2) * R, *dnn = d_h + 2 * (size_t)(m + 2) * R;
+    const zd *hp = (const zd *)c->gm_hpin;
+    int jend = 0;
+    run_step(0);
+    for (int j = 0; j < m; ++j) {
+      // classical Gram-Schmidt with a selective second pass, and the normalised
+      // next vector, all on the device
+      int *gate = (int *)c->gm_gate;
+      g.mdot(V, vs, j + 1, w, dh1);
+      k_orth<<<gv, 256, 0, c->stream>>>(n, R, j + 1, V, vs, dh1, w, nullptr);
+      g.launch_check();
+      g.mdot(w, 0, 1, w, dnn);
+      k_reorth_gate<<<(R + 127) / 128, 128, 0, c->stream>>>(R, j + 1, dh1, dnn, gate);
+      g.launch_check();
+      g.mdot(V, vs, j + 1, w, dh2, gate);
+      k_orth<<<gv, 256, 0, c->stream>>>(n, R, j + 1, V, vs, dh2, w, gate);
+      g.launch_check();
+      g.mdot(w, 0, 1, w, dnn);
+      k_scale_norm<<<gv, 256, 0, c->stream>>>(n, w, dnn, (const zd *)c->gm_act, V + (size_t)(j + 1) * vs);
+      g.launch_check();
+      SIE_CUDA(cudaMemcpyAsync(c->gm_hpin, d_h, 3 * (size_t)(m + 2) * R * sizeof(zd), cudaMemcpyDeviceToHost,
+                               c->stream));
+      SIE_CUDA(cudaEventRecord(c->gm_ev, c->stream));
+      // the next step goes to the GPU before the host looks at the Hessenberg column:
+      // if the cycle stops here, its result is simply not used
+      if (j + 1 < m) run_step(j + 1);
+      SIE_CUDA(cudaEventSynchronize(c->gm_ev));
       for (int r = 0; r < R; ++r) {
         cd *Hc = &H[((size_t)r * (m + 1)) * m];  // column-major per RHS: H[i + j (m+1)]
-        for (int i = 0; i <= j; ++i)
-          Hc[i + (size_t)j * (m + 1)] = cd(h1[(size_t)i * R + r].re + h2[(size_t)i * R + r].re,
-                                           h1[(size_t)i * R + r].im + h2[(size_t)i * R + r].im);
-        Hc[j + 1 + (size_t)j * (m + 1)] = hn[r];
-        sc[r] = (active[r] && hn[r] > 0) ? zd(1.0 / hn[r], 0.0) : zd();
+        for (int i = 0; i <= j; ++i) {
+          const zd a1 = hp[(size_t)i * R + r], a2 = hp[(size_t)(m + 2) * R + (size_t)i * R + r];
+          Hc[i + (size_t)j * (m + 1)] = cd(a1.re + a2.re, a1.im + a2.im);
+        }
+        Hc[j + 1 + (size_t)j * (m + 1)] = std::sqrt(std::max(0.0, hp[2 * (size_t)(m + 2) * R + r].re));
       }
-      SIE_CUDA(cudaMemcpyAsync(d_s, sc.data(), R * sizeof(zd), cudaMemcpyHostToDevice, c->stream));
-      k_scale<<<gv, 256, 0, c->stream>>>(n, w, d_s, V + (size_t)(j + 1) * vs);
-      g.launch_check();
       // Givens rotations per RHS
       bool all_done = true;
       for (int r = 0; r < R; ++r) {
@@ -413,10 +456,14 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
   op_permute_in(c, b_user, b, R);
   op_permute_in(c, x_user, x, R);
   sie_prec prec = o->prec == 1 ? SIE_PREC_MIXED : SIE_PREC_FP64;
+  struct Eager {  // eager steps for this call only, also when it throws
+    sie_ctx *c;
+    ~Eager() { c->graphs_off = false; }
+  } eager{c};
+  c->graphs_off = o->no_graphs != 0;
   sie_status rc = run_gmres_internal(c, b, x, R, o->restart, o->max_iters, o->tol, prec, o->precond, nullptr, st);
   op_permute_out(c, x, x_user, R);
   SIE_CUDA(cudaStreamSynchronize(c->stream));
-  check_device_errors(c);
   return rc;
 }
 

@@ -116,3 +116,21 @@ def test_batched_solve_equals_single_solves(case):
         sie.gmres_solve(s.ctx, b[r:r + 1].contiguous(), x1, 1, restart=50, max_iters=500, tol=1e-8,
                         prec=sie.SIE_PREC_FP64, precond=1)
         assert rel(xb[r], _host(x1)[0]) < 1e-6
+
+
+def test_eager_steps_equal_graph_steps(case):
+    """Krylov steps launched eagerly give the same iterations and currents as
+    the captured-graph steps (same kernels in the same order)."""
+    name, s, d = case
+    if name != "coated_r075":
+        pytest.skip("one case suffices")
+    b = torch.zeros((1, s.ne, 2), dtype=torch.complex128, device="cuda")
+    sie.sie_plane_wave_rhs(s.ctx, [[0.0, 0.0, 0.0, 1.0]], b)
+    out = []
+    for graphs in (True, False):
+        x = torch.zeros_like(b)
+        st = sie.gmres_solve(s.ctx, b, x, 1, restart=50, max_iters=1000, tol=1e-6, prec=sie.SIE_PREC_MIXED,
+                             precond=1, graphs=graphs)
+        out.append((st[0]["iters"], _host(x)))
+    assert out[0][0] == out[1][0]
+    assert rel(out[0][1], out[1][1]) < 1e-12
