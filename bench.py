@@ -35,6 +35,9 @@ DIGITS = 3.0
 TOL = 1e-4
 RESTART = 50
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) of one k_near_spmv<float> launch on this workload, from one
+# ncu capture (profiles/near_spmv_coated_c2.md); valid while that kernel is unchanged
+NEAR_SPMV_TRAFFIC_BYTES = 508350208 + 500992
 
 
 def measured_peaks():
@@ -307,7 +310,8 @@ def main():
     ach = near_bytes_fp32 / (stages["near_spmv"]["fp32_ms"] * 1e-3) / 1e9
     roofline = {"kernel": "k_near_spmv<float> (near-field 2x2 block-sparse product)", "bound": "hbm",
                 "achieved": ach, "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "algorithmic_bytes_per_launch": near_bytes_fp32,
+                "traffic": NEAR_SPMV_TRAFFIC_BYTES if WORKLOAD == "coated_c2" else None,
+                "algorithmic_bytes_per_launch": near_bytes_fp32,
                 "fp64_achieved": near_bytes_fp64 / (stages["near_spmv"]["fp64_ms"] * 1e-3) / 1e9}
     pat_bytes = sie.sie_query(s.ctx, 6)
     mv_bytes32 = near_bytes_fp32 + pat_bytes // 2
@@ -323,7 +327,8 @@ def main():
     line = {
         "metric": METRIC, "value": ms / 1e3 * 1.0, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64 (FP32 complex operator) + c128 Arnoldi", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32",
+        "precision": "FP32 complex operator, ILU(0) and RCS; FP64 Arnoldi, Givens and true residual", "data": "synthetic",
         "config": {"workload": WORKLOAD, "unknowns": 2 * ne, "levels": LEVELS, "digits": DIGITS, "tol": TOL,
                    "restart": RESTART, "nrhs_per_gpu": 1, "parallelism": f"replicas{ws}",
                    "l2": f"operator data {(near_bytes_fp32 + pat_bytes // 2) / 1e6:.0f} MB > 129 MB L2 (no flush)"},
