@@ -114,6 +114,13 @@ struct IluHost {
   int *d_lo_ptr = nullptr, *d_lo_col = nullptr, *d_up_ptr = nullptr, *d_up_col = nullptr;
   // per row, [9] starts of each column colour's blocks within its off-box range (the 9th = end)
   int *d_lo_cptr = nullptr, *d_up_cptr = nullptr;
+  // single-RHS sweep steps (forward colours 0..7, backward 6..0): pieces of the
+  // boxes' off-box work, 5 ints each (box, v0, v1, index in box, pieces of box);
+  // step s uses pieces [piece_ptr[s], piece_ptr[s+1])
+  std::vector<int> piece_ptr;
+  int *d_pieces = nullptr;
+  int *d_piece_count = nullptr;     // per box arrival counter (self-resetting)
+  void *d_piece_scratch = nullptr;  // per piece row partials [piece][2 max_box] complex (FP64 size)
   void *d_lo64 = nullptr, *d_lo32 = nullptr, *d_up64 = nullptr, *d_up32 = nullptr;  // off-box blocks [.][4]
   // in-box inverses packed by rows, per box: strictly lower part of L_bb^{-1}
   // (its diagonal blocks are identities; row i holds blocks j < i) and the

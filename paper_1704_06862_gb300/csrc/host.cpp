@@ -892,8 +892,42 @@ static void build_ilu(sie_ctx *c) {
       }
       return cp;
     };
-    I.d_lo_cptr = dev_upload(c, colour_ptrs(lo_ptr, lo_col));
-    I.d_up_cptr = dev_upload(c, colour_ptrs(up_ptr, up_col));
+    const std::vector<int> lcp = colour_ptrs(lo_ptr, lo_col), ucp = colour_ptrs(up_ptr, up_col);
+    I.d_lo_cptr = dev_upload(c, lcp);
+    I.d_up_cptr = dev_upload(c, ucp);
+    // pieces of the single-RHS sweep steps: step s < 8 is forward colour s
+    // (source colour s - 1), step s >= 8 backward colour 14 - s (source 15 - s)
+    const int PIECE = 1024;  // ILU_PIECE of the sweep kernel
+    std::vector<int> pieces, pptr(1, 0);
+    size_t maxp = 0;
+    for (int step = 0; step < 15; ++step) {
+      const bool fwd = step < 8;
+      const int colr = fwd ? step : 14 - step, sc = fwd ? colr - 1 : colr + 1;
+      const std::vector<int> &cp = fwd ? lcp : ucp;
+      size_t here = 0;
+      for (int bx = cptr[colr]; bx < cptr[colr + 1]; ++bx) {
+        long total = 0;
+        if (sc >= 0 && sc < 8)
+          for (int i = c->leaf_start[bx]; i < c->leaf_start[bx + 1]; ++i)
+            total += cp[9 * (size_t)i + sc + 1] - cp[9 * (size_t)i + sc];
+        const int npc = (int)std::max<long>(1, (total + PIECE - 1) / PIECE);
+        for (int k = 0; k < npc; ++k) {
+          pieces.push_back(bx);
+          pieces.push_back((int)(total * k / npc));
+          pieces.push_back((int)(total * (k + 1) / npc));
+          pieces.push_back(k);
+          pieces.push_back(npc);
+        }
+        here += npc;
+      }
+      maxp = std::max(maxp, here);
+      pptr.push_back((int)(pieces.size() / 5));
+    }
+    I.piece_ptr = pptr;
+    I.d_pieces = dev_upload(c, pieces);
+    I.d_piece_count = (int *)dev_alloc(c, (size_t)nlb * sizeof(int));
+    SIE_CUDA(cudaMemset(I.d_piece_count, 0, (size_t)nlb * sizeof(int)));
+    I.d_piece_scratch = dev_alloc(c, std::max<size_t>(1, maxp) * 2 * std::max(1, maxb) * sizeof(cd));
   }
   I.d_up_col = dev_upload(c, up_col);
   I.d_lo64 = dev_upload(c, lo_val);

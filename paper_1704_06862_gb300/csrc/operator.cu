@@ -51,6 +51,15 @@ __device__ __forceinline__ cx<T> shfl_down(cx<T> v, int d) {
 }
 // the two unknowns (J, M) of one edge through the read-only path; p is 16-byte
 // aligned (vectors start on 256-byte boundaries, an edge's pair is 2 complex)
+// a value written by another CTA of the same launch: read through L2, not L1
+__device__ __forceinline__ cx<float> ldcg_cx(const cx<float> *p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+  return cx<float>(v.x, v.y);
+}
+__device__ __forceinline__ cx<double> ldcg_cx(const cx<double> *p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+  return cx<double>(v.x, v.y);
+}
 __device__ __forceinline__ void ldg_pair(const cx<float> *p, cx<float> &x0, cx<float> &x1) {
   float4 v = __ldg(reinterpret_cast<const float4 *>(p));
   x0 = cx<float>(v.x, v.y);
@@ -697,21 +706,30 @@ __device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
 // Single right-hand side: the off-box products are pushed one source colour
 // at a time, so that each launch has the whole GPU's worth of short rows.
 // Sweep step for colour c with source colour sc (forward: c-1, backward: c+1):
-//   role A, one CTA per box B of colour c:
+//   role A, the boxes B of colour c (one CTA per piece, below):
 //       t_B = w_B - F_{B,sc} z_sc,   z_B = L_BB^{-1} t_B   (U_BB^{-1} backward);
 //       the last forward step also applies U_BB^{-1} (colour 7 has no later colour);
 //   role B, one warp per row i of the colours still to come:
 //       w_i -= F_{i,sc} z_sc   (the first forward step copies w = src).
 // w lives in z until the row is solved.  Each row's off-box blocks are sorted
 // by column, hence grouped by colour; cptr[i][c] .. cptr[i][c+1] is colour c.
-// In role A the box's blocks from sc are spread evenly over the CTA in groups
-// of 32 (one per lane); a segmented scan over the lanes keyed by row adds each
-// row's products, every warp keeps its own row partials, and the warps'
-// partials are added in warp order, so the result is deterministic.  The
-// packed in-box inverse is copied to shared memory asynchronously meanwhile.
+// In role A the box's blocks from sc (its "virtual range") are cut into
+// pieces of at most ILU_PIECE blocks, one CTA per piece, so that a large box
+// does not hold up the launch.  Within a piece the blocks are spread evenly over the CTA in
+// groups of 32 (one per lane); a segmented scan over the lanes keyed by row
+// adds each row's products, every warp keeps its own row partials, and the
+// warps' partials are added in warp order.  A box of one piece finishes in its
+// CTA, with its packed in-box inverse copied to shared memory asynchronously
+// meanwhile.  A box of several pieces: each piece writes its row partials to
+// scratch and counts itself in; the last to arrive adds the pieces' partials
+// in piece order and finishes the box.  The results are deterministic.
+constexpr int ILU_PIECE = 1024;
+
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int colour, int nboxA, int box0, int rb0,
-                                                  int rb1, int stage_tri, const int *__restrict__ box_start,
+__global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int colour, int npieceA,
+                                                  const int *__restrict__ pieces, int rb0, int rb1, int stage_tri,
+                                                  int nmax, cx<T> *scratch, int *counter,
+                                                  const int *__restrict__ box_start,
                                                   const int *__restrict__ cptr, const int *__restrict__ off_col,
                                                   const cx<T> *__restrict__ off_val,
                                                   const int64_t *__restrict__ tri_off, const cx<T> *__restrict__ tri,
@@ -727,9 +745,9 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
   const bool has_src = sc >= 0 && sc < 8;
   // w of rows not yet solved: src before the first forward step has run
   const cx<T> *w = (forward && colour == 0) ? src : z;
-  if ((int)blockIdx.x >= nboxA) {
+  if ((int)blockIdx.x >= npieceA) {
     // ---- role B: rows of later colours take the contribution of colour sc
-    const int i = rb0 + ((int)blockIdx.x - nboxA) * NW + warp;
+    const int i = rb0 + ((int)blockIdx.x - npieceA) * NW + warp;
     if (i >= rb1) return;
     if (!has_src) {
       if (lane < 2) z[2 * (size_t)i + lane] = src[2 * (size_t)i + lane];
@@ -775,11 +793,13 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
     }
     return;
   }
-  // ---- role A: one box of this colour
-  const int b = box0 + blockIdx.x;
+  // ---- role A: one piece of a box of this colour
+  const int *pc = pieces + 5 * (size_t)blockIdx.x;
+  const int b = pc[0], v0 = pc[1], v1 = pc[2], kp = pc[3], np = pc[4];
   const int s0 = box_start[b], n = box_start[b + 1] - s0;
   const int ntri = forward ? n * (n - 1) / 2 : n * (n + 1) / 2;
   const cx<T> *Mg = tri + 4 * tri_off[b];
+  stage_tri = stage_tri && np == 1;  // only a box that finishes in this CTA prefetches its inverse
   // shared: [packed triangle (if staged)] [NW][n][2] partials, [2n] t, [2n] t2, [n+1] prefix, [n] starts
   cx<T> *Ms = reinterpret_cast<cx<T> *>(smem_raw);
   cx<T> *part = Ms + (stage_tri ? 4 * (size_t)ntri : 0);
@@ -818,8 +838,8 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
     if (lane == 0) pre[n] = carry;
   }
   __syncthreads();
-  const int total = pre[n];
-  const int ng = (total + 31) >> 5;
+  const int total = v1;  // this piece: virtual indices [v0, v1) of the box's blocks from sc
+  const int ng = (v1 - v0 + 31) >> 5;
   const int g0 = (int)((int64_t)warp * ng / NW), g1 = (int)((int64_t)(warp + 1) * ng / NW);
   cx<T> *pw = part + (size_t)warp * 2 * n;
   // virtual index v of the box's blocks -> row (last row whose prefix is <= v) and block index
@@ -852,7 +872,7 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
   };
   for (int g = g0; g < g1; g += 2) {
     // two groups in flight: issue both groups' loads, then reduce
-    const int vA = g * 32 + lane, vB = vA + 32;
+    const int vA = v0 + g * 32 + lane, vB = vA + 32;
     const bool hasB = g + 1 < g1;
     int rA = -1, rB = -1, qA = 0, qB = 0, cA = 0, cB = 0;
     V16 uA[NV], uB[NV];
@@ -887,14 +907,46 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
     if (hasB) segsum(rB, b0, b1);
   }
   __syncthreads();
-  for (int li = threadIdx.x; li < n; li += NT) {
-    cx<T> u0 = w[2 * (size_t)(s0 + li)], u1 = w[2 * (size_t)(s0 + li) + 1];
-    for (int ww = 0; ww < NW; ++ww) {
-      u0 -= part[(size_t)ww * 2 * n + 2 * li];
-      u1 -= part[(size_t)ww * 2 * n + 2 * li + 1];
+  if (np == 1) {
+    for (int li = threadIdx.x; li < n; li += NT) {
+      cx<T> u0 = w[2 * (size_t)(s0 + li)], u1 = w[2 * (size_t)(s0 + li) + 1];
+      for (int ww = 0; ww < NW; ++ww) {
+        u0 -= part[(size_t)ww * 2 * n + 2 * li];
+        u1 -= part[(size_t)ww * 2 * n + 2 * li + 1];
+      }
+      t[2 * li] = u0;
+      t[2 * li + 1] = u1;
     }
-    t[2 * li] = u0;
-    t[2 * li + 1] = u1;
+  } else {
+    cx<T> *mine = scratch + (size_t)blockIdx.x * 2 * nmax;
+    for (int li = threadIdx.x; li < n; li += NT) {
+      cx<T> u0, u1;
+      for (int ww = 0; ww < NW; ++ww) {
+        u0 += part[(size_t)ww * 2 * n + 2 * li];
+        u1 += part[(size_t)ww * 2 * n + 2 * li + 1];
+      }
+      mine[2 * li] = u0;
+      mine[2 * li + 1] = u1;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int s_last;
+    if (threadIdx.x == 0) s_last = atomicAdd(&counter[b], 1) == np - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) counter[b] = 0;  // ready for the next launch
+    const cx<T> *first = scratch + (size_t)(blockIdx.x - kp) * 2 * nmax;
+    for (int li = threadIdx.x; li < n; li += NT) {
+      cx<T> u0 = w[2 * (size_t)(s0 + li)], u1 = w[2 * (size_t)(s0 + li) + 1];
+      for (int k = 0; k < np; ++k) {
+        const cx<T> *pk = first + (size_t)k * 2 * nmax + 2 * li;
+        u0 -= ldcg_cx(pk);
+        u1 -= ldcg_cx(pk + 1);
+      }
+      t[2 * li] = u0;
+      t[2 * li + 1] = u1;
+    }
   }
   if (stage_tri) cp_async_wait_all();
   __syncthreads();
@@ -1195,13 +1247,14 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
     for (int step = 0; step < 15; ++step) {
       const bool fwd = step < 8;
       const int colr = fwd ? step : 14 - step;
-      const int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
+      const int np = I.piece_ptr[step + 1] - I.piece_ptr[step];
       const int rb0 = fwd ? rows_from(colr + 1) : 0, rb1 = fwd ? c->ne : rows_from(colr);
       const int nrowB = rb1 - rb0;
-      const int grid = cnt + (nrowB + NW - 1) / NW;
+      const int grid = np + (nrowB + NW - 1) / NW;
       if (grid == 0) continue;
       k_ilu_sweep<T, NT><<<grid, NT, smem, c->stream>>>(
-          fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, cnt, first, rb0, rb1, stage, I.d_box_start,
+          fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, np, I.d_pieces + 5 * (size_t)I.piece_ptr[step], rb0, rb1, stage, mb,
+          (cx<T> *)I.d_piece_scratch, I.d_piece_count, I.d_box_start,
           fwd ? I.d_lo_cptr : I.d_up_cptr, fwd ? I.d_lo_col : I.d_up_col,
           (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? I.d_tl_off : I.d_tu_off,
           (const cx<T> *)(fwd ? tsel<T>::tl(I) : tsel<T>::tu(I)), I.d_tu_off, (const cx<T> *)tsel<T>::tu(I), r, z);
