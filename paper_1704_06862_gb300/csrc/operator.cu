@@ -709,7 +709,7 @@ __device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
 //   role A, the boxes B of colour c (one CTA per piece, below):
 //       t_B = w_B - F_{B,sc} z_sc,   z_B = L_BB^{-1} t_B   (U_BB^{-1} backward);
 //       the last forward step also applies U_BB^{-1} (colour 7 has no later colour);
-//   role B, one warp per row i of the colours still to come:
+//   role B, half a warp per row i of the colours still to come:
 //       w_i -= F_{i,sc} z_sc   (the first forward step copies w = src).
 // w lives in z until the row is solved.  Each row's off-box blocks are sorted
 // by column, hence grouped by colour; cptr[i][c] .. cptr[i][c+1] is colour c.
@@ -746,24 +746,29 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
   // w of rows not yet solved: src before the first forward step has run
   const cx<T> *w = (forward && colour == 0) ? src : z;
   if ((int)blockIdx.x >= npieceA) {
-    // ---- role B: rows of later colours take the contribution of colour sc
-    const int i = rb0 + ((int)blockIdx.x - npieceA) * NW + warp;
-    if (i >= rb1) return;
+    // ---- role B: rows of later colours take the contribution of colour sc;
+    // half a warp per row (rows hold about 40 blocks per source colour)
+    const int hl = lane & 15;
+    const int i = rb0 + ((int)blockIdx.x - npieceA) * 2 * NW + 2 * warp + (lane >> 4);
+    const bool row_ok = i < rb1;
     if (!has_src) {
-      if (lane < 2) z[2 * (size_t)i + lane] = src[2 * (size_t)i + lane];
+      if (row_ok && hl < 2) z[2 * (size_t)i + hl] = src[2 * (size_t)i + hl];
       return;
     }
-    const int q0 = cptr[9 * (size_t)i + sc], q1 = cptr[9 * (size_t)i + sc + 1];
-    if (q0 == q1) return;
+    int q0 = 0, q1 = 0;
+    if (row_ok) {
+      q0 = cptr[9 * (size_t)i + sc];
+      q1 = cptr[9 * (size_t)i + sc + 1];
+    }
     cx<T> a0, a1;
-    int q = q0 + lane;
-    for (; q + 32 < q1; q += 64) {
-      const int c0 = __ldg(off_col + q), c1 = __ldg(off_col + q + 32);
+    int q = q0 + hl;
+    for (; q + 16 < q1; q += 32) {
+      const int c0 = __ldg(off_col + q), c1 = __ldg(off_col + q + 16);
       V16 u0[NV], u1[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         u0[v] = __ldg(Ov + (size_t)q * NV + v);
-        u1[v] = __ldg(Ov + (size_t)(q + 32) * NV + v);
+        u1[v] = __ldg(Ov + (size_t)(q + 16) * NV + v);
       }
       cx<T> x0, x1, y0, y1;
       ldg_pair(z + 2 * (size_t)c0, x0, x1);  // colour sc: not written by this launch
@@ -785,9 +790,12 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
       a0 = cfma(b0[0], x0, cfma(b0[1], x1, a0));
       a1 = cfma(b0[2], x0, cfma(b0[3], x1, a1));
     }
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    if (lane == 0) {
+#pragma unroll
+    for (int d = 8; d > 0; d >>= 1) {  // within the half warp
+      a0 += shfl_down(a0, d);
+      a1 += shfl_down(a1, d);
+    }
+    if (row_ok && hl == 0 && q1 > q0) {
       z[2 * (size_t)i] -= a0;
       z[2 * (size_t)i + 1] -= a1;
     }
@@ -1250,7 +1258,7 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
       const int np = I.piece_ptr[step + 1] - I.piece_ptr[step];
       const int rb0 = fwd ? rows_from(colr + 1) : 0, rb1 = fwd ? c->ne : rows_from(colr);
       const int nrowB = rb1 - rb0;
-      const int grid = np + (nrowB + NW - 1) / NW;
+      const int grid = np + (nrowB + 2 * NW - 1) / (2 * NW);
       if (grid == 0) continue;
       k_ilu_sweep<T, NT><<<grid, NT, smem, c->stream>>>(
           fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, np, I.d_pieces + 5 * (size_t)I.piece_ptr[step], rb0, rb1, stage, mb,
