@@ -709,7 +709,7 @@ __device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
 //   role A, the boxes B of colour c (one CTA per piece, below):
 //       t_B = w_B - F_{B,sc} z_sc,   z_B = L_BB^{-1} t_B   (U_BB^{-1} backward);
 //       the last forward step also applies U_BB^{-1} (colour 7 has no later colour);
-//   role B, half a warp per row i of the colours still to come:
+//   role B, ILU_RL lanes per row i of the colours still to come:
 //       w_i -= F_{i,sc} z_sc   (the first forward step copies w = src).
 // w lives in z until the row is solved.  Each row's off-box blocks are sorted
 // by column, hence grouped by colour; cptr[i][c] .. cptr[i][c+1] is colour c.
@@ -724,6 +724,7 @@ __device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
 // scratch and counts itself in; the last to arrive adds the pieces' partials
 // in piece order and finishes the box.  The results are deterministic.
 constexpr int ILU_PIECE = 1024;
+constexpr int ILU_RL = 8;  // lanes per pushed row
 
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int colour, int npieceA,
@@ -747,9 +748,9 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
   const cx<T> *w = (forward && colour == 0) ? src : z;
   if ((int)blockIdx.x >= npieceA) {
     // ---- role B: rows of later colours take the contribution of colour sc;
-    // half a warp per row (rows hold about 40 blocks per source colour)
-    const int hl = lane & 15;
-    const int i = rb0 + ((int)blockIdx.x - npieceA) * 2 * NW + 2 * warp + (lane >> 4);
+    // ILU_RL lanes per row (rows hold about 40 blocks per source colour)
+    const int hl = lane & (ILU_RL - 1);
+    const int i = rb0 + ((int)blockIdx.x - npieceA) * (32 / ILU_RL) * NW + (32 / ILU_RL) * warp + lane / ILU_RL;
     const bool row_ok = i < rb1;
     if (!has_src) {
       if (row_ok && hl < 2) z[2 * (size_t)i + hl] = src[2 * (size_t)i + hl];
@@ -762,13 +763,13 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
     }
     cx<T> a0, a1;
     int q = q0 + hl;
-    for (; q + 16 < q1; q += 32) {
-      const int c0 = __ldg(off_col + q), c1 = __ldg(off_col + q + 16);
+    for (; q + ILU_RL < q1; q += 2 * ILU_RL) {
+      const int c0 = __ldg(off_col + q), c1 = __ldg(off_col + q + ILU_RL);
       V16 u0[NV], u1[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         u0[v] = __ldg(Ov + (size_t)q * NV + v);
-        u1[v] = __ldg(Ov + (size_t)(q + 16) * NV + v);
+        u1[v] = __ldg(Ov + (size_t)(q + ILU_RL) * NV + v);
       }
       cx<T> x0, x1, y0, y1;
       ldg_pair(z + 2 * (size_t)c0, x0, x1);  // colour sc: not written by this launch
@@ -791,7 +792,7 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
       a1 = cfma(b0[2], x0, cfma(b0[3], x1, a1));
     }
 #pragma unroll
-    for (int d = 8; d > 0; d >>= 1) {  // within the half warp
+    for (int d = ILU_RL / 2; d > 0; d >>= 1) {  // within the row's lanes
       a0 += shfl_down(a0, d);
       a1 += shfl_down(a1, d);
     }
@@ -1258,7 +1259,7 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
       const int np = I.piece_ptr[step + 1] - I.piece_ptr[step];
       const int rb0 = fwd ? rows_from(colr + 1) : 0, rb1 = fwd ? c->ne : rows_from(colr);
       const int nrowB = rb1 - rb0;
-      const int grid = np + (nrowB + 2 * NW - 1) / (2 * NW);
+      const int grid = np + (nrowB + (32 / ILU_RL) * NW - 1) / ((32 / ILU_RL) * NW);
       if (grid == 0) continue;
       k_ilu_sweep<T, NT><<<grid, NT, smem, c->stream>>>(
           fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, np, I.d_pieces + 5 * (size_t)I.piece_ptr[step], rb0, rb1, stage, mb,
