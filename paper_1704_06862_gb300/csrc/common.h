@@ -83,6 +83,11 @@ struct LevelHost {
   void *d_up64 = nullptr, *d_up32 = nullptr;     // [8][K] shift, child -> this (parent) level
   void *d_dn64 = nullptr, *d_dn32 = nullptr;     // [8][K] shift, this level -> child
   int *d_il_ptr = nullptr, *d_il_src = nullptr, *d_il_slot = nullptr;
+  // sibling groups (the children of one box of the level above) for the M2L:
+  // per group up to 8 member boxes and the union of their interaction lists,
+  // one entry per source: (source box, member mask, translator slot per member)
+  int ngroups = 0, max_group_entries = 0;
+  int *d_grp_ptr = nullptr, *d_grp_box = nullptr, *d_grp_ent = nullptr;
   int *d_ch_ptr = nullptr, *d_ch_idx = nullptr, *d_oct = nullptr, *d_parent = nullptr;
   // work buffers (capacity nrhs_cap): S and I [nbox][2][2][K][R]
   void *d_S = nullptr, *d_I = nullptr;

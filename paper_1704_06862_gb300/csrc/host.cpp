@@ -2,6 +2,7 @@
 // pattern and preconditioner ordering, MLFMM tables, ILU(0) factorisation,
 // and the extern "C" entry points declared in sie.h.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -605,6 +606,46 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
       B.d_il_ptr = dev_upload(c, B.il_ptr);
       B.d_il_src = dev_upload(c, B.il_src);
       B.d_il_slot = dev_upload(c, B.il_slot);
+      {
+        // sibling groups: the union of the members' interaction lists, per source
+        // the members that take it and their translator slots
+        LevelHost &Pg = R.lev[lv - 1];
+        std::vector<int> gptr(1, 0), gbox, gent;
+        for (int pb = 0; pb < Pg.nbox; ++pb) {
+          const int m = Pg.ch_ptr[pb + 1] - Pg.ch_ptr[pb];
+          if (m == 0) continue;
+          SIE_REQUIRE(m <= 8, SIE_EINVAL, "octree: more than 8 children");
+          std::map<int, std::array<int, 8>> ent;
+          for (int u = 0; u < 8; ++u) gbox.push_back(u < m ? Pg.ch_idx[Pg.ch_ptr[pb] + u] : -1);
+          for (int u = 0; u < m; ++u) {
+            const int b = Pg.ch_idx[Pg.ch_ptr[pb] + u];
+            for (int e = B.il_ptr[b]; e < B.il_ptr[b + 1]; ++e) {
+              auto it = ent.find(B.il_src[e]);
+              if (it == ent.end()) {
+                std::array<int, 8> a;
+                a.fill(-1);
+                it = ent.emplace(B.il_src[e], a).first;
+              }
+              it->second[u] = B.il_slot[e];
+            }
+          }
+          for (auto &kv : ent) {
+            int mask = 0;
+            for (int u = 0; u < 8; ++u)
+              if (kv.second[u] >= 0) mask |= 1 << u;
+            gent.push_back(kv.first);
+            gent.push_back(mask);
+            for (int u = 0; u < 8; ++u) gent.push_back(std::max(0, kv.second[u]));
+          }
+          gptr.push_back((int)(gent.size() / 10));
+        }
+        B.ngroups = (int)gptr.size() - 1;
+        B.max_group_entries = 0;
+        for (int q = 0; q < B.ngroups; ++q) B.max_group_entries = std::max(B.max_group_entries, gptr[q + 1] - gptr[q]);
+        B.d_grp_ptr = dev_upload(c, gptr);
+        B.d_grp_box = dev_upload(c, gbox);
+        B.d_grp_ent = dev_upload(c, gent.empty() ? std::vector<int>(10, 0) : gent);
+      }
       // shifts between this level (parent) and its children
       if (lv < leaf) {
         std::vector<cd> up(8 * K), dn(8 * K);

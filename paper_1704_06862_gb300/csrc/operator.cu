@@ -596,6 +596,56 @@ __global__ void k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr,
   }
 }
 
+// Diagonal M2L by sibling groups: the children of one box share most of their
+// interaction lists, so one CTA takes a group (up to 8 targets) for a chunk of
+// directions, thread k.  For each source of the union (entries staged in shared
+// memory) the four S components are read once and applied to every member
+// that has the source in its list, with that member's translator:
+//   I_u(k) = sum_{sources s of u} T_{u-s}(k) S_s(k).
+// Per source and direction: 4 pattern loads plus one translator load per
+// member, instead of 4 + 1 per member and source.
+template <typename T>
+__global__ void __launch_bounds__(128) k_m2l_group(int K, int nrhs, const int *__restrict__ grp_ptr,
+                                                  const int *__restrict__ grp_box, const int *__restrict__ grp_ent,
+                                                  const cx<T> *__restrict__ Tr, const cx<T> *__restrict__ S,
+                                                  cx<T> *__restrict__ I) {
+  extern __shared__ __align__(16) int ents[];  // [n][10]
+  const int g = blockIdx.y, r = blockIdx.z;
+  const int e0 = grp_ptr[g], ne = grp_ptr[g + 1] - e0;
+  for (int i = threadIdx.x; i < ne * 10; i += blockDim.x) ents[i] = grp_ent[(size_t)e0 * 10 + i];
+  __syncthreads();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const size_t cs = (size_t)nrhs * K;
+  cx<T> acc[8][4];
+#pragma unroll 2
+  for (int e = 0; e < ne; ++e) {
+    const int *E = ents + 10 * e;
+    const int src = E[0], mask = E[1];
+    const cx<T> *sp = S + ((size_t)src * 4 * nrhs + r) * K + k;
+    const cx<T> s0 = sp[0], s1 = sp[cs], s2 = sp[2 * cs], s3 = sp[3 * cs];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (mask & (1 << u)) {
+        const cx<T> t = Tr[(size_t)E[2 + u] * K + k];
+        acc[u][0] = cfma(t, s0, acc[u][0]);
+        acc[u][1] = cfma(t, s1, acc[u][1]);
+        acc[u][2] = cfma(t, s2, acc[u][2]);
+        acc[u][3] = cfma(t, s3, acc[u][3]);
+      }
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int b = grp_box[8 * (size_t)g + u];
+    if (b < 0) continue;
+    cx<T> *o = I + ((size_t)b * 4 * nrhs + r) * K + k;
+    o[0] = acc[u][0];
+    o[cs] = acc[u][1];
+    o[2 * cs] = acc[u][2];
+    o[3 * cs] = acc[u][3];
+  }
+}
+
 // Leaf receive with the JMCFIE weights of medium l (weights and constants
 // folded into the translators).  Per box the combined fields
 //   F1 = I^J - khat x I^M / eta,   F3 = -eta khat x I^J - I^M,
@@ -1192,12 +1242,23 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       SIE_CHECK_LAUNCH();
       c->launches += 2;
     }
-    // translations at every level
+    // translations at every level: per target box for few right-hand sides (more
+    // CTAs in flight), by sibling groups for blocks of 8 or more (fewer loads)
     for (int lv = 2; lv <= leaf; ++lv) {
       LevelHost &B = G.lev[lv];
-      dim3 grid((B.K + 127) / 128, B.nbox);
-      k_m2l<T><<<grid, 128, 0, c->stream>>>(B.nbox, B.K, R, B.d_il_ptr, B.d_il_src, B.d_il_slot,
-                                            (const cx<T> *)tsel<T>::Tr(B), (const cx<T> *)B.d_S, (cx<T> *)B.d_I);
+      if (R >= 8 && B.ngroups > 0) {
+        SIE_REQUIRE(B.ngroups <= 65535 && R <= 65535, SIE_EINVAL, "MLFMM: too many sibling groups for one launch");
+        dim3 grid((B.K + 127) / 128, B.ngroups, R);
+        const size_t smem = (size_t)B.max_group_entries * 10 * sizeof(int);
+        set_smem(k_m2l_group<T>, smem);
+        k_m2l_group<T><<<grid, 128, smem, c->stream>>>(B.K, R, B.d_grp_ptr, B.d_grp_box, B.d_grp_ent,
+                                                       (const cx<T> *)tsel<T>::Tr(B), (const cx<T> *)B.d_S,
+                                                       (cx<T> *)B.d_I);
+      } else {
+        dim3 grid((B.K + 127) / 128, B.nbox);
+        k_m2l<T><<<grid, 128, 0, c->stream>>>(B.nbox, B.K, R, B.d_il_ptr, B.d_il_src, B.d_il_slot,
+                                              (const cx<T> *)tsel<T>::Tr(B), (const cx<T> *)B.d_S, (cx<T> *)B.d_I);
+      }
       SIE_CHECK_LAUNCH();
       c->launches++;
     }

@@ -134,3 +134,22 @@ def test_eager_steps_equal_graph_steps(case):
         out.append((st[0]["iters"], _host(x)))
     assert out[0][0] == out[1][0]
     assert rel(out[0][1], out[1][1]) < 1e-12
+
+
+def test_block_product_equals_single_products(case):
+    """A block of 9 right-hand sides (the translations then run by sibling
+    groups) gives the products of the right-hand sides one at a time (per
+    target box), in both precisions."""
+    name, s, d = case
+    if name != "coated_r075":
+        pytest.skip("one case suffices")
+    x = np.concatenate([d["x"]] * 5)[:9] * np.arange(1, 10)[:, None]
+    xb = _dev(x, s.ne)
+    for prec, tol in ((sie.SIE_PREC_FP64, 1e-12), (sie.SIE_PREC_MIXED, 1e-5)):
+        yb = torch.zeros_like(xb)
+        sie.mlfmm_matvec(s.ctx, xb, yb, 9, prec)
+        yb = _host(yb)
+        for r in (0, 4, 8):
+            y1 = torch.zeros_like(xb[r:r + 1])
+            sie.mlfmm_matvec(s.ctx, xb[r:r + 1].contiguous(), y1, 1, prec)
+            assert rel(yb[r], _host(y1)[0]) < tol
