@@ -37,7 +37,7 @@ RESTART = 50
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one k_near_spmv<float> launch on this workload, from one
 # ncu capture (profiles/near_spmv_coated_c2.md); valid while that kernel is unchanged
-NEAR_SPMV_TRAFFIC_BYTES = 508350208 + 500992
+NEAR_SPMV_TRAFFIC_BYTES = 508421888 + 521984
 
 
 def measured_peaks():
