@@ -1230,7 +1230,11 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       dim3 grid(C.nbox, R);
       auto args = [&](auto kern) {
         set_smem(kern, smem);
-        kern<<<grid, 256, smem, c->stream>>>(C.K, C.L, P.K, P.L, R, C.d_oct, (const T *)tsel<T>::tp(C),
+        // threads sized to the larger task list (phi step: theta rows x column pairs;
+        // theta step: row pairs x column pairs), so small levels fit more CTAs per SM
+        const int tasks = std::max(nthc * (P.L + 1), (nthp + 1) / 2 * (P.L + 1));
+        const int threads = std::min(256, std::max(64, (tasks + 31) / 32 * 32));
+        kern<<<grid, threads, smem, c->stream>>>(C.K, C.L, P.K, P.L, R, C.d_oct, (const T *)tsel<T>::tp(C),
                                              (const T *)tsel<T>::tp(P), (const T *)tsel<T>::Phi(P),
                                              (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
                                              (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
@@ -1273,7 +1277,9 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       dim3 grid(C.nbox, R);
       auto args = [&](auto kern) {
         set_smem(kern, smem);
-        kern<<<grid, 256, smem, c->stream>>>(C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C),
+        const int tasks = std::max((nthc + 1) / 2 * (P.L + 1), nthc * (C.L + 1));
+        const int threads = std::min(256, std::max(64, (tasks + 31) / 32 * 32));
+        kern<<<grid, threads, smem, c->stream>>>(C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C),
                                              (const T *)tsel<T>::tp(P), (const T *)tsel<T>::Phi(P),
                                              (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
                                              (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
