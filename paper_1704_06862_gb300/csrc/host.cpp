@@ -938,7 +938,7 @@ static void build_ilu(sie_ctx *c) {
     I.d_up_cptr = dev_upload(c, ucp);
     // pieces of the single-RHS sweep steps: step s < 8 is forward colour s
     // (source colour s - 1), step s >= 8 backward colour 14 - s (source 15 - s)
-    const int PIECE = 1024;  // ILU_PIECE of the sweep kernel
+    const int PIECE = 1024;  // blocks per piece of a box's off-box work
     std::vector<int> pieces, pptr(1, 0);
     size_t maxp = 0;
     for (int step = 0; step < 15; ++step) {

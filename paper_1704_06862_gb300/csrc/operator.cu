@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int 
                                                   const int *__restrict__ basis_p, const int *__restrict__ sign,
                                                   const cx<T> *__restrict__ V, const cx<T> *__restrict__ x,
                                                   cx<T> *__restrict__ S) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
   const size_t per = (size_t)2 * K;  // complex values per basis
   cx<T> *ring = reinterpret_cast<cx<T> *>(smem_raw);       // [STAGES][cb][2][K]
@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, i
                                                      const int *__restrict__ basis_p, const cx<T> *__restrict__ P,
                                                      const cx<T> *__restrict__ I, cx<T> eta, cx<T> ieta,
                                                      cx<T> *__restrict__ y) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const size_t per = (size_t)2 * K;
@@ -764,7 +764,7 @@ __device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
 // w lives in z until the row is solved.  Each row's off-box blocks are sorted
 // by column, hence grouped by colour; cptr[i][c] .. cptr[i][c+1] is colour c.
 // In role A the box's blocks from sc (its "virtual range") are cut into
-// pieces of at most ILU_PIECE blocks, one CTA per piece, so that a large box
+// pieces of at most 1024 blocks (cut at setup), one CTA per piece, so that a large box
 // does not hold up the launch.  Within a piece the blocks are spread evenly over the CTA in
 // groups of 32 (one per lane); a segmented scan over the lanes keyed by row
 // adds each row's products, every warp keeps its own row partials, and the
@@ -773,7 +773,6 @@ __device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
 // meanwhile.  A box of several pieces: each piece writes its row partials to
 // scratch and counts itself in; the last to arrive adds the pieces' partials
 // in piece order and finishes the box.  The results are deterministic.
-constexpr int ILU_PIECE = 1024;
 constexpr int ILU_RL = 8;  // lanes per pushed row
 
 template <typename T, int NT>
@@ -1044,30 +1043,90 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
   }
 }
 
-// Block of right-hand sides: rows one per warp with lanes over the blocks of
-// the row; RB right-hand sides share every block load.
+// Block of right-hand sides: the same 15 sweep steps as the single-RHS path,
+// RB right-hand sides sharing every block load.  Role A: one CTA per box of
+// the colour, rows one per warp over the row's blocks from the source colour,
+// then the in-box inverse(s); role B: 8 lanes per row of the colours still to
+// come.  Right-hand sides beyond RB are taken in further passes.
 template <typename T, int RB>
-__global__ void __launch_bounds__(512) k_ilu_colour(int ne, int nrhs, int forward, int box0,
-                                                    const int *__restrict__ box_start,
-                                                    const int *__restrict__ off_ptr,
-                                                    const int *__restrict__ off_col,
-                                                    const cx<T> *__restrict__ off_val,
-                                                    const int64_t *__restrict__ tri_off,
-                                                    const cx<T> *__restrict__ tri, const cx<T> *src, cx<T> *z) {
+__global__ void __launch_bounds__(256) k_ilu_sweep_blk(int ne, int nrhs, int forward, int both, int colour,
+                                                      int nboxA, int box0, int rb0, int rb1,
+                                                      const int *__restrict__ box_start,
+                                                      const int *__restrict__ cptr, const int *__restrict__ off_col,
+                                                      const cx<T> *__restrict__ off_val,
+                                                      const int64_t *__restrict__ tri_off,
+                                                      const cx<T> *__restrict__ tri,
+                                                      const int64_t *__restrict__ tri2_off,
+                                                      const cx<T> *__restrict__ tri2, const cx<T> *src, cx<T> *z) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T> *t = reinterpret_cast<cx<T> *>(smem_raw);  // [RB][2n]
-  const int b = box0 + blockIdx.x;
-  const int s0 = box_start[b], n = box_start[b + 1] - s0;
-  const cx<T> *M = tri + 4 * tri_off[b];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const size_t vs = (size_t)ne * 2;
   typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V16;
   constexpr int NV = (int)(4 * sizeof(cx<T>) / sizeof(V16));
   const V16 *Ov = reinterpret_cast<const V16 *>(off_val);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const size_t vs = (size_t)ne * 2;
+  const int sc = forward ? colour - 1 : colour + 1;
+  const bool has_src = sc >= 0 && sc < 8;
+  const cx<T> *w = (forward && colour == 0) ? src : z;
+  if ((int)blockIdx.x >= nboxA) {
+    // ---- role B
+    const int hl = threadIdx.x & 7;
+    const int i = rb0 + ((int)blockIdx.x - nboxA) * ((int)blockDim.x / 8) + (int)(threadIdx.x >> 3);
+    const bool row_ok = i < rb1;
+    if (!has_src) {
+      if (row_ok)
+        for (int rr = 0; rr < nrhs; ++rr)
+          if (hl < 2) z[(size_t)rr * vs + 2 * (size_t)i + hl] = src[(size_t)rr * vs + 2 * (size_t)i + hl];
+      return;
+    }
+    int q0 = 0, q1 = 0;
+    if (row_ok) {
+      q0 = cptr[9 * (size_t)i + sc];
+      q1 = cptr[9 * (size_t)i + sc + 1];
+    }
+    for (int r0 = 0; r0 < nrhs; r0 += RB) {
+      const int nr = min(RB, nrhs - r0);
+      cx<T> a0[RB], a1[RB];
+      for (int q = q0 + hl; q < q1; q += 8) {
+        const int cc = __ldg(off_col + q);
+        V16 u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = __ldg(Ov + (size_t)q * NV + v);
+        const cx<T> *bb = reinterpret_cast<const cx<T> *>(u);
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+          if (rr < nr) {
+            cx<T> x0, x1;
+            ldg_pair(z + (size_t)(r0 + rr) * vs + 2 * (size_t)cc, x0, x1);  // colour sc: not written here
+            a0[rr] = cfma(bb[0], x0, cfma(bb[1], x1, a0[rr]));
+            a1[rr] = cfma(bb[2], x0, cfma(bb[3], x1, a1[rr]));
+          }
+      }
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr) {
+#pragma unroll
+        for (int d = 4; d > 0; d >>= 1) {
+          a0[rr] += shfl_down(a0[rr], d);
+          a1[rr] += shfl_down(a1[rr], d);
+        }
+        if (rr < nr && row_ok && hl == 0 && q1 > q0) {
+          cx<T> *o = z + (size_t)(r0 + rr) * vs + 2 * (size_t)i;
+          o[0] -= a0[rr];
+          o[1] -= a1[rr];
+        }
+      }
+    }
+    return;
+  }
+  // ---- role A
+  cx<T> *t = reinterpret_cast<cx<T> *>(smem_raw);  // [RB][2n]
+  const int b = box0 + blockIdx.x;
+  const int s0 = box_start[b], n = box_start[b + 1] - s0;
+  cx<T> *t2 = t + (size_t)RB * 2 * n;               // [RB][2n]
   for (int r0 = 0; r0 < nrhs; r0 += RB) {
     const int nr = min(RB, nrhs - r0);
     for (int li = warp; li < n; li += nw) {
-      const int i = s0 + li, q0 = off_ptr[i], q1 = off_ptr[i + 1];
+      const int i = s0 + li;
+      const int q0 = has_src ? cptr[9 * (size_t)i + sc] : 0, q1 = has_src ? cptr[9 * (size_t)i + sc + 1] : 0;
       cx<T> a0[RB], a1[RB];
       for (int q = q0 + lane; q < q1; q += 32) {
         const int cc = __ldg(off_col + q);
@@ -1079,7 +1138,7 @@ __global__ void __launch_bounds__(512) k_ilu_colour(int ne, int nrhs, int forwar
         for (int rr = 0; rr < RB; ++rr)
           if (rr < nr) {
             cx<T> x0, x1;
-            ldg_pair(z + (size_t)(r0 + rr) * vs + 2 * (size_t)cc, x0, x1);  // other colours only
+            ldg_pair(z + (size_t)(r0 + rr) * vs + 2 * (size_t)cc, x0, x1);
             a0[rr] = cfma(bb[0], x0, cfma(bb[1], x1, a0[rr]));
             a1[rr] = cfma(bb[2], x0, cfma(bb[3], x1, a1[rr]));
           }
@@ -1089,44 +1148,54 @@ __global__ void __launch_bounds__(512) k_ilu_colour(int ne, int nrhs, int forwar
         if (rr < nr) {
           const cx<T> u0 = warp_sum(a0[rr]), u1 = warp_sum(a1[rr]);
           if (lane == 0) {
-            const cx<T> *sr = src + (size_t)(r0 + rr) * vs + 2 * (size_t)i;
-            t[(size_t)rr * 2 * n + 2 * li] = sr[0] - u0;
-            t[(size_t)rr * 2 * n + 2 * li + 1] = sr[1] - u1;
+            const cx<T> *wr = w + (size_t)(r0 + rr) * vs + 2 * (size_t)i;
+            t[(size_t)rr * 2 * n + 2 * li] = wr[0] - u0;
+            t[(size_t)rr * 2 * n + 2 * li + 1] = wr[1] - u1;
           }
         }
     }
     __syncthreads();
-    for (int li = warp; li < n; li += nw) {
-      const int j0 = forward ? 0 : li, j1 = forward ? li : n;
-      const cx<T> *row = M + 4 * (size_t)(forward ? li * (li - 1) / 2 : li * n - li * (li - 1) / 2);
-      cx<T> a0[RB], a1[RB];
-      for (int j = j0 + lane; j < j1; j += 32) {
-        const cx<T> *B = row + 4 * (j - j0);
-        const cx<T> b0 = B[0], b1 = B[1], b2 = B[2], b3 = B[3];
+    for (int pass = 0; pass < (both ? 2 : 1); ++pass) {
+      const bool lower = forward && pass == 0;
+      const cx<T> *M = pass == 0 ? tri + 4 * tri_off[b] : tri2 + 4 * tri2_off[b];
+      const cx<T> *in = pass == 0 ? t : t2;
+      for (int li = warp; li < n; li += nw) {
+        const int j0 = lower ? 0 : li, j1 = lower ? li : n;
+        const cx<T> *row = M + 4 * (size_t)(lower ? li * (li - 1) / 2 : li * n - li * (li - 1) / 2);
+        cx<T> a0[RB], a1[RB];
+        for (int j = j0 + lane; j < j1; j += 32) {
+          const cx<T> *B = row + 4 * (j - j0);
+          const cx<T> b0 = B[0], b1 = B[1], b2 = B[2], b3 = B[3];
+#pragma unroll
+          for (int rr = 0; rr < RB; ++rr)
+            if (rr < nr) {
+              const cx<T> x0 = in[(size_t)rr * 2 * n + 2 * j], x1 = in[(size_t)rr * 2 * n + 2 * j + 1];
+              a0[rr] = cfma(b0, x0, cfma(b1, x1, a0[rr]));
+              a1[rr] = cfma(b2, x0, cfma(b3, x1, a1[rr]));
+            }
+        }
 #pragma unroll
         for (int rr = 0; rr < RB; ++rr)
           if (rr < nr) {
-            const cx<T> x0 = t[(size_t)rr * 2 * n + 2 * j], x1 = t[(size_t)rr * 2 * n + 2 * j + 1];
-            a0[rr] = cfma(b0, x0, cfma(b1, x1, a0[rr]));
-            a1[rr] = cfma(b2, x0, cfma(b3, x1, a1[rr]));
+            cx<T> u0 = warp_sum(a0[rr]), u1 = warp_sum(a1[rr]);
+            if (lane == 0) {
+              if (lower) {
+                u0 += in[(size_t)rr * 2 * n + 2 * li];
+                u1 += in[(size_t)rr * 2 * n + 2 * li + 1];
+              }
+              if (both && pass == 0) {
+                t2[(size_t)rr * 2 * n + 2 * li] = u0;
+                t2[(size_t)rr * 2 * n + 2 * li + 1] = u1;
+              } else {
+                cx<T> *o = z + (size_t)(r0 + rr) * vs + 2 * (size_t)(s0 + li);
+                o[0] = u0;
+                o[1] = u1;
+              }
+            }
           }
       }
-#pragma unroll
-      for (int rr = 0; rr < RB; ++rr)
-        if (rr < nr) {
-          cx<T> u0 = warp_sum(a0[rr]), u1 = warp_sum(a1[rr]);
-          if (lane == 0) {
-            if (forward) {
-              u0 += t[(size_t)rr * 2 * n + 2 * li];
-              u1 += t[(size_t)rr * 2 * n + 2 * li + 1];
-            }
-            cx<T> *o = z + (size_t)(r0 + rr) * vs + 2 * (size_t)(s0 + li);
-            o[0] = u0;
-            o[1] = u1;
-          }
-        }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -1339,24 +1408,25 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
     }
     return;
   }
-  for (int pass = 0; pass < 2; ++pass) {
-    const bool fwd = pass == 0;
-    const int *optr = fwd ? I.d_lo_ptr : I.d_up_ptr, *ocol = fwd ? I.d_lo_col : I.d_up_col;
-    const cx<T> *oval = (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I));
-    const int64_t *toff = fwd ? I.d_tl_off : I.d_tu_off;
-    const cx<T> *tri = (const cx<T> *)(fwd ? tsel<T>::tl(I) : tsel<T>::tu(I));
-    for (int q = 0; q < 8; ++q) {
-      const int colr = fwd ? q : 7 - q;
-      const int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
-      if (cnt == 0) continue;
-      constexpr int RB = sizeof(T) == 4 ? 8 : 4;
-      const size_t smem = 2 * (size_t)mb * RB * sizeof(cx<T>);
-      set_smem(k_ilu_colour<T, RB>, smem);
-      k_ilu_colour<T, RB><<<cnt, 32 * std::min(16, mb), smem, c->stream>>>(
-          c->ne, nrhs, fwd ? 1 : 0, first, I.d_box_start, optr, ocol, oval, toff, tri, fwd ? r : z, z);
-      SIE_CHECK_LAUNCH();
-      c->launches++;
-    }
+  // block of right-hand sides: the same 15 steps, RB right-hand sides per block load
+  constexpr int RB = sizeof(T) == 4 ? 8 : 4;
+  const size_t smem = 2 * (size_t)RB * 2 * mb * sizeof(cx<T>);
+  set_smem(k_ilu_sweep_blk<T, RB>, smem);
+  auto rows_from = [&](int colr) { return c->leaf_start[I.colour_ptr[colr]]; };
+  for (int step = 0; step < 15; ++step) {
+    const bool fwd = step < 8;
+    const int colr = fwd ? step : 14 - step;
+    const int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
+    const int rb0 = fwd ? rows_from(colr + 1) : 0, rb1 = fwd ? c->ne : rows_from(colr);
+    const int grid = cnt + (rb1 - rb0 + 31) / 32;  // role B: 32 rows per 256-thread CTA
+    if (grid == 0) continue;
+    k_ilu_sweep_blk<T, RB><<<grid, 256, smem, c->stream>>>(
+        c->ne, nrhs, fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, cnt, first, rb0, rb1, I.d_box_start,
+        fwd ? I.d_lo_cptr : I.d_up_cptr, fwd ? I.d_lo_col : I.d_up_col,
+        (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? I.d_tl_off : I.d_tu_off,
+        (const cx<T> *)(fwd ? tsel<T>::tl(I) : tsel<T>::tu(I)), I.d_tu_off, (const cx<T> *)tsel<T>::tu(I), r, z);
+    SIE_CHECK_LAUNCH();
+    c->launches++;
   }
 }
 

@@ -151,6 +151,25 @@ def test_ilu_apply(coated, prec, tol):
     assert rel(_host(out)[0], z.reshape(-1)) < tol
 
 
+@pytest.mark.parametrize("prec,tol", [(sie.SIE_PREC_FP64, 1e-9), (sie.SIE_PREC_MIXED, 1e-4)])
+def test_ilu_apply_block(coated, prec, tol):
+    """ILU(0) applied to a block of 10 right-hand sides (two passes of the
+    block kernel's right-hand-side chunk in FP32, three in FP64) against the
+    oracle ILU(0), column by column."""
+    c = coated
+    F, perm = _oracle_ilu(c)
+    V = geo.random_coefficients(2 * c.ne, 10, seed=23)
+    out = torch.zeros_like(_dev(V, c.ne))
+    sie.ilu_apply(c.s.ctx, _dev(V, c.ne), out, 10, prec)
+    got = _host(out)
+    for r in (0, 7, 9):
+        vp = V[r].reshape(c.ne, 2)[perm].reshape(-1)
+        zp = solvers.ilu_apply(F, vp)
+        z = np.empty_like(V[r]).reshape(c.ne, 2)
+        z[perm] = zp.reshape(c.ne, 2)
+        assert rel(got[r], z.reshape(-1)) < tol
+
+
 def test_rhs_and_rcs(sphere, coated):
     for c in (sphere, coated):
         inc = np.array([[0.0, 0.0, 0.0, 1.0], [0.7, 0.3, 0.4, 2.0]])
