@@ -192,7 +192,11 @@ struct sie_ctx {
   int64_t nrhs_cap = 0;
   void *d_xi = nullptr, *d_yi = nullptr;          // internal-order FP64 vectors [R][ne][2]
   void *d_xf = nullptr, *d_yf = nullptr;          // FP32 copies
-  void *d_scratch = nullptr;                      // upward-pass child contributions
+  void *d_scratch = nullptr;                      // upward-pass child contributions, one slice per medium
+  size_t scratch_region = 0;                      // bytes of one medium's slice
+  std::vector<cudaStream_t> rstream;              // one stream per medium for the far-field passes
+  std::vector<cudaEvent_t> ev_join;               // end of each medium's passes
+  cudaEvent_t ev_fork = nullptr;                  // start of the far field on the context stream
   void *d_stage = nullptr;                        // small host-to-device staging area
   size_t stage_bytes = 0;
   // Krylov storage of the last solve shape (restart m, nrhs R)
@@ -217,6 +221,7 @@ T *dev_upload(sie_ctx *c, const std::vector<T> &v) {
 }
 void ensure_work(sie_ctx *c, int64_t nrhs);
 void *stage(sie_ctx *c, size_t bytes);
+void region_streams(sie_ctx *c);  // creates the per-medium streams and events once
 
 // ------------------------------------------------------------------ launchers (fill.cu)
 void launch_near_fill(sie_ctx *c, int region);

@@ -26,6 +26,19 @@ void *dev_alloc(sie_ctx *c, size_t bytes) {
   return p;
 }
 
+void region_streams(sie_ctx *c) {
+  if (c->rstream.size() == c->reg.size() && c->ev_fork) return;
+  if (!c->ev_fork) SIE_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  while (c->rstream.size() < c->reg.size()) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    SIE_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    SIE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->rstream.push_back(s);
+    c->ev_join.push_back(e);
+  }
+}
+
 void *stage(sie_ctx *c, size_t bytes) {
   if (bytes > c->stage_bytes) {
     c->d_stage = dev_alloc(c, std::max(bytes, (size_t)4096));
@@ -52,7 +65,8 @@ void ensure_work(sie_ctx *c, int64_t nrhs) {
         scratch = std::max(scratch, (size_t)L.nbox * 4 * R.lev[l - 1].K * nrhs * sizeof(zd));
     }
   }
-  c->d_scratch = dev_alloc(c, scratch);
+  c->scratch_region = (scratch + 255) / 256 * 256;
+  c->d_scratch = dev_alloc(c, std::max<size_t>(256, c->scratch_region * c->reg.size()));
   c->nrhs_cap = nrhs;
   c->work_gen++;
 }
@@ -149,6 +163,9 @@ extern "C" void sie_destroy(sie_ctx *c) {
   nn_free(c);
   graphs_free(c);
   for (auto &b : c->bufs) cudaFree(b.p);
+  for (auto s : c->rstream) cudaStreamDestroy(s);
+  for (auto e : c->ev_join) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->gm_hpin) cudaFreeHost(c->gm_hpin);
   if (c->gm_ev) cudaEventDestroy(c->gm_ev);
   if (c->own_stream) cudaStreamDestroy(c->stream);

@@ -1268,8 +1268,17 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
   const int leaf = c->levels - 1;
   const int R = nrhs;
   if (c->levels < 3) return;  // every basis pair is near: no far field
-  for (RegionHost &G : c->reg) {
+  // The media are independent until the receive: each medium's aggregation,
+  // upward pass, translations and downward pass run on a stream of their own
+  // (parallel branches when the step is captured as a graph), after which the
+  // receives add into y one medium at a time on the context stream.
+  region_streams(c);
+  SIE_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+  for (size_t gi = 0; gi < c->reg.size(); ++gi) {
+    RegionHost &G = c->reg[gi];
     if (G.nb == 0) continue;
+    cudaStream_t st = c->rstream[gi];
+    SIE_CUDA(cudaStreamWaitEvent(st, c->ev_fork, 0));
     LevelHost &LL = G.lev[leaf];
     // aggregation at the leaf level
     const size_t per_basis = (size_t)2 * LL.K * sizeof(cx<T>);
@@ -1279,7 +1288,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       auto agg = [&](auto kern, int rb) {
         const size_t smem = STAGES * cb * per_basis + (size_t)G.max_leaf * rb * 2 * sizeof(cx<T>);
         set_smem(kern, smem);
-        kern<<<LL.nbox, 256, smem, c->stream>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p, G.d_basis_sign,
+        kern<<<LL.nbox, 256, smem, st>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p, G.d_basis_sign,
                                                 (const cx<T> *)tsel<T>::V(G), x, (cx<T> *)LL.d_S);
       };
       if (R == 1) agg(k_aggregate<T, 1>, 1);
@@ -1295,7 +1304,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       auto smem_for = [&](int jm) { return ((size_t)3 * jm * C.K + (size_t)3 * jm * nthc * Np) * sizeof(cx<T>) + tabs; };
       // one source (J or M) per pass: fewer registers, more CTAs per SM (measured faster than both at once)
       const size_t smem = smem_for(1);
-      cx<T> *Y = (cx<T> *)c->d_scratch;
+      cx<T> *Y = (cx<T> *)((char *)c->d_scratch + gi * c->scratch_region);
       dim3 grid(C.nbox, R);
       auto args = [&](auto kern) {
         set_smem(kern, smem);
@@ -1303,14 +1312,14 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
         // theta step: row pairs x column pairs), so small levels fit more CTAs per SM
         const int tasks = std::max(nthc * (P.L + 1), (nthp + 1) / 2 * (P.L + 1));
         const int threads = std::min(256, std::max(64, (tasks + 31) / 32 * 32));
-        kern<<<grid, threads, smem, c->stream>>>(C.K, C.L, P.K, P.L, R, C.d_oct, (const T *)tsel<T>::tp(C),
+        kern<<<grid, threads, smem, st>>>(C.K, C.L, P.K, P.L, R, C.d_oct, (const T *)tsel<T>::tp(C),
                                              (const T *)tsel<T>::tp(P), (const T *)tsel<T>::Phi(P),
                                              (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
                                              (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
       };
       args(k_interp_up<T, 1>);
       SIE_CHECK_LAUNCH();
-      k_up_sum<T><<<dim3((P.K + 127) / 128, P.nbox), 128, 0, c->stream>>>(P.K, R, P.d_ch_ptr, P.d_ch_idx, Y,
+      k_up_sum<T><<<dim3((P.K + 127) / 128, P.nbox), 128, 0, st>>>(P.K, R, P.d_ch_ptr, P.d_ch_idx, Y,
                                                                            (cx<T> *)P.d_S);
       SIE_CHECK_LAUNCH();
       c->launches += 2;
@@ -1324,12 +1333,12 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
         dim3 grid((B.K + 127) / 128, B.ngroups, R);
         const size_t smem = (size_t)B.max_group_entries * 10 * sizeof(int);
         set_smem(k_m2l_group<T>, smem);
-        k_m2l_group<T><<<grid, 128, smem, c->stream>>>(B.K, R, B.d_grp_ptr, B.d_grp_box, B.d_grp_ent,
+        k_m2l_group<T><<<grid, 128, smem, st>>>(B.K, R, B.d_grp_ptr, B.d_grp_box, B.d_grp_ent,
                                                        (const cx<T> *)tsel<T>::Tr(B), (const cx<T> *)B.d_S,
                                                        (cx<T> *)B.d_I);
       } else {
         dim3 grid((B.K + 127) / 128, B.nbox);
-        k_m2l<T><<<grid, 128, 0, c->stream>>>(B.nbox, B.K, R, B.d_il_ptr, B.d_il_src, B.d_il_slot,
+        k_m2l<T><<<grid, 128, 0, st>>>(B.nbox, B.K, R, B.d_il_ptr, B.d_il_src, B.d_il_slot,
                                               (const cx<T> *)tsel<T>::Tr(B), (const cx<T> *)B.d_S, (cx<T> *)B.d_I);
       }
       SIE_CHECK_LAUNCH();
@@ -1348,7 +1357,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
         set_smem(kern, smem);
         const int tasks = std::max((nthc + 1) / 2 * (P.L + 1), nthc * (C.L + 1));
         const int threads = std::min(256, std::max(64, (tasks + 31) / 32 * 32));
-        kern<<<grid, threads, smem, c->stream>>>(C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C),
+        kern<<<grid, threads, smem, st>>>(C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C),
                                              (const T *)tsel<T>::tp(P), (const T *)tsel<T>::Phi(P),
                                              (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
                                              (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
@@ -1357,6 +1366,15 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
+    SIE_CUDA(cudaEventRecord(c->ev_join[gi], st));
+  }
+  for (size_t gi = 0; gi < c->reg.size(); ++gi) {
+    RegionHost &G = c->reg[gi];
+    if (G.nb == 0) continue;
+    SIE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join[gi], 0));
+    LevelHost &LL = G.lev[leaf];
+    const size_t per_basis = (size_t)2 * LL.K * sizeof(cx<T>);
+    const int cb = (int)std::max<size_t>(1, std::min<size_t>(32, (32 * 1024) / per_basis));  // bases per chunk
     // receive at the leaves
     {
       std::complex<double> ie = 1.0 / G.eta;
