@@ -236,7 +236,8 @@ void launch_to_f32(sie_ctx *c, const double *src, float *dst, int64_t n);
 template <typename T>
 void op_near(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool accumulate);
 template <typename T>
-void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs);
+void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool forked = false);  // forked: far_fork already recorded
+void far_fork(sie_ctx *c);
 template <typename T>
 void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs);
 void op_permute_in(sie_ctx *c, const zd *user, zd *internal, int nrhs);    // user -> internal

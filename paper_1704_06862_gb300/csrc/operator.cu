@@ -1264,7 +1264,7 @@ void op_near(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool accumulate) {
 }
 
 template <typename T>
-void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
+void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool forked) {
   const int leaf = c->levels - 1;
   const int R = nrhs;
   if (c->levels < 3) return;  // every basis pair is near: no far field
@@ -1273,7 +1273,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs) {
   // (parallel branches when the step is captured as a graph), after which the
   // receives add into y one medium at a time on the context stream.
   region_streams(c);
-  SIE_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+  if (!forked) SIE_CUDA(cudaEventRecord(c->ev_fork, c->stream));
   for (size_t gi = 0; gi < c->reg.size(); ++gi) {
     RegionHost &G = c->reg[gi];
     if (G.nb == 0) continue;
@@ -1471,18 +1471,27 @@ void op_f2d(sie_ctx *c, const zf *a, zd *b, int64_t n) {
   c->launches++;
 }
 
+// marks on the context stream where the media's far-field passes may start
+void far_fork(sie_ctx *c) {
+  region_streams(c);
+  SIE_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+}
+
 void apply_matvec(sie_ctx *c, const zd *x, zd *y, int nrhs, sie_prec prec, int parts) {
   int64_t n = (int64_t)nrhs * c->ne * 2;
   if (prec == SIE_PREC_FP64) {
+    // the media's far-field passes start first and overlap the near-field product
+    if (parts & 2) far_fork(c);
     if (parts & 1) op_near<double>(c, x, y, nrhs, false);
     else SIE_CUDA(cudaMemsetAsync(y, 0, n * sizeof(zd), c->stream));
-    if (parts & 2) op_far<double>(c, x, y, nrhs);
+    if (parts & 2) op_far<double>(c, x, y, nrhs, true);
   } else {
     zf *xf = (zf *)c->d_xf, *yf = (zf *)c->d_yf;
     op_d2f(c, x, xf, n);
+    if (parts & 2) far_fork(c);
     if (parts & 1) op_near<float>(c, xf, yf, nrhs, false);
     else SIE_CUDA(cudaMemsetAsync(yf, 0, n * sizeof(zf), c->stream));
-    if (parts & 2) op_far<float>(c, xf, yf, nrhs);
+    if (parts & 2) op_far<float>(c, xf, yf, nrhs, true);
     op_f2d(c, yf, y, n);
   }
 }
@@ -1501,7 +1510,7 @@ void apply_ilu(sie_ctx *c, const zd *r, zd *z, int nrhs, sie_prec prec) {
 
 template void op_near<double>(sie_ctx *, const zd *, zd *, int, bool);
 template void op_near<float>(sie_ctx *, const zf *, zf *, int, bool);
-template void op_far<double>(sie_ctx *, const zd *, zd *, int);
-template void op_far<float>(sie_ctx *, const zf *, zf *, int);
+template void op_far<double>(sie_ctx *, const zd *, zd *, int, bool);
+template void op_far<float>(sie_ctx *, const zf *, zf *, int, bool);
 template void op_ilu<double>(sie_ctx *, const zd *, zd *, int);
 template void op_ilu<float>(sie_ctx *, const zf *, zf *, int);
