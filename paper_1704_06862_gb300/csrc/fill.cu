@@ -462,7 +462,8 @@ __global__ void __launch_bounds__(128) k_farfield_part(int npts, int nobs, const
                                                        const double *__restrict__ qpos, const zd *__restrict__ qcur,
                                                        zd k0, zd *part) {
   __shared__ double sp[FF_TP][4];
-  __shared__ zd sc[FF_TP][6];
+  __shared__ double2 sc_raw[FF_TP * 6];  // raw storage: zd has a constructor
+  zd(*sc)[6] = reinterpret_cast<zd(*)[6]>(sc_raw);
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y, NS = gridDim.y, r = blockIdx.z;
   V3 rh = v3(0.0, 0.0, 0.0);
@@ -508,7 +509,8 @@ __global__ void __launch_bounds__(128) k_farfield_part32(int npts, int nobs, con
                                                          const double *__restrict__ qpos, const zd *__restrict__ qcur,
                                                          double r0x, double r0y, double r0z, zd k0, zd *part) {
   __shared__ float4 sp[FF_TP];
-  __shared__ zf sc[FF_TP][6];
+  __shared__ float2 sc_raw[FF_TP * 6];  // raw storage: zf has a constructor
+  zf(*sc)[6] = reinterpret_cast<zf(*)[6]>(sc_raw);
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y, NS = gridDim.y, r = blockIdx.z;
   float rx = 0.f, ry = 0.f, rz = 0.f;

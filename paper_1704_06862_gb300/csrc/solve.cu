@@ -60,7 +60,8 @@ __global__ void k_reorth_gate(int nrhs, int nvec, const zd *__restrict__ h, cons
 
 __global__ void k_mdot_sum(int nrhs, int nblk, const zd *__restrict__ part, zd *__restrict__ h) {
   const int i = blockIdx.x, r = blockIdx.y;
-  __shared__ zd red[256];
+  __shared__ double2 red_raw[256];  // raw storage: zd has a constructor
+  zd *red = reinterpret_cast<zd *>(red_raw);
   zd acc;
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += part[((size_t)i * nrhs + r) * nblk + b];
   red[threadIdx.x] = acc;
