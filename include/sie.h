@@ -84,7 +84,7 @@ sie_status sie_build_mesh(sie_ctx *ctx, const double *verts, int64_t nv, const i
                           int64_t nt, const int32_t *tri_regions, const double *media, int32_t nr,
                           double freq_hz, int64_t *n_rwg_out);
 
-/* MLFMM options (the paper gives none; readings in the design doc). */
+/* MLFMM options (the paper gives none; the readings adopted are stated per field). */
 typedef struct {
   int32_t levels;   /* octree levels including the root, in [2, 12]; 2 puts
                        every basis pair in the near field (dense product,
@@ -97,7 +97,8 @@ typedef struct {
 
 /* Octree, near-field pattern, preconditioner ordering and the far-field
  * tables of every medium: direction samples, M2L translators, exact
- * (spherical-harmonic projection) interpolation matrices, shift phases.
+ * separable interpolation tables (trigonometric in phi, Lagrange in cos theta),
+ * shift phases, sibling groups for the block translations.
  * Requires sie_build_mesh.  Synchronous. */
 sie_status mlfmm_setup(sie_ctx *ctx, const sie_mlfmm_opts *opts);
 

@@ -17,8 +17,8 @@ What it computes (plain definitions, no acceleration):
 * dense LU, restarted GMRES, ILU(0) on the near-field pattern        -> solvers.py
 * octree box assignment, near pattern, colour ordering               -> tree.py
 
-Readings of garbled or silent passages are listed in the design doc and repeated
-in each function's docstring.  Parity status: every function is pinned by a
+Readings of garbled or silent passages are stated in each function's
+docstring.  Parity status: every function is pinned by a
 ``-m "not gpu"`` test (tests/test_oracle_*.py) except where its docstring says
 "parity unpinned".
 """

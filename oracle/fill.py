@@ -1,6 +1,6 @@
 """Dense Galerkin JMCFIE matrix and excitation (oracle, test infrastructure).
 
-Formulation (e^{+j w t}; readings of the garbled passages listed in the design doc):
+Formulation (e^{+j w t}; readings of the garbled passages stated here):
 
 Per medium l (Eqs. 5-7) with k_l, eta_l and the four boundary equations
 (Eqs. 8-11) written from Maxwell's equations with the *inward* normal
@@ -20,8 +20,8 @@ JMCFIE (Eq. 14 for one interface, Eq. 16 for several):
 The N-parts carry the (-1)^l of Eq. 14 with l = 1 the host (s_l = -(-1)^l);
 the T-parts are weighted by s_l so that the operators of the two media add
 across an interface (PMCHWT-type); with these signs every eigenvalue of the
-discrete operator lies in the right half-plane (reading of the garbled signs,
-the design doc).  Tested with RWG t_m = b_m (Galerkin, Eqs. 13-14 of the
+discrete operator lies in the right half-plane (the reading adopted for the
+garbled signs).  Tested with RWG t_m = b_m (Galerkin, Eqs. 13-14 of the
 discretisation section).  Unknowns and rows are scaled so that every block is
 dimensionless: unknown pair (eta_0 c_n, v_n), J-row multiplied by eta_0.  With
 eta~_l = eta_l / eta_0 and the Galerkin matrices

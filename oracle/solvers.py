@@ -5,7 +5,7 @@
   Iterative Methods for Sparse Linear Systems, Alg. 9.6), modified
   Gram-Schmidt, complex Givens rotations.  The paper solves with
   ILU-preconditioned BiCGStab; the measured workload uses GMRES(50) with the
-  same ILU (reading of the solver choice).
+  same ILU (the reading adopted for the solver choice).
 * ``ilu0``: incomplete LU with zero fill on a given sparsity pattern (the
   paper's ILU preconditioner, cited without detail): L unit lower, U upper,
   (L U)_ij = A_ij for every (i, j) of the pattern; IKJ elimination order.

@@ -245,7 +245,7 @@ def test_null_body_scatters_nothing():
 
 
 def test_jmcfie_spectrum_right_half_plane():
-    """With the combination signs read from Eq. 14, the discrete
+    """With the combination signs read from Eq. 14 (adopted reading), the discrete
     operator of a dielectric sphere has its whole spectrum in Re > 0 (the
     property that makes the combined formulation converge quickly)."""
     m = Mesh(**geo.homogeneous_sphere(nu=3, radius=0.5, eps_r=4.0))
