@@ -319,6 +319,39 @@ def test_fgmres_matches_lu():
     assert hist[-1] < 1e-10 and its > 10          # restarts happened
 
 
+@pytest.mark.parametrize("solver", ["bicgstab", "cgs"])
+def test_bicgstab_cgs_match_lu(solver):
+    """The paper's solvers converge to the dense solution, unpreconditioned and
+    with a right preconditioner (the residual they monitor is b - A x)."""
+    f = getattr(solvers, solver)
+    A, b = _rand_system()
+    xe = np.linalg.solve(A, b)
+    D = np.diag(np.diag(A))
+    for M in (None, lambda v: np.linalg.solve(D, v)):
+        x, its, hist = f(lambda v: A @ v, b, precond=M, tol=1e-11, maxit=500)
+        assert np.linalg.norm(x - xe) < 1e-9 * np.linalg.norm(xe)
+        assert np.linalg.norm(b - A @ x) < 1e-10 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "cgs"])
+def test_bicgstab_cgs_finite_termination(solver):
+    """Both are built on BiCG: with three distinct eigenvalues the BiCG
+    residual polynomial vanishes after three steps, so they stop within three
+    iterations; with the exact inverse as preconditioner, after one."""
+    f = getattr(solvers, solver)
+    rng = np.random.default_rng(11)
+    n = 30
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    lam = np.array([1.0 + 0.5j, 2.0, 5.0 - 1.0j])[rng.integers(0, 3, n)]
+    A = Q @ np.diag(lam) @ Q.conj().T
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, its, hist = f(lambda v: A @ v, b, tol=1e-9, maxit=50)
+    assert its <= 3 and np.linalg.norm(b - A @ x) < 1e-8 * np.linalg.norm(b)
+    Ai = np.linalg.inv(A)
+    x, its, hist = f(lambda v: A @ v, b, precond=lambda v: Ai @ v, tol=1e-9, maxit=50)
+    assert its == 1 and np.linalg.norm(b - A @ x) < 1e-8 * np.linalg.norm(b)
+
+
 def test_ilu0_full_pattern_is_exact_lu():
     A, b = _rand_system(40)
     F = solvers.ilu0(sp.csr_matrix(A))
