@@ -168,6 +168,10 @@ typedef struct {
                           correction is dropped for the rest of a solve as soon
                           as a restart cycle fails to reduce the true residual),
                           all as right preconditioning */
+  int32_t method;      /* 0: FGMRES(restart) (default); 1: BiCGStab; 2: CGS
+                          (the paper's solvers; right-preconditioned, restarted
+                          from the FP64 true residual when the recurrence
+                          residual reaches tol; restart and no_graphs unused) */
   int32_t no_graphs;   /* 0: each Krylov step (preconditioner + product) is
                           captured once as a CUDA graph and replayed; 1: every
                           step is launched eagerly (same kernels, same results;

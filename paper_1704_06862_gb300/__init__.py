@@ -44,7 +44,8 @@ class sie_fill_opts(ctypes.Structure):
 
 class sie_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("prec", ctypes.c_int32), ("precond", ctypes.c_int32), ("no_graphs", ctypes.c_int32)]
+                ("prec", ctypes.c_int32), ("precond", ctypes.c_int32), ("method", ctypes.c_int32),
+                ("no_graphs", ctypes.c_int32)]
 
 
 class sie_solve_stats(ctypes.Structure):
@@ -178,9 +179,13 @@ def sie_plane_wave_rhs(ctx, inc, b):
     _check(ctx, load_library().sie_plane_wave_rhs(ctx, _ptr(inc), len(inc), _ptr(b)))
 
 
+SOLVE_FGMRES, SOLVE_BICGSTAB, SOLVE_CGS = 0, 1, 2
+
+
 def gmres_solve(ctx, b, x, nrhs, restart=50, max_iters=1000, tol=1e-4, prec=SIE_PREC_FP64, precond=1,
-                check=True, graphs=True):
-    o = sie_solve_opts(int(restart), int(max_iters), float(tol), int(prec), int(precond), 0 if graphs else 1)
+                check=True, graphs=True, method=SOLVE_FGMRES):
+    o = sie_solve_opts(int(restart), int(max_iters), float(tol), int(prec), int(precond), int(method),
+                       0 if graphs else 1)
     st = (sie_solve_stats * int(nrhs))()
     rc = load_library().gmres_solve(ctx, _ptr(b), _ptr(x), int(nrhs), ctypes.byref(o), st)
     stats = [dict(iters=s.iters, restarts=s.restarts, rel_residual=s.rel_residual, converged=bool(s.converged))

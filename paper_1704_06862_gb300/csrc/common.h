@@ -201,6 +201,8 @@ struct sie_ctx {
   size_t stage_bytes = 0;
   // Krylov storage of the last solve shape (restart m, nrhs R)
   int gm_m = 0, gm_R = 0, gw_R = 0;
+  int bi_R = 0;  // BiCGStab / CGS work vectors, per block size
+  void *bi_buf = nullptr, *bi_coef = nullptr, *bi_part = nullptr, *bi_dot = nullptr;
   int64_t work_gen = 0;     // bumped whenever work buffers are (re)allocated
   void *graphs = nullptr;   // captured per-step operator graphs (solve.cu)
   void *nn = nullptr;  // learned-preconditioner state (nn.cu)

@@ -1204,6 +1204,9 @@ extern "C" sie_status gmres_solve(sie_ctx *c, const void *b, void *x, int64_t nr
     SIE_REQUIRE(o->restart >= 1 && o->restart <= 500 && o->max_iters >= 1 && o->tol > 0, SIE_EINVAL,
                 "gmres_solve: bad options");
     SIE_REQUIRE(o->precond >= 0 && o->precond <= 2, SIE_EINVAL, "gmres_solve: precond must be 0, 1 or 2");
+    SIE_REQUIRE(o->method >= 0 && o->method <= 2, SIE_EINVAL, "gmres_solve: method must be 0, 1 or 2");
+    SIE_REQUIRE(o->method == 0 || o->precond <= 1, SIE_EINVAL,
+                "gmres_solve: the learned correction needs FGMRES (a variable preconditioner)");
     SIE_REQUIRE(o->precond == 0 || c->ilu.ready, SIE_ESTATE, "gmres_solve: ILU requested but not built");
     SIE_REQUIRE(o->precond != 2 || nn_trained(c), SIE_ESTATE, "gmres_solve: learned preconditioner not trained");
     rc = run_gmres(c, (const zd *)b, (zd *)x, (int)nrhs, o, st);

@@ -111,6 +111,25 @@ __global__ void k_sub(int64_t n, const zd *a, const zd *b, zd *out) {
     out[t] = a[t] - b[t];
 }
 
+// out[r] = a[r] + c[r] b[r]   (per right-hand-side complex coefficient)
+__global__ void k_axpy_r(int n, const zd *__restrict__ a, const zd *__restrict__ cf, const zd *__restrict__ b,
+                         zd *__restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (t >= n) return;
+  const size_t i = (size_t)r * n + t;
+  out[i] = a[i] + cf[r] * b[i];
+}
+// out[r] = a[r] + c1[r] (b[r] + c2[r] d[r])
+__global__ void k_axpy2_r(int n, const zd *__restrict__ a, const zd *__restrict__ c1, const zd *__restrict__ b,
+                          const zd *__restrict__ c2, const zd *__restrict__ d, zd *__restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (t >= n) return;
+  const size_t i = (size_t)r * n + t;
+  out[i] = a[i] + c1[r] * (b[i] + c2[r] * d[i]);
+}
+
 // x[r] += sum_j Z_j[r] y[j][r]
 __global__ void k_xupd(int n, int nrhs, int m, const zd *__restrict__ Z, size_t zstride, const zd *__restrict__ y,
                        zd *__restrict__ x) {
@@ -446,6 +465,210 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
   return conv ? SIE_OK : SIE_ENOTCONV;
 }
 
+// BiCGStab (method 1) and CGS (method 2), right-preconditioned, for R
+// right-hand sides in lockstep on internal-order FP64 vectors; the inner
+// operator and preconditioner in `prec`.  Scalars per right-hand side on the
+// host.  When the recurrence residual of every active right-hand side is
+// below tol, the true residual b - A x with the FP64 operator decides; a
+// right-hand side that is not there restarts from its current x (iterative
+// refinement).  Breakdown (a zero inner product) also restarts.
+sie_status run_bicg_internal(sie_ctx *c, const zd *b, zd *x, int R, int max_iters, double tol, sie_prec prec,
+                             int precond, int method, sie_solve_stats *st) {
+  const int n = 2 * c->ne;
+  const size_t vs = (size_t)R * n;
+  ensure_work(c, R);
+  constexpr int NV = 9;  // r, r0, p, v, s|u, t|q, ph, sh|uh, w
+  if (c->bi_R != R) {
+    c->bi_buf = dev_alloc(c, NV * vs * sizeof(zd));
+    c->bi_coef = dev_alloc(c, 4 * (size_t)R * sizeof(zd));
+    c->bi_part = dev_alloc(c, (size_t)4 * R * ((n + 1023) / 1024) * sizeof(zd));
+    c->bi_dot = dev_alloc(c, 4 * (size_t)R * sizeof(zd));
+    c->bi_R = R;
+  }
+  zd *B = (zd *)c->bi_buf;
+  zd *r = B, *r0 = B + vs, *p = B + 2 * vs, *v = B + 3 * vs, *s_ = B + 4 * vs, *t = B + 5 * vs, *ph = B + 6 * vs,
+     *sh = B + 7 * vs, *w = B + 8 * vs;
+  zd *cf = (zd *)c->bi_coef, *dd = (zd *)c->bi_dot;
+  Gm g{c, n, R, std::max(1, (n + 1023) / 1024), (zd *)c->bi_part};
+  dim3 gv((n + 255) / 256, R);
+  auto precon = [&](const zd *in, zd *out) {
+    if (precond >= 1) apply_ilu(c, in, out, R, prec);
+    else SIE_CUDA(cudaMemcpyAsync(out, in, vs * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
+  };
+  // per right-hand-side dots <a[r], b[r]> -> host
+  auto dots = [&](const zd *a, const zd *bb, std::vector<cd> &out) {
+    g.mdot(a, 0, 1, bb, dd);
+    std::vector<zd> h(R);
+    SIE_CUDA(cudaMemcpyAsync(h.data(), dd, R * sizeof(zd), cudaMemcpyDeviceToHost, c->stream));
+    SIE_CUDA(cudaStreamSynchronize(c->stream));
+    out.resize(R);
+    for (int q = 0; q < R; ++q) out[q] = cd(h[q].re, h[q].im);
+  };
+  auto coef = [&](int slot, const std::vector<cd> &vals) {
+    std::vector<zd> h(R);
+    for (int q = 0; q < R; ++q) h[q] = zd(vals[q].real(), vals[q].imag());
+    SIE_CUDA(cudaMemcpyAsync(cf + (size_t)slot * R, h.data(), R * sizeof(zd), cudaMemcpyHostToDevice, c->stream));
+    return cf + (size_t)slot * R;
+  };
+  auto axpy = [&](const zd *a, const std::vector<cd> &k, const zd *bb, zd *out, int slot) {
+    k_axpy_r<<<gv, 256, 0, c->stream>>>(n, a, coef(slot, k), bb, out);
+    g.launch_check();
+  };
+  std::vector<cd> bn2, rn2;
+  dots(b, b, bn2);
+  std::vector<double> bn(R);
+  for (int q = 0; q < R; ++q) bn[q] = std::sqrt(std::max(0.0, bn2[q].real()));
+  std::vector<int> iters(R, 0), restarts(R, 0), active(R, 1);
+  std::vector<double> relres(R, 0.0);
+  sie_status status = SIE_OK;
+  const std::vector<cd> one(R, cd(1.0)), mone(R, cd(-1.0));
+  auto relnorm = [&](const std::vector<cd> &nn, int q) {
+    return bn[q] > 0 ? std::sqrt(std::max(0.0, nn[q].real())) / bn[q] : 0.0;
+  };
+  std::vector<cd> xn2;
+  dots(x, x, xn2);
+  bool x_zero = true;
+  for (int q = 0; q < R; ++q) x_zero = x_zero && xn2[q].real() == 0.0;
+  int stalls = 0;  // restarts in a row without a single step (repeated breakdown)
+  for (bool first_cycle = true;; first_cycle = false) {
+    // true residual with the FP64 operator (r = b for a zero initial guess)
+    if (first_cycle && x_zero) {
+      SIE_CUDA(cudaMemcpyAsync(r, b, vs * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      apply_matvec(c, x, w, R, SIE_PREC_FP64, 3);
+      axpy(b, mone, w, r, 0);
+    }
+    dots(r, r, rn2);
+    bool any = false;
+    for (int q = 0; q < R; ++q) {
+      relres[q] = relnorm(rn2, q);
+      if (!std::isfinite(relres[q])) status = SIE_EBREAKDOWN;
+      active[q] = relres[q] > tol && iters[q] < max_iters && std::isfinite(relres[q]);
+      if (active[q]) {
+        any = true;
+        restarts[q]++;
+      }
+    }
+    if (!any || status != SIE_OK) break;
+    SIE_CUDA(cudaMemcpyAsync(r0, r, vs * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
+    SIE_CUDA(cudaMemsetAsync(p, 0, vs * sizeof(zd), c->stream));
+    SIE_CUDA(cudaMemsetAsync(v, 0, vs * sizeof(zd), c->stream));  // CGS: q
+    std::vector<cd> rho_old(R, cd(1.0)), alpha(R, cd(1.0)), omega(R, cd(1.0)), rho;
+    bool first = true, breakdown = false;
+    int steps = 0;
+    for (;;) {
+      dots(r0, r, rho);
+      std::vector<cd> k1(R, 0.0), k2(R, 0.0), k3(R, 0.0);
+      for (int q = 0; q < R; ++q)
+        if (active[q] && (rho[q] == 0.0 || !std::isfinite(std::abs(rho[q])))) breakdown = true;
+      if (breakdown) break;
+      if (method == 1) {
+        // p = r + beta (p - omega v)
+        for (int q = 0; q < R; ++q)
+          if (active[q]) {
+            const cd beta = first ? cd(0.0) : (rho[q] / rho_old[q]) * (alpha[q] / omega[q]);
+            k1[q] = beta;
+            k2[q] = -omega[q];
+          }
+        k_axpy2_r<<<gv, 256, 0, c->stream>>>(n, r, coef(0, k1), p, coef(1, k2), v, p);
+        g.launch_check();
+        precon(p, ph);
+        apply_matvec(c, ph, v, R, prec, 3);
+        std::vector<cd> rv;
+        dots(r0, v, rv);
+        for (int q = 0; q < R; ++q) {
+          if (!active[q]) continue;
+          if (rv[q] == 0.0) breakdown = true;
+          alpha[q] = rho[q] / rv[q];
+          k1[q] = -alpha[q];
+        }
+        if (breakdown) break;
+        axpy(r, k1, v, s_, 2);  // s = r - alpha v (r for finished right-hand sides)
+        precon(s_, sh);
+        apply_matvec(c, sh, t, R, prec, 3);
+        std::vector<cd> ts, tt;
+        dots(t, s_, ts);
+        dots(t, t, tt);
+        for (int q = 0; q < R; ++q) {
+          k1[q] = k2[q] = 0.0;
+          if (!active[q]) continue;
+          omega[q] = tt[q].real() > 0 ? ts[q] / tt[q] : cd(0.0);  // t = 0 only when s = 0
+          k1[q] = alpha[q];
+          k2[q] = omega[q] / (alpha[q] == 0.0 ? cd(1.0) : alpha[q]);
+        }
+        // x += alpha (ph + (omega / alpha) sh);  r = s - omega t
+        k_axpy2_r<<<gv, 256, 0, c->stream>>>(n, x, coef(0, k1), ph, coef(1, k2), sh, x);
+        g.launch_check();
+        for (int q = 0; q < R; ++q) k3[q] = active[q] ? -omega[q] : cd(0.0);
+        axpy(s_, k3, t, r, 2);
+      } else {
+        // u = r + beta q;  p = u + beta (q + beta p)
+        zd *u = s_, *qv = v;
+        for (int q = 0; q < R; ++q)
+          if (active[q]) k1[q] = first ? cd(0.0) : rho[q] / rho_old[q];
+        axpy(r, k1, qv, u, 0);
+        k_axpy2_r<<<gv, 256, 0, c->stream>>>(n, u, coef(1, k1), qv, coef(2, k1), p, p);
+        g.launch_check();
+        precon(p, ph);
+        apply_matvec(c, ph, t, R, prec, 3);  // t = A M^-1 p
+        std::vector<cd> rv;
+        dots(r0, t, rv);
+        for (int q = 0; q < R; ++q) {
+          k1[q] = 0.0;
+          if (!active[q]) continue;
+          if (rv[q] == 0.0) breakdown = true;
+          alpha[q] = rho[q] / rv[q];
+          k1[q] = -alpha[q];
+        }
+        if (breakdown) break;
+        axpy(u, k1, t, qv, 0);              // q = u - alpha t
+        axpy(u, one, qv, w, 1);             // w = u + q
+        precon(w, sh);                       // uh = M^-1 (u + q)
+        for (int q = 0; q < R; ++q) k2[q] = -k1[q];
+        axpy(x, k2, sh, x, 2);               // x += alpha uh
+        apply_matvec(c, sh, t, R, prec, 3);
+        axpy(r, k1, t, r, 3);                // r -= alpha A uh
+      }
+      first = false;
+      ++steps;
+      rho_old = rho;
+      dots(r, r, rn2);
+      bool all_done = true;
+      for (int q = 0; q < R; ++q) {
+        if (!active[q]) continue;
+        iters[q]++;
+        const double e = relnorm(rn2, q);
+        if (!std::isfinite(e)) {
+          status = SIE_EBREAKDOWN;
+          break;
+        }
+        if (e <= tol || iters[q] >= max_iters) active[q] = 0;  // frozen: coefficients 0 from now on
+        else all_done = false;
+      }
+      if (all_done || status != SIE_OK) break;
+    }
+    if (status != SIE_OK) break;
+    stalls = steps == 0 ? stalls + 1 : 0;
+    if (breakdown && stalls >= 2) {
+      status = SIE_EBREAKDOWN;
+      break;
+    }
+  }
+  SIE_CUDA(cudaStreamSynchronize(c->stream));
+  bool conv = true;
+  for (int q = 0; q < R; ++q) {
+    if (st) {
+      st[q].iters = iters[q];
+      st[q].restarts = restarts[q];
+      st[q].rel_residual = relres[q];
+      st[q].converged = relres[q] <= tol ? 1 : 0;
+    }
+    if (!(relres[q] <= tol)) conv = false;
+  }
+  if (status != SIE_OK) return status;
+  return conv ? SIE_OK : SIE_ENOTCONV;
+}
+
 sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_solve_opts *o, sie_solve_stats *st) {
   const size_t vs = (size_t)R * 2 * c->ne;
   if (c->gw_R != R) {
@@ -462,7 +685,9 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
     ~Eager() { c->graphs_off = false; }
   } eager{c};
   c->graphs_off = o->no_graphs != 0;
-  sie_status rc = run_gmres_internal(c, b, x, R, o->restart, o->max_iters, o->tol, prec, o->precond, nullptr, st);
+  sie_status rc = o->method == 0
+                      ? run_gmres_internal(c, b, x, R, o->restart, o->max_iters, o->tol, prec, o->precond, nullptr, st)
+                      : run_bicg_internal(c, b, x, R, o->max_iters, o->tol, prec, o->precond, o->method, st);
   op_permute_out(c, x, x_user, R);
   SIE_CUDA(cudaStreamSynchronize(c->stream));
   return rc;

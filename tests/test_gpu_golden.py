@@ -153,3 +153,17 @@ def test_block_product_equals_single_products(case):
             y1 = torch.zeros_like(xb[r:r + 1])
             sie.mlfmm_matvec(s.ctx, xb[r:r + 1].contiguous(), y1, 1, prec)
             assert rel(yb[r], _host(y1)[0]) < tol
+
+
+@pytest.mark.parametrize("method", [sie.SOLVE_BICGSTAB, sie.SOLVE_CGS])
+def test_bicgstab_cgs_solution(case, method):
+    """The paper's solvers with ILU(0) on the MLFMM operator (mixed precision,
+    FP64 true residual at the end) reach the dense-LU currents."""
+    name, s, d = case
+    b = torch.zeros((1, s.ne, 2), dtype=torch.complex128, device="cuda")
+    sie.sie_plane_wave_rhs(s.ctx, [[0.0, 0.0, 0.0, 1.0]], b)
+    x = torch.zeros_like(b)
+    st = sie.gmres_solve(s.ctx, b, x, 1, max_iters=1000, tol=1e-6, prec=sie.SIE_PREC_MIXED, precond=1,
+                         method=method)
+    assert st[0]["converged"]
+    assert rel(_host(x)[0], d["xs"]) < 1e-3

@@ -221,3 +221,27 @@ def test_tiny_body_near_only_and_errors():
         sie.mlfmm_setup(ctx, 4)
     assert e.value.code == 4
     sie.sie_destroy(ctx)
+
+
+@pytest.mark.parametrize("method,name", [(sie.SOLVE_BICGSTAB, "bicgstab"), (sie.SOLVE_CGS, "cgs")])
+def test_bicgstab_cgs_match_oracle_dense(sphere, method, name):
+    """With two levels every pair is near, so the product is the dense
+    Galerkin matrix: the GPU BiCGStab / CGS (FP64, no preconditioner) take the
+    oracle's steps on the oracle's matrix and reach the dense-LU solution."""
+    c = sphere
+    s2 = sie.Solver(c.mesh, levels=2)
+    try:
+        inc = np.array([[0.3, 0.2, 0.0, 1.0]])
+        bo = fill.rhs(c.m, inc)[0]
+        b = _dev(bo[None], c.ne)
+        x = torch.zeros_like(b)
+        st = sie.gmres_solve(s2.ctx, b, x, 1, max_iters=500, tol=1e-8, prec=sie.SIE_PREC_FP64, precond=0,
+                             method=method)
+        xo, its, _ = getattr(solvers, name)(lambda v: c.Z @ v, bo, tol=1e-8, maxit=500)
+        xe = solvers.lu_solve(c.Z, bo)
+        assert st[0]["converged"]
+        assert abs(st[0]["iters"] - its) <= 2
+        assert rel(_host(x)[0], xe) < 1e-6
+        assert rel(xo, xe) < 1e-6
+    finally:
+        s2.close()
