@@ -236,13 +236,48 @@ def region_operators(mesh: Mesh, l, rows=None, chunk=24, outer_n=4, freq_hz=None
     return out
 
 
-def assemble(mesh: Mesh, freq_hz=None, rows=None, chunk=24, outer_n=4):
-    """Dense JMCFIE matrix (scaled), shape [2 ne, 2 ne] with per-edge (J, M)
-    interleaving; if ``rows`` (edge indices) is given only those edge rows are
-    returned, shape [2 len(rows), 2 ne]."""
+FORMULATIONS = ("jmcfie", "ctf", "cnf", "pmchwt")
+
+
+def formulation_weights(formulation, eta):
+    """Weights (aTJ, aNJ, aTM, aNM) of medium l (relative impedance eta~_l) in
+    J-row = sum_l s_l [aTJ T-EFIE_l / eta_l - aNJ N-MFIE_l] and
+    M-row = sum_l s_l [aNM N-EFIE_l - aTM eta_l T-MFIE_l]:
+    JMCFIE (Eq. 14) all 1; CTF the tangential parts only; CNF the normal
+    parts only; PMCHWT the tangential equations unweighted by the medium's
+    impedance (aTJ = eta~_l, aTM = 1 / eta~_l), whose 1/2 jump terms cancel
+    between the two sides of an interface.  The variants the paper compares
+    its JMCFIE with (its iteration-count study)."""
+    if formulation == "jmcfie":
+        return 1.0, 1.0, 1.0, 1.0
+    if formulation == "ctf":
+        return 1.0, 0.0, 1.0, 0.0
+    if formulation == "cnf":
+        return 0.0, 1.0, 0.0, 1.0
+    if formulation == "pmchwt":
+        return eta, 0.0, 1.0 / eta, 0.0
+    raise ValueError(f"unknown formulation {formulation!r}")
+
+
+def assemble(mesh: Mesh, freq_hz=None, rows=None, chunk=24, outer_n=4, formulation="jmcfie"):
+    """Dense matrix (scaled) of the given formulation (default JMCFIE), shape
+    [2 ne, 2 ne] with per-edge (J, M) interleaving; if ``rows`` (edge indices)
+    is given only those edge rows are returned, shape [2 len(rows), 2 ne].
+    Tangential (T) and normal (N) parts of each block, per medium:
+      JJ: T  ss L                      N  -sn NK + 1/2 ss G
+      JM: T  (ss K + 1/2 sm Gx) / eta  N  sn NL / eta
+      MJ: T -(ss K + 1/2 sm Gx) eta    N -sn NL eta
+      MM: T  ss L                      N  -sn NK + 1/2 ss G
+    weighted by formulation_weights (J-row: aTJ, aNJ; M-row: aTM, aNM)."""
+    return assemble_variants(mesh, (formulation,), freq_hz, rows, chunk, outer_n)[formulation]
+
+
+def assemble_variants(mesh: Mesh, formulations=FORMULATIONS, freq_hz=None, rows=None, chunk=24, outer_n=4):
+    """``assemble`` for several formulations from one evaluation of the
+    media's Galerkin matrices: dict formulation -> matrix."""
     ne = mesh.ne
     rows = np.arange(ne) if rows is None else np.asarray(rows, np.int64)
-    Z = np.zeros((2 * len(rows), 2 * ne), np.complex128)
+    out = {f: np.zeros((2 * len(rows), 2 * ne), np.complex128) for f in formulations}
     for l in range(mesh.nr):
         op = region_operators(mesh, l, rows, chunk, outer_n, freq_hz)
         s = mesh.region_sign(l)
@@ -250,11 +285,15 @@ def assemble(mesh: Mesh, freq_hz=None, rows=None, chunk=24, outer_n=4):
         sn = s[None, :]
         ss = sm * sn
         eta = op["eta"]
-        Z[0::2, 0::2] += ss * op["L"] - sn * op["NK"] + 0.5 * ss * op["G"]
-        Z[0::2, 1::2] += (ss * op["K"] + sn * op["NL"]) / eta + 0.5 * sm * op["Gx"] / eta
-        Z[1::2, 0::2] += -(ss * op["K"] + sn * op["NL"]) * eta - 0.5 * sm * op["Gx"] * eta
-        Z[1::2, 1::2] += ss * op["L"] - sn * op["NK"] + 0.5 * ss * op["G"]
-    return Z
+        tK = ss * op["K"] + 0.5 * sm * op["Gx"]
+        nN = -sn * op["NK"] + 0.5 * ss * op["G"]
+        for f, Z in out.items():
+            aTJ, aNJ, aTM, aNM = formulation_weights(f, eta)
+            Z[0::2, 0::2] += aTJ * ss * op["L"] + aNJ * nN
+            Z[0::2, 1::2] += (aTJ * tK + aNJ * sn * op["NL"]) / eta
+            Z[1::2, 0::2] += -(aTM * tK + aNM * sn * op["NL"]) * eta
+            Z[1::2, 1::2] += aTM * ss * op["L"] + aNM * nN
+    return out
 
 
 def plane_wave(theta_i, phi_i, pol, E0=1.0):
@@ -270,8 +309,9 @@ def plane_wave(theta_i, phi_i, pol, E0=1.0):
     return khat, e * E0
 
 
-def rhs(mesh: Mesh, inc, freq_hz=None):
-    """Excitation vectors, shape [nrhs, 2 ne], rows (J, M) interleaved.
+def rhs(mesh: Mesh, inc, freq_hz=None, formulation="jmcfie"):
+    """Excitation vectors, shape [nrhs, 2 ne], rows (J, M) interleaved, of the
+    given formulation (weights of the host medium, formulation_weights).
     inc: rows (theta_i, phi_i, pol_angle, E0)."""
     k0 = k0_of(freq_hz)
     inc = np.atleast_2d(np.asarray(inc, np.float64))
@@ -297,8 +337,9 @@ def rhs(mesh: Mesh, inc, freq_hz=None):
         m = d["e"]
         ok = m >= 0
         s = s_edge[np.maximum(m, 0)]
-        bJ = s * fE / eta0 + fnH
-        bM = s * eta0 * fH - fnE
+        aTJ, aNJ, aTM, aNM = formulation_weights(formulation, eta0)
+        bJ = aTJ * s * fE / eta0 + aNJ * fnH
+        bM = aTM * s * eta0 * fH - aNM * fnE
         np.add.at(out[ri], 2 * m[ok], bJ[ok])
         np.add.at(out[ri], 2 * m[ok] + 1, bM[ok])
     return out
