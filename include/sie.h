@@ -106,6 +106,15 @@ typedef struct {
   int32_t outer_order;  /* n of the n x n collapsed-Gauss outer rule on
                            singular / near-singular triangle pairs (4) */
   int32_t build_ilu;    /* nonzero: factor ILU(0) of the near field */
+  int32_t formulation;  /* 0 JMCFIE (Eq. 14/16, the paper's); 1 CTF, 2 CNF,
+                           3 PMCHWT: the variants it is compared with.  With
+                           T and N the tangential and normal equations of
+                           medium l (Eqs. 8-11), J-row = sum_l s_l [aTJ T-EFIE /
+                           eta_l - aNJ N-MFIE], M-row = sum_l s_l [aNM N-EFIE -
+                           aTM eta_l T-MFIE]; JMCFIE all weights 1, CTF only T,
+                           CNF only N, PMCHWT aTJ = eta~_l, aTM = 1/eta~_l, no N.
+                           Applies to the near field, the receive patterns and
+                           sie_plane_wave_rhs.  Other values: SIE_EINVAL. */
 } sie_fill_opts;
 
 /* Near-field fill on the GPU in FP64 (Eqs. 23-26 with singularity

@@ -39,7 +39,7 @@ class sie_mlfmm_opts(ctypes.Structure):
 
 
 class sie_fill_opts(ctypes.Structure):
-    _fields_ = [("outer_order", ctypes.c_int32), ("build_ilu", ctypes.c_int32)]
+    _fields_ = [("outer_order", ctypes.c_int32), ("build_ilu", ctypes.c_int32), ("formulation", ctypes.c_int32)]
 
 
 class sie_solve_opts(ctypes.Structure):
@@ -151,8 +151,11 @@ def mlfmm_setup(ctx, levels, digits=3.0):
     _check(ctx, load_library().mlfmm_setup(ctx, ctypes.byref(o)))
 
 
-def sie_fill_nearfield(ctx, outer_order=4, build_ilu=True):
-    o = sie_fill_opts(int(outer_order), 1 if build_ilu else 0)
+FORM_JMCFIE, FORM_CTF, FORM_CNF, FORM_PMCHWT = 0, 1, 2, 3
+
+
+def sie_fill_nearfield(ctx, outer_order=4, build_ilu=True, formulation=FORM_JMCFIE):
+    o = sie_fill_opts(int(outer_order), 1 if build_ilu else 0, int(formulation))
     _check(ctx, load_library().sie_fill_nearfield(ctx, ctypes.byref(o)))
 
 
@@ -284,11 +287,12 @@ class Solver:
     """Owns one context: mesh -> tree -> fill, then operator calls on torch tensors."""
 
     def __init__(self, mesh: dict, levels: int, digits: float = 3.0, freq_hz: float = 299792458.0,
-                 device: int = 0, stream=None, outer_order: int = 4, build_ilu: bool = True):
+                 device: int = 0, stream=None, outer_order: int = 4, build_ilu: bool = True,
+                 formulation: int = FORM_JMCFIE):
         self.ctx = sie_create(device, stream)
         self.ne = sie_build_mesh(self.ctx, mesh["verts"], mesh["tris"], mesh["tri_regions"], mesh["media"], freq_hz)
         mlfmm_setup(self.ctx, levels, digits)
-        sie_fill_nearfield(self.ctx, outer_order, build_ilu)
+        sie_fill_nearfield(self.ctx, outer_order, build_ilu, formulation)
 
     def close(self):
         if getattr(self, "ctx", None) is not None:

@@ -176,6 +176,7 @@ struct sie_ctx {
   double *d_tri_sg = nullptr;    // per triangle: 3 signs * len/(2A)
   int *d_tri_reg = nullptr;      // [nt][2]
   bool graphs_off = false;       // Krylov steps launched eagerly (sie_solve_opts.no_graphs)
+  int form = 0;                  // sie_fill_opts.formulation
   int *d_tri0 = nullptr;         // triangles bounding the host medium (region 0)
   int ntri0 = 0;
   void *d_ff = nullptr;          // far-field work: point positions, point currents, partial sums
@@ -224,6 +225,8 @@ T *dev_upload(sie_ctx *c, const std::vector<T> &v) {
 void ensure_work(sie_ctx *c, int64_t nrhs);
 void *stage(sie_ctx *c, size_t bytes);
 void region_streams(sie_ctx *c);  // creates the per-medium streams and events once
+// weights (aTJ, aNJ, aTM, aNM) of medium l for the context's formulation
+void form_weights(const sie_ctx *c, int l, std::complex<double> w[4]);
 
 // ------------------------------------------------------------------ launchers (fill.cu)
 void launch_near_fill(sie_ctx *c, int region);

@@ -126,7 +126,7 @@ __device__ void tri_potentials(V3 r, const Tri &T, double &I1, V3 &Irho, V3 &Igr
 // block-sparse near matrix.
 __global__ void k_near_fill(const int *pairs, int64_t npairs, const double *tri, const int *te, const double *tsg,
                             const int *treg, int region, zd k, zd eta, const double *quad, int nq,
-                            const int *row_ptr, const int *col, double *near) {
+                            const int *row_ptr, const int *col, double *near, zd aTJ, zd aNJ, zd aTM, zd aNM) {
   int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= npairs) return;
   int p = pairs[3 * id], q = pairs[3 * id + 1], sing = pairs[3 * id + 2];
@@ -235,12 +235,13 @@ __global__ void k_near_fill(const int *pairs, int64_t npairs, const double *tri,
       }
       if (a >= hi || col[a] != nn) continue;  // far pair: carried by the MLFMM
       zd Lij = L[i][j] - ((2.0 * P.c[i]) * (2.0 * Q.c[j])) * (joverk * SG);
-      // J-row = sum_l s_l [T-EFIE_l / eta_l - N-MFIE_l], M-row = sum_l s_l [N-EFIE_l - eta_l T-MFIE_l]
-      zd jj = ss * Lij - sn * NK[i][j];
-      zd kn = ss * K[i][j] + sn * NL[i][j];
-      zd jm = kn * ieta;
-      zd mj = -(kn * eta);
-      zd mm = jj;
+      // J-row = sum_l s_l [aTJ T-EFIE_l / eta_l - aNJ N-MFIE_l],
+      // M-row = sum_l s_l [aNM N-EFIE_l - aTM eta_l T-MFIE_l]
+      const zd tl = ss * Lij, nk = -(sn * NK[i][j]), tk = ss * K[i][j], nl = sn * NL[i][j];
+      zd jj = aTJ * tl + aNJ * nk;
+      zd jm = (aTJ * tk + aNJ * nl) * ieta;
+      zd mj = -((aTM * tk + aNM * nl) * eta);
+      zd mm = aTM * tl + aNM * nk;
       double *o = near + 8 * (size_t)a;
       atomicAdd(o + 0, jj.re); atomicAdd(o + 1, jj.im);
       atomicAdd(o + 2, jm.re); atomicAdd(o + 3, jm.im);
@@ -251,9 +252,12 @@ __global__ void k_near_fill(const int *pairs, int64_t npairs, const double *tri,
 }
 
 // Identity (Gram) terms of both media of each triangle: +1/2 <t, b> per
-// side on the J and M rows, +-1/2 <t, n x b> weighted by eta~ per side.
+// side on the J and M rows (normal parts, weights aNJ / aNM), +-1/2 <t, n x b>
+// weighted by eta~ per side (tangential parts, weights aTJ / aTM).
+// w: per medium (aTJ, aNJ, aTM, aNM).
 __global__ void k_identity(int nt, const double *tri, const int *te, const double *tsg, const int *treg,
-                           const zd *etas, const int *row_ptr, const int *col, double *near, int *err) {
+                           const zd *etas, const zd *w, const int *row_ptr, const int *col, double *near,
+                           int *err) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   Tri P;
@@ -270,10 +274,13 @@ __global__ void k_identity(int nt, const double *tri, const int *te, const doubl
         Gx[i][j] += W * dot(F[i], cross(P.n, F[j]));
       }
   }
-  zd ep = etas[treg[2 * t]], em = etas[treg[2 * t + 1]];
+  const int lp = treg[2 * t], lm = treg[2 * t + 1];
+  zd ep = etas[lp], em = etas[lm];
+  const zd *wp = w + 4 * lp, *wm = w + 4 * lm;
   auto inv = [](zd z) { return zd(z.re, -z.im) * (1.0 / (z.re * z.re + z.im * z.im)); };
-  zd cjm = 0.5 * (inv(ep) - inv(em));
-  zd cmj = -0.5 * (ep - em);
+  zd cjm = 0.5 * (wp[0] * inv(ep) - wm[0] * inv(em));
+  zd cmj = -0.5 * (wp[2] * ep - wm[2] * em);
+  zd cjj = 0.5 * (wp[1] + wm[1]), cmm = 0.5 * (wp[3] + wm[3]);
   for (int i = 0; i < 3; ++i) {
     int m = P.e[i];
     if (m < 0) continue;
@@ -290,11 +297,11 @@ __global__ void k_identity(int nt, const double *tri, const int *te, const doubl
         continue;
       }
       double *o = near + 8 * (size_t)a;
-      zd jm = Gx[i][j] * cjm, mj = Gx[i][j] * cmj;
-      atomicAdd(o + 0, Gm[i][j]);
+      zd jm = Gx[i][j] * cjm, mj = Gx[i][j] * cmj, jj = Gm[i][j] * cjj, mm = Gm[i][j] * cmm;
+      atomicAdd(o + 0, jj.re); atomicAdd(o + 1, jj.im);
       atomicAdd(o + 2, jm.re); atomicAdd(o + 3, jm.im);
       atomicAdd(o + 4, mj.re); atomicAdd(o + 5, mj.im);
-      atomicAdd(o + 6, Gm[i][j]);
+      atomicAdd(o + 6, mm.re); atomicAdd(o + 7, mm.im);
     }
   }
 }
@@ -350,23 +357,26 @@ __global__ void k_patterns(int nb, int K, const int *basis_p, const int *basis_b
 // V(-k) taken at the antipodal sample (theta row L - it, phi column + pi),
 // where the theta unit vector is the same and the phi unit vector reversed.
 // Written over RN in place (each thread reads only its own RN entries).
-__global__ void k_receive_fold(int nb, int K, int L, const int *sign, const zd *V, zd *RN) {
+// With the formulation's tangential and normal weights aT, aN (equal on
+// both rows; PMCHWT's per-row impedance factors are applied at the receive).
+__global__ void k_receive_fold(int nb, int K, int L, const int *sign, const zd *V, zd *RN, double aT, double aN) {
   const int kk = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
   if (kk >= K || i >= nb) return;
   const int nph = 2 * L + 2, it = kk / nph, jp = kk - it * nph;
   const int ka = (L - it) * nph + (jp + L + 1) % nph;
-  const double s = (double)sign[i];
+  const double s = aT * (double)sign[i];
   const zd *Vi = V + (size_t)i * 2 * K;
   zd *Ri = RN + (size_t)i * 2 * K;
   const zd rt = Ri[kk], rp = Ri[K + kk];
-  Ri[kk] = s * Vi[ka] + rp;
-  Ri[K + kk] = (-s) * Vi[K + ka] - rt;
+  Ri[kk] = s * Vi[ka] + aN * rp;
+  Ri[K + kk] = (-s) * Vi[K + ka] - aN * rt;
 }
 
 // Tested excitation, host medium 0 only (Eqs. 20-21 with Eq. 30).
 __global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris, const int *edge_reg,
-                      const double *tri, const int *te, const double *tsg, zd k0, zd eta0, zd *b) {
+                      const double *tri, const int *te, const double *tsg, zd k0, zd eta0, zd *b, zd aTJ, zd aNJ,
+                      zd aTM, zd aNM) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   int r = blockIdx.y;
   if (p >= ne || r >= nrhs) return;
@@ -406,8 +416,8 @@ __global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris,
       fnE += dot(f, cross(T.n, e)) * w;
     }
   }
-  out[0] = (s0 * fE) * ie0 + fnH;
-  out[1] = s0 * (eta0 * fH) - fnE;
+  out[0] = aTJ * ((s0 * fE) * ie0) + aNJ * fnH;
+  out[1] = aTM * (s0 * (eta0 * fH)) - aNM * fnE;
 }
 
 // Far field (Eqs. 27-29), in two steps.  (1) Surface currents at the
@@ -609,9 +619,12 @@ void launch_near_fill(sie_ctx *c, int l) {
   if (R.npairs == 0) return;
   int bs = 128;
   int64_t nb = (R.npairs + bs - 1) / bs;
+  std::complex<double> w[4];
+  form_weights(c, l, w);
   k_near_fill<<<(unsigned)nb, bs, 0, c->stream>>>(R.d_pairs, R.npairs, c->d_tri, c->d_tri_e, c->d_tri_sg,
                                                    c->d_tri_reg, l, to_zd(R.k), to_zd(R.eta), c->d_quad,
-                                                   c->nq_sing, c->d_row_ptr, c->d_col, (double *)c->d_near64);
+                                                   c->nq_sing, c->d_row_ptr, c->d_col, (double *)c->d_near64,
+                                                   to_zd(w[0]), to_zd(w[1]), to_zd(w[2]), to_zd(w[3]));
   SIE_CHECK_LAUNCH();
   c->launches++;
 }
@@ -621,10 +634,18 @@ void launch_identity(sie_ctx *c) {
   std::vector<zd> et(c->nr);
   for (int l = 0; l < c->nr; ++l) et[l] = to_zd(c->etareg[l]);
   zd *d_et = dev_upload(c, et);
+  std::vector<zd> wv(4 * (size_t)c->nr);
+  for (int l = 0; l < c->nr; ++l) {
+    std::complex<double> w[4];
+    form_weights(c, l, w);
+    for (int q = 0; q < 4; ++q) wv[4 * l + q] = to_zd(w[q]);
+  }
+  zd *d_w = dev_upload(c, wv);
   int *d_err = (int *)dev_alloc(c, sizeof(int));
   SIE_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), c->stream));
   k_identity<<<(c->nt + 127) / 128, 128, 0, c->stream>>>(c->nt, c->d_tri, c->d_tri_e, c->d_tri_sg, c->d_tri_reg,
-                                                        d_et, c->d_row_ptr, c->d_col, (double *)c->d_near64, d_err);
+                                                        d_et, d_w, c->d_row_ptr, c->d_col, (double *)c->d_near64,
+                                                        d_err);
   SIE_CHECK_LAUNCH();
   c->launches++;
   int err = 0;
@@ -658,8 +679,11 @@ void launch_patterns(sie_ctx *c, int l) {
   for (int i0 = 0; i0 < R.nb; i0 += 65535) {
     int cnt = std::min(65535, R.nb - i0);
     dim3 grid((K + 127) / 128, cnt);
+    // tangential and normal weights of the folded pattern (PMCHWT: tangential only,
+    // its impedance factors are applied per row at the receive)
+    const double aT = c->form == 2 ? 0.0 : 1.0, aN = (c->form == 0 || c->form == 2) ? 1.0 : 0.0;
     k_receive_fold<<<grid, 128, 0, c->stream>>>(cnt, K, LL.L, R.d_basis_sign + i0, (const zd *)R.d_V64 + (size_t)i0 * 2 * K,
-                                                (zd *)R.d_P64 + (size_t)i0 * 2 * K);
+                                                (zd *)R.d_P64 + (size_t)i0 * 2 * K, aT, aN);
     SIE_CHECK_LAUNCH();
     c->launches++;
   }
@@ -670,8 +694,11 @@ void launch_patterns(sie_ctx *c, int l) {
 void launch_rhs(sie_ctx *c, const double *inc_dev, int nrhs, zd *b) {
   upload_radon();
   dim3 grid((c->ne + 127) / 128, nrhs);
+  std::complex<double> w[4];
+  form_weights(c, 0, w);
   k_rhs<<<grid, 128, 0, c->stream>>>(c->ne, nrhs, inc_dev, c->d_edge_tris, c->d_edge_reg, c->d_tri, c->d_tri_e,
-                                     c->d_tri_sg, to_zd(c->kreg[0]), to_zd(c->etareg[0]), b);
+                                     c->d_tri_sg, to_zd(c->kreg[0]), to_zd(c->etareg[0]), b, to_zd(w[0]),
+                                     to_zd(w[1]), to_zd(w[2]), to_zd(w[3]));
   SIE_CHECK_LAUNCH();
   c->launches++;
 }

@@ -26,6 +26,16 @@ void *dev_alloc(sie_ctx *c, size_t bytes) {
   return p;
 }
 
+void form_weights(const sie_ctx *c, int l, std::complex<double> w[4]) {
+  const std::complex<double> e = c->etareg[l];
+  switch (c->form) {
+    case 1: w[0] = 1.0; w[1] = 0.0; w[2] = 1.0; w[3] = 0.0; break;        // CTF
+    case 2: w[0] = 0.0; w[1] = 1.0; w[2] = 0.0; w[3] = 1.0; break;        // CNF
+    case 3: w[0] = e; w[1] = 0.0; w[2] = 1.0 / e; w[3] = 0.0; break;     // PMCHWT
+    default: w[0] = w[1] = w[2] = w[3] = 1.0;                            // JMCFIE
+  }
+}
+
 void region_streams(sie_ctx *c) {
   if (c->rstream.size() == c->reg.size() && c->ev_fork) return;
   if (!c->ev_fork) SIE_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
@@ -1010,6 +1020,8 @@ static void build_ilu(sie_ctx *c) {
 static void fill_all(sie_ctx *c, const sie_fill_opts *o) {
   const int ne = c->ne, nt = c->nt;
   int on = o ? o->outer_order : 4;
+  c->form = o ? o->formulation : 0;
+  SIE_REQUIRE(c->form >= 0 && c->form <= 3, SIE_EINVAL, "sie_fill_nearfield: formulation must be 0..3");
   SIE_REQUIRE(on >= 2 && on <= 12, SIE_EINVAL, "sie_fill_nearfield: outer_order must be in [2, 12]");
   // geometry tables, internal edge ids
   std::vector<double> tri(22 * (size_t)nt);

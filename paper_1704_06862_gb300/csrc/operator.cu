@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, i
                                                      const int *__restrict__ box_start,
                                                      const int *__restrict__ basis_p, const cx<T> *__restrict__ P,
                                                      const cx<T> *__restrict__ I, cx<T> eta, cx<T> ieta,
-                                                     cx<T> *__restrict__ y) {
+                                                     cx<T> *__restrict__ y, cx<T> cJ, cx<T> cM) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -715,8 +715,8 @@ __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, i
             const cx<T> sj = warp_sum(yj[rr]), sm = warp_sum(ym[rr]);
             if (lane == 0) {
               cx<T> *o = y + ((size_t)(r0 + rr) * ne + p) * 2;
-              o[0] += sj;
-              o[1] -= sm;
+              o[0] += cJ * sj;
+              o[1] -= cM * sm;
             }
           }
       }
@@ -1378,13 +1378,17 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool forked) {
     // receive at the leaves
     {
       std::complex<double> ie = 1.0 / G.eta;
+      // per-row factors of the receive: PMCHWT weights the tangential J-row by
+      // eta~ and the M-row by 1/eta~; the other formulations fold theirs into P
+      const std::complex<double> cj = c->form == 3 ? G.eta : 1.0, cm = c->form == 3 ? 1.0 / G.eta : 1.0;
       auto rec = [&](auto kern, int rb) {
         const size_t smem = STAGES * cb * per_basis + (size_t)rb * 4 * LL.K * sizeof(cx<T>);
         set_smem(kern, smem);
         kern<<<LL.nbox, 256, smem, c->stream>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p,
                                                 (const cx<T> *)tsel<T>::P(G), (const cx<T> *)LL.d_I,
                                                 cx<T>((T)G.eta.real(), (T)G.eta.imag()),
-                                                cx<T>((T)ie.real(), (T)ie.imag()), y);
+                                                cx<T>((T)ie.real(), (T)ie.imag()), y, cx<T>((T)cj.real(), (T)cj.imag()),
+                                                cx<T>((T)cm.real(), (T)cm.imag()));
       };
       if (R == 1) rec(k_disaggregate<T, 1>, 1);
       else rec(k_disaggregate<T, 4>, 4);

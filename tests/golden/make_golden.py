@@ -16,6 +16,9 @@ Stored: seeded x (2 columns), y = Z x, y_near = Z_near x (touching-box
 pattern), plane-wave excitation b, dense-LU solution, bistatic RCS of that
 solution at 361 angles, and the Mie series at the same angles.
 
+  sphere_c1_forms  the sphere_c1 case in the four formulations (JMCFIE, CTF,
+                 CNF, PMCHWT): per formulation the products y and y_near of
+                 the seeded x, the excitation b, the LU currents and their RCS.
   mie_coated_c2  the coated-sphere Mie series alone (core 1.0 lambda0, eps 4;
                  shell 1.5 lambda0, eps 2.56; x-polarised incidence along -z),
                  361 bistatic angles in phi = 0: the reference of the benchmark
@@ -72,6 +75,29 @@ def make(name):
           f"max {err.max():.3f} dB")
 
 
+def make_forms():
+    spec = CASES["sphere_c1"]
+    t0 = time.time()
+    m = Mesh(**spec["mesh"]())
+    Zs = fill.assemble_variants(m)
+    x = geo.random_coefficients(2 * m.ne, 2, seed=1234)
+    mask = tree.near_mask(m, spec["levels"])
+    mk = np.repeat(np.repeat(mask, 2, 0), 2, 1)
+    inc = np.array([[0.0, 0.0, 0.0, 1.0]])
+    obs = geo.bistatic_angles(361)
+    out = dict(x=x, obs=obs, levels=spec["levels"], ne=m.ne)
+    for f, Z in Zs.items():
+        b = fill.rhs(m, inc, formulation=f)
+        xs = solvers.lu_solve(Z, b[0])
+        out[f"y_{f}"] = (Z @ x.T).T
+        out[f"y_near_{f}"] = ((Z * mk) @ x.T).T
+        out[f"b_{f}"] = b
+        out[f"xs_{f}"] = xs
+        out[f"rcs_{f}"] = farfield.rcs(m, xs[None], obs)[0]
+    np.savez_compressed(os.path.join(HERE, "sphere_c1_forms.npz"), **out)
+    print(f"sphere_c1_forms: ne={m.ne} {time.time() - t0:.0f}s")
+
+
 def make_mie_coated_c2():
     obs = geo.bistatic_angles(361)
     ref = mie.coated_bistatic(1.0, 1.5, 4.0, 2.56, obs[:, 0])
@@ -80,8 +106,10 @@ def make_mie_coated_c2():
 
 
 if __name__ == "__main__":
-    for n in (sys.argv[1:] or list(CASES) + ["mie_coated_c2"]):
+    for n in (sys.argv[1:] or list(CASES) + ["sphere_c1_forms", "mie_coated_c2"]):
         if n == "mie_coated_c2":
             make_mie_coated_c2()
+        elif n == "sphere_c1_forms":
+            make_forms()
         else:
             make(n)
