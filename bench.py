@@ -166,6 +166,7 @@ def main():
     ap.add_argument("--batch", type=int, default=16, help="right-hand sides of the batched monostatic leg")
     ap.add_argument("--no-graphs", action="store_true", help="launch every Krylov step eagerly (for profilers)")
     ap.add_argument("--no-solvers", action="store_true", help="skip the solver comparison leg")
+    ap.add_argument("--no-forms", action="store_true", help="skip the formulation comparison leg")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -319,11 +320,44 @@ def main():
     # Mie check of the chosen form
     # (stored Mie series of the coated sphere, written by tests/golden/make_golden.py)
     mie_db = None
+    mie_ref = None
     mie_path = os.path.join(ROOT, "tests", "golden", "mie_coated_c2.npz")
     if theta_i == 0.0 and os.path.exists(mie_path):
-        ref = np.load(mie_path)["mie"]
-        d = 10 * np.log10(rcs[0, :, 0]) - 10 * np.log10(ref)
+        mie_ref = np.load(mie_path)["mie"]
+        d = 10 * np.log10(rcs[0, :, 0]) - 10 * np.log10(mie_ref)
         mie_db = {"mean_abs_db": float(np.mean(np.abs(d))), "max_abs_db": float(np.max(np.abs(d)))}
+    # the formulations the paper compares JMCFIE with, on the same mesh and tree
+    # (each its own context: fill, patterns and ILU(0) of that formulation)
+    forms_cmp = None
+    if not args.no_forms:
+        forms_cmp = {"jmcfie": {"ms_to_rcs": ms, "iters": st["iters"], "converged": st["converged"],
+                                "rcs_vs_mie_mean_db": mie_db["mean_abs_db"] if mie_db else None}}
+        for fname, form in (("ctf", sie.FORM_CTF), ("cnf", sie.FORM_CNF), ("pmchwt", sie.FORM_PMCHWT)):
+            sf = sie.Solver(mesh, levels=LEVELS, digits=DIGITS, stream=stream, formulation=form)
+            bf = sf.vec(1)
+            xf = sf.vec(1)
+            sie.sie_plane_wave_rhs(sf.ctx, inc, bf)
+
+            def one():
+                xf.zero_()
+                stf = sie.gmres_solve(sf.ctx, bf, xf, 1, restart=RESTART, max_iters=1000, tol=TOL,
+                                      prec=sie.SIE_PREC_MIXED, precond=1, check=False, graphs=not args.no_graphs)
+                return stf[0], sie.rcs_farfield_prec(sf.ctx, xf, 1, obs, sie.SIE_PREC_MIXED)
+            one()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stf, rcsf = one()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row = {"ms_to_rcs": e0.elapsed_time(e1), "iters": stf["iters"], "converged": stf["converged"],
+                   "rel_residual": stf["rel_residual"], "rcs_vs_mie_mean_db": None}
+            if mie_ref is not None:
+                row["rcs_vs_mie_mean_db"] = float(np.mean(np.abs(10 * np.log10(rcsf[0, :, 0]) - 10 * np.log10(mie_ref))))
+            forms_cmp[fname] = row
+            del bf, xf
+            sf.close()
 
     # stage timings (CUDA events on the library stream) and the roofline of the dominant kernel
     stages = {}
@@ -362,7 +396,7 @@ def main():
         "iters": st["iters"], "rel_residual": st["rel_residual"], "setup_s": t_setup,
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
                 "d2h_bytes_per_step": int(rcs.nbytes)},
-        "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
+        "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
     }
     if rank == 0:
