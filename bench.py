@@ -34,6 +34,7 @@ LEVELS = 5
 DIGITS = 3.0
 TOL = 1e-4
 RESTART = 50
+NANO_LEVELS = 4
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one k_near_spmv<float> launch on this workload, from one
 # ncu capture (profiles/near_spmv_coated_c2.md); valid while that kernel is unchanged
@@ -167,6 +168,7 @@ def main():
     ap.add_argument("--no-graphs", action="store_true", help="launch every Krylov step eagerly (for profilers)")
     ap.add_argument("--no-solvers", action="store_true", help="skip the solver comparison leg")
     ap.add_argument("--no-forms", action="store_true", help="skip the formulation comparison leg")
+    ap.add_argument("--no-nano", action="store_true", help="skip the plasmonic nanoparticle leg")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -359,6 +361,47 @@ def main():
             del bf, xf
             sf.close()
 
+    # plasmonic coated nanoparticle (negative-permittivity, lossy media; its own
+    # mesh and tree): time to RCS with ILU(0) FGMRES(50) and BiCGStab in the mixed
+    # form, and FGMRES(50) in the plain FP64 form
+    nano = None
+    if not args.no_nano:
+        t0 = time.perf_counter()
+        sn = sie.Solver(geo.workload("nanoparticle"), levels=NANO_LEVELS, digits=DIGITS, stream=stream)
+        torch.cuda.synchronize()
+        nano = {"unknowns": 2 * sn.ne, "levels": NANO_LEVELS, "setup_s": time.perf_counter() - t0}
+        bn = sn.vec(1)
+        xn = sn.vec(1)
+        sie.sie_plane_wave_rhs(sn.ctx, inc, bn)
+        nano_path = os.path.join(ROOT, "tests", "golden", "nanoparticle.npz")
+        mie_n = np.load(nano_path)["mie"] if theta_i == 0.0 and os.path.exists(nano_path) else None
+        for label, method, pr in (("fgmres_ilu", 0, sie.SIE_PREC_MIXED), ("bicgstab_ilu", 1, sie.SIE_PREC_MIXED),
+                                  ("fgmres_ilu_plain_fp64", 0, sie.SIE_PREC_FP64)):
+            def one():
+                xn.zero_()
+                stn = sie.gmres_solve(sn.ctx, bn, xn, 1, restart=RESTART, max_iters=3000, tol=TOL,
+                                      prec=pr, precond=1, check=False, method=method,
+                                      graphs=not args.no_graphs)
+                return stn[0], sie.rcs_farfield_prec(sn.ctx, xn, 1, obs, pr)
+            one()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stn, rcsn = one()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row = {"ms_to_rcs": e0.elapsed_time(e1), "iters": stn["iters"], "converged": stn["converged"],
+                   "rel_residual": stn["rel_residual"], "rcs_vs_mie_mean_db": None, "rcs_vs_mie_max_db": None}
+            if mie_n is not None:
+                dn = np.abs(10 * np.log10(rcsn[0, :, 0]) - 10 * np.log10(mie_n))
+                row["rcs_vs_mie_mean_db"] = float(dn.mean())
+                row["rcs_vs_mie_max_db"] = float(dn.max())
+            nano[label] = row
+        nano["matvec_fp32_ms"] = sie.sie_stage_timing(sn.ctx, 3, 1, sie.SIE_PREC_MIXED, 20)
+        del bn, xn
+        sn.close()
+
     # stage timings (CUDA events on the library stream) and the roofline of the dominant kernel
     stages = {}
     for name, stg in (("near_spmv", 0), ("far_mlfmm", 1), ("ilu_sweeps", 2), ("matvec", 3)):
@@ -396,7 +439,8 @@ def main():
         "iters": st["iters"], "rel_residual": st["rel_residual"], "setup_s": t_setup,
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
                 "d2h_bytes_per_step": int(rcs.nbytes)},
-        "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
+        "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp,
+        "nanoparticle": nano, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
     }
     if rank == 0:

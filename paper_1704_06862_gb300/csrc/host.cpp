@@ -571,8 +571,10 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
         B.il_ptr.push_back((int)B.il_src.size());
       }
     }
-    // directions and tables
-    double kr = R.k.real();
+    // directions and tables; the truncation follows |k|: in a lossy medium
+    // the addition theorem converges at the rate set by the modulus of k d,
+    // not its real part (a metal's k is nearly imaginary)
+    double kr = std::abs(R.k);
     for (int lv = 2; lv <= leaf; ++lv) {
       LevelHost &B = R.lev[lv];
       B.L = trunc_L(kr, B.a, digits);

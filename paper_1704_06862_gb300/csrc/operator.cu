@@ -220,13 +220,13 @@ __device__ __forceinline__ void cta_copy_async(void *dst, const void *src, size_
 // Every level's S and I are laid out [box][J/M][theta/phi][r][k]: for one
 // right-hand side the K samples of a component are contiguous, so a warp over
 // k reads and writes whole lines for any number of right-hand sides.
-// One CTA per leaf box, threads over the directions k (up to AGG_KS per
-// thread).  The box's patterns, one contiguous block, stream through shared
+// One CTA per leaf box, threads over the directions k (up to KS per thread:
+// 2, or 4 for the finely sampled leaves of strongly lossy media).  The box's patterns, one contiguous block, stream through shared
 // memory in chunks of cb bases by asynchronous copies into a two-stage ring,
 // so a whole chunk is in flight at once; the box's signed coefficients are
 // staged in shared memory and each pattern value serves RB right-hand sides.
-constexpr int AGG_KS = 2, STAGES = 2;
-template <typename T, int RB>
+constexpr int STAGES = 2;
+template <typename T, int RB, int KS>
 __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int cb, const int *__restrict__ box_start,
                                                   const int *__restrict__ basis_p, const int *__restrict__ sign,
                                                   const cx<T> *__restrict__ V, const cx<T> *__restrict__ x,
@@ -262,14 +262,14 @@ __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int 
       xs[2 * idx] = xj;
       xs[2 * idx + 1] = xm;
     }
-    cx<T> a0[AGG_KS][RB], a1[AGG_KS][RB], a2[AGG_KS][RB], a3[AGG_KS][RB];
+    cx<T> a0[KS][RB], a1[KS][RB], a2[KS][RB], a3[KS][RB];
     for (int ch = 0; ch < nch; ++ch) {
       cp_async_wait_s<STAGES - 1>();
       __syncthreads();  // chunk ch (and, the first time, the coefficients) visible to all
       const int li0 = ch * cb, m = min(cb, n - li0);
       const cx<T> *v = ring + (size_t)(ch % STAGES) * cb * per;
 #pragma unroll
-      for (int s = 0; s < AGG_KS; ++s) {
+      for (int s = 0; s < KS; ++s) {
         const int k = threadIdx.x + s * blockDim.x;
         if (k >= K) break;
         for (int li = 0; li < m; ++li) {
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int 
     }
     cp_async_wait_s<0>();
 #pragma unroll
-    for (int s = 0; s < AGG_KS; ++s) {
+    for (int s = 0; s < KS; ++s) {
       const int k = threadIdx.x + s * blockDim.x;
       if (k >= K) break;
 #pragma unroll
@@ -1283,7 +1283,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool forked) {
     // aggregation at the leaf level
     const size_t per_basis = (size_t)2 * LL.K * sizeof(cx<T>);
     const int cb = (int)std::max<size_t>(1, std::min<size_t>(32, (32 * 1024) / per_basis));  // bases per chunk
-    SIE_REQUIRE(LL.K <= AGG_KS * 256, SIE_EINVAL, "MLFMM: too many leaf directions for the aggregation kernel");
+    SIE_REQUIRE(LL.K <= 4 * 256, SIE_EINVAL, "MLFMM: too many leaf directions for the aggregation kernel");
     {
       auto agg = [&](auto kern, int rb) {
         const size_t smem = STAGES * cb * per_basis + (size_t)G.max_leaf * rb * 2 * sizeof(cx<T>);
@@ -1291,8 +1291,10 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool forked) {
         kern<<<LL.nbox, 256, smem, st>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p, G.d_basis_sign,
                                                 (const cx<T> *)tsel<T>::V(G), x, (cx<T> *)LL.d_S);
       };
-      if (R == 1) agg(k_aggregate<T, 1>, 1);
-      else agg(k_aggregate<T, 4>, 4);
+      // more than 512 leaf directions: four per thread, one right-hand side per pass
+      if (LL.K > 2 * 256) agg(k_aggregate<T, 1, 4>, 1);
+      else if (R == 1) agg(k_aggregate<T, 1, 2>, 1);
+      else agg(k_aggregate<T, 4, 2>, 4);
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
@@ -1390,7 +1392,9 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool forked) {
                                                 cx<T>((T)ie.real(), (T)ie.imag()), y, cx<T>((T)cj.real(), (T)cj.imag()),
                                                 cx<T>((T)cm.real(), (T)cm.imag()));
       };
-      if (R == 1) rec(k_disaggregate<T, 1>, 1);
+      // blocks of right-hand sides four at a time while the box's fields fit in shared memory
+      const bool fits4 = STAGES * cb * per_basis + (size_t)4 * 4 * LL.K * sizeof(cx<T>) <= 227 * 1024;
+      if (R == 1 || !fits4) rec(k_disaggregate<T, 1>, 1);
       else rec(k_disaggregate<T, 4>, 4);
       SIE_CHECK_LAUNCH();
       c->launches++;

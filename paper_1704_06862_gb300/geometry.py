@@ -118,6 +118,14 @@ def tetra_body(size=0.3, eps_r=4.0):
     return dict(verts=v, tris=t, tri_regions=regions, media=media)
 
 
+# Plasmonic coated nanoparticle: silver-like core in a gold-like shell at
+# 545 THz (lambda0 = 550 nm).  Assumed round permittivities with negative real
+# parts and loss (e^{+jwt}: eps'' < 0), of the size of noble-metal data at
+# that wavelength; not tabulated measurements.
+NANO_EPS_CORE = -10.0 - 0.8j
+NANO_EPS_SHELL = -5.0 - 2.0j
+
+
 # Named workloads (sizes follow the configurations the solver is measured on)
 def workload(name: str):
     if name == "sphere_c1":      # radius 0.5 lambda0, eps 4, 1280 tri, 3840 unknowns
@@ -126,6 +134,8 @@ def workload(name: str):
         return coated_sphere(30, 20)
     if name == "coated_small":   # reduced coated sphere, ~12.5k unknowns
         return coated_sphere(12, 8)
+    if name == "nanoparticle":   # plasmonic coated sphere (core 230, shell 250 at 550 nm), 30 720 unknowns
+        return coated_sphere(16, 16, 250 / 550, 230 / 550, NANO_EPS_SHELL, NANO_EPS_CORE)
     if name == "coated_tiny":    # coated sphere small enough for dense CPU checks
         return coated_sphere(6, 4)
     if name == "sphere_tiny":

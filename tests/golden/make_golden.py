@@ -12,6 +12,10 @@ Cases
   sphere_lossy eps_r = 6 - 0.6j sphere (complex wavenumber), radius 0.5, nu = 8.
   coated_r075  coated sphere, core 0.5 (eps 4), shell 0.75 (eps 2.56), nu 12/8
                (12480 unknowns, three media); 4-level tree (leaf 0.1875).
+  nanoparticle plasmonic coated sphere: core 230/550 (eps -10 - 0.8j), shell
+               250/550 (eps -5 - 2j), nu 6/6 (4320 unknowns); 3-level tree.
+               Its Mie series is also the reference of the finer
+               nanoparticle workload (same radii, media and angles).
 Stored: seeded x (2 columns), y = Z x, y_near = Z_near x (touching-box
 pattern), plane-wave excitation b, dense-LU solution, bistatic RCS of that
 solution at 361 angles, and the Mie series at the same angles.
@@ -46,6 +50,12 @@ CASES = {
     "sphere_lossy": dict(mesh=lambda: geo.homogeneous_sphere(nu=8, radius=0.5, eps_r=6.0 - 0.6j), levels=3,
                          radius=0.5, eps=6.0 - 0.6j),
     "coated_r075": dict(mesh=lambda: geo.coated_sphere(12, 8, 0.75, 0.5, 2.56, 4.0), levels=4, coated=(0.5, 0.75)),
+    # plasmonic coated nanoparticle: silver-like core (230 nm) in a gold-like
+    # shell (20 nm) at 545 THz, scaled to lambda0 = 550 nm; permittivities are
+    # assumed round values with negative real parts (e^{+jwt}, loss eps'' < 0)
+    "nanoparticle": dict(mesh=lambda: geo.coated_sphere(6, 6, 250 / 550, 230 / 550, geo.NANO_EPS_SHELL,
+                                                        geo.NANO_EPS_CORE),
+                         levels=3, coated=(230 / 550, 250 / 550), eps=(geo.NANO_EPS_CORE, geo.NANO_EPS_SHELL)),
 }
 
 
@@ -65,7 +75,8 @@ def make(name):
     obs = geo.bistatic_angles(361)
     rcs = farfield.rcs(m, xs[None], obs)[0]
     if "coated" in spec:
-        ref = mie.coated_bistatic(spec["coated"][0], spec["coated"][1], 4.0, 2.56, obs[:, 0])
+        ec, es = spec.get("eps", (4.0, 2.56))
+        ref = mie.coated_bistatic(spec["coated"][0], spec["coated"][1], ec, es, obs[:, 0])
     else:
         ref = mie.sphere_bistatic(spec["radius"], spec.get("eps", 4.0), obs[:, 0])
     np.savez_compressed(os.path.join(HERE, f"{name}.npz"), x=x, y=y, y_near=y_near, b=b, xs=xs, obs=obs,

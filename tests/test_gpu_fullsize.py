@@ -1,5 +1,7 @@
-"""Parity at the measured workload's full size (coated sphere, 78 000
-unknowns, 5-level MLFMM, the launch configuration bench.py times): the product
+"""Parity at the measured workloads' full size (coated sphere, 78 000
+unknowns, 5-level MLFMM, the launch configuration bench.py times; plasmonic
+coated nanoparticle, 30 720 unknowns, 4-level MLFMM, bench.py's nanoparticle
+leg): the product
 is checked on rows the oracle computes one by one (dense JMCFIE rows of the
 sampled bases against all bases), and the near-field entries of those rows
 element by element.
@@ -18,19 +20,20 @@ from oracle import fill, tree  # noqa: E402
 from oracle.rwg import Mesh  # noqa: E402
 
 
-@pytest.fixture(scope="module")
-def full():
+@pytest.fixture(scope="module", params=[("coated_c2", 5), ("nanoparticle", 4)])
+def full(request):
     import __graft_entry__ as g
     g.build()
-    mesh = geo.workload("coated_c2")
-    s = sie.Solver(mesh, levels=5, digits=3.0)
+    name, levels = request.param
+    mesh = geo.workload(name)
+    s = sie.Solver(mesh, levels=levels, digits=3.0)
     m = Mesh(**mesh)
-    yield s, m
+    yield s, m, levels
     s.close()
 
 
 def test_sampled_rows(full):
-    s, m = full
+    s, m, levels = full
     assert s.ne == m.ne
     rng = np.random.default_rng(2017)
     rows = np.sort(rng.choice(m.ne, 8, replace=False))
@@ -43,7 +46,7 @@ def test_sampled_rows(full):
     torch.cuda.synchronize()
     got = y.cpu().numpy().reshape(m.ne, 2)[rows].reshape(-1)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    print(f"full-size sampled rows: rel L2 {err:.2e}")
+    print(f"full-size sampled rows ({m.ne} bases): rel L2 {err:.2e}")
     assert err < 1e-3
     # near entries of those rows, element by element
     r, c, v = sie.sie_near_export(s.ctx)
@@ -52,6 +55,6 @@ def test_sampled_rows(full):
     li = np.array([loc[e] for e in r[sel]])
     refb = np.stack([Zr[2 * li + a, 2 * c[sel] + bb] for a in range(2) for bb in range(2)], axis=1)
     assert np.max(np.abs(v[sel] - refb)) < 1e-9 * np.max(np.abs(Zr))
-    ijk = tree.box_coords(m, 5)
+    ijk = tree.box_coords(m, levels)
     near = np.abs(ijk[rows][:, None, :] - ijk[None, :, :]).max(axis=2) <= 1
     assert sel.sum() == near.sum()
