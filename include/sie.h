@@ -57,8 +57,13 @@ typedef enum {
 
 typedef enum {
   SIE_PREC_FP64 = 0,   /* plain form: every step in FP64 */
-  SIE_PREC_MIXED = 1   /* near field, translations, patterns, ILU in FP32 complex;
-                          Arnoldi, Givens, true residual in FP64 */
+  SIE_PREC_MIXED = 1,  /* near field, translations, patterns, ILU in FP32 complex;
+                          Arnoldi, Givens, true residual in FP64 vectors */
+  SIE_PREC_NEAR64 = 2  /* products only (mlfmm_matvec, sie_matvec_parts, the
+                          whole-product stage timing): FP64 near field, FP32
+                          far field (patterns, translations, receive sums)
+                          added into the FP64 product; the true-residual
+                          operator of the mixed form */
 } sie_prec;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -170,7 +175,8 @@ sie_status sie_plane_wave_rhs(sie_ctx *ctx, const double *inc_host, int64_t nrhs
 typedef struct {
   int32_t restart;     /* Krylov dimension per cycle (50) */
   int32_t max_iters;   /* total inner iterations per right-hand side */
-  double tol;          /* relative residual ||b - A x|| / ||b|| (FP64 operator) */
+  double tol;          /* relative true residual ||b - A x|| / ||b||, A the
+                          residual operator (below) */
   int32_t prec;        /* sie_prec of the inner operator and preconditioner */
   int32_t precond;     /* 0: none, 1: ILU(0), 2: ILU(0) followed by the learned
                           correction (needs nnprec_train or nnprec_params; the
@@ -185,12 +191,21 @@ typedef struct {
                           captured once as a CUDA graph and replayed; 1: every
                           step is launched eagerly (same kernels, same results;
                           for tools that cannot follow graph launches) */
+  int32_t residual_far_fp64;  /* operator of the true residual (restarts and
+                          the convergence decision) in the mixed form: 0
+                          SIE_PREC_NEAR64 (FP64 near field, FP32 far field,
+                          FP64 vectors) when tol >= 5e-5, the whole FP64
+                          operator for smaller tol (the FP32 far field puts
+                          the NEAR64 product within a few 1e-6 of the FP64
+                          one, a floor for the residuals it can certify); 1
+                          the whole FP64 operator.  The plain form always
+                          uses the FP64 operator. */
 } sie_solve_opts;
 
 typedef struct {
   int32_t iters;        /* inner iterations used */
   int32_t restarts;     /* restart cycles (true-residual recomputations) */
-  double rel_residual;  /* final true relative residual, FP64 operator */
+  double rel_residual;  /* final true relative residual, residual operator */
   int32_t converged;    /* 1 if rel_residual <= tol */
 } sie_solve_stats;
 

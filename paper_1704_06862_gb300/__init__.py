@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libsie.so")
 
 SIE_PREC_FP64 = 0
 SIE_PREC_MIXED = 1
+SIE_PREC_NEAR64 = 2   # products only: FP64 near field + FP32 far field into the FP64 product
 
 STATUS = {0: "SIE_OK", 1: "SIE_EINVAL", 2: "SIE_ENOMEM", 3: "SIE_ECUDA", 4: "SIE_ESTATE", 5: "SIE_ENOTCONV",
           6: "SIE_EBREAKDOWN", 7: "SIE_ETIMEOUT", 8: "SIE_EZEROPIVOT"}
@@ -45,7 +46,7 @@ class sie_fill_opts(ctypes.Structure):
 class sie_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("prec", ctypes.c_int32), ("precond", ctypes.c_int32), ("method", ctypes.c_int32),
-                ("no_graphs", ctypes.c_int32)]
+                ("no_graphs", ctypes.c_int32), ("residual_far_fp64", ctypes.c_int32)]
 
 
 class sie_solve_stats(ctypes.Structure):
@@ -186,9 +187,9 @@ SOLVE_FGMRES, SOLVE_BICGSTAB, SOLVE_CGS = 0, 1, 2
 
 
 def gmres_solve(ctx, b, x, nrhs, restart=50, max_iters=1000, tol=1e-4, prec=SIE_PREC_FP64, precond=1,
-                check=True, graphs=True, method=SOLVE_FGMRES):
+                check=True, graphs=True, method=SOLVE_FGMRES, residual_far_fp64=False):
     o = sie_solve_opts(int(restart), int(max_iters), float(tol), int(prec), int(precond), int(method),
-                       0 if graphs else 1)
+                       0 if graphs else 1, 1 if residual_far_fp64 else 0)
     st = (sie_solve_stats * int(nrhs))()
     rc = load_library().gmres_solve(ctx, _ptr(b), _ptr(x), int(nrhs), ctypes.byref(o), st)
     stats = [dict(iters=s.iters, restarts=s.restarts, rel_residual=s.rel_residual, converged=bool(s.converged))

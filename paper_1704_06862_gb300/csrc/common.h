@@ -240,8 +240,9 @@ void launch_to_f32(sie_ctx *c, const double *src, float *dst, int64_t n);
 // ------------------------------------------------------------------ launchers (operator.cu)
 template <typename T>
 void op_near(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool accumulate);
-template <typename T>
-void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool forked = false);  // forked: far_fork already recorded
+// forked: far_fork already recorded; TY: type of the product y the receives add into
+template <typename T, typename TY = T>
+void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked = false);
 void far_fork(sie_ctx *c);
 template <typename T>
 void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs);
@@ -262,8 +263,9 @@ struct Recorder {  // training pairs taken at the restarts of one solve
   int cap;
   int *count;
 };
+// prec: inner operator and preconditioner; rprec: operator of the true residual
 sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int max_iters, double tol,
-                              sie_prec prec, int precond, Recorder *rec, sie_solve_stats *st);
+                              sie_prec prec, sie_prec rprec, int precond, Recorder *rec, sie_solve_stats *st);
 void op_sub(sie_ctx *c, const zd *a, const zd *b, zd *out, int64_t n);
 void graphs_free(sie_ctx *c);
 

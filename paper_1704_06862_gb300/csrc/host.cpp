@@ -1171,7 +1171,8 @@ extern "C" sie_status sie_matvec_parts(sie_ctx *c, const void *x, void *y, int64
   return guard(c, [&] {
     SIE_REQUIRE(c->have_fill, SIE_ESTATE, "matvec: call sie_fill_nearfield first");
     SIE_REQUIRE(x && y && x != y && nrhs >= 1 && nrhs <= 4096, SIE_EINVAL, "matvec: bad buffers or nrhs");
-    SIE_REQUIRE(prec == SIE_PREC_FP64 || prec == SIE_PREC_MIXED, SIE_EINVAL, "matvec: bad precision");
+    SIE_REQUIRE(prec == SIE_PREC_FP64 || prec == SIE_PREC_MIXED || prec == SIE_PREC_NEAR64, SIE_EINVAL,
+                "matvec: bad precision");
     SIE_REQUIRE(parts >= 1 && parts <= 3, SIE_EINVAL, "matvec: parts must be 1, 2 or 3");
     ensure_work(c, nrhs);
     op_permute_in(c, (const zd *)x, (zd *)c->d_xi, (int)nrhs);
@@ -1219,6 +1220,9 @@ extern "C" sie_status gmres_solve(sie_ctx *c, const void *b, void *x, int64_t nr
                 "gmres_solve: bad options");
     SIE_REQUIRE(o->precond >= 0 && o->precond <= 2, SIE_EINVAL, "gmres_solve: precond must be 0, 1 or 2");
     SIE_REQUIRE(o->method >= 0 && o->method <= 2, SIE_EINVAL, "gmres_solve: method must be 0, 1 or 2");
+    SIE_REQUIRE(o->prec == SIE_PREC_FP64 || o->prec == SIE_PREC_MIXED, SIE_EINVAL, "gmres_solve: prec must be 0 or 1");
+    SIE_REQUIRE(o->residual_far_fp64 == 0 || o->residual_far_fp64 == 1, SIE_EINVAL,
+                "gmres_solve: residual_far_fp64 must be 0 or 1");
     SIE_REQUIRE(o->method == 0 || o->precond <= 1, SIE_EINVAL,
                 "gmres_solve: the learned correction needs FGMRES (a variable preconditioner)");
     SIE_REQUIRE(o->precond == 0 || c->ilu.ready, SIE_ESTATE, "gmres_solve: ILU requested but not built");
@@ -1277,6 +1281,8 @@ extern "C" sie_status sie_stage_timing(sie_ctx *c, int32_t stage, int64_t nrhs, 
     SIE_REQUIRE(ms && stage >= 0 && stage <= 3 && nrhs >= 1 && nrhs <= 4096 && reps >= 1, SIE_EINVAL,
                 "sie_stage_timing: bad arguments");
     SIE_REQUIRE(stage != 2 || c->ilu.ready, SIE_ESTATE, "sie_stage_timing: no ILU factors");
+    SIE_REQUIRE(prec == SIE_PREC_FP64 || prec == SIE_PREC_MIXED || (prec == SIE_PREC_NEAR64 && stage == 3),
+                SIE_EINVAL, "sie_stage_timing: prec 0 or 1 (2 for the whole product only)");
     ensure_work(c, nrhs);
     size_t n = (size_t)nrhs * c->ne * 2;
     SIE_CUDA(cudaMemsetAsync(c->d_xi, 0, n * sizeof(zd), c->stream));
@@ -1300,7 +1306,9 @@ extern "C" sie_status sie_stage_timing(sie_ctx *c, int32_t stage, int64_t nrhs, 
           else op_ilu<float>(c, (const zf *)c->d_xf, (zf *)c->d_yf, (int)nrhs);
           break;
         default:
-          if (f64) {
+          if (prec == SIE_PREC_NEAR64) {
+            apply_matvec(c, (const zd *)c->d_xi, (zd *)c->d_yi, (int)nrhs, SIE_PREC_NEAR64, 3);
+          } else if (f64) {
             op_near<double>(c, (const zd *)c->d_xi, (zd *)c->d_yi, (int)nrhs, false);
             op_far<double>(c, (const zd *)c->d_xi, (zd *)c->d_yi, (int)nrhs);
           } else {

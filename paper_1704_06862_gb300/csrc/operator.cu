@@ -655,12 +655,14 @@ __global__ void __launch_bounds__(128) k_m2l_group(int K, int nrhs, const int *_
 // with its combined receive pattern P (antipodal radiation pattern for the
 // tangential test, t x n pattern for the n x operators, signs folded in).
 // The box's P block streams through shared memory as in k_aggregate.
-template <typename T, int RB>
+// The sums are formed in T and added into y of type TY (FP32 far field into
+// an FP64 product for the true residual of the mixed form).
+template <typename T, int RB, typename TY>
 __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, int cb,
                                                      const int *__restrict__ box_start,
                                                      const int *__restrict__ basis_p, const cx<T> *__restrict__ P,
                                                      const cx<T> *__restrict__ I, cx<T> eta, cx<T> ieta,
-                                                     cx<T> *__restrict__ y, cx<T> cJ, cx<T> cM) {
+                                                     cx<TY> *__restrict__ y, cx<T> cJ, cx<T> cM) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -714,9 +716,9 @@ __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, i
           if (rr < nr) {
             const cx<T> sj = warp_sum(yj[rr]), sm = warp_sum(ym[rr]);
             if (lane == 0) {
-              cx<T> *o = y + ((size_t)(r0 + rr) * ne + p) * 2;
-              o[0] += cJ * sj;
-              o[1] -= cM * sm;
+              cx<TY> *o = y + ((size_t)(r0 + rr) * ne + p) * 2;
+              o[0] += cx<TY>(cJ * sj);
+              o[1] -= cx<TY>(cM * sm);
             }
           }
       }
@@ -1263,8 +1265,8 @@ void op_near(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool accumulate) {
   c->launches++;
 }
 
-template <typename T>
-void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool forked) {
+template <typename T, typename TY>
+void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
   const int leaf = c->levels - 1;
   const int R = nrhs;
   if (c->levels < 3) return;  // every basis pair is near: no far field
@@ -1394,8 +1396,8 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool forked) {
       };
       // blocks of right-hand sides four at a time while the box's fields fit in shared memory
       const bool fits4 = STAGES * cb * per_basis + (size_t)4 * 4 * LL.K * sizeof(cx<T>) <= 227 * 1024;
-      if (R == 1 || !fits4) rec(k_disaggregate<T, 1>, 1);
-      else rec(k_disaggregate<T, 4>, 4);
+      if (R == 1 || !fits4) rec(k_disaggregate<T, 1, TY>, 1);
+      else rec(k_disaggregate<T, 4, TY>, 4);
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
@@ -1493,6 +1495,15 @@ void apply_matvec(sie_ctx *c, const zd *x, zd *y, int nrhs, sie_prec prec, int p
     if (parts & 1) op_near<double>(c, x, y, nrhs, false);
     else SIE_CUDA(cudaMemsetAsync(y, 0, n * sizeof(zd), c->stream));
     if (parts & 2) op_far<double>(c, x, y, nrhs, true);
+  } else if (prec == SIE_PREC_NEAR64) {
+    // FP64 near field; the far field from an FP32 copy of x, its receives
+    // adding into the FP64 product
+    zf *xf = (zf *)c->d_xf;
+    if (parts & 2) op_d2f(c, x, xf, n);
+    if (parts & 2) far_fork(c);
+    if (parts & 1) op_near<double>(c, x, y, nrhs, false);
+    else SIE_CUDA(cudaMemsetAsync(y, 0, n * sizeof(zd), c->stream));
+    if (parts & 2) op_far<float, double>(c, xf, y, nrhs, true);
   } else {
     zf *xf = (zf *)c->d_xf, *yf = (zf *)c->d_yf;
     op_d2f(c, x, xf, n);
@@ -1518,7 +1529,8 @@ void apply_ilu(sie_ctx *c, const zd *r, zd *z, int nrhs, sie_prec prec) {
 
 template void op_near<double>(sie_ctx *, const zd *, zd *, int, bool);
 template void op_near<float>(sie_ctx *, const zf *, zf *, int, bool);
-template void op_far<double>(sie_ctx *, const zd *, zd *, int, bool);
-template void op_far<float>(sie_ctx *, const zf *, zf *, int, bool);
+template void op_far<double, double>(sie_ctx *, const zd *, zd *, int, bool);
+template void op_far<float, float>(sie_ctx *, const zf *, zf *, int, bool);
+template void op_far<float, double>(sie_ctx *, const zf *, zd *, int, bool);
 template void op_ilu<double>(sie_ctx *, const zd *, zd *, int);
 template void op_ilu<float>(sie_ctx *, const zf *, zf *, int);

@@ -3,8 +3,10 @@
 // Gram-Schmidt with one re-orthogonalisation, and the true residual at every
 // restart are FP64 on the device; the Hessenberg least-squares problem (Givens
 // rotations) is solved on the host.  With SIE_PREC_MIXED the inner operator
-// and preconditioner run in FP32 while the restart residual uses the FP64
-// operator, which makes the restarts an iterative refinement.
+// and preconditioner run in FP32 while the restart residual is recomputed in
+// FP64 vectors with the FP64 near field (SIE_PREC_NEAR64: far field in FP32,
+// added into the FP64 product; or the whole FP64 operator on request), which
+// makes the restarts an iterative refinement.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -257,7 +259,7 @@ void graphs_free(sie_ctx *c) {
 // (one right-hand side), the iterate and true residual of every restart
 // before convergence are copied out as training pairs.
 sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int max_iters, double tol,
-                              sie_prec prec, int precond, Recorder *rec, sie_solve_stats *st) {
+                              sie_prec prec, sie_prec rprec, int precond, Recorder *rec, sie_solve_stats *st) {
   const int n = 2 * c->ne;
   const size_t vs = (size_t)R * n;
   ensure_work(c, R);
@@ -302,11 +304,11 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
   for (int r = 0; r < R; ++r) x_zero = x_zero && xn[r] == 0.0;
   bool first = true;
   for (;;) {
-    // true residual with the FP64 operator (r = b for a zero initial guess)
+    // true residual with the residual operator rprec (r = b for a zero initial guess)
     if (first && x_zero) {
       SIE_CUDA(cudaMemcpyAsync(w, b, vs * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
     } else {
-      apply_matvec(c, x, w, R, SIE_PREC_FP64, 3);
+      apply_matvec(c, x, w, R, rprec, 3);
       k_sub<<<std::min(152 * 16, (int)((vs + 255) / 256)), 256, 0, c->stream>>>((int64_t)vs, b, w, w);
       g.launch_check();
     }
@@ -469,11 +471,11 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
 // right-hand sides in lockstep on internal-order FP64 vectors; the inner
 // operator and preconditioner in `prec`.  Scalars per right-hand side on the
 // host.  When the recurrence residual of every active right-hand side is
-// below tol, the true residual b - A x with the FP64 operator decides; a
+// below tol, the true residual b - A x with the residual operator decides; a
 // right-hand side that is not there restarts from its current x (iterative
 // refinement).  Breakdown (a zero inner product) also restarts.
 sie_status run_bicg_internal(sie_ctx *c, const zd *b, zd *x, int R, int max_iters, double tol, sie_prec prec,
-                             int precond, int method, sie_solve_stats *st) {
+                             sie_prec rprec, int precond, int method, sie_solve_stats *st) {
   const int n = 2 * c->ne;
   const size_t vs = (size_t)R * n;
   ensure_work(c, R);
@@ -531,11 +533,11 @@ sie_status run_bicg_internal(sie_ctx *c, const zd *b, zd *x, int R, int max_iter
   for (int q = 0; q < R; ++q) x_zero = x_zero && xn2[q].real() == 0.0;
   int stalls = 0;  // restarts in a row without a single step (repeated breakdown)
   for (bool first_cycle = true;; first_cycle = false) {
-    // true residual with the FP64 operator (r = b for a zero initial guess)
+    // true residual with the residual operator rprec (r = b for a zero initial guess)
     if (first_cycle && x_zero) {
       SIE_CUDA(cudaMemcpyAsync(r, b, vs * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream));
     } else {
-      apply_matvec(c, x, w, R, SIE_PREC_FP64, 3);
+      apply_matvec(c, x, w, R, rprec, 3);
       axpy(b, mone, w, r, 0);
     }
     dots(r, r, rn2);
@@ -680,14 +682,23 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
   op_permute_in(c, b_user, b, R);
   op_permute_in(c, x_user, x, R);
   sie_prec prec = o->prec == 1 ? SIE_PREC_MIXED : SIE_PREC_FP64;
+  // true residual: the plain form keeps every step in FP64.  The mixed form
+  // uses the FP64 near field with the FP32 far field, whose rounding leaves
+  // the residual operator within a few 1e-6 (relative) of the FP64 operator:
+  // it decides convergence only for tolerances well above that floor, the
+  // whole FP64 operator below it (or on request).
+  constexpr double kNear64MinTol = 5e-5;
+  sie_prec rprec = prec == SIE_PREC_MIXED && !o->residual_far_fp64 && o->tol >= kNear64MinTol ? SIE_PREC_NEAR64
+                                                                                              : SIE_PREC_FP64;
   struct Eager {  // eager steps for this call only, also when it throws
     sie_ctx *c;
     ~Eager() { c->graphs_off = false; }
   } eager{c};
   c->graphs_off = o->no_graphs != 0;
   sie_status rc = o->method == 0
-                      ? run_gmres_internal(c, b, x, R, o->restart, o->max_iters, o->tol, prec, o->precond, nullptr, st)
-                      : run_bicg_internal(c, b, x, R, o->max_iters, o->tol, prec, o->precond, o->method, st);
+                      ? run_gmres_internal(c, b, x, R, o->restart, o->max_iters, o->tol, prec, rprec, o->precond,
+                                           nullptr, st)
+                      : run_bicg_internal(c, b, x, R, o->max_iters, o->tol, prec, rprec, o->precond, o->method, st);
   op_permute_out(c, x, x_user, R);
   SIE_CUDA(cudaStreamSynchronize(c->stream));
   return rc;

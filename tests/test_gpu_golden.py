@@ -7,7 +7,13 @@ fill, dense product, dense LU, far field, Mie series).
 Tolerances:
 * near part of the product: same integrals on both sides -> 1e-12.
 * whole product, FP64 MLFMM: relative L2 1e-3 (the far-field accuracy target).
-* FP32 (mixed) product vs FP64 product: 1e-4.
+* FP32 (mixed) product vs FP64 product: 1e-4; the true-residual product of
+  the mixed form (FP64 near field, FP32 far field into the FP64 product):
+  near part 1e-12, whole product vs FP64 1e-5.
+* mixed-form solves: the FP64-operator residual of the returned currents
+  within 1.5 x tol at tol 1e-6 (there the true residual uses the whole FP64
+  operator) and within 1.05 x tol at tol 1e-4 (FP64 near field + FP32 far
+  field, a few 1e-6 from the FP64 operator).
 * currents solved to 1e-6 vs dense LU: 1e-3 relative L2.
 * RCS of the solved currents vs the oracle RCS of the LU currents: 0.2 dB on
   angles within 30 dB of the peak.
@@ -75,6 +81,12 @@ def test_product_near_far_and_mixed(case):
     assert err < 1e-3
     sie.mlfmm_matvec(s.ctx, x, y, 2, sie.SIE_PREC_MIXED)
     assert rel(_host(y), y64) < 1e-4
+    sie.sie_matvec_parts(s.ctx, x, y, 2, sie.SIE_PREC_NEAR64, parts=1)
+    assert rel(_host(y), d["y_near"]) < 1e-12
+    sie.mlfmm_matvec(s.ctx, x, y, 2, sie.SIE_PREC_NEAR64)
+    e64 = rel(_host(y), y64)
+    print(f"{name}: true-residual product (FP64 near, FP32 far) vs FP64 product rel L2 {e64:.2e}")
+    assert e64 < 1e-5
 
 
 @pytest.mark.parametrize("prec", [sie.SIE_PREC_FP64, sie.SIE_PREC_MIXED])
@@ -96,6 +108,12 @@ def test_solution_and_rcs(case, prec):
           f"{db.max():.3f} dB, vs Mie mean {mie_db.mean():.3f} dB")
     assert err < 1e-3
     assert db.max() < 0.2
+    if prec == sie.SIE_PREC_MIXED:
+        y = torch.zeros_like(b)
+        sie.mlfmm_matvec(s.ctx, x, y, 1, sie.SIE_PREC_FP64)
+        r64 = rel(_host(y), _host(b))
+        print(f"{name}: FP64-operator residual {r64:.2e} (solver's {st[0]['rel_residual']:.2e})")
+        assert r64 < 1.5e-6
 
 
 def test_batched_solve_equals_single_solves(case):
@@ -153,6 +171,30 @@ def test_block_product_equals_single_products(case):
             y1 = torch.zeros_like(xb[r:r + 1])
             sie.mlfmm_matvec(s.ctx, xb[r:r + 1].contiguous(), y1, 1, prec)
             assert rel(yb[r], _host(y1)[0]) < tol
+
+
+def test_residual_operator_choice(case):
+    """At tol 1e-4 the mixed form's true residual uses the FP64 near field +
+    FP32 far field (restarts every 10 iterations, so it decides several
+    times): it takes the iterations of the whole-FP64 residual to within two,
+    and the currents it returns meet the tolerance under the FP64 operator
+    too (within 5 %)."""
+    name, s, d = case
+    if name != "coated_r075":
+        pytest.skip("one case suffices")
+    b = torch.zeros((1, s.ne, 2), dtype=torch.complex128, device="cuda")
+    sie.sie_plane_wave_rhs(s.ctx, [[0.0, 0.0, 0.0, 1.0]], b)
+    its = []
+    for full in (True, False):
+        x = torch.zeros_like(b)
+        st = sie.gmres_solve(s.ctx, b, x, 1, restart=10, max_iters=1000, tol=1e-4, prec=sie.SIE_PREC_MIXED,
+                             precond=1, residual_far_fp64=full)
+        assert st[0]["converged"] and st[0]["restarts"] >= 1
+        its.append(st[0]["iters"])
+        y = torch.zeros_like(b)
+        sie.mlfmm_matvec(s.ctx, x, y, 1, sie.SIE_PREC_FP64)
+        assert rel(_host(y), _host(b)) < 1.05e-4
+    assert abs(its[0] - its[1]) <= 2
 
 
 @pytest.mark.parametrize("method", [sie.SOLVE_BICGSTAB, sie.SOLVE_CGS])
