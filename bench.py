@@ -169,6 +169,8 @@ def main():
     ap.add_argument("--no-solvers", action="store_true", help="skip the solver comparison leg")
     ap.add_argument("--no-forms", action="store_true", help="skip the formulation comparison leg")
     ap.add_argument("--no-nano", action="store_true", help="skip the plasmonic nanoparticle leg")
+    ap.add_argument("--formulation-study", action="store_true",
+                    help="add the iterations-versus-unknowns study of the formulations on the two-layer sphere")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -407,6 +409,35 @@ def main():
         del bn, xn
         sn.close()
 
+    # iterations versus unknowns per formulation (the comparison of Fig. 6) on the
+    # two-layer sphere at four mesh densities: FGMRES(50) with ILU(0) and without
+    # a preconditioner, mixed form, tol 1e-4, at most 1000 iterations
+    study = None
+    if args.formulation_study:
+        study = {"solver": "FGMRES(50), ILU(0) ('ilu') or none ('none'), mixed form, tol 1e-4, max 1000 iterations",
+                 "rows": []}
+        for nu_o, nu_i in ((12, 8), (18, 12), (24, 16), (30, 20)):
+            mesh_s = geo.coated_sphere(nu_o, nu_i)
+            row = {"nu_outer": nu_o, "nu_inner": nu_i}
+            for fname, form in (("jmcfie", sie.FORM_JMCFIE), ("ctf", sie.FORM_CTF), ("cnf", sie.FORM_CNF),
+                                ("pmchwt", sie.FORM_PMCHWT)):
+                sf = sie.Solver(mesh_s, levels=LEVELS, digits=DIGITS, stream=stream, formulation=form)
+                row["unknowns"] = 2 * sf.ne
+                bf = sf.vec(1)
+                xf = sf.vec(1)
+                sie.sie_plane_wave_rhs(sf.ctx, inc, bf)
+                row[fname] = {}
+                for pname, pc in (("ilu", 1), ("none", 0)):
+                    xf.zero_()
+                    stf = sie.gmres_solve(sf.ctx, bf, xf, 1, restart=RESTART, max_iters=1000, tol=TOL,
+                                          prec=sie.SIE_PREC_MIXED, precond=pc, check=False,
+                                          graphs=not args.no_graphs)
+                    row[fname][pname] = {"iters": stf[0]["iters"], "converged": stf[0]["converged"],
+                                         "rel_residual": stf[0]["rel_residual"]}
+                del bf, xf
+                sf.close()
+            study["rows"].append(row)
+
     # stage timings (CUDA events on the library stream) and the roofline of the dominant kernel
     stages = {}
     for name, stg in (("near_spmv", 0), ("far_mlfmm", 1), ("ilu_sweeps", 2), ("matvec", 3)):
@@ -448,7 +479,7 @@ def main():
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
                 "d2h_bytes_per_step": int(rcs.nbytes)},
         "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp,
-        "nanoparticle": nano, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
+        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
     }
     if rank == 0:

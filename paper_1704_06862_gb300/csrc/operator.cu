@@ -776,6 +776,7 @@ __device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
 // scratch and counts itself in; the last to arrive adds the pieces' partials
 // in piece order and finishes the box.  The results are deterministic.
 constexpr int ILU_RL = 8;  // lanes per pushed row
+constexpr int ILU_RU = 2;  // blocks per lane and iteration of a pushed row
 
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int colour, int npieceA,
@@ -814,24 +815,28 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
     }
     cx<T> a0, a1;
     int q = q0 + hl;
-    for (; q + ILU_RL < q1; q += 2 * ILU_RL) {
-      const int c0 = __ldg(off_col + q), c1 = __ldg(off_col + q + ILU_RL);
-      V16 u0[NV], u1[NV];
+    // ILU_RU blocks per lane and iteration: their column and value loads are
+    // issued together, then the z gathers they select
+    for (; q + (ILU_RU - 1) * ILU_RL < q1; q += ILU_RU * ILU_RL) {
+      int cc[ILU_RU];
+      V16 uu[ILU_RU][NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        u0[v] = __ldg(Ov + (size_t)q * NV + v);
-        u1[v] = __ldg(Ov + (size_t)(q + ILU_RL) * NV + v);
+      for (int u = 0; u < ILU_RU; ++u) {
+        cc[u] = __ldg(off_col + q + u * ILU_RL);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) uu[u][v] = __ldg(Ov + (size_t)(q + u * ILU_RL) * NV + v);
       }
-      cx<T> x0, x1, y0, y1;
-      ldg_pair(z + 2 * (size_t)c0, x0, x1);  // colour sc: not written by this launch
-      ldg_pair(z + 2 * (size_t)c1, y0, y1);
-      const cx<T> *b0 = reinterpret_cast<const cx<T> *>(u0), *b1 = reinterpret_cast<const cx<T> *>(u1);
-      a0 = cfma(b0[0], x0, cfma(b0[1], x1, a0));
-      a1 = cfma(b0[2], x0, cfma(b0[3], x1, a1));
-      a0 = cfma(b1[0], y0, cfma(b1[1], y1, a0));
-      a1 = cfma(b1[2], y0, cfma(b1[3], y1, a1));
+      cx<T> xx[ILU_RU][2];
+#pragma unroll
+      for (int u = 0; u < ILU_RU; ++u) ldg_pair(z + 2 * (size_t)cc[u], xx[u][0], xx[u][1]);  // colour sc: not written by this launch
+#pragma unroll
+      for (int u = 0; u < ILU_RU; ++u) {
+        const cx<T> *bb = reinterpret_cast<const cx<T> *>(uu[u]);
+        a0 = cfma(bb[0], xx[u][0], cfma(bb[1], xx[u][1], a0));
+        a1 = cfma(bb[2], xx[u][0], cfma(bb[3], xx[u][1], a1));
+      }
     }
-    if (q < q1) {
+    for (; q < q1; q += ILU_RL) {
       const int c0 = __ldg(off_col + q);
       V16 u0[NV];
 #pragma unroll
