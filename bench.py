@@ -39,6 +39,10 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one k_near_spmv<float> launch on this workload, from one
 # ncu capture (profiles/near_spmv_coated_c2.md); valid while that kernel is unchanged
 NEAR_SPMV_TRAFFIC_BYTES = 508421888 + 521984
+# DRAM bytes (read + write) of one single-RHS FP32 ILU(0) apply (15 k_ilu_sweep<float, 512>
+# launches) on this workload, from one ncu capture (profiles/ilu_sweep_coated_c2.md); valid
+# while that kernel is unchanged
+ILU_APPLY_TRAFFIC_BYTES = 566043136 + 182016
 
 
 def measured_peaks():
@@ -63,15 +67,21 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.rows = []
+        self.n0 = 0
         self.proc = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            # the timed region starts once nvidia-smi is sampling; only later samples count
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.n0 = len(self.rows)
         except Exception:
             self.proc = None
 
@@ -87,6 +97,8 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        if len(self.rows) > self.n0:
+            self.rows = self.rows[self.n0:]
         sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -158,7 +170,7 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -447,12 +459,20 @@ def main():
     near_bytes_fp32 = nnzb * (4 * 8 + 4) + (ne + 1) * 4 + 2 * (2 * ne * 8)
     near_bytes_fp64 = nnzb * (4 * 16 + 4) + (ne + 1) * 4 + 2 * (2 * ne * 16)
     peak, peak_src = measured_peaks()
+    # the kernel with the largest share of the solve's time: the ILU(0) sweeps
+    # (one apply = 15 dependent k_ilu_sweep launches; bytes and time per apply)
+    ilu_bytes = sie.sie_query(s.ctx, 9)
+    ach_ilu = ilu_bytes / (stages["ilu_sweeps"]["fp32_ms"] * 1e-3) / 1e9
+    roofline = {"kernel": "k_ilu_sweep<float, 512> (ILU(0) apply: 15 colour sweep steps)", "bound": "hbm",
+                "achieved": ach_ilu, "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": ach_ilu / peak,
+                "traffic": ILU_APPLY_TRAFFIC_BYTES if WORKLOAD == "coated_c2" else None,
+                "algorithmic_bytes_per_apply": ilu_bytes, "launches_per_apply": 15}
     ach = near_bytes_fp32 / (stages["near_spmv"]["fp32_ms"] * 1e-3) / 1e9
-    roofline = {"kernel": "k_near_spmv<float> (near-field 2x2 block-sparse product)", "bound": "hbm",
-                "achieved": ach, "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak,
-                "traffic": NEAR_SPMV_TRAFFIC_BYTES if WORKLOAD == "coated_c2" else None,
-                "algorithmic_bytes_per_launch": near_bytes_fp32,
-                "fp64_achieved": near_bytes_fp64 / (stages["near_spmv"]["fp64_ms"] * 1e-3) / 1e9}
+    roofline_near = {"kernel": "k_near_spmv<float> (near-field 2x2 block-sparse product)", "bound": "hbm",
+                     "achieved": ach, "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": NEAR_SPMV_TRAFFIC_BYTES if WORKLOAD == "coated_c2" else None,
+                     "algorithmic_bytes_per_launch": near_bytes_fp32,
+                     "fp64_achieved": near_bytes_fp64 / (stages["near_spmv"]["fp64_ms"] * 1e-3) / 1e9}
     pat_bytes = sie.sie_query(s.ctx, 6)
     mv_bytes32 = near_bytes_fp32 + pat_bytes // 2
     matvec = {"fp32_ms": stages["matvec"]["fp32_ms"], "fp64_ms": stages["matvec"]["fp64_ms"],
@@ -480,7 +500,7 @@ def main():
                 "d2h_bytes_per_step": int(rcs.nbytes)},
         "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp,
         "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
-        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
+        "roofline": roofline, "roofline_near_spmv": roofline_near, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

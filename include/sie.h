@@ -310,6 +310,10 @@ sie_status sie_stage_timing(sie_ctx *ctx, int32_t stage, int64_t nrhs, int32_t p
  *   0 n_rwg, 1 near blocks, 2 levels, 3 regions, 4 leaf boxes (all media),
  *   5 bytes of the FP64 near field, 6 bytes of FP64 leaf patterns,
  *   7 device bytes held, 8 kernel launches so far,
+ *   9 algorithmic bytes of one single-RHS FP32 ILU(0) apply (off-box factor
+ *     blocks with their column indices, in-box inverse blocks, per row the
+ *     colour pointers of both sweeps and the source and result vectors; 0
+ *     without ILU factors),
  *   100 + 16*l + j: K (directions) of medium l at level j. */
 sie_status sie_query(const sie_ctx *ctx, int32_t key, int64_t *value);
 

@@ -133,6 +133,7 @@ struct IluHost {
   int64_t *d_tl_off = nullptr, *d_tu_off = nullptr;  // per box offsets, in blocks
   void *d_tl64 = nullptr, *d_tl32 = nullptr, *d_tu64 = nullptr, *d_tu32 = nullptr;
   int max_box = 0;
+  int64_t nblk_off = 0, nblk_inv = 0;  // off-box factor blocks (L and U); in-box inverse blocks
 };
 
 struct sie_ctx {

@@ -1015,6 +1015,8 @@ static void build_ilu(sie_ctx *c) {
   I.d_up32 = f32(up_val);
   I.d_tl32 = f32(tl);
   I.d_tu32 = f32(tu);
+  I.nblk_off = (int64_t)lo_col.size() + (int64_t)up_col.size();
+  I.nblk_inv = (int64_t)(tl.size() + tu.size()) / 4;
   I.ready = true;
 }
 
@@ -1348,6 +1350,9 @@ extern "C" sie_status sie_query(const sie_ctx *c, int32_t key, int64_t *v) {
     }
     case 7: *v = c->dev_bytes; return SIE_OK;
     case 8: *v = c->launches; return SIE_OK;
+    case 9:  // algorithmic bytes of one single-RHS FP32 ILU(0) apply
+      *v = c->ilu.ready ? c->ilu.nblk_off * (32 + 4) + c->ilu.nblk_inv * 32 + (int64_t)c->ne * (2 * 9 * 4 + 2 * 16) : 0;
+      return SIE_OK;
     default:
       if (key >= 100 && key < 100 + 16 * 64) {
         int l = (key - 100) / 16, j = (key - 100) % 16;
