@@ -115,6 +115,20 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_incidence(rank):
+    """Each rank solves its own incidence (replicas): theta_i = 0.05 rad x rank,
+    phi_i = 0, theta-polarised, unit amplitude."""
+    return np.array([[0.05 * rank, 0.0, 0.0, 1.0]])
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (the job's time) on every rank."""
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------- CPU oracle timing
 def oracle_sample(mesh, rng_seed=0, nrows=4):
     """Time the oracle on a bounded sample of the workload and extrapolate its
@@ -143,7 +157,13 @@ def oracle_sample(mesh, rng_seed=0, nrows=4):
     est = t_mesh + t_rows / nrows * m.ne + t_lu * (N / n_lu) ** 3 + t_ff / len(obs) * 361
     sample = (f"oracle on host: {nrows} dense JMCFIE edge rows of {m.ne} ({t_rows:.1f} s), dense LU n={n_lu} "
               f"({t_lu:.2f} s, scaled by N^3 to N={N}), far field at {len(obs)} of 361 angles; extrapolated")
-    return est, sample, t_mesh + t_rows + t_lu + t_ff
+    return est, sample, t_mesh + t_rows + t_lu + t_ff, N
+
+
+def arm_config(unknowns, ws):
+    """The workload keys both arms report."""
+    return {"workload": WORKLOAD, "unknowns": unknowns, "levels": LEVELS, "digits": DIGITS, "tol": TOL,
+            "restart": RESTART, "nrhs_per_gpu": 1, "parallelism": f"replicas{ws}"}
 
 
 def run_reference(args, ws, rank):
@@ -153,14 +173,14 @@ def run_reference(args, ws, rank):
     mesh = geo.workload(WORKLOAD)
     vals = []
     for i in range(args.warmup + args.steps):
-        est, sample, spent = oracle_sample(mesh, rng_seed=i, nrows=2)
+        est, sample, spent, unknowns = oracle_sample(mesh, rng_seed=i, nrows=2)
         if i >= args.warmup:
             vals.append(est)
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "unknowns": None, "levels": LEVELS},
+            "config": arm_config(unknowns, ws),
             "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "sample": sample, "value": v, "unit": "s"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -208,8 +228,8 @@ def main():
     ne = s.ne
     obs = geo.bistatic_angles(361)
     # each rank its own incidence (replicas)
-    theta_i = 0.0 + 0.05 * rank
-    inc = np.array([[theta_i, 0.0, 0.0, 1.0]])
+    inc = rank_incidence(rank)
+    theta_i = float(inc[0, 0])
     b_dev = s.vec(1)
     x = s.vec(1)
     sie.sie_plane_wave_rhs(s.ctx, inc, b_dev)
@@ -239,9 +259,7 @@ def main():
             dist.barrier()
         ms = e0.elapsed_time(e1) / steps
         if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms, dist, "cuda")
         return ms, out
 
     for _ in range(args.warmup):
@@ -482,7 +500,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        est, sample, spent = oracle_sample(mesh)
+        est, sample, spent, _ = oracle_sample(mesh)
         cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
                "sample_wall_s": spent}
     line = {
@@ -491,9 +509,8 @@ def main():
         "vs_baseline": None, "dtype": "f32",
         "precision": "FP32 complex operator, ILU(0) and RCS; FP64 Arnoldi, Givens and true-residual vectors, "
                      "true residual with the FP64 near field and the FP32 far field", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "unknowns": 2 * ne, "levels": LEVELS, "digits": DIGITS, "tol": TOL,
-                   "restart": RESTART, "nrhs_per_gpu": 1, "parallelism": f"replicas{ws}",
-                   "l2": f"operator data {(near_bytes_fp32 + pat_bytes // 2) / 1e6:.0f} MB > 129 MB L2 (no flush)"},
+        "config": dict(arm_config(2 * ne, ws),
+                       l2=f"operator data {(near_bytes_fp32 + pat_bytes // 2) / 1e6:.0f} MB > 129 MB L2 (no flush)"),
         "iters": st["iters"], "rel_residual": st["rel_residual"], "fp64_operator_rel_residual": fp64_resid,
         "setup_s": t_setup,
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
