@@ -264,6 +264,8 @@ struct Recorder {  // training pairs taken at the restarts of one solve
   int cap;
   int *count;
 };
+// operator of the true residual for inner precision prec and tolerance tol
+sie_prec residual_prec(sie_prec prec, double tol, bool far_fp64);
 // prec: inner operator and preconditioner; rprec: operator of the true residual
 sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int max_iters, double tol,
                               sie_prec prec, sie_prec rprec, int precond, Recorder *rec, sie_solve_stats *st);

@@ -404,7 +404,8 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
       SIE_CUDA(cudaMemsetAsync(xs, 0, (size_t)ne2 * sizeof(zd), c->stream));
       int first = npairs;
       Recorder rec{rec_x, rec_r, cap_pairs, &npairs};
-      run_gmres_internal(c, b, xs, 1, o->record_restart, 1000, 1e-7, SIE_PREC_MIXED, SIE_PREC_NEAR64, 1, &rec, nullptr);
+      run_gmres_internal(c, b, xs, 1, o->record_restart, 1000, 1e-7, SIE_PREC_MIXED,
+                         residual_prec(SIE_PREC_MIXED, 1e-7, false), 1, &rec, nullptr);
       for (int k = first; k < npairs; ++k) owner.push_back(t);
       // errors e_k = x* - x_k (stored over rec_x)
       for (int k = first; k < npairs; ++k) {
@@ -524,11 +525,13 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
       sie_solve_stats sv;
       S.ready = false;
       SIE_CUDA(cudaMemsetAsync(xs, 0, (size_t)ne2 * sizeof(zd), c->stream));
-      run_gmres_internal(c, b, xs, 1, 50, 1000, 1e-4, SIE_PREC_MIXED, SIE_PREC_NEAR64, 1, nullptr, &sv);
+      run_gmres_internal(c, b, xs, 1, 50, 1000, 1e-4, SIE_PREC_MIXED, residual_prec(SIE_PREC_MIXED, 1e-4, false),
+                         1, nullptr, &sv);
       it_ilu = sv.iters;
       S.ready = true;
       SIE_CUDA(cudaMemsetAsync(xs, 0, (size_t)ne2 * sizeof(zd), c->stream));
-      run_gmres_internal(c, b, xs, 1, 50, 1000, 1e-4, SIE_PREC_MIXED, SIE_PREC_NEAR64, 2, nullptr, &sv);
+      run_gmres_internal(c, b, xs, 1, 50, 1000, 1e-4, SIE_PREC_MIXED, residual_prec(SIE_PREC_MIXED, 1e-4, false),
+                         2, nullptr, &sv);
       it_nn = sv.iters;
       enabled = it_nn < it_ilu;
     }

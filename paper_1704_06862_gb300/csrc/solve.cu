@@ -671,6 +671,16 @@ sie_status run_bicg_internal(sie_ctx *c, const zd *b, zd *x, int R, int max_iter
   return conv ? SIE_OK : SIE_ENOTCONV;
 }
 
+// Operator of the true residual.  The plain form keeps every step in FP64.
+// The mixed form uses the FP64 near field with the FP32 far field, whose
+// rounding leaves the residual operator within a few 1e-6 (relative) of the
+// FP64 operator: it decides convergence only for tolerances well above that
+// floor, the whole FP64 operator below it (or on request).
+sie_prec residual_prec(sie_prec prec, double tol, bool far_fp64) {
+  constexpr double kNear64MinTol = 5e-5;
+  return prec == SIE_PREC_MIXED && !far_fp64 && tol >= kNear64MinTol ? SIE_PREC_NEAR64 : SIE_PREC_FP64;
+}
+
 sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_solve_opts *o, sie_solve_stats *st) {
   const size_t vs = (size_t)R * 2 * c->ne;
   if (c->gw_R != R) {
@@ -682,14 +692,7 @@ sie_status run_gmres(sie_ctx *c, const zd *b_user, zd *x_user, int R, const sie_
   op_permute_in(c, b_user, b, R);
   op_permute_in(c, x_user, x, R);
   sie_prec prec = o->prec == 1 ? SIE_PREC_MIXED : SIE_PREC_FP64;
-  // true residual: the plain form keeps every step in FP64.  The mixed form
-  // uses the FP64 near field with the FP32 far field, whose rounding leaves
-  // the residual operator within a few 1e-6 (relative) of the FP64 operator:
-  // it decides convergence only for tolerances well above that floor, the
-  // whole FP64 operator below it (or on request).
-  constexpr double kNear64MinTol = 5e-5;
-  sie_prec rprec = prec == SIE_PREC_MIXED && !o->residual_far_fp64 && o->tol >= kNear64MinTol ? SIE_PREC_NEAR64
-                                                                                              : SIE_PREC_FP64;
+  const sie_prec rprec = residual_prec(prec, o->tol, o->residual_far_fp64 != 0);
   struct Eager {  // eager steps for this call only, also when it throws
     sie_ctx *c;
     ~Eager() { c->graphs_off = false; }
