@@ -515,7 +515,7 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
       SIE_CHECK_LAUNCH();
       SIE_CUDA(cudaStreamSynchronize(c->stream));
     }
-    // the plain ILU(0) solver is the judge: solve the last (held-out) incidence
+    // the plain ILU(0) solver decides: solve the last (held-out) incidence
     // with and without the correction; keep it only if it saves iterations
     int it_ilu = -1, it_nn = -1;
     if (enabled) {
