@@ -226,6 +226,8 @@ __device__ __forceinline__ void cta_copy_async(void *dst, const void *src, size_
 // so a whole chunk is in flight at once; the box's signed coefficients are
 // staged in shared memory and each pattern value serves RB right-hand sides.
 constexpr int STAGES = 2;
+// single-RHS ILU sweep steps launched with programmatic dependent launch
+constexpr bool ILU_PDL = true;
 template <typename T, int RB, int KS>
 __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int cb, const int *__restrict__ box_start,
                                                   const int *__restrict__ basis_p, const int *__restrict__ sign,
@@ -775,6 +777,15 @@ __device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
 // meanwhile.  A box of several pieces: each piece writes its row partials to
 // scratch and counts itself in; the last to arrive adds the pieces' partials
 // in piece order and finishes the box.  The results are deterministic.
+// Programmatic dependent launch of the sweep steps: a step may start while
+// the previous one drains and reads only static data (factors, pointers,
+// packed inverses) before pdl_wait(), which returns once the previous step has
+// completed and its writes are visible; pdl_release(), issued after the wait,
+// then lets the next step launch, so a step never overlaps the one two back.
+// Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 constexpr int ILU_RL = 8;  // lanes per pushed row
 constexpr int ILU_RU = 2;  // blocks per lane and iteration of a pushed row
 
@@ -804,14 +815,16 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
     const int hl = lane & (ILU_RL - 1);
     const int i = rb0 + ((int)blockIdx.x - npieceA) * (32 / ILU_RL) * NW + (32 / ILU_RL) * warp + lane / ILU_RL;
     const bool row_ok = i < rb1;
+    int q0 = 0, q1 = 0;
+    if (row_ok && has_src) {
+      q0 = cptr[9 * (size_t)i + sc];
+      q1 = cptr[9 * (size_t)i + sc + 1];
+    }
+    pdl_wait();
+    pdl_release();
     if (!has_src) {
       if (row_ok && hl < 2) z[2 * (size_t)i + hl] = src[2 * (size_t)i + hl];
       return;
-    }
-    int q0 = 0, q1 = 0;
-    if (row_ok) {
-      q0 = cptr[9 * (size_t)i + sc];
-      q1 = cptr[9 * (size_t)i + sc + 1];
     }
     cx<T> a0, a1;
     int q = q0 + hl;
@@ -903,6 +916,8 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
     if (lane == 0) pre[n] = carry;
   }
   __syncthreads();
+  pdl_wait();  // z, w and the piece scratch below come from earlier steps
+  pdl_release();
   const int total = v1;  // this piece: virtual indices [v0, v1) of the box's blocks from sc
   const int ng = (v1 - v0 + 31) >> 5;
   const int g0 = (int)((int64_t)warp * ng / NW), g1 = (int)((int64_t)(warp + 1) * ng / NW);
@@ -1430,12 +1445,26 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
       const int nrowB = rb1 - rb0;
       const int grid = np + (nrowB + (32 / ILU_RL) * NW - 1) / ((32 / ILU_RL) * NW);
       if (grid == 0) continue;
-      k_ilu_sweep<T, NT><<<grid, NT, smem, c->stream>>>(
-          fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, np, I.d_pieces + 5 * (size_t)I.piece_ptr[step], rb0, rb1, stage, mb,
-          (cx<T> *)I.d_piece_scratch, I.d_piece_count, I.d_box_start,
-          fwd ? I.d_lo_cptr : I.d_up_cptr, fwd ? I.d_lo_col : I.d_up_col,
-          (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? I.d_tl_off : I.d_tu_off,
-          (const cx<T> *)(fwd ? tsel<T>::tl(I) : tsel<T>::tu(I)), I.d_tu_off, (const cx<T> *)tsel<T>::tu(I), r, z);
+      // each step may launch while the previous one drains (programmatic
+      // dependent launch; the kernel waits before it reads z)
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(NT);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = c->stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = ILU_PDL ? 1 : 0;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      SIE_CUDA(cudaLaunchKernelEx(
+          &cfg, k_ilu_sweep<T, NT>, fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, np,
+          (const int *)(I.d_pieces + 5 * (size_t)I.piece_ptr[step]), rb0, rb1, stage, mb,
+          (cx<T> *)I.d_piece_scratch, I.d_piece_count, (const int *)I.d_box_start,
+          (const int *)(fwd ? I.d_lo_cptr : I.d_up_cptr), (const int *)(fwd ? I.d_lo_col : I.d_up_col),
+          (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), (const int64_t *)(fwd ? I.d_tl_off : I.d_tu_off),
+          (const cx<T> *)(fwd ? tsel<T>::tl(I) : tsel<T>::tu(I)), (const int64_t *)I.d_tu_off,
+          (const cx<T> *)tsel<T>::tu(I), (const cx<T> *)r, z));
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
