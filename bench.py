@@ -42,7 +42,7 @@ NEAR_SPMV_TRAFFIC_BYTES = 508421888 + 521984
 # DRAM bytes (read + write) of one single-RHS FP32 ILU(0) apply (15 k_ilu_sweep<float, 512>
 # launches) on this workload, from one ncu capture (profiles/ilu_sweep_coated_c2.md); valid
 # while that kernel is unchanged
-ILU_APPLY_TRAFFIC_BYTES = 566043136 + 182016
+ILU_APPLY_TRAFFIC_BYTES = 566056448 + 122624
 
 
 def measured_peaks():
