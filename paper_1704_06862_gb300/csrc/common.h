@@ -12,6 +12,33 @@
 
 #define SIE_HD __host__ __device__ __forceinline__
 
+// ------------------------------------------------------------------ launch chaining
+// Programmatic dependent launch: a kernel launched with chained = true may
+// start while its predecessor on the stream drains.  It reads only static
+// data (tables, factors, pointers) before pdl_wait(), which returns once the
+// predecessor has completed and its writes are visible; pdl_release(), issued
+// after the wait, lets the next kernel launch, so a kernel never overlaps the
+// one two back.  Without the launch attribute both are no-ops.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+#endif
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(bool chained, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                           cudaStream_t st, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = chained ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
 // ------------------------------------------------------------------ complex
 template <typename T>
 struct cx {

@@ -777,14 +777,9 @@ __device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
 // meanwhile.  A box of several pieces: each piece writes its row partials to
 // scratch and counts itself in; the last to arrive adds the pieces' partials
 // in piece order and finishes the box.  The results are deterministic.
-// Programmatic dependent launch of the sweep steps: a step may start while
-// the previous one drains and reads only static data (factors, pointers,
-// packed inverses) before pdl_wait(), which returns once the previous step has
-// completed and its writes are visible; pdl_release(), issued after the wait,
-// then lets the next step launch, so a step never overlaps the one two back.
-// Without the launch attribute both are no-ops.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+// The sweep steps are chained (programmatic dependent launch, common.h): a
+// step reads its static prologue (row colour pointers, prefixes, the packed
+// inverse) while the previous step drains, and waits before it touches z.
 
 constexpr int ILU_RL = 8;  // lanes per pushed row
 constexpr int ILU_RU = 2;  // blocks per lane and iteration of a pushed row
@@ -1447,18 +1442,8 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
       if (grid == 0) continue;
       // each step may launch while the previous one drains (programmatic
       // dependent launch; the kernel waits before it reads z)
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(grid);
-      cfg.blockDim = dim3(NT);
-      cfg.dynamicSmemBytes = smem;
-      cfg.stream = c->stream;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-      attr[0].val.programmaticStreamSerializationAllowed = ILU_PDL ? 1 : 0;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      SIE_CUDA(cudaLaunchKernelEx(
-          &cfg, k_ilu_sweep<T, NT>, fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, np,
+      SIE_CUDA(launch_chained(
+          ILU_PDL, k_ilu_sweep<T, NT>, dim3(grid), dim3(NT), smem, c->stream, fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, np,
           (const int *)(I.d_pieces + 5 * (size_t)I.piece_ptr[step]), rb0, rb1, stage, mb,
           (cx<T> *)I.d_piece_scratch, I.d_piece_count, (const int *)I.d_box_start,
           (const int *)(fwd ? I.d_lo_cptr : I.d_up_cptr), (const int *)(fwd ? I.d_lo_col : I.d_up_col),

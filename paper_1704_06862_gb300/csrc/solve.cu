@@ -23,9 +23,14 @@ typedef std::complex<double> cd;
 // synchronisation); stage 2 adds the partials in chunk order.  With a gate,
 // right-hand sides whose gate is 0 get zero partials.
 constexpr int MD_CH = 1024;
+// Gram-Schmidt kernels chained by programmatic dependent launch (each waits
+// for its predecessor first thing: stream order, launch latency hidden)
+constexpr bool GS_CHAINED = true;
 __global__ void __launch_bounds__(256) k_mdot_part(int n, int nrhs, int nvec, int nblk, const zd *__restrict__ V,
                                                   size_t vstride, const zd *__restrict__ w, zd *__restrict__ part,
                                                   const int *__restrict__ gate) {
+  pdl_wait();
+  pdl_release();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r = blockIdx.y;
   const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
   if (gw >= nvec * nblk) return;
@@ -50,6 +55,8 @@ __global__ void __launch_bounds__(256) k_mdot_part(int n, int nrhs, int nvec, in
 // repeated only when |w'| < |w| / sqrt(2), i.e. |w'|^2 < |h|^2.
 __global__ void k_reorth_gate(int nrhs, int nvec, const zd *__restrict__ h, const zd *__restrict__ nn1,
                               int *__restrict__ gate) {
+  pdl_wait();
+  pdl_release();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
   double hh = 0.0;
@@ -61,6 +68,8 @@ __global__ void k_reorth_gate(int nrhs, int nvec, const zd *__restrict__ h, cons
 }
 
 __global__ void k_mdot_sum(int nrhs, int nblk, const zd *__restrict__ part, zd *__restrict__ h) {
+  pdl_wait();
+  pdl_release();
   const int i = blockIdx.x, r = blockIdx.y;
   __shared__ double2 red_raw[256];  // raw storage: zd has a constructor
   zd *red = reinterpret_cast<zd *>(red_raw);
@@ -78,6 +87,8 @@ __global__ void k_mdot_sum(int nrhs, int nblk, const zd *__restrict__ part, zd *
 // w[r] -= sum_{i<=j} V_i[r] h[i][r]
 __global__ void k_orth(int n, int nrhs, int j1, const zd *__restrict__ V, size_t vstride, const zd *__restrict__ h,
                        zd *__restrict__ w, const int *__restrict__ gate) {
+  pdl_wait();
+  pdl_release();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int r = blockIdx.y;
   if (t >= n || (gate && !gate[r])) return;
@@ -99,6 +110,8 @@ __global__ void k_scale(int n, const zd *__restrict__ a, const zd *__restrict__ 
 // sides that are finished (act[r] == 0) or whose new vector vanished
 __global__ void k_scale_norm(int n, const zd *__restrict__ a, const zd *__restrict__ nn, const zd *__restrict__ act,
                              zd *__restrict__ out) {
+  pdl_wait();
+  pdl_release();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int r = blockIdx.y;
   if (t >= n) return;
@@ -155,9 +168,11 @@ struct Gm {
   }
   // h[i][r] = <V_i[r], w[r]> for i < nvec
   void mdot(const zd *V, size_t vstride, int nvec, const zd *w, zd *d_h, const int *gate = nullptr) {
-    k_mdot_part<<<dim3((nvec * nblk + 7) / 8, R), 256, 0, c->stream>>>(n, R, nvec, nblk, V, vstride, w, part, gate);
+    SIE_CUDA(launch_chained(GS_CHAINED, k_mdot_part, dim3((nvec * nblk + 7) / 8, R), dim3(256), 0, c->stream, n, R, nvec,
+                            nblk, V, vstride, w, part, gate));
     launch_check();
-    k_mdot_sum<<<dim3(nvec, R), 256, 0, c->stream>>>(R, nblk, part, d_h);
+    SIE_CUDA(launch_chained(GS_CHAINED, k_mdot_sum, dim3(nvec, R), dim3(256), 0, c->stream, R, nblk, (const zd *)part,
+                            d_h));
     launch_check();
   }
   void norms(const zd *w, zd *d_h, std::vector<double> &out) {
@@ -368,16 +383,20 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
       // next vector, all on the device
       int *gate = (int *)c->gm_gate;
       g.mdot(V, vs, j + 1, w, dh1);
-      k_orth<<<gv, 256, 0, c->stream>>>(n, R, j + 1, V, vs, dh1, w, nullptr);
+      SIE_CUDA(launch_chained(GS_CHAINED, k_orth, gv, dim3(256), 0, c->stream, n, R, j + 1, (const zd *)V, vs,
+                              (const zd *)dh1, w, (const int *)nullptr));
       g.launch_check();
       g.mdot(w, 0, 1, w, dnn);
-      k_reorth_gate<<<(R + 127) / 128, 128, 0, c->stream>>>(R, j + 1, dh1, dnn, gate);
+      SIE_CUDA(launch_chained(GS_CHAINED, k_reorth_gate, dim3((R + 127) / 128), dim3(128), 0, c->stream, R, j + 1,
+                              (const zd *)dh1, (const zd *)dnn, gate));
       g.launch_check();
       g.mdot(V, vs, j + 1, w, dh2, gate);
-      k_orth<<<gv, 256, 0, c->stream>>>(n, R, j + 1, V, vs, dh2, w, gate);
+      SIE_CUDA(launch_chained(GS_CHAINED, k_orth, gv, dim3(256), 0, c->stream, n, R, j + 1, (const zd *)V, vs,
+                              (const zd *)dh2, w, (const int *)gate));
       g.launch_check();
       g.mdot(w, 0, 1, w, dnn);
-      k_scale_norm<<<gv, 256, 0, c->stream>>>(n, w, dnn, (const zd *)c->gm_act, V + (size_t)(j + 1) * vs);
+      SIE_CUDA(launch_chained(GS_CHAINED, k_scale_norm, gv, dim3(256), 0, c->stream, n, (const zd *)w, (const zd *)dnn,
+                              (const zd *)c->gm_act, V + (size_t)(j + 1) * vs));
       g.launch_check();
       SIE_CUDA(cudaMemcpyAsync(c->gm_hpin, d_h, 3 * (size_t)(m + 2) * R * sizeof(zd), cudaMemcpyDeviceToHost,
                                c->stream));
