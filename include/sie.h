@@ -209,11 +209,15 @@ typedef struct {
   int32_t converged;    /* 1 if rel_residual <= tol */
 } sie_solve_stats;
 
-/* Right-preconditioned flexible GMRES(restart) for nrhs right-hand sides in
- * lockstep (block of independent Krylov spaces).  b_dev, x_dev complex128
- * [nrhs][n_rwg][2] user order; x_dev holds the initial guess on entry.
- * stats_host [nrhs] receives per-RHS results.  Synchronous.  Returns
- * SIE_ENOTCONV if any RHS did not reach tol. */
+/* Right-preconditioned flexible GMRES(restart) (or BiCGStab / CGS, see
+ * opts->method) for nrhs right-hand sides in lockstep (block of independent
+ * Krylov spaces).  b_dev, x_dev complex128 [nrhs][n_rwg][2] user order; x_dev
+ * holds the initial guess on entry and the solution on return.  stats_host
+ * [nrhs] receives per-RHS results.  Synchronous.  Returns SIE_ENOTCONV if any
+ * RHS did not reach tol (x_dev and the stats still hold the last iterate),
+ * SIE_EBREAKDOWN on a non-finite residual or repeated breakdown, SIE_EINVAL
+ * for options out of range, SIE_ESTATE when the ILU(0) factors or the
+ * learned correction requested are not built. */
 sie_status gmres_solve(sie_ctx *ctx, const void *b_dev, void *x_dev, int64_t nrhs,
                        const sie_solve_opts *opts, sie_solve_stats *stats_host);
 
@@ -232,7 +236,7 @@ sie_status gmres_solve(sie_ctx *ctx, const void *b_dev, void *x_dev, int64_t nrh
  * incidences is held out: the output is scaled by the least-squares factor
  * gamma (at most 1) fitted on their pairs; the correction is kept only if it
  * lowers their loss below 95 % of the loss of no correction AND the plain
- * ILU(0) solver, acting as judge, needs more FGMRES(50) iterations than the
+ * ILU(0) solver, which decides, needs more FGMRES(50) iterations than the
  * corrected one on the last held-out incidence.  Synchronous. */
 typedef struct {
   const double *train_inc;  /* host [ntrain][4] incidences, as sie_plane_wave_rhs */
@@ -301,7 +305,8 @@ sie_status sie_near_export(sie_ctx *ctx, int32_t *rows, int32_t *cols, double *v
  * work vectors and returns the mean milliseconds per launch, measured with
  * CUDA events on that stream.  stage: 0 near-field block-sparse product,
  * 1 MLFMM far field (all media, all levels), 2 ILU(0) forward + backward
- * sweeps, 3 whole product (near + far).  prec as for mlfmm_matvec.
+ * sweeps, 3 whole product (near + far).  prec: SIE_PREC_FP64 or
+ * SIE_PREC_MIXED; SIE_PREC_NEAR64 for stage 3 only (else SIE_EINVAL).
  * Synchronous.  Not a numerical operation of the method; the paper has no
  * counterpart. */
 sie_status sie_stage_timing(sie_ctx *ctx, int32_t stage, int64_t nrhs, int32_t prec, int32_t reps, double *ms_out);
