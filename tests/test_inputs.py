@@ -1,0 +1,51 @@
+"""The seeded synthetic inputs: sizes, radii, media and incidences of the
+workloads the tests and the bench use (geodesic spheres of frequency nu have
+20 nu^2 triangles and 30 nu^2 edges; two unknowns per edge)."""
+import numpy as np
+import pytest
+
+from paper_1704_06862_gb300 import geometry as geo
+
+
+def _unknowns(mesh):
+    return 3 * len(mesh["tris"])      # closed surfaces: edges = 3/2 triangles, two unknowns per edge
+
+
+@pytest.mark.parametrize("name,unknowns,radii", [
+    ("sphere_c1", 3840, (0.5,)),
+    ("coated_c2", 78000, (1.5, 1.0)),
+    ("coated_small", 12480, (1.5, 1.0)),
+    ("nanoparticle", 30720, (250 / 550, 230 / 550)),
+])
+def test_workload_sizes_and_radii(name, unknowns, radii):
+    m = geo.workload(name)
+    assert _unknowns(m) == unknowns
+    r = np.linalg.norm(m["verts"], axis=1)
+    assert np.allclose(sorted(set(np.round(r, 12)), reverse=True), radii)
+
+
+def test_workload_media():
+    m = geo.workload("coated_c2")
+    assert np.allclose(m["media"][:, 0], [1.0, 2.56, 4.0]) and np.allclose(m["media"][:, 1], 0.0)
+    n = geo.workload("nanoparticle")
+    eps = n["media"][:, 0] + 1j * n["media"][:, 1]
+    assert np.allclose(eps, [1.0, geo.NANO_EPS_SHELL, geo.NANO_EPS_CORE])
+    assert np.all(n["media"][1:, 0] < 0) and np.all(n["media"][1:, 1] < 0)   # metals: Re eps < 0, loss e^{+jwt}
+    # regions: the outer surface separates host (0) and shell (1), the inner shell (1) and core (2)
+    assert set(map(tuple, n["tri_regions"])) == {(0, 1), (1, 2)}
+
+
+def test_seeded_generators_are_deterministic():
+    a = geo.random_coefficients(100, 2, seed=1234)
+    b = geo.random_coefficients(100, 2, seed=1234)
+    assert a.dtype == np.complex128 and np.array_equal(a, b)
+    assert not np.array_equal(a, geo.random_coefficients(100, 2, seed=1235))
+    assert abs(np.mean(np.abs(geo.random_coefficients(20000, 1)) ** 2) - 1.0) < 0.03   # unit variance
+
+
+def test_incidence_sets():
+    obs = geo.bistatic_angles(361)
+    assert obs.shape == (361, 2) and obs[0, 0] == 0.0 and np.isclose(obs[-1, 0], np.pi) and np.all(obs[:, 1] == 0)
+    inc = geo.monostatic_incidences(16)
+    assert inc.shape == (16, 4) and np.isclose(inc[-1, 0], np.pi)
+    assert np.all(inc[:, 1] == 0) and np.all(inc[:, 2] == 0) and np.all(inc[:, 3] == 1)
