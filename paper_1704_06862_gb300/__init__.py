@@ -188,6 +188,15 @@ SOLVE_FGMRES, SOLVE_BICGSTAB, SOLVE_CGS = 0, 1, 2
 
 def gmres_solve(ctx, b, x, nrhs, restart=50, max_iters=1000, tol=1e-4, prec=SIE_PREC_FP64, precond=1,
                 check=True, graphs=True, method=SOLVE_FGMRES, residual_far_fp64=False):
+    """``gmres_solve`` of the C ABI on torch CUDA tensors b, x [nrhs, n_rwg, 2]
+    (x: initial guess in, solution out).  method: SOLVE_FGMRES (restarted
+    flexible GMRES), SOLVE_BICGSTAB or SOLVE_CGS; precond: 0 none, 1 ILU(0),
+    2 ILU(0) with the learned correction (FGMRES only); prec: arithmetic of
+    the inner product and preconditioner (SIE_PREC_FP64 or SIE_PREC_MIXED);
+    graphs=False launches every step eagerly; residual_far_fp64=True makes the
+    mixed form's true residual use the whole FP64 operator.  Returns one dict
+    per right-hand side (iters, restarts, rel_residual, converged); with
+    check=True a failed convergence raises SieError."""
     o = sie_solve_opts(int(restart), int(max_iters), float(tol), int(prec), int(precond), int(method),
                        0 if graphs else 1, 1 if residual_far_fp64 else 0)
     st = (sie_solve_stats * int(nrhs))()
