@@ -214,10 +214,18 @@ def test_null_body_scatters_nothing():
     incident wave with zero scattered field (Eqs. 1-2, extinction).  Every
     sign of the formulation and excitation enters this check: the scattered
     field must vanish as the mesh is refined, and the currents must approach
-    n x H and -n x E of the incident wave."""
+    n x H and -n x E of the incident wave.
+
+    With eps_r = 1 the discrete scattered field is pure discretisation error
+    (the RWG space cannot hold the incident wave's surface currents exactly),
+    so its level is set by the mesh, not by a tolerance: -22.2 dBsm at nu = 3
+    and -30.4 dBsm at nu = 5 with the adopted JMCFIE signs, about 35 dB below
+    the +5 dBsm a real body of this size scatters.  The bound -28 dBsm sits
+    2.4 dB above the nu = 5 level, and the refinement step (at least 5 dB
+    lower from nu = 3 to nu = 5, measured 8.2 dB) pins the convergence to
+    zero, which a sign error anywhere in the formulation would break."""
     _, _, s3 = _null_case(3)
     m, x, s5 = _null_case(5)
-    # a real body of this size scatters ~ +5 dBsm
     assert 10 * np.log10(s5.max()) < -28.0
     assert 10 * np.log10(s5.max()) < 10 * np.log10(s3.max()) - 5.0
     op = fill.region_operators(m, 0)
@@ -256,18 +264,30 @@ def test_jmcfie_spectrum_right_half_plane():
 
 @pytest.mark.slow
 def test_sphere_converges_to_mie():
-    """Homogeneous sphere, eps_r = 4, radius 0.5 lambda0 (Fig. 5 type check):
-    the RCS error against Mie shrinks with mesh refinement."""
-    obs = geo.bistatic_angles(37)
+    """Homogeneous sphere, eps_r = 4, radius 0.5 lambda0 (the Fig. 5 check of
+    the paper, on the geometry of the homogeneous-sphere workload): bistatic
+    RCS at all 361 angles of the phi = 0 plane, nulls included, against the
+    Lorenz-Mie series under mesh refinement nu = 4, 6, 8 (nu = 8 is the
+    3840-unknown workload mesh).  The mean |error| in dB must fall at each
+    step at close to the second-order rate of a flat-facet RWG discretisation
+    (error ~ h^2, h ~ 1/nu: the ratio between meshes at least 0.8 of
+    (nu_fine / nu_coarse)^2), the maximum must fall too, and the finest mesh
+    must be inside the 0.2 dB bar of the method (measured 0.634, 0.287,
+    0.165 dB mean; 1.10, 0.54, 0.32 dB max)."""
+    obs = geo.bistatic_angles(361)
     ref = 10 * np.log10(mie.sphere_bistatic(0.5, 4.0, obs[:, 0]))
-    errs = []
-    for nu in (3, 5):
+    nus = (4, 6, 8)
+    mean, mx = [], []
+    for nu in nus:
         m = Mesh(**geo.homogeneous_sphere(nu=nu, radius=0.5, eps_r=4.0))
         x = solvers.lu_solve(fill.assemble(m), fill.rhs(m, [[0, 0, 0, 1.0]])[0])
-        s = 10 * np.log10(farfield.rcs(m, x, obs)[0][:, 0])
-        errs.append(np.mean(np.abs(s - ref)))
-    assert errs[1] < 0.6 * errs[0]
-    assert errs[1] < 1.0
+        d = np.abs(10 * np.log10(farfield.rcs(m, x, obs)[0][:, 0]) - ref)
+        mean.append(d.mean())
+        mx.append(d.max())
+    for i in range(len(nus) - 1):
+        assert mean[i + 1] < mean[i] and mx[i + 1] < mx[i], (mean, mx)
+        assert mean[i] / mean[i + 1] > 0.8 * (nus[i + 1] / nus[i]) ** 2, (mean, mx)
+    assert mean[-1] < 0.2 and mx[-1] < 0.4, (mean, mx)
 
 
 # ---------------------------------------------------------------- Mie series
