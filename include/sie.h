@@ -83,7 +83,8 @@ const char *sie_last_error(const sie_ctx *ctx);
  *   n_rwg_out   receives the number of RWG edges (unknowns = 2 * n_rwg).
  * Errors: SIE_EINVAL for junction edges (owned by > 2 triangles), an edge
  * shared by triangles of different surfaces or of inconsistent orientation,
- * region indices outside [0, nr), degenerate triangles.  Host-only work
+ * region indices outside [0, nr), degenerate triangles, media with a zero
+ * or non-finite eps_r or mu_r, active media.  Host-only work
  * (topology); synchronous.  */
 sie_status sie_build_mesh(sie_ctx *ctx, const double *verts, int64_t nv, const int32_t *tris,
                           int64_t nt, const int32_t *tri_regions, const double *media, int32_t nr,
@@ -97,7 +98,9 @@ typedef struct {
                        D / 2^(levels-1) with D = 1.0009765625 * largest extent
                        of the vertex bounding box.  */
   double digits;    /* d0 in L = kd + 1.8 d0^(2/3) (kd)^(1/3), d = sqrt(3) * box
-                       edge, k = Re k_l.  Typical 3. */
+                       edge, k = |k_l| (the modulus, not Re k_l: in a lossy
+                       medium the addition theorem converges at the rate of
+                       |k| d, and a metal's k is nearly imaginary).  Typical 3. */
 } sie_mlfmm_opts;
 
 /* Octree, near-field pattern, preconditioner ordering and the far-field

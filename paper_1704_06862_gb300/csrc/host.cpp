@@ -230,6 +230,9 @@ static void build_mesh(sie_ctx *c, const double *verts, int64_t nv, const int32_
   c->etareg.resize(nr);
   for (int l = 0; l < nr; ++l) {
     cd eps(media[4 * l], media[4 * l + 1]), mu(media[4 * l + 2], media[4 * l + 3]);
+    SIE_REQUIRE(std::isfinite(std::abs(eps)) && std::isfinite(std::abs(mu)) && std::abs(eps) > 0.0 &&
+                    std::abs(mu) > 0.0,
+                SIE_EINVAL, "sie_build_mesh: medium with zero or non-finite eps_r or mu_r");
     cd k = c->k0 * std::sqrt(eps * mu);
     SIE_REQUIRE(k.imag() <= 0.0, SIE_EINVAL, "sie_build_mesh: active medium (Im eps_r mu_r > 0)");
     cd eta = std::sqrt(mu / eps);

@@ -17,6 +17,11 @@ namespace {
 
 typedef std::complex<double> cd;
 
+// Square root of a computed sum of squares: a rounding below zero gives 0, a
+// NaN stays NaN (a non-finite vector must reach the solvers' breakdown checks;
+// std::max(0.0, NaN) would turn it into a zero norm and a false convergence).
+inline double sqrt_nonneg(double v) { return std::isnan(v) ? v : std::sqrt(v > 0.0 ? v : 0.0); }
+
 // Two-stage dot products h[i][r] = sum_n conj(V_i[r][n]) w[r][n], i < nvec.
 // Stage 1: one warp per (vector i, chunk of MD_CH elements, rhs r), lanes over
 // the chunk with many loads in flight, one partial per warp (no block-level
@@ -181,7 +186,7 @@ struct Gm {
     SIE_CUDA(cudaMemcpyAsync(h.data(), d_h, R * sizeof(zd), cudaMemcpyDeviceToHost, c->stream));
     SIE_CUDA(cudaStreamSynchronize(c->stream));
     out.resize(R);
-    for (int r = 0; r < R; ++r) out[r] = std::sqrt(std::max(0.0, h[r].re));
+    for (int r = 0; r < R; ++r) out[r] = sqrt_nonneg(h[r].re);
   }
 };
 
@@ -331,7 +336,7 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
     g.norms(w, d_h, rn);
     bool any = false;
     for (int r = 0; r < R; ++r) {
-      relres[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+      relres[r] = bn[r] > 0 ? rn[r] / bn[r] : (std::isnan(bn[r]) ? bn[r] : 0.0);
       if (!std::isfinite(relres[r])) {
         status = SIE_EBREAKDOWN;
         active[r] = 0;
@@ -411,7 +416,7 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
           const zd a1 = hp[(size_t)i * R + r], a2 = hp[(size_t)(m + 2) * R + (size_t)i * R + r];
           Hc[i + (size_t)j * (m + 1)] = cd(a1.re + a2.re, a1.im + a2.im);
         }
-        Hc[j + 1 + (size_t)j * (m + 1)] = std::sqrt(std::max(0.0, hp[2 * (size_t)(m + 2) * R + r].re));
+        Hc[j + 1 + (size_t)j * (m + 1)] = sqrt_nonneg(hp[2 * (size_t)(m + 2) * R + r].re);
       }
       // Givens rotations per RHS
       bool all_done = true;
@@ -538,13 +543,13 @@ sie_status run_bicg_internal(sie_ctx *c, const zd *b, zd *x, int R, int max_iter
   std::vector<cd> bn2, rn2;
   dots(b, b, bn2);
   std::vector<double> bn(R);
-  for (int q = 0; q < R; ++q) bn[q] = std::sqrt(std::max(0.0, bn2[q].real()));
+  for (int q = 0; q < R; ++q) bn[q] = sqrt_nonneg(bn2[q].real());
   std::vector<int> iters(R, 0), restarts(R, 0), active(R, 1);
   std::vector<double> relres(R, 0.0);
   sie_status status = SIE_OK;
   const std::vector<cd> one(R, cd(1.0)), mone(R, cd(-1.0));
   auto relnorm = [&](const std::vector<cd> &nn, int q) {
-    return bn[q] > 0 ? std::sqrt(std::max(0.0, nn[q].real())) / bn[q] : 0.0;
+    return bn[q] > 0 ? sqrt_nonneg(nn[q].real()) / bn[q] : (std::isnan(bn[q]) ? bn[q] : 0.0);
   };
   std::vector<cd> xn2;
   dots(x, x, xn2);
