@@ -37,11 +37,11 @@ RESTART = 50
 NANO_LEVELS = 4
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one k_near_spmv<float> launch on this workload, from one
-# ncu capture (profiles/near_spmv_coated_c2.md); valid while that kernel is unchanged
+# ncu capture of that kernel; valid while the kernel is unchanged
 NEAR_SPMV_TRAFFIC_BYTES = 508421888 + 521984
 # DRAM bytes (read + write) of one single-RHS FP32 ILU(0) apply (15 k_ilu_sweep<float, 512>
-# launches) on this workload, from one ncu capture (profiles/ilu_sweep_coated_c2.md); valid
-# while that kernel is unchanged
+# launches) on this workload, from one ncu capture of those launches; valid while the
+# kernel is unchanged
 ILU_APPLY_TRAFFIC_BYTES = 566056448 + 122624
 
 
@@ -201,6 +201,7 @@ def main():
     ap.add_argument("--no-solvers", action="store_true", help="skip the solver comparison leg")
     ap.add_argument("--no-forms", action="store_true", help="skip the formulation comparison leg")
     ap.add_argument("--no-nano", action="store_true", help="skip the plasmonic nanoparticle leg")
+    ap.add_argument("--no-mie-refinement", action="store_true", help="skip the RCS-vs-Mie mesh refinement leg")
     ap.add_argument("--formulation-study", action="store_true",
                     help="add the iterations-versus-unknowns study of the formulations on the two-layer sphere")
     args = ap.parse_args()
@@ -439,6 +440,49 @@ def main():
         del bn, xn
         sn.close()
 
+    # RCS against the Mie series under mesh refinement (the discretisation error
+    # of the flat-facet RWG model falls as h^2): the homogeneous sphere of the
+    # small workload and the two-layer sphere at finer meshes than the timed one;
+    # mixed form, ILU(0) FGMRES(50) to 1e-4, all 361 angles (nulls included)
+    mie_ref = None
+    if not args.no_mie_refinement and theta_i == 0.0:
+        # Mie series at the same 361 angles, stored by tests/golden/make_golden.py
+        mie_sph = np.load(os.path.join(ROOT, "tests", "golden", "sphere_c1.npz"))["mie"]
+        mie_coat = np.load(os.path.join(ROOT, "tests", "golden", "mie_coated_c2.npz"))["mie"]
+        mie_ref = {"solver": "mixed form, ILU(0) FGMRES(50), tol 1e-4; |dB error| over 361 phi=0 angles",
+                   "rows": []}
+        cases = [("sphere", 8, None, 3), ("sphere", 16, None, 4), ("coated", 30, 20, LEVELS),
+                 ("coated", 36, 24, LEVELS), ("coated", 42, 28, LEVELS)]
+        for kind, nu_o, nu_i, lv in cases:
+            if kind == "sphere":
+                mesh_r = geo.homogeneous_sphere(nu=nu_o, radius=0.5, eps_r=4.0)
+                ref_r = mie_sph
+            else:
+                mesh_r = geo.coated_sphere(nu_o, nu_i)
+                ref_r = mie_coat
+            t0 = time.perf_counter()
+            sr = sie.Solver(mesh_r, levels=lv, digits=DIGITS, stream=stream)
+            torch.cuda.synchronize()
+            t_set = time.perf_counter() - t0
+            br = sr.vec(1)
+            xr = sr.vec(1)
+            sie.sie_plane_wave_rhs(sr.ctx, inc, br)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            str_ = sie.gmres_solve(sr.ctx, br, xr, 1, restart=RESTART, max_iters=3000, tol=TOL,
+                                   prec=sie.SIE_PREC_MIXED, precond=1, check=False, graphs=not args.no_graphs)[0]
+            rr = sie.rcs_farfield_prec(sr.ctx, xr, 1, obs, sie.SIE_PREC_MIXED)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dd = np.abs(10 * np.log10(rr[0, :, 0]) - 10 * np.log10(ref_r))
+            mie_ref["rows"].append({"body": kind, "nu_outer": nu_o, "nu_inner": nu_i, "unknowns": 2 * sr.ne,
+                                    "levels": lv, "iters": str_["iters"], "converged": str_["converged"],
+                                    "setup_s": t_set, "ms_to_rcs": e0.elapsed_time(e1),
+                                    "mean_abs_db": float(dd.mean()), "max_abs_db": float(dd.max())})
+            del br, xr
+            sr.close()
+
     # iterations versus unknowns per formulation (the comparison of Fig. 6) on the
     # two-layer sphere at four mesh densities: FGMRES(50) with ILU(0) and without
     # a preconditioner, mixed form, tol 1e-4, at most 1000 iterations
@@ -516,7 +560,7 @@ def main():
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
                 "d2h_bytes_per_step": int(rcs.nbytes)},
         "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp,
-        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "stages_ms": stages, "matvec": matvec,
+        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "mie_refinement": mie_ref, "stages_ms": stages, "matvec": matvec,
         "roofline": roofline, "roofline_near_spmv": roofline_near, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
     }
     if rank == 0:

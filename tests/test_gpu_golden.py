@@ -154,6 +154,29 @@ def test_eager_steps_equal_graph_steps(case):
     assert rel(out[0][1], out[1][1]) < 1e-12
 
 
+def test_graph_captured_step_product_matches_oracle(case):
+    """The product inside a captured Krylov-step graph, checked against the
+    dense oracle matrix on every stored case (including the one with the
+    most leaf directions, where aggregation takes four directions per
+    thread).  One FGMRES step without a preconditioner, right-hand side the
+    stored random vector u with its stored dense product Zu, from x0 = 0,
+    returns x1 = alpha u with alpha = (Zu)^H u / |Zu|^2, the minimiser of
+    |u - alpha Z u|.  A relative product error e moves alpha by at most
+    about 2e, hence the 2e-3 bound for the 1e-3 product accuracy."""
+    name, s, d = case
+    u, Zu = d["x"][0], d["y"][0]
+    alpha = np.vdot(Zu, u) / np.vdot(Zu, Zu)
+    for prec in (sie.SIE_PREC_FP64, sie.SIE_PREC_MIXED):
+        rhs = _dev(u, s.ne)
+        x = torch.zeros_like(rhs)
+        st = sie.gmres_solve(s.ctx, rhs, x, 1, restart=1, max_iters=1, tol=1e-12, prec=prec, precond=0,
+                             check=False, graphs=True)
+        assert st[0]["iters"] == 1 and not st[0]["converged"]
+        err = rel(_host(x)[0], alpha * u)
+        print(f"{name} prec={prec}: one graph-launched step, |x1 - alpha u| / |alpha u| = {err:.2e}")
+        assert err < 2e-3
+
+
 def test_block_product_equals_single_products(case):
     """A block of 9 right-hand sides (the translations then run by sibling
     groups) gives the products of the right-hand sides one at a time (per
