@@ -40,8 +40,8 @@ FALLBACK_HBM_GBS = 6800.0
 # ncu capture of that kernel; valid while the kernel is unchanged
 NEAR_SPMV_TRAFFIC_BYTES = 508421888 + 521984
 # DRAM bytes (read + write) of one single-RHS FP32 ILU(0) apply (15 k_ilu_sweep<float, 512>
-# launches) on this workload, from one ncu capture of those launches; valid while the
-# kernel is unchanged
+# launches) on this workload, from one ncu capture of those launches; valid while the kernel
+# is unchanged (None otherwise)
 ILU_APPLY_TRAFFIC_BYTES = 566056448 + 122624
 
 
@@ -513,10 +513,18 @@ def main():
             study["rows"].append(row)
 
     # stage timings (CUDA events on the library stream) and the roofline of the dominant kernel
+    graphs_state = sie.sie_query(s.ctx, 10)
     stages = {}
     for name, stg in (("near_spmv", 0), ("far_mlfmm", 1), ("ilu_sweeps", 2), ("matvec", 3)):
         stages[name] = {"fp32_ms": sie.sie_stage_timing(s.ctx, stg, 1, sie.SIE_PREC_MIXED, 20),
                         "fp64_ms": sie.sie_stage_timing(s.ctx, stg, 1, sie.SIE_PREC_FP64, 10)}
+    # the same ILU(0) apply as one persistent cooperative launch (grid barriers between the steps)
+    sie.sie_set_param(s.ctx, 1, 0)
+    stages["ilu_sweeps_persistent"] = {
+        "fp32_ms": sie.sie_stage_timing(s.ctx, 2, 1, sie.SIE_PREC_MIXED, 20),
+        "fp64_ms": sie.sie_stage_timing(s.ctx, 2, 1, sie.SIE_PREC_FP64, 10)}
+    sie.sie_set_param(s.ctx, 1, 1)
+    sie.sie_device_status(s.ctx)
     nnzb = sie.sie_query(s.ctx, 1)
     near_bytes_fp32 = nnzb * (4 * 8 + 4) + (ne + 1) * 4 + 2 * (2 * ne * 8)
     near_bytes_fp64 = nnzb * (4 * 16 + 4) + (ne + 1) * 4 + 2 * (2 * ne * 16)
@@ -561,7 +569,7 @@ def main():
                 "d2h_bytes_per_step": int(rcs.nbytes)},
         "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp,
         "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "mie_refinement": mie_ref, "stages_ms": stages, "matvec": matvec,
-        "roofline": roofline, "roofline_near_spmv": roofline_near, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
+        "roofline": roofline, "roofline_near_spmv": roofline_near, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches), "krylov_step_graphs": graphs_state,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -314,6 +314,31 @@ sie_status sie_near_export(sie_ctx *ctx, int32_t *rows, int32_t *cols, double *v
  * counterpart. */
 sie_status sie_stage_timing(sie_ctx *ctx, int32_t stage, int64_t nrhs, int32_t prec, int32_t reps, double *ms_out);
 
+/* Bounded device-side waits.  The single-right-hand-side ILU(0) apply can
+ * run its 15 colour steps in one cooperative launch whose steps are separated
+ * by grid barriers (sie_set_param key 1 = 0); a CTA polls a barrier at most
+ * `wait limit` times (about
+ * 0.1-1 us per poll) before it gives up, records the failure in a device
+ * flag and returns, so the launch always ends (its output is then invalid).
+ * sie_device_status synchronises the context's stream and returns
+ * SIE_ETIMEOUT if such a wait gave up since the last call (clearing the
+ * record), SIE_OK otherwise.  gmres_solve checks the record at every restart
+ * and returns SIE_ETIMEOUT.  Not a numerical operation of the method; the
+ * paper has no counterpart. */
+sie_status sie_device_status(sie_ctx *ctx);
+
+/* Runtime parameters (key, value):
+ *   0  wait limit: polls of a device-side barrier before it gives up
+ *      (default 2^21, about a second; 0 makes every wait give up at once,
+ *      for testing the failure path); in [0, 2^30].
+ *   1  schedule of the single-right-hand-side ILU(0) apply: 0 one
+ *      persistent cooperative launch for the 15 colour steps, with grid
+ *      barriers between them; 1 (default, faster on GB300: 0.24 against
+ *      0.37 ms on a 78 000-unknown case) one launch per step, chained by
+ *      programmatic dependent launch.  Same results, bit for bit.
+ * Errors: SIE_EINVAL for an unknown key or a value out of range. */
+sie_status sie_set_param(sie_ctx *ctx, int32_t key, int64_t value);
+
 /* Integer facts about the context for tests and reports: keys
  *   0 n_rwg, 1 near blocks, 2 levels, 3 regions, 4 leaf boxes (all media),
  *   5 bytes of the FP64 near field, 6 bytes of FP64 leaf patterns,
@@ -322,6 +347,8 @@ sie_status sie_stage_timing(sie_ctx *ctx, int32_t stage, int64_t nrhs, int32_t p
  *     blocks with their column indices, in-box inverse blocks, per row the
  *     colour pointers of both sweeps and the source and result vectors; 0
  *     without ILU factors),
+ *   10 Krylov step graphs of the last FGMRES solve: 1 captured and replayed,
+ *     0 capture failed and the steps ran eagerly, -1 none captured,
  *   100 + 16*l + j: K (directions) of medium l at level j. */
 sie_status sie_query(const sie_ctx *ctx, int32_t key, int64_t *value);
 

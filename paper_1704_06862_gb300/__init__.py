@@ -26,7 +26,7 @@ STATUS = {0: "SIE_OK", 1: "SIE_EINVAL", 2: "SIE_ENOMEM", 3: "SIE_ECUDA", 4: "SIE
 EXPORTED = ["sie_create", "sie_destroy", "sie_last_error", "sie_build_mesh", "mlfmm_setup", "sie_fill_nearfield",
             "mlfmm_matvec", "sie_matvec_parts", "ilu_apply", "sie_plane_wave_rhs", "gmres_solve", "rcs_farfield", "rcs_farfield_prec",
             "sie_near_export", "sie_stage_timing", "sie_query", "ilu_apply_noalloc", "nnprec_train",
-            "nnprec_params", "nnprec_loss_grad"]
+            "nnprec_params", "nnprec_loss_grad", "sie_device_status", "sie_set_param"]
 
 
 class SieError(RuntimeError):
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH):
         "nnprec_train": ([P, P, P], I32),
         "nnprec_params": ([P, P, I32], I32),
         "nnprec_loss_grad": ([P, P, P, I64, ctypes.POINTER(D), P], I32),
+        "sie_device_status": ([P], I32),
+        "sie_set_param": ([P, I32, I64], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -284,6 +286,19 @@ def nnprec_loss_grad(ctx, X, T):
     g = np.zeros(NN_PARAMS, np.float32)
     _check(ctx, load_library().nnprec_loss_grad(ctx, _ptr(X), _ptr(T), len(X), ctypes.byref(loss), _ptr(g)))
     return loss.value, g
+
+
+def sie_device_status(ctx):
+    """Raises SieError (SIE_ETIMEOUT) if a bounded device-side wait gave up
+    since the last call; synchronises the context's stream."""
+    _check(ctx, load_library().sie_device_status(ctx))
+
+
+def sie_set_param(ctx, key, value):
+    """Runtime parameter: key 0 the wait limit of device-side barriers (polls),
+    key 1 the single-RHS ILU(0) schedule (0 persistent launch, 1 one launch
+    per colour step, the default)."""
+    _check(ctx, load_library().sie_set_param(ctx, int(key), int(value)))
 
 
 def sie_query(ctx, key):

@@ -39,6 +39,24 @@ cudaError_t launch_chained(bool chained, void (*kern)(KArgs...), dim3 grid, dim3
   return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
 }
 
+// Cooperative launch: every CTA of the grid is resident at once (the driver
+// refuses the launch otherwise), which a grid barrier inside the kernel needs.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cooperative(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                               Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
+
 // ------------------------------------------------------------------ complex
 template <typename T>
 struct cx {
@@ -161,6 +179,7 @@ struct IluHost {
   void *d_tl64 = nullptr, *d_tl32 = nullptr, *d_tu64 = nullptr, *d_tu32 = nullptr;
   int max_box = 0;
   int64_t nblk_off = 0, nblk_inv = 0;  // off-box factor blocks (L and U); in-box inverse blocks
+  unsigned *d_bar = nullptr;  // grid-barrier arrival count of the persistent apply (cleared before each launch)
 };
 
 struct sie_ctx {
@@ -239,6 +258,11 @@ struct sie_ctx {
   void *gm_h = nullptr, *gm_s = nullptr, *gm_part = nullptr, *gm_act = nullptr, *gm_gate = nullptr;
   void *gm_hpin = nullptr;        // pinned host mirror of gm_h (one copy per Krylov step)
   cudaEvent_t gm_ev = nullptr;    // marks that copy
+  // bounded device-side waits: polls before a wait gives up, and the flag a
+  // kernel sets when one did (read and cleared by sie_device_status and the solvers)
+  int wait_limit = 1 << 21;
+  int *d_err = nullptr;
+  int ilu_schedule = 1;           // single-RHS ILU apply: 0 persistent cooperative launch, 1 one launch per step
 };
 
 // ------------------------------------------------------------------ host helpers (host.cpp)
@@ -252,6 +276,9 @@ T *dev_upload(sie_ctx *c, const std::vector<T> &v) {
 }
 void ensure_work(sie_ctx *c, int64_t nrhs);
 void *stage(sie_ctx *c, size_t bytes);
+// throws SIE_ETIMEOUT if a device-side wait gave up since the last check
+// (synchronises the context stream; clears the record)
+void check_device_error(sie_ctx *c);
 void region_streams(sie_ctx *c);  // creates the per-medium streams and events once
 // weights (aTJ, aNJ, aTM, aNM) of medium l for the context's formulation
 void form_weights(const sie_ctx *c, int l, std::complex<double> w[4]);
@@ -298,6 +325,8 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
                               sie_prec prec, sie_prec rprec, int precond, Recorder *rec, sie_solve_stats *st);
 void op_sub(sie_ctx *c, const zd *a, const zd *b, zd *out, int64_t n);
 void graphs_free(sie_ctx *c);
+// Krylov step graphs: -1 none captured yet, 0 capture failed (steps run eagerly), 1 in use
+int graphs_state(const sie_ctx *c);
 
 // ------------------------------------------------------------------ learned preconditioner (nn.cu)
 bool nn_ready(sie_ctx *c);

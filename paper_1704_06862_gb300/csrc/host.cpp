@@ -57,6 +57,21 @@ void *stage(sie_ctx *c, size_t bytes) {
   return c->d_stage;
 }
 
+void check_device_error(sie_ctx *c) {
+  if (!c->d_err) return;
+  int e = 0;
+  SIE_CUDA(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SIE_CUDA(cudaStreamSynchronize(c->stream));
+  if (e) {
+    // a launch that gave up may have left a box's piece count part-way
+    if (c->ilu.d_piece_count)
+      SIE_CUDA(cudaMemsetAsync(c->ilu.d_piece_count, 0, (size_t)c->ilu.nboxes * sizeof(int), c->stream));
+    SIE_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    SIE_CUDA(cudaStreamSynchronize(c->stream));
+    throw SieError{SIE_ETIMEOUT, "a bounded device-side wait gave up (grid barrier of the ILU(0) apply)"};
+  }
+}
+
 void ensure_work(sie_ctx *c, int64_t nrhs) {
   if (nrhs <= c->nrhs_cap) return;
   size_t n = (size_t)nrhs * c->ne * 2;
@@ -1001,6 +1016,11 @@ static void build_ilu(sie_ctx *c) {
     I.d_piece_count = (int *)dev_alloc(c, (size_t)nlb * sizeof(int));
     SIE_CUDA(cudaMemset(I.d_piece_count, 0, (size_t)nlb * sizeof(int)));
     I.d_piece_scratch = dev_alloc(c, std::max<size_t>(1, maxp) * 2 * std::max(1, maxb) * sizeof(cd));
+    I.d_bar = (unsigned *)dev_alloc(c, sizeof(unsigned));
+    if (!c->d_err) {
+      c->d_err = (int *)dev_alloc(c, sizeof(int));
+      SIE_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+    }
   }
   I.d_up_col = dev_upload(c, up_col);
   I.d_lo64 = dev_upload(c, lo_val);
@@ -1335,6 +1355,29 @@ extern "C" sie_status sie_stage_timing(sie_ctx *c, int32_t stage, int64_t nrhs, 
   });
 }
 
+extern "C" sie_status sie_device_status(sie_ctx *c) {
+  return guard(c, [&] { check_device_error(c); });
+}
+
+extern "C" sie_status sie_set_param(sie_ctx *c, int32_t key, int64_t value) {
+  return guard(c, [&] {
+    switch (key) {
+      case 0:
+        SIE_REQUIRE(value >= 0 && value <= (1ll << 30), SIE_EINVAL, "sie_set_param: wait limit out of range");
+        c->wait_limit = (int)value;
+        graphs_free(c);  // captured steps hold the limit as a launch argument
+        break;
+      case 1:
+        SIE_REQUIRE(value == 0 || value == 1, SIE_EINVAL, "sie_set_param: ILU schedule must be 0 or 1");
+        c->ilu_schedule = (int)value;
+        graphs_free(c);  // captured steps hold the other schedule's launches
+        break;
+      default:
+        throw SieError{SIE_EINVAL, "sie_set_param: unknown key"};
+    }
+  });
+}
+
 extern "C" sie_status sie_query(const sie_ctx *c, int32_t key, int64_t *v) {
   if (!c || !v) return SIE_EINVAL;
   switch (key) {
@@ -1356,6 +1399,7 @@ extern "C" sie_status sie_query(const sie_ctx *c, int32_t key, int64_t *v) {
     case 9:  // algorithmic bytes of one single-RHS FP32 ILU(0) apply
       *v = c->ilu.ready ? c->ilu.nblk_off * (32 + 4) + c->ilu.nblk_inv * 32 + (int64_t)c->ne * (2 * 9 * 4 + 2 * 16) : 0;
       return SIE_OK;
+    case 10: *v = graphs_state(c); return SIE_OK;
     default:
       if (key >= 100 && key < 100 + 16 * 64) {
         int l = (key - 100) / 16, j = (key - 100) % 16;

@@ -60,6 +60,17 @@ __device__ __forceinline__ cx<double> ldcg_cx(const cx<double> *p) {
   const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
   return cx<double>(v.x, v.y);
 }
+// the pair through L2 (ld.global.cg): for values written earlier in the same launch
+__device__ __forceinline__ void ldcg_pair(const cx<float> *p, cx<float> &x0, cx<float> &x1) {
+  const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+  x0 = cx<float>(v.x, v.y);
+  x1 = cx<float>(v.z, v.w);
+}
+__device__ __forceinline__ void ldcg_pair(const cx<double> *p, cx<double> &x0, cx<double> &x1) {
+  const double2 v0 = __ldcg(reinterpret_cast<const double2 *>(p)), v1 = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+  x0 = cx<double>(v0.x, v0.y);
+  x1 = cx<double>(v1.x, v1.y);
+}
 __device__ __forceinline__ void ldg_pair(const cx<float> *p, cx<float> &x0, cx<float> &x1) {
   float4 v = __ldg(reinterpret_cast<const float4 *>(p));
   x0 = cx<float>(v.x, v.y);
@@ -69,6 +80,13 @@ __device__ __forceinline__ void ldg_pair(const cx<double> *p, cx<double> &x0, cx
   double2 v0 = __ldg(reinterpret_cast<const double2 *>(p)), v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
   x0 = cx<double>(v0.x, v0.y);
   x1 = cx<double>(v1.x, v1.y);
+}
+// z gathers of the ILU sweeps: a chained step reads values of earlier launches
+// through the read-only path; the persistent kernel reads them through L2
+template <bool CHAINED, typename T>
+__device__ __forceinline__ void ldz_pair(const cx<T> *p, cx<T> &x0, cx<T> &x1) {
+  if (CHAINED) ldg_pair(p, x0, x1);
+  else ldcg_pair(p, x0, x1);
 }
 template <typename T>
 __device__ __forceinline__ cx<T> warp_sum(cx<T> v) {
@@ -784,17 +802,22 @@ __device__ __forceinline__ cx<T> shfl_up(cx<T> v, int d) {
 constexpr int ILU_RL = 8;  // lanes per pushed row
 constexpr int ILU_RU = 2;  // blocks per lane and iteration of a pushed row
 
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int colour, int npieceA,
-                                                  const int *__restrict__ pieces, int rb0, int rb1, int stage_tri,
-                                                  int nmax, cx<T> *scratch, int *counter,
-                                                  const int *__restrict__ box_start,
-                                                  const int *__restrict__ cptr, const int *__restrict__ off_col,
-                                                  const cx<T> *__restrict__ off_val,
-                                                  const int64_t *__restrict__ tri_off, const cx<T> *__restrict__ tri,
-                                                  const int64_t *__restrict__ tri2_off,
-                                                  const cx<T> *__restrict__ tri2, const cx<T> *src, cx<T> *z) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// One work item of a sweep step: a piece of a box of the step's colour
+// (role A, item < npieceA) or a group of rows of the colours still to come
+// (role B).  CHAINED: launched as its own grid with programmatic dependent
+// launch (static prologue before pdl_wait); otherwise called from the
+// persistent kernel, where a grid barrier separates the steps.  Values written
+// earlier in the same launch (z, w, the piece partials) are read through L2
+// (ld.global.cg): L1 is not coherent across CTAs within a launch.
+template <typename T, int NT, bool CHAINED>
+__device__ __forceinline__ void ilu_item(int item, int forward, int both, int colour, int npieceA,
+                                         const int *__restrict__ pieces, int rb0, int rb1, int stage_tri, int nmax,
+                                         cx<T> *scratch, int *counter, const int *__restrict__ box_start,
+                                         const int *__restrict__ cptr, const int *__restrict__ off_col,
+                                         const cx<T> *__restrict__ off_val, const int64_t *__restrict__ tri_off,
+                                         const cx<T> *__restrict__ tri, const int64_t *__restrict__ tri2_off,
+                                         const cx<T> *__restrict__ tri2, const cx<T> *src, cx<T> *z,
+                                         unsigned char *smem_raw) {
   constexpr int NW = NT / 32;
   typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V16;
   constexpr int NV = (int)(4 * sizeof(cx<T>) / sizeof(V16));
@@ -804,19 +827,21 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
   const bool has_src = sc >= 0 && sc < 8;
   // w of rows not yet solved: src before the first forward step has run
   const cx<T> *w = (forward && colour == 0) ? src : z;
-  if ((int)blockIdx.x >= npieceA) {
+  if (item >= npieceA) {
     // ---- role B: rows of later colours take the contribution of colour sc;
     // ILU_RL lanes per row (rows hold about 40 blocks per source colour)
     const int hl = lane & (ILU_RL - 1);
-    const int i = rb0 + ((int)blockIdx.x - npieceA) * (32 / ILU_RL) * NW + (32 / ILU_RL) * warp + lane / ILU_RL;
+    const int i = rb0 + (item - npieceA) * (32 / ILU_RL) * NW + (32 / ILU_RL) * warp + lane / ILU_RL;
     const bool row_ok = i < rb1;
     int q0 = 0, q1 = 0;
     if (row_ok && has_src) {
       q0 = cptr[9 * (size_t)i + sc];
       q1 = cptr[9 * (size_t)i + sc + 1];
     }
-    pdl_wait();
-    pdl_release();
+    if (CHAINED) {
+      pdl_wait();
+      pdl_release();
+    }
     if (!has_src) {
       if (row_ok && hl < 2) z[2 * (size_t)i + hl] = src[2 * (size_t)i + hl];
       return;
@@ -836,7 +861,7 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
       }
       cx<T> xx[ILU_RU][2];
 #pragma unroll
-      for (int u = 0; u < ILU_RU; ++u) ldg_pair(z + 2 * (size_t)cc[u], xx[u][0], xx[u][1]);  // colour sc: not written by this launch
+      for (int u = 0; u < ILU_RU; ++u) ldz_pair<CHAINED>(z + 2 * (size_t)cc[u], xx[u][0], xx[u][1]);
 #pragma unroll
       for (int u = 0; u < ILU_RU; ++u) {
         const cx<T> *bb = reinterpret_cast<const cx<T> *>(uu[u]);
@@ -850,7 +875,7 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
 #pragma unroll
       for (int v = 0; v < NV; ++v) u0[v] = __ldg(Ov + (size_t)q * NV + v);
       cx<T> x0, x1;
-      ldg_pair(z + 2 * (size_t)c0, x0, x1);
+      ldz_pair<CHAINED>(z + 2 * (size_t)c0, x0, x1);
       const cx<T> *b0 = reinterpret_cast<const cx<T> *>(u0);
       a0 = cfma(b0[0], x0, cfma(b0[1], x1, a0));
       a1 = cfma(b0[2], x0, cfma(b0[3], x1, a1));
@@ -861,13 +886,13 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
       a1 += shfl_down(a1, d);
     }
     if (row_ok && hl == 0 && q1 > q0) {
-      z[2 * (size_t)i] -= a0;
-      z[2 * (size_t)i + 1] -= a1;
+      z[2 * (size_t)i] = ldcg_cx(z + 2 * (size_t)i) - a0;
+      z[2 * (size_t)i + 1] = ldcg_cx(z + 2 * (size_t)i + 1) - a1;
     }
     return;
   }
   // ---- role A: one piece of a box of this colour
-  const int *pc = pieces + 5 * (size_t)blockIdx.x;
+  const int *pc = pieces + 5 * (size_t)item;
   const int b = pc[0], v0 = pc[1], v1 = pc[2], kp = pc[3], np = pc[4];
   const int s0 = box_start[b], n = box_start[b + 1] - s0;
   const int ntri = forward ? n * (n - 1) / 2 : n * (n + 1) / 2;
@@ -911,8 +936,10 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
     if (lane == 0) pre[n] = carry;
   }
   __syncthreads();
-  pdl_wait();  // z, w and the piece scratch below come from earlier steps
-  pdl_release();
+  if (CHAINED) {
+    pdl_wait();  // z, w and the piece scratch below come from earlier steps
+    pdl_release();
+  }
   const int total = v1;  // this piece: virtual indices [v0, v1) of the box's blocks from sc
   const int ng = (v1 - v0 + 31) >> 5;
   const int g0 = (int)((int64_t)warp * ng / NW), g1 = (int)((int64_t)(warp + 1) * ng / NW);
@@ -967,14 +994,14 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
     if (rA >= 0) {
       const cx<T> *bb = reinterpret_cast<const cx<T> *>(uA);
       cx<T> x0, x1;
-      ldg_pair(z + 2 * (size_t)cA, x0, x1);
+      ldz_pair<CHAINED>(z + 2 * (size_t)cA, x0, x1);
       a0 = cfma(bb[0], x0, bb[1] * x1);
       a1 = cfma(bb[2], x0, bb[3] * x1);
     }
     if (rB >= 0) {
       const cx<T> *bb = reinterpret_cast<const cx<T> *>(uB);
       cx<T> x0, x1;
-      ldg_pair(z + 2 * (size_t)cB, x0, x1);
+      ldz_pair<CHAINED>(z + 2 * (size_t)cB, x0, x1);
       b0 = cfma(bb[0], x0, bb[1] * x1);
       b1 = cfma(bb[2], x0, bb[3] * x1);
     }
@@ -984,7 +1011,7 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
   __syncthreads();
   if (np == 1) {
     for (int li = threadIdx.x; li < n; li += NT) {
-      cx<T> u0 = w[2 * (size_t)(s0 + li)], u1 = w[2 * (size_t)(s0 + li) + 1];
+      cx<T> u0 = ldcg_cx(w + 2 * (size_t)(s0 + li)), u1 = ldcg_cx(w + 2 * (size_t)(s0 + li) + 1);
       for (int ww = 0; ww < NW; ++ww) {
         u0 -= part[(size_t)ww * 2 * n + 2 * li];
         u1 -= part[(size_t)ww * 2 * n + 2 * li + 1];
@@ -993,7 +1020,7 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
       t[2 * li + 1] = u1;
     }
   } else {
-    cx<T> *mine = scratch + (size_t)blockIdx.x * 2 * nmax;
+    cx<T> *mine = scratch + (size_t)item * 2 * nmax;
     for (int li = threadIdx.x; li < n; li += NT) {
       cx<T> u0, u1;
       for (int ww = 0; ww < NW; ++ww) {
@@ -1011,9 +1038,9 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
     if (!s_last) return;
     __threadfence();
     if (threadIdx.x == 0) counter[b] = 0;  // ready for the next launch
-    const cx<T> *first = scratch + (size_t)(blockIdx.x - kp) * 2 * nmax;
+    const cx<T> *first = scratch + (size_t)(item - kp) * 2 * nmax;
     for (int li = threadIdx.x; li < n; li += NT) {
-      cx<T> u0 = w[2 * (size_t)(s0 + li)], u1 = w[2 * (size_t)(s0 + li) + 1];
+      cx<T> u0 = ldcg_cx(w + 2 * (size_t)(s0 + li)), u1 = ldcg_cx(w + 2 * (size_t)(s0 + li) + 1);
       for (int k = 0; k < np; ++k) {
         const cx<T> *pk = first + (size_t)k * 2 * nmax + 2 * li;
         u0 -= ldcg_cx(pk);
@@ -1057,6 +1084,92 @@ __global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int col
       }
     }
     if (both && pass == 0) __syncthreads();
+  }
+}
+
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_ilu_sweep(int forward, int both, int colour, int npieceA,
+                                                  const int *__restrict__ pieces, int rb0, int rb1, int stage_tri,
+                                                  int nmax, cx<T> *scratch, int *counter,
+                                                  const int *__restrict__ box_start,
+                                                  const int *__restrict__ cptr, const int *__restrict__ off_col,
+                                                  const cx<T> *__restrict__ off_val,
+                                                  const int64_t *__restrict__ tri_off, const cx<T> *__restrict__ tri,
+                                                  const int64_t *__restrict__ tri2_off,
+                                                  const cx<T> *__restrict__ tri2, const cx<T> *src, cx<T> *z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ilu_item<T, NT, true>((int)blockIdx.x, forward, both, colour, npieceA, pieces, rb0, rb1, stage_tri, nmax, scratch,
+                        counter, box_start, cptr, off_col, off_val, tri_off, tri, tri2_off, tri2, src, z, smem_raw);
+}
+
+// The whole single-RHS apply in one cooperative launch: the 15 sweep steps run
+// in order, each over all resident CTAs (work items taken in index order with
+// a stride of the grid size), separated by a grid barrier: every CTA counts
+// itself in on a device-scope counter (release) and waits (acquire) until the
+// whole grid has arrived.  The wait is bounded: after wait_limit polls the
+// CTA records SIE_ETIMEOUT's cause in *err and returns, and every other CTA
+// gives up at its next barrier once *err is set, so the launch always ends.
+// *bar must be zero at launch (cleared on the stream before it).
+struct IluStepDesc {
+  int forward, both, colour, npieceA, piece0, rb0, rb1, nitems;
+  const int *cptr, *col;
+  const void *val;
+  const int64_t *tri_off;
+  const void *tri;
+};
+struct IluPlan {
+  IluStepDesc s[15];
+  int nsteps;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// false when the wait gave up (limit reached, or another CTA gave up first)
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int wait_limit, int *err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    for (int it = 0;; ++it) {
+      if (it >= wait_limit || *(volatile int *)err) {
+        ok = 0;
+        atomicOr(err, 1);
+        break;
+      }
+      if (ld_acquire_gpu(bar) >= target) break;
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_ilu_persistent(IluPlan P, const int *__restrict__ pieces, int stage_tri,
+                                                          int nmax, cx<T> *scratch, int *counter,
+                                                          const int *__restrict__ box_start,
+                                                          const int64_t *__restrict__ tu_off,
+                                                          const cx<T> *__restrict__ tu, const cx<T> *src, cx<T> *z,
+                                                          unsigned *bar, int wait_limit, int *err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int st = 0; st < P.nsteps; ++st) {
+    const IluStepDesc &S = P.s[st];
+    for (int it = blockIdx.x; it < S.nitems; it += gridDim.x) {
+      ilu_item<T, NT, false>(it, S.forward, S.both, S.colour, S.npieceA, pieces + 5 * (size_t)S.piece0, S.rb0, S.rb1,
+                             stage_tri, nmax, scratch, counter, box_start, S.cptr, S.col,
+                             reinterpret_cast<const cx<T> *>(S.val), S.tri_off, reinterpret_cast<const cx<T> *>(S.tri),
+                             tu_off, tu, src, z, smem_raw);
+      __syncthreads();  // shared memory is reused by the next item
+    }
+    if (st + 1 < P.nsteps && !grid_barrier(bar, (unsigned)(st + 1) * gridDim.x, wait_limit, err)) return;
   }
 }
 
@@ -1429,8 +1542,62 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
     const size_t trib = (size_t)mb * (mb + 1) / 2 * 4 * sizeof(cx<T>);
     const int stage = base + trib <= 100 * 1024 ? 1 : 0;
     const size_t smem = base + (stage ? trib : 0);
-    set_smem(k_ilu_sweep<T, NT>, smem);
     auto rows_from = [&](int colr) { return c->leaf_start[I.colour_ptr[colr]]; };
+    if (c->ilu_schedule == 0) {
+      // the 15 steps in one cooperative launch of as many CTAs as fit on the GPU at once
+      auto kern = k_ilu_persistent<T, NT>;
+      set_smem(kern, smem);
+      static std::mutex mu;
+      static std::map<std::pair<int, size_t>, int> grid_of;  // (device, shared bytes) -> resident CTAs
+      int dev = 0;
+      SIE_CUDA(cudaGetDevice(&dev));
+      int grid = 0;
+      {
+        std::lock_guard<std::mutex> lock(mu);
+        int &g = grid_of[{dev * 2 + (sizeof(T) == 4 ? 1 : 0), smem}];
+        if (g == 0) {
+          int per_sm = 0, nsm = 0;
+          SIE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+          SIE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+          SIE_REQUIRE(per_sm >= 1, SIE_EINVAL, "ILU(0) apply: the sweep kernel does not fit on one SM");
+          g = per_sm * nsm;
+        }
+        grid = g;
+      }
+      IluPlan P = {};
+      P.nsteps = 0;
+      for (int step = 0; step < 15; ++step) {
+        const bool fwd = step < 8;
+        const int colr = fwd ? step : 14 - step;
+        const int np = I.piece_ptr[step + 1] - I.piece_ptr[step];
+        const int rb0 = fwd ? rows_from(colr + 1) : 0, rb1 = fwd ? c->ne : rows_from(colr);
+        const int nitems = np + (rb1 - rb0 + (32 / ILU_RL) * NW - 1) / ((32 / ILU_RL) * NW);
+        if (nitems == 0) continue;
+        IluStepDesc &D = P.s[P.nsteps++];
+        D.forward = fwd ? 1 : 0;
+        D.both = colr == 7 ? 1 : 0;
+        D.colour = colr;
+        D.npieceA = np;
+        D.piece0 = I.piece_ptr[step];
+        D.rb0 = rb0;
+        D.rb1 = rb1;
+        D.nitems = nitems;
+        D.cptr = fwd ? I.d_lo_cptr : I.d_up_cptr;
+        D.col = fwd ? I.d_lo_col : I.d_up_col;
+        D.val = fwd ? tsel<T>::lo(I) : tsel<T>::upv(I);
+        D.tri_off = fwd ? I.d_tl_off : I.d_tu_off;
+        D.tri = fwd ? tsel<T>::tl(I) : tsel<T>::tu(I);
+      }
+      SIE_CUDA(cudaMemsetAsync(I.d_bar, 0, sizeof(unsigned), c->stream));
+      SIE_CUDA(launch_cooperative(kern, dim3(grid), dim3(NT), smem, c->stream, P, (const int *)I.d_pieces, stage, mb,
+                                  (cx<T> *)I.d_piece_scratch, I.d_piece_count, (const int *)I.d_box_start,
+                                  (const int64_t *)I.d_tu_off, (const cx<T> *)tsel<T>::tu(I), (const cx<T> *)r, z,
+                                  I.d_bar, c->wait_limit, c->d_err));
+      SIE_CHECK_LAUNCH();
+      c->launches++;
+      return;
+    }
+    set_smem(k_ilu_sweep<T, NT>, smem);
     // forward colours 0..7 (the last also applies U^{-1}), then backward 6..0
     for (int step = 0; step < 15; ++step) {
       const bool fwd = step < 8;

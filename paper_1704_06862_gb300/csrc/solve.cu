@@ -264,6 +264,15 @@ StepGraphs &step_graphs(sie_ctx *c, int m, int R, sie_prec prec, int precond) {
 
 }  // namespace
 
+int graphs_state(const sie_ctx *c) {
+  if (!c->graphs) return -1;
+  const StepGraphs &G = *(const StepGraphs *)c->graphs;
+  if (!G.ok) return 0;
+  for (auto e : G.ex)
+    if (e) return 1;
+  return -1;
+}
+
 void graphs_free(sie_ctx *c) {
   if (!c->graphs) return;
   StepGraphs *G = (StepGraphs *)c->graphs;
@@ -334,6 +343,7 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
     }
     first = false;
     g.norms(w, d_h, rn);
+    check_device_error(c);  // a preconditioner apply whose bounded wait gave up
     bool any = false;
     for (int r = 0; r < R; ++r) {
       relres[r] = bn[r] > 0 ? rn[r] / bn[r] : (std::isnan(bn[r]) ? bn[r] : 0.0);
@@ -476,6 +486,7 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
     if (status != SIE_OK) break;
   }
   SIE_CUDA(cudaStreamSynchronize(c->stream));
+  check_device_error(c);
   bool conv = true;
   for (int r = 0; r < R; ++r) {
     if (st) {
@@ -565,6 +576,7 @@ sie_status run_bicg_internal(sie_ctx *c, const zd *b, zd *x, int R, int max_iter
       axpy(b, mone, w, r, 0);
     }
     dots(r, r, rn2);
+    check_device_error(c);
     bool any = false;
     for (int q = 0; q < R; ++q) {
       relres[q] = relnorm(rn2, q);
@@ -681,6 +693,7 @@ sie_status run_bicg_internal(sie_ctx *c, const zd *b, zd *x, int R, int max_iter
     }
   }
   SIE_CUDA(cudaStreamSynchronize(c->stream));
+  check_device_error(c);
   bool conv = true;
   for (int q = 0; q < R; ++q) {
     if (st) {

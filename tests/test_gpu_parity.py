@@ -151,6 +151,59 @@ def test_ilu_apply(coated, prec, tol):
     assert rel(_host(out)[0], z.reshape(-1)) < tol
 
 
+@pytest.mark.parametrize("prec", [sie.SIE_PREC_FP64, sie.SIE_PREC_MIXED])
+def test_ilu_schedules_agree(coated, prec):
+    """One persistent cooperative launch for the 15 colour steps and one
+    launch per step (the default) give identical results (same items, same
+    order)."""
+    c = coated
+    v = _dev(geo.random_coefficients(2 * c.ne, 1, seed=22)[0], c.ne)
+    out = []
+    try:
+        for sched in (0, 1):
+            sie.sie_set_param(c.s.ctx, 1, sched)
+            z = torch.full_like(v, float("nan"))
+            sie.ilu_apply(c.s.ctx, v, z, 1, prec)
+            out.append(_host(z))
+    finally:
+        sie.sie_set_param(c.s.ctx, 1, 1)
+    assert np.all(np.isfinite(out[0])) and np.array_equal(out[0], out[1])
+
+
+def test_ilu_barrier_wait_gives_up_cleanly(coated):
+    """The grid barriers of the persistent ILU(0) apply have a bounded wait.
+    With a wait limit of 0 every barrier gives up at once (no GPU fault, no
+    hang): sie_device_status and gmres_solve report SIE_ETIMEOUT, and with
+    the limit restored the same context applies ILU(0) correctly again."""
+    c = coated
+    sie.sie_set_param(c.s.ctx, 1, 0)
+    v = _dev(geo.random_coefficients(2 * c.ne, 1, seed=23)[0], c.ne)
+    ref = torch.zeros_like(v)
+    sie.ilu_apply(c.s.ctx, v, ref, 1, sie.SIE_PREC_MIXED)
+    sie.sie_device_status(c.s.ctx)
+    try:
+        sie.sie_set_param(c.s.ctx, 0, 0)
+        z = torch.zeros_like(v)
+        sie.ilu_apply(c.s.ctx, v, z, 1, sie.SIE_PREC_MIXED)
+        with pytest.raises(sie.SieError) as e:
+            sie.sie_device_status(c.s.ctx)
+        assert e.value.code == 7
+        sie.sie_device_status(c.s.ctx)        # the record was cleared
+        b = torch.zeros_like(v)
+        sie.sie_plane_wave_rhs(c.s.ctx, [[0.0, 0.0, 0.0, 1.0]], b)
+        with pytest.raises(sie.SieError) as e:
+            sie.gmres_solve(c.s.ctx, b, torch.zeros_like(b), 1, restart=50, max_iters=100, tol=1e-4,
+                            prec=sie.SIE_PREC_MIXED, precond=1)
+        assert e.value.code == 7
+    finally:
+        sie.sie_set_param(c.s.ctx, 0, 1 << 21)
+    z = torch.zeros_like(v)
+    sie.ilu_apply(c.s.ctx, v, z, 1, sie.SIE_PREC_MIXED)
+    sie.sie_device_status(c.s.ctx)
+    sie.sie_set_param(c.s.ctx, 1, 1)
+    assert torch.equal(z, ref)
+
+
 @pytest.mark.parametrize("prec,tol", [(sie.SIE_PREC_FP64, 1e-9), (sie.SIE_PREC_MIXED, 1e-4)])
 def test_ilu_apply_block(coated, prec, tol):
     """ILU(0) applied to a block of 10 right-hand sides (two passes of the
