@@ -202,6 +202,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the formulation comparison leg")
     ap.add_argument("--no-nano", action="store_true", help="skip the plasmonic nanoparticle leg")
     ap.add_argument("--no-mie-refinement", action="store_true", help="skip the RCS-vs-Mie mesh refinement leg")
+    ap.add_argument("--cube-sweep", type=int, default=0,
+                    help="incidences of the cube's monostatic sweep (0: skip the leg)")
+    ap.add_argument("--cube-block", type=int, default=64, help="right-hand sides per block of the cube sweep")
+    ap.add_argument("--tuning-file", default=None, help="where the cube leg's autotuner writes its choice (JSON)")
     ap.add_argument("--formulation-study", action="store_true",
                     help="add the iterations-versus-unknowns study of the formulations on the two-layer sphere")
     args = ap.parse_args()
@@ -483,6 +487,60 @@ def main():
             del br, xr
             sr.close()
 
+    # monostatic RCS sweep of the lossy dielectric cube (3 lambda0, eps 6 - 0.6j,
+    # 104 976 unknowns): the incidences solved as blocks of right-hand sides
+    # (block products, block ILU sweeps, FGMRES in lockstep), mixed form,
+    # ILU(0) FGMRES(50) to 1e-4, theta-theta RCS of each incidence
+    cube = None
+    if args.cube_sweep > 0:
+        t0 = time.perf_counter()
+        sc = sie.Solver(geo.workload("cube_c3"), levels=LEVELS, digits=DIGITS, stream=stream)
+        torch.cuda.synchronize()
+        cube = {"workload": "cube_c3", "unknowns": 2 * sc.ne, "levels": LEVELS, "incidences": args.cube_sweep,
+                "block": args.cube_block, "setup_s": time.perf_counter() - t0}
+        inc_c = geo.monostatic_incidences(args.cube_sweep)
+        B = min(args.cube_block, args.cube_sweep)
+        # tile shapes of the block kernels for this block size, chosen by the autotuner
+        far_default = sie.sie_stage_timing(sc.ctx, 1, B, sie.SIE_PREC_MIXED, 3)
+        cube["tuning"] = sie.sie_autotune(sc.ctx, B, reps=2, path=args.tuning_file)
+        cube["far_ms_per_block_default_tiles"] = far_default
+        bc = sc.vec(B)
+        xc = sc.vec(B)
+        # untimed: work buffers of the block size and the first captured steps
+        sie.sie_plane_wave_rhs(sc.ctx, inc_c[:B], bc)
+        sie.gmres_solve(sc.ctx, bc, xc, B, restart=RESTART, max_iters=2, tol=TOL, prec=sie.SIE_PREC_MIXED,
+                        precond=1, check=False, graphs=not args.no_graphs)
+        torch.cuda.synchronize()
+        mono_c = np.zeros(args.cube_sweep)
+        iters_c = []
+        conv_c = True
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i0 in range(0, args.cube_sweep, B):
+            nb_ = min(B, args.cube_sweep - i0)
+            sie.sie_plane_wave_rhs(sc.ctx, inc_c[i0:i0 + nb_], bc[:nb_])
+            xc.zero_()
+            stc = sie.gmres_solve(sc.ctx, bc[:nb_], xc[:nb_], nb_, restart=RESTART, max_iters=3000, tol=TOL,
+                                  prec=sie.SIE_PREC_MIXED, precond=1, check=False, graphs=not args.no_graphs)
+            obs_c = np.stack([inc_c[i0:i0 + nb_, 0], inc_c[i0:i0 + nb_, 1]], axis=1)
+            rc = sie.rcs_farfield_prec(sc.ctx, xc[:nb_], nb_, obs_c, sie.SIE_PREC_MIXED)
+            mono_c[i0:i0 + nb_] = rc[np.arange(nb_), np.arange(nb_), 0]
+            iters_c += [t["iters"] for t in stc]
+            conv_c = conv_c and all(t["converged"] for t in stc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_c = e0.elapsed_time(e1)
+        db_c = 10 * np.log10(mono_c)
+        cube.update({"ms_sweep": ms_c, "rhs_per_s": args.cube_sweep / (ms_c / 1e3),
+                     "ms_per_rhs": ms_c / args.cube_sweep, "iters_max": max(iters_c), "iters_mean": float(np.mean(iters_c)),
+                     "all_converged": conv_c, "mirror_symmetry_max_db": float(np.max(np.abs(db_c - db_c[::-1]))),
+                     "far_ms_per_rhs_at_block": sie.sie_stage_timing(sc.ctx, 1, B, sie.SIE_PREC_MIXED, 3) / B,
+                     "far_ms_per_rhs_single": sie.sie_stage_timing(sc.ctx, 1, 1, sie.SIE_PREC_MIXED, 10),
+                     "monostatic_rcs_dbsm": [round(float(v), 3) for v in db_c]})
+        del bc, xc
+        sc.close()
+
     # iterations versus unknowns per formulation (the comparison of Fig. 6) on the
     # two-layer sphere at four mesh densities: FGMRES(50) with ILU(0) and without
     # a preconditioner, mixed form, tol 1e-4, at most 1000 iterations
@@ -568,7 +626,7 @@ def main():
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
                 "d2h_bytes_per_step": int(rcs.nbytes)},
         "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp,
-        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "mie_refinement": mie_ref, "stages_ms": stages, "matvec": matvec,
+        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "mie_refinement": mie_ref, "cube_monostatic": cube, "stages_ms": stages, "matvec": matvec,
         "roofline": roofline, "roofline_near_spmv": roofline_near, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches), "krylov_step_graphs": graphs_state,
     }
     if rank == 0:

@@ -336,8 +336,34 @@ sie_status sie_device_status(sie_ctx *ctx);
  *      barriers between them; 1 (default, faster on GB300: 0.24 against
  *      0.37 ms on a 78 000-unknown case) one launch per step, chained by
  *      programmatic dependent launch.  Same results, bit for bit.
+ *   2  tensor-core leaf aggregation (FP32 operator of the Krylov steps, not
+ *      the true residual): used from this many right-hand sides on (default
+ *      16; 0 never), in [0, 4096].
+ *   3  right-hand sides per pass of the tensor-core aggregation: 0 (by the
+ *      block size, default), 16, 32 or 64.
+ *   4  right-hand sides per block load of the near-field product (blocks of
+ *      right-hand sides): 0 (default: 8 in FP32, 4 in FP64), 4, 8 or 16.
+ *   5  the same for the block ILU(0) sweeps.
+ *   6  right-hand sides per pass of the leaf receive: 0 (default 4), 1, 2, 4.
+ *   7  M2L form: -1 (default: sibling groups from 8 right-hand sides on, per
+ *      target box below), 0 per target box, 1 sibling groups from 2 on.
+ * Keys 2-7 are tile shapes: results agree to rounding (the tensor-core
+ * aggregation to its FP32-level split operands), speed differs.
  * Errors: SIE_EINVAL for an unknown key or a value out of range. */
 sie_status sie_set_param(sie_ctx *ctx, int32_t key, int64_t value);
+
+/* Autotuner of the tile shapes for blocks of nrhs right-hand sides (FP32
+ * kernels of the mixed form): coordinate descent over the parameters of
+ * sie_set_param keys 4 (near field), 5 (ILU sweeps), 2-3 (aggregation:
+ * SIMT or tensor cores and their pass size), 6 (receive), 7 (M2L form), each
+ * candidate timed with CUDA events on the context's stream over `reps`
+ * launches of its stage after a warm-up launch; the fastest is kept in the
+ * context.  choice_out [5] receives (near RB, ILU RB, aggregation: 0 SIMT or
+ * the tensor-core pass size, receive RB, M2L form); ms_out [3] (or NULL) the
+ * best near-field, ILU and far-field milliseconds.  nrhs in [2, 4096].
+ * Allocates work buffers for nrhs right-hand sides.  Synchronous.  Not a
+ * numerical operation of the method; the paper has no counterpart. */
+sie_status sie_autotune(sie_ctx *ctx, int64_t nrhs, int32_t reps, int64_t *choice_out, double *ms_out);
 
 /* Integer facts about the context for tests and reports: keys
  *   0 n_rwg, 1 near blocks, 2 levels, 3 regions, 4 leaf boxes (all media),

@@ -26,7 +26,7 @@ STATUS = {0: "SIE_OK", 1: "SIE_EINVAL", 2: "SIE_ENOMEM", 3: "SIE_ECUDA", 4: "SIE
 EXPORTED = ["sie_create", "sie_destroy", "sie_last_error", "sie_build_mesh", "mlfmm_setup", "sie_fill_nearfield",
             "mlfmm_matvec", "sie_matvec_parts", "ilu_apply", "sie_plane_wave_rhs", "gmres_solve", "rcs_farfield", "rcs_farfield_prec",
             "sie_near_export", "sie_stage_timing", "sie_query", "ilu_apply_noalloc", "nnprec_train",
-            "nnprec_params", "nnprec_loss_grad", "sie_device_status", "sie_set_param"]
+            "nnprec_params", "nnprec_loss_grad", "sie_device_status", "sie_set_param", "sie_autotune"]
 
 
 class SieError(RuntimeError):
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
         "nnprec_loss_grad": ([P, P, P, I64, ctypes.POINTER(D), P], I32),
         "sie_device_status": ([P], I32),
         "sie_set_param": ([P, I32, I64], I32),
+        "sie_autotune": ([P, I64, I32, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -162,27 +163,54 @@ def sie_fill_nearfield(ctx, outer_order=4, build_ilu=True, formulation=FORM_JMCF
     _check(ctx, load_library().sie_fill_nearfield(ctx, ctypes.byref(o)))
 
 
+# Stream order between torch and the library.  The library works on its
+# context's stream; torch tensors are filled and read on torch's current
+# stream.  A call on device buffers first waits for torch's pending work on
+# its inputs and outputs, and the asynchronous calls below wait for their own
+# work before returning, so their results are ready for torch (and a bounded
+# device wait that gave up is reported as SIE_ETIMEOUT).
+def _torch_ready():
+    import sys
+    torch = sys.modules.get("torch")
+    if torch is not None and torch.cuda.is_initialized():
+        torch.cuda.current_stream().synchronize()
+
+
+def _done(ctx):
+    _check(ctx, load_library().sie_device_status(ctx))
+
+
 def mlfmm_matvec(ctx, x, y, nrhs, prec=SIE_PREC_FP64):
+    _torch_ready()
     _check(ctx, load_library().mlfmm_matvec(ctx, _ptr(x), _ptr(y), int(nrhs), int(prec)))
+    _done(ctx)
 
 
 def sie_matvec_parts(ctx, x, y, nrhs, prec=SIE_PREC_FP64, parts=3):
+    _torch_ready()
     _check(ctx, load_library().sie_matvec_parts(ctx, _ptr(x), _ptr(y), int(nrhs), int(prec), int(parts)))
+    _done(ctx)
 
 
 def ilu_apply(ctx, r, z, nrhs, prec=SIE_PREC_FP64):
+    _torch_ready()
     _check(ctx, load_library().ilu_apply(ctx, _ptr(r), _ptr(z), int(nrhs), int(prec)))
+    _done(ctx)
 
 
 def ilu_apply_noalloc(ctx, r, z, nrhs, prec=SIE_PREC_FP64):
     """ilu_apply without any device allocation (scratch: a fixed 16 MiB
     array inside the library; nrhs * n_rwg <= 174762)."""
+    _torch_ready()
     _check(ctx, load_library().ilu_apply_noalloc(ctx, _ptr(r), _ptr(z), int(nrhs), int(prec)))
+    _done(ctx)
 
 
 def sie_plane_wave_rhs(ctx, inc, b):
     inc = np.ascontiguousarray(np.atleast_2d(inc), np.float64)
+    _torch_ready()
     _check(ctx, load_library().sie_plane_wave_rhs(ctx, _ptr(inc), len(inc), _ptr(b)))
+    _done(ctx)
 
 
 SOLVE_FGMRES, SOLVE_BICGSTAB, SOLVE_CGS = 0, 1, 2
@@ -201,6 +229,7 @@ def gmres_solve(ctx, b, x, nrhs, restart=50, max_iters=1000, tol=1e-4, prec=SIE_
     check=True a failed convergence raises SieError."""
     o = sie_solve_opts(int(restart), int(max_iters), float(tol), int(prec), int(precond), int(method),
                        0 if graphs else 1, 1 if residual_far_fp64 else 0)
+    _torch_ready()
     st = (sie_solve_stats * int(nrhs))()
     rc = load_library().gmres_solve(ctx, _ptr(b), _ptr(x), int(nrhs), ctypes.byref(o), st)
     stats = [dict(iters=s.iters, restarts=s.restarts, rel_residual=s.rel_residual, converged=bool(s.converged))
@@ -213,6 +242,7 @@ def gmres_solve(ctx, b, x, nrhs, restart=50, max_iters=1000, tol=1e-4, prec=SIE_
 def rcs_farfield(ctx, x, nrhs, obs):
     obs = np.ascontiguousarray(obs, np.float64)
     out = np.zeros((int(nrhs), len(obs), 2), np.float64)
+    _torch_ready()
     _check(ctx, load_library().rcs_farfield(ctx, _ptr(x), int(nrhs), _ptr(obs), len(obs), _ptr(out)))
     return out
 
@@ -220,6 +250,7 @@ def rcs_farfield(ctx, x, nrhs, obs):
 def rcs_farfield_prec(ctx, x, nrhs, obs, prec=SIE_PREC_FP64):
     obs = np.ascontiguousarray(obs, np.float64)
     out = np.zeros((int(nrhs), len(obs), 2), np.float64)
+    _torch_ready()
     _check(ctx, load_library().rcs_farfield_prec(ctx, _ptr(x), int(nrhs), _ptr(obs), len(obs), int(prec), _ptr(out)))
     return out
 
@@ -299,6 +330,37 @@ def sie_set_param(ctx, key, value):
     key 1 the single-RHS ILU(0) schedule (0 persistent launch, 1 one launch
     per colour step, the default)."""
     _check(ctx, load_library().sie_set_param(ctx, int(key), int(value)))
+
+
+TUNING_KEYS = {"near_rb": 4, "ilu_rb": 5, "aggregation": 3, "receive_rb": 6, "m2l": 7}
+
+
+def sie_autotune(ctx, nrhs, reps=3, path=None):
+    """Autotune the block-RHS tile shapes for nrhs right-hand sides (kept in
+    the context).  Returns {"nrhs", "near_rb", "ilu_rb", "aggregation",
+    "receive_rb", "m2l", "ms": [near, ilu, far]}; with a path, also writes it
+    there as JSON (read back with apply_tuning)."""
+    import json
+    ch = np.zeros(5, np.int64)
+    ms = np.zeros(3, np.float64)
+    _check(ctx, load_library().sie_autotune(ctx, int(nrhs), int(reps), _ptr(ch), _ptr(ms)))
+    out = {"nrhs": int(nrhs), "near_rb": int(ch[0]), "ilu_rb": int(ch[1]), "aggregation": int(ch[2]),
+           "receive_rb": int(ch[3]), "m2l": int(ch[4]), "ms": [float(v) for v in ms]}
+    if path:
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+    return out
+
+
+def apply_tuning(ctx, tuning):
+    """Set the tile shapes of a sie_autotune result (a dict or a JSON path)."""
+    import json
+    if isinstance(tuning, str):
+        with open(tuning) as f:
+            tuning = json.load(f)
+    sie_set_param(ctx, 2, 2 if tuning["aggregation"] else 0)
+    for name, key in TUNING_KEYS.items():
+        sie_set_param(ctx, key, tuning[name])
 
 
 def sie_query(ctx, key):

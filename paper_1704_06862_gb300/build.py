@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsie.so")
-SOURCES = ["host.cpp", "fill.cu", "operator.cu", "solve.cu", "noalloc.cu", "nn.cu"]
+SOURCES = ["host.cpp", "fill.cu", "operator.cu", "solve.cu", "noalloc.cu", "nn.cu", "tensor.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

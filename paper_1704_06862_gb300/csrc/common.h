@@ -263,6 +263,14 @@ struct sie_ctx {
   int wait_limit = 1 << 21;
   int *d_err = nullptr;
   int ilu_schedule = 1;           // single-RHS ILU apply: 0 persistent cooperative launch, 1 one launch per step
+  // tensor-core leaf aggregation (FP32 operator, blocks of right-hand sides):
+  // used from agg_tc_min_rhs right-hand sides on (0: never), agg_tc_rb per pass (0: by block size)
+  int agg_tc_min_rhs = 16, agg_tc_rb = 0;
+  // tile shapes of the block-RHS kernels (0 or -1: the built-in rule; set by
+  // sie_set_param or chosen by sie_autotune): right-hand sides per block load
+  // of the near-field product and the ILU sweeps, per pass of the leaf
+  // receive; M2L form (0 per target box, 1 by sibling groups)
+  int tune_near_rb = 0, tune_ilu_rb = 0, tune_rec_rb = 0, tune_m2l = -1;
 };
 
 // ------------------------------------------------------------------ host helpers (host.cpp)
@@ -301,6 +309,11 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked = false
 void far_fork(sie_ctx *c);
 template <typename T>
 void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs);
+// tensor-core leaf aggregation (tensor.cu): right-hand sides per pass for a
+// block of nrhs (0: the SIMT kernel is used), and the launch for one medium
+int agg_tc_block(const sie_ctx *c, int nrhs);
+bool op_aggregate_tc(sie_ctx *c, int rb, int K, int nbox, int max_leaf, int nrhs, const int *box_start,
+                     const int *basis_p, const int *sign, const zf *V, const zf *x, zf *S, cudaStream_t st);
 void op_permute_in(sie_ctx *c, const zd *user, zd *internal, int nrhs);    // user -> internal
 void op_permute_out(sie_ctx *c, const zd *internal, zd *user, int nrhs);   // internal -> user
 void op_d2f(sie_ctx *c, const zd *a, zf *b, int64_t n);

@@ -1299,15 +1299,10 @@ extern "C" sie_status sie_near_export(sie_ctx *c, int32_t *rows, int32_t *cols, 
   });
 }
 
-extern "C" sie_status sie_stage_timing(sie_ctx *c, int32_t stage, int64_t nrhs, int32_t prec, int32_t reps,
-                                       double *ms) {
-  return guard(c, [&] {
-    SIE_REQUIRE(c->have_fill, SIE_ESTATE, "sie_stage_timing: call sie_fill_nearfield first");
-    SIE_REQUIRE(ms && stage >= 0 && stage <= 3 && nrhs >= 1 && nrhs <= 4096 && reps >= 1, SIE_EINVAL,
-                "sie_stage_timing: bad arguments");
-    SIE_REQUIRE(stage != 2 || c->ilu.ready, SIE_ESTATE, "sie_stage_timing: no ILU factors");
-    SIE_REQUIRE(prec == SIE_PREC_FP64 || prec == SIE_PREC_MIXED || (prec == SIE_PREC_NEAR64 && stage == 3),
-                SIE_EINVAL, "sie_stage_timing: prec 0 or 1 (2 for the whole product only)");
+// Mean device milliseconds of one launch of a stage of the hot path (after one
+// warm-up launch), CUDA events on the context's stream.
+static double time_stage(sie_ctx *c, int stage, int64_t nrhs, int prec, int reps) {
+  {
     ensure_work(c, nrhs);
     size_t n = (size_t)nrhs * c->ne * 2;
     SIE_CUDA(cudaMemsetAsync(c->d_xi, 0, n * sizeof(zd), c->stream));
@@ -1351,7 +1346,81 @@ extern "C" sie_status sie_stage_timing(sie_ctx *c, int32_t stage, int64_t nrhs, 
     SIE_CUDA(cudaEventElapsedTime(&t, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    *ms = (double)t / reps;
+    return (double)t / reps;
+  }
+}
+
+extern "C" sie_status sie_stage_timing(sie_ctx *c, int32_t stage, int64_t nrhs, int32_t prec, int32_t reps,
+                                       double *ms) {
+  return guard(c, [&] {
+    SIE_REQUIRE(c->have_fill, SIE_ESTATE, "sie_stage_timing: call sie_fill_nearfield first");
+    SIE_REQUIRE(ms && stage >= 0 && stage <= 3 && nrhs >= 1 && nrhs <= 4096 && reps >= 1, SIE_EINVAL,
+                "sie_stage_timing: bad arguments");
+    SIE_REQUIRE(stage != 2 || c->ilu.ready, SIE_ESTATE, "sie_stage_timing: no ILU factors");
+    SIE_REQUIRE(prec == SIE_PREC_FP64 || prec == SIE_PREC_MIXED || (prec == SIE_PREC_NEAR64 && stage == 3),
+                SIE_EINVAL, "sie_stage_timing: prec 0 or 1 (2 for the whole product only)");
+    *ms = time_stage(c, stage, nrhs, prec, reps);
+  });
+}
+
+// Autotuner of the block-RHS tile shapes: for each tunable parameter in turn
+// (coordinate descent), time the stage it belongs to for each candidate value
+// with the others held, keep the fastest.  FP32 (mixed-form) kernels.
+extern "C" sie_status sie_autotune(sie_ctx *c, int64_t nrhs, int32_t reps, int64_t *choice, double *ms) {
+  return guard(c, [&] {
+    SIE_REQUIRE(c->have_fill, SIE_ESTATE, "sie_autotune: call sie_fill_nearfield first");
+    SIE_REQUIRE(choice && nrhs >= 2 && nrhs <= 4096 && reps >= 1, SIE_EINVAL, "sie_autotune: bad arguments");
+    const int R = (int)nrhs;
+    graphs_free(c);
+    auto best_of = [&](int stage, int *param, std::initializer_list<int> cands) {
+      double tbest = 1e300;
+      int vbest = *param;
+      for (int v : cands) {
+        *param = v;
+        const double t = time_stage(c, stage, R, SIE_PREC_MIXED, reps);
+        if (t < tbest) {
+          tbest = t;
+          vbest = v;
+        }
+      }
+      *param = vbest;
+      return tbest;
+    };
+    double t_near = best_of(0, &c->tune_near_rb, {4, 8, 16});
+    double t_ilu = c->ilu.ready ? best_of(2, &c->tune_ilu_rb, {4, 8, 16}) : 0.0;
+    // far field: aggregation (0 SIMT, else tensor cores with that many right-hand
+    // sides per pass), receive passes, M2L form
+    int agg = 0;
+    {
+      std::vector<int> cands{0};
+      for (int rb : {16, 32, 64})
+        if (R >= 16 && rb <= std::max(16, R)) cands.push_back(rb);
+      double tb = 1e300;
+      for (int v : cands) {
+        c->agg_tc_min_rhs = v ? 2 : 0;
+        c->agg_tc_rb = v;
+        const double t = time_stage(c, 1, R, SIE_PREC_MIXED, reps);
+        if (t < tb) {
+          tb = t;
+          agg = v;
+        }
+      }
+      c->agg_tc_min_rhs = agg ? 2 : 0;
+      c->agg_tc_rb = agg;
+    }
+    best_of(1, &c->tune_rec_rb, {1, 2, 4});
+    double t_far = best_of(1, &c->tune_m2l, {0, 1});
+    choice[0] = c->tune_near_rb;
+    choice[1] = c->tune_ilu_rb;
+    choice[2] = agg;
+    choice[3] = c->tune_rec_rb;
+    choice[4] = c->tune_m2l;
+    if (ms) {
+      ms[0] = t_near;
+      ms[1] = t_ilu;
+      ms[2] = t_far;
+    }
+    graphs_free(c);
   });
 }
 
@@ -1371,6 +1440,35 @@ extern "C" sie_status sie_set_param(sie_ctx *c, int32_t key, int64_t value) {
         SIE_REQUIRE(value == 0 || value == 1, SIE_EINVAL, "sie_set_param: ILU schedule must be 0 or 1");
         c->ilu_schedule = (int)value;
         graphs_free(c);  // captured steps hold the other schedule's launches
+        break;
+      case 2:
+        SIE_REQUIRE(value >= 0 && value <= 4096, SIE_EINVAL, "sie_set_param: tensor-core aggregation threshold out of range");
+        c->agg_tc_min_rhs = (int)value;
+        graphs_free(c);
+        break;
+      case 3:
+        SIE_REQUIRE(value == 0 || value == 16 || value == 32 || value == 64, SIE_EINVAL,
+                    "sie_set_param: tensor-core aggregation block must be 0, 16, 32 or 64");
+        c->agg_tc_rb = (int)value;
+        graphs_free(c);
+        break;
+      case 4:
+      case 5:
+        SIE_REQUIRE(value == 0 || value == 4 || value == 8 || value == 16, SIE_EINVAL,
+                    "sie_set_param: block size must be 0, 4, 8 or 16");
+        (key == 4 ? c->tune_near_rb : c->tune_ilu_rb) = (int)value;
+        graphs_free(c);
+        break;
+      case 6:
+        SIE_REQUIRE(value == 0 || value == 1 || value == 2 || value == 4, SIE_EINVAL,
+                    "sie_set_param: receive block must be 0, 1, 2 or 4");
+        c->tune_rec_rb = (int)value;
+        graphs_free(c);
+        break;
+      case 7:
+        SIE_REQUIRE(value >= -1 && value <= 1, SIE_EINVAL, "sie_set_param: M2L form must be -1, 0 or 1");
+        c->tune_m2l = (int)value;
+        graphs_free(c);
         break;
       default:
         throw SieError{SIE_EINVAL, "sie_set_param: unknown key"};

@@ -1382,13 +1382,21 @@ template <typename T>
 void op_near(sie_ctx *c, const cx<T> *x, cx<T> *y, int nrhs, bool accumulate) {
   int warps_per_block = 8;
   int blocks = (c->ne + warps_per_block - 1) / warps_per_block;
-  if (nrhs == 1)
+  if (nrhs == 1) {
     k_near_spmv<T><<<blocks, 32 * warps_per_block, 0, c->stream>>>(c->ne, nrhs, c->d_row_ptr, c->d_col,
                                                                    (const cx<T> *)tsel<T>::near(c), x, y,
                                                                    accumulate ? 1 : 0);
-  else
-    k_near_spmv_blk<T, sizeof(T) == 4 ? 8 : 4><<<blocks, 32 * warps_per_block, 0, c->stream>>>(
-        c->ne, nrhs, c->d_row_ptr, c->d_col, (const cx<T> *)tsel<T>::near(c), x, y, accumulate ? 1 : 0);
+  } else {
+    // right-hand sides per block load: tuned, else 8 (FP32) / 4 (FP64)
+    const int rb = c->tune_near_rb ? c->tune_near_rb : (sizeof(T) == 4 ? 8 : 4);
+    auto go = [&](auto kern) {
+      kern<<<blocks, 32 * warps_per_block, 0, c->stream>>>(c->ne, nrhs, c->d_row_ptr, c->d_col,
+                                                          (const cx<T> *)tsel<T>::near(c), x, y, accumulate ? 1 : 0);
+    };
+    if (rb == 16) go(k_near_spmv_blk<T, 16>);
+    else if (rb == 8) go(k_near_spmv_blk<T, 8>);
+    else go(k_near_spmv_blk<T, 4>);
+  }
   SIE_CHECK_LAUNCH();
   c->launches++;
 }
@@ -1421,12 +1429,21 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
         kern<<<LL.nbox, 256, smem, st>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p, G.d_basis_sign,
                                                 (const cx<T> *)tsel<T>::V(G), x, (cx<T> *)LL.d_S);
       };
-      // more than 512 leaf directions: four per thread, one right-hand side per pass
-      if (LL.K > 2 * 256) agg(k_aggregate<T, 1, 4>, 1);
-      else if (R == 1) agg(k_aggregate<T, 1, 2>, 1);
-      else agg(k_aggregate<T, 4, 2>, 4);
-      SIE_CHECK_LAUNCH();
-      c->launches++;
+      // blocks of right-hand sides in the FP32 operator: split-BF16 products on
+      // the tensor cores (not in the true-residual operator, TY = double, whose
+      // accuracy floor decides convergence: there the FP32 SIMT kernel)
+      const int tc_rb = (std::is_same<T, float>::value && std::is_same<TY, float>::value) ? agg_tc_block(c, R) : 0;
+      const bool tc = tc_rb > 0 && op_aggregate_tc(c, tc_rb, LL.K, LL.nbox, G.max_leaf, R, G.d_box_start,
+                                                   G.d_basis_p, G.d_basis_sign, (const zf *)tsel<T>::V(G),
+                                                   (const zf *)x, (zf *)LL.d_S, st);
+      if (!tc) {
+        // more than 512 leaf directions: four per thread, one right-hand side per pass
+        if (LL.K > 2 * 256) agg(k_aggregate<T, 1, 4>, 1);
+        else if (R == 1) agg(k_aggregate<T, 1, 2>, 1);
+        else agg(k_aggregate<T, 4, 2>, 4);
+        SIE_CHECK_LAUNCH();
+        c->launches++;
+      }
     }
     // upward pass: interpolate + shift each child, then sum into parents
     for (int lv = leaf; lv >= 3; --lv) {
@@ -1460,7 +1477,8 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
     // CTAs in flight), by sibling groups for blocks of 8 or more (fewer loads)
     for (int lv = 2; lv <= leaf; ++lv) {
       LevelHost &B = G.lev[lv];
-      if (R >= 8 && B.ngroups > 0) {
+      const bool by_group = B.ngroups > 0 && (c->tune_m2l >= 0 ? (c->tune_m2l == 1 && R >= 2) : R >= 8);
+      if (by_group) {
         SIE_REQUIRE(B.ngroups <= 65535 && R <= 65535, SIE_EINVAL, "MLFMM: too many sibling groups for one launch");
         dim3 grid((B.K + 127) / 128, B.ngroups, R);
         const size_t smem = (size_t)B.max_group_entries * 10 * sizeof(int);
@@ -1522,10 +1540,13 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
                                                 cx<T>((T)ie.real(), (T)ie.imag()), y, cx<T>((T)cj.real(), (T)cj.imag()),
                                                 cx<T>((T)cm.real(), (T)cm.imag()));
       };
-      // blocks of right-hand sides four at a time while the box's fields fit in shared memory
-      const bool fits4 = STAGES * cb * per_basis + (size_t)4 * 4 * LL.K * sizeof(cx<T>) <= 227 * 1024;
-      if (R == 1 || !fits4) rec(k_disaggregate<T, 1, TY>, 1);
-      else rec(k_disaggregate<T, 4, TY>, 4);
+      // blocks of right-hand sides RB at a time (tuned, else 4) while the box's fields fit in shared memory
+      auto fits = [&](int rb) { return STAGES * cb * per_basis + (size_t)rb * 4 * LL.K * sizeof(cx<T>) <= 227 * 1024; };
+      int rb = R == 1 ? 1 : (c->tune_rec_rb ? c->tune_rec_rb : 4);
+      while (rb > 1 && !fits(rb)) rb /= 2;
+      if (rb == 4) rec(k_disaggregate<T, 4, TY>, 4);
+      else if (rb == 2) rec(k_disaggregate<T, 2, TY>, 2);
+      else rec(k_disaggregate<T, 1, TY>, 1);
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
@@ -1622,26 +1643,32 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
     }
     return;
   }
-  // block of right-hand sides: the same 15 steps, RB right-hand sides per block load
-  constexpr int RB = sizeof(T) == 4 ? 8 : 4;
-  const size_t smem = 2 * (size_t)RB * 2 * mb * sizeof(cx<T>);
-  set_smem(k_ilu_sweep_blk<T, RB>, smem);
-  auto rows_from = [&](int colr) { return c->leaf_start[I.colour_ptr[colr]]; };
-  for (int step = 0; step < 15; ++step) {
-    const bool fwd = step < 8;
-    const int colr = fwd ? step : 14 - step;
-    const int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
-    const int rb0 = fwd ? rows_from(colr + 1) : 0, rb1 = fwd ? c->ne : rows_from(colr);
-    const int grid = cnt + (rb1 - rb0 + 31) / 32;  // role B: 32 rows per 256-thread CTA
-    if (grid == 0) continue;
-    k_ilu_sweep_blk<T, RB><<<grid, 256, smem, c->stream>>>(
-        c->ne, nrhs, fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, cnt, first, rb0, rb1, I.d_box_start,
-        fwd ? I.d_lo_cptr : I.d_up_cptr, fwd ? I.d_lo_col : I.d_up_col,
-        (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? I.d_tl_off : I.d_tu_off,
-        (const cx<T> *)(fwd ? tsel<T>::tl(I) : tsel<T>::tu(I)), I.d_tu_off, (const cx<T> *)tsel<T>::tu(I), r, z);
-    SIE_CHECK_LAUNCH();
-    c->launches++;
-  }
+  // block of right-hand sides: the same 15 steps, RB right-hand sides per block
+  // load (tuned, else 8 in FP32 and 4 in FP64)
+  const int rbq = c->tune_ilu_rb ? c->tune_ilu_rb : (sizeof(T) == 4 ? 8 : 4);
+  auto sweeps = [&](auto kern, int RB) {
+    const size_t smem = 2 * (size_t)RB * 2 * mb * sizeof(cx<T>);
+    set_smem(kern, smem);
+    auto rows_from = [&](int colr) { return c->leaf_start[I.colour_ptr[colr]]; };
+    for (int step = 0; step < 15; ++step) {
+      const bool fwd = step < 8;
+      const int colr = fwd ? step : 14 - step;
+      const int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
+      const int rb0 = fwd ? rows_from(colr + 1) : 0, rb1 = fwd ? c->ne : rows_from(colr);
+      const int grid = cnt + (rb1 - rb0 + 31) / 32;  // role B: 32 rows per 256-thread CTA
+      if (grid == 0) continue;
+      kern<<<grid, 256, smem, c->stream>>>(
+          c->ne, nrhs, fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, cnt, first, rb0, rb1, I.d_box_start,
+          fwd ? I.d_lo_cptr : I.d_up_cptr, fwd ? I.d_lo_col : I.d_up_col,
+          (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? I.d_tl_off : I.d_tu_off,
+          (const cx<T> *)(fwd ? tsel<T>::tl(I) : tsel<T>::tu(I)), I.d_tu_off, (const cx<T> *)tsel<T>::tu(I), r, z);
+      SIE_CHECK_LAUNCH();
+      c->launches++;
+    }
+  };
+  if (rbq == 16 && 2 * (size_t)16 * 2 * mb * sizeof(cx<T>) <= 227 * 1024) sweeps(k_ilu_sweep_blk<T, 16>, 16);
+  else if (rbq >= 8) sweeps(k_ilu_sweep_blk<T, 8>, 8);
+  else sweeps(k_ilu_sweep_blk<T, 4>, 4);
 }
 
 void op_permute_in(sie_ctx *c, const zd *u, zd *v, int nrhs) {

@@ -1,0 +1,332 @@
+// Tensor-core (tcgen05) contractions of the MLFMM for blocks of right-hand
+// sides: leaf aggregation S_b = sum_{n in b} V_n (x) [eta0 c, v]_n as a dense
+// product per leaf box, in split BF16 with FP32 accumulation in tensor memory.
+//
+// For one box with n bases, K directions and a pass of RB right-hand sides,
+// the complex product S[(t,k)][(jm,r)] = sum_n V[n][t][k] X[n][jm][r] is the
+// real product  D = A B  with
+//   rows    m = 2 (t K + k) + ri        (4K rows: theta/phi, direction, re/im)
+//   columns j = jm RB + r               (2 RB: J/M source, right-hand side)
+//   inner   c = 2 n + ci                (2 n: basis, re/im of the coefficient)
+//   A[m][c] = (ri, ci) = (0,0): Re V, (0,1): -Im V, (1,0): Im V, (1,1): Re V
+//   B[c][j] = s_n Re x (ci = 0) or s_n Im x (ci = 1), x the coefficient of basis n.
+// Each operand is split into three BF16 parts, a = a0 + a1 + a2 with
+// a0 = bf16(a), a1 = bf16(a - a0), a2 = bf16(a - a0 - a1) (8 significant bits
+// each, about 24 together), and D accumulates the six products a_i b_j with
+// i + j <= 2 (the dropped terms are below 2^-26 of the product): FP32-level
+// operands.  Two parts (three products, about 16 bits) are not enough here:
+// the diagonal translations that follow add many plane-wave terms much larger
+// than their sum (the more so the larger the truncation L), which amplified
+// the 16-bit operands' error to 2e-4 of the whole product on a test cube.
+//
+// Mapping (one CTA per leaf box, 256 threads):
+//   * B (all k-steps of the box) is staged once per pass of right-hand sides;
+//   * A is staged per 128-row tile of D and chunk of two 16-wide k-steps;
+//   * one thread issues the MMAs (M = 128, N = 2 RB, K = 16, kind::f16 with
+//     BF16 operands, both K-major, no swizzle) into a 128 x N FP32 tile in
+//     tensor memory and commits them to an mbarrier; the waits on it are
+//     bounded (SIE_ETIMEOUT's flag, then the CTA frees its tensor memory and
+//     returns);
+//   * the eight warps read the tile back (tcgen05.ld, warp w its lane
+//     quarter w % 4 and column half w / 4) and write S.
+// Shared-memory operand layout: the canonical no-swizzle K-major form, core
+// matrices of 8 rows x 16 bytes (8 BF16 along K), 128 bytes each; within one
+// k-step the two core matrices of a row group are 128 bytes apart (leading
+// byte offset) and row groups 256 bytes apart (stride byte offset).
+#include <cuda_bf16.h>
+
+#include "common.h"
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor of tcgen05.mma: start address, leading and
+// stride byte offsets (all >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
+// 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase with the given parity; false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    if (mbar_try_wait(b, parity)) return true;
+    if (it > 64) __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {  // one whole warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {  // one whole warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 32 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row, col) of a k-major operand tile stored as
+// consecutive 16-wide k-steps of `rows` rows each (no-swizzle core matrices)
+__device__ __forceinline__ uint32_t op_off(int row, int col, int rows) {
+  const int s = col >> 4, cc = col & 15;
+  return (uint32_t)(s * rows * 32 + (row >> 3) * 256 + (cc >> 3) * 128 + (row & 7) * 16 + (cc & 7) * 2);
+}
+// the three BF16 parts of v, stored at byte offset off of the parts' arrays
+// (consecutive arrays `stride` bytes apart)
+__device__ __forceinline__ void split_store(unsigned char *base, size_t stride, uint32_t off, float v) {
+  const __nv_bfloat16 p0 = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(p0);
+  const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+  *reinterpret_cast<__nv_bfloat16 *>(base + off) = p0;
+  *reinterpret_cast<__nv_bfloat16 *>(base + stride + off) = p1;
+  *reinterpret_cast<__nv_bfloat16 *>(base + 2 * stride + off) = p2;
+}
+
+constexpr int TC_THREADS = 256;
+constexpr int TC_M = 128;     // rows of one D tile
+constexpr int TC_KCH = 2;     // k-steps of A staged at a time
+constexpr int TC_PARTS = 3;   // BF16 parts per operand
+constexpr int TC_A_BYTES = TC_KCH * TC_M * 32;  // one part of an A chunk
+
+// Leaf aggregation of one medium on the tensor cores, RB right-hand sides per
+// pass (N = 2 RB columns).  ks_max: 16-wide k-steps of the largest box.
+template <int RB>
+__global__ void __launch_bounds__(TC_THREADS) k_aggregate_tc(int K, int ne, int nrhs, int ks_max,
+                                                            const int *__restrict__ box_start,
+                                                            const int *__restrict__ basis_p,
+                                                            const int *__restrict__ sign,
+                                                            const cx<float> *__restrict__ V,
+                                                            const cx<float> *__restrict__ x, cx<float> *__restrict__ S,
+                                                            int wait_limit, int *err) {
+  constexpr int N = 2 * RB;
+  constexpr int NCOLS = N < 32 ? 32 : N;  // tensor-memory columns (a power of two >= 32)
+  constexpr uint32_t IDESC = idesc_bf16_f32(TC_M, N);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const size_t bpart = (size_t)ks_max * N * 32;  // bytes of one part of B
+  unsigned char *Bp = smem_raw;                    // [TC_PARTS][ks_max k-steps][N rows][16]
+  unsigned char *Ap = Bp + TC_PARTS * bpart;       // [TC_PARTS][TC_KCH k-steps][128 rows][16]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
+  const int ks = max(1, (2 * n + 15) >> 4);  // k-steps of this box (an empty box: one step of zeros, D = 0)
+  const int K2 = 2 * K;              // (theta/phi, direction) pairs
+  const int mtiles = (2 * K2 + TC_M - 1) / TC_M;
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    s_fail = 0;
+  }
+  if (warp == 0) tmem_alloc(&s_tmem, NCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  unsigned phase = 0;
+  for (int r0 = 0; r0 < nrhs && !s_fail; r0 += RB) {
+    const int nr = min(RB, nrhs - r0);
+    // ---- B: all k-steps of the box, rows j = (jm, r), columns c = (basis, re/im)
+    for (int idx = tid; idx < N * ks * 8; idx += TC_THREADS) {
+      // one thread per (row j, pair of columns = one basis)
+      const int j = idx % N, cp = idx / N;  // cp: basis slot 0 .. 8 ks - 1
+      const int jm = j / RB, r = j - jm * RB;
+      float re = 0.f, im = 0.f;
+      if (cp < n && r < nr) {
+        const int p = basis_p[i0 + cp];
+        const float sg = (float)sign[i0 + cp];
+        const cx<float> v = x[((size_t)(r0 + r) * ne + p) * 2 + jm];
+        re = sg * v.re;
+        im = sg * v.im;
+      }
+      split_store(Bp, bpart, op_off(j, 2 * cp, N), re);
+      split_store(Bp, bpart, op_off(j, 2 * cp + 1, N), im);
+    }
+    for (int mt = 0; mt < mtiles; ++mt) {
+      for (int k0 = 0; k0 < ks; k0 += TC_KCH) {
+        const int kn = min(TC_KCH, ks - k0);
+        // ---- A chunk: rows m = 2 tk + ri of this tile, columns of k-steps k0 .. k0 + kn
+        for (int idx = tid; idx < 64 * kn * 8; idx += TC_THREADS) {
+          const int tkl = idx & 63, nbl = idx >> 6;  // (direction pair, basis) of the chunk
+          const int tk = mt * 64 + tkl, nb = k0 * 8 + nbl;
+          float vr = 0.f, vi = 0.f;
+          if (tk < K2 && nb < n) {
+            const cx<float> v = V[(size_t)(i0 + nb) * K2 + tk];
+            vr = v.re;
+            vi = v.im;
+          }
+          const int c = 2 * nbl;  // column within the chunk
+          split_store(Ap, TC_A_BYTES, op_off(2 * tkl, c, TC_M), vr);
+          split_store(Ap, TC_A_BYTES, op_off(2 * tkl, c + 1, TC_M), -vi);
+          split_store(Ap, TC_A_BYTES, op_off(2 * tkl + 1, c, TC_M), vi);
+          split_store(Ap, TC_A_BYTES, op_off(2 * tkl + 1, c + 1, TC_M), vr);
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          tc_fence_after();
+          for (int s = 0; s < kn; ++s) {
+            // the six part products a_i b_j with i + j <= 2, smallest first
+            for (int q = 0; q < 6; ++q) {
+              const int i = q < 3 ? 2 - q : (q < 5 ? 1 - (q - 3) : 0), jj = q < 3 ? q : (q < 5 ? q - 3 : 0);
+              const uint64_t ad = smem_desc(smem_u32(Ap + i * TC_A_BYTES + s * TC_M * 32), 128, 256);
+              const uint64_t bd = smem_desc(smem_u32(Bp + jj * bpart + (size_t)(k0 + s) * N * 32), 128, 256);
+              tc_mma(tmem, ad, bd, IDESC, (k0 + s) > 0 || q > 0 ? 1 : 0);
+            }
+          }
+          tc_commit(&mbar);
+        }
+        // the products have read this chunk (and, at the last chunk, D is complete)
+        const bool ok = mbar_wait(&mbar, phase, wait_limit);
+        phase ^= 1u;
+        if (!ok) {
+          if (lane == 0) atomicOr(err, 1);
+          s_fail = 1;
+        }
+        tc_fence_after();
+        __syncthreads();
+        if (s_fail) break;
+      }
+      if (s_fail) break;
+      // ---- D tile -> S: warp w reads lanes 32 (w % 4) .. + 31, columns (w / 4) N/2 .. + N/2
+      {
+        const int m = 32 * (warp & 3) + lane, gm = mt * TC_M + m;
+        const int tk = gm >> 1, ri = gm & 1;
+        const int t = tk / K, k = tk - t * K;
+        const int jc0 = (warp >> 2) * (N / 2);
+        for (int c0 = 0; c0 < N / 2; c0 += 32) {
+          float v[32];
+          if (N / 2 >= 32) {
+            tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(jc0 + c0), v);
+          } else {
+            // N / 2 = 16: read the 32 columns once (warps 0-3) and keep this half
+            float w[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16), w);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = w[jc0 + q];
+          }
+          if (tk < K2) {
+            const int cmax = min(32, N / 2 - c0);
+            for (int q = 0; q < cmax; ++q) {
+              const int j = jc0 + c0 + q, jm = j / RB, r = j - jm * RB;
+              if (r < nr) {
+                float *o = reinterpret_cast<float *>(S + ((size_t)b * 4 * nrhs + (size_t)(jm * 2 + t) * nrhs + r0 + r) * K + k);
+                o[ri] = v[q];
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();  // D read by every warp before the next tile's products overwrite it
+      tc_fence_after();
+    }
+  }
+  // after a wait gave up the products may still be in flight: wait for them
+  // (bounded again) before the tensor memory is freed
+  if (s_fail) mbar_wait(&mbar, phase ^ 1u, wait_limit);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
+template <int RB>
+size_t agg_tc_smem(int max_leaf) {
+  const int ks_max = std::max(1, (2 * max_leaf + 15) / 16);
+  return (size_t)TC_PARTS * ks_max * (2 * RB) * 32 + TC_PARTS * (size_t)TC_A_BYTES;
+}
+
+template <int RB>
+void launch_agg_tc(sie_ctx *c, int K, int nbox, int max_leaf, int nrhs, const int *box_start, const int *basis_p,
+                   const int *sign, const zf *V, const zf *x, zf *S, cudaStream_t st) {
+  const int ks_max = std::max(1, (2 * max_leaf + 15) / 16);
+  const size_t smem = agg_tc_smem<RB>(max_leaf);
+  static bool raised[64] = {};
+  int dev = 0;
+  SIE_CUDA(cudaGetDevice(&dev));
+  if (dev < 64 && !raised[dev]) {
+    SIE_CUDA(cudaFuncSetAttribute(k_aggregate_tc<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    raised[dev] = true;
+  }
+  k_aggregate_tc<RB><<<nbox, TC_THREADS, smem, st>>>(K, c->ne, nrhs, ks_max, box_start, basis_p, sign, V, x, S,
+                                                     c->wait_limit, c->d_err);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+
+}  // namespace
+
+// block size of the tensor-core aggregation for nrhs right-hand sides (0: not used)
+int agg_tc_block(const sie_ctx *c, int nrhs) {
+  if (c->agg_tc_min_rhs <= 0 || nrhs < c->agg_tc_min_rhs) return 0;
+  if (c->agg_tc_rb) return c->agg_tc_rb;
+  return nrhs >= 64 ? 64 : nrhs >= 32 ? 32 : 16;
+}
+
+bool op_aggregate_tc(sie_ctx *c, int rb, int K, int nbox, int max_leaf, int nrhs, const int *box_start,
+                     const int *basis_p, const int *sign, const zf *V, const zf *x, zf *S, cudaStream_t st) {
+  // fewer right-hand sides per pass while the largest box's operands do not fit in shared memory
+  auto fits = [&](int r) {
+    return (r == 64 ? agg_tc_smem<64>(max_leaf) : r == 32 ? agg_tc_smem<32>(max_leaf) : agg_tc_smem<16>(max_leaf)) <=
+           200 * 1024;
+  };
+  while (rb > 16 && !fits(rb)) rb /= 2;
+  if (!fits(rb)) return false;
+  switch (rb) {
+    case 16: launch_agg_tc<16>(c, K, nbox, max_leaf, nrhs, box_start, basis_p, sign, V, x, S, st); return true;
+    case 32: launch_agg_tc<32>(c, K, nbox, max_leaf, nrhs, box_start, basis_p, sign, V, x, S, st); return true;
+    case 64: launch_agg_tc<64>(c, K, nbox, max_leaf, nrhs, box_start, basis_p, sign, V, x, S, st); return true;
+    default: return false;
+  }
+}

@@ -118,6 +118,68 @@ def tetra_body(size=0.3, eps_r=4.0):
     return dict(verts=v, tris=t, tri_regions=regions, media=media)
 
 
+def cube_surface(n: int, side: float, center=(0.0, 0.0, 0.0)):
+    """Closed cube surface of edge ``side`` on a structured grid of n x n
+    squares per face, each square cut into two right triangles: 12 n^2
+    triangles, 18 n^2 edges, 6 n^2 + 2 vertices, normals pointing outward.
+    Vertices are merged across faces by exact integer lattice keys.  The
+    diagonal of each square leans one way in the lower half of a face and
+    the other way in the upper half (with respect to each in-plane axis), so
+    for even n the triangulation is mirror-symmetric under x -> -x, y -> -y
+    and z -> -z (the mirror images of the RCS are exact symmetries of the
+    discrete problem, not only of the body)."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    key_to_idx: dict = {}
+    pts = []
+    tris = []
+
+    def vid(ijk):
+        idx = key_to_idx.get(ijk)
+        if idx is None:
+            idx = len(pts)
+            key_to_idx[ijk] = idx
+            pts.append(ijk)
+        return idx
+
+    h = n / 2.0
+    for axis in range(3):
+        a1, a2 = (axis + 1) % 3, (axis + 2) % 3
+        for side_sign in (0, n):
+            for i in range(n):
+                for j in range(n):
+                    def corner(di, dj):
+                        p = [0, 0, 0]
+                        p[axis] = side_sign
+                        p[a1] = i + di
+                        p[a2] = j + dj
+                        return vid(tuple(p))
+                    v00, v10, v01, v11 = corner(0, 0), corner(1, 0), corner(0, 1), corner(1, 1)
+                    # lean of the diagonal mirrors about the face's centre lines
+                    if (i + 0.5 < h) == (j + 0.5 < h):
+                        tris.append((v00, v10, v11))
+                        tris.append((v00, v11, v01))
+                    else:
+                        tris.append((v00, v10, v01))
+                        tris.append((v10, v11, v01))
+    P = (np.array(pts, dtype=np.float64) / n - 0.5) * side + np.asarray(center, np.float64)
+    T = np.array(tris, dtype=np.int32)
+    c = P[T].mean(axis=1) - np.asarray(center)
+    nrm = np.cross(P[T[:, 1]] - P[T[:, 0]], P[T[:, 2]] - P[T[:, 0]])
+    flip = np.einsum("ij,ij->i", nrm, c) < 0
+    T[flip] = T[flip][:, [0, 2, 1]]
+    return P, T
+
+
+def dielectric_cube(n=54, side=3.0, eps_r=6.0 - 0.6j, mu_r=1.0):
+    """Homogeneous (lossy) dielectric cube in free space, one interface."""
+    v, t = cube_surface(n, side)
+    regions = np.tile(np.array([[0, 1]], np.int32), (len(t), 1))
+    eps = complex(eps_r)
+    media = np.array([[1.0, 0.0, 1.0, 0.0], [eps.real, eps.imag, mu_r, 0.0]], np.float64)
+    return dict(verts=v, tris=t, tri_regions=regions, media=media)
+
+
 # Plasmonic coated nanoparticle: silver-like core in a gold-like shell at
 # 545 THz (lambda0 = 550 nm).  Assumed round permittivities with negative real
 # parts and loss (e^{+jwt}: eps'' < 0), of the size of noble-metal data at
@@ -136,6 +198,12 @@ def workload(name: str):
         return coated_sphere(12, 8)
     if name == "nanoparticle":   # plasmonic coated sphere (core 230, shell 250 at 550 nm), 30 720 unknowns
         return coated_sphere(16, 16, 250 / 550, 230 / 550, NANO_EPS_SHELL, NANO_EPS_CORE)
+    if name == "cube_c3":        # cube 3 lambda0, eps 6 - 0.6j, 54 x 54 squares per face, 104 976 unknowns
+        return dielectric_cube(54, 3.0, 6.0 - 0.6j)
+    if name == "cube_small":     # same material, 0.6 lambda0, 14 x 14 squares per face: dense CPU checks
+        return dielectric_cube(14, 0.6, 6.0 - 0.6j)
+    if name == "cube_tiny":      # same material, 0.6 lambda0, 6 x 6 squares per face
+        return dielectric_cube(6, 0.6, 6.0 - 0.6j)
     if name == "coated_tiny":    # coated sphere small enough for dense CPU checks
         return coated_sphere(6, 4)
     if name == "sphere_tiny":

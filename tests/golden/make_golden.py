@@ -16,6 +16,10 @@ Cases
                250/550 (eps -5 - 2j), nu 6/6 (4320 unknowns); 3-level tree.
                Its Mie series is also the reference of the finer
                nanoparticle workload (same radii, media and angles).
+  cube_small   lossy dielectric cube (eps 6 - 0.6j), edge 0.6 lambda0, 14 x 14
+               squares per face (7056 unknowns); 3-level tree; no Mie series
+               (stored as NaN); also the monostatic theta-theta RCS of 8
+               theta-polarised incidences theta_i in [0, pi], phi = 0.
 Stored: seeded x (2 columns), y = Z x, y_near = Z_near x (touching-box
 pattern), plane-wave excitation b, dense-LU solution, bistatic RCS of that
 solution at 361 angles, and the Mie series at the same angles.
@@ -56,6 +60,13 @@ CASES = {
     "nanoparticle": dict(mesh=lambda: geo.coated_sphere(6, 6, 250 / 550, 230 / 550, geo.NANO_EPS_SHELL,
                                                         geo.NANO_EPS_CORE),
                          levels=3, coated=(230 / 550, 250 / 550), eps=(geo.NANO_EPS_CORE, geo.NANO_EPS_SHELL)),
+    # lossy dielectric cube (eps 6 - 0.6j, the material of the cube workload),
+    # edge 0.6 lambda0, 14 x 14 squares per face: sharp edges and corners, no
+    # closed form (no Mie series); monostatic RCS of 8 incidences stored
+    # (triangles at most 0.3 of the leaf box edge, as in the cube workload: on a
+    # coarser mesh the RWG supports overhang their boxes and the far part of
+    # the product loses accuracy whatever the number of directions)
+    "cube_small": dict(mesh=lambda: geo.workload("cube_small"), levels=3, mie=False, mono=8),
 }
 
 
@@ -74,13 +85,22 @@ def make(name):
     xs = solvers.lu_solve(Z, b[0])
     obs = geo.bistatic_angles(361)
     rcs = farfield.rcs(m, xs[None], obs)[0]
-    if "coated" in spec:
+    extra = {}
+    if not spec.get("mie", True):
+        ref = np.full(len(obs), np.nan)
+    elif "coated" in spec:
         ec, es = spec.get("eps", (4.0, 2.56))
         ref = mie.coated_bistatic(spec["coated"][0], spec["coated"][1], ec, es, obs[:, 0])
     else:
         ref = mie.sphere_bistatic(spec["radius"], spec.get("eps", 4.0), obs[:, 0])
+    if "mono" in spec:
+        # monostatic sweep: theta-polarised incidences theta_i in [0, pi], phi = 0, received theta-theta
+        minc = geo.monostatic_incidences(spec["mono"])
+        X = np.stack([solvers.lu_solve(Z, bb) for bb in fill.rhs(m, minc)])
+        R = farfield.rcs(m, X, np.stack([minc[:, 0], minc[:, 1]], axis=1))
+        extra = dict(mono_inc=minc, mono_rcs=np.array([R[i, i, 0] for i in range(len(minc))]))
     np.savez_compressed(os.path.join(HERE, f"{name}.npz"), x=x, y=y, y_near=y_near, b=b, xs=xs, obs=obs,
-                        rcs=rcs, mie=ref, levels=spec["levels"], ne=m.ne)
+                        rcs=rcs, mie=ref, levels=spec["levels"], ne=m.ne, **extra)
     err = np.abs(10 * np.log10(rcs[:, 0]) - 10 * np.log10(ref))
     print(f"{name}: ne={m.ne} fill+solve {time.time() - t0:.0f}s  RCS vs Mie mean {err.mean():.3f} dB, "
           f"max {err.max():.3f} dB")

@@ -1,7 +1,8 @@
 """Parity at the measured workloads' full size (coated sphere, 78 000
 unknowns, 5-level MLFMM, the launch configuration bench.py times; plasmonic
 coated nanoparticle, 30 720 unknowns, 4-level MLFMM, bench.py's nanoparticle
-leg): the product
+leg; lossy dielectric cube, 104 976 unknowns, 5-level MLFMM, bench.py's
+monostatic sweep): the product
 is checked on rows the oracle computes one by one (dense JMCFIE rows of the
 sampled bases against all bases), and the near-field entries of those rows
 element by element.
@@ -20,7 +21,7 @@ from oracle import fill, tree  # noqa: E402
 from oracle.rwg import Mesh  # noqa: E402
 
 
-@pytest.fixture(scope="module", params=[("coated_c2", 5), ("nanoparticle", 4)])
+@pytest.fixture(scope="module", params=[("coated_c2", 5), ("nanoparticle", 4), ("cube_c3", 5)])
 def full(request):
     import __graft_entry__ as g
     g.build()

@@ -173,7 +173,8 @@ def test_ilu_schedules_agree(coated, prec):
 def test_ilu_barrier_wait_gives_up_cleanly(coated):
     """The grid barriers of the persistent ILU(0) apply have a bounded wait.
     With a wait limit of 0 every barrier gives up at once (no GPU fault, no
-    hang): sie_device_status and gmres_solve report SIE_ETIMEOUT, and with
+    hang): the call (through sie_device_status) and gmres_solve report
+    SIE_ETIMEOUT, and with
     the limit restored the same context applies ILU(0) correctly again."""
     c = coated
     sie.sie_set_param(c.s.ctx, 1, 0)
@@ -184,9 +185,8 @@ def test_ilu_barrier_wait_gives_up_cleanly(coated):
     try:
         sie.sie_set_param(c.s.ctx, 0, 0)
         z = torch.zeros_like(v)
-        sie.ilu_apply(c.s.ctx, v, z, 1, sie.SIE_PREC_MIXED)
-        with pytest.raises(sie.SieError) as e:
-            sie.sie_device_status(c.s.ctx)
+        with pytest.raises(sie.SieError) as e:   # the binding reads the device record after the call
+            sie.ilu_apply(c.s.ctx, v, z, 1, sie.SIE_PREC_MIXED)
         assert e.value.code == 7
         sie.sie_device_status(c.s.ctx)        # the record was cleared
         b = torch.zeros_like(v)

@@ -49,3 +49,24 @@ def test_incidence_sets():
     inc = geo.monostatic_incidences(16)
     assert inc.shape == (16, 4) and np.isclose(inc[-1, 0], np.pi)
     assert np.all(inc[:, 1] == 0) and np.all(inc[:, 2] == 0) and np.all(inc[:, 3] == 1)
+
+
+def test_cube_workload():
+    """Cube of the monostatic workload: 3 lambda0 edge, 54 x 54 squares per
+    face (104 976 unknowns), eps 6 - 0.6j; closed, outward, mirror-symmetric."""
+    m = geo.workload("cube_c3")
+    assert _unknowns(m) == 104976
+    v, t = m["verts"], m["tris"]
+    assert np.allclose(v.min(axis=0), -1.5) and np.allclose(v.max(axis=0), 1.5)
+    eps = m["media"][1, 0] + 1j * m["media"][1, 1]
+    assert eps == 6.0 - 0.6j
+    s = geo.workload("cube_small")
+    vs, ts = s["verts"], s["tris"]
+    vol = np.sum(np.einsum("ij,ij->i", vs[ts[:, 0]], np.cross(vs[ts[:, 1]], vs[ts[:, 2]]))) / 6
+    assert np.isclose(vol, 0.6 ** 3)                     # closed and outward
+    key = lambda V: {tuple(sorted(tuple(np.round(V[i], 9)) for i in tr)) for tr in ts}
+    ref = key(vs)
+    for ax in range(3):
+        w = vs.copy()
+        w[:, ax] *= -1
+        assert key(w) == ref                               # mirror-symmetric triangulation
