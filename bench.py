@@ -206,6 +206,8 @@ def main():
                     help="incidences of the cube's monostatic sweep (0: skip the leg)")
     ap.add_argument("--cube-block", type=int, default=64, help="right-hand sides per block of the cube sweep")
     ap.add_argument("--tuning-file", default=None, help="where the cube leg's autotuner writes its choice (JSON)")
+    ap.add_argument("--ellipsoid", action="store_true",
+                    help="add the ellipsoid leg (355 488 unknowns, learned preconditioner on 32 incidences)")
     ap.add_argument("--formulation-study", action="store_true",
                     help="add the iterations-versus-unknowns study of the formulations on the two-layer sphere")
     args = ap.parse_args()
@@ -541,6 +543,52 @@ def main():
         del bc, xc
         sc.close()
 
+    # lossy dielectric ellipsoid (semi-axes 4 x 2 x 1 lambda0, eps 3 - 0.2j,
+    # 355 488 unknowns, 7 levels): the learned preconditioner trained on
+    # solver-generated pairs of 32 random incidences (uniform on the sphere,
+    # seed 2017), then ILU(0) FGMRES against ILU(0) + network FGMRES on held-out
+    # incidences (seed 2018), mixed form, tol 1e-4
+    ell = None
+    if args.ellipsoid:
+        t0 = time.perf_counter()
+        se = sie.Solver(geo.workload("ellipsoid_c4"), levels=7, digits=DIGITS, stream=stream)
+        torch.cuda.synchronize()
+        ell = {"workload": "ellipsoid_c4", "unknowns": 2 * se.ne, "levels": 7, "setup_s": time.perf_counter() - t0}
+
+        def uniform_incidences(n, seed):
+            rng = np.random.default_rng(seed)
+            return np.stack([np.arccos(rng.uniform(-1, 1, n)), rng.uniform(0, 2 * np.pi, n), np.zeros(n),
+                             np.ones(n)], axis=1)
+
+        ell["train"] = sie.nnprec_train(se.ctx, uniform_incidences(32, 2017), record_restart=5, max_pairs=256,
+                                        epochs=12, batch=4096, lr=1e-3, seed=7)
+        test_inc = uniform_incidences(4, 2018)
+        be = se.vec(1)
+        xe = se.vec(1)
+        rows = []
+        for i in range(len(test_inc)):
+            sie.sie_plane_wave_rhs(se.ctx, test_inc[i:i + 1], be)
+            row = {"theta": float(test_inc[i, 0]), "phi": float(test_inc[i, 1])}
+            for label, pc in (("ilu", 1), ("ilu_nn", 2)):
+                if pc == 2 and not ell["train"]["enabled"]:
+                    continue
+                xe.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ste = sie.gmres_solve(se.ctx, be, xe, 1, restart=RESTART, max_iters=3000, tol=TOL,
+                                      prec=sie.SIE_PREC_MIXED, precond=pc, check=False, graphs=not args.no_graphs)[0]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row[label] = {"iters": ste["iters"], "converged": ste["converged"], "ms": e0.elapsed_time(e1)}
+            rows.append(row)
+        ell["held_out"] = rows
+        ell["far_ms"] = sie.sie_stage_timing(se.ctx, 1, 1, sie.SIE_PREC_MIXED, 5)
+        ell["matvec_ms"] = sie.sie_stage_timing(se.ctx, 3, 1, sie.SIE_PREC_MIXED, 5)
+        ell["ilu_ms"] = sie.sie_stage_timing(se.ctx, 2, 1, sie.SIE_PREC_MIXED, 5)
+        del be, xe
+        se.close()
+
     # iterations versus unknowns per formulation (the comparison of Fig. 6) on the
     # two-layer sphere at four mesh densities: FGMRES(50) with ILU(0) and without
     # a preconditioner, mixed form, tol 1e-4, at most 1000 iterations
@@ -626,7 +674,7 @@ def main():
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
                 "d2h_bytes_per_step": int(rcs.nbytes)},
         "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp,
-        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "mie_refinement": mie_ref, "cube_monostatic": cube, "stages_ms": stages, "matvec": matvec,
+        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "mie_refinement": mie_ref, "cube_monostatic": cube, "ellipsoid": ell, "stages_ms": stages, "matvec": matvec,
         "roofline": roofline, "roofline_near_spmv": roofline_near, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches), "krylov_step_graphs": graphs_state,
     }
     if rank == 0:

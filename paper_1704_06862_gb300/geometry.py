@@ -171,6 +171,79 @@ def cube_surface(n: int, side: float, center=(0.0, 0.0, 0.0)):
     return P, T
 
 
+def box_surface(nx: int, ny: int, nz: int):
+    """Closed surface of the cube [-1, 1]^3 on a structured grid with nx, ny,
+    nz divisions along x, y, z, each rectangle cut into two triangles whose
+    diagonals mirror about the faces' centre lines (as in cube_surface):
+    4 (nx ny + ny nz + nz nx) triangles, outward normals."""
+    n = (nx, ny, nz)
+    key_to_idx: dict = {}
+    pts = []
+    tris = []
+
+    def vid(ijk):
+        idx = key_to_idx.get(ijk)
+        if idx is None:
+            idx = len(pts)
+            key_to_idx[ijk] = idx
+            pts.append(ijk)
+        return idx
+
+    for axis in range(3):
+        a1, a2 = (axis + 1) % 3, (axis + 2) % 3
+        for side_sign in (0, n[axis]):
+            for i in range(n[a1]):
+                for j in range(n[a2]):
+                    def corner(di, dj):
+                        p = [0, 0, 0]
+                        p[axis] = side_sign
+                        p[a1] = i + di
+                        p[a2] = j + dj
+                        return vid(tuple(p))
+                    v00, v10, v01, v11 = corner(0, 0), corner(1, 0), corner(0, 1), corner(1, 1)
+                    if (2 * i + 1 < n[a1]) == (2 * j + 1 < n[a2]):
+                        tris.append((v00, v10, v11))
+                        tris.append((v00, v11, v01))
+                    else:
+                        tris.append((v00, v10, v01))
+                        tris.append((v10, v11, v01))
+    P = 2.0 * np.array(pts, dtype=np.float64) / np.array(n, dtype=np.float64) - 1.0
+    T = np.array(tris, dtype=np.int32)
+    c = P[T].mean(axis=1)
+    nrm = np.cross(P[T[:, 1]] - P[T[:, 0]], P[T[:, 2]] - P[T[:, 0]])
+    flip = np.einsum("ij,ij->i", nrm, c) < 0
+    T[flip] = T[flip][:, [0, 2, 1]]
+    return P, T
+
+
+def ellipsoid_surface(m: int, axes=(4.0, 2.0, 1.0)):
+    """Tri-axial ellipsoid with semi-axes (a, b, c), a >= b >= c, by the
+    cube-sphere mapping: the surface of [-1, 1]^3 with divisions proportional
+    to the semi-axes (m a / c, m b / c, m along x, y, z) is projected radially
+    onto the unit sphere and scaled by the semi-axes, which keeps the
+    triangles near-isotropic.  Every vertex lies on the ellipsoid; outward
+    normals.  4 m^2 (ab + bc + ca) / c^2 triangles."""
+    a, b, c = (float(v) for v in axes)
+    nx, ny, nz = int(round(m * a / c)), int(round(m * b / c)), int(m)
+    P, T = box_surface(nx, ny, nz)
+    U = P / np.linalg.norm(P, axis=1, keepdims=True)
+    V = U * np.array([a, b, c])
+    ctr = V[T].mean(axis=1)
+    nrm = np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]])
+    flip = np.einsum("ij,ij->i", nrm, ctr) < 0
+    T[flip] = T[flip][:, [0, 2, 1]]
+    return V, T
+
+
+def dielectric_ellipsoid(m=46, axes=(4.0, 2.0, 1.0), eps_r=3.0 - 0.2j, mu_r=1.0):
+    """Homogeneous (lossy) dielectric ellipsoid in free space, one interface."""
+    v, t = ellipsoid_surface(m, axes)
+    regions = np.tile(np.array([[0, 1]], np.int32), (len(t), 1))
+    eps = complex(eps_r)
+    media = np.array([[1.0, 0.0, 1.0, 0.0], [eps.real, eps.imag, mu_r, 0.0]], np.float64)
+    return dict(verts=v, tris=t, tri_regions=regions, media=media)
+
+
 def dielectric_cube(n=54, side=3.0, eps_r=6.0 - 0.6j, mu_r=1.0):
     """Homogeneous (lossy) dielectric cube in free space, one interface."""
     v, t = cube_surface(n, side)
@@ -204,6 +277,10 @@ def workload(name: str):
         return dielectric_cube(14, 0.6, 6.0 - 0.6j)
     if name == "cube_tiny":      # same material, 0.6 lambda0, 6 x 6 squares per face
         return dielectric_cube(6, 0.6, 6.0 - 0.6j)
+    if name == "ellipsoid_c4":   # semi-axes 4 x 2 x 1 lambda0, eps 3 - 0.2j, 355 488 unknowns
+        return dielectric_ellipsoid(46, (4.0, 2.0, 1.0), 3.0 - 0.2j)
+    if name == "ellipsoid_small":  # semi-axes 1.0 x 0.5 x 0.25 lambda0, same material: dense CPU checks
+        return dielectric_ellipsoid(4, (1.0, 0.5, 0.25), 3.0 - 0.2j)
     if name == "coated_tiny":    # coated sphere small enough for dense CPU checks
         return coated_sphere(6, 4)
     if name == "sphere_tiny":

@@ -20,6 +20,9 @@ Cases
                squares per face (7056 unknowns); 3-level tree; no Mie series
                (stored as NaN); also the monostatic theta-theta RCS of 8
                theta-polarised incidences theta_i in [0, pi], phi = 0.
+  ellipsoid_small  lossy dielectric ellipsoid (eps 3 - 0.2j), semi-axes 1.0 x
+               0.5 x 0.25 lambda0, cube-sphere mesh (2688 unknowns); 4-level
+               tree; no Mie series; monostatic RCS of 8 incidences as above.
 Stored: seeded x (2 columns), y = Z x, y_near = Z_near x (touching-box
 pattern), plane-wave excitation b, dense-LU solution, bistatic RCS of that
 solution at 361 angles, and the Mie series at the same angles.
@@ -67,6 +70,9 @@ CASES = {
     # coarser mesh the RWG supports overhang their boxes and the far part of
     # the product loses accuracy whatever the number of directions)
     "cube_small": dict(mesh=lambda: geo.workload("cube_small"), levels=3, mie=False, mono=8),
+    # tri-axial lossy dielectric ellipsoid (eps 3 - 0.2j, the material of the
+    # ellipsoid workload), semi-axes 1.0 x 0.5 x 0.25 lambda0, cube-sphere mesh
+    "ellipsoid_small": dict(mesh=lambda: geo.workload("ellipsoid_small"), levels=4, mie=False, mono=8),
 }
 
 

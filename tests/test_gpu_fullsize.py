@@ -2,7 +2,8 @@
 unknowns, 5-level MLFMM, the launch configuration bench.py times; plasmonic
 coated nanoparticle, 30 720 unknowns, 4-level MLFMM, bench.py's nanoparticle
 leg; lossy dielectric cube, 104 976 unknowns, 5-level MLFMM, bench.py's
-monostatic sweep): the product
+monostatic sweep; lossy dielectric ellipsoid, 355 488 unknowns, 7-level
+MLFMM, bench.py's learned-preconditioner leg): the product
 is checked on rows the oracle computes one by one (dense JMCFIE rows of the
 sampled bases against all bases), and the near-field entries of those rows
 element by element.
@@ -21,7 +22,7 @@ from oracle import fill, tree  # noqa: E402
 from oracle.rwg import Mesh  # noqa: E402
 
 
-@pytest.fixture(scope="module", params=[("coated_c2", 5), ("nanoparticle", 4), ("cube_c3", 5)])
+@pytest.fixture(scope="module", params=[("coated_c2", 5), ("nanoparticle", 4), ("cube_c3", 5), ("ellipsoid_c4", 7)])
 def full(request):
     import __graft_entry__ as g
     g.build()

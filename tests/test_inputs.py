@@ -70,3 +70,28 @@ def test_cube_workload():
         w = vs.copy()
         w[:, ax] *= -1
         assert key(w) == ref                               # mirror-symmetric triangulation
+
+
+def test_ellipsoid_workload():
+    """Ellipsoid of the learned-preconditioner workload: semi-axes 4 x 2 x 1
+    lambda0, eps 3 - 0.2j, 355 488 unknowns (edges about lambda0 / 28), every
+    vertex on the ellipsoid, closed, outward, near-isotropic triangles,
+    mirror-symmetric triangulation."""
+    m = geo.workload("ellipsoid_c4")
+    assert _unknowns(m) == 355488
+    v, t = m["verts"], m["tris"]
+    assert np.allclose(np.sum((v / [4.0, 2.0, 1.0]) ** 2, axis=1), 1.0)
+    eps = m["media"][1, 0] + 1j * m["media"][1, 1]
+    assert eps == 3.0 - 0.2j
+    e = np.linalg.norm(v[t[:, [1, 2, 0]]] - v[t], axis=2)
+    assert 0.03 < e.mean() < 0.04 and (e.max(1) / e.min(1)).max() < 2.5
+    vol = np.sum(np.einsum("ij,ij->i", v[t[:, 0]], np.cross(v[t[:, 1]], v[t[:, 2]]))) / 6
+    assert abs(vol / (4 / 3 * np.pi * 8.0) - 1) < 1e-3
+    s = geo.workload("ellipsoid_small")
+    vs, ts = s["verts"], s["tris"]
+    key = lambda V: {tuple(sorted(tuple(np.round(V[i], 9)) for i in tr)) for tr in ts}
+    ref = key(vs)
+    for ax in range(3):
+        w = vs.copy()
+        w[:, ax] *= -1
+        assert key(w) == ref

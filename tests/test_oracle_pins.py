@@ -310,10 +310,13 @@ def test_cube_monostatic_mirror_symmetry():
     assert np.max(np.abs(mono - mono[::-1])) < 0.02
     # broadside incidences see a face, the 45-degree-ish ones an edge: a real spread
     assert np.ptp(mono) > 1.0
-    # the stored oracle values of the finer cube (same body) obey the same symmetry
-    d = np.load(os.path.join(os.path.dirname(__file__), "golden", "cube_small.npz"))
-    ds = 10 * np.log10(d["mono_rcs"])
-    assert np.max(np.abs(ds - ds[::-1])) < 0.02
+    # the stored oracle values of the finer cube (same body) and of the
+    # tri-axial ellipsoid (z -> -z is one of its principal-plane mirrors) obey
+    # the same symmetry
+    for name in ("cube_small", "ellipsoid_small"):
+        d = np.load(os.path.join(os.path.dirname(__file__), "golden", f"{name}.npz"))
+        ds = 10 * np.log10(d["mono_rcs"])
+        assert np.max(np.abs(ds - ds[::-1])) < 0.02, name
 
 
 # ---------------------------------------------------------------- Mie series
