@@ -631,6 +631,10 @@ def main():
         "fp64_ms": sie.sie_stage_timing(s.ctx, 2, 1, sie.SIE_PREC_FP64, 10)}
     sie.sie_set_param(s.ctx, 1, 1)
     sie.sie_device_status(s.ctx)
+    # the far field with the M2L by sibling groups split over warps (the alternative form)
+    sie.sie_set_param(s.ctx, 7, 2)
+    stages["far_mlfmm_m2l_split_groups"] = {"fp32_ms": sie.sie_stage_timing(s.ctx, 1, 1, sie.SIE_PREC_MIXED, 20)}
+    sie.sie_set_param(s.ctx, 7, -1)
     nnzb = sie.sie_query(s.ctx, 1)
     near_bytes_fp32 = nnzb * (4 * 8 + 4) + (ne + 1) * 4 + 2 * (2 * ne * 8)
     near_bytes_fp64 = nnzb * (4 * 16 + 4) + (ne + 1) * 4 + 2 * (2 * ne * 16)

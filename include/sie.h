@@ -345,8 +345,9 @@ sie_status sie_device_status(sie_ctx *ctx);
  *      right-hand sides): 0 (default: 8 in FP32, 4 in FP64), 4, 8 or 16.
  *   5  the same for the block ILU(0) sweeps.
  *   6  right-hand sides per pass of the leaf receive: 0 (default 4), 1, 2, 4.
- *   7  M2L form: -1 (default: sibling groups from 8 right-hand sides on, per
- *      target box below), 0 per target box, 1 sibling groups from 2 on.
+ *   7  M2L form: -1 (default: sibling groups from 8 right-hand sides on,
+ *      per target box below), 0 per target box, 1 sibling groups from 2 on,
+ *      2 sibling groups whose union list is split over the warps of a CTA.
  * Keys 2-7 are tile shapes: results agree to rounding (the tensor-core
  * aggregation to its FP32-level split operands), speed differs.
  * Errors: SIE_EINVAL for an unknown key or a value out of range. */

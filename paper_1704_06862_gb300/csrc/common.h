@@ -269,7 +269,8 @@ struct sie_ctx {
   // tile shapes of the block-RHS kernels (0 or -1: the built-in rule; set by
   // sie_set_param or chosen by sie_autotune): right-hand sides per block load
   // of the near-field product and the ILU sweeps, per pass of the leaf
-  // receive; M2L form (0 per target box, 1 by sibling groups)
+  // receive; M2L form (0 per target box, 1 by sibling groups, 2 by sibling
+  // groups split over warps)
   int tune_near_rb = 0, tune_ilu_rb = 0, tune_rec_rb = 0, tune_m2l = -1;
 };
 

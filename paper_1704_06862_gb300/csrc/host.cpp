@@ -1409,7 +1409,7 @@ extern "C" sie_status sie_autotune(sie_ctx *c, int64_t nrhs, int32_t reps, int64
       c->agg_tc_rb = agg;
     }
     best_of(1, &c->tune_rec_rb, {1, 2, 4});
-    double t_far = best_of(1, &c->tune_m2l, {0, 1});
+    double t_far = best_of(1, &c->tune_m2l, {0, 1, 2});
     choice[0] = c->tune_near_rb;
     choice[1] = c->tune_ilu_rb;
     choice[2] = agg;
@@ -1466,7 +1466,7 @@ extern "C" sie_status sie_set_param(sie_ctx *c, int32_t key, int64_t value) {
         graphs_free(c);
         break;
       case 7:
-        SIE_REQUIRE(value >= -1 && value <= 1, SIE_EINVAL, "sie_set_param: M2L form must be -1, 0 or 1");
+        SIE_REQUIRE(value >= -1 && value <= 2, SIE_EINVAL, "sie_set_param: M2L form must be -1, 0, 1 or 2");
         c->tune_m2l = (int)value;
         graphs_free(c);
         break;

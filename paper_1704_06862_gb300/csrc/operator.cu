@@ -688,6 +688,71 @@ __global__ void __launch_bounds__(128) k_m2l_group(int K, int nrhs, const int *_
   }
 }
 
+// Diagonal M2L by sibling groups, with the group's union list split over the
+// SW warps of the CTA for one slice of 32 directions (lane = direction): warp
+// w takes entries w, w + SW, ...; each keeps partial sums for all (up to 8)
+// members; the warps' partials are then added in warp order (deterministic)
+// and written.  Same loads per source as k_m2l_group (4 pattern values, one
+// translator per member that has the source), with SW times more warps in
+// flight per direction slice, which a single right-hand side needs to fill the GPU.
+template <typename T, int SW>
+__global__ void __launch_bounds__(32 * SW) k_m2l_split(int K, int nrhs, const int *__restrict__ grp_ptr,
+                                                      const int *__restrict__ grp_box, const int *__restrict__ grp_ent,
+                                                      const cx<T> *__restrict__ Tr, const cx<T> *__restrict__ S,
+                                                      cx<T> *__restrict__ I) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T> *part = reinterpret_cast<cx<T> *>(smem_raw);                 // [SW - 1][8][4][32]
+  int *ents = reinterpret_cast<int *>(part + (size_t)(SW - 1) * 8 * 4 * 32);  // [n][10]
+  const int g = blockIdx.y, r = blockIdx.z, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e0 = grp_ptr[g], ne = grp_ptr[g + 1] - e0;
+  for (int i = threadIdx.x; i < ne * 10; i += blockDim.x) ents[i] = grp_ent[(size_t)e0 * 10 + i];
+  __syncthreads();
+  const int k = blockIdx.x * 32 + lane;
+  const bool kin = k < K;
+  const int kk = kin ? k : K - 1;  // out-of-range lanes load a valid direction, write nothing
+  const size_t cs = (size_t)nrhs * K;
+  cx<T> acc[8][4];
+  for (int e = warp; e < ne; e += SW) {
+    const int *E = ents + 10 * e;
+    const int src = E[0], mask = E[1];
+    const cx<T> *sp = S + ((size_t)src * 4 * nrhs + r) * K + kk;
+    const cx<T> s0 = sp[0], s1 = sp[cs], s2 = sp[2 * cs], s3 = sp[3 * cs];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (mask & (1 << u)) {
+        const cx<T> t = Tr[(size_t)E[2 + u] * K + kk];
+        acc[u][0] = cfma(t, s0, acc[u][0]);
+        acc[u][1] = cfma(t, s1, acc[u][1]);
+        acc[u][2] = cfma(t, s2, acc[u][2]);
+        acc[u][3] = cfma(t, s3, acc[u][3]);
+      }
+  }
+  if (warp > 0) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) part[(((size_t)(warp - 1) * 8 + u) * 4 + q) * 32 + lane] = acc[u][q];
+  }
+  __syncthreads();
+  if (warp != 0 || !kin) return;
+#pragma unroll
+  for (int w = 1; w < SW; ++w)
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[u][q] += part[(((size_t)(w - 1) * 8 + u) * 4 + q) * 32 + lane];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int b = grp_box[8 * (size_t)g + u];
+    if (b < 0) continue;
+    cx<T> *o = I + ((size_t)b * 4 * nrhs + r) * K + k;
+    o[0] = acc[u][0];
+    o[cs] = acc[u][1];
+    o[2 * cs] = acc[u][2];
+    o[3 * cs] = acc[u][3];
+  }
+}
+
 // Leaf receive with the JMCFIE weights of medium l (weights and constants
 // folded into the translators).  Per box the combined fields
 //   F1 = I^J - khat x I^M / eta,   F3 = -eta khat x I^J - I^M,
@@ -1504,7 +1569,18 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
     for (int lv = 2; lv <= leaf; ++lv) {
       LevelHost &B = G.lev[lv];
       const bool by_group = B.ngroups > 0 && (c->tune_m2l >= 0 ? (c->tune_m2l == 1 && R >= 2) : R >= 8);
-      if (by_group) {
+      // (split groups measured slower than per target box for one right-hand side: 0.603 vs 0.558 ms far field)
+      const bool by_split = B.ngroups > 0 && !by_group && c->tune_m2l == 2;
+      if (by_split) {
+        // sibling groups split over 4 warps, 32 directions per CTA
+        SIE_REQUIRE(B.ngroups <= 65535 && R <= 65535, SIE_EINVAL, "MLFMM: too many sibling groups for one launch");
+        constexpr int SW = 4;
+        const size_t smem = (size_t)(SW - 1) * 8 * 4 * 32 * sizeof(cx<T>) + (size_t)B.max_group_entries * 10 * sizeof(int);
+        set_smem(k_m2l_split<T, SW>, smem);
+        k_m2l_split<T, SW><<<dim3((B.K + 31) / 32, B.ngroups, R), 32 * SW, smem, st>>>(
+            B.K, R, B.d_grp_ptr, B.d_grp_box, B.d_grp_ent, (const cx<T> *)tsel<T>::Tr(B), (const cx<T> *)B.d_S,
+            (cx<T> *)B.d_I);
+      } else if (by_group) {
         SIE_REQUIRE(B.ngroups <= 65535 && R <= 65535, SIE_EINVAL, "MLFMM: too many sibling groups for one launch");
         dim3 grid((B.K + 127) / 128, B.ngroups, R);
         const size_t smem = (size_t)B.max_group_entries * 10 * sizeof(int);

@@ -76,7 +76,7 @@ def test_tile_shapes_give_the_same_product(solver):
             sie.sie_set_param(s.ctx, 6, rb)
             assert np.array_equal(_prod(s, x, 2), far_ref)
         scale = np.linalg.norm(ref)
-        for m2l in (0, 1):
+        for m2l in (0, 1, 2):
             for agg in (0, 16):
                 _reset(s)
                 sie.sie_set_param(s.ctx, 7, m2l)
@@ -97,7 +97,7 @@ def test_autotune_choices_round_trip(solver, tmp_path):
         t = sie.sie_autotune(s.ctx, R, reps=1, path=path)
         print(f"autotune at {R} right-hand sides: {t}")
         assert t["near_rb"] in (4, 8, 16) and t["ilu_rb"] in (4, 8, 16) and t["receive_rb"] in (1, 2, 4)
-        assert t["aggregation"] in (0, 16, 32, 64) and t["m2l"] in (0, 1)
+        assert t["aggregation"] in (0, 16, 32, 64) and t["m2l"] in (0, 1, 2)
         assert all(v > 0 for v in t["ms"])
         assert json.load(open(path)) == t
         tuned = _prod(s, x)
