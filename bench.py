@@ -42,7 +42,7 @@ NEAR_SPMV_TRAFFIC_BYTES = 508421888 + 521984
 # DRAM bytes (read + write) of one single-RHS FP32 ILU(0) apply (15 k_ilu_sweep<float, 512>
 # launches) on this workload, from one ncu capture of those launches; valid while the kernel
 # is unchanged (None otherwise)
-ILU_APPLY_TRAFFIC_BYTES = 566056448 + 122624
+ILU_APPLY_TRAFFIC_BYTES = 566045184 + 139520
 
 
 def measured_peaks():
@@ -202,7 +202,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the formulation comparison leg")
     ap.add_argument("--no-nano", action="store_true", help="skip the plasmonic nanoparticle leg")
     ap.add_argument("--no-mie-refinement", action="store_true", help="skip the RCS-vs-Mie mesh refinement leg")
-    ap.add_argument("--cube-sweep", type=int, default=0,
+    ap.add_argument("--cube-sweep", type=int, default=256,
                     help="incidences of the cube's monostatic sweep (0: skip the leg)")
     ap.add_argument("--cube-block", type=int, default=64, help="right-hand sides per block of the cube sweep")
     ap.add_argument("--tuning-file", default=None, help="where the cube leg's autotuner writes its choice (JSON)")
