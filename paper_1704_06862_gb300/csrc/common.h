@@ -151,6 +151,11 @@ struct RegionHost {
   double *d_box_centre = nullptr;  // leaf box centres [nleaf][3]
   void *d_V64 = nullptr, *d_V32 = nullptr;    // radiation patterns [nb][2][Kleaf]
   void *d_P64 = nullptr, *d_P32 = nullptr;  // combined receive patterns [nb][2][Kleaf] (k_receive_fold)
+  // the radiation patterns as the pre-split A operand of the tensor-core
+  // aggregation (tensor.cu: per box, chunks in the shared-memory byte layout)
+  void *d_agg_op = nullptr;
+  int64_t *d_agg_off = nullptr;   // [nleaf+1] byte offsets of the boxes
+  size_t agg_op_bytes = 0;
   int *d_pairs = nullptr;       // near triangle pairs (p, q, singular) for the fill
   int64_t npairs = 0;
 };
@@ -314,7 +319,9 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs);
 // block of nrhs (0: the SIMT kernel is used), and the launch for one medium
 int agg_tc_block(const sie_ctx *c, int nrhs);
 bool op_aggregate_tc(sie_ctx *c, int rb, int K, int nbox, int max_leaf, int nrhs, const int *box_start,
-                     const int *basis_p, const int *sign, const zf *V, const zf *x, zf *S, cudaStream_t st);
+                     const int64_t *box_off, const int *basis_p, const int *sign, const unsigned char *Aop,
+                     const zf *x, zf *S, cudaStream_t st);
+void build_agg_operand(sie_ctx *c, RegionHost &R, int K);  // at setup, after the FP32 patterns
 void op_permute_in(sie_ctx *c, const zd *user, zd *internal, int nrhs);    // user -> internal
 void op_permute_out(sie_ctx *c, const zd *internal, zd *user, int nrhs);   // internal -> user
 void op_d2f(sie_ctx *c, const zd *a, zf *b, int64_t n);

@@ -1521,8 +1521,8 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
       // accuracy floor decides convergence: there the FP32 SIMT kernel)
       const int tc_rb = (std::is_same<T, float>::value && std::is_same<TY, float>::value) ? agg_tc_block(c, R) : 0;
       const bool tc = tc_rb > 0 && op_aggregate_tc(c, tc_rb, LL.K, LL.nbox, G.max_leaf, R, G.d_box_start,
-                                                   G.d_basis_p, G.d_basis_sign, (const zf *)tsel<T>::V(G),
-                                                   (const zf *)x, (zf *)LL.d_S, st);
+                                                   G.d_agg_off, G.d_basis_p, G.d_basis_sign,
+                                                   (const unsigned char *)G.d_agg_op, (const zf *)x, (zf *)LL.d_S, st);
       if (!tc) {
         // more than 512 leaf directions: four per thread, one right-hand side per pass
         if (LL.K > 2 * 256) agg(k_aggregate<T, 1, 4>, 1);

@@ -20,8 +20,15 @@
 // the 16-bit operands' error to 2e-4 of the whole product on a test cube.
 //
 // Mapping (one CTA per leaf box, 256 threads):
-//   * B (all k-steps of the box) is staged once per pass of right-hand sides;
-//   * A is staged per 128-row tile of D and chunk of two 16-wide k-steps;
+//   * A does not depend on the right-hand sides: it is split and laid out at
+//     setup (k_agg_operand_build) in HBM in the exact shared-memory byte
+//     layout, per box as chunks of (128-row tile, up to four k-steps, three
+//     parts); the kernel streams the chunks with bulk asynchronous copies
+//     (cp.async.bulk, completion counted in bytes on an mbarrier) into a
+//     two-stage ring, the copy of chunk q + 1 in flight while the MMAs of
+//     chunk q run;
+//   * B (all k-steps of the box) is staged by the threads once per pass of
+//     right-hand sides;
 //   * one thread issues the MMAs (M = 128, N = 2 RB, K = 16, kind::f16 with
 //     BF16 operands, both K-major, no swizzle) into a 128 x N FP32 tile in
 //     tensor memory and commits them to an mbarrier; the waits on it are
@@ -92,6 +99,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, int limi
   return false;
 }
 
+// bulk asynchronous copy global -> shared, completion counted on an mbarrier:
+// the issuing thread first announces the bytes (arrive + expect_tx)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(b))
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {  // one whole warp
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(dst)), "r"(ncols)
                : "memory");
@@ -136,18 +157,52 @@ __device__ __forceinline__ void split_store(unsigned char *base, size_t stride, 
 
 constexpr int TC_THREADS = 256;
 constexpr int TC_M = 128;     // rows of one D tile
-constexpr int TC_KCH = 2;     // k-steps of A staged at a time
+constexpr int TC_KCH = 4;     // k-steps per A chunk
 constexpr int TC_PARTS = 3;   // BF16 parts per operand
-constexpr int TC_A_BYTES = TC_KCH * TC_M * 32;  // one part of an A chunk
+constexpr int TC_KSTEP = TC_M * 32;                    // bytes of one part of one k-step of A (128 x 16 BF16)
+constexpr int TC_STAGE = TC_PARTS * TC_KCH * TC_KSTEP;  // one ring stage: a whole chunk
+
+// Layout of the pre-split A operand of one box (byte offsets from the box's
+// start): chunk (row tile mt, chunk kc) at (mt ks + TC_KCH kc) TC_PARTS TC_KSTEP,
+// holding its kn = min(TC_KCH, ks - TC_KCH kc) k-steps as [part][k-step][128 x 16]
+// in the core-matrix layout of op_off.  ks = max(1, ceil(2 n / 16)).
+__global__ void k_agg_operand_build(int K, const int *__restrict__ box_start, const int64_t *__restrict__ box_off,
+                                    const cx<float> *__restrict__ V, unsigned char *__restrict__ A) {
+  const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
+  const int ks = max(1, (2 * n + 15) >> 4), K2 = 2 * K, mtiles = (2 * K2 + TC_M - 1) / TC_M;
+  unsigned char *base = A + box_off[b];
+  const int per = 64 * 8;  // (row pair, basis) per (tile, k-step)
+  for (int idx = threadIdx.x; idx < mtiles * ks * per; idx += blockDim.x) {
+    const int ts = idx / per, e = idx - ts * per;
+    const int mt = ts / ks, sg = ts - mt * ks;  // row tile, global k-step
+    const int tkl = e >> 3, nbl = e & 7;
+    const int tk = mt * 64 + tkl, nb = sg * 8 + nbl;
+    float vr = 0.f, vi = 0.f;
+    if (tk < K2 && nb < n) {
+      const cx<float> v = V[(size_t)(i0 + nb) * K2 + tk];
+      vr = v.re;
+      vi = v.im;
+    }
+    const int kc = sg / TC_KCH, sl = sg - kc * TC_KCH, kn = min(TC_KCH, ks - kc * TC_KCH);
+    unsigned char *chunk = base + (size_t)(mt * ks + kc * TC_KCH) * TC_PARTS * TC_KSTEP + (size_t)sl * TC_KSTEP;
+    const size_t pstride = (size_t)kn * TC_KSTEP;  // between the parts of the chunk
+    const int c = 2 * nbl;
+    split_store(chunk, pstride, op_off(2 * tkl, c, TC_M), vr);
+    split_store(chunk, pstride, op_off(2 * tkl, c + 1, TC_M), -vi);
+    split_store(chunk, pstride, op_off(2 * tkl + 1, c, TC_M), vi);
+    split_store(chunk, pstride, op_off(2 * tkl + 1, c + 1, TC_M), vr);
+  }
+}
 
 // Leaf aggregation of one medium on the tensor cores, RB right-hand sides per
 // pass (N = 2 RB columns).  ks_max: 16-wide k-steps of the largest box.
 template <int RB>
 __global__ void __launch_bounds__(TC_THREADS) k_aggregate_tc(int K, int ne, int nrhs, int ks_max,
                                                             const int *__restrict__ box_start,
+                                                            const int64_t *__restrict__ box_off,
                                                             const int *__restrict__ basis_p,
                                                             const int *__restrict__ sign,
-                                                            const cx<float> *__restrict__ V,
+                                                            const unsigned char *__restrict__ Aop,
                                                             const cx<float> *__restrict__ x, cx<float> *__restrict__ S,
                                                             int wait_limit, int *err) {
   constexpr int N = 2 * RB;
@@ -156,17 +211,21 @@ __global__ void __launch_bounds__(TC_THREADS) k_aggregate_tc(int K, int ne, int 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const size_t bpart = (size_t)ks_max * N * 32;  // bytes of one part of B
   unsigned char *Bp = smem_raw;                    // [TC_PARTS][ks_max k-steps][N rows][16]
-  unsigned char *Ap = Bp + TC_PARTS * bpart;       // [TC_PARTS][TC_KCH k-steps][128 rows][16]
-  __shared__ __align__(8) uint64_t mbar;
+  unsigned char *ring = Bp + TC_PARTS * bpart;     // [2][TC_STAGE]
+  __shared__ __align__(8) uint64_t full[2], mma_done;
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
   const int ks = max(1, (2 * n + 15) >> 4);  // k-steps of this box (an empty box: one step of zeros, D = 0)
-  const int K2 = 2 * K;              // (theta/phi, direction) pairs
+  const int K2 = 2 * K;                      // (theta/phi, direction) pairs
   const int mtiles = (2 * K2 + TC_M - 1) / TC_M;
+  const int nkc = (ks + TC_KCH - 1) / TC_KCH, nq = mtiles * nkc;  // chunks per pass
+  const unsigned char *abox = Aop + box_off[b];
   if (tid == 0) {
-    mbar_init(&mbar, 1);
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&mma_done, 1);
     s_fail = 0;
   }
   if (warp == 0) tmem_alloc(&s_tmem, NCOLS);
@@ -174,12 +233,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_aggregate_tc(int K, int ne, int 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  unsigned phase = 0;
+  unsigned pf0 = 0, pf1 = 0, pm = 0;  // phases of the two ring stages and of the MMA barrier
+  int issued = 0, consumed = 0;       // chunks copied in and used (thread 0's count is the one that matters)
+  auto issue = [&](int q) {           // thread 0: chunk q into stage q & 1
+    const int mt = q / nkc, kc = q - mt * nkc, kn = min(TC_KCH, ks - kc * TC_KCH);
+    const uint32_t bytes = (uint32_t)(TC_PARTS * kn * TC_KSTEP);
+    uint64_t *bar = &full[q & 1];
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(ring + (size_t)(q & 1) * TC_STAGE, abox + (size_t)(mt * ks + kc * TC_KCH) * TC_PARTS * TC_KSTEP, bytes,
+             bar);
+  };
   for (int r0 = 0; r0 < nrhs && !s_fail; r0 += RB) {
     const int nr = min(RB, nrhs - r0);
     // ---- B: all k-steps of the box, rows j = (jm, r), columns c = (basis, re/im)
     for (int idx = tid; idx < N * ks * 8; idx += TC_THREADS) {
-      // one thread per (row j, pair of columns = one basis)
       const int j = idx % N, cp = idx / N;  // cp: basis slot 0 .. 8 ks - 1
       const int jm = j / RB, r = j - jm * RB;
       float re = 0.f, im = 0.f;
@@ -193,52 +260,59 @@ __global__ void __launch_bounds__(TC_THREADS) k_aggregate_tc(int K, int ne, int 
       split_store(Bp, bpart, op_off(j, 2 * cp, N), re);
       split_store(Bp, bpart, op_off(j, 2 * cp + 1, N), im);
     }
-    for (int mt = 0; mt < mtiles; ++mt) {
-      for (int k0 = 0; k0 < ks; k0 += TC_KCH) {
-        const int kn = min(TC_KCH, ks - k0);
-        // ---- A chunk: rows m = 2 tk + ri of this tile, columns of k-steps k0 .. k0 + kn
-        for (int idx = tid; idx < 64 * kn * 8; idx += TC_THREADS) {
-          const int tkl = idx & 63, nbl = idx >> 6;  // (direction pair, basis) of the chunk
-          const int tk = mt * 64 + tkl, nb = k0 * 8 + nbl;
-          float vr = 0.f, vi = 0.f;
-          if (tk < K2 && nb < n) {
-            const cx<float> v = V[(size_t)(i0 + nb) * K2 + tk];
-            vr = v.re;
-            vi = v.im;
-          }
-          const int c = 2 * nbl;  // column within the chunk
-          split_store(Ap, TC_A_BYTES, op_off(2 * tkl, c, TC_M), vr);
-          split_store(Ap, TC_A_BYTES, op_off(2 * tkl, c + 1, TC_M), -vi);
-          split_store(Ap, TC_A_BYTES, op_off(2 * tkl + 1, c, TC_M), vi);
-          split_store(Ap, TC_A_BYTES, op_off(2 * tkl + 1, c + 1, TC_M), vr);
-        }
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-          tc_fence_after();
-          for (int s = 0; s < kn; ++s) {
-            // the six part products a_i b_j with i + j <= 2, smallest first
-            for (int q = 0; q < 6; ++q) {
-              const int i = q < 3 ? 2 - q : (q < 5 ? 1 - (q - 3) : 0), jj = q < 3 ? q : (q < 5 ? q - 3 : 0);
-              const uint64_t ad = smem_desc(smem_u32(Ap + i * TC_A_BYTES + s * TC_M * 32), 128, 256);
-              const uint64_t bd = smem_desc(smem_u32(Bp + jj * bpart + (size_t)(k0 + s) * N * 32), 128, 256);
-              tc_mma(tmem, ad, bd, IDESC, (k0 + s) > 0 || q > 0 ? 1 : 0);
-            }
-          }
-          tc_commit(&mbar);
-        }
-        // the products have read this chunk (and, at the last chunk, D is complete)
-        const bool ok = mbar_wait(&mbar, phase, wait_limit);
-        phase ^= 1u;
-        if (!ok) {
-          if (lane == 0) atomicOr(err, 1);
-          s_fail = 1;
-        }
-        tc_fence_after();
-        __syncthreads();
-        if (s_fail) break;
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      issue(0);
+      issued = 1;
+      if (nq > 1) {
+        issue(1);
+        issued = 2;
       }
+    }
+    for (int q = 0; q < nq; ++q) {
+      const int st = q & 1, mt = q / nkc, kc = q - mt * nkc, kn = min(TC_KCH, ks - kc * TC_KCH);
+      const bool ok_full = mbar_wait(&full[st], st ? pf1 : pf0, wait_limit);
+      if (ok_full) {  // a stage's phase advances only when its copy has arrived
+        if (st) pf1 ^= 1u;
+        else pf0 ^= 1u;
+      }
+      if (!ok_full) {
+        if (lane == 0) atomicOr(err, 1);
+        s_fail = 1;
+      }
+      __syncthreads();
       if (s_fail) break;
+      consumed = q + 1;
+      if (tid == 0) {
+        tc_fence_after();
+        const unsigned char *stage = ring + (size_t)st * TC_STAGE;
+        for (int s = 0; s < kn; ++s) {
+          // the six part products a_i b_j with i + j <= 2, smallest first
+          for (int p6 = 0; p6 < 6; ++p6) {
+            const int i = p6 < 3 ? 2 - p6 : (p6 < 5 ? 1 - (p6 - 3) : 0), jj = p6 < 3 ? p6 : (p6 < 5 ? p6 - 3 : 0);
+            const uint64_t ad = smem_desc(smem_u32(stage + (size_t)(i * kn + s) * TC_KSTEP), 128, 256);
+            const uint64_t bd = smem_desc(smem_u32(Bp + jj * bpart + (size_t)(kc * TC_KCH + s) * N * 32), 128, 256);
+            tc_mma(tmem, ad, bd, IDESC, (kc > 0 || s > 0 || p6 > 0) ? 1 : 0);
+          }
+        }
+        tc_commit(&mma_done);
+      }
+      const bool ok_mma = mbar_wait(&mma_done, pm, wait_limit);
+      pm ^= 1u;
+      if (!ok_mma) {
+        if (lane == 0) atomicOr(err, 1);
+        s_fail = 1;
+      }
+      tc_fence_after();
+      // the stage is free: the next-but-one chunk goes into it
+      if (tid == 0 && ok_mma && q + 2 < nq) {
+        issue(q + 2);
+        issued = q + 3;
+      }
+      __syncthreads();
+      if (s_fail) break;
+      if (kc < nkc - 1) continue;
       // ---- D tile -> S: warp w reads lanes 32 (w % 4) .. + 31, columns (w / 4) N/2 .. + N/2
       {
         const int m = 32 * (warp & 3) + lane, gm = mt * TC_M + m;
@@ -254,15 +328,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_aggregate_tc(int K, int ne, int 
             float w[32];
             tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16), w);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = w[jc0 + q];
+            for (int qq = 0; qq < 16; ++qq) v[qq] = w[jc0 + qq];
           }
           if (tk < K2) {
             const int cmax = min(32, N / 2 - c0);
-            for (int q = 0; q < cmax; ++q) {
-              const int j = jc0 + c0 + q, jm = j / RB, r = j - jm * RB;
+            for (int qq = 0; qq < cmax; ++qq) {
+              const int j = jc0 + c0 + qq, jm = j / RB, r = j - jm * RB;
               if (r < nr) {
                 float *o = reinterpret_cast<float *>(S + ((size_t)b * 4 * nrhs + (size_t)(jm * 2 + t) * nrhs + r0 + r) * K + k);
-                o[ri] = v[q];
+                o[ri] = v[qq];
               }
             }
           }
@@ -273,9 +347,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_aggregate_tc(int K, int ne, int 
       tc_fence_after();
     }
   }
-  // after a wait gave up the products may still be in flight: wait for them
-  // (bounded again) before the tensor memory is freed
-  if (s_fail) mbar_wait(&mbar, phase ^ 1u, wait_limit);
+  // after a wait gave up, copies and products may still be in flight: wait for
+  // them (bounded again) before the shared and tensor memory are released
+  if (s_fail && tid == 0) {
+    // at most two chunks are outstanding, one per stage, each waited on its stage's pending phase
+    for (int q = consumed; q < issued; ++q) mbar_wait(&full[q & 1], (q & 1) ? pf1 : pf0, wait_limit);
+    mbar_wait(&mma_done, pm ^ 1u, wait_limit);
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, NCOLS);
@@ -284,12 +362,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_aggregate_tc(int K, int ne, int 
 template <int RB>
 size_t agg_tc_smem(int max_leaf) {
   const int ks_max = std::max(1, (2 * max_leaf + 15) / 16);
-  return (size_t)TC_PARTS * ks_max * (2 * RB) * 32 + TC_PARTS * (size_t)TC_A_BYTES;
+  return (size_t)TC_PARTS * ks_max * (2 * RB) * 32 + 2 * (size_t)TC_STAGE;
 }
 
 template <int RB>
-void launch_agg_tc(sie_ctx *c, int K, int nbox, int max_leaf, int nrhs, const int *box_start, const int *basis_p,
-                   const int *sign, const zf *V, const zf *x, zf *S, cudaStream_t st) {
+void launch_agg_tc(sie_ctx *c, int K, int nbox, int max_leaf, int nrhs, const int *box_start, const int64_t *box_off,
+                   const int *basis_p, const int *sign, const unsigned char *Aop, const zf *x, zf *S, cudaStream_t st) {
   const int ks_max = std::max(1, (2 * max_leaf + 15) / 16);
   const size_t smem = agg_tc_smem<RB>(max_leaf);
   static bool raised[64] = {};
@@ -299,8 +377,8 @@ void launch_agg_tc(sie_ctx *c, int K, int nbox, int max_leaf, int nrhs, const in
     SIE_CUDA(cudaFuncSetAttribute(k_aggregate_tc<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     raised[dev] = true;
   }
-  k_aggregate_tc<RB><<<nbox, TC_THREADS, smem, st>>>(K, c->ne, nrhs, ks_max, box_start, basis_p, sign, V, x, S,
-                                                     c->wait_limit, c->d_err);
+  k_aggregate_tc<RB><<<nbox, TC_THREADS, smem, st>>>(K, c->ne, nrhs, ks_max, box_start, box_off, basis_p, sign, Aop,
+                                                     x, S, c->wait_limit, c->d_err);
   SIE_CHECK_LAUNCH();
   c->launches++;
 }
@@ -314,8 +392,30 @@ int agg_tc_block(const sie_ctx *c, int nrhs) {
   return nrhs >= 64 ? 64 : nrhs >= 32 ? 32 : 16;
 }
 
+// pre-split A operand of the tensor-core aggregation for one medium (setup)
+void build_agg_operand(sie_ctx *c, RegionHost &R, int K) {
+  const int nbox = (int)R.box_start.size() - 1;
+  if (nbox <= 0) return;
+  const int K2 = 2 * K, mtiles = (2 * K2 + TC_M - 1) / TC_M;
+  std::vector<int64_t> off(nbox + 1, 0);
+  for (int b = 0; b < nbox; ++b) {
+    const int n = R.box_start[b + 1] - R.box_start[b];
+    const int ks = std::max(1, (2 * n + 15) / 16);
+    off[b + 1] = off[b] + (int64_t)mtiles * ks * TC_PARTS * TC_KSTEP;
+  }
+  R.agg_op_bytes = (size_t)off[nbox];
+  R.d_agg_off = dev_upload(c, off);
+  R.d_agg_op = dev_alloc(c, R.agg_op_bytes);
+  k_agg_operand_build<<<nbox, 256, 0, c->stream>>>(K, R.d_box_start, R.d_agg_off, (const zf *)R.d_V32,
+                                                  (unsigned char *)R.d_agg_op);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+
 bool op_aggregate_tc(sie_ctx *c, int rb, int K, int nbox, int max_leaf, int nrhs, const int *box_start,
-                     const int *basis_p, const int *sign, const zf *V, const zf *x, zf *S, cudaStream_t st) {
+                     const int64_t *box_off, const int *basis_p, const int *sign, const unsigned char *Aop,
+                     const zf *x, zf *S, cudaStream_t st) {
+  if (!Aop) return false;
   // fewer right-hand sides per pass while the largest box's operands do not fit in shared memory
   auto fits = [&](int r) {
     return (r == 64 ? agg_tc_smem<64>(max_leaf) : r == 32 ? agg_tc_smem<32>(max_leaf) : agg_tc_smem<16>(max_leaf)) <=
@@ -324,9 +424,9 @@ bool op_aggregate_tc(sie_ctx *c, int rb, int K, int nbox, int max_leaf, int nrhs
   while (rb > 16 && !fits(rb)) rb /= 2;
   if (!fits(rb)) return false;
   switch (rb) {
-    case 16: launch_agg_tc<16>(c, K, nbox, max_leaf, nrhs, box_start, basis_p, sign, V, x, S, st); return true;
-    case 32: launch_agg_tc<32>(c, K, nbox, max_leaf, nrhs, box_start, basis_p, sign, V, x, S, st); return true;
-    case 64: launch_agg_tc<64>(c, K, nbox, max_leaf, nrhs, box_start, basis_p, sign, V, x, S, st); return true;
+    case 16: launch_agg_tc<16>(c, K, nbox, max_leaf, nrhs, box_start, box_off, basis_p, sign, Aop, x, S, st); return true;
+    case 32: launch_agg_tc<32>(c, K, nbox, max_leaf, nrhs, box_start, box_off, basis_p, sign, Aop, x, S, st); return true;
+    case 64: launch_agg_tc<64>(c, K, nbox, max_leaf, nrhs, box_start, box_off, basis_p, sign, Aop, x, S, st); return true;
     default: return false;
   }
 }
