@@ -348,19 +348,25 @@ sie_status sie_device_status(sie_ctx *ctx);
  *   7  M2L form: -1 (default: sibling groups from 8 right-hand sides on,
  *      per target box below), 0 per target box, 1 sibling groups from 2 on,
  *      2 sibling groups whose union list is split over the warps of a CTA.
- * Keys 2-7 are tile shapes: results agree to rounding (the tensor-core
- * aggregation to its FP32-level split operands), speed differs.
+ *   8  tensor-core leaf receive (FP32 operator of the Krylov steps, blocks
+ *      of right-hand sides): right-hand sides per pass, 0 (default: the
+ *      SIMT receive), 16, 32 or 64.
+ * Keys 2-8 are tile shapes: results agree to rounding (the tensor-core
+ * aggregation and receive to their FP32-level split operands), speed
+ * differs.
  * Errors: SIE_EINVAL for an unknown key or a value out of range. */
 sie_status sie_set_param(sie_ctx *ctx, int32_t key, int64_t value);
 
 /* Autotuner of the tile shapes for blocks of nrhs right-hand sides (FP32
  * kernels of the mixed form): coordinate descent over the parameters of
  * sie_set_param keys 4 (near field), 5 (ILU sweeps), 2-3 (aggregation:
- * SIMT or tensor cores and their pass size), 6 (receive), 7 (M2L form), each
+ * SIMT or tensor cores and their pass size), 6 (receive), 8 (receive on the
+ * tensor cores, from 16 right-hand sides on), 7 (M2L form), each
  * candidate timed with CUDA events on the context's stream over `reps`
  * launches of its stage after a warm-up launch; the fastest is kept in the
- * context.  choice_out [5] receives (near RB, ILU RB, aggregation: 0 SIMT or
- * the tensor-core pass size, receive RB, M2L form); ms_out [3] (or NULL) the
+ * context.  choice_out [6] receives (near RB, ILU RB, aggregation: 0 SIMT or
+ * the tensor-core pass size, receive RB, M2L form, tensor-core receive pass
+ * size or 0); ms_out [3] (or NULL) the
  * best near-field, ILU and far-field milliseconds.  nrhs in [2, 4096].
  * Allocates work buffers for nrhs right-hand sides.  Synchronous.  Not a
  * numerical operation of the method; the paper has no counterpart. */

@@ -332,20 +332,20 @@ def sie_set_param(ctx, key, value):
     _check(ctx, load_library().sie_set_param(ctx, int(key), int(value)))
 
 
-TUNING_KEYS = {"near_rb": 4, "ilu_rb": 5, "aggregation": 3, "receive_rb": 6, "m2l": 7}
+TUNING_KEYS = {"near_rb": 4, "ilu_rb": 5, "aggregation": 3, "receive_rb": 6, "m2l": 7, "receive_tc": 8}
 
 
 def sie_autotune(ctx, nrhs, reps=3, path=None):
     """Autotune the block-RHS tile shapes for nrhs right-hand sides (kept in
     the context).  Returns {"nrhs", "near_rb", "ilu_rb", "aggregation",
-    "receive_rb", "m2l", "ms": [near, ilu, far]}; with a path, also writes it
+    "receive_rb", "m2l", "receive_tc", "ms": [near, ilu, far]}; with a path, also writes it
     there as JSON (read back with apply_tuning)."""
     import json
-    ch = np.zeros(5, np.int64)
+    ch = np.zeros(6, np.int64)
     ms = np.zeros(3, np.float64)
     _check(ctx, load_library().sie_autotune(ctx, int(nrhs), int(reps), _ptr(ch), _ptr(ms)))
     out = {"nrhs": int(nrhs), "near_rb": int(ch[0]), "ilu_rb": int(ch[1]), "aggregation": int(ch[2]),
-           "receive_rb": int(ch[3]), "m2l": int(ch[4]), "ms": [float(v) for v in ms]}
+           "receive_rb": int(ch[3]), "m2l": int(ch[4]), "receive_tc": int(ch[5]), "ms": [float(v) for v in ms]}
     if path:
         with open(path, "w") as f:
             json.dump(out, f, indent=1)
@@ -360,7 +360,7 @@ def apply_tuning(ctx, tuning):
             tuning = json.load(f)
     sie_set_param(ctx, 2, 2 if tuning["aggregation"] else 0)
     for name, key in TUNING_KEYS.items():
-        sie_set_param(ctx, key, tuning[name])
+        sie_set_param(ctx, key, tuning.get(name, 0))
 
 
 def sie_query(ctx, key):

@@ -156,6 +156,10 @@ struct RegionHost {
   void *d_agg_op = nullptr;
   int64_t *d_agg_off = nullptr;   // [nleaf+1] byte offsets of the boxes
   size_t agg_op_bytes = 0;
+  // the combined receive patterns as the pre-split A operand of the tensor-core receive
+  void *d_rec_op = nullptr;
+  int64_t *d_rec_off = nullptr;
+  size_t rec_op_bytes = 0;
   int *d_pairs = nullptr;       // near triangle pairs (p, q, singular) for the fill
   int64_t npairs = 0;
 };
@@ -277,6 +281,8 @@ struct sie_ctx {
   // receive; M2L form (0 per target box, 1 by sibling groups, 2 by sibling
   // groups split over warps)
   int tune_near_rb = 0, tune_ilu_rb = 0, tune_rec_rb = 0, tune_m2l = -1;
+  // tensor-core leaf receive: right-hand sides per pass (0: the SIMT receive)
+  int rec_tc_rb = 0;
 };
 
 // ------------------------------------------------------------------ host helpers (host.cpp)
@@ -322,6 +328,11 @@ bool op_aggregate_tc(sie_ctx *c, int rb, int K, int nbox, int max_leaf, int nrhs
                      const int64_t *box_off, const int *basis_p, const int *sign, const unsigned char *Aop,
                      const zf *x, zf *S, cudaStream_t st);
 void build_agg_operand(sie_ctx *c, RegionHost &R, int K);  // at setup, after the FP32 patterns
+// tensor-core leaf receive (tensor.cu): adds the medium's far field into the FP32 product y
+bool op_receive_tc(sie_ctx *c, int rb, int K, int nbox, int nrhs, const int *box_start, const int64_t *box_off,
+                   const int *basis_p, const unsigned char *Aop, const zf *I, zf eta, zf ieta, zf cJ, zf cM, zf *y,
+                   cudaStream_t st);
+void build_rec_operand(sie_ctx *c, RegionHost &R, int K);  // at setup, after the FP32 receive patterns
 void op_permute_in(sie_ctx *c, const zd *user, zd *internal, int nrhs);    // user -> internal
 void op_permute_out(sie_ctx *c, const zd *internal, zd *user, int nrhs);   // internal -> user
 void op_d2f(sie_ctx *c, const zd *a, zf *b, int64_t n);

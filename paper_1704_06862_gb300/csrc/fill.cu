@@ -690,6 +690,7 @@ void launch_patterns(sie_ctx *c, int l) {
   launch_to_f32(c, (const double *)R.d_V64, (float *)R.d_V32, (int64_t)n * 2);
   launch_to_f32(c, (const double *)R.d_P64, (float *)R.d_P32, (int64_t)n * 2);
   build_agg_operand(c, R, K);
+  build_rec_operand(c, R, K);
 }
 
 void launch_rhs(sie_ctx *c, const double *inc_dev, int nrhs, zd *b) {

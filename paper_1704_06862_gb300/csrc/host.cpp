@@ -1409,12 +1409,14 @@ extern "C" sie_status sie_autotune(sie_ctx *c, int64_t nrhs, int32_t reps, int64
       c->agg_tc_rb = agg;
     }
     best_of(1, &c->tune_rec_rb, {1, 2, 4});
+    if (R >= 16) best_of(1, &c->rec_tc_rb, {0, 16, 32, 64});
     double t_far = best_of(1, &c->tune_m2l, {0, 1, 2});
     choice[0] = c->tune_near_rb;
     choice[1] = c->tune_ilu_rb;
     choice[2] = agg;
     choice[3] = c->tune_rec_rb;
     choice[4] = c->tune_m2l;
+    choice[5] = c->rec_tc_rb;
     if (ms) {
       ms[0] = t_near;
       ms[1] = t_ilu;
@@ -1468,6 +1470,12 @@ extern "C" sie_status sie_set_param(sie_ctx *c, int32_t key, int64_t value) {
       case 7:
         SIE_REQUIRE(value >= -1 && value <= 2, SIE_EINVAL, "sie_set_param: M2L form must be -1, 0, 1 or 2");
         c->tune_m2l = (int)value;
+        graphs_free(c);
+        break;
+      case 8:
+        SIE_REQUIRE(value == 0 || value == 16 || value == 32 || value == 64, SIE_EINVAL,
+                    "sie_set_param: tensor-core receive block must be 0, 16, 32 or 64");
+        c->rec_tc_rb = (int)value;
         graphs_free(c);
         break;
       default:

@@ -1645,6 +1645,16 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
                                                 cx<T>((T)ie.real(), (T)ie.imag()), y, cx<T>((T)cj.real(), (T)cj.imag()),
                                                 cx<T>((T)cm.real(), (T)cm.imag()));
       };
+      // blocks of right-hand sides in the FP32 Krylov operator: split-BF16 products
+      // on the tensor cores when chosen (sie_set_param key 8 or the autotuner)
+      const bool rec_tc = std::is_same<T, float>::value && std::is_same<TY, float>::value && R >= 2 &&
+                          c->rec_tc_rb > 0 &&
+                          op_receive_tc(c, c->rec_tc_rb, LL.K, LL.nbox, R, G.d_box_start, G.d_rec_off, G.d_basis_p,
+                                        (const unsigned char *)G.d_rec_op, (const zf *)LL.d_I,
+                                        zf((float)G.eta.real(), (float)G.eta.imag()),
+                                        zf((float)ie.real(), (float)ie.imag()), zf((float)cj.real(), (float)cj.imag()),
+                                        zf((float)cm.real(), (float)cm.imag()), (zf *)y, c->stream);
+      if (rec_tc) continue;
       // blocks of right-hand sides RB at a time (tuned, else 4) while the box's fields fit in shared memory
       auto fits = [&](int rb) { return STAGES * cb * per_basis + (size_t)rb * 4 * LL.K * sizeof(cx<T>) <= 227 * 1024; };
       int rb = R == 1 ? 1 : (c->tune_rec_rb ? c->tune_rec_rb : 4);

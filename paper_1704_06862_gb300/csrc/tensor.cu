@@ -42,6 +42,9 @@
 // byte offset) and row groups 256 bytes apart (stride byte offset).
 #include <cuda_bf16.h>
 
+#include <map>
+#include <mutex>
+
 #include "common.h"
 
 namespace {
@@ -383,6 +386,229 @@ void launch_agg_tc(sie_ctx *c, int K, int nbox, int max_leaf, int nrhs, const in
   c->launches++;
 }
 
+// ---------------------------------------------------------------- leaf receive
+// For one box with n bases, a pass of RB right-hand sides and the box's
+// incoming patterns I (J/M, theta/phi), the receive of the JMCFIE rows
+//   y_J[p(n)] += cJ sum_(t,k) P[n][t][k] F1[t][k],  y_M[p(n)] -= cM sum_(t,k) P[n][t][k] F3[t][k]
+// with the combined fields F1 = I^J - khat x I^M / eta, F3 = -eta khat x I^J - I^M
+// (khat x (a_t, a_p) = (-a_p, a_t)) is the real product D = A B with
+//   rows    m = 2 n + ri                  (the box's bases, re/im; 128-row tiles of 64 bases)
+//   columns j = out RB + r                (out 0: J row, F1; out 1: M row, F3)
+//   inner   c = 2 (t K + k) + ci          (4K: theta/phi, direction, re/im of F)
+//   A[m][c] = the 2 x 2 real form of P[n][t][k] (as in the aggregation)
+//   B[c][j] = Re F_out[t][k][r] (ci = 0) or Im F_out[t][k][r] (ci = 1).
+// A (the receive patterns) is split at setup into the same chunked
+// shared-memory layout as the aggregation operand and streamed by bulk
+// copies; B is formed by the threads from I chunk by chunk (four k-steps =
+// 32 (t, k) pairs), into a second buffer while the previous chunk's MMAs run.
+__global__ void k_rec_operand_build(int K, const int *__restrict__ box_start, const int64_t *__restrict__ box_off,
+                                    const cx<float> *__restrict__ P, unsigned char *__restrict__ A) {
+  const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
+  const int K2 = 2 * K, ks = (2 * K2 + 15) >> 4, mtiles = max(1, (n + 63) >> 6);
+  unsigned char *base = A + box_off[b];
+  const int per = 64 * 8;  // (basis, direction pair) per (tile, k-step)
+  for (int idx = threadIdx.x; idx < mtiles * ks * per; idx += blockDim.x) {
+    const int ts = idx / per, e = idx - ts * per;
+    const int mt = ts / ks, sg = ts - mt * ks;
+    const int nl = e >> 3, tkl = e & 7;  // local basis (row pair), (t, k) pair within the k-step
+    const int nb = mt * 64 + nl, tk = sg * 8 + tkl;
+    float vr = 0.f, vi = 0.f;
+    if (nb < n && tk < K2) {
+      const cx<float> v = P[(size_t)(i0 + nb) * K2 + tk];
+      vr = v.re;
+      vi = v.im;
+    }
+    const int kc = sg / TC_KCH, sl = sg - kc * TC_KCH, kn = min(TC_KCH, ks - kc * TC_KCH);
+    unsigned char *chunk = base + (size_t)(mt * ks + kc * TC_KCH) * TC_PARTS * TC_KSTEP + (size_t)sl * TC_KSTEP;
+    const size_t pstride = (size_t)kn * TC_KSTEP;
+    const int c = 2 * tkl;
+    split_store(chunk, pstride, op_off(2 * nl, c, TC_M), vr);
+    split_store(chunk, pstride, op_off(2 * nl, c + 1, TC_M), -vi);
+    split_store(chunk, pstride, op_off(2 * nl + 1, c, TC_M), vi);
+    split_store(chunk, pstride, op_off(2 * nl + 1, c + 1, TC_M), vr);
+  }
+}
+
+// B of one chunk (k-steps kc TC_KCH .. + kn) of the receive: rows j = (out, r),
+// columns c = 2 (t, k) + ci, three parts of (TC_KCH x N x 16) BF16 each
+template <int RB>
+__device__ __forceinline__ void rec_stage_b(unsigned char *Bc, int kc, int kn, int K, int nrhs, int r0, int nr,
+                                            const cx<float> *__restrict__ Ib, cx<float> eta, cx<float> ieta) {
+  constexpr int N = 2 * RB;
+  const size_t bpart = (size_t)TC_KCH * N * 32;
+  const int K2 = 2 * K;
+  const size_t cs = (size_t)nrhs * K;
+  for (int idx = threadIdx.x; idx < 8 * kn * RB; idx += TC_THREADS) {
+    const int tkl = idx % (8 * kn), r = idx / (8 * kn);  // consecutive threads: consecutive directions
+    const int tk = kc * TC_KCH * 8 + tkl;
+    cx<float> f1, f3;
+    if (tk < K2 && r < nr) {
+      const int t = tk >= K ? 1 : 0, k = tk - t * K;
+      const cx<float> *ib = Ib + (size_t)(r0 + r) * K + k;
+      const cx<float> iJt = ib[0], iJp = ib[cs], iMt = ib[2 * cs], iMp = ib[3 * cs];
+      f1 = t ? iJp - iMt * ieta : iJt + iMp * ieta;
+      f3 = t ? -(eta * iJt) - iMp : eta * iJp - iMt;
+    }
+    const int c = 2 * tkl;
+    split_store(Bc, bpart, op_off(r, c, N), f1.re);
+    split_store(Bc, bpart, op_off(r, c + 1, N), f1.im);
+    split_store(Bc, bpart, op_off(RB + r, c, N), f3.re);
+    split_store(Bc, bpart, op_off(RB + r, c + 1, N), f3.im);
+  }
+}
+
+// Leaf receive of one medium on the tensor cores, RB right-hand sides per pass;
+// adds into y (FP32 product of the Krylov operator).  One CTA per leaf box.
+template <int RB>
+__global__ void __launch_bounds__(TC_THREADS) k_receive_tc(int K, int ne, int nrhs, const int *__restrict__ box_start,
+                                                          const int64_t *__restrict__ box_off,
+                                                          const int *__restrict__ basis_p,
+                                                          const unsigned char *__restrict__ Aop,
+                                                          const cx<float> *__restrict__ I, cx<float> eta,
+                                                          cx<float> ieta, cx<float> cJ, cx<float> cM,
+                                                          cx<float> *__restrict__ y, int wait_limit, int *err) {
+  constexpr int N = 2 * RB;
+  constexpr int NCOLS = N < 32 ? 32 : N;
+  constexpr uint32_t IDESC = idesc_bf16_f32(TC_M, N);
+  constexpr size_t BCH = (size_t)TC_PARTS * TC_KCH * N * 32;  // one B chunk buffer
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *ring = smem_raw;                 // [2][TC_STAGE]: A chunks
+  unsigned char *Bbuf = ring + 2 * (size_t)TC_STAGE;  // [2][BCH]: B chunks
+  __shared__ __align__(8) uint64_t full[2], mma_done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
+  const int K2 = 2 * K, ks = (2 * K2 + 15) >> 4, nkc = (ks + TC_KCH - 1) / TC_KCH;
+  const int mtiles = max(1, (n + 63) >> 6), nq = mtiles * nkc;
+  const unsigned char *abox = Aop + box_off[b];
+  const cx<float> *Ib = I + (size_t)b * 4 * nrhs * K;
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&mma_done, 1);
+    s_fail = 0;
+  }
+  if (warp == 0) tmem_alloc(&s_tmem, NCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  unsigned pf0 = 0, pf1 = 0, pm = 0;
+  int issued = 0, consumed = 0;
+  auto issue = [&](int q) {  // thread 0: A chunk q into stage q & 1
+    const int mt = q / nkc, kc = q - mt * nkc, kn = min(TC_KCH, ks - kc * TC_KCH);
+    const uint32_t bytes = (uint32_t)(TC_PARTS * kn * TC_KSTEP);
+    uint64_t *bar = &full[q & 1];
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(ring + (size_t)(q & 1) * TC_STAGE, abox + (size_t)(mt * ks + kc * TC_KCH) * TC_PARTS * TC_KSTEP, bytes,
+             bar);
+  };
+  for (int r0 = 0; r0 < nrhs && !s_fail; r0 += RB) {
+    const int nr = min(RB, nrhs - r0);
+    if (tid == 0) {
+      issue(0);
+      issued = 1;
+      if (nq > 1) {
+        issue(1);
+        issued = 2;
+      }
+    }
+    rec_stage_b<RB>(Bbuf, 0, min(TC_KCH, ks), K, nrhs, r0, nr, Ib, eta, ieta);
+    for (int q = 0; q < nq; ++q) {
+      const int st = q & 1, mt = q / nkc, kc = q - mt * nkc, kn = min(TC_KCH, ks - kc * TC_KCH);
+      fence_async_smem();  // this chunk's B (written by the threads) visible to the tensor cores
+      const bool ok_full = mbar_wait(&full[st], st ? pf1 : pf0, wait_limit);
+      if (ok_full) {
+        if (st) pf1 ^= 1u;
+        else pf0 ^= 1u;
+      } else {
+        if (lane == 0) atomicOr(err, 1);
+        s_fail = 1;
+      }
+      __syncthreads();
+      if (s_fail) break;
+      consumed = q + 1;
+      if (tid == 0) {
+        tc_fence_after();
+        const unsigned char *stage = ring + (size_t)st * TC_STAGE;
+        const unsigned char *Bc = Bbuf + (size_t)st * BCH;
+        for (int s = 0; s < kn; ++s)
+          for (int p6 = 0; p6 < 6; ++p6) {
+            const int i = p6 < 3 ? 2 - p6 : (p6 < 5 ? 1 - (p6 - 3) : 0), jj = p6 < 3 ? p6 : (p6 < 5 ? p6 - 3 : 0);
+            const uint64_t ad = smem_desc(smem_u32(stage + (size_t)(i * kn + s) * TC_KSTEP), 128, 256);
+            const uint64_t bd = smem_desc(smem_u32(Bc + (size_t)jj * TC_KCH * N * 32 + (size_t)s * N * 32), 128, 256);
+            tc_mma(tmem, ad, bd, IDESC, (kc > 0 || s > 0 || p6 > 0) ? 1 : 0);
+          }
+        tc_commit(&mma_done);
+      }
+      // meanwhile the threads form the next chunk's B in the other buffer
+      if (q + 1 < nq) {
+        const int kc1 = (q + 1) % nkc;
+        rec_stage_b<RB>(Bbuf + (size_t)((q + 1) & 1) * BCH, kc1, min(TC_KCH, ks - kc1 * TC_KCH), K, nrhs, r0, nr, Ib,
+                        eta, ieta);
+      }
+      const bool ok_mma = mbar_wait(&mma_done, pm, wait_limit);
+      pm ^= 1u;
+      if (!ok_mma) {
+        if (lane == 0) atomicOr(err, 1);
+        s_fail = 1;
+      }
+      tc_fence_after();
+      if (tid == 0 && ok_mma && q + 2 < nq) {
+        issue(q + 2);
+        issued = q + 3;
+      }
+      __syncthreads();
+      if (s_fail) break;
+      if (kc < nkc - 1) continue;
+      // ---- D tile -> y: row m = 2 n + ri, the partner lane holds the other part
+      {
+        const int m = 32 * (warp & 3) + lane, nl = mt * 64 + (m >> 1), ri = m & 1;
+        const int jc0 = (warp >> 2) * (N / 2);
+        const int p = nl < n ? basis_p[i0 + nl] : 0;
+        for (int c0 = 0; c0 < N / 2; c0 += 32) {
+          float v[32];
+          if (N / 2 >= 32) {
+            tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(jc0 + c0), v);
+          } else {
+            float w[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16), w);
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq) v[qq] = w[jc0 + qq];
+          }
+          const int cmax = min(32, N / 2 - c0);
+          for (int qq = 0; qq < cmax; ++qq) {
+            const float mine = v[qq], other = __shfl_xor_sync(0xffffffffu, mine, 1);
+            const int j = jc0 + c0 + qq, out = j / RB, r = j - out * RB;
+            if (ri == 0 && nl < n && r < nr) {
+              const cx<float> sres(mine, other);
+              cx<float> *o = y + ((size_t)(r0 + r) * ne + p) * 2 + out;
+              if (out == 0) *o += cJ * sres;
+              else *o -= cM * sres;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+    }
+  }
+  if (s_fail && tid == 0) {
+    for (int q = consumed; q < issued; ++q) mbar_wait(&full[q & 1], (q & 1) ? pf1 : pf0, wait_limit);
+    mbar_wait(&mma_done, pm ^ 1u, wait_limit);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
+template <int RB>
+constexpr size_t rec_tc_smem() {
+  return 2 * (size_t)TC_STAGE + 2 * (size_t)TC_PARTS * TC_KCH * (2 * RB) * 32;
+}
+
 }  // namespace
 
 // block size of the tensor-core aggregation for nrhs right-hand sides (0: not used)
@@ -427,6 +653,56 @@ bool op_aggregate_tc(sie_ctx *c, int rb, int K, int nbox, int max_leaf, int nrhs
     case 16: launch_agg_tc<16>(c, K, nbox, max_leaf, nrhs, box_start, box_off, basis_p, sign, Aop, x, S, st); return true;
     case 32: launch_agg_tc<32>(c, K, nbox, max_leaf, nrhs, box_start, box_off, basis_p, sign, Aop, x, S, st); return true;
     case 64: launch_agg_tc<64>(c, K, nbox, max_leaf, nrhs, box_start, box_off, basis_p, sign, Aop, x, S, st); return true;
+    default: return false;
+  }
+}
+
+// pre-split A operand of the tensor-core receive for one medium (setup)
+void build_rec_operand(sie_ctx *c, RegionHost &R, int K) {
+  const int nbox = (int)R.box_start.size() - 1;
+  if (nbox <= 0) return;
+  const int ks = (4 * K + 15) / 16;
+  std::vector<int64_t> off(nbox + 1, 0);
+  for (int b = 0; b < nbox; ++b) {
+    const int n = R.box_start[b + 1] - R.box_start[b];
+    const int mtiles = std::max(1, (n + 63) / 64);
+    off[b + 1] = off[b] + (int64_t)mtiles * ks * TC_PARTS * TC_KSTEP;
+  }
+  R.rec_op_bytes = (size_t)off[nbox];
+  R.d_rec_off = dev_upload(c, off);
+  R.d_rec_op = dev_alloc(c, R.rec_op_bytes);
+  k_rec_operand_build<<<nbox, 256, 0, c->stream>>>(K, R.d_box_start, R.d_rec_off, (const zf *)R.d_P32,
+                                                  (unsigned char *)R.d_rec_op);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+
+bool op_receive_tc(sie_ctx *c, int rb, int K, int nbox, int nrhs, const int *box_start, const int64_t *box_off,
+                   const int *basis_p, const unsigned char *Aop, const zf *I, zf eta, zf ieta, zf cJ, zf cM, zf *y,
+                   cudaStream_t st) {
+  if (!Aop) return false;
+  auto go = [&](auto kern, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, bool> raised;
+    int dev = 0;
+    SIE_CUDA(cudaGetDevice(&dev));
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      bool &r = raised[{dev, reinterpret_cast<const void *>(kern)}];
+      if (!r) {
+        SIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        r = true;
+      }
+    }
+    kern<<<nbox, TC_THREADS, smem, st>>>(K, c->ne, nrhs, box_start, box_off, basis_p, Aop, I, eta, ieta, cJ, cM, y,
+                                         c->wait_limit, c->d_err);
+    SIE_CHECK_LAUNCH();
+    c->launches++;
+  };
+  switch (rb) {
+    case 16: go(k_receive_tc<16>, rec_tc_smem<16>()); return true;
+    case 32: go(k_receive_tc<32>, rec_tc_smem<32>()); return true;
+    case 64: go(k_receive_tc<64>, rec_tc_smem<64>()); return true;
     default: return false;
   }
 }

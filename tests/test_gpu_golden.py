@@ -261,6 +261,53 @@ def test_tensor_core_aggregation(case):
         sie.sie_set_param(s.ctx, 3, 0)
 
 
+def test_tensor_core_receive(case):
+    """Leaf receive as split-BF16 tensor-core products (tcgen05; the receive
+    patterns bulk-copied, the box's combined fields formed per chunk by the
+    threads) for blocks of right-hand sides, against the SIMT receive on the
+    same block: the far parts within 1e-5 of the whole product for passes of
+    16, 32 and 64 right-hand sides and a ragged block (40); with both leaf
+    contractions on the tensor cores the whole product of the first two
+    columns within 1e-3 of the stored dense oracle product and of all
+    columns within 1e-4 of the FP64 product."""
+    name, s, d = case
+    if name not in ("coated_r075", "cube_small", "nanoparticle"):
+        pytest.skip("three media, sharp edges and the most leaf directions suffice")
+    R = 40
+    ph = np.exp(1j * np.linspace(0.0, 2.0, R // 2))
+    X = np.concatenate([d["x"] * p for p in ph])
+    x = _dev(X, s.ne)
+
+    def product(rec_tc, parts):
+        sie.sie_set_param(s.ctx, 8, rec_tc)
+        y = torch.zeros_like(x)
+        sie.sie_matvec_parts(s.ctx, x, y, R, sie.SIE_PREC_MIXED, parts)
+        return _host(y)
+
+    try:
+        sie.sie_set_param(s.ctx, 2, 0)                       # SIMT aggregation: isolate the receive
+        whole = np.linalg.norm(product(0, 3))
+        ref = product(0, 2)
+        for rb in (16, 32, 64):
+            got = product(rb, 2)
+            diff = np.linalg.norm(got - ref)
+            print(f"{name}: tensor-core receive, {rb} right-hand sides per pass: far part rel diff "
+                  f"{diff / np.linalg.norm(ref):.2e}, relative to the product {diff / whole:.2e}")
+            assert np.all(np.isfinite(got)) and diff < 1e-5 * whole
+        sie.sie_set_param(s.ctx, 2, 16)
+        sie.sie_set_param(s.ctx, 8, 32)
+        y = torch.zeros_like(x)
+        sie.mlfmm_matvec(s.ctx, x, y, R, sie.SIE_PREC_MIXED)
+        y64 = torch.zeros_like(x)
+        sie.mlfmm_matvec(s.ctx, x, y64, R, sie.SIE_PREC_FP64)
+        yh = _host(y)
+        assert rel(yh[:2], d["y"]) < 1e-3
+        assert rel(yh, _host(y64)) < 1e-4
+    finally:
+        sie.sie_set_param(s.ctx, 2, 16)
+        sie.sie_set_param(s.ctx, 8, 0)
+
+
 def test_block_product_equals_single_products(case):
     """A block of 9 right-hand sides (the translations then run by sibling
     groups) gives the products of the right-hand sides one at a time (per

@@ -50,7 +50,8 @@ def _ilu(s, x):
 
 
 def _reset(s):
-    sie.apply_tuning(s.ctx, {"near_rb": 0, "ilu_rb": 0, "aggregation": 0, "receive_rb": 0, "m2l": -1})
+    sie.apply_tuning(s.ctx, {"near_rb": 0, "ilu_rb": 0, "aggregation": 0, "receive_rb": 0, "m2l": -1,
+                             "receive_tc": 0})
     sie.sie_set_param(s.ctx, 2, 16)
 
 
@@ -78,11 +79,13 @@ def test_tile_shapes_give_the_same_product(solver):
         scale = np.linalg.norm(ref)
         for m2l in (0, 1, 2):
             for agg in (0, 16):
-                _reset(s)
-                sie.sie_set_param(s.ctx, 7, m2l)
-                sie.sie_set_param(s.ctx, 2, 2 if agg else 0)
-                sie.sie_set_param(s.ctx, 3, agg)
-                assert np.linalg.norm(_prod(s, x) - ref) < 1e-5 * scale, (m2l, agg)
+                for rtc in (0, 16):
+                    _reset(s)
+                    sie.sie_set_param(s.ctx, 7, m2l)
+                    sie.sie_set_param(s.ctx, 2, 2 if agg else 0)
+                    sie.sie_set_param(s.ctx, 3, agg)
+                    sie.sie_set_param(s.ctx, 8, rtc)
+                    assert np.linalg.norm(_prod(s, x) - ref) < 1e-5 * scale, (m2l, agg, rtc)
     finally:
         _reset(s)
 
@@ -97,7 +100,7 @@ def test_autotune_choices_round_trip(solver, tmp_path):
         t = sie.sie_autotune(s.ctx, R, reps=1, path=path)
         print(f"autotune at {R} right-hand sides: {t}")
         assert t["near_rb"] in (4, 8, 16) and t["ilu_rb"] in (4, 8, 16) and t["receive_rb"] in (1, 2, 4)
-        assert t["aggregation"] in (0, 16, 32, 64) and t["m2l"] in (0, 1, 2)
+        assert t["aggregation"] in (0, 16, 32, 64) and t["m2l"] in (0, 1, 2) and t["receive_tc"] in (0, 16, 32, 64)
         assert all(v > 0 for v in t["ms"])
         assert json.load(open(path)) == t
         tuned = _prod(s, x)
