@@ -349,8 +349,9 @@ sie_status sie_device_status(sie_ctx *ctx);
  *      per target box below), 0 per target box, 1 sibling groups from 2 on,
  *      2 sibling groups whose union list is split over the warps of a CTA.
  *   8  tensor-core leaf receive (FP32 operator of the Krylov steps, blocks
- *      of right-hand sides): right-hand sides per pass, 0 (default: the
- *      SIMT receive), 16, 32 or 64.
+ *      of right-hand sides): right-hand sides per pass, -1 (default: from 16
+ *      right-hand sides on, 16, 32 or 64 by the block size), 0 (the SIMT
+ *      receive), 16, 32 or 64.
  * Keys 2-8 are tile shapes: results agree to rounding (the tensor-core
  * aggregation and receive to their FP32-level split operands), speed
  * differs.

@@ -360,7 +360,7 @@ def apply_tuning(ctx, tuning):
             tuning = json.load(f)
     sie_set_param(ctx, 2, 2 if tuning["aggregation"] else 0)
     for name, key in TUNING_KEYS.items():
-        sie_set_param(ctx, key, tuning.get(name, 0))
+        sie_set_param(ctx, key, tuning.get(name, {"m2l": -1, "receive_tc": -1}.get(name, 0)))
 
 
 def sie_query(ctx, key):

@@ -281,8 +281,9 @@ struct sie_ctx {
   // receive; M2L form (0 per target box, 1 by sibling groups, 2 by sibling
   // groups split over warps)
   int tune_near_rb = 0, tune_ilu_rb = 0, tune_rec_rb = 0, tune_m2l = -1;
-  // tensor-core leaf receive: right-hand sides per pass (0: the SIMT receive)
-  int rec_tc_rb = 0;
+  // tensor-core leaf receive: right-hand sides per pass (0: the SIMT receive,
+  // -1: from 16 right-hand sides on, by the block size)
+  int rec_tc_rb = -1;
 };
 
 // ------------------------------------------------------------------ host helpers (host.cpp)
@@ -324,6 +325,7 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs);
 // tensor-core leaf aggregation (tensor.cu): right-hand sides per pass for a
 // block of nrhs (0: the SIMT kernel is used), and the launch for one medium
 int agg_tc_block(const sie_ctx *c, int nrhs);
+int rec_tc_block(const sie_ctx *c, int nrhs);
 bool op_aggregate_tc(sie_ctx *c, int rb, int K, int nbox, int max_leaf, int nrhs, const int *box_start,
                      const int64_t *box_off, const int *basis_p, const int *sign, const unsigned char *Aop,
                      const zf *x, zf *S, cudaStream_t st);

@@ -1473,8 +1473,8 @@ extern "C" sie_status sie_set_param(sie_ctx *c, int32_t key, int64_t value) {
         graphs_free(c);
         break;
       case 8:
-        SIE_REQUIRE(value == 0 || value == 16 || value == 32 || value == 64, SIE_EINVAL,
-                    "sie_set_param: tensor-core receive block must be 0, 16, 32 or 64");
+        SIE_REQUIRE(value == -1 || value == 0 || value == 16 || value == 32 || value == 64, SIE_EINVAL,
+                    "sie_set_param: tensor-core receive block must be -1, 0, 16, 32 or 64");
         c->rec_tc_rb = (int)value;
         graphs_free(c);
         break;

@@ -1645,11 +1645,11 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
                                                 cx<T>((T)ie.real(), (T)ie.imag()), y, cx<T>((T)cj.real(), (T)cj.imag()),
                                                 cx<T>((T)cm.real(), (T)cm.imag()));
       };
-      // blocks of right-hand sides in the FP32 Krylov operator: split-BF16 products
-      // on the tensor cores when chosen (sie_set_param key 8 or the autotuner)
-      const bool rec_tc = std::is_same<T, float>::value && std::is_same<TY, float>::value && R >= 2 &&
-                          c->rec_tc_rb > 0 &&
-                          op_receive_tc(c, c->rec_tc_rb, LL.K, LL.nbox, R, G.d_box_start, G.d_rec_off, G.d_basis_p,
+      // blocks of right-hand sides in the FP32 Krylov operator (not the true
+      // residual): split-BF16 products on the tensor cores (sie_set_param key 8)
+      const int rec_rb = (std::is_same<T, float>::value && std::is_same<TY, float>::value) ? rec_tc_block(c, R) : 0;
+      const bool rec_tc = rec_rb > 0 &&
+                          op_receive_tc(c, rec_rb, LL.K, LL.nbox, R, G.d_box_start, G.d_rec_off, G.d_basis_p,
                                         (const unsigned char *)G.d_rec_op, (const zf *)LL.d_I,
                                         zf((float)G.eta.real(), (float)G.eta.imag()),
                                         zf((float)ie.real(), (float)ie.imag()), zf((float)cj.real(), (float)cj.imag()),

@@ -618,6 +618,13 @@ int agg_tc_block(const sie_ctx *c, int nrhs) {
   return nrhs >= 64 ? 64 : nrhs >= 32 ? 32 : 16;
 }
 
+// right-hand sides per pass of the tensor-core receive for a block of nrhs (0: the SIMT receive)
+int rec_tc_block(const sie_ctx *c, int nrhs) {
+  if (c->rec_tc_rb >= 0) return nrhs >= 2 ? c->rec_tc_rb : 0;
+  if (nrhs < 16) return 0;
+  return nrhs >= 64 ? 64 : nrhs >= 32 ? 32 : 16;
+}
+
 // pre-split A operand of the tensor-core aggregation for one medium (setup)
 void build_agg_operand(sie_ctx *c, RegionHost &R, int K) {
   const int nbox = (int)R.box_start.size() - 1;

@@ -305,7 +305,7 @@ def test_tensor_core_receive(case):
         assert rel(yh, _host(y64)) < 1e-4
     finally:
         sie.sie_set_param(s.ctx, 2, 16)
-        sie.sie_set_param(s.ctx, 8, 0)
+        sie.sie_set_param(s.ctx, 8, -1)
 
 
 def test_block_product_equals_single_products(case):

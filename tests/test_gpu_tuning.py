@@ -51,7 +51,7 @@ def _ilu(s, x):
 
 def _reset(s):
     sie.apply_tuning(s.ctx, {"near_rb": 0, "ilu_rb": 0, "aggregation": 0, "receive_rb": 0, "m2l": -1,
-                             "receive_tc": 0})
+                             "receive_tc": -1})
     sie.sie_set_param(s.ctx, 2, 16)
 
 
@@ -100,7 +100,7 @@ def test_autotune_choices_round_trip(solver, tmp_path):
         t = sie.sie_autotune(s.ctx, R, reps=1, path=path)
         print(f"autotune at {R} right-hand sides: {t}")
         assert t["near_rb"] in (4, 8, 16) and t["ilu_rb"] in (4, 8, 16) and t["receive_rb"] in (1, 2, 4)
-        assert t["aggregation"] in (0, 16, 32, 64) and t["m2l"] in (0, 1, 2) and t["receive_tc"] in (0, 16, 32, 64)
+        assert t["aggregation"] in (0, 16, 32, 64) and t["m2l"] in (0, 1, 2) and t["receive_tc"] in (-1, 0, 16, 32, 64)
         assert all(v > 0 for v in t["ms"])
         assert json.load(open(path)) == t
         tuned = _prod(s, x)
