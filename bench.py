@@ -166,6 +166,25 @@ def arm_config(unknowns, ws):
             "restart": RESTART, "nrhs_per_gpu": 1, "parallelism": f"replicas{ws}"}
 
 
+def oracle_c1_full():
+    """The oracle end to end, nothing extrapolated, on the small workload it
+    can finish (homogeneous sphere, 3 840 unknowns): dense JMCFIE fill, dense
+    LU, bistatic RCS at 361 angles."""
+    from oracle import farfield, fill, solvers
+    from oracle.rwg import Mesh
+    from paper_1704_06862_gb300 import geometry as geo
+    t0 = time.perf_counter()
+    m = Mesh(**geo.workload("sphere_c1"))
+    Z = fill.assemble(m)
+    t1 = time.perf_counter()
+    x = solvers.lu_solve(Z, fill.rhs(m, [[0.0, 0.0, 0.0, 1.0]])[0])
+    t2 = time.perf_counter()
+    farfield.rcs(m, x[None], geo.bistatic_angles(361))
+    t3 = time.perf_counter()
+    return {"workload": "sphere_c1", "unknowns": 2 * m.ne, "s_to_rcs": t3 - t0, "fill_s": t1 - t0, "lu_s": t2 - t1,
+            "rcs_s": t3 - t2, "cores": os.cpu_count()}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -177,12 +196,14 @@ def run_reference(args, ws, rank):
         if i >= args.warmup:
             vals.append(est)
     v = float(np.mean(vals))
+    c1 = None if args.no_c1 else oracle_c1_full()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": arm_config(unknowns, ws),
             "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "sample": sample, "value": v, "unit": "s"},
-            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "oracle_c1_end_to_end": c1}
     print(json.dumps(line), flush=True)
 
 
@@ -206,6 +227,8 @@ def main():
                     help="incidences of the cube's monostatic sweep (0: skip the leg)")
     ap.add_argument("--cube-block", type=int, default=64, help="right-hand sides per block of the cube sweep")
     ap.add_argument("--tuning-file", default=None, help="where the cube leg's autotuner writes its choice (JSON)")
+    ap.add_argument("--no-c1", action="store_true",
+                    help="skip the small homogeneous-sphere leg (GPU arm) / its full oracle run (reference arm)")
     ap.add_argument("--ellipsoid", action="store_true",
                     help="add the ellipsoid leg (355 488 unknowns, learned preconditioner on 32 incidences)")
     ap.add_argument("--formulation-study", action="store_true",
@@ -446,6 +469,31 @@ def main():
         del bn, xn
         sn.close()
 
+    # the small homogeneous-sphere workload (3 840 unknowns) end to end on the
+    # GPU, beside the oracle's end-to-end time on the same case (reference arm)
+    c1 = None
+    if not args.no_c1:
+        t0 = time.perf_counter()
+        s1 = sie.Solver(geo.workload("sphere_c1"), levels=3, digits=DIGITS, stream=stream)
+        torch.cuda.synchronize()
+        c1 = {"workload": "sphere_c1", "unknowns": 2 * s1.ne, "levels": 3, "setup_s": time.perf_counter() - t0}
+        b1 = s1.vec(1)
+        x1 = s1.vec(1)
+        for rep in range(2):                     # the first solve captures the step graphs
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sie.sie_plane_wave_rhs(s1.ctx, inc, b1)
+            x1.zero_()
+            st1 = sie.gmres_solve(s1.ctx, b1, x1, 1, restart=RESTART, max_iters=3000, tol=TOL,
+                                  prec=sie.SIE_PREC_MIXED, precond=1, check=False, graphs=not args.no_graphs)[0]
+            sie.rcs_farfield_prec(s1.ctx, x1, 1, obs, sie.SIE_PREC_MIXED)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        c1.update({"ms_to_rcs": e0.elapsed_time(e1), "iters": st1["iters"], "converged": st1["converged"]})
+        del b1, x1
+        s1.close()
+
     # RCS against the Mie series under mesh refinement (the discretisation error
     # of the flat-facet RWG model falls as h^2): the homogeneous sphere of the
     # small workload and the two-layer sphere at finer meshes than the timed one;
@@ -678,7 +726,7 @@ def main():
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
                 "d2h_bytes_per_step": int(rcs.nbytes)},
         "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp,
-        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "mie_refinement": mie_ref, "cube_monostatic": cube, "ellipsoid": ell, "stages_ms": stages, "matvec": matvec,
+        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "mie_refinement": mie_ref, "sphere_c1": c1, "cube_monostatic": cube, "ellipsoid": ell, "stages_ms": stages, "matvec": matvec,
         "roofline": roofline, "roofline_near_spmv": roofline_near, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches), "krylov_step_graphs": graphs_state,
     }
     if rank == 0:
