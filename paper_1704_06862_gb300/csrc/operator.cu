@@ -338,11 +338,125 @@ __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int 
 // Register tiles: a G task owns the columns jp and jp + Np/2 of one theta row;
 // an H task owns the pair (jp, jp + Np/2), whose phi + pi partners are each
 // other, for two parent theta rows, so every shared-memory load feeds several FMAs.
+// Exact separable interpolation of one child's pattern to the parent
+// sampling, shifted to the parent centre (upward pass).  One CTA per (child,
+// right-hand side), JM of the sources J, M per pass.  The pattern is carried
+// as three Cartesian components: (theta, phi) -> xyz at the child directions
+// (A), trigonometric interpolation in phi (G = A Phi^T), the folded Lagrange
+// step in theta (H = Th+ G + Th- G(phi + pi)), xyz -> (theta, phi) at the
+// parent directions, times the shift exp(j k khat.(c_child - c_parent)).
+// Output Y[child][J|M][theta|phi][r][k_parent]; k_up_sum adds the children.
+// Register tiles: a G task owns the columns jp and jp + Np/2 of one theta row;
+// an H task owns the pair (jp, jp + Np/2), whose phi + pi partners are each
+// other, for two parent theta rows, so every shared-memory load feeds several FMAs.
+template <typename T, int JM>
+__global__ void __launch_bounds__(256) k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs,
+                                                  const int *__restrict__ oct, const T *__restrict__ tpc,
+                                                  const T *__restrict__ tpp, const T *__restrict__ Phi,
+                                                  const T *__restrict__ Thp, const T *__restrict__ Thm,
+                                                  const cx<T> *__restrict__ up, const cx<T> *__restrict__ Sc,
+                                                  cx<T> *__restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int Q = 3 * JM, IP = 2;
+  const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1, nthp = Lp + 1, hp = Lp + 1;
+  cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [Q][Kc]
+  cx<T> *G = A + (size_t)Q * Kc;                    // [Q][nthc][Np]
+  T *PhT = reinterpret_cast<T *>(G + (size_t)Q * nthc * Np);  // [Nc][Np]
+  T *Tps = PhT + Nc * Np, *Tms = Tps + nthp * nthc;           // [nthp][nthc]
+  const int c = blockIdx.x, r = blockIdx.y, o = oct[c], tid = threadIdx.x, NT = blockDim.x;
+  for (int i = tid; i < Np * Nc; i += NT) {
+    const int jp = i / Nc, jc = i - jp * Nc;
+    PhT[jc * Np + jp] = Phi[i];
+  }
+  for (int i = tid; i < nthp * nthc; i += NT) {
+    Tps[i] = Thp[i];
+    Tms[i] = Thm[i];
+  }
+  const int nib = (nthp + IP - 1) / IP;
+  for (int jm0 = 0; jm0 < 2; jm0 += JM) {
+    __syncthreads();
+    for (int i = tid; i < JM * Kc; i += NT) {
+      const int m = i / Kc, t = i - m * Kc;
+      const cx<T> *st = Sc + (((size_t)c * 4 + (jm0 + m) * 2) * nrhs + r) * Kc;
+      const cx<T> ft = st[t], fp = st[(size_t)nrhs * Kc + t];
+      const T *u = tpc + 6 * (size_t)t;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) A[(size_t)(m * 3 + x) * Kc + t] = ft * u[x] + fp * u[3 + x];
+    }
+    __syncthreads();
+    for (int task = tid; task < nthc * hp; task += NT) {
+      const int ic = task / hp, jp = task - ic * hp;
+      cx<T> g0[Q], g1[Q];
+      for (int jc = 0; jc < Nc; ++jc) {
+        const T f0 = PhT[jc * Np + jp], f1 = PhT[jc * Np + jp + hp];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const cx<T> a = A[(size_t)q * Kc + ic * Nc + jc];
+          g0[q].re = fma(f0, a.re, g0[q].re);
+          g0[q].im = fma(f0, a.im, g0[q].im);
+          g1[q].re = fma(f1, a.re, g1[q].re);
+          g1[q].im = fma(f1, a.im, g1[q].im);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        G[((size_t)q * nthc + ic) * Np + jp] = g0[q];
+        G[((size_t)q * nthc + ic) * Np + jp + hp] = g1[q];
+      }
+    }
+    __syncthreads();
+    for (int task = tid; task < nib * hp; task += NT) {
+      const int ib = task / hp, jh = task - ib * hp, ip0 = ib * IP;
+      cx<T> h0[IP][Q], h1[IP][Q];  // parent columns jh and jh + hp
+      for (int ic = 0; ic < nthc; ++ic) {
+        cx<T> ga[Q], gb[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          ga[q] = G[((size_t)q * nthc + ic) * Np + jh];
+          gb[q] = G[((size_t)q * nthc + ic) * Np + jh + hp];
+        }
+#pragma unroll
+        for (int k = 0; k < IP; ++k) {
+          const int ip = min(ip0 + k, nthp - 1);
+          const T a = Tps[ip * nthc + ic], bq = Tms[ip * nthc + ic];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            h0[k][q].re = fma(a, ga[q].re, fma(bq, gb[q].re, h0[k][q].re));
+            h0[k][q].im = fma(a, ga[q].im, fma(bq, gb[q].im, h0[k][q].im));
+            h1[k][q].re = fma(a, gb[q].re, fma(bq, ga[q].re, h1[k][q].re));
+            h1[k][q].im = fma(a, gb[q].im, fma(bq, ga[q].im, h1[k][q].im));
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < IP; ++k) {
+        const int ip = ip0 + k;
+        if (ip >= nthp) break;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int tp = ip * Np + jh + half * hp;
+          const T *u = tpp + 6 * (size_t)tp;
+          const cx<T> sh = up[(size_t)o * Kp + tp];
+#pragma unroll
+          for (int m = 0; m < JM; ++m) {
+            const cx<T> *H = half ? &h1[k][3 * m] : &h0[k][3 * m];
+            const cx<T> yt = H[0] * u[0] + H[1] * u[1] + H[2] * u[2];
+            const cx<T> yp = H[0] * u[3] + H[1] * u[4] + H[2] * u[5];
+            Y[(((size_t)c * 4 + (jm0 + m) * 2) * nrhs + r) * Kp + tp] = sh * yt;
+            Y[(((size_t)c * 4 + (jm0 + m) * 2 + 1) * nrhs + r) * Kp + tp] = sh * yp;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Chunked form of k_interp_up for parent samplings too large for shared memory.
 // The parent's column pairs (jp, jp + Np/2) are taken cw at a time (a chunk:
 // G holds only its 2 cw columns), so a large parent sampling fits in shared
 // memory; with one chunk (cw = Np/2) the arithmetic is that of a single pass.
 template <typename T, int JM>
-__global__ void __launch_bounds__(256) k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs, int cw_max,
+__global__ void __launch_bounds__(256) k_interp_up_chunked(int Kc, int Lc, int Kp, int Lp, int nrhs, int cw_max,
                                                   const int *__restrict__ oct, const T *__restrict__ tpc,
                                                   const T *__restrict__ tpp, const T *__restrict__ Phi,
                                                   const T *__restrict__ Thp, const T *__restrict__ Thm,
@@ -469,12 +583,120 @@ __global__ void k_up_sum(int Kp, int nrhs, const int *__restrict__ ch_ptr, const
 // Register tiles as in k_interp_up: a theta-step task owns the column pair
 // (j, j + Np/2) for two child theta rows; a phi-step task owns the child
 // columns jc and jc + Nc/2 of one theta row.
+// Exact transpose of k_interp_up (anterpolation, downward pass), with the
+// receive shift exp(-j k khat.(c_child - c_parent)): one CTA per (child box,
+// right-hand side), I_child += Interp^T [dn (.) I_parent].  Quadrature weights
+// are folded into the translators, so the adjoint is the plain transpose.
+// Register tiles as in k_interp_up: a theta-step task owns the column pair
+// (j, j + Np/2) for two child theta rows; a phi-step task owns the child
+// columns jc and jc + Nc/2 of one theta row.
+template <typename T, int JM>
+__global__ void __launch_bounds__(256) k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs,
+                                                  const int *__restrict__ parent, const int *__restrict__ oct,
+                                                  const T *__restrict__ tpc, const T *__restrict__ tpp,
+                                                  const T *__restrict__ Phi, const T *__restrict__ Thp,
+                                                  const T *__restrict__ Thm, const cx<T> *__restrict__ dn,
+                                                  const cx<T> *__restrict__ Ip, cx<T> *__restrict__ Ic) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int Q = 3 * JM, IC = 2;
+  const int Nc = 2 * Lc + 2, Np = 2 * Lp + 2, nthc = Lc + 1, nthp = Lp + 1, hp = Lp + 1, hc = Lc + 1;
+  cx<T> *A = reinterpret_cast<cx<T> *>(smem_raw);  // [Q][Kp]
+  cx<T> *G = A + (size_t)Q * Kp;                    // [Q][nthc][Np]
+  T *Ps = reinterpret_cast<T *>(G + (size_t)Q * nthc * Np);  // Phi [Np][Nc]
+  T *Tps = Ps + Np * Nc, *Tms = Tps + nthp * nthc;           // [nthp][nthc]
+  const int c = blockIdx.x, r = blockIdx.y, pb = parent[c], o = oct[c], tid = threadIdx.x, NT = blockDim.x;
+  for (int i = tid; i < Np * Nc; i += NT) Ps[i] = Phi[i];
+  for (int i = tid; i < nthp * nthc; i += NT) {
+    Tps[i] = Thp[i];
+    Tms[i] = Thm[i];
+  }
+  const int nicb = (nthc + IC - 1) / IC;
+  for (int jm0 = 0; jm0 < 2; jm0 += JM) {
+    __syncthreads();
+    for (int i = tid; i < JM * Kp; i += NT) {
+      const int m = i / Kp, t = i - m * Kp;
+      const cx<T> *it = Ip + (((size_t)pb * 4 + (jm0 + m) * 2) * nrhs + r) * Kp;
+      const cx<T> sh = dn[(size_t)o * Kp + t];
+      const cx<T> ut = sh * it[t], up_ = sh * it[(size_t)nrhs * Kp + t];
+      const T *u = tpp + 6 * (size_t)t;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) A[(size_t)(m * 3 + x) * Kp + t] = ut * u[x] + up_ * u[3 + x];
+    }
+    __syncthreads();
+    // transpose of the theta step: G[q][ic][j] = sum_ip Th+[ip][ic] A[q][ip][j] + Th-[ip][ic] A[q][ip][j + Np/2]
+    for (int task = tid; task < nicb * hp; task += NT) {
+      const int cb = task / hp, jh = task - cb * hp, ic0 = cb * IC;
+      cx<T> g0[IC][Q], g1[IC][Q];
+      for (int ip = 0; ip < nthp; ++ip) {
+        cx<T> aa[Q], ab[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          aa[q] = A[(size_t)q * Kp + ip * Np + jh];
+          ab[q] = A[(size_t)q * Kp + ip * Np + jh + hp];
+        }
+#pragma unroll
+        for (int k = 0; k < IC; ++k) {
+          const int ic = min(ic0 + k, nthc - 1);
+          const T w1 = Tps[ip * nthc + ic], w2 = Tms[ip * nthc + ic];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            g0[k][q].re = fma(w1, aa[q].re, fma(w2, ab[q].re, g0[k][q].re));
+            g0[k][q].im = fma(w1, aa[q].im, fma(w2, ab[q].im, g0[k][q].im));
+            g1[k][q].re = fma(w1, ab[q].re, fma(w2, aa[q].re, g1[k][q].re));
+            g1[k][q].im = fma(w1, ab[q].im, fma(w2, aa[q].im, g1[k][q].im));
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < IC; ++k) {
+        const int ic = ic0 + k;
+        if (ic >= nthc) break;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          G[((size_t)q * nthc + ic) * Np + jh] = g0[k][q];
+          G[((size_t)q * nthc + ic) * Np + jh + hp] = g1[k][q];
+        }
+      }
+    }
+    __syncthreads();
+    // transpose of the phi step, projection to (theta, phi) at the child directions
+    for (int task = tid; task < nthc * hc; task += NT) {
+      const int ic = task / hc, jc = task - ic * hc;
+      cx<T> c0[Q], c1[Q];
+      for (int jp = 0; jp < Np; ++jp) {
+        const T f0 = Ps[jp * Nc + jc], f1 = Ps[jp * Nc + jc + hc];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const cx<T> g = G[((size_t)q * nthc + ic) * Np + jp];
+          c0[q].re = fma(f0, g.re, c0[q].re);
+          c0[q].im = fma(f0, g.im, c0[q].im);
+          c1[q].re = fma(f1, g.re, c1[q].re);
+          c1[q].im = fma(f1, g.im, c1[q].im);
+        }
+      }
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int tc = ic * Nc + jc + half * hc;
+        const T *u = tpc + 6 * (size_t)tc;
+#pragma unroll
+        for (int m = 0; m < JM; ++m) {
+          const cx<T> *C = half ? &c1[3 * m] : &c0[3 * m];
+          cx<T> *it = Ic + (((size_t)c * 4 + (jm0 + m) * 2) * nrhs + r) * Kc;
+          it[tc] += C[0] * u[0] + C[1] * u[1] + C[2] * u[2];
+          it[(size_t)nrhs * Kc + tc] += C[0] * u[3] + C[1] * u[4] + C[2] * u[5];
+        }
+      }
+    }
+  }
+}
+
+// Chunked form of k_anterp_dn for parent samplings too large for shared memory.
 // The parent's column pairs are taken cw at a time (a chunk of A and G in
 // shared memory); each chunk adds its part of the phi-transpose sums into the
 // child, columns jp of the chunk first, then their partners jp + Np/2 (with
 // one chunk, the order of a single pass over jp = 0 .. Np - 1).
 template <typename T, int JM>
-__global__ void __launch_bounds__(256) k_anterp_dn(int Kc, int Lc, int Kp, int Lp, int nrhs, int cw_max,
+__global__ void __launch_bounds__(256) k_anterp_dn_chunked(int Kc, int Lc, int Kp, int Lp, int nrhs, int cw_max,
                                                   const int *__restrict__ parent, const int *__restrict__ oct,
                                                   const T *__restrict__ tpc, const T *__restrict__ tpp,
                                                   const T *__restrict__ Phi, const T *__restrict__ Thp,
@@ -499,18 +721,25 @@ __global__ void __launch_bounds__(256) k_anterp_dn(int Kc, int Lc, int Kp, int L
     for (int j0 = 0; j0 < hp; j0 += CW) {
       const int cw = min(CW, hp - j0);
       __syncthreads();  // A and G free again
-      for (int i = tid; i < JM * nthp * 2 * cw; i += NT) {
-        const int m = i / (nthp * 2 * cw), rem = i - m * (nthp * 2 * cw);
-        const int ip = rem / (2 * cw), jj = rem - ip * (2 * cw);
-        const int half = jj >= cw ? 1 : 0, jl = jj - half * cw;
-        const int t = ip * Np + j0 + jl + half * hp;
+      const int per_m = nthp * 2 * cw;
+      for (int i = tid; i < JM * per_m; i += NT) {
+        const int m = i / per_m, rem = i - m * per_m;
+        int t, a;  // parent direction, index within the component's [nthp][2 CW] block
+        if (cw == hp) {  // one chunk: the block is the parent sampling itself
+          t = rem;
+          a = rem;
+        } else {
+          const int ip = rem / (2 * cw), jj = rem - ip * (2 * cw);
+          const int half = jj >= cw ? 1 : 0, jl = jj - half * cw;
+          t = ip * Np + j0 + jl + half * hp;
+          a = ip * G2 + half * CW + jl;
+        }
         const cx<T> *it = Ip + (((size_t)pb * 4 + (jm0 + m) * 2) * nrhs + r) * Kp;
         const cx<T> sh = dn[(size_t)o * Kp + t];
         const cx<T> ut = sh * it[t], up_ = sh * it[(size_t)nrhs * Kp + t];
         const T *u = tpp + 6 * (size_t)t;
 #pragma unroll
-        for (int x = 0; x < 3; ++x)
-          A[((size_t)(m * 3 + x) * nthp + ip) * G2 + half * CW + jl] = ut * u[x] + up_ * u[3 + x];
+        for (int x = 0; x < 3; ++x) A[(size_t)(m * 3 + x) * nthp * G2 + a] = ut * u[x] + up_ * u[3 + x];
       }
       __syncthreads();
       // transpose of the theta step: G[q][ic][j] = sum_ip Th+[ip][ic] A[q][ip][j] + Th-[ip][ic] A[q][ip][j + Np/2]
@@ -554,19 +783,19 @@ __global__ void __launch_bounds__(256) k_anterp_dn(int Kc, int Lc, int Kp, int L
       for (int task = tid; task < nthc * hc; task += NT) {
         const int ic = task / hc, jc = task - ic * hc;
         cx<T> c0[Q], c1[Q];
-        for (int half = 0; half < 2; ++half)
-          for (int jl = 0; jl < cw; ++jl) {
-            const int jp = j0 + jl + half * hp;
-            const T f0 = Ps[jp * Nc + jc], f1 = Ps[jp * Nc + jc + hc];
+        // G columns jj: jp = j0 + jj for jj < cw, j0 + jj - cw + hp after (one chunk: jp = jj)
+        for (int jj = 0; jj < 2 * cw; ++jj) {
+          const int jp = j0 + (jj < cw ? jj : jj - cw + hp), gj = jj < cw ? jj : jj - cw + CW;
+          const T f0 = Ps[jp * Nc + jc], f1 = Ps[jp * Nc + jc + hc];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-              const cx<T> g = G[((size_t)q * nthc + ic) * G2 + half * CW + jl];
-              c0[q].re = fma(f0, g.re, c0[q].re);
-              c0[q].im = fma(f0, g.im, c0[q].im);
-              c1[q].re = fma(f1, g.re, c1[q].re);
-              c1[q].im = fma(f1, g.im, c1[q].im);
-            }
+          for (int q = 0; q < Q; ++q) {
+            const cx<T> g = G[((size_t)q * nthc + ic) * G2 + gj];
+            c0[q].re = fma(f0, g.re, c0[q].re);
+            c0[q].im = fma(f0, g.im, c0[q].im);
+            c1[q].re = fma(f1, g.re, c1[q].re);
+            c1[q].im = fma(f1, g.im, c1[q].im);
           }
+        }
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
           const int tc = ic * Nc + jc + half * hc;
@@ -1546,18 +1775,23 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
       const size_t smem = smem_for(cw);
       cx<T> *Y = (cx<T> *)((char *)c->d_scratch + gi * c->scratch_region);
       dim3 grid(C.nbox, R);
-      auto args = [&](auto kern) {
-        set_smem(kern, smem);
-        // threads sized to the larger task list (phi step: theta rows x column pairs;
-        // theta step: row pairs x column pairs), so small levels fit more CTAs per SM
-        const int tasks = std::max(nthc * cw, (nthp + 1) / 2 * cw);
-        const int threads = std::min(256, std::max(64, (tasks + 31) / 32 * 32));
-        kern<<<grid, threads, smem, st>>>(C.K, C.L, P.K, P.L, R, cw, C.d_oct, (const T *)tsel<T>::tp(C),
-                                             (const T *)tsel<T>::tp(P), (const T *)tsel<T>::Phi(P),
-                                             (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
-                                             (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
-      };
-      args(k_interp_up<T, 1>);
+      // threads sized to the larger task list (phi step: theta rows x column pairs;
+      // theta step: row pairs x column pairs), so small levels fit more CTAs per SM
+      const int tasks = std::max(nthc * cw, (nthp + 1) / 2 * cw);
+      const int threads = std::min(256, std::max(64, (tasks + 31) / 32 * 32));
+      if (cw == P.L + 1) {  // the whole parent sampling at once: the single-pass kernel
+        set_smem(k_interp_up<T, 1>, smem);
+        k_interp_up<T, 1><<<grid, threads, smem, st>>>(
+            C.K, C.L, P.K, P.L, R, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
+            (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
+            (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
+      } else {
+        set_smem(k_interp_up_chunked<T, 1>, smem);
+        k_interp_up_chunked<T, 1><<<grid, threads, smem, st>>>(
+            C.K, C.L, P.K, P.L, R, cw, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
+            (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
+            (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
+      }
       SIE_CHECK_LAUNCH();
       k_up_sum<T><<<dim3((P.K + 127) / 128, P.nbox), 128, 0, st>>>(P.K, R, P.d_ch_ptr, P.d_ch_idx, Y,
                                                                            (cx<T> *)P.d_S);
@@ -1608,16 +1842,21 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
       while (cw > 1 && smem_for(cw) > 200 * 1024) cw = (cw + 1) / 2;
       const size_t smem = smem_for(cw);
       dim3 grid(C.nbox, R);
-      auto args = [&](auto kern) {
-        set_smem(kern, smem);
-        const int tasks = std::max((nthc + 1) / 2 * cw, nthc * (C.L + 1));
-        const int threads = std::min(256, std::max(64, (tasks + 31) / 32 * 32));
-        kern<<<grid, threads, smem, st>>>(C.K, C.L, P.K, P.L, R, cw, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C),
-                                             (const T *)tsel<T>::tp(P), (const T *)tsel<T>::Phi(P),
-                                             (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
-                                             (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
-      };
-      args(k_anterp_dn<T, 1>);
+      const int tasks = std::max((nthc + 1) / 2 * cw, nthc * (C.L + 1));
+      const int threads = std::min(256, std::max(64, (tasks + 31) / 32 * 32));
+      if (cw == P.L + 1) {  // the whole parent sampling at once: the single-pass kernel
+        set_smem(k_anterp_dn<T, 1>, smem);
+        k_anterp_dn<T, 1><<<grid, threads, smem, st>>>(
+            C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
+            (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
+            (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
+      } else {
+        set_smem(k_anterp_dn_chunked<T, 1>, smem);
+        k_anterp_dn_chunked<T, 1><<<grid, threads, smem, st>>>(
+            C.K, C.L, P.K, P.L, R, cw, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
+            (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
+            (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
+      }
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
