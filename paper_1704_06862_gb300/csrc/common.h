@@ -148,6 +148,7 @@ struct RegionHost {
   int max_leaf = 0;             // most bases in one leaf box
   std::vector<LevelHost> lev;   // index = level number; levels 2..leaf carry tables
   int *d_basis_p = nullptr, *d_basis_sign = nullptr, *d_box_start = nullptr, *d_basis_box = nullptr;
+  int rpart_off = 0;            // first row of this medium in the concatenated receive outputs
   double *d_box_centre = nullptr;  // leaf box centres [nleaf][3]
   void *d_V64 = nullptr, *d_V32 = nullptr;    // radiation patterns [nb][2][Kleaf]
   void *d_P64 = nullptr, *d_P32 = nullptr;  // combined receive patterns [nb][2][Kleaf] (k_receive_fold)
@@ -190,6 +191,11 @@ struct IluHost {
   int64_t nblk_off = 0, nblk_inv = 0;  // off-box factor blocks (L and U); in-box inverse blocks
   unsigned *d_bar = nullptr;  // grid-barrier arrival count of the persistent apply (cleared before each launch)
 };
+
+// most right-hand sides per product whose leaf receives run concurrently (one
+// output block per medium, then a combine in medium order); larger blocks
+// receive one medium after another directly into y
+constexpr int RPART_MAX_RHS = 8;
 
 struct sie_ctx {
   int device = 0;
@@ -251,6 +257,12 @@ struct sie_ctx {
   void *d_xf = nullptr, *d_yf = nullptr;          // FP32 copies
   void *d_scratch = nullptr;                      // upward-pass child contributions, one slice per medium
   size_t scratch_region = 0;                      // bytes of one medium's slice
+  // concurrent receives (blocks of up to RPART_MAX_RHS right-hand sides): each
+  // medium writes its rows [r][rpart_nb][2] here, a combine kernel adds them
+  // into y in medium order; d_rmap [ne][2]: a basis's rows (lower medium first)
+  void *d_rpart = nullptr;
+  int rpart_cap = 0, rpart_nb = 0;
+  int *d_rmap = nullptr;
   std::vector<cudaStream_t> rstream;              // one stream per medium for the far-field passes
   std::vector<cudaEvent_t> ev_join;               // end of each medium's passes
   cudaEvent_t ev_fork = nullptr;                  // start of the far field on the context stream

@@ -92,6 +92,9 @@ void ensure_work(sie_ctx *c, int64_t nrhs) {
   }
   c->scratch_region = (scratch + 255) / 256 * 256;
   c->d_scratch = dev_alloc(c, std::max<size_t>(256, c->scratch_region * c->reg.size()));
+  // per-medium receive outputs for the concurrent receives of small blocks
+  c->rpart_cap = (int)std::min<int64_t>(nrhs, RPART_MAX_RHS);
+  c->d_rpart = dev_alloc(c, std::max<size_t>(256, (size_t)c->rpart_nb * 2 * c->rpart_cap * sizeof(zd)));
   c->nrhs_cap = nrhs;
   c->work_gen++;
 }
@@ -778,6 +781,24 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
     for (int b = 0; b < LL.nbox; ++b)
       for (int x = 0; x < 3; ++x) cen[3 * b + x] = c->origin[x] + (LL.ijk[3 * b + x] + 0.5) * c->hleaf;
     R.d_box_centre = dev_upload(c, cen);
+  }
+  // receive map: each basis lies on one interface, so its far field comes from
+  // (at most) two media; per basis the positions of its rows in the
+  // concatenated per-medium receive outputs, lower medium first (-1: none)
+  {
+    std::vector<int> rmap((size_t)2 * ne, -1);
+    int off = 0;
+    for (auto &R : c->reg) {
+      R.rpart_off = off;
+      for (int i = 0; i < R.nb; ++i) {
+        const int p = R.basis_p[i];
+        SIE_REQUIRE(rmap[2 * (size_t)p + 1] < 0, SIE_EINVAL, "mlfmm_setup: a basis in more than two media");
+        rmap[2 * (size_t)p + (rmap[2 * (size_t)p] < 0 ? 0 : 1)] = off + i;
+      }
+      off += R.nb;
+    }
+    c->rpart_nb = off;
+    c->d_rmap = dev_upload(c, rmap);
   }
   c->have_tree = true;
 }

@@ -814,12 +814,15 @@ __global__ void __launch_bounds__(256) k_anterp_dn_chunked(int Kc, int Lc, int K
 }
 
 // Diagonal M2L translation: I_b(k) = sum_{b' in IL(b)} T_{b-b'}(k) S_b'(k), 4 components.
+// One warp per (target box, slice of 32 directions), the boxes fastest in the
+// grid, so the CTAs in flight at one time share a slice of the translators.
 template <typename T>
-__global__ void k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr, const int *__restrict__ il_src,
-                      const int *__restrict__ il_slot, const cx<T> *__restrict__ Tr, const cx<T> *__restrict__ S,
-                      cx<T> *__restrict__ I) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  int b = blockIdx.y;
+__global__ void __launch_bounds__(32) k_m2l(int nbox, int K, int nrhs, const int *__restrict__ il_ptr,
+                                            const int *__restrict__ il_src, const int *__restrict__ il_slot,
+                                            const cx<T> *__restrict__ Tr, const cx<T> *__restrict__ S,
+                                            cx<T> *__restrict__ I) {
+  int k = blockIdx.y * 32 + threadIdx.x;
+  int b = blockIdx.x;
   if (k >= K) return;
   int e0 = il_ptr[b], e1 = il_ptr[b + 1];
   const size_t cs = (size_t)nrhs * K;  // component stride
@@ -998,7 +1001,8 @@ __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, i
                                                      const int *__restrict__ box_start,
                                                      const int *__restrict__ basis_p, const cx<T> *__restrict__ P,
                                                      const cx<T> *__restrict__ I, cx<T> eta, cx<T> ieta,
-                                                     cx<TY> *__restrict__ y, cx<T> cJ, cx<T> cM) {
+                                                     cx<TY> *__restrict__ y, cx<T> cJ, cx<T> cM,
+                                                     cx<T> *__restrict__ part, int part_off, int part_nb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x, i0 = box_start[b], n = box_start[b + 1] - i0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1052,9 +1056,15 @@ __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, i
           if (rr < nr) {
             const cx<T> sj = warp_sum(yj[rr]), sm = warp_sum(ym[rr]);
             if (lane == 0) {
-              cx<TY> *o = y + ((size_t)(r0 + rr) * ne + p) * 2;
-              o[0] += cx<TY>(cJ * sj);
-              o[1] -= cx<TY>(cM * sm);
+              if (part) {  // this medium's rows, added into y later in medium order
+                cx<T> *o = part + ((size_t)(r0 + rr) * part_nb + part_off + i0 + li0 + li) * 2;
+                o[0] = cJ * sj;
+                o[1] = cM * sm;
+              } else {
+                cx<TY> *o = y + ((size_t)(r0 + rr) * ne + p) * 2;
+                o[0] += cx<TY>(cJ * sj);
+                o[1] -= cx<TY>(cM * sm);
+              }
             }
           }
       }
@@ -1064,6 +1074,29 @@ __global__ void __launch_bounds__(256) k_disaggregate(int K, int ne, int nrhs, i
     cp_async_wait_s<0>();
     __syncthreads();
   }
+}
+
+// The receives' rows added into y in medium order (the lower medium first, as
+// when the receives add into y one medium after another):
+//   y_J += r_J(a) + ... ,  y_M -= r_M(a) ... ; thread = (right-hand side, basis).
+template <typename T, typename TY>
+__global__ void k_rec_combine(int ne, int nrhs, int part_nb, const int *__restrict__ rmap,
+                              const cx<T> *__restrict__ part, cx<TY> *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nrhs * ne) return;
+  const int r = (int)(i / ne), p = (int)(i - (int64_t)r * ne);
+  cx<TY> *o = y + i * 2;
+  cx<TY> yj = o[0], ym = o[1];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int a = rmap[2 * (size_t)p + j];
+    if (a < 0) continue;
+    const cx<T> *q = part + ((size_t)r * part_nb + a) * 2;
+    yj += cx<TY>(q[0]);
+    ym -= cx<TY>(q[1]);
+  }
+  o[0] = yj;
+  o[1] = ym;
 }
 
 // ---------------------------------------------------------------- ILU(0) sweeps
@@ -1724,9 +1757,54 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
   if (c->levels < 3) return;  // every basis pair is near: no far field
   // The media are independent until the receive: each medium's aggregation,
   // upward pass, translations and downward pass run on a stream of their own
-  // (parallel branches when the step is captured as a graph), after which the
-  // receives add into y one medium at a time on the context stream.
+  // (parallel branches when the step is captured as a graph).  For small blocks
+  // each branch ends with its medium's receive into the medium's own rows, and
+  // a combine adds them into y in medium order; otherwise the receives add into
+  // y one medium at a time on the context stream.
   region_streams(c);
+  // leaf receive of medium gi on stream rs: into y directly (part = nullptr) or
+  // into the medium's rows of d_rpart
+  auto receive = [&](size_t gi, cudaStream_t rs, cx<T> *part) {
+    RegionHost &G = c->reg[gi];
+    LevelHost &LL = G.lev[leaf];
+    const size_t per_basis = (size_t)2 * LL.K * sizeof(cx<T>);
+    const int cb = (int)std::max<size_t>(1, std::min<size_t>(32, (32 * 1024) / per_basis));  // bases per chunk
+    std::complex<double> ie = 1.0 / G.eta;
+    // per-row factors of the receive: PMCHWT weights the tangential J-row by
+    // eta~ and the M-row by 1/eta~; the other formulations fold theirs into P
+    const std::complex<double> cj = c->form == 3 ? G.eta : 1.0, cm = c->form == 3 ? 1.0 / G.eta : 1.0;
+    auto rec = [&](auto kern, int rb) {
+      const size_t smem = STAGES * cb * per_basis + (size_t)rb * 4 * LL.K * sizeof(cx<T>);
+      set_smem(kern, smem);
+      kern<<<LL.nbox, 256, smem, rs>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p, (const cx<T> *)tsel<T>::P(G),
+                                       (const cx<T> *)LL.d_I, cx<T>((T)G.eta.real(), (T)G.eta.imag()),
+                                       cx<T>((T)ie.real(), (T)ie.imag()), y, cx<T>((T)cj.real(), (T)cj.imag()),
+                                       cx<T>((T)cm.real(), (T)cm.imag()), part, G.rpart_off, c->rpart_nb);
+    };
+    // blocks of right-hand sides in the FP32 Krylov operator (not the true
+    // residual): split-BF16 products on the tensor cores (sie_set_param key 8)
+    const int rec_rb = (std::is_same<T, float>::value && std::is_same<TY, float>::value) ? rec_tc_block(c, R) : 0;
+    const bool rec_tc = rec_rb > 0 && !part &&
+                        op_receive_tc(c, rec_rb, LL.K, LL.nbox, R, G.d_box_start, G.d_rec_off, G.d_basis_p,
+                                      (const unsigned char *)G.d_rec_op, (const zf *)LL.d_I,
+                                      zf((float)G.eta.real(), (float)G.eta.imag()),
+                                      zf((float)ie.real(), (float)ie.imag()), zf((float)cj.real(), (float)cj.imag()),
+                                      zf((float)cm.real(), (float)cm.imag()), (zf *)y, rs);
+    if (rec_tc) return;
+    // blocks of right-hand sides RB at a time (tuned, else 4) while the box's fields fit in shared memory
+    auto fits = [&](int rb) { return STAGES * cb * per_basis + (size_t)rb * 4 * LL.K * sizeof(cx<T>) <= 227 * 1024; };
+    int rb = R == 1 ? 1 : (c->tune_rec_rb ? c->tune_rec_rb : 4);
+    while (rb > 1 && !fits(rb)) rb /= 2;
+    if (rb == 4) rec(k_disaggregate<T, 4, TY>, 4);
+    else if (rb == 2) rec(k_disaggregate<T, 2, TY>, 2);
+    else rec(k_disaggregate<T, 1, TY>, 1);
+    SIE_CHECK_LAUNCH();
+    c->launches++;
+  };
+  // small blocks in the SIMT receive: the media's receives run concurrently,
+  // each in its own branch, and a combine adds them into y in medium order
+  const int rec_rb0 = (std::is_same<T, float>::value && std::is_same<TY, float>::value) ? rec_tc_block(c, R) : 0;
+  const bool par = rec_rb0 == 0 && R <= c->rpart_cap && c->d_rpart != nullptr && c->d_rmap != nullptr;
   if (!forked) SIE_CUDA(cudaEventRecord(c->ev_fork, c->stream));
   for (size_t gi = 0; gi < c->reg.size(); ++gi) {
     RegionHost &G = c->reg[gi];
@@ -1823,8 +1901,9 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
                                                        (const cx<T> *)tsel<T>::Tr(B), (const cx<T> *)B.d_S,
                                                        (cx<T> *)B.d_I);
       } else {
-        dim3 grid((B.K + 127) / 128, B.nbox);
-        k_m2l<T><<<grid, 128, 0, st>>>(B.nbox, B.K, R, B.d_il_ptr, B.d_il_src, B.d_il_slot,
+        SIE_REQUIRE((B.K + 31) / 32 <= 65535, SIE_EINVAL, "MLFMM: too many directions for one launch");
+        dim3 grid(B.nbox, (B.K + 31) / 32);
+        k_m2l<T><<<grid, 32, 0, st>>>(B.nbox, B.K, R, B.d_il_ptr, B.d_il_src, B.d_il_slot,
                                               (const cx<T> *)tsel<T>::Tr(B), (const cx<T> *)B.d_S, (cx<T> *)B.d_I);
       }
       SIE_CHECK_LAUNCH();
@@ -1860,50 +1939,25 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
       SIE_CHECK_LAUNCH();
       c->launches++;
     }
+    if (par) receive(gi, st, (cx<T> *)c->d_rpart);
     SIE_CUDA(cudaEventRecord(c->ev_join[gi], st));
+  }
+  if (par) {
+    // every medium's rows are in d_rpart: add them into y in medium order
+    for (size_t gi = 0; gi < c->reg.size(); ++gi)
+      if (c->reg[gi].nb > 0) SIE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join[gi], 0));
+    const int64_t n = (int64_t)R * c->ne;
+    k_rec_combine<T, TY><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->ne, R, c->rpart_nb, c->d_rmap,
+                                                                            (const cx<T> *)c->d_rpart, y);
+    SIE_CHECK_LAUNCH();
+    c->launches++;
+    return;
   }
   for (size_t gi = 0; gi < c->reg.size(); ++gi) {
     RegionHost &G = c->reg[gi];
     if (G.nb == 0) continue;
     SIE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join[gi], 0));
-    LevelHost &LL = G.lev[leaf];
-    const size_t per_basis = (size_t)2 * LL.K * sizeof(cx<T>);
-    const int cb = (int)std::max<size_t>(1, std::min<size_t>(32, (32 * 1024) / per_basis));  // bases per chunk
-    // receive at the leaves
-    {
-      std::complex<double> ie = 1.0 / G.eta;
-      // per-row factors of the receive: PMCHWT weights the tangential J-row by
-      // eta~ and the M-row by 1/eta~; the other formulations fold theirs into P
-      const std::complex<double> cj = c->form == 3 ? G.eta : 1.0, cm = c->form == 3 ? 1.0 / G.eta : 1.0;
-      auto rec = [&](auto kern, int rb) {
-        const size_t smem = STAGES * cb * per_basis + (size_t)rb * 4 * LL.K * sizeof(cx<T>);
-        set_smem(kern, smem);
-        kern<<<LL.nbox, 256, smem, c->stream>>>(LL.K, c->ne, R, cb, G.d_box_start, G.d_basis_p,
-                                                (const cx<T> *)tsel<T>::P(G), (const cx<T> *)LL.d_I,
-                                                cx<T>((T)G.eta.real(), (T)G.eta.imag()),
-                                                cx<T>((T)ie.real(), (T)ie.imag()), y, cx<T>((T)cj.real(), (T)cj.imag()),
-                                                cx<T>((T)cm.real(), (T)cm.imag()));
-      };
-      // blocks of right-hand sides in the FP32 Krylov operator (not the true
-      // residual): split-BF16 products on the tensor cores (sie_set_param key 8)
-      const int rec_rb = (std::is_same<T, float>::value && std::is_same<TY, float>::value) ? rec_tc_block(c, R) : 0;
-      const bool rec_tc = rec_rb > 0 &&
-                          op_receive_tc(c, rec_rb, LL.K, LL.nbox, R, G.d_box_start, G.d_rec_off, G.d_basis_p,
-                                        (const unsigned char *)G.d_rec_op, (const zf *)LL.d_I,
-                                        zf((float)G.eta.real(), (float)G.eta.imag()),
-                                        zf((float)ie.real(), (float)ie.imag()), zf((float)cj.real(), (float)cj.imag()),
-                                        zf((float)cm.real(), (float)cm.imag()), (zf *)y, c->stream);
-      if (rec_tc) continue;
-      // blocks of right-hand sides RB at a time (tuned, else 4) while the box's fields fit in shared memory
-      auto fits = [&](int rb) { return STAGES * cb * per_basis + (size_t)rb * 4 * LL.K * sizeof(cx<T>) <= 227 * 1024; };
-      int rb = R == 1 ? 1 : (c->tune_rec_rb ? c->tune_rec_rb : 4);
-      while (rb > 1 && !fits(rb)) rb /= 2;
-      if (rb == 4) rec(k_disaggregate<T, 4, TY>, 4);
-      else if (rb == 2) rec(k_disaggregate<T, 2, TY>, 2);
-      else rec(k_disaggregate<T, 1, TY>, 1);
-      SIE_CHECK_LAUNCH();
-      c->launches++;
-    }
+    receive(gi, c->stream, nullptr);
   }
 }
 
