@@ -401,7 +401,8 @@ def main():
     if not args.no_forms:
         forms_cmp = {"jmcfie": {"ms_to_rcs": ms, "iters": st["iters"], "converged": st["converged"],
                                 "rcs_vs_mie_mean_db": mie_db["mean_abs_db"] if mie_db else None}}
-        for fname, form in (("ctf", sie.FORM_CTF), ("cnf", sie.FORM_CNF), ("pmchwt", sie.FORM_PMCHWT)):
+        for fname, form in (("ctf", sie.FORM_CTF), ("cnf", sie.FORM_CNF), ("pmchwt", sie.FORM_PMCHWT),
+                            ("ictf", sie.FORM_ICTF)):
             sf = sie.Solver(mesh, levels=LEVELS, digits=DIGITS, stream=stream, formulation=form)
             bf = sf.vec(1)
             xf = sf.vec(1)
@@ -648,7 +649,7 @@ def main():
             mesh_s = geo.coated_sphere(nu_o, nu_i)
             row = {"nu_outer": nu_o, "nu_inner": nu_i}
             for fname, form in (("jmcfie", sie.FORM_JMCFIE), ("ctf", sie.FORM_CTF), ("cnf", sie.FORM_CNF),
-                                ("pmchwt", sie.FORM_PMCHWT)):
+                                ("pmchwt", sie.FORM_PMCHWT), ("ictf", sie.FORM_ICTF)):
                 sf = sie.Solver(mesh_s, levels=LEVELS, digits=DIGITS, stream=stream, formulation=form)
                 row["unknowns"] = 2 * sf.ne
                 bf = sf.vec(1)

@@ -121,8 +121,16 @@ typedef struct {
                            eta_l - aNJ N-MFIE], M-row = sum_l s_l [aNM N-EFIE -
                            aTM eta_l T-MFIE]; JMCFIE all weights 1, CTF only T,
                            CNF only N, PMCHWT aTJ = eta~_l, aTM = 1/eta~_l, no N.
+                           4 ICTF (the improved CTF of the Fig. 6 comparison,
+                           read as: CTF with each interface's tangential
+                           equations normalised by the mean relative
+                           impedance e = (eta~_a + eta~_b)/2 of its two media
+                           instead of each medium's own), i.e. the PMCHWT rows
+                           times 1/e (J-row) and e (M-row) per basis.
                            Applies to the near field, the receive patterns and
-                           sie_plane_wave_rhs.  Other values: SIE_EINVAL. */
+                           sie_plane_wave_rhs (ICTF: also to every product of
+                           mlfmm_matvec and to the ILU(0) factors).  Other
+                           values: SIE_EINVAL. */
 } sie_fill_opts;
 
 /* Near-field fill on the GPU in FP64 (Eqs. 23-26 with singularity

@@ -236,7 +236,7 @@ def region_operators(mesh: Mesh, l, rows=None, chunk=24, outer_n=4, freq_hz=None
     return out
 
 
-FORMULATIONS = ("jmcfie", "ctf", "cnf", "pmchwt")
+FORMULATIONS = ("jmcfie", "ctf", "cnf", "pmchwt", "ictf")
 
 
 def formulation_weights(formulation, eta):
@@ -254,9 +254,26 @@ def formulation_weights(formulation, eta):
         return 1.0, 0.0, 1.0, 0.0
     if formulation == "cnf":
         return 0.0, 1.0, 0.0, 1.0
-    if formulation == "pmchwt":
+    if formulation in ("pmchwt", "ictf"):
         return eta, 0.0, 1.0 / eta, 0.0
     raise ValueError(f"unknown formulation {formulation!r}")
+
+
+def ictf_row_weights(mesh: Mesh, freq_hz=None, rows=None):
+    """Row weights of the ICTF (the improved CTF of the Fig. 6 comparison,
+    defined in a reference outside the paper's text; reading taken here): the
+    CTF weights each medium's tangential equations by that medium's own
+    impedance, the ICTF normalises both tangential equations of an interface
+    by the mean relative impedance e = (eta~_a + eta~_b) / 2 of the two media
+    it separates.  Summed over the two media with the PMCHWT weights, this is
+    J-row = (1/e) sum_l s_l T-EFIE_l, M-row = -e sum_l s_l T-MFIE_l: the
+    PMCHWT rows of each edge times (1/e, e).  Returns (wJ, wM) per row edge."""
+    k0 = k0_of(freq_hz)
+    rows = np.arange(mesh.ne) if rows is None else np.asarray(rows, np.int64)
+    eta = np.array([material(mesh.media[l], k0)[1] for l in range(mesh.nr)])
+    er = mesh.edge_regions[rows]
+    e = 0.5 * (eta[er[:, 0]] + eta[er[:, 1]])
+    return 1.0 / e, e
 
 
 def assemble(mesh: Mesh, freq_hz=None, rows=None, chunk=24, outer_n=4, formulation="jmcfie"):
@@ -293,6 +310,10 @@ def assemble_variants(mesh: Mesh, formulations=FORMULATIONS, freq_hz=None, rows=
             Z[0::2, 1::2] += (aTJ * tK + aNJ * sn * op["NL"]) / eta
             Z[1::2, 0::2] += -(aTM * tK + aNM * sn * op["NL"]) * eta
             Z[1::2, 1::2] += aTM * ss * op["L"] + aNM * nN
+    if "ictf" in out:
+        wJ, wM = ictf_row_weights(mesh, freq_hz, rows)
+        out["ictf"][0::2, :] *= wJ[:, None]
+        out["ictf"][1::2, :] *= wM[:, None]
     return out
 
 
@@ -342,4 +363,8 @@ def rhs(mesh: Mesh, inc, freq_hz=None, formulation="jmcfie"):
         bM = aTM * s * eta0 * fH - aNM * fnE
         np.add.at(out[ri], 2 * m[ok], bJ[ok])
         np.add.at(out[ri], 2 * m[ok] + 1, bM[ok])
+    if formulation == "ictf":
+        wJ, wM = ictf_row_weights(mesh, freq_hz)
+        out[:, 0::2] *= wJ[None, :]
+        out[:, 1::2] *= wM[None, :]
     return out

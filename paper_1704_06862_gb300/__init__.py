@@ -155,7 +155,7 @@ def mlfmm_setup(ctx, levels, digits=3.0):
     _check(ctx, load_library().mlfmm_setup(ctx, ctypes.byref(o)))
 
 
-FORM_JMCFIE, FORM_CTF, FORM_CNF, FORM_PMCHWT = 0, 1, 2, 3
+FORM_JMCFIE, FORM_CTF, FORM_CNF, FORM_PMCHWT, FORM_ICTF = 0, 1, 2, 3, 4
 
 
 def sie_fill_nearfield(ctx, outer_order=4, build_ilu=True, formulation=FORM_JMCFIE):

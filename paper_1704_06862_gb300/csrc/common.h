@@ -239,6 +239,8 @@ struct sie_ctx {
   int *d_tri_reg = nullptr;      // [nt][2]
   bool graphs_off = false;       // Krylov steps launched eagerly (sie_solve_opts.no_graphs)
   int form = 0;                  // sie_fill_opts.formulation
+  std::vector<std::complex<double>> rowscale;  // ICTF: per basis (J-row, M-row) weights, internal order
+  void *d_rowscale = nullptr;                  // the same on the device [ne][2]
   int *d_tri0 = nullptr;         // triangles bounding the host medium (region 0)
   int ntri0 = 0;
   void *d_ff = nullptr;          // far-field work: point positions, point currents, partial sums
@@ -315,6 +317,8 @@ void check_device_error(sie_ctx *c);
 void region_streams(sie_ctx *c);  // creates the per-medium streams and events once
 // weights (aTJ, aNJ, aTM, aNM) of medium l for the context's formulation
 void form_weights(const sie_ctx *c, int l, std::complex<double> w[4]);
+// ICTF: y[r][p][j] *= rowscale[p][j] (no-op for the other formulations)
+void op_rowscale(sie_ctx *c, zd *y, int nrhs);
 
 // ------------------------------------------------------------------ launchers (fill.cu)
 void launch_near_fill(sie_ctx *c, int region);

@@ -703,6 +703,7 @@ void launch_rhs(sie_ctx *c, const double *inc_dev, int nrhs, zd *b) {
                                      to_zd(w[1]), to_zd(w[2]), to_zd(w[3]));
   SIE_CHECK_LAUNCH();
   c->launches++;
+  op_rowscale(c, b, nrhs);  // ICTF: the excitation's rows scaled like the operator's
 }
 
 void launch_farfield(sie_ctx *c, const zd *x, int nrhs, const double *obs, int nobs, double *out, sie_prec prec) {

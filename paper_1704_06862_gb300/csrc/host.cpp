@@ -31,7 +31,8 @@ void form_weights(const sie_ctx *c, int l, std::complex<double> w[4]) {
   switch (c->form) {
     case 1: w[0] = 1.0; w[1] = 0.0; w[2] = 1.0; w[3] = 0.0; break;        // CTF
     case 2: w[0] = 0.0; w[1] = 1.0; w[2] = 0.0; w[3] = 1.0; break;        // CNF
-    case 3: w[0] = e; w[1] = 0.0; w[2] = 1.0 / e; w[3] = 0.0; break;     // PMCHWT
+    case 3:                                                              // PMCHWT
+    case 4: w[0] = e; w[1] = 0.0; w[2] = 1.0 / e; w[3] = 0.0; break;     // ICTF: PMCHWT rows, scaled per interface
     default: w[0] = w[1] = w[2] = w[3] = 1.0;                            // JMCFIE
   }
 }
@@ -835,6 +836,14 @@ static void build_ilu(sie_ctx *c) {
   const int64_t nnz = c->row_ptr[ne];
   std::vector<cd> F((size_t)nnz * 4);
   SIE_CUDA(cudaMemcpy(F.data(), c->d_near64, (size_t)nnz * 4 * sizeof(cd), cudaMemcpyDeviceToHost));
+  if (c->form == 4)  // ICTF: the near matrix of the system is D N (rows of block row i by D_i)
+    for (int i = 0; i < ne; ++i)
+      for (int e = c->row_ptr[i]; e < c->row_ptr[i + 1]; ++e) {
+        F[4 * (size_t)e] *= c->rowscale[2 * (size_t)i];
+        F[4 * (size_t)e + 1] *= c->rowscale[2 * (size_t)i];
+        F[4 * (size_t)e + 2] *= c->rowscale[2 * (size_t)i + 1];
+        F[4 * (size_t)e + 3] *= c->rowscale[2 * (size_t)i + 1];
+      }
   std::vector<int> diag(ne, -1);
   for (int i = 0; i < ne; ++i)
     for (int e = c->row_ptr[i]; e < c->row_ptr[i + 1]; ++e)
@@ -1069,7 +1078,7 @@ static void fill_all(sie_ctx *c, const sie_fill_opts *o) {
   const int ne = c->ne, nt = c->nt;
   int on = o ? o->outer_order : 4;
   c->form = o ? o->formulation : 0;
-  SIE_REQUIRE(c->form >= 0 && c->form <= 3, SIE_EINVAL, "sie_fill_nearfield: formulation must be 0..3");
+  SIE_REQUIRE(c->form >= 0 && c->form <= 4, SIE_EINVAL, "sie_fill_nearfield: formulation must be 0..4");
   SIE_REQUIRE(on >= 2 && on <= 12, SIE_EINVAL, "sie_fill_nearfield: outer_order must be in [2, 12]");
   // geometry tables, internal edge ids
   std::vector<double> tri(22 * (size_t)nt);
@@ -1198,6 +1207,20 @@ static void fill_all(sie_ctx *c, const sie_fill_opts *o) {
     for (int l = 0; l < c->nr; ++l)
       if (c->reg[l].nb > 0) launch_patterns(c, l);
   launch_to_f32(c, (const double *)c->d_near64, (float *)c->d_near32, nnz * 8);
+  if (c->form == 4) {
+    // ICTF row weights per basis (internal order): the tangential equations of
+    // an interface between media a and b normalised by the mean relative
+    // impedance eta~ = (eta~_a + eta~_b) / 2: J-row 1 / eta~, M-row eta~
+    std::vector<cd> d((size_t)2 * ne);
+    for (int p = 0; p < ne; ++p) {
+      const int t = c->tp[c->perm[p]];
+      const cd em = 0.5 * (c->etareg[c->tri_reg[2 * t]] + c->etareg[c->tri_reg[2 * t + 1]]);
+      d[2 * (size_t)p] = 1.0 / em;
+      d[2 * (size_t)p + 1] = em;
+    }
+    c->rowscale = d;
+    c->d_rowscale = dev_upload(c, d);
+  }
   SIE_CUDA(cudaStreamSynchronize(c->stream));
   if (!o || o->build_ilu) build_ilu(c);
   c->have_fill = true;

@@ -1679,6 +1679,12 @@ __global__ void __launch_bounds__(256) k_ilu_sweep_blk(int ne, int nrhs, int for
 }
 
 // ---------------------------------------------------------------- vectors
+__global__ void k_rowscale(int ne, int nrhs, const zd *__restrict__ d, zd *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nrhs * ne * 2) return;
+  y[i] = d[i % (2 * (int64_t)ne)] * y[i];
+}
+
 __global__ void k_perm_in(int ne, int nrhs, const int *__restrict__ perm, const zd *__restrict__ u, zd *__restrict__ v) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   int r = blockIdx.y;
@@ -1772,7 +1778,8 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
     std::complex<double> ie = 1.0 / G.eta;
     // per-row factors of the receive: PMCHWT weights the tangential J-row by
     // eta~ and the M-row by 1/eta~; the other formulations fold theirs into P
-    const std::complex<double> cj = c->form == 3 ? G.eta : 1.0, cm = c->form == 3 ? 1.0 / G.eta : 1.0;
+    const bool pm = c->form == 3 || c->form == 4;
+    const std::complex<double> cj = pm ? G.eta : 1.0, cm = pm ? 1.0 / G.eta : 1.0;
     auto rec = [&](auto kern, int rb) {
       const size_t smem = STAGES * cb * per_basis + (size_t)rb * 4 * LL.K * sizeof(cx<T>);
       set_smem(kern, smem);
@@ -2108,6 +2115,14 @@ void far_fork(sie_ctx *c) {
   SIE_CUDA(cudaEventRecord(c->ev_fork, c->stream));
 }
 
+void op_rowscale(sie_ctx *c, zd *y, int nrhs) {
+  if (c->form != 4 || !c->d_rowscale) return;
+  const int64_t n = (int64_t)nrhs * c->ne * 2;
+  k_rowscale<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->ne, nrhs, (const zd *)c->d_rowscale, y);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
+}
+
 void apply_matvec(sie_ctx *c, const zd *x, zd *y, int nrhs, sie_prec prec, int parts) {
   int64_t n = (int64_t)nrhs * c->ne * 2;
   if (prec == SIE_PREC_FP64) {
@@ -2134,6 +2149,7 @@ void apply_matvec(sie_ctx *c, const zd *x, zd *y, int nrhs, sie_prec prec, int p
     if (parts & 2) op_far<float>(c, xf, yf, nrhs, true);
     op_f2d(c, yf, y, n);
   }
+  op_rowscale(c, y, nrhs);  // ICTF: D (N + F) x
 }
 
 void apply_ilu(sie_ctx *c, const zd *r, zd *z, int nrhs, sie_prec prec) {

@@ -27,8 +27,8 @@ Stored: seeded x (2 columns), y = Z x, y_near = Z_near x (touching-box
 pattern), plane-wave excitation b, dense-LU solution, bistatic RCS of that
 solution at 361 angles, and the Mie series at the same angles.
 
-  sphere_c1_forms  the sphere_c1 case in the four formulations (JMCFIE, CTF,
-                 CNF, PMCHWT): per formulation the products y and y_near of
+  sphere_c1_forms  the sphere_c1 case in the five formulations (JMCFIE, CTF,
+                 CNF, PMCHWT, ICTF): per formulation the products y and y_near of
                  the seeded x, the excitation b, the LU currents and their RCS.
   mie_coated_c2  the coated-sphere Mie series alone (core 1.0 lambda0, eps 4;
                  shell 1.5 lambda0, eps 2.56; x-polarised incidence along -z),

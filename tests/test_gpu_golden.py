@@ -371,14 +371,16 @@ def forms():
 
 
 @pytest.mark.parametrize("form,fname", [(sie.FORM_JMCFIE, "jmcfie"), (sie.FORM_CTF, "ctf"),
-                                        (sie.FORM_CNF, "cnf"), (sie.FORM_PMCHWT, "pmchwt")])
+                                        (sie.FORM_CNF, "cnf"), (sie.FORM_PMCHWT, "pmchwt"),
+                                        (sie.FORM_ICTF, "ictf")])
 def test_formulation_variants(forms, form, fname):
     """Each formulation (fill weights, folded receive patterns, excitation)
     against the oracle's dense matrix of that formulation: near part exactly,
     MLFMM product to 1e-3, excitation exactly, solved currents to 1e-3 for
     JMCFIE and 5e-3 for the variants (the product's 1e-3-level error grows
-    with the condition number, 2-4 times JMCFIE's for CTF, CNF and PMCHWT on
-    this sphere), and their RCS to 0.2 dB."""
+    with the condition number, 2-4 times JMCFIE's for CTF, CNF, PMCHWT and
+    ICTF on this sphere), and their RCS to 0.2 dB.  ICTF's row weights act on
+    every product part and on the excitation."""
     d = forms
     s = sie.Solver(make_golden.CASES["sphere_c1"]["mesh"](), levels=int(d["levels"]), formulation=form)
     try:

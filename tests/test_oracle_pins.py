@@ -484,7 +484,7 @@ def test_formulation_variants():
     PMCHWT has symmetric diagonal blocks and JM = -MJ (its jump terms cancel
     across the interface); and the iteration counts order as expected for
     these integral equations (the combined forms converge faster than
-    PMCHWT)."""
+    PMCHWT; ICTF between CTF and PMCHWT, as the paper's comparison reports)."""
     m = Mesh(**geo.homogeneous_sphere(nu=5, radius=0.5, eps_r=4.0))
     obs = geo.bistatic_angles(37)
     ref = mie.sphere_bistatic(0.5, 4.0, obs[:, 0])
@@ -503,3 +503,31 @@ def test_formulation_variants():
     assert np.abs(D - D.T).max() < 1e-2 * np.abs(D).max()
     assert np.abs(B + C).max() < 1e-13 * np.abs(B).max()
     assert its["jmcfie"] < its["ctf"] < its["pmchwt"] and its["cnf"] < its["ctf"]
+    # the paper's ordering of its Fig. 6 comparison: ICTF above CTF, PMCHWT above both
+    assert its["ctf"] < its["ictf"] < its["pmchwt"]
+    # ICTF re-weights whole rows of the PMCHWT system (per interface), so its
+    # discrete solution is the PMCHWT one; a weight applied to columns, to only
+    # one of the two media or not to the excitation breaks this
+    bP = fill.rhs(m, [[0.0, 0.0, 0.0, 1.0]], formulation="pmchwt")[0]
+    bI = fill.rhs(m, [[0.0, 0.0, 0.0, 1.0]], formulation="ictf")[0]
+    xP, xI = solvers.lu_solve(P, bP), solvers.lu_solve(Zs["ictf"], bI)
+    assert np.abs(xI - xP).max() < 1e-9 * np.abs(xP).max()
+    assert np.abs(Zs["ictf"] - P).max() > 1e-2 * np.abs(P).max()   # a different system
+
+
+def test_ictf_matched_impedance():
+    """Media with eps_r = mu_r have the free-space impedance: every weight of
+    the tangential forms is 1, so CTF, ICTF and PMCHWT are the same matrix
+    and excitation (their weights differ only through the impedances)."""
+    g = geo.homogeneous_sphere(nu=3, radius=0.5, eps_r=2.0)
+    media = np.array(g["media"], np.float64)
+    media[1] = [2.0, 0.0, 2.0, 0.0]
+    g["media"] = media
+    m = Mesh(**g)
+    Zs = fill.assemble_variants(m, ("ctf", "pmchwt", "ictf"))
+    scale = np.abs(Zs["pmchwt"]).max()
+    assert np.abs(Zs["ictf"] - Zs["pmchwt"]).max() < 1e-13 * scale
+    assert np.abs(Zs["ctf"] - Zs["pmchwt"]).max() < 1e-13 * scale
+    inc = [[0.3, 0.2, 0.0, 1.0]]
+    bP, bI = fill.rhs(m, inc, formulation="pmchwt"), fill.rhs(m, inc, formulation="ictf")
+    assert np.abs(bI - bP).max() < 1e-14 * np.abs(bP).max()
