@@ -338,17 +338,6 @@ __global__ void __launch_bounds__(256) k_aggregate(int K, int ne, int nrhs, int 
 // Register tiles: a G task owns the columns jp and jp + Np/2 of one theta row;
 // an H task owns the pair (jp, jp + Np/2), whose phi + pi partners are each
 // other, for two parent theta rows, so every shared-memory load feeds several FMAs.
-// Exact separable interpolation of one child's pattern to the parent
-// sampling, shifted to the parent centre (upward pass).  One CTA per (child,
-// right-hand side), JM of the sources J, M per pass.  The pattern is carried
-// as three Cartesian components: (theta, phi) -> xyz at the child directions
-// (A), trigonometric interpolation in phi (G = A Phi^T), the folded Lagrange
-// step in theta (H = Th+ G + Th- G(phi + pi)), xyz -> (theta, phi) at the
-// parent directions, times the shift exp(j k khat.(c_child - c_parent)).
-// Output Y[child][J|M][theta|phi][r][k_parent]; k_up_sum adds the children.
-// Register tiles: a G task owns the columns jp and jp + Np/2 of one theta row;
-// an H task owns the pair (jp, jp + Np/2), whose phi + pi partners are each
-// other, for two parent theta rows, so every shared-memory load feeds several FMAs.
 template <typename T, int JM>
 __global__ void __launch_bounds__(256) k_interp_up(int Kc, int Lc, int Kp, int Lp, int nrhs,
                                                   const int *__restrict__ oct, const T *__restrict__ tpc,
@@ -569,20 +558,26 @@ __global__ void k_up_sum(int Kp, int nrhs, const int *__restrict__ ch_ptr, const
   int b = blockIdx.y;
   if (t >= Kp) return;
   const int s0 = ch_ptr[b], s1 = ch_ptr[b + 1];
-  for (int qr = 0; qr < 4 * nrhs; ++qr) {
-    cx<T> acc;
-    for (int s = s0; s < s1; ++s) acc += Y[((size_t)ch_idx[s] * 4 * nrhs + qr) * Kp + t];
-    Sp[((size_t)b * 4 * nrhs + qr) * Kp + t] = acc;
+  const size_t cs = (size_t)nrhs * Kp;  // component stride
+  for (int r = 0; r < nrhs; ++r) {
+    // the four components of a child loaded together, children in order
+    cx<T> a0, a1, a2, a3;
+#pragma unroll 4
+    for (int s = s0; s < s1; ++s) {
+      const cx<T> *y = Y + ((size_t)ch_idx[s] * 4 * nrhs + r) * Kp + t;
+      a0 += y[0];
+      a1 += y[cs];
+      a2 += y[2 * cs];
+      a3 += y[3 * cs];
+    }
+    cx<T> *o = Sp + ((size_t)b * 4 * nrhs + r) * Kp + t;
+    o[0] = a0;
+    o[cs] = a1;
+    o[2 * cs] = a2;
+    o[3 * cs] = a3;
   }
 }
 
-// Exact transpose of k_interp_up (anterpolation, downward pass), with the
-// receive shift exp(-j k khat.(c_child - c_parent)): one CTA per (child box,
-// right-hand side), I_child += Interp^T [dn (.) I_parent].  Quadrature weights
-// are folded into the translators, so the adjoint is the plain transpose.
-// Register tiles as in k_interp_up: a theta-step task owns the column pair
-// (j, j + Np/2) for two child theta rows; a phi-step task owns the child
-// columns jc and jc + Nc/2 of one theta row.
 // Exact transpose of k_interp_up (anterpolation, downward pass), with the
 // receive shift exp(-j k khat.(c_child - c_parent)): one CTA per (child box,
 // right-hand side), I_child += Interp^T [dn (.) I_parent].  Quadrature weights
