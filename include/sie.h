@@ -360,9 +360,12 @@ sie_status sie_device_status(sie_ctx *ctx);
  *      of right-hand sides): right-hand sides per pass, -1 (default: from 16
  *      right-hand sides on, 16, 32 or 64 by the block size), 0 (the SIMT
  *      receive), 16, 32 or 64.
- * Keys 2-8 are tile shapes: results agree to rounding (the tensor-core
- * aggregation and receive to their FP32-level split operands), speed
- * differs.
+ *   9  dense layers of the learned preconditioner with BF16 activations and
+ *      weights (its forward pass): 1 (default) on the tensor cores
+ *      (tcgen05, FP32 accumulation in tensor memory), 0 on the SIMT tiles.
+ * Keys 2-9 are tile shapes: results agree to rounding (the tensor-core
+ * aggregation and receive to their FP32-level split operands, the network's
+ * layers to the order of their FP32 sums), speed differs.
  * Errors: SIE_EINVAL for an unknown key or a value out of range. */
 sie_status sie_set_param(sie_ctx *ctx, int32_t key, int64_t value);
 

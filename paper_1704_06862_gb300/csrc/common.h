@@ -298,6 +298,8 @@ struct sie_ctx {
   // tensor-core leaf receive: right-hand sides per pass (0: the SIMT receive,
   // -1: from 16 right-hand sides on, by the block size)
   int rec_tc_rb = -1;
+  // learned-preconditioner layers X W^T on the tensor cores (1) or the SIMT tiles (0)
+  int nn_tc = 1;
 };
 
 // ------------------------------------------------------------------ host helpers (host.cpp)
@@ -347,6 +349,10 @@ bool op_aggregate_tc(sie_ctx *c, int rb, int K, int nbox, int max_leaf, int nrhs
                      const zf *x, zf *S, cudaStream_t st);
 void build_agg_operand(sie_ctx *c, RegionHost &R, int K);  // at setup, after the FP32 patterns
 // tensor-core leaf receive (tensor.cu): adds the medium's far field into the FP32 product y
+// one dense layer act(X W^T + bias) of the learned preconditioner on the
+// tensor cores (BF16 X [M][K], W [N][K]); false when the shape is not covered
+bool nn_dense_tc(sie_ctx *c, int M, int N, int K, const void *X, const void *W, const float *bias, int relu,
+                 float *Cf, void *Cb);
 bool op_receive_tc(sie_ctx *c, int rb, int K, int nbox, int nrhs, const int *box_start, const int64_t *box_off,
                    const int *basis_p, const unsigned char *Aop, const zf *I, zf eta, zf ieta, zf cJ, zf cM, zf *y,
                    cudaStream_t st);

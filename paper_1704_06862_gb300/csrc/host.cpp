@@ -1522,6 +1522,11 @@ extern "C" sie_status sie_set_param(sie_ctx *c, int32_t key, int64_t value) {
         c->rec_tc_rb = (int)value;
         graphs_free(c);
         break;
+      case 9:
+        SIE_REQUIRE(value == 0 || value == 1, SIE_EINVAL, "sie_set_param: learned-preconditioner layers must be 0 or 1");
+        c->nn_tc = (int)value;
+        graphs_free(c);
+        break;
       default:
         throw SieError{SIE_EINVAL, "sie_set_param: unknown key"};
     }

@@ -13,6 +13,8 @@
 #include <cmath>
 #include <random>
 
+#include <type_traits>
+
 #include "common.h"
 
 namespace {
@@ -308,6 +310,11 @@ static void nn_alloc(sie_ctx *c, int cap) {
 template <typename TA, typename TB>
 static void dense(sie_ctx *c, int M, int N, int K, const TA *A, int lda, int ta, const TB *B, int ldb, int tb,
                   const float *bias, int relu, float *Cf, bf16 *Cb) {
+  // the forward layers (BF16 activations times BF16 weights, both K-major) on
+  // the tensor cores; the gradient products (FP32 factors) on the SIMT tiles
+  if (std::is_same<TA, bf16>::value && std::is_same<TB, bf16>::value && !ta && tb && lda == K && ldb == K &&
+      nn_dense_tc(c, M, N, K, A, B, bias, relu, Cf, Cb))
+    return;
   dim3 grid((N + 63) / 64, (M + 63) / 64);
   k_dense<TA, TB><<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, ta, B, ldb, tb, bias, relu, Cf, Cb);
   SIE_CHECK_LAUNCH();

@@ -42,6 +42,31 @@ def test_gradient_matches_oracle(solver):
     assert np.allclose(sie.nnprec_params(solver.ctx), theta)
 
 
+def test_tensor_core_layers_match_simt(solver):
+    """The forward layers (BF16 activations x BF16 weights, FP32 accumulation)
+    on the tensor cores against the SIMT tiles: the same products summed in
+    another order, on 300 samples (two full 128-row tiles and a ragged one)."""
+    import time
+    rng = np.random.default_rng(5)
+    theta = (rng.standard_normal(sie.NN_PARAMS) * 0.05).astype(np.float32)
+    sie.nnprec_params(solver.ctx, theta)
+    X = rng.standard_normal((300, 128)).astype(np.float32)
+    T = rng.standard_normal((300, 128)).astype(np.float32)
+    try:
+        out = {}
+        for key in (0, 1):
+            sie.sie_set_param(solver.ctx, 9, key)
+            t0 = time.perf_counter()
+            out[key] = sie.nnprec_loss_grad(solver.ctx, X, T)
+            print(f"layers {'tensor cores' if key else 'SIMT'}: {1e3 * (time.perf_counter() - t0):.2f} ms")
+        (l0, g0), (l1, g1) = out[0], out[1]
+        assert np.isfinite(l1) and np.all(np.isfinite(g1))
+        assert abs(l1 - l0) <= 1e-5 * l0
+        assert np.linalg.norm(g1 - g0) <= 1e-3 * np.linalg.norm(g0)
+    finally:
+        sie.sie_set_param(solver.ctx, 9, 1)
+
+
 def test_training_and_solve_keep_the_answer(solver):
     s = solver
     rng = np.random.default_rng(2017)
