@@ -1,6 +1,8 @@
 """Learned preconditioner on the GPU: gradients against the oracle network,
-and training on solver-generated pairs followed by a solve whose converged
-answer must not change (only the iteration count may).
+the tensor-core layers against the SIMT ones, and training on
+solver-generated pairs followed by solves whose converged answer must not
+change; the network is used only where its gate found fewer iterations on a
+held-out incidence (re-checked here), otherwise the solve is plain ILU(0).
 
 Tolerances: loss 1e-4 and gradient 2e-2 relative L2 (the device stores
 activations in BF16 after FP32 accumulation; the oracle rounds the same
@@ -89,4 +91,18 @@ def test_training_and_solve_keep_the_answer(solver):
         assert out[0]["converged"]
     print(f"ILU(0) iters {res[1][0]}, ILU(0)+network iters {res[2][0]}; training {st}")
     assert res[2][1] < 1e-3 and res[1][1] < 1e-3
-    assert res[2][0] <= 1.25 * res[1][0] + 2
+    if st["enabled"]:
+        # the gate's promise, re-checked: on the held-out incidence (the last
+        # training one) at 1e-4 the network saves iterations
+        assert st["judge_iters_nn"] < st["judge_iters_ilu"]
+        bh = torch.zeros_like(b)
+        sie.sie_plane_wave_rhs(s.ctx, [list(train[-1])], bh)
+        its = {}
+        for pc in (1, 2):
+            x = torch.zeros_like(bh)
+            its[pc] = sie.gmres_solve(s.ctx, bh, x, 1, restart=50, max_iters=1000, tol=1e-4,
+                                      prec=sie.SIE_PREC_MIXED, precond=pc)[0]["iters"]
+        assert its[2] < its[1]
+    else:
+        # gated off (no gain found): the solve is plain ILU(0), step for step
+        assert res[2][0] == res[1][0]
