@@ -23,16 +23,20 @@ typedef std::complex<double> cd;
 inline double sqrt_nonneg(double v) { return std::isnan(v) ? v : std::sqrt(v > 0.0 ? v : 0.0); }
 
 // Two-stage dot products h[i][r] = sum_n conj(V_i[r][n]) w[r][n], i < nvec.
-// Stage 1: one warp per (vector i, chunk of MD_CH elements, rhs r), lanes over
-// the chunk with many loads in flight, one partial per warp (no block-level
-// synchronisation); stage 2 adds the partials in chunk order.  With a gate,
+// Stage 1: one warp per (vector i, chunk of ch elements, rhs r), lanes over
+// the chunk with four independent accumulators (the FP64 multiply-adds of
+// this GPU are few and long: independent chains keep them busy), one partial
+// per warp (no block-level synchronisation); stage 2 adds the partials in
+// chunk order.  Chunks of MD_CH elements for several vectors, MD_CH1 for a
+// single one (a norm), so that either fills the GPU.  With a gate,
 // right-hand sides whose gate is 0 get zero partials.
-constexpr int MD_CH = 1024;
+constexpr int MD_CH = 1024, MD_CH1 = 256;
 // Gram-Schmidt kernels chained by programmatic dependent launch (each waits
 // for its predecessor first thing: stream order, launch latency hidden)
 constexpr bool GS_CHAINED = true;
-__global__ void __launch_bounds__(256) k_mdot_part(int n, int nrhs, int nvec, int nblk, const zd *__restrict__ V,
-                                                  size_t vstride, const zd *__restrict__ w, zd *__restrict__ part,
+__global__ void __launch_bounds__(256) k_mdot_part(int n, int nrhs, int nvec, int nblk, int ch,
+                                                  const zd *__restrict__ V, size_t vstride,
+                                                  const zd *__restrict__ w, zd *__restrict__ part,
                                                   const int *__restrict__ gate) {
   pdl_wait();
   pdl_release();
@@ -44,9 +48,18 @@ __global__ void __launch_bounds__(256) k_mdot_part(int n, int nrhs, int nvec, in
   if (!gate || gate[r]) {
     const zd *a = V + (size_t)i * vstride + (size_t)r * n;
     const zd *x = w + (size_t)r * n;
-    const int t1 = min(n, (blk + 1) * MD_CH);
-#pragma unroll 8
-    for (int t = blk * MD_CH + lane; t < t1; t += 32) acc = cfma(conj(a[t]), x[t], acc);
+    const int t1 = min(n, (blk + 1) * ch);
+    zd a1, a2, a3;
+    int t = blk * ch + lane;
+#pragma unroll 2
+    for (; t + 96 < t1; t += 128) {
+      acc = cfma(conj(a[t]), x[t], acc);
+      a1 = cfma(conj(a[t + 32]), x[t + 32], a1);
+      a2 = cfma(conj(a[t + 64]), x[t + 64], a2);
+      a3 = cfma(conj(a[t + 96]), x[t + 96], a3);
+    }
+    for (; t < t1; t += 32) acc = cfma(conj(a[t]), x[t], acc);
+    acc = (acc + a1) + (a2 + a3);
     for (int d = 16; d > 0; d >>= 1) {
       acc.re += __shfl_down_sync(0xffffffffu, acc.re, d);
       acc.im += __shfl_down_sync(0xffffffffu, acc.im, d);
@@ -97,10 +110,19 @@ __global__ void k_orth(int n, int nrhs, int j1, const zd *__restrict__ V, size_t
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int r = blockIdx.y;
   if (t >= n || (gate && !gate[r])) return;
-  zd acc = w[(size_t)r * n + t];
-#pragma unroll 8
-  for (int i = 0; i < j1; ++i) acc -= V[(size_t)i * vstride + (size_t)r * n + t] * h[(size_t)i * nrhs + r];
-  w[(size_t)r * n + t] = acc;
+  // four independent accumulators over the vectors (see k_mdot_part)
+  const zd *v = V + (size_t)r * n + t;
+  zd a0, a1, a2, a3;
+  int i = 0;
+#pragma unroll 2
+  for (; i + 3 < j1; i += 4) {
+    a0 += v[(size_t)i * vstride] * h[(size_t)i * nrhs + r];
+    a1 += v[(size_t)(i + 1) * vstride] * h[(size_t)(i + 1) * nrhs + r];
+    a2 += v[(size_t)(i + 2) * vstride] * h[(size_t)(i + 2) * nrhs + r];
+    a3 += v[(size_t)(i + 3) * vstride] * h[(size_t)(i + 3) * nrhs + r];
+  }
+  for (; i < j1; ++i) a0 += v[(size_t)i * vstride] * h[(size_t)i * nrhs + r];
+  w[(size_t)r * n + t] = w[(size_t)r * n + t] - ((a0 + a1) + (a2 + a3));
 }
 
 // out[r] = a[r] * s[r]
@@ -173,10 +195,13 @@ struct Gm {
   }
   // h[i][r] = <V_i[r], w[r]> for i < nvec
   void mdot(const zd *V, size_t vstride, int nvec, const zd *w, zd *d_h, const int *gate = nullptr) {
-    SIE_CUDA(launch_chained(GS_CHAINED, k_mdot_part, dim3((nvec * nblk + 7) / 8, R), dim3(256), 0, c->stream, n, R, nvec,
-                            nblk, V, vstride, w, part, gate));
+    // a single vector (a norm) in finer chunks; the partial buffer holds
+    // 4 nvec_max R chunks of MD_CH elements, enough for either
+    const int ch = nvec == 1 ? MD_CH1 : MD_CH, nb = std::max(1, (n + ch - 1) / ch);
+    SIE_CUDA(launch_chained(GS_CHAINED, k_mdot_part, dim3((nvec * nb + 7) / 8, R), dim3(256), 0, c->stream, n, R, nvec,
+                            nb, ch, V, vstride, w, part, gate));
     launch_check();
-    SIE_CUDA(launch_chained(GS_CHAINED, k_mdot_sum, dim3(nvec, R), dim3(256), 0, c->stream, R, nblk, (const zd *)part,
+    SIE_CUDA(launch_chained(GS_CHAINED, k_mdot_sum, dim3(nvec, R), dim3(256), 0, c->stream, R, nb, (const zd *)part,
                             d_h));
     launch_check();
   }
@@ -305,7 +330,7 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
     c->gm_hpin = nullptr;
     SIE_CUDA(cudaMallocHost(&c->gm_hpin, 3 * (size_t)(m + 2) * R * sizeof(zd)));
     if (!c->gm_ev) SIE_CUDA(cudaEventCreateWithFlags(&c->gm_ev, cudaEventDisableTiming));
-    c->gm_part = dev_alloc(c, (size_t)(m + 2) * R * ((n + MD_CH - 1) / MD_CH) * sizeof(zd));
+    c->gm_part = dev_alloc(c, (size_t)std::max(m + 2, 4) * R * ((n + MD_CH - 1) / MD_CH) * sizeof(zd));
     c->gm_gate = dev_alloc(c, (size_t)R * sizeof(int));
     c->gm_m = m;
     c->gm_R = R;
