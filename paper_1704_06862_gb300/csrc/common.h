@@ -280,7 +280,11 @@ struct sie_ctx {
   void *gm_V = nullptr, *gm_Z = nullptr, *gm_b = nullptr, *gm_x = nullptr, *gm_w = nullptr;
   void *gm_h = nullptr, *gm_s = nullptr, *gm_part = nullptr, *gm_act = nullptr, *gm_gate = nullptr;
   void *gm_hpin = nullptr;        // pinned host mirror of gm_h (one copy per Krylov step)
-  cudaEvent_t gm_ev = nullptr;    // marks that copy
+  cudaEvent_t gm_ev = nullptr;    // marks that copy (made on gm_cs)
+  cudaStream_t gm_cs = nullptr;   // side stream of the copy
+  cudaEvent_t gm_ev0 = nullptr;   // the step's Gram-Schmidt done (gm_cs waits on it)
+  void *gm_npart = nullptr;       // per-CTA partial norms of the fused update
+  void *gm_cnt = nullptr;         // completion counter of the fused update (self-resetting)
   // bounded device-side waits: polls before a wait gives up, and the flag a
   // kernel sets when one did (read and cleared by sie_device_status and the solvers)
   int wait_limit = 1 << 21;

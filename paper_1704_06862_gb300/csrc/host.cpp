@@ -197,6 +197,8 @@ extern "C" void sie_destroy(sie_ctx *c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->gm_hpin) cudaFreeHost(c->gm_hpin);
   if (c->gm_ev) cudaEventDestroy(c->gm_ev);
+  if (c->gm_ev0) cudaEventDestroy(c->gm_ev0);
+  if (c->gm_cs) cudaStreamDestroy(c->gm_cs);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -68,23 +68,6 @@ __global__ void __launch_bounds__(256) k_mdot_part(int n, int nrhs, int nvec, in
   if (lane == 0) part[((size_t)i * nrhs + r) * nblk + blk] = acc;
 }
 
-// Selective second Gram-Schmidt pass (Daniel-Gragg-Kaufman-Stewart test):
-// after the first pass w' = w - V h, |w|^2 = |w'|^2 + |h|^2, and the pass is
-// repeated only when |w'| < |w| / sqrt(2), i.e. |w'|^2 < |h|^2.
-__global__ void k_reorth_gate(int nrhs, int nvec, const zd *__restrict__ h, const zd *__restrict__ nn1,
-                              int *__restrict__ gate) {
-  pdl_wait();
-  pdl_release();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs) return;
-  double hh = 0.0;
-  for (int i = 0; i < nvec; ++i) {
-    const zd v = h[(size_t)i * nrhs + r];
-    hh += v.re * v.re + v.im * v.im;
-  }
-  gate[r] = nn1[r].re < hh ? 1 : 0;
-}
-
 __global__ void k_mdot_sum(int nrhs, int nblk, const zd *__restrict__ part, zd *__restrict__ h) {
   pdl_wait();
   pdl_release();
@@ -102,27 +85,77 @@ __global__ void k_mdot_sum(int nrhs, int nblk, const zd *__restrict__ part, zd *
   if (threadIdx.x == 0) h[(size_t)i * nrhs + r] = red[0];
 }
 
-// w[r] -= sum_{i<=j} V_i[r] h[i][r]
-__global__ void k_orth(int n, int nrhs, int j1, const zd *__restrict__ V, size_t vstride, const zd *__restrict__ h,
-                       zd *__restrict__ w, const int *__restrict__ gate) {
+// One classical Gram-Schmidt update fused with the norm that follows it:
+//   w[r] -= sum_{i<j1} V_i[r] h[i][r]   (unless gate_in is given and gate_in[r] == 0),
+//   nn[r] = |w[r]|^2,
+// and with gate_out the selective second-pass test (Daniel-Gragg-Kaufman-
+// Stewart): after the first pass |w|^2 = |w'|^2 + |h|^2, and the pass is
+// repeated only when |w'| < |w| / sqrt(2), i.e. |w'|^2 < |h|^2.  Each CTA adds its squares in a fixed order and writes one
+// partial; the last CTA to finish (a counter, reset by that CTA) adds the
+// partials in CTA order, one warp per right-hand side: deterministic, and one
+// launch instead of three.
+__global__ void __launch_bounds__(256) k_orth_norm(int n, int nrhs, int j1, const zd *__restrict__ V, size_t vstride,
+                                                  const zd *__restrict__ h, zd *__restrict__ w,
+                                                  const int *__restrict__ gate_in, double *__restrict__ npart,
+                                                  unsigned *__restrict__ cnt, zd *__restrict__ nn,
+                                                  int *__restrict__ gate_out) {
   pdl_wait();
   pdl_release();
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int r = blockIdx.y;
-  if (t >= n || (gate && !gate[r])) return;
-  // four independent accumulators over the vectors (see k_mdot_part)
-  const zd *v = V + (size_t)r * n + t;
-  zd a0, a1, a2, a3;
-  int i = 0;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double sq = 0.0;
+  if (t < n) {
+    zd x = w[(size_t)r * n + t];
+    if (!gate_in || gate_in[r]) {
+      const zd *v = V + (size_t)r * n + t;
+      zd a0, a1, a2, a3;
+      int i = 0;
 #pragma unroll 2
-  for (; i + 3 < j1; i += 4) {
-    a0 += v[(size_t)i * vstride] * h[(size_t)i * nrhs + r];
-    a1 += v[(size_t)(i + 1) * vstride] * h[(size_t)(i + 1) * nrhs + r];
-    a2 += v[(size_t)(i + 2) * vstride] * h[(size_t)(i + 2) * nrhs + r];
-    a3 += v[(size_t)(i + 3) * vstride] * h[(size_t)(i + 3) * nrhs + r];
+      for (; i + 3 < j1; i += 4) {
+        a0 += v[(size_t)i * vstride] * h[(size_t)i * nrhs + r];
+        a1 += v[(size_t)(i + 1) * vstride] * h[(size_t)(i + 1) * nrhs + r];
+        a2 += v[(size_t)(i + 2) * vstride] * h[(size_t)(i + 2) * nrhs + r];
+        a3 += v[(size_t)(i + 3) * vstride] * h[(size_t)(i + 3) * nrhs + r];
+      }
+      for (; i < j1; ++i) a0 += v[(size_t)i * vstride] * h[(size_t)i * nrhs + r];
+      x = x - ((a0 + a1) + (a2 + a3));
+      w[(size_t)r * n + t] = x;
+    }
+    sq = x.re * x.re + x.im * x.im;
   }
-  for (; i < j1; ++i) a0 += v[(size_t)i * vstride] * h[(size_t)i * nrhs + r];
-  w[(size_t)r * n + t] = w[(size_t)r * n + t] - ((a0 + a1) + (a2 + a3));
+  for (int d = 16; d > 0; d >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, d);
+  __shared__ double red[8];
+  __shared__ int s_last;
+  if (lane == 0) red[warp] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) b += red[k];
+    npart[(size_t)r * gridDim.x + blockIdx.x] = b;
+    __threadfence();
+    const unsigned prev = atomicAdd(cnt, 1u);
+    s_last = prev == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int rr = warp; rr < nrhs; rr += (int)(blockDim.x >> 5)) {
+    double a = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) a += __ldcg(npart + (size_t)rr * gridDim.x + b);
+    for (int d = 16; d > 0; d >>= 1) a += __shfl_down_sync(0xffffffffu, a, d);
+    if (lane == 0) {
+      nn[rr] = zd(a, 0.0);
+      if (gate_out) {
+        double hh = 0.0;
+        for (int i = 0; i < j1; ++i) {
+          const zd v = h[(size_t)i * nrhs + rr];
+          hh += v.re * v.re + v.im * v.im;
+        }
+        gate_out[rr] = a < hh ? 1 : 0;
+      }
+    }
+  }
+  if (threadIdx.x == 0) *cnt = 0u;
 }
 
 // out[r] = a[r] * s[r]
@@ -332,6 +365,11 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
     if (!c->gm_ev) SIE_CUDA(cudaEventCreateWithFlags(&c->gm_ev, cudaEventDisableTiming));
     c->gm_part = dev_alloc(c, (size_t)std::max(m + 2, 4) * R * ((n + MD_CH - 1) / MD_CH) * sizeof(zd));
     c->gm_gate = dev_alloc(c, (size_t)R * sizeof(int));
+    c->gm_npart = dev_alloc(c, (size_t)R * ((n + 255) / 256) * sizeof(double));
+    c->gm_cnt = dev_alloc(c, 256);
+    SIE_CUDA(cudaMemsetAsync(c->gm_cnt, 0, 256, c->stream));
+    if (!c->gm_cs) SIE_CUDA(cudaStreamCreateWithFlags(&c->gm_cs, cudaStreamNonBlocking));
+    if (!c->gm_ev0) SIE_CUDA(cudaEventCreateWithFlags(&c->gm_ev0, cudaEventDisableTiming));
     c->gm_m = m;
     c->gm_R = R;
     c->work_gen++;
@@ -422,25 +460,29 @@ sie_status run_gmres_internal(sie_ctx *c, const zd *b, zd *x, int R, int m, int 
       // classical Gram-Schmidt with a selective second pass, and the normalised
       // next vector, all on the device
       int *gate = (int *)c->gm_gate;
+      double *npart = (double *)c->gm_npart;
+      unsigned *cnt = (unsigned *)c->gm_cnt;
+      // the previous step's Hessenberg copy (on the side stream) has read d_h
+      if (j > 0) SIE_CUDA(cudaStreamWaitEvent(c->stream, c->gm_ev, 0));
       g.mdot(V, vs, j + 1, w, dh1);
-      SIE_CUDA(launch_chained(GS_CHAINED, k_orth, gv, dim3(256), 0, c->stream, n, R, j + 1, (const zd *)V, vs,
-                              (const zd *)dh1, w, (const int *)nullptr));
-      g.launch_check();
-      g.mdot(w, 0, 1, w, dnn);
-      SIE_CUDA(launch_chained(GS_CHAINED, k_reorth_gate, dim3((R + 127) / 128), dim3(128), 0, c->stream, R, j + 1,
-                              (const zd *)dh1, (const zd *)dnn, gate));
+      // first pass's update, |w'|^2 and the second-pass test
+      SIE_CUDA(launch_chained(GS_CHAINED, k_orth_norm, gv, dim3(256), 0, c->stream, n, R, j + 1, (const zd *)V, vs,
+                              (const zd *)dh1, w, (const int *)nullptr, npart, cnt, dnn, gate));
       g.launch_check();
       g.mdot(V, vs, j + 1, w, dh2, gate);
-      SIE_CUDA(launch_chained(GS_CHAINED, k_orth, gv, dim3(256), 0, c->stream, n, R, j + 1, (const zd *)V, vs,
-                              (const zd *)dh2, w, (const int *)gate));
+      SIE_CUDA(launch_chained(GS_CHAINED, k_orth_norm, gv, dim3(256), 0, c->stream, n, R, j + 1, (const zd *)V, vs,
+                              (const zd *)dh2, w, (const int *)gate, npart, cnt, dnn, (int *)nullptr));
       g.launch_check();
-      g.mdot(w, 0, 1, w, dnn);
       SIE_CUDA(launch_chained(GS_CHAINED, k_scale_norm, gv, dim3(256), 0, c->stream, n, (const zd *)w, (const zd *)dnn,
                               (const zd *)c->gm_act, V + (size_t)(j + 1) * vs));
       g.launch_check();
+      // the Hessenberg column goes to the host on a side stream, so that the
+      // next step does not wait for the copy
+      SIE_CUDA(cudaEventRecord(c->gm_ev0, c->stream));
+      SIE_CUDA(cudaStreamWaitEvent(c->gm_cs, c->gm_ev0, 0));
       SIE_CUDA(cudaMemcpyAsync(c->gm_hpin, d_h, 3 * (size_t)(m + 2) * R * sizeof(zd), cudaMemcpyDeviceToHost,
-                               c->stream));
-      SIE_CUDA(cudaEventRecord(c->gm_ev, c->stream));
+                               c->gm_cs));
+      SIE_CUDA(cudaEventRecord(c->gm_ev, c->gm_cs));
       // the next step goes to the GPU before the host looks at the Hessenberg column:
       // if the cycle stops here, its result is simply not used
       if (j + 1 < m) run_step(j + 1);
