@@ -83,27 +83,37 @@ __global__ void k_chunk_scatter(int nchunk, const int *__restrict__ cstart, cons
 // C[M][N] = act(sum_k A(i,k) B(k,j) + bias[j]) with FP32 accumulation.
 // A(i,k) = A[ta ? k*lda + i : i*lda + k], B(k,j) = B[tb ? j*ldb + k : k*ldb + j].
 // Writes C as FP32 (Cf) and/or BF16 (Cb); relu != 0 applies max(0, .).
+// Split over K (gridDim.z > 1, kch inner indices per slice): slice z adds
+// k in [z kch, min(K, (z + 1) kch)) and writes its raw partial tile to
+// Cf + z M N (no bias or activation); k_splitk_sum adds the slices in order.
 template <typename TA, typename TB>
-__global__ void k_dense(int M, int N, int K, const TA *__restrict__ A, int lda, int ta, const TB *__restrict__ B,
-                        int ldb, int tb, const float *__restrict__ bias, int relu, float *__restrict__ Cf,
-                        bf16 *__restrict__ Cb) {
+__global__ void k_dense(int M, int N, int K, int kch, const TA *__restrict__ A, int lda, int ta,
+                        const TB *__restrict__ B, int ldb, int tb, const float *__restrict__ bias, int relu,
+                        float *__restrict__ Cf, bf16 *__restrict__ Cb) {
   __shared__ float As[16][65];
   __shared__ float Bs[16][65];
   int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int kb = blockIdx.z * kch, ke = min(K, kb + kch);
+  if (gridDim.z > 1) {
+    Cf += (size_t)blockIdx.z * M * N;
+    bias = nullptr;
+    relu = 0;
+    Cb = nullptr;
+  }
   float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  for (int k0 = kb; k0 < ke; k0 += 16) {
     for (int t = threadIdx.x; t < 16 * 64; t += 256) {
       int kk, mm;
       if (ta) { mm = t % 64; kk = t / 64; } else { kk = t % 16; mm = t / 16; }
       int gi = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gi < M && gk < K) ? ld(A, ta ? (size_t)gk * lda + gi : (size_t)gi * lda + gk) : 0.f;
+      As[kk][mm] = (gi < M && gk < ke) ? ld(A, ta ? (size_t)gk * lda + gi : (size_t)gi * lda + gk) : 0.f;
     }
     for (int t = threadIdx.x; t < 16 * 64; t += 256) {
       int kk, nn;
       if (tb) { kk = t % 16; nn = t / 16; } else { nn = t % 64; kk = t / 64; }
       int gj = n0 + nn, gk = k0 + kk;
-      Bs[kk][nn] = (gj < N && gk < K) ? ld(B, tb ? (size_t)gj * ldb + gk : (size_t)gk * ldb + gj) : 0.f;
+      Bs[kk][nn] = (gj < N && gk < ke) ? ld(B, tb ? (size_t)gj * ldb + gk : (size_t)gk * ldb + gj) : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -132,6 +142,19 @@ __global__ void k_dense(int M, int N, int K, const TA *__restrict__ A, int lda, 
         if (Cb) Cb[(size_t)gi * N + gj] = __float2bfloat16(v);
       }
     }
+}
+
+// C = act(sum_z P[z] + bias), the slices of a split-K product added in order
+__global__ void k_splitk_sum(int64_t mn, int N, int S, const float *__restrict__ P, const float *__restrict__ bias,
+                             int relu, float *__restrict__ Cf, bf16 *__restrict__ Cb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= mn) return;
+  float v = 0.f;
+  for (int z = 0; z < S; ++z) v += P[(size_t)z * mn + i];
+  if (bias) v += bias[i % N];
+  if (relu) v = fmaxf(v, 0.f);
+  if (Cf) Cf[i] = v;
+  if (Cb) Cb[i] = __float2bfloat16(v);
 }
 
 // dH = dY .* (H > 0) in place (H stored in BF16)
@@ -257,6 +280,8 @@ struct NnState {
   int nchunk = 0;
   int *d_cstart = nullptr, *d_clen = nullptr;
   float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;  // FP32 master, Adam moments, gradient
+  float *splitk = nullptr;  // partial tiles of split-K products
+  size_t splitk_cap = 0;
   bf16 *wb = nullptr;                                             // BF16 weights
   int cap = 0;                                                    // activation capacity (samples)
   bf16 *X = nullptr, *H1 = nullptr, *H2 = nullptr;
@@ -316,7 +341,29 @@ static void dense(sie_ctx *c, int M, int N, int K, const TA *A, int lda, int ta,
       nn_dense_tc(c, M, N, K, A, B, bias, relu, Cf, Cb))
     return;
   dim3 grid((N + 63) / 64, (M + 63) / 64);
-  k_dense<TA, TB><<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, ta, B, ldb, tb, bias, relu, Cf, Cb);
+  // a long inner dimension on few output tiles (the weight gradients, summed
+  // over the samples): split K so that the GPU fills, slices added in order
+  const int tiles = (int)(grid.x * grid.y);
+  int S = 1;
+  if (K >= 1024 && tiles < 152) S = std::min((K + 255) / 256, std::max(1, (4 * 152) / tiles));
+  NnState &St = nn(c);
+  if (S > 1 && St.splitk_cap < (size_t)S * M * N) {
+    St.splitk = (float *)dev_alloc(c, (size_t)S * M * N * sizeof(float));
+    St.splitk_cap = (size_t)S * M * N;
+  }
+  if (S > 1) {
+    const int kch = ((K + S - 1) / S + 15) / 16 * 16;
+    S = (K + kch - 1) / kch;
+    grid.z = S;
+    k_dense<TA, TB><<<grid, 256, 0, c->stream>>>(M, N, K, kch, A, lda, ta, B, ldb, tb, bias, relu, St.splitk, Cb);
+    SIE_CHECK_LAUNCH();
+    const int64_t mn = (int64_t)M * N;
+    k_splitk_sum<<<(unsigned)((mn + 255) / 256), 256, 0, c->stream>>>(mn, N, S, St.splitk, bias, relu, Cf, Cb);
+    SIE_CHECK_LAUNCH();
+    c->launches += 2;
+    return;
+  }
+  k_dense<TA, TB><<<grid, 256, 0, c->stream>>>(M, N, K, K, A, lda, ta, B, ldb, tb, bias, relu, Cf, Cb);
   SIE_CHECK_LAUNCH();
   c->launches++;
 }

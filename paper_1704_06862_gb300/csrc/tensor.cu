@@ -612,54 +612,74 @@ constexpr size_t rec_tc_smem() {
 // ---------------------------------------------------------------- learned-preconditioner layers
 // One dense layer of the learned preconditioner, C = act(X W^T + bias), with
 // BF16 X [M][K] and W [N][K] (both K-major, the network's storage) and FP32
-// accumulation in tensor memory: one CTA per 128-row tile of X, the whole K
-// (16 <= K <= 256, a multiple of 16) and N (128 or 256 columns) in one pass.
+// accumulation in tensor memory: one CTA per (128-row tile of X, NT-column
+// slice of W), the whole K (16 <= K <= 256, a multiple of 16) in one pass.
 // The threads stage both operands into the no-swizzle core-matrix layout
-// (16-byte pieces along K); one thread issues the K/16 MMAs (M = 128, N,
-// K = 16) and commits them to an mbarrier (bounded wait, SIE_ETIMEOUT's flag);
-// warp w reads lanes 32 (w % 4) .. + 31 and columns (w / 4) N/2 .. + N/2 back,
-// adds the bias, applies max(0, .) if relu and writes FP32 (Cf) and/or BF16
-// (Cb) rows [M][N].  Rows past M are staged as zeros and not written.
-template <int N>
-__global__ void __launch_bounds__(TC_THREADS) k_dense_tc(int M, int K, const __nv_bfloat16 *__restrict__ X,
+// (16-byte pieces along K, eight loads in flight per thread); one thread
+// issues the K/16 MMAs (M = 128, N = NT, K = 16) and commits them to an
+// mbarrier (bounded wait, SIE_ETIMEOUT's flag); warp w reads lanes
+// 32 (w % 4) .. + 31 and columns (w / 4) NT/2 .. + NT/2 back, adds the bias,
+// applies max(0, .) if relu and writes FP32 (Cf) and/or BF16 (Cb) rows
+// [M][N].  Rows past M are staged as zeros and not written.
+template <int NT>
+__global__ void __launch_bounds__(TC_THREADS) k_dense_tc(int M, int N, int K, const __nv_bfloat16 *__restrict__ X,
                                                         const __nv_bfloat16 *__restrict__ W,
                                                         const float *__restrict__ bias, int relu,
                                                         float *__restrict__ Cf, __nv_bfloat16 *__restrict__ Cb,
                                                         int wait_limit, int *err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *As = smem_raw;                     // [K/16 k-steps][128 rows][16 BF16]
-  unsigned char *Bs = As + (size_t)K * TC_M * 2;    // [K/16 k-steps][N rows][16 BF16]
+  unsigned char *Bs = As + (size_t)K * TC_M * 2;    // [K/16 k-steps][NT rows][16 BF16]
   __shared__ __align__(8) uint64_t done;
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, m0 = blockIdx.x * TC_M;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * NT;
   if (tid == 0) {
     mbar_init(&done, 1);
     s_fail = 0;
   }
-  if (warp == 0) tmem_alloc(&s_tmem, N);
+  if (warp == 0) tmem_alloc(&s_tmem, NT);
   const int kp = K >> 3;  // 16-byte pieces per row
-  for (int idx = tid; idx < TC_M * kp; idx += TC_THREADS) {
-    const int row = idx / kp, pc = idx - row * kp;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (m0 + row < M) v = *reinterpret_cast<const uint4 *>(X + (size_t)(m0 + row) * K + 8 * pc);
-    *reinterpret_cast<uint4 *>(As + op_off(row, 8 * pc, TC_M)) = v;
-  }
-  for (int idx = tid; idx < N * kp; idx += TC_THREADS) {
-    const int row = idx / kp, pc = idx - row * kp;
-    *reinterpret_cast<uint4 *>(Bs + op_off(row, 8 * pc, N)) =
-        *reinterpret_cast<const uint4 *>(W + (size_t)row * K + 8 * pc);
+  constexpr int U = 8;    // loads in flight per thread
+  // A: 128 rows of X, B: rows n0 .. n0 + NT - 1 of W; pieces 0 .. (128 + NT) kp - 1
+  const int na = TC_M * kp, ntot = (TC_M + NT) * kp;
+  for (int base = tid; base < ntot; base += TC_THREADS * U) {
+    uint4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * TC_THREADS;
+      v[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (idx < na) {
+        const int row = idx / kp, pc = idx - row * kp;
+        if (m0 + row < M) v[u] = *reinterpret_cast<const uint4 *>(X + (size_t)(m0 + row) * K + 8 * pc);
+      } else if (idx < ntot) {
+        const int row = (idx - na) / kp, pc = (idx - na) - row * kp;
+        v[u] = *reinterpret_cast<const uint4 *>(W + (size_t)(n0 + row) * K + 8 * pc);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * TC_THREADS;
+      if (idx < na) {
+        const int row = idx / kp, pc = idx - row * kp;
+        *reinterpret_cast<uint4 *>(As + op_off(row, 8 * pc, TC_M)) = v[u];
+      } else if (idx < ntot) {
+        const int row = (idx - na) / kp, pc = (idx - na) - row * kp;
+        *reinterpret_cast<uint4 *>(Bs + op_off(row, 8 * pc, NT)) = v[u];
+      }
+    }
   }
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  constexpr uint32_t IDESC = idesc_bf16_f32(TC_M, N);
+  constexpr uint32_t IDESC = idesc_bf16_f32(TC_M, NT);
   if (tid == 0) {
     for (int s = 0; s < (K >> 4); ++s) {
       const uint64_t ad = smem_desc(smem_u32(As + (size_t)s * TC_M * 32), 128, 256);
-      const uint64_t bd = smem_desc(smem_u32(Bs + (size_t)s * N * 32), 128, 256);
+      const uint64_t bd = smem_desc(smem_u32(Bs + (size_t)s * NT * 32), 128, 256);
       tc_mma(tmem, ad, bd, IDESC, s > 0 ? 1 : 0);
     }
     tc_commit(&done);
@@ -672,14 +692,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_dense_tc(int M, int K, const __n
   tc_fence_after();
   __syncthreads();
   if (!s_fail) {
-    const int row = 32 * (warp & 3) + lane, gm = m0 + row, c0 = (warp >> 2) * (N / 2);
-    for (int cc = 0; cc < N / 2; cc += 32) {
+    const int row = 32 * (warp & 3) + lane, gm = m0 + row, c0 = (warp >> 2) * (NT / 2);
+    for (int cc = 0; cc < NT / 2; cc += 32) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + cc), v);
       if (gm < M) {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
-          const int col = c0 + cc + q;
+          const int col = n0 + c0 + cc + q;
           float y = v[q] + (bias ? bias[col] : 0.f);
           if (relu) y = fmaxf(y, 0.f);
           if (Cf) Cf[(size_t)gm * N + col] = y;
@@ -692,7 +712,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_dense_tc(int M, int K, const __n
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, N);
+  if (warp == 0) tmem_dealloc(tmem, NT);
 }
 
 }  // namespace
@@ -804,29 +824,26 @@ bool op_receive_tc(sie_ctx *c, int rb, int K, int nbox, int nrhs, const int *box
 // (nothing launched) for shapes or alignments it does not cover.
 bool nn_dense_tc(sie_ctx *c, int M, int N, int K, const void *X, const void *W, const float *bias, int relu,
                  float *Cf, void *Cb) {
-  if (!c->nn_tc || M <= 0 || (N != 128 && N != 256) || K < 16 || K > 256 || (K & 15)) return false;
+  constexpr int NT = 64;  // columns per CTA
+  if (!c->nn_tc || M <= 0 || N <= 0 || N % NT || N / NT > 65535 || K < 16 || K > 256 || (K & 15)) return false;
   if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(W) & 15)) return false;
-  const size_t smem = (size_t)K * TC_M * 2 + (size_t)N * K * 2;
-  auto go = [&](auto kern) {
-    static std::mutex mu;
-    static std::map<std::pair<int, const void *>, bool> raised;
-    int dev = 0;
-    SIE_CUDA(cudaGetDevice(&dev));
-    {
-      std::lock_guard<std::mutex> lock(mu);
-      bool &r = raised[{dev, reinterpret_cast<const void *>(kern)}];
-      if (!r) {
-        SIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        r = true;
-      }
+  const size_t smem = (size_t)K * TC_M * 2 + (size_t)NT * K * 2;
+  static std::mutex mu;
+  static std::map<int, bool> raised;
+  int dev = 0;
+  SIE_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    bool &r = raised[dev];
+    if (!r) {
+      SIE_CUDA(cudaFuncSetAttribute(k_dense_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      r = true;
     }
-    kern<<<(M + TC_M - 1) / TC_M, TC_THREADS, smem, c->stream>>>(
-        M, K, reinterpret_cast<const __nv_bfloat16 *>(X), reinterpret_cast<const __nv_bfloat16 *>(W), bias, relu, Cf,
-        reinterpret_cast<__nv_bfloat16 *>(Cb), c->wait_limit, c->d_err);
-    SIE_CHECK_LAUNCH();
-    c->launches++;
-  };
-  if (N == 256) go(k_dense_tc<256>);
-  else go(k_dense_tc<128>);
+  }
+  k_dense_tc<NT><<<dim3((M + TC_M - 1) / TC_M, N / NT), TC_THREADS, smem, c->stream>>>(
+      M, N, K, reinterpret_cast<const __nv_bfloat16 *>(X), reinterpret_cast<const __nv_bfloat16 *>(W), bias, relu, Cf,
+      reinterpret_cast<__nv_bfloat16 *>(Cb), c->wait_limit, c->d_err);
+  SIE_CHECK_LAUNCH();
+  c->launches++;
   return true;
 }
