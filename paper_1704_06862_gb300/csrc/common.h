@@ -262,6 +262,8 @@ struct sie_ctx {
   // concurrent receives (blocks of up to RPART_MAX_RHS right-hand sides): each
   // medium writes its rows [r][rpart_nb][2] here, a combine kernel adds them
   // into y in medium order; d_rmap [ne][2]: a basis's rows (lower medium first)
+  void *d_iluT = nullptr;        // block ILU(0): interleaved source and result, [2][n][iluT_R] (FP64 capacity)
+  int iluT_R = 0;
   void *d_rpart = nullptr;
   int rpart_cap = 0, rpart_nb = 0;
   int *d_rmap = nullptr;

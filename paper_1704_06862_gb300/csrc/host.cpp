@@ -96,6 +96,12 @@ void ensure_work(sie_ctx *c, int64_t nrhs) {
   // per-medium receive outputs for the concurrent receives of small blocks
   c->rpart_cap = (int)std::min<int64_t>(nrhs, RPART_MAX_RHS);
   c->d_rpart = dev_alloc(c, std::max<size_t>(256, (size_t)c->rpart_nb * 2 * c->rpart_cap * sizeof(zd)));
+  // right-hand-side-interleaved source and result of the block ILU(0) sweeps
+  // ([n][Rp] each, Rp = nrhs rounded up to 16; the widest block used is 16)
+  if (nrhs >= 2) {
+    c->iluT_R = (int)((nrhs + 15) / 16 * 16);
+    c->d_iluT = dev_alloc(c, (size_t)2 * c->iluT_R * c->ne * 2 * sizeof(zd));
+  }
   c->nrhs_cap = nrhs;
   c->work_gen++;
 }

@@ -1673,6 +1673,203 @@ __global__ void __launch_bounds__(256) k_ilu_sweep_blk(int ne, int nrhs, int for
   }
 }
 
+// The block sweeps on right-hand-side-interleaved vectors: zT[(2 i + c) Rp + r]
+// (row i, J/M component c, right-hand side r < Rp, Rp a multiple of RB, the
+// padding right-hand sides zero).  The same 15 steps and roles as
+// k_ilu_sweep_blk, but the RB values of one vector entry are one contiguous,
+// aligned run, so each block of a factor gathers them with RB / 2 (FP32) or
+// RB (FP64) 16-byte loads instead of RB scattered ones; the padding lanes
+// carry zeros through (the sweep is linear), so no lane is masked.
+template <typename T, int RB>
+__device__ __forceinline__ void ld_rb(const cx<T> *__restrict__ p, cx<T> (&x)[RB]) {
+  typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V16;
+  constexpr int PER = (int)(sizeof(V16) / sizeof(cx<T>));
+  const V16 *q = reinterpret_cast<const V16 *>(p);
+#pragma unroll
+  for (int u = 0; u < RB / PER; ++u) {
+    const V16 v = __ldcg(q + u);
+    memcpy(&x[u * PER], &v, sizeof(V16));
+  }
+}
+
+template <typename T, int RB>
+__global__ void __launch_bounds__(256) k_ilu_sweep_blkT(int ne, int Rp, int forward, int both, int colour,
+                                                       int nboxA, int box0, int rb0, int rb1,
+                                                       const int *__restrict__ box_start,
+                                                       const int *__restrict__ cptr,
+                                                       const int *__restrict__ off_col,
+                                                       const cx<T> *__restrict__ off_val,
+                                                       const int64_t *__restrict__ tri_off,
+                                                       const cx<T> *__restrict__ tri,
+                                                       const int64_t *__restrict__ tri2_off,
+                                                       const cx<T> *__restrict__ tri2, const cx<T> *src, cx<T> *z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V16;
+  constexpr int NV = (int)(4 * sizeof(cx<T>) / sizeof(V16));
+  const V16 *Ov = reinterpret_cast<const V16 *>(off_val);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int sc = forward ? colour - 1 : colour + 1;
+  const bool has_src = sc >= 0 && sc < 8;
+  const cx<T> *w = (forward && colour == 0) ? src : z;
+  if ((int)blockIdx.x >= nboxA) {
+    // ---- role B: 8 lanes per row of the colours still to come
+    const int hl = threadIdx.x & 7;
+    const int i = rb0 + ((int)blockIdx.x - nboxA) * ((int)blockDim.x / 8) + (int)(threadIdx.x >> 3);
+    const bool row_ok = i < rb1;
+    if (!has_src) {
+      if (row_ok)
+        for (int e = hl; e < 2 * Rp; e += 8) z[(size_t)2 * i * Rp + e] = src[(size_t)2 * i * Rp + e];
+      return;
+    }
+    int q0 = 0, q1 = 0;
+    if (row_ok) {
+      q0 = cptr[9 * (size_t)i + sc];
+      q1 = cptr[9 * (size_t)i + sc + 1];
+    }
+    for (int r0 = 0; r0 < Rp; r0 += RB) {
+      cx<T> a0[RB], a1[RB];
+      for (int q = q0 + hl; q < q1; q += 8) {
+        const int cc = __ldg(off_col + q);
+        V16 u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = __ldg(Ov + (size_t)q * NV + v);
+        const cx<T> *bb = reinterpret_cast<const cx<T> *>(u);
+        cx<T> x0[RB], x1[RB];  // colour sc: not written in this step
+        ld_rb<T, RB>(z + (size_t)2 * cc * Rp + r0, x0);
+        ld_rb<T, RB>(z + ((size_t)2 * cc + 1) * Rp + r0, x1);
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+          a0[rr] = cfma(bb[0], x0[rr], cfma(bb[1], x1[rr], a0[rr]));
+          a1[rr] = cfma(bb[2], x0[rr], cfma(bb[3], x1[rr], a1[rr]));
+        }
+      }
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr) {
+#pragma unroll
+        for (int d = 4; d > 0; d >>= 1) {
+          a0[rr] += shfl_down(a0[rr], d);
+          a1[rr] += shfl_down(a1[rr], d);
+        }
+      }
+      if (row_ok && hl == 0 && q1 > q0) {
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+          z[(size_t)2 * i * Rp + r0 + rr] -= a0[rr];
+          z[((size_t)2 * i + 1) * Rp + r0 + rr] -= a1[rr];
+        }
+      }
+    }
+    return;
+  }
+
+  // ---- role A: one CTA per box of this colour
+  cx<T> *t = reinterpret_cast<cx<T> *>(smem_raw);  // [RB][2n]
+  const int b = box0 + blockIdx.x;
+  const int s0 = box_start[b], n = box_start[b + 1] - s0;
+  cx<T> *t2 = t + (size_t)RB * 2 * n;               // [RB][2n]
+  for (int r0 = 0; r0 < Rp; r0 += RB) {
+    for (int li = warp; li < n; li += nw) {
+      const int i = s0 + li;
+      const int q0 = has_src ? cptr[9 * (size_t)i + sc] : 0, q1 = has_src ? cptr[9 * (size_t)i + sc + 1] : 0;
+      cx<T> a0[RB], a1[RB];
+      for (int q = q0 + lane; q < q1; q += 32) {
+        const int cc = __ldg(off_col + q);
+        V16 u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = __ldg(Ov + (size_t)q * NV + v);
+        const cx<T> *bb = reinterpret_cast<const cx<T> *>(u);
+        cx<T> x0[RB], x1[RB];
+        ld_rb<T, RB>(z + (size_t)2 * cc * Rp + r0, x0);
+        ld_rb<T, RB>(z + ((size_t)2 * cc + 1) * Rp + r0, x1);
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+          a0[rr] = cfma(bb[0], x0[rr], cfma(bb[1], x1[rr], a0[rr]));
+          a1[rr] = cfma(bb[2], x0[rr], cfma(bb[3], x1[rr], a1[rr]));
+        }
+      }
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr) {
+        const cx<T> u0 = warp_sum(a0[rr]), u1 = warp_sum(a1[rr]);
+        if (lane == 0) {
+          t[(size_t)rr * 2 * n + 2 * li] = w[(size_t)2 * i * Rp + r0 + rr] - u0;
+          t[(size_t)rr * 2 * n + 2 * li + 1] = w[((size_t)2 * i + 1) * Rp + r0 + rr] - u1;
+        }
+      }
+    }
+    __syncthreads();
+    for (int pass = 0; pass < (both ? 2 : 1); ++pass) {
+      const bool lower = forward && pass == 0;
+      const cx<T> *M = pass == 0 ? tri + 4 * tri_off[b] : tri2 + 4 * tri2_off[b];
+      const cx<T> *in = pass == 0 ? t : t2;
+      for (int li = warp; li < n; li += nw) {
+        const int j0 = lower ? 0 : li, j1 = lower ? li : n;
+        const cx<T> *row = M + 4 * (size_t)(lower ? li * (li - 1) / 2 : li * n - li * (li - 1) / 2);
+        cx<T> a0[RB], a1[RB];
+        for (int j = j0 + lane; j < j1; j += 32) {
+          const cx<T> *B = row + 4 * (j - j0);
+          const cx<T> b0 = B[0], b1 = B[1], b2 = B[2], b3 = B[3];
+#pragma unroll
+          for (int rr = 0; rr < RB; ++rr) {
+            const cx<T> x0 = in[(size_t)rr * 2 * n + 2 * j], x1 = in[(size_t)rr * 2 * n + 2 * j + 1];
+            a0[rr] = cfma(b0, x0, cfma(b1, x1, a0[rr]));
+            a1[rr] = cfma(b2, x0, cfma(b3, x1, a1[rr]));
+          }
+        }
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+          cx<T> u0 = warp_sum(a0[rr]), u1 = warp_sum(a1[rr]);
+          if (lane == 0) {
+            if (lower) {
+              u0 += in[(size_t)rr * 2 * n + 2 * li];
+              u1 += in[(size_t)rr * 2 * n + 2 * li + 1];
+            }
+            if (both && pass == 0) {
+              t2[(size_t)rr * 2 * n + 2 * li] = u0;
+              t2[(size_t)rr * 2 * n + 2 * li + 1] = u1;
+            } else {
+              z[(size_t)2 * (s0 + li) * Rp + r0 + rr] = u0;
+              z[((size_t)2 * (s0 + li) + 1) * Rp + r0 + rr] = u1;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// [R][m] -> [m][Rp] (zero rows r >= R) and back, in 32 x 32 tiles through shared memory
+template <typename T>
+__global__ void k_rhs_interleave(int m, int R, int Rp, const cx<T> *__restrict__ a, cx<T> *__restrict__ b) {
+  __shared__ __align__(16) unsigned char tile_raw[32 * 33 * sizeof(cx<T>)];  // raw storage: cx has a constructor
+  cx<T>(*tile)[33] = reinterpret_cast<cx<T>(*)[33]>(tile_raw);
+  const int e0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, e = e0 + threadIdx.x;
+    tile[k][threadIdx.x] = (r < R && e < m) ? a[(size_t)r * m + e] : cx<T>();
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int e = e0 + k, r = r0 + threadIdx.x;
+    if (e < m && r < Rp) b[(size_t)e * Rp + r] = tile[threadIdx.x][k];
+  }
+}
+template <typename T>
+__global__ void k_rhs_deinterleave(int m, int R, int Rp, const cx<T> *__restrict__ b, cx<T> *__restrict__ a) {
+  __shared__ __align__(16) unsigned char tile_raw[32 * 33 * sizeof(cx<T>)];  // raw storage: cx has a constructor
+  cx<T>(*tile)[33] = reinterpret_cast<cx<T>(*)[33]>(tile_raw);
+  const int e0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int e = e0 + k, r = r0 + threadIdx.x;
+    tile[k][threadIdx.x] = (e < m && r < Rp) ? b[(size_t)e * Rp + r] : cx<T>();
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, e = e0 + threadIdx.x;
+    if (r < R && e < m) a[(size_t)r * m + e] = tile[threadIdx.x][k];
+  }
+}
+
 // ---------------------------------------------------------------- vectors
 __global__ void k_rowscale(int ne, int nrhs, const zd *__restrict__ d, zd *__restrict__ y) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2076,8 +2273,47 @@ void op_ilu(sie_ctx *c, const cx<T> *r, cx<T> *z, int nrhs) {
       c->launches++;
     }
   };
-  if (rbq == 16 && 2 * (size_t)16 * 2 * mb * sizeof(cx<T>) <= 227 * 1024) sweeps(k_ilu_sweep_blk<T, 16>, 16);
-  else if (rbq >= 8) sweeps(k_ilu_sweep_blk<T, 8>, 8);
+  const int RBu = (rbq == 16 && 2 * (size_t)16 * 2 * mb * sizeof(cx<T>) <= 227 * 1024) ? 16 : rbq >= 8 ? 8 : 4;
+  // with the context's work buffers: the sweeps on right-hand-side-interleaved
+  // copies of r and z (contiguous gathers); without them (the allocation-free
+  // entry on a context that never ran a block) on r and z as they are
+  const int Rp = (nrhs + RBu - 1) / RBu * RBu, m = 2 * c->ne;
+  if (c->d_iluT && Rp <= c->iluT_R) {
+    cx<T> *rT = (cx<T> *)c->d_iluT, *zT = rT + (size_t)Rp * m;
+    const dim3 tg((m + 31) / 32, (Rp + 31) / 32), tb(32, 8);
+    k_rhs_interleave<T><<<tg, tb, 0, c->stream>>>(m, nrhs, Rp, r, rT);
+    SIE_CHECK_LAUNCH();
+    auto sweepsT = [&](auto kern) {
+      const size_t smem = 2 * (size_t)RBu * 2 * mb * sizeof(cx<T>);
+      set_smem(kern, smem);
+      auto rows_from = [&](int colr) { return c->leaf_start[I.colour_ptr[colr]]; };
+      for (int step = 0; step < 15; ++step) {
+        const bool fwd = step < 8;
+        const int colr = fwd ? step : 14 - step;
+        const int first = I.colour_ptr[colr], cnt = I.colour_ptr[colr + 1] - first;
+        const int rb0 = fwd ? rows_from(colr + 1) : 0, rb1 = fwd ? c->ne : rows_from(colr);
+        const int grid = cnt + (rb1 - rb0 + 31) / 32;  // role B: 32 rows per 256-thread CTA
+        if (grid == 0) continue;
+        kern<<<grid, 256, smem, c->stream>>>(
+            c->ne, Rp, fwd ? 1 : 0, colr == 7 ? 1 : 0, colr, cnt, first, rb0, rb1, I.d_box_start,
+            fwd ? I.d_lo_cptr : I.d_up_cptr, fwd ? I.d_lo_col : I.d_up_col,
+            (const cx<T> *)(fwd ? tsel<T>::lo(I) : tsel<T>::upv(I)), fwd ? I.d_tl_off : I.d_tu_off,
+            (const cx<T> *)(fwd ? tsel<T>::tl(I) : tsel<T>::tu(I)), I.d_tu_off, (const cx<T> *)tsel<T>::tu(I),
+            (const cx<T> *)rT, zT);
+        SIE_CHECK_LAUNCH();
+        c->launches++;
+      }
+    };
+    if (RBu == 16) sweepsT(k_ilu_sweep_blkT<T, 16>);
+    else if (RBu == 8) sweepsT(k_ilu_sweep_blkT<T, 8>);
+    else sweepsT(k_ilu_sweep_blkT<T, 4>);
+    k_rhs_deinterleave<T><<<tg, tb, 0, c->stream>>>(m, nrhs, Rp, zT, z);
+    SIE_CHECK_LAUNCH();
+    c->launches += 2;
+    return;
+  }
+  if (RBu == 16) sweeps(k_ilu_sweep_blk<T, 16>, 16);
+  else if (RBu == 8) sweeps(k_ilu_sweep_blk<T, 8>, 8);
   else sweeps(k_ilu_sweep_blk<T, 4>, 4);
 }
 
