@@ -79,3 +79,28 @@ def test_noalloc_ilu_matches_ilu_apply_on_consecutive_calls(nrhs):
         assert e.value.code == 1
     finally:
         s.close()
+
+
+def test_noalloc_block_on_a_fresh_context_matches_interleaved_path():
+    """On a context that never ran a block of right-hand sides the
+    allocation-free apply takes the block sweeps on the vectors as they are;
+    once ilu_apply has set up the context's interleaved work buffers the
+    block sweeps run on right-hand-side-interleaved copies.  Both give the
+    same preconditioner (same sums per right-hand side, other order)."""
+    import __graft_entry__ as g
+    g.build()
+    for prec, tol in ((sie.SIE_PREC_FP64, 1e-9), (sie.SIE_PREC_MIXED, 1e-5)):
+        s = sie.Solver(geo.coated_sphere(**MESH), levels=4)
+        try:
+            r = _rand(s, 5, 33)
+            z_direct = torch.zeros_like(r)
+            sie.ilu_apply_noalloc(s.ctx, r, z_direct, 5, prec)   # no work buffers yet
+            torch.cuda.synchronize()
+            z_inter = torch.zeros_like(r)
+            sie.ilu_apply(s.ctx, r, z_inter, 5, prec)            # allocates them, interleaved sweeps
+            torch.cuda.synchronize()
+            a, b = z_direct.cpu().numpy(), z_inter.cpu().numpy()
+            assert np.all(np.isfinite(a)) and np.all(np.isfinite(b))
+            assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b)
+        finally:
+            s.close()
