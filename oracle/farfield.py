@@ -28,13 +28,12 @@ def far_amplitudes(mesh: Mesh, x, obs, freq_hz=None):
     k, eta = material(mesh.media[0], k0)
     bR, wR = radon7()
     tris0 = mesh.region_tris(0)
-    s_edge = mesh.region_sign(0)
-    d = _tri_data(mesh, tris0)
+    d = _tri_data(mesh, tris0, 0)        # region 0's functions (side signs included)
     pts = points(mesh.verts[mesh.tris[tris0]], bR)                 # [T,A,3]
     W = mesh.area[tris0][:, None] * wR[None, :]
     F = d["c"][:, :, None, None] * (pts[:, None, :, :] - d["v"][:, :, None, :])     # [T,i,A,3]
     m = d["e"]
-    s = np.where(m >= 0, s_edge[np.maximum(m, 0)], 0.0)
+    s = np.where(m >= 0, 1.0, 0.0)
     th, ph = obs[:, 0], obs[:, 1]
     rhat = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
     that = np.stack([np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)], 1)

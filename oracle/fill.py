@@ -141,18 +141,26 @@ def _combine(W, r, tp, tq, I_G, I_Gr, I_gG, k):
     return L, K, NL, NK
 
 
-def _tri_data(mesh: Mesh, idx):
+def _tri_data(mesh: Mesh, idx, l=None):
     """Per-triangle basis data for triangles idx: local-edge coefficient
-    c = sigma l/(2A), divergence d = sigma l / A, free-vertex coords v, normal n."""
+    c = sigma l/(2A), divergence d = sigma l / A, free-vertex coords v, normal n.
+    With a region l: the pieces of region l's functions, i.e. sigma times
+    s_l(T) (the side of T that l is on), and the normal s_l(T) n_T of region l
+    (Eqs. 12-13 applied per triangle, which also covers junction edges)."""
     te = mesh.tri_edge[idx]
     sg = mesh.tri_sign[idx]
+    n = mesh.normal[idx]
+    if l is not None:
+        st = mesh.tri_region_sign(l)[idx]
+        sg = sg * st[:, None]
+        n = n * st[:, None]
     ln = np.where(te >= 0, mesh.length[np.maximum(te, 0)], 0.0)
     A = mesh.area[idx]
     return dict(
         c=sg * ln / (2.0 * A[:, None]),
         d=sg * ln / A[:, None],
         v=mesh.verts[mesh.tri_free[idx]],
-        n=mesh.normal[idx],
+        n=n,
         e=te,
     )
 
@@ -160,15 +168,16 @@ def _tri_data(mesh: Mesh, idx):
 def region_operators(mesh: Mesh, l, rows=None, chunk=24, outer_n=4, freq_hz=None):
     """Galerkin matrices of medium l over all edges (rows restricted to
     ``rows``): dict with L, K, NL, NK [nrows, ne] (zero where an edge is not
-    on the boundary of B_l), Gram G and Gx [nrows, ne], and k, eta~."""
+    on the boundary of B_l), Gram G and Gx [nrows, ne], and k, eta~.  They are
+    taken between region l's own functions (each triangle's piece times the
+    side sign s_l(T)) with region l's normals s_l(T) n_T, so the side signs of
+    Eqs. 12-13 are already in them."""
     k0 = k0_of(freq_hz)
     ne = mesh.ne
     rows = np.arange(ne) if rows is None else np.asarray(rows, np.int64)
     row_map = -np.ones(ne, np.int64)
     row_map[rows] = np.arange(len(rows))
-    need_tri = np.zeros(mesh.nt, bool)
-    need_tri[mesh.tp[rows]] = True
-    need_tri[mesh.tm[rows]] = True
+    need_tri = np.any(np.isin(mesh.tri_edge, rows) & (mesh.tri_edge >= 0), axis=1)
     k, eta = material(mesh.media[l], k0)
     out = {nm: np.zeros((len(rows), ne), np.complex128) for nm in ("L", "K", "NL", "NK", "G", "Gx")}
     out["k"], out["eta"] = k, eta
@@ -181,7 +190,7 @@ def region_operators(mesh: Mesh, l, rows=None, chunk=24, outer_n=4, freq_hz=None
     pts_all = points(tv_all, bR)                                          # [Q,7,3]
     wq_all = mesh.area[tris_l][:, None] * wR[None, :]
     tq_all = dict(pts=pts_all, wq=wq_all)
-    src = _tri_data(mesh, tris_l)
+    src = _tri_data(mesh, tris_l, l)
     test_local = np.nonzero(need_tri[tris_l])[0]
     sing = singular_pairs(mesh, tris_l, test_local)          # [len(test_local), Q]
 
@@ -268,6 +277,8 @@ def ictf_row_weights(mesh: Mesh, freq_hz=None, rows=None):
     it separates.  Summed over the two media with the PMCHWT weights, this is
     J-row = (1/e) sum_l s_l T-EFIE_l, M-row = -e sum_l s_l T-MFIE_l: the
     PMCHWT rows of each edge times (1/e, e).  Returns (wJ, wM) per row edge."""
+    if np.any(mesh.junction):
+        raise ValueError("ICTF: the mean impedance of an interface is not defined at junction edges")
     k0 = k0_of(freq_hz)
     rows = np.arange(mesh.ne) if rows is None else np.asarray(rows, np.int64)
     eta = np.array([material(mesh.media[l], k0)[1] for l in range(mesh.nr)])
@@ -296,20 +307,18 @@ def assemble_variants(mesh: Mesh, formulations=FORMULATIONS, freq_hz=None, rows=
     rows = np.arange(ne) if rows is None else np.asarray(rows, np.int64)
     out = {f: np.zeros((2 * len(rows), 2 * ne), np.complex128) for f in formulations}
     for l in range(mesh.nr):
+        # region l's operators between its own functions (side signs s_l of
+        # Eqs. 12-13 included per triangle, region normals n_l)
         op = region_operators(mesh, l, rows, chunk, outer_n, freq_hz)
-        s = mesh.region_sign(l)
-        sm = s[rows][:, None]
-        sn = s[None, :]
-        ss = sm * sn
         eta = op["eta"]
-        tK = ss * op["K"] + 0.5 * sm * op["Gx"]
-        nN = -sn * op["NK"] + 0.5 * ss * op["G"]
+        tK = op["K"] + 0.5 * op["Gx"]
+        nN = -op["NK"] + 0.5 * op["G"]
         for f, Z in out.items():
             aTJ, aNJ, aTM, aNM = formulation_weights(f, eta)
-            Z[0::2, 0::2] += aTJ * ss * op["L"] + aNJ * nN
-            Z[0::2, 1::2] += (aTJ * tK + aNJ * sn * op["NL"]) / eta
-            Z[1::2, 0::2] += -(aTM * tK + aNM * sn * op["NL"]) * eta
-            Z[1::2, 1::2] += aTM * ss * op["L"] + aNM * nN
+            Z[0::2, 0::2] += aTJ * op["L"] + aNJ * nN
+            Z[0::2, 1::2] += (aTJ * tK + aNJ * op["NL"]) / eta
+            Z[1::2, 0::2] += -(aTM * tK + aNM * op["NL"]) * eta
+            Z[1::2, 1::2] += aTM * op["L"] + aNM * nN
     if "ictf" in out:
         wJ, wM = ictf_row_weights(mesh, freq_hz, rows)
         out["ictf"][0::2, :] *= wJ[:, None]
@@ -339,8 +348,7 @@ def rhs(mesh: Mesh, inc, freq_hz=None, formulation="jmcfie"):
     _, eta0 = material(mesh.media[0], k0)
     bR, wR = radon7()
     tris0 = mesh.region_tris(0)
-    s_edge = mesh.region_sign(0)
-    d = _tri_data(mesh, tris0)
+    d = _tri_data(mesh, tris0, 0)        # region 0's functions and normals (side signs included)
     pts = points(mesh.verts[mesh.tris[tris0]], bR)
     W = mesh.area[tris0][:, None] * wR[None, :]
     F = d["c"][:, :, None, None] * (pts[:, None, :, :] - d["v"][:, :, None, :])      # [T,i,A,3]
@@ -357,10 +365,9 @@ def rhs(mesh: Mesh, inc, freq_hz=None, formulation="jmcfie"):
         fnE = np.einsum("ta,tiax,tax->ti", W, Fxn, E)
         m = d["e"]
         ok = m >= 0
-        s = s_edge[np.maximum(m, 0)]
         aTJ, aNJ, aTM, aNM = formulation_weights(formulation, eta0)
-        bJ = aTJ * s * fE / eta0 + aNJ * fnH
-        bM = aTM * s * eta0 * fH - aNM * fnE
+        bJ = aTJ * fE / eta0 + aNJ * fnH
+        bM = aTM * eta0 * fH - aNM * fnE
         np.add.at(out[ri], 2 * m[ok], bJ[ok])
         np.add.at(out[ri], 2 * m[ok] + 1, bM[ok])
     if formulation == "ictf":

@@ -97,6 +97,85 @@ def homogeneous_sphere(nu=8, radius=0.5, eps_r=4.0, mu_r=1.0):
     return dict(verts=v, tris=t, tri_regions=regions, media=media)
 
 
+def latlong_sphere(nlat: int, nlon: int, radius: float):
+    """Sphere meshed on nlat latitude bands (even: the equator z = 0 is a ring
+    of mesh edges) and nlon meridians; outward-oriented triangles.  Returns
+    vertices, triangles and the vertex indices of the equator ring (in order
+    of increasing longitude)."""
+    if nlat % 2 or nlat < 2 or nlon < 3:
+        raise ValueError("latlong_sphere: nlat must be even and >= 2, nlon >= 3")
+    verts = [(0.0, 0.0, radius)]
+    ring = []
+    for i in range(1, nlat):
+        th = np.pi * i / nlat
+        row = []
+        for j in range(nlon):
+            ph = 2.0 * np.pi * j / nlon
+            row.append(len(verts))
+            verts.append((radius * np.sin(th) * np.cos(ph), radius * np.sin(th) * np.sin(ph), radius * np.cos(th)))
+        ring.append(row)
+    south = len(verts)
+    verts.append((0.0, 0.0, -radius))
+    tris = []
+    for j in range(nlon):
+        j1 = (j + 1) % nlon
+        tris.append((0, ring[0][j], ring[0][j1]))
+        for i in range(nlat - 2):
+            a, b, c, d = ring[i][j], ring[i][j1], ring[i + 1][j], ring[i + 1][j1]
+            tris.append((a, c, d))
+            tris.append((a, d, b))
+        tris.append((south, ring[-1][j1], ring[-1][j]))
+    return np.array(verts, np.float64), np.array(tris, np.int32), np.array(ring[nlat // 2 - 1], np.int32)
+
+
+def split_sphere(nlat=8, nlon=16, nrings=2, radius=0.3, eps_upper=4.0, eps_lower=4.0):
+    """Dielectric sphere cut by the plane z = 0 into an upper region 1 and a
+    lower region 2 (three surfaces: upper hemisphere 0|1, lower hemisphere
+    0|2, the disk 1|2, meeting at the equator's junction edges).  The disk is
+    meshed on nrings concentric rings of nlon points sharing the equator
+    vertices; its normal +z points into region 1.  With eps_upper == eps_lower
+    the body is the homogeneous sphere of the same outer mesh."""
+    v, t, eq = latlong_sphere(nlat, nlon, radius)
+    cen = v[:, 2]
+    up = np.array([cen[list(tr)].mean() > 0 for tr in t])
+    verts = [tuple(x) for x in v]
+    rings = []
+    for r in range(1, nrings):
+        rho = radius * r / nrings
+        row = []
+        for j in range(nlon):
+            ph = 2.0 * np.pi * j / nlon
+            row.append(len(verts))
+            verts.append((rho * np.cos(ph), rho * np.sin(ph), 0.0))
+        rings.append(row)
+    rings.append(list(eq))
+    centre = len(verts)
+    verts.append((0.0, 0.0, 0.0))
+    disk = []
+    for j in range(nlon):
+        j1 = (j + 1) % nlon
+        disk.append((centre, rings[0][j], rings[0][j1]))   # counter-clockwise seen from +z: normal +z
+        for r in range(nrings - 1):
+            a, b, c, d = rings[r][j], rings[r][j1], rings[r + 1][j], rings[r + 1][j1]
+            disk.append((a, c, d))
+            disk.append((a, d, b))
+    tris = np.concatenate([t, np.array(disk, np.int32)])
+    regions = np.concatenate([np.where(up[:, None], [[0, 1]], [[0, 2]]),
+                              np.tile(np.array([[1, 2]]), (len(disk), 1))]).astype(np.int32)
+    eu, el = complex(eps_upper), complex(eps_lower)
+    media = np.array([[1, 0, 1, 0], [eu.real, eu.imag, 1, 0], [el.real, el.imag, 1, 0]], np.float64)
+    return dict(verts=np.array(verts, np.float64), tris=tris, tri_regions=regions, media=media)
+
+
+def latlong_homogeneous_sphere(nlat=8, nlon=16, radius=0.3, eps_r=4.0):
+    """The outer surface of split_sphere as a single homogeneous body."""
+    v, t, _ = latlong_sphere(nlat, nlon, radius)
+    regions = np.tile(np.array([[0, 1]], np.int32), (len(t), 1))
+    e = complex(eps_r)
+    media = np.array([[1, 0, 1, 0], [e.real, e.imag, 1, 0]], np.float64)
+    return dict(verts=v, tris=t, tri_regions=regions, media=media)
+
+
 def coated_sphere(nu_outer=30, nu_inner=20, r_outer=1.5, r_inner=1.0, eps_shell=2.56, eps_core=4.0):
     """Two-layer sphere: region 0 free space, region 1 shell, region 2 core."""
     vo, to = geodesic_sphere(nu_outer, r_outer)

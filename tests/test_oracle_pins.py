@@ -531,3 +531,47 @@ def test_ictf_matched_impedance():
     inc = [[0.3, 0.2, 0.0, 1.0]]
     bP, bI = fill.rhs(m, inc, formulation="pmchwt"), fill.rhs(m, inc, formulation="ictf")
     assert np.abs(bI - bP).max() < 1e-14 * np.abs(bP).max()
+
+
+def test_junction_edges_split_sphere():
+    """Junction edges (three surfaces meeting at an edge, Eq. 16's multilayer
+    setting): a sphere cut by the plane z = 0 into two regions of the same
+    eps has the same exterior field as the uncut sphere of the same outer
+    mesh.  Its equator edges are shared by an upper-hemisphere (0|1), a
+    lower-hemisphere (0|2) and a disk (1|2) triangle; the region-based RWG
+    ties them to one unknown with per-triangle coefficients a_T such that every
+    region's equivalent current is divergence-conforming across the edge.
+    Pins: the constraints hold on every junction edge; the split body's RCS
+    approaches the uncut body's as the mesh is refined (discretisation error
+    of the disk: 0.23 then 0.089 dB mean, the h^2 rate), far below what a
+    wrong coefficient gives (flipping the disk's: 3.4 dB mean); both stay
+    within the coarse-mesh distance of the Mie series."""
+    obs = geo.bistatic_angles(37)
+    inc = [[0.0, 0.0, 0.0, 1.0]]
+    ref = mie.sphere_bistatic(0.3, 4.0, obs[:, 0])
+
+    def rcs_of(m):
+        Z = fill.assemble(m)
+        x = solvers.lu_solve(Z, fill.rhs(m, inc)[0])
+        return farfield.rcs(m, x[None], obs)[0][:, 0]
+
+    diffs = []
+    for nl, no, nr in ((8, 16, 2), (12, 24, 3)):
+        ms = Mesh(**geo.split_sphere(nl, no, nr))
+        assert int(ms.junction.sum()) == no                      # the equator edges
+        for e in np.nonzero(ms.junction)[0]:
+            sides = [(t, ms.tri_sign[t, j]) for t in range(ms.nt) for j in range(3) if ms.tri_edge[t, j] == e]
+            assert len(sides) == 3
+            for l in range(3):
+                on = [(t, a) for t, a in sides if l in ms.tri_regions[t]]
+                assert len(on) == 2
+                (t1, a1), (t2, a2) = on
+                s1 = 1.0 if ms.tri_regions[t1, 0] == l else -1.0
+                s2 = 1.0 if ms.tri_regions[t2, 0] == l else -1.0
+                assert s1 * a1 == -s2 * a2
+        mh = Mesh(**geo.latlong_homogeneous_sphere(nl, no))
+        rs, rh = rcs_of(ms), rcs_of(mh)
+        d = np.abs(10 * np.log10(rs) - 10 * np.log10(rh))
+        diffs.append(d.mean())
+        assert np.abs(10 * np.log10(rs) - 10 * np.log10(ref)).mean() < 1.0
+    assert diffs[0] < 0.3 and diffs[1] < 0.12 and diffs[1] < 0.5 * diffs[0], diffs
