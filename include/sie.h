@@ -81,11 +81,17 @@ const char *sie_last_error(const sie_ctx *ctx);
  *               Passive media only (Im(eps_r mu_r) <= 0).
  *   freq_hz     frequency.
  *   n_rwg_out   receives the number of RWG edges (unknowns = 2 * n_rwg).
- * Errors: SIE_EINVAL for junction edges (owned by > 2 triangles), an edge
- * shared by triangles of different surfaces or of inconsistent orientation,
- * region indices outside [0, nr), degenerate triangles, media with a zero
- * or non-finite eps_r or mu_r, active media.  Host-only work
- * (topology); synchronous.  */
+ * Junction edges (three or more surfaces meeting at an edge, Eq. 16's
+ * multi-boundary bodies): each region touching the edge must see exactly two
+ * of its triangles; the edge carries one unknown whose per-triangle
+ * coefficients a_T make every region's current divergence-conforming across
+ * it (s_l(T1) a_T1 = -s_l(T2) a_T2, s_l(T) = +1 when l is T's "+" region),
+ * i.e. region l's basis function is an RWG function on its two triangles.
+ * Errors: SIE_EINVAL for a junction edge where a region does not see two of
+ * the triangles, an ordinary edge shared by triangles of different surfaces
+ * or of inconsistent orientation, region indices outside [0, nr),
+ * degenerate triangles, media with a zero or non-finite eps_r or mu_r,
+ * active media.  Host-only work (topology); synchronous.  */
 sie_status sie_build_mesh(sie_ctx *ctx, const double *verts, int64_t nv, const int32_t *tris,
                           int64_t nt, const int32_t *tri_regions, const double *media, int32_t nr,
                           double freq_hz, int64_t *n_rwg_out);

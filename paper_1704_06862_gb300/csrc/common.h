@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstdio>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "sie.h"
@@ -148,6 +149,13 @@ struct RegionHost {
   int max_leaf = 0;             // most bases in one leaf box
   std::vector<LevelHost> lev;   // index = level number; levels 2..leaf carry tables
   int *d_basis_p = nullptr, *d_basis_sign = nullptr, *d_box_start = nullptr, *d_basis_box = nullptr;
+  // per basis of the medium: its two triangles in this medium and the sign of
+  // each triangle's piece in the radiation pattern (1, 1 for an ordinary edge,
+  // whose medium sign is basis_sign; s_l(T) for a junction edge, basis_sign 1)
+  std::vector<int> ptri;
+  std::vector<double> psg;
+  int *d_ptri = nullptr;
+  double *d_psg = nullptr;
   int rpart_off = 0;            // first row of this medium in the concatenated receive outputs
   double *d_box_centre = nullptr;  // leaf box centres [nleaf][3]
   void *d_V64 = nullptr, *d_V32 = nullptr;    // radiation patterns [nb][2][Kleaf]
@@ -217,7 +225,14 @@ struct sie_ctx {
   std::vector<int> edge_v, tp, tm, vp, vm;  // user edge numbering
   std::vector<double> elen;
   std::vector<int> tri_edge, tri_free;  // [nt][3] user edge index / free vertex
-  std::vector<double> tri_sign;         // [nt][3]
+  std::vector<double> tri_sign;         // [nt][3] coefficient of the edge's function on the triangle:
+                                        // +1 on T+, -1 on T-; a_T at a junction edge
+  // per edge: the media it lies in, each with its two triangles (region, T1, T2);
+  // two entries for an ordinary edge, one per touching region at a junction
+  std::vector<int> emed_ptr;
+  std::vector<std::array<int, 3>> emed;
+  std::vector<char> ejunc;              // per edge: 1 at a junction
+  int njunc = 0;                        // junction edges
   std::vector<std::complex<double>> kreg, etareg;
 
   // tree and ordering
@@ -248,8 +263,7 @@ struct sie_ctx {
   int *d_row_ptr = nullptr, *d_col = nullptr;
   void *d_near64 = nullptr, *d_near32 = nullptr;  // [nnzb][4] blocks
   int *d_perm = nullptr, *d_inv = nullptr;
-  int *d_edge_tris = nullptr;    // per internal edge: T+, T-
-  int *d_edge_reg = nullptr;     // per internal edge: (r+, r-)
+  int *d_edge_tris = nullptr;    // per internal edge: its two triangles in medium 0 (-1: not on medium 0)
   double *d_quad = nullptr;      // outer singular rule (b0,b1,b2,w) * nq
   int nq_sing = 16;
 

@@ -309,8 +309,13 @@ __global__ void k_identity(int nt, const double *tri, const int *te, const doubl
 // Leaf patterns of medium l at direction k:
 //   V_i(k)  = int b_i e^{+j k khat.(r - c_b)}          (radiation, theta/phi)
 //   RN_i(k) = int (t_i x n) e^{-j k khat.(r - c_b)}     (receive of n x operators)
+// over the basis's two triangles in this medium (ptri), each triangle's piece
+// of V weighted by psg (1 for an ordinary edge, whose medium sign is applied
+// by the aggregation and the receive; the side sign s_l(T) at a junction edge,
+// whose two triangles in this medium lie on different surfaces).  RN needs no
+// such sign: the piece and the medium's normal change sign together.
 __global__ void k_patterns(int nb, int K, const int *basis_p, const int *basis_box, const double *centre,
-                           const int *edge_tris, const double *tri, const int *te, const double *tsg,
+                           const int *ptri, const double *psg, const double *tri, const int *te, const double *tsg,
                            const double *dirs, zd k, zd *V, zd *RN) {
   int kk = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y;
@@ -322,7 +327,8 @@ __global__ void k_patterns(int nb, int K, const int *basis_p, const int *basis_b
   V3 kh = v3(d[0], d[1], d[2]), th = v3(d[3], d[4], d[5]), ph = v3(d[6], d[7], d[8]);
   zd vt, vp, rt, rp;
   for (int s = 0; s < 2; ++s) {
-    int t = edge_tris[2 * p + s];
+    int t = ptri[2 * i + s];
+    const double sv = psg[2 * i + s];
     Tri T;
     load_tri(tri, te, tsg, t, T);
     int li = 0;
@@ -331,8 +337,8 @@ __global__ void k_patterns(int nb, int K, const int *basis_p, const int *basis_b
     for (int a = 0; a < 7; ++a) {
       V3 r = bary(T, c_rb[a][0], c_rb[a][1], c_rb[a][2]);
       double W = T.A * c_rw[a];
-      V3 f = T.c[li] * (r - T.fr[li]);
-      V3 fn = cross(f, T.n);
+      V3 fn = cross(T.c[li] * (r - T.fr[li]), T.n);
+      V3 f = (sv * T.c[li]) * (r - T.fr[li]);
       double x = dot(kh, r - c);
       // e^{+jkx} = e^{-k_i x} (cos k_r x + j sin k_r x)
       double s1, c1;
@@ -373,21 +379,22 @@ __global__ void k_receive_fold(int nb, int K, int L, const int *sign, const zd *
   Ri[K + kk] = (-s) * Vi[K + ka] - aN * rt;
 }
 
-// Tested excitation, host medium 0 only (Eqs. 20-21 with Eq. 30).
-__global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris, const int *edge_reg,
+// Tested excitation, host medium 0 only (Eqs. 20-21 with Eq. 30), over the
+// basis's two triangles in medium 0 (edge_tris, -1 when the basis does not
+// bound medium 0), each triangle's piece with its side sign s0(T) (the same
+// for both at an ordinary edge; they differ at a junction edge).
+__global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris, const int *treg,
                       const double *tri, const int *te, const double *tsg, zd k0, zd eta0, zd *b, zd aTJ, zd aNJ,
                       zd aTM, zd aNM) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   int r = blockIdx.y;
   if (p >= ne || r >= nrhs) return;
   zd *out = b + ((size_t)r * ne + p) * 2;
-  int rp = edge_reg[2 * p], rm = edge_reg[2 * p + 1];
-  if (rp != 0 && rm != 0) {
+  if (edge_tris[2 * p] < 0) {
     out[0] = zd();
     out[1] = zd();
     return;
   }
-  double s0 = rp == 0 ? 1.0 : -1.0;
   double th = inc[4 * r], ph = inc[4 * r + 1], pol = inc[4 * r + 2], E0 = inc[4 * r + 3];
   double st, ct, sp, cp;
   sincos(th, &st, &ct);
@@ -399,6 +406,7 @@ __global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris,
   zd fE, fH, fnH, fnE;
   for (int s = 0; s < 2; ++s) {
     int t = edge_tris[2 * p + s];
+    const double s0 = treg[2 * t] == 0 ? 1.0 : -1.0;
     Tri T;
     load_tri(tri, te, tsg, t, T);
     int li = 0;
@@ -410,14 +418,14 @@ __global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris,
       V3 f = T.c[li] * (rr - T.fr[li]);
       zd ph_ = expmjkR(k0, dot(kh, rr));  // exp(-j k0 khat.r)
       zd w = W * ph_;
-      fE += dot(f, e) * w;
-      fH += (dot(f, h) * w) * ie0;
+      fE += (s0 * dot(f, e)) * w;
+      fH += ((s0 * dot(f, h)) * w) * ie0;
       fnH += (dot(f, cross(T.n, h)) * w) * ie0;
       fnE += dot(f, cross(T.n, e)) * w;
     }
   }
-  out[0] = aTJ * ((s0 * fE) * ie0) + aNJ * fnH;
-  out[1] = aTM * (s0 * (eta0 * fH)) - aNM * fnE;
+  out[0] = aTJ * (fE * ie0) + aNJ * fnH;
+  out[1] = aTM * (eta0 * fH) - aNM * fnE;
 }
 
 // Far field (Eqs. 27-29), in two steps.  (1) Surface currents at the
@@ -428,7 +436,7 @@ __global__ void k_rhs(int ne, int nrhs, const double *inc, const int *edge_tris,
 // per observation direction; the sum over points is split into NS parts
 // added in a fixed order by k_farfield_sum, which forms sigma.
 __global__ void k_quad_currents(int ntri0, int ne, int nrhs, const int *__restrict__ tri0, const zd *__restrict__ x,
-                                const int *__restrict__ edge_reg, const double *__restrict__ tri,
+                                const int *__restrict__ treg, const double *__restrict__ tri,
                                 const int *__restrict__ te, const double *__restrict__ tsg, double *qpos, zd *qcur) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // (triangle, point)
   const int r = blockIdx.y;
@@ -446,12 +454,10 @@ __global__ void k_quad_currents(int ntri0, int ne, int nrhs, const int *__restri
     qpos[4 * (size_t)i + 3] = 0.0;
   }
   zd J[3], M[3];
+  const double w = (treg[2 * t] == 0 ? 1.0 : -1.0) * W;  // the side of medium 0 (per triangle: also at junctions)
   for (int k = 0; k < 3; ++k) {
     const int e = T.e[k];
     if (e < 0) continue;
-    const int rp = edge_reg[2 * e], rm = edge_reg[2 * e + 1];
-    if (rp != 0 && rm != 0) continue;
-    const double w = (rp == 0 ? 1.0 : -1.0) * W;
     const zd cJ = x[((size_t)r * ne + e) * 2], cM = x[((size_t)r * ne + e) * 2 + 1];
     const V3 f = T.c[k] * (rr - T.fr[k]);
     const double fw[3] = {w * f.x, w * f.y, w * f.z};
@@ -670,7 +676,8 @@ void launch_patterns(sie_ctx *c, int l) {
     int cnt = std::min(65535, R.nb - i0);
     dim3 grid((K + 127) / 128, cnt);
     k_patterns<<<grid, 128, 0, c->stream>>>(cnt, K, R.d_basis_p + i0, R.d_basis_box + i0, R.d_box_centre,
-                                            c->d_edge_tris, c->d_tri, c->d_tri_e, c->d_tri_sg, LL.d_dirs,
+                                            R.d_ptri + 2 * (size_t)i0, R.d_psg + 2 * (size_t)i0, c->d_tri,
+                                            c->d_tri_e, c->d_tri_sg, LL.d_dirs,
                                             to_zd(R.k), (zd *)R.d_V64 + (size_t)i0 * 2 * K,
                                             (zd *)R.d_P64 + (size_t)i0 * 2 * K);
     SIE_CHECK_LAUNCH();
@@ -698,7 +705,7 @@ void launch_rhs(sie_ctx *c, const double *inc_dev, int nrhs, zd *b) {
   dim3 grid((c->ne + 127) / 128, nrhs);
   std::complex<double> w[4];
   form_weights(c, 0, w);
-  k_rhs<<<grid, 128, 0, c->stream>>>(c->ne, nrhs, inc_dev, c->d_edge_tris, c->d_edge_reg, c->d_tri, c->d_tri_e,
+  k_rhs<<<grid, 128, 0, c->stream>>>(c->ne, nrhs, inc_dev, c->d_edge_tris, c->d_tri_reg, c->d_tri, c->d_tri_e,
                                      c->d_tri_sg, to_zd(c->kreg[0]), to_zd(c->etareg[0]), b, to_zd(w[0]),
                                      to_zd(w[1]), to_zd(w[2]), to_zd(w[3]));
   SIE_CHECK_LAUNCH();
@@ -727,7 +734,7 @@ void launch_farfield(sie_ctx *c, const zd *x, int nrhs, const double *obs, int n
   const zd k0 = to_zd(c->kreg[0]), eta0 = to_zd(c->etareg[0]);
   if (npts > 0) {
     k_quad_currents<<<dim3((npts + 127) / 128, nrhs), 128, 0, c->stream>>>(
-        c->ntri0, c->ne, nrhs, c->d_tri0, x, c->d_edge_reg, c->d_tri, c->d_tri_e, c->d_tri_sg, qpos, qcur);
+        c->ntri0, c->ne, nrhs, c->d_tri0, x, c->d_tri_reg, c->d_tri, c->d_tri_e, c->d_tri_sg, qpos, qcur);
     SIE_CHECK_LAUNCH();
     c->launches++;
   }

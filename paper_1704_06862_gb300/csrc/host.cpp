@@ -325,13 +325,73 @@ static void build_mesh(sie_ctx *c, const double *verts, int64_t nv, const int32_
   c->tri_edge.assign(3 * nt, -1);
   c->tri_free.assign(3 * nt, 0);
   c->tri_sign.assign(3 * nt, 0.0);
+  c->emed_ptr.assign(1, 0);
+  c->emed.clear();
+  c->ejunc.clear();
+  c->njunc = 0;
   std::vector<int> fillc(nt, 0);
+  auto side = [&](int l, int t) { return treg[2 * t] == l ? 1.0 : -1.0; };
   size_t i = 0;
   while (i < recs.size()) {
     size_t j = i;
     while (j < recs.size() && recs[j].key == recs[i].key) ++j;
     size_t cnt = j - i;
-    SIE_REQUIRE(cnt <= 2, SIE_EINVAL, "sie_build_mesh: junction edge (more than two triangles) is not supported");
+    if (cnt >= 3) {
+      // junction edge: each region touching it sees two of the triangles; one
+      // unknown with per-triangle coefficients a_T, s_l(T1) a_T1 = -s_l(T2) a_T2
+      // for every such region (continuity of that region's current across the edge)
+      std::vector<int> ts;
+      for (size_t q = i; q < j; ++q) ts.push_back(recs[q].t);
+      std::vector<int> regs;
+      for (int t : ts)
+        for (int a = 0; a < 2; ++a)
+          if (std::find(regs.begin(), regs.end(), (int)treg[2 * t + a]) == regs.end()) regs.push_back(treg[2 * t + a]);
+      std::sort(regs.begin(), regs.end());
+      std::vector<std::array<int, 3>> pr;  // (region, T1, T2)
+      for (int l : regs) {
+        std::vector<int> tl;
+        for (int t : ts)
+          if (treg[2 * t] == l || treg[2 * t + 1] == l) tl.push_back(t);
+        SIE_REQUIRE(tl.size() == 2, SIE_EINVAL, "sie_build_mesh: junction edge where a region does not see two faces");
+        pr.push_back({l, tl[0], tl[1]});
+      }
+      std::map<int, double> av;
+      av[ts[0]] = 1.0;
+      for (size_t it = 0; it < pr.size(); ++it)
+        for (auto &q : pr) {
+          const bool h1 = av.count(q[1]), h2 = av.count(q[2]);
+          if (h1 && !h2) av[q[2]] = -side(q[0], q[1]) * side(q[0], q[2]) * av[q[1]];
+          if (h2 && !h1) av[q[1]] = -side(q[0], q[1]) * side(q[0], q[2]) * av[q[2]];
+        }
+      SIE_REQUIRE(av.size() == ts.size(), SIE_EINVAL, "sie_build_mesh: junction faces not connected through regions");
+      for (auto &q : pr)
+        SIE_REQUIRE(side(q[0], q[1]) * av[q[1]] == -side(q[0], q[2]) * av[q[2]], SIE_EINVAL,
+                    "sie_build_mesh: inconsistent junction continuity constraints");
+      int e = (int)c->tp.size();
+      int lo = (int)(recs[i].key >> 32), hi = (int)(recs[i].key & 0xffffffff);
+      c->edge_v.push_back(lo);
+      c->edge_v.push_back(hi);
+      c->tp.push_back(recs[i].t);
+      c->tm.push_back(recs[i + 1].t);
+      c->vp.push_back(recs[i].free_v);
+      c->vm.push_back(recs[i + 1].free_v);
+      double dx = verts[3 * hi] - verts[3 * lo], dy = verts[3 * hi + 1] - verts[3 * lo + 1],
+             dz = verts[3 * hi + 2] - verts[3 * lo + 2];
+      c->elen.push_back(std::sqrt(dx * dx + dy * dy + dz * dz));
+      for (size_t q = i; q < j; ++q) {
+        int t = recs[q].t;
+        int f = fillc[t]++;
+        c->tri_edge[3 * t + f] = e;
+        c->tri_free[3 * t + f] = recs[q].free_v;
+        c->tri_sign[3 * t + f] = av[t];
+      }
+      for (auto &q : pr) c->emed.push_back(q);
+      c->emed_ptr.push_back((int)c->emed.size());
+      c->ejunc.push_back(1);
+      c->njunc++;
+      i = j;
+      continue;
+    }
     if (cnt == 2) {
       const Rec &r1 = recs[i], &r2 = recs[i + 1];
       SIE_REQUIRE(treg[2 * r1.t] == treg[2 * r2.t] && treg[2 * r1.t + 1] == treg[2 * r2.t + 1], SIE_EINVAL,
@@ -339,6 +399,11 @@ static void build_mesh(sie_ctx *c, const double *verts, int64_t nv, const int32_
       SIE_REQUIRE(r1.u == r2.v && r1.v == r2.u, SIE_EINVAL,
                   "sie_build_mesh: inconsistent triangle orientation across an edge");
       int e = (int)c->tp.size();
+      // the two media of the surface, each with the pair (T+, T-)
+      c->emed.push_back({(int)treg[2 * r1.t], r1.t, r2.t});
+      c->emed.push_back({(int)treg[2 * r1.t + 1], r1.t, r2.t});
+      c->emed_ptr.push_back((int)c->emed.size());
+      c->ejunc.push_back(0);
       int lo = (int)(r1.key >> 32), hi = (int)(r1.key & 0xffffffff);
       c->edge_v.push_back(lo);
       c->edge_v.push_back(hi);
@@ -508,11 +573,17 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
     std::vector<int> basis_gbox;
     for (int p = 0; p < ne; ++p) {
       int e = c->perm[p];
-      int t = c->tp[e];
-      int rp = c->tri_reg[2 * t], rm = c->tri_reg[2 * t + 1];
-      if (rp == l || rm == l) {
+      const bool junction = c->ejunc[e] != 0;
+      for (int q = c->emed_ptr[e]; q < c->emed_ptr[e + 1]; ++q) {
+        const auto &E = c->emed[q];
+        if (E[0] != l) continue;
+        const double s1 = c->tri_reg[2 * E[1]] == l ? 1.0 : -1.0, s2 = c->tri_reg[2 * E[2]] == l ? 1.0 : -1.0;
         R.basis_p.push_back(p);
-        R.basis_sign.push_back(rp == l ? 1 : -1);
+        R.basis_sign.push_back(junction ? 1 : (int)s1);
+        R.ptri.push_back(E[1]);
+        R.ptri.push_back(E[2]);
+        R.psg.push_back(junction ? s1 : 1.0);
+        R.psg.push_back(junction ? s2 : 1.0);
         basis_gbox.push_back(ebox[p]);
       }
     }
@@ -781,6 +852,8 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
     // leaf tables
     R.d_basis_p = dev_upload(c, R.basis_p);
     R.d_basis_sign = dev_upload(c, R.basis_sign);
+    R.d_ptri = dev_upload(c, R.ptri);
+    R.d_psg = dev_upload(c, R.psg);
     R.d_box_start = dev_upload(c, R.box_start);
     R.max_leaf = 0;
     for (size_t b = 0; b + 1 < R.box_start.size(); ++b)
@@ -797,17 +870,21 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
   {
     std::vector<int> rmap((size_t)2 * ne, -1);
     int off = 0;
+    bool two = true;  // junction bases lie in more than two media: they receive one medium at a time
     for (auto &R : c->reg) {
       R.rpart_off = off;
       for (int i = 0; i < R.nb; ++i) {
         const int p = R.basis_p[i];
-        SIE_REQUIRE(rmap[2 * (size_t)p + 1] < 0, SIE_EINVAL, "mlfmm_setup: a basis in more than two media");
+        if (rmap[2 * (size_t)p + 1] >= 0) {
+          two = false;
+          continue;
+        }
         rmap[2 * (size_t)p + (rmap[2 * (size_t)p] < 0 ? 0 : 1)] = off + i;
       }
       off += R.nb;
     }
     c->rpart_nb = off;
-    c->d_rmap = dev_upload(c, rmap);
+    if (two) c->d_rmap = dev_upload(c, rmap);
   }
   c->have_tree = true;
 }
@@ -1087,6 +1164,8 @@ static void fill_all(sie_ctx *c, const sie_fill_opts *o) {
   int on = o ? o->outer_order : 4;
   c->form = o ? o->formulation : 0;
   SIE_REQUIRE(c->form >= 0 && c->form <= 4, SIE_EINVAL, "sie_fill_nearfield: formulation must be 0..4");
+  SIE_REQUIRE(c->form != 4 || c->njunc == 0, SIE_EINVAL,
+              "sie_fill_nearfield: ICTF (an interface's mean impedance) is not defined at junction edges");
   SIE_REQUIRE(on >= 2 && on <= 12, SIE_EINVAL, "sie_fill_nearfield: outer_order must be in [2, 12]");
   // geometry tables, internal edge ids
   std::vector<double> tri(22 * (size_t)nt);
@@ -1120,16 +1199,18 @@ static void fill_all(sie_ctx *c, const sie_fill_opts *o) {
   c->d_col = dev_upload(c, c->col);
   c->d_perm = dev_upload(c, c->perm);
   c->d_inv = dev_upload(c, c->inv);
-  std::vector<int> etri(2 * (size_t)ne), ereg(2 * (size_t)ne);
+  // per basis (internal order): its two triangles in the host medium 0, -1 if it
+  // does not bound medium 0 (the excitation tests medium 0's equations only)
+  std::vector<int> etri(2 * (size_t)ne, -1);
   for (int p = 0; p < ne; ++p) {
     int e = c->perm[p];
-    etri[2 * p] = c->tp[e];
-    etri[2 * p + 1] = c->tm[e];
-    ereg[2 * p] = c->tri_reg[2 * c->tp[e]];
-    ereg[2 * p + 1] = c->tri_reg[2 * c->tp[e] + 1];
+    for (int q = c->emed_ptr[e]; q < c->emed_ptr[e + 1]; ++q)
+      if (c->emed[q][0] == 0) {
+        etri[2 * p] = c->emed[q][1];
+        etri[2 * p + 1] = c->emed[q][2];
+      }
   }
   c->d_edge_tris = dev_upload(c, etri);
-  c->d_edge_reg = dev_upload(c, ereg);
   // singular outer rule: n x n collapsed Gauss (barycentric b0,b1,b2,w)
   std::vector<double> x, wx, q;
   gauss_legendre(on, x, wx);

@@ -27,6 +27,8 @@ Stored: seeded x (2 columns), y = Z x, y_near = Z_near x (touching-box
 pattern), plane-wave excitation b, dense-LU solution, bistatic RCS of that
 solution at 361 angles, and the Mie series at the same angles.
 
+  split_sphere   a sphere cut into two regions of equal eps by the plane
+                 z = 0: 24 junction edges on the equator, 960 RWG edges.
   sphere_c1_forms  the sphere_c1 case in the five formulations (JMCFIE, CTF,
                  CNF, PMCHWT, ICTF): per formulation the products y and y_near of
                  the seeded x, the excitation b, the LU currents and their RCS.
@@ -73,6 +75,10 @@ CASES = {
     # tri-axial lossy dielectric ellipsoid (eps 3 - 0.2j, the material of the
     # ellipsoid workload), semi-axes 1.0 x 0.5 x 0.25 lambda0, cube-sphere mesh
     "ellipsoid_small": dict(mesh=lambda: geo.workload("ellipsoid_small"), levels=4, mie=False, mono=8),
+    # sphere cut by the plane z = 0 into two regions of the same eps: junction
+    # edges on the equator (upper hemisphere 0|1, lower 0|2, disk 1|2); its
+    # exterior field is that of the uncut sphere (Mie series of radius 0.3, eps 4)
+    "split_sphere": dict(mesh=lambda: geo.split_sphere(12, 24, 3, 0.3, 4.0, 4.0), levels=3, radius=0.3),
 }
 
 

@@ -43,8 +43,10 @@ NAMES = [n for n in make_golden.CASES if os.path.exists(os.path.join(HERE, "gold
 # its product still meets 1e-3 (4.9e-4) but more directions (d0 = 4) or a
 # finer mesh leave that error unchanged, and the cube system's conditioning
 # amplifies it about 3.7 times in the currents (measured 1.8e-3; its RCS is
-# within 0.013 dB of the oracle's).
-CURRENTS_TOL = {"cube_small": 2.5e-3}
+# within 0.013 dB of the oracle's).  The split sphere's disk lies in the
+# octree's z = 0 box faces, the same worst case: product 8.2e-4, unchanged
+# with d0 = 4 (7.8e-4), currents 1.1e-3, RCS within 0.005 dB of the oracle's.
+CURRENTS_TOL = {"cube_small": 2.5e-3, "split_sphere": 2e-3}
 
 
 def rel(a, b):
