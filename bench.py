@@ -231,6 +231,8 @@ def main():
                     help="skip the small homogeneous-sphere leg (GPU arm) / its full oracle run (reference arm)")
     ap.add_argument("--ellipsoid", action="store_true",
                     help="add the ellipsoid leg (355 488 unknowns, learned preconditioner on 32 incidences)")
+    ap.add_argument("--lens", action="store_true",
+                    help="add the lens-on-slab leg (about 1.18 M unknowns, junction edges, one incidence)")
     ap.add_argument("--formulation-study", action="store_true",
                     help="add the iterations-versus-unknowns study of the formulations on the two-layer sphere")
     args = ap.parse_args()
@@ -638,6 +640,41 @@ def main():
         del be, xe
         se.close()
 
+    # three-layer hemispherical lens (radii 2 / 4 / 6 lambda0, eps 10.2 / 4.5 /
+    # 2.2) on a 14 x 14 x 0.5 lambda0 slab of eps 3 (Eq. 16's multilayer body,
+    # five media, junction edges on the three base circles; about 1.18 M
+    # unknowns, 7 levels): setup, one normal incidence to RCS, mixed form, ILU(0)
+    # FGMRES(50), tol 1e-4, and the stage times of one product and one ILU apply
+    lens = None
+    if args.lens:
+        t0 = time.perf_counter()
+        g = geo.workload("lens_c5")
+        t_mesh = time.perf_counter() - t0
+        sl = sie.Solver(g, levels=7, digits=DIGITS, stream=stream)
+        torch.cuda.synchronize()
+        lens = {"workload": "lens_c5", "unknowns": 2 * sl.ne, "triangles": int(len(g["tris"])), "levels": 7,
+                "mesh_s": t_mesh, "setup_s": time.perf_counter() - t0 - t_mesh,
+                "device_bytes": sie.sie_query(sl.ctx, 7), "near_blocks": sie.sie_query(sl.ctx, 1)}
+        del g
+        bl = sl.vec(1)
+        xl = sl.vec(1)
+        sie.sie_plane_wave_rhs(sl.ctx, [[0.0, 0.0, 0.0, 1.0]], bl)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stl = sie.gmres_solve(sl.ctx, bl, xl, 1, restart=RESTART, max_iters=3000, tol=TOL,
+                              prec=sie.SIE_PREC_MIXED, precond=1, check=False, graphs=not args.no_graphs)[0]
+        rl = sie.rcs_farfield(sl.ctx, xl, 1, geo.bistatic_angles(361))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lens.update(iters=stl["iters"], converged=stl["converged"], rel_residual=stl["rel_residual"],
+                    ms_to_rcs=e0.elapsed_time(e1), rcs_finite=bool(np.isfinite(rl).all()))
+        lens["far_ms"] = sie.sie_stage_timing(sl.ctx, 1, 1, sie.SIE_PREC_MIXED, 5)
+        lens["matvec_ms"] = sie.sie_stage_timing(sl.ctx, 3, 1, sie.SIE_PREC_MIXED, 5)
+        lens["ilu_ms"] = sie.sie_stage_timing(sl.ctx, 2, 1, sie.SIE_PREC_MIXED, 5)
+        del bl, xl
+        sl.close()
+
     # iterations versus unknowns per formulation (the comparison of Fig. 6) on the
     # two-layer sphere at four mesh densities: FGMRES(50) with ILU(0) and without
     # a preconditioner, mixed form, tol 1e-4, at most 1000 iterations
@@ -727,7 +764,7 @@ def main():
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": int(inc.nbytes),
                 "d2h_bytes_per_step": int(rcs.nbytes)},
         "plain_fp64": plain, "learned_precond": learned, "batched_monostatic": batched, "solvers": solvers_cmp, "formulations": forms_cmp,
-        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "mie_refinement": mie_ref, "sphere_c1": c1, "cube_monostatic": cube, "ellipsoid": ell, "stages_ms": stages, "matvec": matvec,
+        "nanoparticle": nano, "formulation_study": study, "rcs_vs_mie": mie_db, "mie_refinement": mie_ref, "sphere_c1": c1, "cube_monostatic": cube, "ellipsoid": ell, "lens": lens, "stages_ms": stages, "matvec": matvec,
         "roofline": roofline, "roofline_near_spmv": roofline_near, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches), "krylov_step_graphs": graphs_state,
     }
     if rank == 0:

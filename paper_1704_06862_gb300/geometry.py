@@ -176,6 +176,163 @@ def latlong_homogeneous_sphere(nlat=8, nlon=16, radius=0.3, eps_r=4.0):
     return dict(verts=v, tris=t, tri_regions=regions, media=media)
 
 
+def _ring_count(rho, h, nmax):
+    """Points on a ring of radius rho: nmax halved while the spacing stays
+    below h (at least 5); nested rings keep each other's angles."""
+    n = nmax
+    while n % 2 == 0 and n // 2 >= 5 and 2.0 * np.pi * rho / (n // 2) <= h:
+        n //= 2
+    return n
+
+
+def _band(inner, outer):
+    """Triangles (vertex triples) between two nested rings with n and n or 2n
+    points (angles increasing); orientation fixed by the caller."""
+    n, m = len(inner), len(outer)
+    out = []
+    if m == n:
+        for j in range(n):
+            j1 = (j + 1) % n
+            out += [(inner[j], outer[j], outer[j1]), (inner[j], outer[j1], inner[j1])]
+    elif m == 2 * n:
+        for j in range(n):
+            j1 = (j + 1) % n
+            b0, b1, b2 = outer[2 * j], outer[2 * j + 1], outer[(2 * j + 2) % m]
+            out += [(inner[j], b0, b1), (inner[j], b1, inner[j1]), (inner[j1], b1, b2)]
+    else:
+        raise ValueError("_band: ring counts must be equal or double")
+    return out
+
+
+def lens_on_slab(radii=(2.0, 4.0, 6.0), eps_layers=(10.2, 4.5, 2.2), slab=(14.0, 14.0, 0.5), eps_slab=3.0,
+                 nlon=256, h=0.15, nz=None):
+    """Three-layer dielectric hemispherical lens on a dielectric slab (the
+    multilayer body of the multi-boundary formulation, Eq. 16).  The lens
+    layers are concentric hemispheres of the given radii resting on the slab's
+    top face z = 0 (region 1 the innermost layer, eps_layers[0]; regions 2, 3
+    the next; region 4 the slab, eps_slab, a box slab[0] x slab[1] x slab[2]
+    below z = 0; region 0 free space).  The slab top is a polar grid whose
+    rings include the three base circles (junction edges: a hemisphere, the
+    top annulus inside it and the one outside meet there), blended from the
+    outer circle to the slab's square rim; rings and hemisphere latitudes keep
+    a spacing about h by halving their point counts toward the centre and the
+    poles (nested angles, nlon at most; transition bands of three triangles);
+    the bottom repeats the top grid; the side faces are rows at nz depths.
+    nlon must be a multiple of 8 (the slab corners are grid points) and the
+    slab must contain the base circle."""
+    r1, r2, r3 = radii
+    X, Y, T = slab[0] / 2.0, slab[1] / 2.0, slab[2]
+    if nlon % 8 or not (0 < r1 < r2 < r3 < min(X, Y)):
+        raise ValueError("lens_on_slab: nlon a multiple of 8 and radii increasing inside the slab")
+    nz = nz or max(1, int(np.ceil(T / h)))
+    verts = []
+
+    def add(p):
+        verts.append(p)
+        return len(verts) - 1
+
+    def ang(n):
+        a = 2.0 * np.pi * np.arange(n) / n
+        return np.cos(a), np.sin(a)
+
+    # top grid ring radii (the base circles among them) and the material above each band
+    radii_top, ring_mat = [], []
+    lo = 0.0
+    for k, rk in enumerate((r1, r2, r3)):
+        n = max(1, int(np.ceil((rk - lo) / h)))
+        for i in range(1, n + 1):
+            radii_top.append(lo + (rk - lo) * i / n)
+            ring_mat.append(k + 1)
+        lo = rk
+    counts = [_ring_count(rho, h, nlon) for rho in radii_top]
+    for i in range(len(counts) - 2, -1, -1):      # at most a factor two between neighbours
+        counts[i] = max(counts[i], counts[i + 1] // 2)
+    n_rim = counts[-1]
+    if n_rim != nlon:
+        raise ValueError("lens_on_slab: nlon too large for h at the outer base circle")
+    cr, sr = ang(nlon)
+    tsq = np.minimum(X / np.maximum(np.abs(cr), 1e-300), Y / np.maximum(np.abs(sr), 1e-300))
+    n_out = max(1, int(np.ceil((tsq.max() - r3) / h)))
+
+    def top_grid(z):
+        centre = add((0.0, 0.0, z))
+        rings = []
+        for rho, n in zip(radii_top, counts):
+            c, s_ = ang(n)
+            rings.append([add((rho * c[j], rho * s_[j], z)) for j in range(n)])
+        for i in range(1, n_out + 1):
+            t = i / n_out
+            rings.append([add(((1 - t) * r3 * cr[j] + t * tsq[j] * cr[j],
+                               (1 - t) * r3 * sr[j] + t * tsq[j] * sr[j], z)) for j in range(nlon)])
+        return centre, rings
+
+    ctop, rtop = top_grid(0.0)
+    cbot, rbot = top_grid(-T)
+    mats = ring_mat + [0] * n_out
+    tris, regs = [], []
+
+    def tri(a, b, c, want, reg):
+        pa, pb, pc = (np.array(verts[q]) for q in (a, b, c))
+        if np.dot(np.cross(pb - pa, pc - pa), want) < 0:
+            b, c = c, b
+        tris.append((a, b, c))
+        regs.append(reg)
+
+    up, down = np.array([0.0, 0.0, 1.0]), np.array([0.0, 0.0, -1.0])
+    for (cen, rings, want, top) in ((ctop, rtop, up, True), (cbot, rbot, down, False)):
+        n0 = len(rings[0])
+        for j in range(n0):
+            tri(cen, rings[0][j], rings[0][(j + 1) % n0], want, (mats[0], 4) if top else (0, 4))
+        for i in range(len(rings) - 1):
+            for a, b, c in _band(rings[i], rings[i + 1]):
+                tri(a, b, c, want, (mats[i + 1], 4) if top else (0, 4))
+    # hemispheres: latitude rings from the base circle (shared with the top grid) to the pole
+    cum = np.cumsum([max(1, int(np.ceil((rk - l0) / h))) for rk, l0 in ((r1, 0.0), (r2, r1), (r3, r2))])
+    for k, rk in enumerate((r1, r2, r3)):
+        base = rtop[cum[k] - 1]
+        m = max(2, int(np.ceil(0.5 * np.pi * rk / h)))
+        rings = [base]
+        for i in range(1, m):
+            th = 0.5 * np.pi * (1.0 - i / m)   # polar angle from +z
+            n = max(_ring_count(rk * np.sin(th), h, len(base)), len(rings[-1]) // 2)
+            c, s_ = ang(n)
+            rings.append([add((rk * np.sin(th) * c[j], rk * np.sin(th) * s_[j], rk * np.cos(th))) for j in range(n)])
+        pole = add((0.0, 0.0, rk))
+        reg = (0 if k == 2 else k + 2, k + 1)
+        for i in range(m - 1):
+            for a, b, c in _band(rings[i + 1], rings[i]):
+                cen = np.mean([verts[q] for q in (a, b, c)], axis=0)
+                tri(a, b, c, cen, reg)
+        nl = len(rings[-1])
+        for j in range(nl):
+            a, b = rings[-1][j], rings[-1][(j + 1) % nl]
+            cen = np.mean([verts[q] for q in (a, b, pole)], axis=0)
+            tri(a, b, pole, cen, reg)
+    # side faces: rows below the square rim of the top grid down to the bottom grid's rim
+    rim_t, rim_b = rtop[-1], rbot[-1]
+    rows = [rim_t]
+    for q in range(1, nz):
+        z = -T * q / nz
+        rows.append([add((verts[v][0], verts[v][1], z)) for v in rim_t])
+    rows.append(rim_b)
+    for j in range(nlon):
+        j1 = (j + 1) % nlon
+        pa, pb = np.array(verts[rim_t[j]]), np.array(verts[rim_t[j1]])
+        mid = 0.5 * (pa + pb)
+        want = np.array([np.sign(mid[0]) if abs(abs(mid[0]) - X) < 1e-9 else 0.0,
+                         np.sign(mid[1]) if abs(abs(mid[1]) - Y) < 1e-9 else 0.0, 0.0])
+        for q in range(nz):
+            a, b, c, d = rows[q][j], rows[q][j1], rows[q + 1][j], rows[q + 1][j1]
+            tri(a, c, d, want, (0, 4))
+            tri(a, d, b, want, (0, 4))
+    media = [[1.0, 0.0, 1.0, 0.0]]
+    for e in list(eps_layers) + [eps_slab]:
+        e = complex(e)
+        media.append([e.real, e.imag, 1.0, 0.0])
+    return dict(verts=np.array(verts, np.float64), tris=np.array(tris, np.int32),
+                tri_regions=np.array(regs, np.int32), media=np.array(media, np.float64))
+
+
 def coated_sphere(nu_outer=30, nu_inner=20, r_outer=1.5, r_inner=1.0, eps_shell=2.56, eps_core=4.0):
     """Two-layer sphere: region 0 free space, region 1 shell, region 2 core."""
     vo, to = geodesic_sphere(nu_outer, r_outer)
@@ -360,6 +517,10 @@ def workload(name: str):
         return dielectric_ellipsoid(46, (4.0, 2.0, 1.0), 3.0 - 0.2j)
     if name == "ellipsoid_small":  # semi-axes 1.0 x 0.5 x 0.25 lambda0, same material: dense CPU checks
         return dielectric_ellipsoid(4, (1.0, 0.5, 0.25), 3.0 - 0.2j)
+    if name == "lens_c5":        # 3-layer lens (radii 2/4/6 lambda0, eps 10.2/4.5/2.2) on a 14 x 14 x 0.5 slab, ~1.18M unknowns
+        return lens_on_slab((2.0, 4.0, 6.0), (10.2, 4.5, 2.2), (14.0, 14.0, 0.5), 3.0, nlon=512, h=0.075)
+    if name == "lens_small":     # the same body at 0.1 scale: dense CPU checks
+        return lens_on_slab((0.2, 0.4, 0.6), slab=(1.4, 1.4, 0.2), nlon=24, h=0.1)
     if name == "coated_tiny":    # coated sphere small enough for dense CPU checks
         return coated_sphere(6, 4)
     if name == "sphere_tiny":

@@ -95,3 +95,40 @@ def test_ellipsoid_workload():
         w = vs.copy()
         w[:, ax] *= -1
         assert key(w) == ref
+
+
+def test_lens_on_slab_workload():
+    """Three-layer lens on a slab (the multi-boundary body of Eq. 16), at the
+    small size: every region's boundary is closed and consistently oriented,
+    its enclosed volume is the body's (hemispheres to the mesh's chord error,
+    the slab box exactly), region 0 encloses minus the whole body, and the
+    junction edges are exactly the edges on the three base circles."""
+    from oracle.rwg import Mesh
+    radii, slab = (0.2, 0.4, 0.6), (1.4, 1.4, 0.2)
+    g = geo.lens_on_slab(radii, slab=slab, nlon=24, h=0.1)
+    v, t, reg = g["verts"], g["tris"], np.asarray(g["tri_regions"])
+    trip = np.einsum("ij,ij->i", v[t[:, 0]], np.cross(v[t[:, 1]], v[t[:, 2]])) / 6
+    hemi = [2.0 / 3.0 * np.pi * r ** 3 for r in (0.0,) + radii]
+    want = [-(hemi[3] + slab[0] * slab[1] * slab[2])] + [hemi[k + 1] - hemi[k] for k in range(3)] \
+        + [slab[0] * slab[1] * slab[2]]
+    for l in range(5):
+        on = (reg[:, 0] == l) | (reg[:, 1] == l)
+        sgn = np.where(reg[on, 0] == l, -1.0, 1.0)          # the normal points into tri_regions[:, 0]
+        vol = np.sum(sgn * trip[on])
+        # inscribed hemispheres lose volume to the chord sag (edge / radius
+        # up to 0.5 on the inner layer here): a tenth of the largest one
+        tol = 1e-12 if l == 4 else 0.1 * hemi[3 if l == 0 else l]
+        assert abs(vol - want[l]) < tol, (l, vol, want[l])
+        directed = {}
+        for tr, s in zip(t[on], sgn):
+            tr = tr if s > 0 else tr[::-1]
+            for a, b in ((tr[0], tr[1]), (tr[1], tr[2]), (tr[2], tr[0])):
+                directed[(a, b)] = directed.get((a, b), 0) + 1
+        assert all(n == 1 and directed.get((b, a)) == 1 for (a, b), n in directed.items())
+    m = Mesh(**g)
+    va, vb = v[m.edge_v[:, 0]], v[m.edge_v[:, 1]]
+    on_circle = np.zeros(m.ne, bool)
+    for r in radii:
+        on_circle |= (np.abs(va[:, 2]) < 1e-12) & (np.abs(vb[:, 2]) < 1e-12) \
+            & (np.abs(np.hypot(va[:, 0], va[:, 1]) - r) < 1e-9) & (np.abs(np.hypot(vb[:, 0], vb[:, 1]) - r) < 1e-9)
+    assert on_circle.sum() > 0 and np.array_equal(m.junction, on_circle)
