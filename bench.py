@@ -232,7 +232,7 @@ def main():
     ap.add_argument("--ellipsoid", action="store_true",
                     help="add the ellipsoid leg (355 488 unknowns, learned preconditioner on 32 incidences)")
     ap.add_argument("--lens", action="store_true",
-                    help="add the lens-on-slab leg (about 1.18 M unknowns, junction edges, one incidence)")
+                    help="add the lens-on-slab leg (1 189 264 unknowns, junction edges, one incidence)")
     ap.add_argument("--formulation-study", action="store_true",
                     help="add the iterations-versus-unknowns study of the formulations on the two-layer sphere")
     args = ap.parse_args()
@@ -640,9 +640,9 @@ def main():
         del be, xe
         se.close()
 
-    # three-layer hemispherical lens (radii 2 / 4 / 6 lambda0, eps 10.2 / 4.5 /
-    # 2.2) on a 14 x 14 x 0.5 lambda0 slab of eps 3 (Eq. 16's multilayer body,
-    # five media, junction edges on the three base circles; about 1.18 M
+    # three-layer hemispherical lens (radii 1.5 / 3 / 6 lambda0, eps 10.2 / 4.5
+    # / 2.2) on a 14 x 14 x 0.5 lambda0 slab of eps 2.2 (Eq. 16's multilayer
+    # body, five media, junction edges on the three base circles; 1 189 264
     # unknowns, 7 levels): setup, one normal incidence to RCS, mixed form, ILU(0)
     # FGMRES(50), tol 1e-4, and the stage times of one product and one ILU apply
     lens = None

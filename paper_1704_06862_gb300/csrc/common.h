@@ -147,7 +147,11 @@ struct RegionHost {
   std::vector<int> basis_sign;  // s_l
   std::vector<int> box_start;   // leaf boxes: [nleaf+1] ranges into the basis list
   int max_leaf = 0;             // most bases in one leaf box
-  std::vector<LevelHost> lev;   // index = level number; levels 2..leaf carry tables
+  std::vector<LevelHost> lev;   // index = level number; levels top..leaf carry tables
+  // coarsest level whose interaction lists are not empty (2 unless the medium's
+  // bases sit in mutually adjacent boxes there): coarser levels translate
+  // nothing, so they are neither aggregated into nor given directions
+  int top = 2;
   int *d_basis_p = nullptr, *d_basis_sign = nullptr, *d_box_start = nullptr, *d_basis_box = nullptr;
   // per basis of the medium: its two triangles in this medium and the sign of
   // each triangle's piece in the radiation pattern (1, 1 for an ordinary edge,

@@ -82,12 +82,12 @@ void ensure_work(sie_ctx *c, int64_t nrhs) {
   c->d_yf = dev_alloc(c, n * sizeof(zf));
   size_t scratch = 0;
   for (auto &R : c->reg) {
-    for (int l = 2; l < (int)R.lev.size(); ++l) {
+    for (int l = R.top; l < (int)R.lev.size(); ++l) {
       LevelHost &L = R.lev[l];
       size_t sz = (size_t)L.nbox * 4 * L.K * nrhs * sizeof(zd);
       L.d_S = dev_alloc(c, sz);
       L.d_I = dev_alloc(c, sz);
-      if (l >= 3)  // children's interpolated patterns in the parent sampling
+      if (l > R.top)  // children's interpolated patterns in the parent sampling
         scratch = std::max(scratch, (size_t)L.nbox * 4 * R.lev[l - 1].K * nrhs * sizeof(zd));
     }
   }
@@ -672,22 +672,28 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
         B.il_ptr.push_back((int)B.il_src.size());
       }
     }
+    R.top = leaf;
+    for (int lv = 2; lv <= leaf; ++lv)
+      if (!R.lev[lv].il_src.empty()) {
+        R.top = lv;
+        break;
+      }
     // directions and tables; the truncation follows |k|: in a lossy medium
     // the addition theorem converges at the rate set by the modulus of k d,
     // not its real part (a metal's k is nearly imaginary)
     double kr = std::abs(R.k);
-    for (int lv = 2; lv <= leaf; ++lv) {
+    for (int lv = R.top; lv <= leaf; ++lv) {
       LevelHost &B = R.lev[lv];
       B.L = trunc_L(kr, B.a, digits);
     }
     std::vector<Dirs> dirs(levels);
-    for (int lv = 2; lv <= leaf; ++lv) {
+    for (int lv = R.top; lv <= leaf; ++lv) {
       dirs[lv] = make_dirs(R.lev[lv].L);
       R.lev[lv].K = dirs[lv].K;
     }
     cd kc = R.k;
     cd pref = kc * kc / (16.0 * PI * PI);
-    for (int lv = 2; lv <= leaf; ++lv) {
+    for (int lv = R.top; lv <= leaf; ++lv) {
       LevelHost &B = R.lev[lv];
       const Dirs &Dd = dirs[lv];
       int K = Dd.K, L = Dd.L;
@@ -844,7 +850,7 @@ static void setup_tree(sie_ctx *c, int levels, double digits) {
         B.d_ch_ptr = dev_upload(c, B.ch_ptr);
         B.d_ch_idx = dev_upload(c, B.ch_idx);
       }
-      if (lv > 2) {
+      if (lv > R.top) {
         B.d_oct = dev_upload(c, B.oct);
         B.d_parent = dev_upload(c, B.parent);
       }

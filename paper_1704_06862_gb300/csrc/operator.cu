@@ -444,7 +444,10 @@ __global__ void __launch_bounds__(256) k_interp_up(int Kc, int Lc, int Kp, int L
 // The parent's column pairs (jp, jp + Np/2) are taken cw at a time (a chunk:
 // G holds only its 2 cw columns), so a large parent sampling fits in shared
 // memory; with one chunk (cw = Np/2) the arithmetic is that of a single pass.
-template <typename T, int JM>
+// GT: the interpolation tables are read from global memory (through L1)
+// instead of shared memory, for the electrically large boxes of dense media
+// whose child pattern and tables together exceed it; same arithmetic.
+template <typename T, int JM, bool GT>
 __global__ void __launch_bounds__(256) k_interp_up_chunked(int Kc, int Lc, int Kp, int Lp, int nrhs, int cw_max,
                                                   const int *__restrict__ oct, const T *__restrict__ tpc,
                                                   const T *__restrict__ tpp, const T *__restrict__ Phi,
@@ -460,14 +463,17 @@ __global__ void __launch_bounds__(256) k_interp_up_chunked(int Kc, int Lc, int K
   T *PhT = reinterpret_cast<T *>(G + (size_t)Q * nthc * G2);  // [Nc][Np]
   T *Tps = PhT + Nc * Np, *Tms = Tps + nthp * nthc;            // [nthp][nthc]
   const int c = blockIdx.x, r = blockIdx.y, o = oct[c], tid = threadIdx.x, NT = blockDim.x;
-  for (int i = tid; i < Np * Nc; i += NT) {
-    const int jp = i / Nc, jc = i - jp * Nc;
-    PhT[jc * Np + jp] = Phi[i];
+  if (!GT) {
+    for (int i = tid; i < Np * Nc; i += NT) {
+      const int jp = i / Nc, jc = i - jp * Nc;
+      PhT[jc * Np + jp] = Phi[i];
+    }
+    for (int i = tid; i < nthp * nthc; i += NT) {
+      Tps[i] = Thp[i];
+      Tms[i] = Thm[i];
+    }
   }
-  for (int i = tid; i < nthp * nthc; i += NT) {
-    Tps[i] = Thp[i];
-    Tms[i] = Thm[i];
-  }
+  const T *Tpa = GT ? Thp : Tps, *Tma = GT ? Thm : Tms;
   const int nib = (nthp + IP - 1) / IP;
   for (int jm0 = 0; jm0 < 2; jm0 += JM) {
     __syncthreads();
@@ -486,7 +492,8 @@ __global__ void __launch_bounds__(256) k_interp_up_chunked(int Kc, int Lc, int K
         const int ic = task / cw, jl = task - ic * cw, jp = j0 + jl;
         cx<T> g0[Q], g1[Q];
         for (int jc = 0; jc < Nc; ++jc) {
-          const T f0 = PhT[jc * Np + jp], f1 = PhT[jc * Np + jp + hp];
+          const T f0 = GT ? Phi[(size_t)jp * Nc + jc] : PhT[jc * Np + jp];
+          const T f1 = GT ? Phi[(size_t)(jp + hp) * Nc + jc] : PhT[jc * Np + jp + hp];
 #pragma unroll
           for (int q = 0; q < Q; ++q) {
             const cx<T> a = A[(size_t)q * Kc + ic * Nc + jc];
@@ -516,7 +523,7 @@ __global__ void __launch_bounds__(256) k_interp_up_chunked(int Kc, int Lc, int K
 #pragma unroll
           for (int k = 0; k < IP; ++k) {
             const int ip = min(ip0 + k, nthp - 1);
-            const T a = Tps[ip * nthc + ic], bq = Tms[ip * nthc + ic];
+            const T a = Tpa[ip * nthc + ic], bq = Tma[ip * nthc + ic];
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
               h0[k][q].re = fma(a, ga[q].re, fma(bq, gb[q].re, h0[k][q].re));
@@ -689,8 +696,9 @@ __global__ void __launch_bounds__(256) k_anterp_dn(int Kc, int Lc, int Kp, int L
 // The parent's column pairs are taken cw at a time (a chunk of A and G in
 // shared memory); each chunk adds its part of the phi-transpose sums into the
 // child, columns jp of the chunk first, then their partners jp + Np/2 (with
-// one chunk, the order of a single pass over jp = 0 .. Np - 1).
-template <typename T, int JM>
+// one chunk, the order of a single pass over jp = 0 .. Np - 1).  GT: the tables
+// are read from global memory, as in k_interp_up_chunked.
+template <typename T, int JM, bool GT>
 __global__ void __launch_bounds__(256) k_anterp_dn_chunked(int Kc, int Lc, int Kp, int Lp, int nrhs, int cw_max,
                                                   const int *__restrict__ parent, const int *__restrict__ oct,
                                                   const T *__restrict__ tpc, const T *__restrict__ tpp,
@@ -706,11 +714,14 @@ __global__ void __launch_bounds__(256) k_anterp_dn_chunked(int Kc, int Lc, int K
   T *Ps = reinterpret_cast<T *>(G + (size_t)Q * nthc * G2);  // Phi [Np][Nc]
   T *Tps = Ps + Np * Nc, *Tms = Tps + nthp * nthc;           // [nthp][nthc]
   const int c = blockIdx.x, r = blockIdx.y, pb = parent[c], o = oct[c], tid = threadIdx.x, NT = blockDim.x;
-  for (int i = tid; i < Np * Nc; i += NT) Ps[i] = Phi[i];
-  for (int i = tid; i < nthp * nthc; i += NT) {
-    Tps[i] = Thp[i];
-    Tms[i] = Thm[i];
+  if (!GT) {
+    for (int i = tid; i < Np * Nc; i += NT) Ps[i] = Phi[i];
+    for (int i = tid; i < nthp * nthc; i += NT) {
+      Tps[i] = Thp[i];
+      Tms[i] = Thm[i];
+    }
   }
+  const T *Psa = GT ? Phi : Ps, *Tpa = GT ? Thp : Tps, *Tma = GT ? Thm : Tms;
   const int nicb = (nthc + IC - 1) / IC;
   for (int jm0 = 0; jm0 < 2; jm0 += JM) {
     for (int j0 = 0; j0 < hp; j0 += CW) {
@@ -751,7 +762,7 @@ __global__ void __launch_bounds__(256) k_anterp_dn_chunked(int Kc, int Lc, int K
 #pragma unroll
           for (int k = 0; k < IC; ++k) {
             const int ic = min(ic0 + k, nthc - 1);
-            const T w1 = Tps[ip * nthc + ic], w2 = Tms[ip * nthc + ic];
+            const T w1 = Tpa[ip * nthc + ic], w2 = Tma[ip * nthc + ic];
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
               g0[k][q].re = fma(w1, aa[q].re, fma(w2, ab[q].re, g0[k][q].re));
@@ -781,7 +792,7 @@ __global__ void __launch_bounds__(256) k_anterp_dn_chunked(int Kc, int Lc, int K
         // G columns jj: jp = j0 + jj for jj < cw, j0 + jj - cw + hp after (one chunk: jp = jj)
         for (int jj = 0; jj < 2 * cw; ++jj) {
           const int jp = j0 + (jj < cw ? jj : jj - cw + hp), gj = jj < cw ? jj : jj - cw + CW;
-          const T f0 = Ps[jp * Nc + jc], f1 = Ps[jp * Nc + jc + hc];
+          const T f0 = Psa[jp * Nc + jc], f1 = Psa[jp * Nc + jc + hc];
 #pragma unroll
           for (int q = 0; q < Q; ++q) {
             const cx<T> g = G[((size_t)q * nthc + ic) * G2 + gj];
@@ -2039,32 +2050,42 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
       }
     }
     // upward pass: interpolate + shift each child, then sum into parents
-    for (int lv = leaf; lv >= 3; --lv) {
+    for (int lv = leaf; lv > G.top; --lv) {
       LevelHost &C = G.lev[lv], &P = G.lev[lv - 1];
       const int nthc = C.L + 1, Nc = 2 * C.L + 2, Np = 2 * P.L + 2, nthp = P.L + 1;
       const size_t tabs = ((size_t)Np * Nc + 2 * (size_t)nthp * nthc) * sizeof(T);
       // one source (J or M) per pass: fewer registers, more CTAs per SM (measured
       // faster than both at once); the parent's column pairs in chunks of cw
-      // (all of them when they fit in shared memory)
-      auto smem_for = [&](int cw) { return ((size_t)3 * C.K + (size_t)3 * nthc * 2 * cw) * sizeof(cx<T>) + tabs; };
+      // (all of them when they fit in shared memory; the tables read from
+      // global memory when even one column pair does not fit beside them)
+      auto smem_for = [&](int cw, bool gt) {
+        return ((size_t)3 * C.K + (size_t)3 * nthc * 2 * cw) * sizeof(cx<T>) + (gt ? 0 : tabs);
+      };
       int cw = P.L + 1;
-      while (cw > 1 && smem_for(cw) > 200 * 1024) cw = (cw + 1) / 2;
-      const size_t smem = smem_for(cw);
+      bool gt = false;
+      while (cw > 1 && smem_for(cw, false) > 200 * 1024) cw = (cw + 1) / 2;
+      if (smem_for(cw, false) > 227 * 1024) {
+        gt = true;
+        cw = P.L + 1;
+        while (cw > 1 && smem_for(cw, true) > 200 * 1024) cw = (cw + 1) / 2;
+      }
+      const size_t smem = smem_for(cw, gt);
       cx<T> *Y = (cx<T> *)((char *)c->d_scratch + gi * c->scratch_region);
       dim3 grid(C.nbox, R);
       // threads sized to the larger task list (phi step: theta rows x column pairs;
       // theta step: row pairs x column pairs), so small levels fit more CTAs per SM
       const int tasks = std::max(nthc * cw, (nthp + 1) / 2 * cw);
       const int threads = std::min(256, std::max(64, (tasks + 31) / 32 * 32));
-      if (cw == P.L + 1) {  // the whole parent sampling at once: the single-pass kernel
+      if (cw == P.L + 1 && !gt) {  // the whole parent sampling at once: the single-pass kernel
         set_smem(k_interp_up<T, 1>, smem);
         k_interp_up<T, 1><<<grid, threads, smem, st>>>(
             C.K, C.L, P.K, P.L, R, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
             (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
             (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
       } else {
-        set_smem(k_interp_up_chunked<T, 1>, smem);
-        k_interp_up_chunked<T, 1><<<grid, threads, smem, st>>>(
+        auto kern = gt ? k_interp_up_chunked<T, 1, true> : k_interp_up_chunked<T, 1, false>;
+        set_smem(kern, smem);
+        kern<<<grid, threads, smem, st>>>(
             C.K, C.L, P.K, P.L, R, cw, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
             (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
             (const cx<T> *)tsel<T>::up(P), (const cx<T> *)C.d_S, Y);
@@ -2077,7 +2098,7 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
     }
     // translations at every level: per target box for few right-hand sides (more
     // CTAs in flight), by sibling groups for blocks of 8 or more (fewer loads)
-    for (int lv = 2; lv <= leaf; ++lv) {
+    for (int lv = G.top; lv <= leaf; ++lv) {
       LevelHost &B = G.lev[lv];
       const bool by_group = B.ngroups > 0 && (c->tune_m2l >= 0 ? (c->tune_m2l == 1 && R >= 2) : R >= 8);
       // (split groups measured slower than per target box for one right-hand side: 0.603 vs 0.558 ms far field)
@@ -2109,28 +2130,37 @@ void op_far(sie_ctx *c, const cx<T> *x, cx<TY> *y, int nrhs, bool forked) {
       c->launches++;
     }
     // downward pass: shift + anterpolate (exact transpose) into children
-    for (int lv = 2; lv < leaf; ++lv) {
+    for (int lv = G.top; lv < leaf; ++lv) {
       LevelHost &P = G.lev[lv], &C = G.lev[lv + 1];
       const int nthc = C.L + 1, Nc = 2 * C.L + 2, Np = 2 * P.L + 2, nthp = P.L + 1;
       const size_t tabs = ((size_t)Np * Nc + 2 * (size_t)nthp * nthc) * sizeof(T);
       // one source (J or M) per pass; the parent's column pairs in chunks of cw
       // (all of them when they fit in shared memory)
-      auto smem_for = [&](int cw) { return ((size_t)3 * nthp * 2 * cw + (size_t)3 * nthc * 2 * cw) * sizeof(cx<T>) + tabs; };
+      auto smem_for = [&](int cw, bool gt) {
+        return ((size_t)3 * nthp * 2 * cw + (size_t)3 * nthc * 2 * cw) * sizeof(cx<T>) + (gt ? 0 : tabs);
+      };
       int cw = P.L + 1;
-      while (cw > 1 && smem_for(cw) > 200 * 1024) cw = (cw + 1) / 2;
-      const size_t smem = smem_for(cw);
+      bool gt = false;
+      while (cw > 1 && smem_for(cw, false) > 200 * 1024) cw = (cw + 1) / 2;
+      if (smem_for(cw, false) > 227 * 1024) {
+        gt = true;
+        cw = P.L + 1;
+        while (cw > 1 && smem_for(cw, true) > 200 * 1024) cw = (cw + 1) / 2;
+      }
+      const size_t smem = smem_for(cw, gt);
       dim3 grid(C.nbox, R);
       const int tasks = std::max((nthc + 1) / 2 * cw, nthc * (C.L + 1));
       const int threads = std::min(256, std::max(64, (tasks + 31) / 32 * 32));
-      if (cw == P.L + 1) {  // the whole parent sampling at once: the single-pass kernel
+      if (cw == P.L + 1 && !gt) {  // the whole parent sampling at once: the single-pass kernel
         set_smem(k_anterp_dn<T, 1>, smem);
         k_anterp_dn<T, 1><<<grid, threads, smem, st>>>(
             C.K, C.L, P.K, P.L, R, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
             (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
             (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);
       } else {
-        set_smem(k_anterp_dn_chunked<T, 1>, smem);
-        k_anterp_dn_chunked<T, 1><<<grid, threads, smem, st>>>(
+        auto kern = gt ? k_anterp_dn_chunked<T, 1, true> : k_anterp_dn_chunked<T, 1, false>;
+        set_smem(kern, smem);
+        kern<<<grid, threads, smem, st>>>(
             C.K, C.L, P.K, P.L, R, cw, C.d_parent, C.d_oct, (const T *)tsel<T>::tp(C), (const T *)tsel<T>::tp(P),
             (const T *)tsel<T>::Phi(P), (const T *)tsel<T>::Thp(P), (const T *)tsel<T>::Thm(P),
             (const cx<T> *)tsel<T>::dn(P), (const cx<T> *)P.d_I, (cx<T> *)C.d_I);

@@ -204,7 +204,7 @@ def _band(inner, outer):
     return out
 
 
-def lens_on_slab(radii=(2.0, 4.0, 6.0), eps_layers=(10.2, 4.5, 2.2), slab=(14.0, 14.0, 0.5), eps_slab=3.0,
+def lens_on_slab(radii=(1.5, 3.0, 6.0), eps_layers=(10.2, 4.5, 2.2), slab=(14.0, 14.0, 0.5), eps_slab=2.2,
                  nlon=256, h=0.15, nz=None):
     """Three-layer dielectric hemispherical lens on a dielectric slab (the
     multilayer body of the multi-boundary formulation, Eq. 16).  The lens
@@ -517,10 +517,10 @@ def workload(name: str):
         return dielectric_ellipsoid(46, (4.0, 2.0, 1.0), 3.0 - 0.2j)
     if name == "ellipsoid_small":  # semi-axes 1.0 x 0.5 x 0.25 lambda0, same material: dense CPU checks
         return dielectric_ellipsoid(4, (1.0, 0.5, 0.25), 3.0 - 0.2j)
-    if name == "lens_c5":        # 3-layer lens (radii 2/4/6 lambda0, eps 10.2/4.5/2.2) on a 14 x 14 x 0.5 slab, ~1.18M unknowns
-        return lens_on_slab((2.0, 4.0, 6.0), (10.2, 4.5, 2.2), (14.0, 14.0, 0.5), 3.0, nlon=512, h=0.075)
+    if name == "lens_c5":        # 3-layer lens (radii 1.5/3/6, eps 10.2/4.5/2.2) on a 14 x 14 x 0.5 slab (eps 2.2), 1 189 264 unknowns
+        return lens_on_slab((1.5, 3.0, 6.0), (10.2, 4.5, 2.2), (14.0, 14.0, 0.5), 2.2, nlon=512, h=0.07)
     if name == "lens_small":     # the same body at 0.1 scale: dense CPU checks
-        return lens_on_slab((0.2, 0.4, 0.6), slab=(1.4, 1.4, 0.2), nlon=24, h=0.1)
+        return lens_on_slab((0.15, 0.3, 0.6), slab=(1.4, 1.4, 0.2), nlon=24, h=0.1)
     if name == "coated_tiny":    # coated sphere small enough for dense CPU checks
         return coated_sphere(6, 4)
     if name == "sphere_tiny":

@@ -81,10 +81,10 @@ CASES = {
     # edges on the equator (upper hemisphere 0|1, lower 0|2, disk 1|2); its
     # exterior field is that of the uncut sphere (Mie series of radius 0.3, eps 4)
     "split_sphere": dict(mesh=lambda: geo.split_sphere(12, 24, 3, 0.3, 4.0, 4.0), levels=3, radius=0.3),
-    # three-layer hemispherical lens (eps 10.2 / 4.5 / 2.2, radii 0.2 / 0.4 /
-    # 0.6 lambda0) on a 1.4 x 1.4 x 0.2 lambda0 slab of eps 3: five media,
+    # three-layer hemispherical lens (eps 10.2 / 4.5 / 2.2, radii 0.15 / 0.3 /
+    # 0.6 lambda0) on a 1.4 x 1.4 x 0.2 lambda0 slab of eps 2.2: five media,
     # junction edges on the three base circles; no closed form
-    "lens_small": dict(mesh=lambda: geo.lens_on_slab((0.2, 0.4, 0.6), slab=(1.4, 1.4, 0.2), nlon=24, h=0.1),
+    "lens_small": dict(mesh=lambda: geo.workload("lens_small"),
                        levels=3, mie=False),
 }
 

@@ -3,7 +3,9 @@ unknowns, 5-level MLFMM, the launch configuration bench.py times; plasmonic
 coated nanoparticle, 30 720 unknowns, 4-level MLFMM, bench.py's nanoparticle
 leg; lossy dielectric cube, 104 976 unknowns, 5-level MLFMM, bench.py's
 monostatic sweep; lossy dielectric ellipsoid, 355 488 unknowns, 7-level
-MLFMM, bench.py's learned-preconditioner leg): the product
+MLFMM, bench.py's learned-preconditioner leg; three-layer lens on a slab,
+1 189 264 unknowns, five media, 7-level MLFMM, bench.py's lens leg, whose
+sample adds junction edges): the product
 is checked on rows the oracle computes one by one (dense JMCFIE rows of the
 sampled bases against all bases), and the near-field entries of those rows
 element by element.
@@ -22,7 +24,8 @@ from oracle import fill, tree  # noqa: E402
 from oracle.rwg import Mesh  # noqa: E402
 
 
-@pytest.fixture(scope="module", params=[("coated_c2", 5), ("nanoparticle", 4), ("cube_c3", 5), ("ellipsoid_c4", 7)])
+@pytest.fixture(scope="module", params=[("coated_c2", 5), ("nanoparticle", 4), ("cube_c3", 5), ("ellipsoid_c4", 7),
+                                                ("lens_c5", 7)], ids=lambda p: p[0])
 def full(request):
     import __graft_entry__ as g
     g.build()
@@ -38,8 +41,12 @@ def test_sampled_rows(full):
     s, m, levels = full
     assert s.ne == m.ne
     rng = np.random.default_rng(2017)
-    rows = np.sort(rng.choice(m.ne, 8, replace=False))
-    Zr = fill.assemble(m, rows=rows)                      # [16, 2 ne]
+    if m.junction.any():        # five media: dense rows cost five times as much; two junction rows among them
+        rows = np.sort(np.concatenate([rng.choice(np.nonzero(~m.junction)[0], 4, replace=False),
+                                       rng.choice(np.nonzero(m.junction)[0], 2, replace=False)]))
+    else:
+        rows = np.sort(rng.choice(m.ne, 8, replace=False))
+    Zr = fill.assemble(m, rows=rows)                      # [2 len(rows), 2 ne]
     x = geo.random_coefficients(2 * m.ne, 1, seed=1234)
     ref = Zr @ x[0]
     xd = torch.from_numpy(x.reshape(1, m.ne, 2)).cuda()

@@ -226,8 +226,8 @@ def test_tensor_core_aggregation(case):
     product of the first two columns within 1e-3 of the stored dense oracle
     product and of all columns within 1e-4 of the FP64 product."""
     name, s, d = case
-    if name not in ("coated_r075", "cube_small", "nanoparticle"):
-        pytest.skip("three media, sharp edges and the most leaf directions suffice")
+    if name not in ("coated_r075", "cube_small", "nanoparticle", "lens_small"):
+        pytest.skip("three media, sharp edges, the most leaf directions and junction edges suffice")
     R = 40
     ph = np.exp(1j * np.linspace(0.0, 2.0, R // 2))
     X = np.concatenate([d["x"] * p for p in ph])          # [R, 2 ne]; rows 0, 1 are the stored vectors
@@ -273,8 +273,8 @@ def test_tensor_core_receive(case):
     columns within 1e-3 of the stored dense oracle product and of all
     columns within 1e-4 of the FP64 product."""
     name, s, d = case
-    if name not in ("coated_r075", "cube_small", "nanoparticle"):
-        pytest.skip("three media, sharp edges and the most leaf directions suffice")
+    if name not in ("coated_r075", "cube_small", "nanoparticle", "lens_small"):
+        pytest.skip("three media, sharp edges, the most leaf directions and junction edges suffice")
     R = 40
     ph = np.exp(1j * np.linspace(0.0, 2.0, R // 2))
     X = np.concatenate([d["x"] * p for p in ph])
@@ -313,10 +313,11 @@ def test_tensor_core_receive(case):
 def test_block_product_equals_single_products(case):
     """A block of 9 right-hand sides (the translations then run by sibling
     groups) gives the products of the right-hand sides one at a time (per
-    target box), in both precisions."""
+    target box), in both precisions; on a layered body and on one with
+    junction edges (bases in more than two media)."""
     name, s, d = case
-    if name != "coated_r075":
-        pytest.skip("one case suffices")
+    if name not in ("coated_r075", "lens_small"):
+        pytest.skip("two cases suffice")
     x = np.concatenate([d["x"]] * 5)[:9] * np.arange(1, 10)[:, None]
     xb = _dev(x, s.ne)
     for prec, tol in ((sie.SIE_PREC_FP64, 1e-12), (sie.SIE_PREC_MIXED, 1e-5)):

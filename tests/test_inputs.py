@@ -104,7 +104,7 @@ def test_lens_on_slab_workload():
     the slab box exactly), region 0 encloses minus the whole body, and the
     junction edges are exactly the edges on the three base circles."""
     from oracle.rwg import Mesh
-    radii, slab = (0.2, 0.4, 0.6), (1.4, 1.4, 0.2)
+    radii, slab = (0.15, 0.3, 0.6), (1.4, 1.4, 0.2)
     g = geo.lens_on_slab(radii, slab=slab, nlon=24, h=0.1)
     v, t, reg = g["verts"], g["tris"], np.asarray(g["tri_regions"])
     trip = np.einsum("ij,ij->i", v[t[:, 0]], np.cross(v[t[:, 1]], v[t[:, 2]])) / 6
@@ -116,8 +116,9 @@ def test_lens_on_slab_workload():
         sgn = np.where(reg[on, 0] == l, -1.0, 1.0)          # the normal points into tri_regions[:, 0]
         vol = np.sum(sgn * trip[on])
         # inscribed hemispheres lose volume to the chord sag (edge / radius
-        # up to 0.5 on the inner layer here): a tenth of the largest one
-        tol = 1e-12 if l == 4 else 0.1 * hemi[3 if l == 0 else l]
+        # about 0.7 on the inner layer here, 12 %): 15 % of the outer one; a
+        # wrong side or material flips or moves whole layers (100 % and more)
+        tol = 1e-12 if l == 4 else 0.15 * hemi[3 if l == 0 else l]
         assert abs(vol - want[l]) < tol, (l, vol, want[l])
         directed = {}
         for tr, s in zip(t[on], sgn):
