@@ -232,7 +232,10 @@ def main():
     ap.add_argument("--ellipsoid", action="store_true",
                     help="add the ellipsoid leg (355 488 unknowns, learned preconditioner on 32 incidences)")
     ap.add_argument("--lens", action="store_true",
-                    help="add the lens-on-slab leg (1 189 264 unknowns, junction edges, one incidence)")
+                    help="add the lens-on-slab leg (1 189 264 unknowns, junction edges): one incidence in the "
+                         "mixed and the plain FP64 forms, a monostatic sweep in blocks, the learned preconditioner")
+    ap.add_argument("--lens-sweep", type=int, default=64, help="incidences of the lens's monostatic sweep (0: skip)")
+    ap.add_argument("--lens-block", type=int, default=16, help="right-hand sides per block of the lens sweep")
     ap.add_argument("--formulation-study", action="store_true",
                     help="add the iterations-versus-unknowns study of the formulations on the two-layer sphere")
     args = ap.parse_args()
@@ -644,7 +647,11 @@ def main():
     # / 2.2) on a 14 x 14 x 0.5 lambda0 slab of eps 2.2 (Eq. 16's multilayer
     # body, five media, junction edges on the three base circles; 1 189 264
     # unknowns, 7 levels): setup, one normal incidence to RCS, mixed form, ILU(0)
-    # FGMRES(50), tol 1e-4, and the stage times of one product and one ILU apply
+    # FGMRES(50), tol 1e-4, and the stage times of one product and one ILU apply;
+    # the same incidence in the plain FP64 form (its RCS the check of the mixed
+    # one); a monostatic sweep (theta_i uniform in [0, 180] degrees, phi = 0) in
+    # blocks of right-hand sides; the learned preconditioner trained on 8
+    # incidences (uniform on the sphere, seed 2017), one held out (seed 2018)
     lens = None
     if args.lens:
         t0 = time.perf_counter()
@@ -672,7 +679,79 @@ def main():
         lens["far_ms"] = sie.sie_stage_timing(sl.ctx, 1, 1, sie.SIE_PREC_MIXED, 5)
         lens["matvec_ms"] = sie.sie_stage_timing(sl.ctx, 3, 1, sie.SIE_PREC_MIXED, 5)
         lens["ilu_ms"] = sie.sie_stage_timing(sl.ctx, 2, 1, sie.SIE_PREC_MIXED, 5)
+        lens["far_fp64_ms"] = sie.sie_stage_timing(sl.ctx, 1, 1, sie.SIE_PREC_FP64, 2)
+        # plain FP64 form of the same incidence: its RCS is the mixed form's check
+        xl.zero_()
+        e0.record(stream)
+        st64 = sie.gmres_solve(sl.ctx, bl, xl, 1, restart=RESTART, max_iters=3000, tol=TOL,
+                               prec=sie.SIE_PREC_FP64, precond=1, check=False, graphs=not args.no_graphs)[0]
+        r64 = sie.rcs_farfield(sl.ctx, xl, 1, geo.bistatic_angles(361))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ok = r64[0, :, 0] > r64[0, :, 0].max() * 1e-3
+        dbl = np.abs(10 * np.log10(rl[0, ok, 0]) - 10 * np.log10(r64[0, ok, 0]))
+        lens["fp64"] = {"iters": st64["iters"], "converged": st64["converged"], "ms_to_rcs": e0.elapsed_time(e1)}
+        lens.update(rcs_vs_fp64_mean_db=float(dbl.mean()), rcs_vs_fp64_max_db=float(dbl.max()))
         del bl, xl
+        if args.lens_sweep > 0:
+            inc_l = geo.monostatic_incidences(args.lens_sweep)
+            B = min(args.lens_block, args.lens_sweep)
+            bs = sl.vec(B)
+            xs = sl.vec(B)
+            sie.sie_plane_wave_rhs(sl.ctx, inc_l[:B], bs)      # untimed: work buffers of the block size
+            sie.gmres_solve(sl.ctx, bs, xs, B, restart=RESTART, max_iters=2, tol=TOL, prec=sie.SIE_PREC_MIXED,
+                            precond=1, check=False, graphs=not args.no_graphs)
+            torch.cuda.synchronize()
+            mono_l = np.zeros(args.lens_sweep)
+            iters_l, conv_l = [], True
+            e0.record(stream)
+            for i0 in range(0, args.lens_sweep, B):
+                nb_ = min(B, args.lens_sweep - i0)
+                sie.sie_plane_wave_rhs(sl.ctx, inc_l[i0:i0 + nb_], bs[:nb_])
+                xs.zero_()
+                stb = sie.gmres_solve(sl.ctx, bs[:nb_], xs[:nb_], nb_, restart=RESTART, max_iters=3000, tol=TOL,
+                                      prec=sie.SIE_PREC_MIXED, precond=1, check=False, graphs=not args.no_graphs)
+                obs_l = np.stack([inc_l[i0:i0 + nb_, 0], inc_l[i0:i0 + nb_, 1]], axis=1)
+                rb = sie.rcs_farfield_prec(sl.ctx, xs[:nb_], nb_, obs_l, sie.SIE_PREC_MIXED)
+                mono_l[i0:i0 + nb_] = rb[np.arange(nb_), np.arange(nb_), 0]
+                iters_l += [t["iters"] for t in stb]
+                conv_l = conv_l and all(t["converged"] for t in stb)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_l = e0.elapsed_time(e1)
+            lens["sweep"] = {"incidences": args.lens_sweep, "block": B, "ms_sweep": ms_l,
+                             "rhs_per_s": args.lens_sweep / (ms_l / 1e3), "ms_per_rhs": ms_l / args.lens_sweep,
+                             "iters_mean": float(np.mean(iters_l)), "iters_max": max(iters_l),
+                             "all_converged": conv_l, "device_bytes": sie.sie_query(sl.ctx, 7),
+                             "monostatic_rcs_dbsm": [round(float(v), 3) for v in 10 * np.log10(mono_l)]}
+            del bs, xs
+
+        def uniform_incidences_l(n, seed):
+            rng = np.random.default_rng(seed)
+            return np.stack([np.arccos(rng.uniform(-1, 1, n)), rng.uniform(0, 2 * np.pi, n), np.zeros(n),
+                             np.ones(n)], axis=1)
+
+        try:
+            lens["train"] = sie.nnprec_train(sl.ctx, uniform_incidences_l(8, 2017), record_restart=5, max_pairs=256,
+                                             epochs=12, batch=4096, lr=1e-3, seed=7)
+        except sie.SieError as e:            # reported in the line, the rest of the bench still runs
+            lens["train"] = {"enabled": False, "error": str(e)}
+        bh = sl.vec(1)
+        xh = sl.vec(1)
+        sie.sie_plane_wave_rhs(sl.ctx, uniform_incidences_l(1, 2018), bh)
+        held = {}
+        for label, pc in (("ilu", 1), ("ilu_nn", 2)):
+            if pc == 2 and not lens["train"]["enabled"]:
+                continue
+            xh.zero_()
+            e0.record(stream)
+            sth = sie.gmres_solve(sl.ctx, bh, xh, 1, restart=RESTART, max_iters=3000, tol=TOL,
+                                  prec=sie.SIE_PREC_MIXED, precond=pc, check=False, graphs=not args.no_graphs)[0]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            held[label] = {"iters": sth["iters"], "converged": sth["converged"], "ms": e0.elapsed_time(e1)}
+        lens["held_out"] = held
+        del bh, xh
         sl.close()
 
     # iterations versus unknowns per formulation (the comparison of Fig. 6) on the
