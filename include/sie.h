@@ -369,7 +369,11 @@ sie_status sie_device_status(sie_ctx *ctx);
  *   9  dense layers of the learned preconditioner with BF16 activations and
  *      weights (its forward pass): 1 (default) on the tensor cores
  *      (tcgen05, FP32 accumulation in tensor memory), 0 on the SIMT tiles.
- * Keys 2-9 are tile shapes: results agree to rounding (the tensor-core
+ *   10 CTAs of the interpolation and anterpolation per (box, right-hand
+ *      side): -1 (default: one per source J, M for one right-hand side on
+ *      levels of fewer than 2048 boxes, one for both otherwise), 0 one for
+ *      both sources in turn, 1 one per source; the same arithmetic.
+ * Keys 2-10 are tile shapes: results agree to rounding (the tensor-core
  * aggregation and receive to their FP32-level split operands, the network's
  * layers to the order of their FP32 sums), speed differs.
  * Errors: SIE_EINVAL for an unknown key or a value out of range. */

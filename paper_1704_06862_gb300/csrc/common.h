@@ -324,6 +324,10 @@ struct sie_ctx {
   int rec_tc_rb = -1;
   // learned-preconditioner layers X W^T on the tensor cores (1) or the SIMT tiles (0)
   int nn_tc = 1;
+  // interpolation and anterpolation CTAs per (box, right-hand side): -1 (one per
+  // source for one right-hand side on levels of fewer than 2048 boxes, else
+  // one), 0 one for both sources J, M, 1 one per source
+  int tune_interp_split = -1;
 };
 
 // ------------------------------------------------------------------ host helpers (host.cpp)

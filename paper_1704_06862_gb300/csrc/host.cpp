@@ -1622,6 +1622,11 @@ extern "C" sie_status sie_set_param(sie_ctx *c, int32_t key, int64_t value) {
         c->nn_tc = (int)value;
         graphs_free(c);
         break;
+      case 10:
+        SIE_REQUIRE(value >= -1 && value <= 1, SIE_EINVAL, "sie_set_param: interpolation split must be -1, 0 or 1");
+        c->tune_interp_split = (int)value;
+        graphs_free(c);
+        break;
       default:
         throw SieError{SIE_EINVAL, "sie_set_param: unknown key"};
     }

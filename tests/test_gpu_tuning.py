@@ -1,8 +1,9 @@
 """Tile shapes of the block-RHS kernels and their autotuner.
 
 Every tile shape computes the same product: the near-field, ILU and receive
-block sizes keep each right-hand side's summation order, so their results
-are identical bit for bit; the M2L forms and the tensor-core aggregation
+block sizes and the split of the interpolation and anterpolation by source
+keep each right-hand side's summation order, so their results are identical
+bit for bit; the M2L forms and the tensor-core aggregation
 change the order or the operand split, so they agree to FP32 rounding (1e-5
 of the product).  The autotuner picks valid values, keeps them in the
 context and writes them to a file that another context reads back."""
@@ -53,6 +54,7 @@ def _reset(s):
     sie.apply_tuning(s.ctx, {"near_rb": 0, "ilu_rb": 0, "aggregation": 0, "receive_rb": 0, "m2l": -1,
                              "receive_tc": -1})
     sie.sie_set_param(s.ctx, 2, 16)
+    sie.sie_set_param(s.ctx, 10, -1)
 
 
 def test_tile_shapes_give_the_same_product(solver):
@@ -75,6 +77,10 @@ def test_tile_shapes_give_the_same_product(solver):
         far_ref = _prod(s, x, 2)
         for rb in (1, 2, 4):
             sie.sie_set_param(s.ctx, 6, rb)
+            assert np.array_equal(_prod(s, x, 2), far_ref)
+        sie.sie_set_param(s.ctx, 6, 0)
+        for split in (0, 1):
+            sie.sie_set_param(s.ctx, 10, split)
             assert np.array_equal(_prod(s, x, 2), far_ref)
         scale = np.linalg.norm(ref)
         for m2l in (0, 1, 2):
