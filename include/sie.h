@@ -276,9 +276,9 @@ typedef struct {
   double gamma;             /* least-squares output scale on the held-out pairs */
   int32_t enabled;          /* 1 if the correction passed both gates; otherwise
                                precond = 2 runs as plain ILU(0) */
-  int32_t judge_iters_ilu;  /* FGMRES(50) iterations to 1e-4 on the last (held-out)
+  int32_t gate_iters_ilu;  /* FGMRES(50) iterations to 1e-4 on the last (held-out)
                                incidence with ILU(0) alone, and with the correction */
-  int32_t judge_iters_nn;   /* (-1: not run, the loss gate already rejected it) */
+  int32_t gate_iters_nn;   /* (-1: not run, the loss gate already rejected it) */
 } sie_nn_stats;
 
 sie_status nnprec_train(sie_ctx *ctx, const sie_nn_opts *opts, sie_nn_stats *stats);

@@ -281,8 +281,8 @@ class sie_nn_opts(ctypes.Structure):
 class sie_nn_stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int32), ("samples", ctypes.c_int64), ("loss_first", ctypes.c_double),
                 ("loss_last", ctypes.c_double), ("ms", ctypes.c_double), ("val_loss_ratio", ctypes.c_double),
-                ("gamma", ctypes.c_double), ("enabled", ctypes.c_int32), ("judge_iters_ilu", ctypes.c_int32),
-                ("judge_iters_nn", ctypes.c_int32)]
+                ("gamma", ctypes.c_double), ("enabled", ctypes.c_int32), ("gate_iters_ilu", ctypes.c_int32),
+                ("gate_iters_nn", ctypes.c_int32)]
 
 
 NN_PARAMS = 128 * 256 + 256 + 256 * 256 + 256 + 256 * 128 + 128
@@ -296,7 +296,7 @@ def nnprec_train(ctx, train_inc, record_restart=5, max_pairs=256, epochs=20, bat
     _check(ctx, load_library().nnprec_train(ctx, ctypes.byref(o), ctypes.byref(st)))
     return dict(pairs=st.pairs, samples=st.samples, loss_first=st.loss_first, loss_last=st.loss_last, ms=st.ms,
                 val_loss_ratio=st.val_loss_ratio, gamma=st.gamma, enabled=bool(st.enabled),
-                judge_iters_ilu=st.judge_iters_ilu, judge_iters_nn=st.judge_iters_nn)
+                gate_iters_ilu=st.gate_iters_ilu, gate_iters_nn=st.gate_iters_nn)
 
 
 def nnprec_params(ctx, params=None):

@@ -589,8 +589,8 @@ extern "C" sie_status nnprec_train(sie_ctx *c, const sie_nn_opts *o, sie_nn_stat
       it_nn = sv.iters;
       enabled = it_nn < it_ilu;
     }
-    st->judge_iters_ilu = it_ilu;
-    st->judge_iters_nn = it_nn;
+    st->gate_iters_ilu = it_ilu;
+    st->gate_iters_nn = it_nn;
     S.trained = true;
     S.ready = enabled;
     st->val_loss_ratio = ratio;

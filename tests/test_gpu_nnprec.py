@@ -94,7 +94,7 @@ def test_training_and_solve_keep_the_answer(solver):
     if st["enabled"]:
         # the gate's promise, re-checked: on the held-out incidence (the last
         # training one) at 1e-4 the network saves iterations
-        assert st["judge_iters_nn"] < st["judge_iters_ilu"]
+        assert st["gate_iters_nn"] < st["gate_iters_ilu"]
         bh = torch.zeros_like(b)
         sie.sie_plane_wave_rhs(s.ctx, [list(train[-1])], bh)
         its = {}
