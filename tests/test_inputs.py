@@ -133,3 +133,26 @@ def test_lens_on_slab_workload():
         on_circle |= (np.abs(va[:, 2]) < 1e-12) & (np.abs(vb[:, 2]) < 1e-12) \
             & (np.abs(np.hypot(va[:, 0], va[:, 1]) - r) < 1e-9) & (np.abs(np.hypot(vb[:, 0], vb[:, 1]) - r) < 1e-9)
     assert on_circle.sum() > 0 and np.array_equal(m.junction, on_circle)
+
+
+def test_lens_on_slab_rejects_degenerate_bodies():
+    """The generator refuses what it cannot mesh conformingly: point counts
+    that do not put grid points on the slab's corners, layer radii out of
+    order, a lens touching the slab's rim (the 6 lambda0 lens on a 12 lambda0
+    square), and more points (nlon) than the outer base circle keeps at spacing
+h (its ring would be halved below the nlon points of the blend to the rim)."""
+    with pytest.raises(ValueError):
+        geo.lens_on_slab((0.15, 0.3, 0.6), slab=(1.4, 1.4, 0.2), nlon=20, h=0.1)
+    with pytest.raises(ValueError):
+        geo.lens_on_slab((0.3, 0.15, 0.6), slab=(1.4, 1.4, 0.2), nlon=24, h=0.1)
+    with pytest.raises(ValueError):
+        geo.lens_on_slab((1.5, 3.0, 6.0), slab=(12.0, 12.0, 0.5), nlon=512, h=0.07)
+    with pytest.raises(ValueError):
+        geo.lens_on_slab((0.15, 0.3, 0.6), slab=(1.4, 1.4, 0.2), nlon=512, h=0.1)
+    assert geo._ring_count(1.0, 0.1, 64) == 64          # spacing 0.098 at 64 points: no halving
+    assert geo._ring_count(0.1, 0.1, 64) == 8           # 0.079 at 8 points; 4 would be below 5
+    for n, m in ((8, 8), (8, 16)):
+        tris = geo._band(list(range(n)), list(range(100, 100 + m)))
+        assert len(tris) == n + m                        # every ring segment in exactly one triangle
+    with pytest.raises(ValueError):
+        geo._band(list(range(8)), list(range(24)))
