@@ -404,7 +404,9 @@ sie_status sie_autotune(sie_ctx *ctx, int64_t nrhs, int32_t reps, int64_t *choic
  *     without ILU factors),
  *   10 Krylov step graphs of the last FGMRES solve: 1 captured and replayed,
  *     0 capture failed and the steps ran eagerly, -1 none captured,
- *   100 + 16*l + j: K (directions) of medium l at level j. */
+ *   100 + 16*l + j: K (directions) of medium l at level j (0 at levels
+ *     coarser than the medium's coarsest level with a non-empty interaction
+ *     list: they translate nothing and are skipped). */
 sie_status sie_query(const sie_ctx *ctx, int32_t key, int64_t *value);
 
 #ifdef __cplusplus
