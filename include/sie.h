@@ -112,8 +112,10 @@ typedef struct {
 /* Octree, near-field pattern, preconditioner ordering and the far-field
  * tables of every medium: direction samples, M2L translators, exact
  * separable interpolation tables (trigonometric in phi, Lagrange in cos theta),
- * shift phases, sibling groups for the block translations.
- * Requires sie_build_mesh.  Synchronous. */
+ * shift phases, sibling groups for the block translations.  Per medium, the
+ * levels coarser than the first one with a non-empty interaction list get no
+ * tables (their translations would be empty).  Requires sie_build_mesh.
+ * Synchronous. */
 sie_status mlfmm_setup(sie_ctx *ctx, const sie_mlfmm_opts *opts);
 
 typedef struct {
